@@ -1,0 +1,903 @@
+/*
+ * Oracle for the PIC-MCC/PPPM particle cycle (arXiv:1801.00972, Sec. III).
+ *
+ * TEST INFRASTRUCTURE ONLY: a plain FP64 CPU restatement of the method that
+ * the CUDA library is checked against.  Only tests, the smoke check and the
+ * benchmark's CPU-baseline leg load it.  It shares no code with the library.
+ * Build with -ffp-contract=off so that every product and sum rounds on its
+ * own (no fused multiply-add), which keeps the arithmetic order written here
+ * the arithmetic that runs.
+ *
+ * One time step, from positions x_k and velocities v_{k-1/2} (Eqs. 1-2):
+ *   1. E at the mesh nodes from Phi_k by central differences (Eq. 4; Sec. III
+ *      "electric field ... by finite differences").
+ *   2. every particle: CIC gather of E (Sec. III, same weighting as the
+ *      deposit); velocity kick (Eq. 2) and drift (Eq. 1).  A particle whose
+ *      cell is in an MD region (grain cell + direct neighbours) instead takes
+ *      md_sub substeps of dt/md_sub with E = E_PIC - E_PIC^dust + E_MD^dust
+ *      (Eqs. 5-6) and an absorption test against the grains after each
+ *      substep.  Electrodes absorb; x and y are periodic.
+ *   3. null-collision Monte Carlo collisions with the argon background
+ *      (Table I: e elastic, excitation, ionization; Ar+ elastic, charge
+ *      exchange); ionization appends an electron and an ion.
+ *   4. grain charges Q = e W (N_ion,abs - N_e,abs) (integer charge steps).
+ *   5. CIC deposit of all particles and of the grain charges into rho (Sec.
+ *      III, box shape, cell-corner nodes), in exact integer fixed point.
+ *   6. exact solve of the discrete Poisson equation (Eq. 3), periodic in x
+ *      and y, Dirichlet electrodes in z (the paper's LU back-solve gives the
+ *      same discrete solution; here a DFT in x,y and a tridiagonal solve in
+ *      z do it).
+ */
+#include "pic_oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define QE    1.602176634e-19      /* elementary charge, C          */
+#define EPS0  8.8541878128e-12     /* vacuum permittivity, F/m      */
+#define ME    9.1093837015e-31     /* electron mass, kg             */
+#define AMU   1.66053906660e-27    /* atomic mass unit, kg          */
+#define KB    1.380649e-23         /* Boltzmann constant, J/K       */
+#define MAR   (39.948 * AMU)       /* argon mass, kg                */
+#define PI_D  3.14159265358979323846
+#define WQ    16384                /* fixed-point CIC weight units per axis (2^14) */
+#define MAXG  8                    /* grains per MD cell */
+
+enum { PUR_MCC = 1, PUR_DIR = 2, PUR_NEUTRAL = 3, PUR_CHILD_DIR = 4, PUR_CHILD_NEUTRAL = 5 };
+
+/* ------------------------------------------------------------------------ */
+/* Philox4x32-10 counter-based generator (Salmon, Moraes, Dror, Shaw, SC'11) */
+/* ------------------------------------------------------------------------ */
+void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4])
+{
+    uint32_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3];
+    uint32_t k0 = key[0], k1 = key[1];
+    for (int r = 0; r < 10; ++r) {
+        if (r > 0) { k0 += 0x9E3779B9u; k1 += 0xBB67AE85u; }
+        uint64_t p0 = (uint64_t)0xD2511F53u * (uint64_t)c0;
+        uint64_t p1 = (uint64_t)0xCD9E8D57u * (uint64_t)c2;
+        uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+        uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+        uint32_t n0 = hi1 ^ c1 ^ k0, n1 = lo1, n2 = hi0 ^ c3 ^ k1, n3 = lo0;
+        c0 = n0; c1 = n1; c2 = n2; c3 = n3;
+    }
+    out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+/* uniform on (0,1): (u + 1/2) 2^-32, exact in double */
+static double u01(uint32_t u) { return ((double)u + 0.5) * 2.3283064365386962890625e-10; }
+
+/* Natural logarithm from +,-,*,/ only: x = m 2^e with m in [sqrt(1/2), sqrt(2)),
+ * ln m = 2 atanh(s), s = (m-1)/(m+1), by its odd power series up to s^23. */
+double orc_ln(double x)
+{
+    int e;
+    double m = frexp(x, &e);
+    if (m < 0.70710678118654752440) { m = m * 2.0; e = e - 1; }
+    double s = (m - 1.0) / (m + 1.0);
+    double s2 = s * s;
+    double p = 1.0 / 23.0;
+    p = p * s2 + 1.0 / 21.0;
+    p = p * s2 + 1.0 / 19.0;
+    p = p * s2 + 1.0 / 17.0;
+    p = p * s2 + 1.0 / 15.0;
+    p = p * s2 + 1.0 / 13.0;
+    p = p * s2 + 1.0 / 11.0;
+    p = p * s2 + 1.0 / 9.0;
+    p = p * s2 + 1.0 / 7.0;
+    p = p * s2 + 1.0 / 5.0;
+    p = p * s2 + 1.0 / 3.0;
+    p = p * s2 + 1.0;
+    double t1 = (double)e * 0.69314718055994530942;
+    double t2 = (2.0 * s) * p;
+    return t1 + t2;
+}
+
+/* A stream of uniforms for one (particle, step, purpose): Philox calls with
+ * the fourth counter word counting the calls. */
+typedef struct { uint32_t ctr[4]; uint32_t key[2]; uint32_t buf[4]; int pos; } rstream;
+
+static void rs_init(rstream* r, uint32_t id, uint32_t step, uint32_t purpose, const uint32_t key[2])
+{
+    r->ctr[0] = id; r->ctr[1] = step; r->ctr[2] = purpose; r->ctr[3] = 0;
+    r->key[0] = key[0]; r->key[1] = key[1]; r->pos = 4;
+}
+static uint32_t rs_next(rstream* r)
+{
+    if (r->pos == 4) { orc_philox4x32_10(r->ctr, r->key, r->buf); r->ctr[3] += 1; r->pos = 0; }
+    return r->buf[r->pos++];
+}
+/* a point uniform in the square (-1,1)^2 */
+static void rs_pair(rstream* r, double* a, double* b)
+{
+    uint32_t ua = rs_next(r), ub = rs_next(r);
+    *a = 2.0 * u01(ua) - 1.0;
+    *b = 2.0 * u01(ub) - 1.0;
+}
+/* isotropic unit vector, Marsaglia (1972) disk rejection */
+static void rs_iso(rstream* r, double out[3])
+{
+    for (int t = 0; t < 128; ++t) {
+        double a, b;
+        rs_pair(r, &a, &b);
+        double s = a * a + b * b;
+        if (s < 1.0) {
+            double q = 2.0 * sqrt(1.0 - s);
+            out[0] = a * q; out[1] = b * q; out[2] = 1.0 - 2.0 * s;
+            return;
+        }
+    }
+    out[0] = 0.0; out[1] = 0.0; out[2] = 1.0;
+}
+/* two standard normals, Marsaglia polar method */
+static void rs_gauss2(rstream* r, double* n1, double* n2)
+{
+    for (int t = 0; t < 128; ++t) {
+        double a, b;
+        rs_pair(r, &a, &b);
+        double s = a * a + b * b;
+        if (s < 1.0) {
+            double f = sqrt((-2.0 * orc_ln(s)) / s);
+            *n1 = a * f; *n2 = b * f;
+            return;
+        }
+    }
+    *n1 = 0.0; *n2 = 0.0;
+}
+static void rs_gauss3(rstream* r, double out[3])
+{
+    double d;
+    rs_gauss2(r, &out[0], &out[1]);
+    rs_gauss2(r, &out[2], &d);
+}
+
+void orc_iso_dir(uint32_t id, uint32_t step, uint32_t purpose, const uint32_t key[2], double out[3])
+{
+    rstream r; rs_init(&r, id, step, purpose, key); rs_iso(&r, out);
+}
+void orc_gauss3(uint32_t id, uint32_t step, uint32_t purpose, const uint32_t key[2], double out[3])
+{
+    rstream r; rs_init(&r, id, step, purpose, key); rs_gauss3(&r, out);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Exact discrete Poisson solve (Eq. 3) on the node mesh                     */
+/* ------------------------------------------------------------------------ */
+/* 2-D DFT of one plane (nx fastest), sign -1 forward, +1 backward (no 1/n). */
+static void dft2(int nx, int ny, const double* cx, const double* sx, const double* cy,
+                 const double* sy, double sign, const double* ire, const double* iim,
+                 double* ore, double* oim, double* tre, double* tim)
+{
+    for (int j = 0; j < ny; ++j)
+        for (int m = 0; m < nx; ++m) {
+            double ar = 0.0, ai = 0.0;
+            for (int i = 0; i < nx; ++i) {
+                int t = (int)(((long)m * i) % nx);
+                double c = cx[t], s = sign * sx[t];
+                double xr = ire[j * nx + i], xi = iim ? iim[j * nx + i] : 0.0;
+                ar += xr * c - xi * s;
+                ai += xr * s + xi * c;
+            }
+            tre[j * nx + m] = ar; tim[j * nx + m] = ai;
+        }
+    for (int m2 = 0; m2 < ny; ++m2)
+        for (int m = 0; m < nx; ++m) {
+            double ar = 0.0, ai = 0.0;
+            for (int j = 0; j < ny; ++j) {
+                int t = (int)(((long)m2 * j) % ny);
+                double c = cy[t], s = sign * sy[t];
+                double xr = tre[j * nx + m], xi = tim[j * nx + m];
+                ar += xr * c - xi * s;
+                ai += xr * s + xi * c;
+            }
+            ore[m2 * nx + m] = ar; oim[m2 * nx + m] = ai;
+        }
+}
+
+/* Solve (sum of the six neighbours - 6 phi)/dx^2 = -f on the interior nodes
+ * k = 1..nz-1, periodic in x,y, phi(k=0) = v_bot, phi(k=nz) = v_top.
+ * f and phi are node arrays indexed (k*ny + j)*nx + i. */
+int orc_poisson(int nx, int ny, int nz, double dx, const double* f, double v_bot,
+                double v_top, double* phi)
+{
+    const int P = nx * ny;
+    const size_t N = (size_t)P * (size_t)(nz + 1);
+    double* re = (double*)calloc(N, sizeof(double));
+    double* im = (double*)calloc(N, sizeof(double));
+    double* cx = (double*)malloc(sizeof(double) * nx);
+    double* sx = (double*)malloc(sizeof(double) * nx);
+    double* cy = (double*)malloc(sizeof(double) * ny);
+    double* sy = (double*)malloc(sizeof(double) * ny);
+    double* tre = (double*)malloc(sizeof(double) * P);
+    double* tim = (double*)malloc(sizeof(double) * P);
+    double* cp = (double*)malloc(sizeof(double) * (nz + 1));
+    double* rr = (double*)malloc(sizeof(double) * (nz + 1));
+    double* ri = (double*)malloc(sizeof(double) * (nz + 1));
+    if (!re || !im || !cx || !sx || !cy || !sy || !tre || !tim || !cp || !rr || !ri) return -1;
+    for (int t = 0; t < nx; ++t) { cx[t] = cos(2.0 * PI_D * t / nx); sx[t] = sin(2.0 * PI_D * t / nx); }
+    for (int t = 0; t < ny; ++t) { cy[t] = cos(2.0 * PI_D * t / ny); sy[t] = sin(2.0 * PI_D * t / ny); }
+
+    /* right-hand side -dx^2 f, transformed plane by plane */
+    double* g = (double*)malloc(sizeof(double) * P);
+    for (int k = 1; k < nz; ++k) {
+        for (int p = 0; p < P; ++p) g[p] = -(dx * dx) * f[(size_t)k * P + p];
+        dft2(nx, ny, cx, sx, cy, sy, -1.0, g, NULL, re + (size_t)k * P, im + (size_t)k * P, tre, tim);
+    }
+    free(g);
+
+    /* one tridiagonal system per Fourier mode:
+     * u_{k-1} + d u_k + u_{k+1} = r_k,  d = 2 cos(th1) + 2 cos(th2) - 6 */
+    for (int m2 = 0; m2 < ny; ++m2)
+        for (int m1 = 0; m1 < nx; ++m1) {
+            const int p = m2 * nx + m1;
+            const double d = (2.0 * cx[m1] + 2.0 * cy[m2]) - 6.0;
+            const double b0 = (p == 0) ? (double)P * v_bot : 0.0;
+            const double bn = (p == 0) ? (double)P * v_top : 0.0;
+            const int n = nz - 1;
+            for (int k = 1; k <= n; ++k) { rr[k] = re[(size_t)k * P + p]; ri[k] = im[(size_t)k * P + p]; }
+            rr[1] -= b0;
+            rr[n] -= bn;
+            /* forward elimination */
+            cp[1] = 1.0 / d;
+            rr[1] = rr[1] / d; ri[1] = ri[1] / d;
+            for (int k = 2; k <= n; ++k) {
+                double mm = d - cp[k - 1];
+                cp[k] = 1.0 / mm;
+                rr[k] = (rr[k] - rr[k - 1]) / mm;
+                ri[k] = (ri[k] - ri[k - 1]) / mm;
+            }
+            for (int k = n - 1; k >= 1; --k) {
+                rr[k] = rr[k] - cp[k] * rr[k + 1];
+                ri[k] = ri[k] - cp[k] * ri[k + 1];
+            }
+            for (int k = 1; k <= n; ++k) { re[(size_t)k * P + p] = rr[k]; im[(size_t)k * P + p] = ri[k]; }
+        }
+
+    /* back to space */
+    double* ore = (double*)malloc(sizeof(double) * P);
+    double* oim = (double*)malloc(sizeof(double) * P);
+    for (int k = 1; k < nz; ++k) {
+        dft2(nx, ny, cx, sx, cy, sy, +1.0, re + (size_t)k * P, im + (size_t)k * P, ore, oim, tre, tim);
+        for (int q = 0; q < P; ++q) phi[(size_t)k * P + q] = ore[q] / (double)P;
+    }
+    for (int q = 0; q < P; ++q) { phi[q] = v_bot; phi[(size_t)nz * P + q] = v_top; }
+    free(ore); free(oim);
+    free(re); free(im); free(cx); free(sx); free(cy); free(sy); free(tre); free(tim);
+    free(cp); free(rr); free(ri);
+    return 0;
+}
+
+/* E = -grad phi at the nodes (Eq. 4): central differences, periodic in x,y;
+ * second-order one-sided differences on the electrode planes. */
+void orc_efield(int nx, int ny, int nz, double dx, const double* phi, double* ex, double* ey, double* ez)
+{
+    const double h2 = 2.0 * dx;
+    for (int k = 0; k <= nz; ++k)
+        for (int j = 0; j < ny; ++j)
+            for (int i = 0; i < nx; ++i) {
+                size_t n = ((size_t)k * ny + j) * nx + i;
+                int ip = (i + 1) % nx, im = (i + nx - 1) % nx;
+                int jp = (j + 1) % ny, jm = (j + ny - 1) % ny;
+                ex[n] = (phi[((size_t)k * ny + j) * nx + im] - phi[((size_t)k * ny + j) * nx + ip]) / h2;
+                ey[n] = (phi[((size_t)k * ny + jm) * nx + i] - phi[((size_t)k * ny + jp) * nx + i]) / h2;
+                const size_t P = (size_t)nx * ny;
+                if (k == 0)
+                    ez[n] = ((3.0 * phi[n] - 4.0 * phi[n + P]) + phi[n + 2 * P]) / h2;
+                else if (k == nz)
+                    ez[n] = ((4.0 * phi[n - P] - 3.0 * phi[n]) - phi[n - 2 * P]) / h2;
+                else
+                    ez[n] = (phi[n - P] - phi[n + P]) / h2;
+            }
+}
+
+/* ------------------------------------------------------------------------ */
+/* simulation state                                                          */
+/* ------------------------------------------------------------------------ */
+typedef struct { uint32_t parent; double x[3], ve[3], vi[3]; } child_rec;
+
+struct orc_sim {
+    orc_cfg c;
+    double Lx, Ly, Lz;
+    double qm[2], hm[2];           /* q/m and (m/2)/e per species */
+    double pnull[2];
+    uint32_t key[2];
+    int64_t n[2], cap[2];
+    double* x[2];
+    double* v[2];
+    uint32_t* id[2];
+    int64_t* rq;                   /* fixed-point charge per node */
+    double *phi, *ex, *ey, *ez;
+    double* xs;                    /* owned copy of the tables */
+    double *gpos, *grad, *gq, *gtab;
+    int64_t* gabs;                 /* [g][species] */
+    int* cell_ng;
+    int* cell_g;
+    int64_t step;
+    uint32_t next_id;
+    int64_t cnt[ORC_C_N];
+    child_rec* ch; int64_t nch, capch;
+    double* mom[2];                /* [node][4]: count, count*vx, count*vy, count*vz */
+    double* mphi;
+    int64_t msteps;
+};
+
+static size_t nodes_of(const orc_sim* s) { return (size_t)s->c.nx * s->c.ny * (s->c.nz + 1); }
+static size_t cells_of(const orc_sim* s) { return (size_t)s->c.nx * s->c.ny * s->c.nz; }
+
+/* cell indices and in-cell fractions of a position */
+static void locate(const orc_sim* s, const double* p, int c[3], double f[3])
+{
+    const int nn[3] = { s->c.nx, s->c.ny, s->c.nz };
+    for (int a = 0; a < 3; ++a) {
+        double q = p[a] / s->c.dx;
+        int i = (int)floor(q);
+        if (i > nn[a] - 1) i = nn[a] - 1;
+        if (i < 0) i = 0;
+        c[a] = i;
+        f[a] = q - (double)i;
+    }
+}
+/* per-axis fixed-point CIC weights (lower corner, upper corner), summing to 2^14 */
+static void qweights(const double f[3], int64_t w[3][2])
+{
+    for (int a = 0; a < 3; ++a) {
+        int64_t q = (int64_t)rint(f[a] * (double)WQ);
+        if (q < 0) q = 0;
+        if (q > WQ) q = WQ;
+        w[a][0] = WQ - q; w[a][1] = q;
+    }
+}
+static size_t node_at(const orc_sim* s, int i, int j, int k)
+{
+    i %= s->c.nx; j %= s->c.ny;
+    return ((size_t)k * s->c.ny + j) * s->c.nx + i;
+}
+static size_t cell_index(const orc_sim* s, const int c[3])
+{
+    return ((size_t)c[2] * s->c.ny + c[1]) * s->c.nx + c[0];
+}
+
+static void deposit_one(const orc_sim* s, int64_t* rq, const double* p, int64_t charge)
+{
+    int c[3]; double f[3]; int64_t w[3][2];
+    locate(s, p, c, f);
+    qweights(f, w);
+    for (int dz = 0; dz < 2; ++dz)
+        for (int dy = 0; dy < 2; ++dy)
+            for (int dxi = 0; dxi < 2; ++dxi)
+                rq[node_at(s, c[0] + dxi, c[1] + dy, c[2] + dz)] += charge * (w[0][dxi] * w[1][dy] * w[2][dz]);
+}
+
+/* CIC gather of a node vector field with the same fixed-point weights */
+static void gather(const orc_sim* s, const double* fx, const double* fy, const double* fz,
+                   const int c[3], const int64_t w[3][2], double E[3])
+{
+    E[0] = 0.0; E[1] = 0.0; E[2] = 0.0;
+    for (int dz = 0; dz < 2; ++dz)
+        for (int dy = 0; dy < 2; ++dy)
+            for (int dxi = 0; dxi < 2; ++dxi) {
+                double wt = (double)(w[0][dxi] * w[1][dy] * w[2][dz]) * 0x1p-42;
+                size_t n = node_at(s, c[0] + dxi, c[1] + dy, c[2] + dz);
+                E[0] = E[0] + wt * fx[n];
+                E[1] = E[1] + wt * fy[n];
+                E[2] = E[2] + wt * fz[n];
+            }
+}
+
+/* minimum-image separation from grain g */
+static void grain_sep(const orc_sim* s, int g, const double* p, double d[3])
+{
+    const double L[2] = { s->Lx, s->Ly };
+    for (int a = 0; a < 2; ++a) {
+        double q = p[a] - s->gpos[3 * g + a];
+        if (q > 0.5 * L[a]) q = q - L[a];
+        else if (q < -0.5 * L[a]) q = q + L[a];
+        d[a] = q;
+    }
+    d[2] = p[2] - s->gpos[3 * g + 2];
+}
+
+/* Eqs. 5-6 inside an MD region: subtract each near grain's mesh field (its
+ * unit-charge node field table times Q, CIC-gathered) and add its Coulomb
+ * field Q (x - x_g) / (4 pi eps0 |x - x_g|^3). */
+static void md_correct(const orc_sim* s, const double* p, const int c[3], const int64_t w[3][2], double E[3])
+{
+    const size_t cell = cell_index(s, c);
+    const double kc = 1.0 / (4.0 * PI_D * EPS0);
+    for (int t = 0; t < s->cell_ng[cell]; ++t) {
+        const int g = s->cell_g[cell * MAXG + t];
+        const int gc[3] = { (int)floor(s->gpos[3 * g] / s->c.dx), (int)floor(s->gpos[3 * g + 1] / s->c.dx),
+                            (int)floor(s->gpos[3 * g + 2] / s->c.dx) };
+        double Ed[3] = { 0.0, 0.0, 0.0 };
+        for (int dz = 0; dz < 2; ++dz)
+            for (int dy = 0; dy < 2; ++dy)
+                for (int dxi = 0; dxi < 2; ++dxi) {
+                    double wt = (double)(w[0][dxi] * w[1][dy] * w[2][dz]) * 0x1p-42;
+                    int li = ((c[0] + dxi - gc[0] + 1) % s->c.nx + s->c.nx) % s->c.nx;
+                    int lj = ((c[1] + dy - gc[1] + 1) % s->c.ny + s->c.ny) % s->c.ny;
+                    int lk = c[2] + dz - gc[2] + 1;
+                    const double* tv = s->gtab + ((size_t)g * 64 + (lk * 4 + lj) * 4 + li) * 3;
+                    Ed[0] = Ed[0] + wt * tv[0];
+                    Ed[1] = Ed[1] + wt * tv[1];
+                    Ed[2] = Ed[2] + wt * tv[2];
+                }
+        double d[3];
+        grain_sep(s, g, p, d);
+        double r2 = (d[0] * d[0] + d[1] * d[1]) + d[2] * d[2];
+        double Q = s->gq[g];
+        double coef = 0.0;
+        if (r2 > 0.0) { double r = sqrt(r2); coef = (Q * kc) / (r2 * r); }
+        for (int a = 0; a < 3; ++a) E[a] = (E[a] - Q * Ed[a]) + coef * d[a];
+    }
+}
+
+/* 0 alive, 1 lost at z=0, 2 lost at z=Lz, 3 invalid (non-finite or moved a box length) */
+static int boundary(const orc_sim* s, double* p)
+{
+    if (!(p[2] >= 0.0)) return (p[2] < 0.0) ? 1 : 3;
+    if (p[2] > s->Lz) return 2;
+    const double L[2] = { s->Lx, s->Ly };
+    for (int a = 0; a < 2; ++a) {
+        if (p[a] < 0.0) p[a] = p[a] + L[a];
+        else if (p[a] >= L[a]) p[a] = p[a] - L[a];
+        if (!(p[a] >= 0.0 && p[a] <= L[a])) return 3;
+    }
+    return 0;
+}
+
+static int absorbed_by(const orc_sim* s, const double* p)
+{
+    int c[3]; double f[3];
+    locate(s, p, c, f);
+    const size_t cell = cell_index(s, c);
+    for (int t = 0; t < s->cell_ng[cell]; ++t) {
+        const int g = s->cell_g[cell * MAXG + t];
+        double d[3];
+        grain_sep(s, g, p, d);
+        double r2 = (d[0] * d[0] + d[1] * d[1]) + d[2] * d[2];
+        if (r2 <= s->grad[g] * s->grad[g]) return g;
+    }
+    return -1;
+}
+
+static double xs_at(const double* tab, int n, double de, double eps)
+{
+    double t = eps / de;
+    if (t >= (double)(n - 1)) return tab[n - 1];
+    int i = (int)t;
+    double fr = t - (double)i;
+    return tab[i] + fr * (tab[i + 1] - tab[i]);
+}
+
+static void push_child(orc_sim* s, const child_rec* r)
+{
+    if (s->nch == s->capch) {
+        s->capch = s->capch ? 2 * s->capch : 64;
+        s->ch = (child_rec*)realloc(s->ch, sizeof(child_rec) * s->capch);
+    }
+    s->ch[s->nch++] = *r;
+}
+
+/* null-collision MCC for one particle after its push (Table I) */
+static void mcc(orc_sim* s, int sp, double* p, double* v, uint32_t id)
+{
+    const uint32_t step = (uint32_t)s->step;
+    uint32_t ctr[4] = { id, step, PUR_MCC, 0 }, u[4];
+    orc_philox4x32_10(ctr, s->key, u);
+    if (u01(u[0]) >= s->pnull[sp]) return;
+    const double ng = s->c.n_gas;
+    const int nx = s->c.n_xs;
+    const double sig_n = sqrt(KB * s->c.t_gas / MAR);
+    if (sp == 0) {
+        double v2 = (v[0] * v[0] + v[1] * v[1]) + v[2] * v[2];
+        double eps = v2 * s->hm[0];
+        double vm = sqrt(v2);
+        double nu_el = (ng * xs_at(s->xs + 0 * nx, nx, s->c.de_e, eps)) * vm;
+        double nu_ex = (ng * xs_at(s->xs + 1 * nx, nx, s->c.de_e, eps)) * vm;
+        double nu_io = (ng * xs_at(s->xs + 2 * nx, nx, s->c.de_e, eps)) * vm;
+        double R = u01(u[1]) * s->c.nu_max_e;
+        double acc = nu_el;
+        rstream rd; rs_init(&rd, id, step, PUR_DIR, s->key);
+        double dir[3];
+        if (R < acc) {
+            /* elastic: isotropic, energy loss (2 m_e / M)(1 - cos chi) */
+            rs_iso(&rd, dir);
+            double cosx = ((dir[0] * v[0] + dir[1] * v[1]) + dir[2] * v[2]) / vm;
+            double fac = 1.0 - ((2.0 * ME) / MAR) * (1.0 - cosx);
+            double vn = vm * sqrt(fac);
+            for (int a = 0; a < 3; ++a) v[a] = vn * dir[a];
+            s->cnt[ORC_C_E_EL]++;
+            return;
+        }
+        acc = acc + nu_ex;
+        if (R < acc) {
+            double e2 = eps - s->c.eps_exc;
+            if (e2 < 0.0) e2 = 0.0;
+            rs_iso(&rd, dir);
+            double vn = sqrt(e2 / s->hm[0]);
+            for (int a = 0; a < 3; ++a) v[a] = vn * dir[a];
+            s->cnt[ORC_C_E_EXC]++;
+            return;
+        }
+        acc = acc + nu_io;
+        if (R < acc) {
+            double e2 = eps - s->c.eps_ion;
+            if (e2 < 0.0) e2 = 0.0;
+            double vn = sqrt((0.5 * e2) / s->hm[0]);
+            rs_iso(&rd, dir);
+            child_rec cr;
+            cr.parent = id;
+            for (int a = 0; a < 3; ++a) { v[a] = vn * dir[a]; cr.x[a] = p[a]; }
+            double d2[3], gn[3];
+            rstream rc; rs_init(&rc, id, step, PUR_CHILD_DIR, s->key); rs_iso(&rc, d2);
+            rstream rn; rs_init(&rn, id, step, PUR_CHILD_NEUTRAL, s->key); rs_gauss3(&rn, gn);
+            for (int a = 0; a < 3; ++a) { cr.ve[a] = vn * d2[a]; cr.vi[a] = sig_n * gn[a]; }
+            push_child(s, &cr);
+            s->cnt[ORC_C_E_ION]++;
+        }
+        return;
+    }
+    /* ions: relative velocity to a neutral drawn from the 300 K Maxwellian */
+    double gn[3];
+    rstream rn; rs_init(&rn, id, step, PUR_NEUTRAL, s->key); rs_gauss3(&rn, gn);
+    double vn[3] = { sig_n * gn[0], sig_n * gn[1], sig_n * gn[2] };
+    double g[3] = { v[0] - vn[0], v[1] - vn[1], v[2] - vn[2] };
+    double g2 = (g[0] * g[0] + g[1] * g[1]) + g[2] * g[2];
+    double eps = g2 * s->hm[1];
+    double gm = sqrt(g2);
+    double nu_el = (ng * xs_at(s->xs + 3 * nx, nx, s->c.de_i, eps)) * gm;
+    double nu_cx = (ng * xs_at(s->xs + 4 * nx, nx, s->c.de_i, eps)) * gm;
+    double R = u01(u[1]) * s->c.nu_max_i;
+    double acc = nu_el;
+    if (R < acc) {
+        /* elastic, isotropic in the centre-of-mass frame (equal masses) */
+        double dir[3];
+        rstream rd; rs_init(&rd, id, step, PUR_DIR, s->key); rs_iso(&rd, dir);
+        for (int a = 0; a < 3; ++a) v[a] = (v[a] + vn[a]) * 0.5 + (0.5 * gm) * dir[a];
+        s->cnt[ORC_C_I_EL]++;
+        return;
+    }
+    acc = acc + nu_cx;
+    if (R < acc) {
+        for (int a = 0; a < 3; ++a) v[a] = vn[a];
+        s->cnt[ORC_C_I_CX]++;
+    }
+}
+
+static int cmp_child(const void* a, const void* b)
+{
+    uint32_t x = ((const child_rec*)a)->parent, y = ((const child_rec*)b)->parent;
+    return (x > y) - (x < y);
+}
+
+static void grow(orc_sim* s, int sp, int64_t need)
+{
+    if (need <= s->cap[sp]) return;
+    int64_t nc = s->cap[sp] ? s->cap[sp] : 16;
+    while (nc < need) nc *= 2;
+    s->x[sp] = (double*)realloc(s->x[sp], sizeof(double) * 3 * nc);
+    s->v[sp] = (double*)realloc(s->v[sp], sizeof(double) * 3 * nc);
+    s->id[sp] = (uint32_t*)realloc(s->id[sp], sizeof(uint32_t) * nc);
+    s->cap[sp] = nc;
+}
+
+static void deposit_all(orc_sim* s)
+{
+    memset(s->rq, 0, sizeof(int64_t) * nodes_of(s));
+    for (int sp = 0; sp < 2; ++sp) {
+        const int64_t charge = sp == 0 ? -1 : 1;
+        for (int64_t q = 0; q < s->n[sp]; ++q) deposit_one(s, s->rq, s->x[sp] + 3 * q, charge);
+    }
+    for (int g = 0; g < s->c.n_grains; ++g)
+        deposit_one(s, s->rq, s->gpos + 3 * g, s->gabs[2 * g + 1] - s->gabs[2 * g + 0]);
+}
+
+static double v_bottom(const orc_sim* s)
+{
+    double t = (double)s->step * s->c.dt;
+    return s->c.v_dc + s->c.v_rf * sin((2.0 * PI_D * s->c.f_rf) * t + s->c.phase);
+}
+
+int orc_solve(orc_sim* s)
+{
+    const size_t N = nodes_of(s);
+    double* f = (double*)malloc(sizeof(double) * N);
+    const double dx = s->c.dx;
+    const double scale = (((QE * s->c.weight) / (dx * dx * dx)) * 0x1p-42) / EPS0;
+    for (size_t q = 0; q < N; ++q) f[q] = (double)s->rq[q] * scale;
+    int rc = orc_poisson(s->c.nx, s->c.ny, s->c.nz, dx, f, v_bottom(s), s->c.v_top, s->phi);
+    free(f);
+    return rc;
+}
+
+static void moments_accumulate(orc_sim* s)
+{
+    const size_t N = nodes_of(s);
+    for (int sp = 0; sp < 2; ++sp)
+        for (int64_t q = 0; q < s->n[sp]; ++q) {
+            int c[3]; double f[3]; int64_t w[3][2];
+            const double* p = s->x[sp] + 3 * q;
+            const double* vv = s->v[sp] + 3 * q;
+            locate(s, p, c, f);
+            qweights(f, w);
+            for (int dz = 0; dz < 2; ++dz)
+                for (int dy = 0; dy < 2; ++dy)
+                    for (int dxi = 0; dxi < 2; ++dxi) {
+                        double wt = (double)(w[0][dxi] * w[1][dy] * w[2][dz]) * 0x1p-42;
+                        double* m = s->mom[sp] + 4 * node_at(s, c[0] + dxi, c[1] + dy, c[2] + dz);
+                        m[0] += wt; m[1] += wt * vv[0]; m[2] += wt * vv[1]; m[3] += wt * vv[2];
+                    }
+        }
+    for (size_t q = 0; q < N; ++q) s->mphi[q] += s->phi[q];
+    s->msteps++;
+}
+
+int orc_advance(orc_sim* s)
+{
+    const size_t N = nodes_of(s);
+    orc_efield(s->c.nx, s->c.ny, s->c.nz, s->c.dx, s->phi, s->ex, s->ey, s->ez);
+    s->nch = 0;
+    const int M = s->c.md_sub > 0 ? s->c.md_sub : 1;
+    const double dt = s->c.dt;
+    const double dtm = dt / (double)M;
+    for (int sp = 0; sp < 2; ++sp) {
+        if (sp == 1 && (s->c.flags & ORC_IONS_FROZEN)) continue;
+        const double qmdt = s->qm[sp] * dt;
+        const double qmdtm = s->qm[sp] * dtm;
+        int64_t keep = 0;
+        for (int64_t q = 0; q < s->n[sp]; ++q) {
+            double p[3], v[3];
+            memcpy(p, s->x[sp] + 3 * q, sizeof p);
+            memcpy(v, s->v[sp] + 3 * q, sizeof v);
+            const uint32_t id = s->id[sp][q];
+            int c[3]; double f[3]; int64_t w[3][2];
+            locate(s, p, c, f);
+            qweights(f, w);
+            int fate = 0, grain = -1;
+            if (s->cell_ng[cell_index(s, c)] == 0) {
+                double E[3];
+                gather(s, s->ex, s->ey, s->ez, c, w, E);
+                for (int a = 0; a < 3; ++a) v[a] = v[a] + qmdt * E[a];
+                for (int a = 0; a < 3; ++a) p[a] = p[a] + v[a] * dt;
+                fate = boundary(s, p);
+            } else {
+                for (int m = 0; m < M; ++m) {
+                    double E[3];
+                    if (m > 0) { locate(s, p, c, f); qweights(f, w); }
+                    gather(s, s->ex, s->ey, s->ez, c, w, E);
+                    md_correct(s, p, c, w, E);
+                    for (int a = 0; a < 3; ++a) v[a] = v[a] + qmdtm * E[a];
+                    for (int a = 0; a < 3; ++a) p[a] = p[a] + v[a] * dtm;
+                    fate = boundary(s, p);
+                    if (fate) break;
+                    grain = absorbed_by(s, p);
+                    if (grain >= 0) break;
+                }
+            }
+            if (fate == 1) { s->cnt[sp == 0 ? ORC_C_LOST_BOT_E : ORC_C_LOST_BOT_I]++; continue; }
+            if (fate == 2) { s->cnt[sp == 0 ? ORC_C_LOST_TOP_E : ORC_C_LOST_TOP_I]++; continue; }
+            if (fate == 3) { s->cnt[ORC_C_ERR]++; continue; }
+            if (grain >= 0) {
+                s->gabs[2 * grain + sp]++;
+                s->cnt[sp == 0 ? ORC_C_ABS_E : ORC_C_ABS_I]++;
+                continue;
+            }
+            if (!(s->c.flags & ORC_NO_MCC)) mcc(s, sp, p, v, id);
+            memcpy(s->x[sp] + 3 * keep, p, sizeof p);
+            memcpy(s->v[sp] + 3 * keep, v, sizeof v);
+            s->id[sp][keep] = id;
+            keep++;
+        }
+        s->n[sp] = keep;
+    }
+    /* grain charges after this step's absorptions */
+    for (int g = 0; g < s->c.n_grains; ++g)
+        s->gq[g] = (QE * s->c.weight) * (double)(s->gabs[2 * g + 1] - s->gabs[2 * g + 0]);
+    /* ionization products, numbered in the order of their parents' ids */
+    qsort(s->ch, (size_t)s->nch, sizeof(child_rec), cmp_child);
+    if ((uint64_t)s->next_id + 2u * (uint64_t)s->nch > 0xFFFFFFFFull) s->cnt[ORC_C_ERR]++;
+    grow(s, 0, s->n[0] + s->nch);
+    grow(s, 1, s->n[1] + s->nch);
+    for (int64_t r = 0; r < s->nch; ++r) {
+        const child_rec* cr = &s->ch[r];
+        memcpy(s->x[0] + 3 * s->n[0], cr->x, sizeof cr->x);
+        memcpy(s->v[0] + 3 * s->n[0], cr->ve, sizeof cr->ve);
+        s->id[0][s->n[0]++] = s->next_id + (uint32_t)(2 * r);
+        memcpy(s->x[1] + 3 * s->n[1], cr->x, sizeof cr->x);
+        memcpy(s->v[1] + 3 * s->n[1], cr->vi, sizeof cr->vi);
+        s->id[1][s->n[1]++] = s->next_id + (uint32_t)(2 * r + 1);
+    }
+    s->next_id += (uint32_t)(2 * s->nch);
+    deposit_all(s);
+    s->step++;
+    (void)N;
+    return 0;
+}
+
+int orc_step(orc_sim* s)
+{
+    int rc = orc_advance(s);
+    if (rc) return rc;
+    rc = orc_solve(s);
+    if (rc) return rc;
+    if (s->c.flags & ORC_MOMENTS) moments_accumulate(s);
+    return 0;
+}
+
+orc_sim* orc_create(const orc_cfg* cfg)
+{
+    orc_sim* s = (orc_sim*)calloc(1, sizeof(orc_sim));
+    s->c = *cfg;
+    const double dx = cfg->dx;
+    s->Lx = cfg->nx * dx; s->Ly = cfg->ny * dx; s->Lz = cfg->nz * dx;
+    s->qm[0] = -QE / ME; s->qm[1] = QE / MAR;
+    s->hm[0] = (0.5 * ME) / QE; s->hm[1] = (0.5 * MAR) / QE;
+    s->pnull[0] = 1.0 - exp(-cfg->nu_max_e * cfg->dt);
+    s->pnull[1] = 1.0 - exp(-cfg->nu_max_i * cfg->dt);
+    s->key[0] = (uint32_t)cfg->seed ^ cfg->run_id;
+    s->key[1] = (uint32_t)(cfg->seed >> 32);
+    const size_t N = nodes_of(s), C = cells_of(s);
+    s->rq = (int64_t*)calloc(N, sizeof(int64_t));
+    s->phi = (double*)calloc(N, sizeof(double));
+    s->ex = (double*)calloc(N, sizeof(double));
+    s->ey = (double*)calloc(N, sizeof(double));
+    s->ez = (double*)calloc(N, sizeof(double));
+    s->mom[0] = (double*)calloc(4 * N, sizeof(double));
+    s->mom[1] = (double*)calloc(4 * N, sizeof(double));
+    s->mphi = (double*)calloc(N, sizeof(double));
+    if (cfg->n_xs > 0) {
+        s->xs = (double*)malloc(sizeof(double) * 5 * cfg->n_xs);
+        memcpy(s->xs, cfg->xs, sizeof(double) * 5 * cfg->n_xs);
+    }
+    const int ng = cfg->n_grains;
+    s->gpos = (double*)calloc(3 * (ng + 1), sizeof(double));
+    s->grad = (double*)calloc(ng + 1, sizeof(double));
+    s->gq = (double*)calloc(ng + 1, sizeof(double));
+    s->gabs = (int64_t*)calloc(2 * (ng + 1), sizeof(int64_t));
+    s->gtab = (double*)calloc((size_t)(ng + 1) * 64 * 3, sizeof(double));
+    if (ng) { memcpy(s->gpos, cfg->gpos, sizeof(double) * 3 * ng); memcpy(s->grad, cfg->grad, sizeof(double) * ng); }
+    s->cell_ng = (int*)calloc(C, sizeof(int));
+    s->cell_g = (int*)calloc(C * MAXG, sizeof(int));
+    /* MD regions: each grain's cell and its 26 direct neighbours */
+    for (int g = 0; g < ng; ++g) {
+        const int gc[3] = { (int)floor(s->gpos[3 * g] / dx), (int)floor(s->gpos[3 * g + 1] / dx),
+                            (int)floor(s->gpos[3 * g + 2] / dx) };
+        for (int dk = -1; dk <= 1; ++dk)
+            for (int dj = -1; dj <= 1; ++dj)
+                for (int di = -1; di <= 1; ++di) {
+                    int c[3] = { (gc[0] + di + cfg->nx) % cfg->nx, (gc[1] + dj + cfg->ny) % cfg->ny, gc[2] + dk };
+                    if (c[2] < 0 || c[2] >= cfg->nz) continue;
+                    size_t ci = cell_index(s, c);
+                    if (s->cell_ng[ci] < MAXG) s->cell_g[ci * MAXG + s->cell_ng[ci]++] = g;
+                    else s->cnt[ORC_C_ERR]++;
+                }
+    }
+    /* unit-charge mesh field of each grain on the 4x4x4 nodes of its region */
+    if (ng) {
+        double* f = (double*)calloc(N, sizeof(double));
+        double* ph = (double*)calloc(N, sizeof(double));
+        double *ex = (double*)calloc(N, sizeof(double)), *ey = (double*)calloc(N, sizeof(double)),
+               *ez = (double*)calloc(N, sizeof(double));
+        int64_t* rq = (int64_t*)calloc(N, sizeof(int64_t));
+        const double scale1 = ((1.0 / (dx * dx * dx)) * 0x1p-42) / EPS0;
+        for (int g = 0; g < ng; ++g) {
+            memset(rq, 0, sizeof(int64_t) * N);
+            deposit_one(s, rq, s->gpos + 3 * g, 1);
+            for (size_t q = 0; q < N; ++q) f[q] = (double)rq[q] * scale1;
+            orc_poisson(cfg->nx, cfg->ny, cfg->nz, dx, f, 0.0, 0.0, ph);
+            orc_efield(cfg->nx, cfg->ny, cfg->nz, dx, ph, ex, ey, ez);
+            const int gc[3] = { (int)floor(s->gpos[3 * g] / dx), (int)floor(s->gpos[3 * g + 1] / dx),
+                                (int)floor(s->gpos[3 * g + 2] / dx) };
+            for (int lk = 0; lk < 4; ++lk)
+                for (int lj = 0; lj < 4; ++lj)
+                    for (int li = 0; li < 4; ++li) {
+                        size_t n = node_at(s, gc[0] - 1 + li + cfg->nx, gc[1] - 1 + lj + cfg->ny, gc[2] - 1 + lk);
+                        double* tv = s->gtab + ((size_t)g * 64 + (lk * 4 + lj) * 4 + li) * 3;
+                        tv[0] = ex[n]; tv[1] = ey[n]; tv[2] = ez[n];
+                    }
+        }
+        free(f); free(ph); free(ex); free(ey); free(ez); free(rq);
+    }
+    uint32_t maxid = 0; int any = 0;
+    for (int sp = 0; sp < 2; ++sp) {
+        grow(s, sp, cfg->n_init[sp] > 0 ? cfg->n_init[sp] : 1);
+        s->n[sp] = cfg->n_init[sp];
+        if (cfg->n_init[sp] > 0) {
+            memcpy(s->x[sp], cfg->x_init[sp], sizeof(double) * 3 * cfg->n_init[sp]);
+            memcpy(s->v[sp], cfg->v_init[sp], sizeof(double) * 3 * cfg->n_init[sp]);
+            memcpy(s->id[sp], cfg->id_init[sp], sizeof(uint32_t) * cfg->n_init[sp]);
+            for (int64_t q = 0; q < cfg->n_init[sp]; ++q)
+                if (!any || s->id[sp][q] > maxid) { maxid = s->id[sp][q]; any = 1; }
+        }
+    }
+    s->next_id = any ? maxid + 1 : 0;
+    s->step = 0;
+    deposit_all(s);
+    orc_solve(s);
+    return s;
+}
+
+void orc_destroy(orc_sim* s)
+{
+    if (!s) return;
+    for (int sp = 0; sp < 2; ++sp) { free(s->x[sp]); free(s->v[sp]); free(s->id[sp]); free(s->mom[sp]); }
+    free(s->rq); free(s->phi); free(s->ex); free(s->ey); free(s->ez); free(s->xs);
+    free(s->gpos); free(s->grad); free(s->gq); free(s->gabs); free(s->gtab);
+    free(s->cell_ng); free(s->cell_g); free(s->ch); free(s->mphi);
+    free(s);
+}
+
+int64_t orc_count(const orc_sim* s, int sp) { return s->n[sp]; }
+void orc_get_particles(const orc_sim* s, int sp, double* x, double* v, uint32_t* id)
+{
+    memcpy(x, s->x[sp], sizeof(double) * 3 * s->n[sp]);
+    memcpy(v, s->v[sp], sizeof(double) * 3 * s->n[sp]);
+    memcpy(id, s->id[sp], sizeof(uint32_t) * s->n[sp]);
+}
+void orc_get_rho(const orc_sim* s, int64_t* rq) { memcpy(rq, s->rq, sizeof(int64_t) * nodes_of(s)); }
+void orc_get_phi(const orc_sim* s, double* phi) { memcpy(phi, s->phi, sizeof(double) * nodes_of(s)); }
+void orc_set_phi(orc_sim* s, const double* phi) { memcpy(s->phi, phi, sizeof(double) * nodes_of(s)); }
+void orc_get_grains(const orc_sim* s, int64_t* n_abs, double* q)
+{
+    memcpy(n_abs, s->gabs, sizeof(int64_t) * 2 * s->c.n_grains);
+    memcpy(q, s->gq, sizeof(double) * s->c.n_grains);
+}
+void orc_get_gtab(const orc_sim* s, double* tab) { memcpy(tab, s->gtab, sizeof(double) * 64 * 3 * s->c.n_grains); }
+void orc_set_gtab(orc_sim* s, const double* tab) { memcpy(s->gtab, tab, sizeof(double) * 64 * 3 * s->c.n_grains); }
+void orc_get_counters(const orc_sim* s, int64_t* c) { memcpy(c, s->cnt, sizeof(int64_t) * ORC_C_N); }
+int64_t orc_step_index(const orc_sim* s) { return s->step; }
+uint32_t orc_next_id(const orc_sim* s) { return s->next_id; }
+
+int orc_moments(const orc_sim* s, int what, double* out)
+{
+    const size_t N = nodes_of(s);
+    if (s->msteps == 0) return -1;
+    const double dx = s->c.dx;
+    const double norm = s->c.weight / ((dx * dx * dx) * (double)s->msteps);
+    switch (what) {
+    case 0: for (size_t q = 0; q < N; ++q) out[q] = s->mphi[q] / (double)s->msteps; return 0;
+    case 1: case 2: {
+        const double* m = s->mom[what - 1];
+        for (size_t q = 0; q < N; ++q) out[q] = m[4 * q] * norm;
+        return 0;
+    }
+    case 3: case 4: {
+        const double* m = s->mom[what - 3];
+        for (size_t q = 0; q < N; ++q)
+            for (int a = 0; a < 3; ++a) out[3 * q + a] = m[4 * q + 1 + a] * norm;
+        return 0;
+    }
+    }
+    return -1;
+}
+
+int orc_field_at(orc_sim* s, const double p[3], double E[3])
+{
+    int c[3]; double f[3]; int64_t w[3][2];
+    orc_efield(s->c.nx, s->c.ny, s->c.nz, s->c.dx, s->phi, s->ex, s->ey, s->ez);
+    locate(s, p, c, f);
+    qweights(f, w);
+    gather(s, s->ex, s->ey, s->ez, c, w, E);
+    int md = s->cell_ng[cell_index(s, c)] > 0;
+    if (md) md_correct(s, p, c, w, E);
+    return md;
+}
+
+void orc_set_grain_counts(orc_sim* s, const int64_t* n_abs)
+{
+    memcpy(s->gabs, n_abs, sizeof(int64_t) * 2 * s->c.n_grains);
+    for (int g = 0; g < s->c.n_grains; ++g)
+        s->gq[g] = (QE * s->c.weight) * (double)(s->gabs[2 * g + 1] - s->gabs[2 * g + 0]);
+    deposit_all(s);
+    orc_solve(s);
+}
+
+void orc_reset_moments(orc_sim* s)
+{
+    const size_t N = nodes_of(s);
+    memset(s->mom[0], 0, sizeof(double) * 4 * N);
+    memset(s->mom[1], 0, sizeof(double) * 4 * N);
+    memset(s->mphi, 0, sizeof(double) * N);
+    s->msteps = 0;
+}
