@@ -1,0 +1,319 @@
+#!/usr/bin/env python
+"""Benchmark of the PIC-MCC/PPPM step on one GB300 (or N independent replicas).
+
+One bench step = one full time step of the particle cycle (gather, push with
+MD subcycling near grains, absorption, MCC, deposit, Poisson solve) of the rf
+sheath workload with a 7-grain cluster: 64x64x256 cells of 0.2 mm, 100 V at
+13.56 MHz, argon at 2 Pa, 1e7 macroparticles (5e6 e + 5e6 Ar+), synthetic
+seeded inputs.  Particle arrays (320 MB mixed, 640 MB FP64) exceed the 129 MB L2.
+
+Prints one JSON line.  ``value`` is mixed-precision particle-steps/s summed
+over ranks; the FP64 path, Poisson solves/s, the push kernel's roofline, an
+end-to-end figure through the C ABI with host buffers and the CPU oracle's
+figure on a bounded sample ride along.
+``--impl reference`` times the CPU oracle alone (rank 0) on the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "particle-steps/s and Poisson solves/s, mixed vs FP64, 1 GB300, % HBM roof"
+BYTES_MIXED = 64     # per particle-step: float4 pos + float4 vel, read and written
+BYTES_FP64 = 128     # double4 pos + double4 vel, read and written
+
+
+def args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", type=int, default=1)
+    ap.add_argument("--fp64-steps", type=int, default=None)
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu):
+        self.gpu = gpu
+        self.proc = None
+        self.f = None
+
+    def __enter__(self):
+        try:
+            self.f = tempfile.TemporaryFile(mode="w+")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(self.gpu)], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.f:
+            return None
+        self.f.seek(0)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.f.read().splitlines():
+            t = [x.strip() for x in line.split(",")]
+            if len(t) < 9:
+                continue
+            try:
+                sm.append(float(t[1]))
+                mx.append(float(t[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, t[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def run_gpu(P, I, wl, parts, prec, steps, warmup, stream, gpu):
+    import torch
+    run = P.Run(wl, parts, prec=prec, stream=stream, sort_every=20)
+    run.step(warmup)
+    _, c0 = run.counts()
+    run.profile(1)
+    k0 = run.profile_read()["kernels"]
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clk = Clocks(gpu)
+    with clk:
+        if torch.distributed.is_initialized():
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        start.record(torch.cuda.current_stream())
+        run.step(steps)
+        end.record(torch.cuda.current_stream())
+        torch.cuda.synchronize()
+        if torch.distributed.is_initialized():
+            torch.distributed.barrier()
+    ms = start.elapsed_time(end)
+    prof = run.profile_read()
+    n, c1 = run.counts()
+    run.close()
+    return dict(ms=ms, pushed=c1["pushed"] - c0["pushed"], prof=prof, kernels=prof["kernels"] - k0,
+                live=[int(x) for x in n], clocks=clk.summary(), counters=c1)
+
+
+def e2e(P, wl, parts, prec, steps, stream):
+    """Through the public API from host buffers: init (host->device copy of the
+    particles), then each step followed by a device->host read of the grain
+    charges (the step's result)."""
+    import numpy as np
+    import torch
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    run = P.Run(wl, parts, prec=prec, stream=stream, sort_every=20)
+    _, c0 = run.counts()
+    for _ in range(steps):
+        run.step(1)
+        run.grains()
+    _, c1 = run.counts()
+    torch.cuda.synchronize()
+    t = time.perf_counter() - t0
+    run.close()
+    h2d = sum(p[0].nbytes + p[1].nbytes + p[2].nbytes for p in parts)
+    d2h = (2 * 8 + 8) * len(wl.grain_r)
+    ps = c1["pushed"] - c0["pushed"]
+    return {"value": ps / t, "unit": "particle-steps/s", "h2d_bytes_per_step": int(h2d // steps),
+            "d2h_bytes_per_step": int(d2h), "seconds": t,
+            "note": "pic_init from host arrays + per-step pic_step(1) and pic_grain_charges"}
+
+
+def oracle_sample(wl, n_particles, steps, seed=1):
+    """The CPU oracle, as it stands, on a bounded sample of the workload: the same
+    mesh, grains and gas with n_particles macroparticles (init excluded)."""
+    import dataclasses
+
+    import oracle as O
+    from paper_1801_00972_gb300 import inputs as I
+    half = n_particles // 2
+    w = dataclasses.replace(wl, n_e=half, n_i=half, weight=wl.weight * wl.n_e / max(half, 1))
+    parts = I.sample_particles(w, seed=seed)
+    s = O.Sim(w, parts)
+    n0 = s.count(0) + s.count(1)
+    t0 = time.perf_counter()
+    done = 0
+    for _ in range(steps):
+        done += s.count(0) + s.count(1)
+        s.step()
+    t = time.perf_counter() - t0
+    return done / t, t, n0
+
+
+def reference_arm(a):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from paper_1801_00972_gb300 import inputs as I
+    wl = I.workload(a.workload)
+    n = 600_000
+    steps = a.steps + a.warmup
+    # keep the whole run to a few minutes: ~0.6 s per oracle step on this mesh
+    budget = 150.0
+    if steps * 0.6 > budget:
+        n = 100_000
+    value, t, n0 = oracle_sample(wl, n, a.warmup + a.steps)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "particle-steps/s", "n_gpus": a.gpus,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1000 * t / (a.warmup + a.steps),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": wl.name + f" {wl.nx}x{wl.ny}x{wl.nz} cells, {len(wl.grain_r)} grains, rf",
+                       "sample_particles": n0},
+            "cpu_baseline": {"value": value, "unit": "particle-steps/s", "cores": 1, "kind": "oracle",
+                             "sample": f"{n0} particles of the workload's 1e7 on its full mesh, "
+                                       f"{a.warmup + a.steps} steps, init excluded"},
+            "e2e": {"value": value, "unit": "particle-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    a = args()
+    if a.impl == "reference":
+        reference_arm(a)
+        return
+    import torch
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        torch.distributed.init_process_group("nccl")
+    from paper_1801_00972_gb300 import build as B
+    if rank == 0:
+        B.build()
+    if world > 1:
+        torch.distributed.barrier()
+    import paper_1801_00972_gb300 as P
+    from paper_1801_00972_gb300 import inputs as I
+    P.load()
+    wl = I.workload(a.workload)
+    # replicas: each rank runs its own independent run (different seed)
+    wl.seed = wl.seed + 1000 * rank
+    parts = I.sample_particles(wl)
+    stream = torch.cuda.current_stream().cuda_stream
+    mixed = run_gpu(P, I, wl, parts, P.PIC_MIXED, a.steps, a.warmup, stream, local)
+    fp64 = None
+    if not a.no_fp64:
+        fp64 = run_gpu(P, I, wl, parts, P.PIC_FP64, a.fp64_steps or max(a.steps // 4, 10), a.warmup, stream, local)
+    ee = None if a.no_e2e else e2e(P, wl, parts, P.PIC_MIXED, max(a.steps // 4, 10), stream)
+
+    def agg(x):
+        if x is None:
+            return None
+        ms = x["ms"]
+        tot = x["pushed"]
+        if world > 1:
+            t = torch.tensor([ms, float(tot)], device="cuda", dtype=torch.float64)
+            m = t.clone()
+            torch.distributed.all_reduce(m[:1], op=torch.distributed.ReduceOp.MAX)
+            torch.distributed.all_reduce(t[1:], op=torch.distributed.ReduceOp.SUM)
+            ms, tot = float(m[0]), float(t[1])
+        return ms, tot
+
+    m_ms, m_tot = agg(mixed)
+    f = agg(fp64)
+    if rank != 0:
+        torch.distributed.destroy_process_group()
+        return
+    peak, peak_kind = peaks()
+    pr = mixed["prof"]
+    push_s = pr["push_ms"] / 1000.0
+    achieved = mixed["pushed"] * BYTES_MIXED / push_s / 1e9 if push_s > 0 else 0.0
+    solves_s = pr["solves"] / (pr["solve_ms"] / 1000.0) if pr["solve_ms"] > 0 else None
+    line = {
+        "metric": METRIC,
+        "value": m_tot / (m_ms / 1000.0),
+        "unit": "particle-steps/s",
+        "n_gpus": world,
+        "steps": a.steps,
+        "warmup": a.warmup,
+        "ms_per_step": m_ms / a.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32 particles + f64 Poisson refinement (mixed)",
+        "data": "synthetic",
+        "config": {"workload": f"rf sheath, 7-grain cluster, {wl.nx}x{wl.ny}x{wl.nz} cells, "
+                               f"{wl.n_e + wl.n_i:.0e} macroparticles, 13.56 MHz 100 V, 2 Pa",
+                   "parallelism": "replicas only" if world > 1 else "1 GPU",
+                   "l2": "inputs larger than L2 (particle arrays 320 MB mixed / 640 MB FP64)",
+                   "sort_every": 20, "tol": 1e-10},
+        "roofline": {"bound": "hbm", "kernel": "k_push32 (fused gather/push/MD/absorb/MCC/deposit)",
+                     "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "peak_kind": peak_kind, "bytes_per_particle_step": BYTES_MIXED, "traffic": None,
+                     "avg_launch_ms": pr["push_ms"] / max(pr["push_launches"], 1),
+                     "launches": pr["push_launches"]},
+        "poisson": {"solves_per_s": solves_s, "iterations_per_solve": pr["solve_iterations"] / max(pr["solves"], 1),
+                    "ms_per_solve": pr["solve_ms"] / max(pr["solves"], 1), "precision": "mixed"},
+        "gpu_launches": mixed["kernels"],
+        "clocks": mixed["clocks"],
+        "live_particles_end": mixed["live"],
+    }
+    if fp64 is not None:
+        fp = fp64["prof"]
+        fpush = fp["push_ms"] / 1000.0
+        fach = fp64["pushed"] * BYTES_FP64 / fpush / 1e9 if fpush > 0 else 0.0
+        line["fp64"] = {"value": f[1] / (f[0] / 1000.0), "unit": "particle-steps/s", "steps": fp64_steps(a),
+                        "ms_per_step": f[0] / fp64_steps(a),
+                        "push_achieved_gbs": fach, "push_frac": fach / peak,
+                        "poisson_solves_per_s": fp["solves"] / (fp["solve_ms"] / 1000.0) if fp["solve_ms"] else None,
+                        "poisson_iterations_per_solve": fp["solve_iterations"] / max(fp["solves"], 1),
+                        "mixed_speedup": (m_tot / m_ms) / (f[1] / f[0])}
+    if ee is not None:
+        line["e2e"] = ee
+    if not a.no_cpu:
+        v, t, n0 = oracle_sample(wl, 400_000, 4)
+        line["cpu_baseline"] = {"value": v, "unit": "particle-steps/s", "cores": 1, "kind": "oracle",
+                                "sample": f"{n0} of the 1e7 particles on the full 64x64x256 mesh with its 7 grains, "
+                                          f"4 steps incl. the exact Poisson solve, init excluded ({t:.1f} s)"}
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def fp64_steps(a):
+    return a.fp64_steps or max(a.steps // 4, 10)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,190 @@
+/*
+ * libpic — GB300 (sm_103a) PIC-MCC/PPPM particle cycle for electrons and Ar+
+ * ions in an rf argon sheath around a fixed, self-consistently charging dust
+ * cluster (Schleede et al., arXiv:1801.00972, Sec. III).
+ *
+ * The calls follow the paper's statement of the problem:
+ *   - mesh, electrodes and rf drive (Sec. III, Fig. 2: cuboid of cubic cells,
+ *     periodic laterally, metallic electrodes at both ends of the discharge
+ *     axis, lower electrode driven sinusoidally, upper grounded).  Here the
+ *     discharge axis is z: electrodes at z = 0 and z = nz*dx, periodic x, y.
+ *   - gas (Sec. III: neutral argon reservoir of constant density at 300 K;
+ *     Table I: e elastic, excitation, ionization; Ar+ elastic, charge
+ *     exchange; cross sections supplied by the caller as tables);
+ *   - grains (Sec. II-III: fixed positions and radii, perfect absorbers,
+ *     charge zero at the start, changed by one super-particle charge per
+ *     absorbed particle);
+ *   - super-particles (Sec. III: weight W real particles each, leapfrog push
+ *     of Eqs. 1-2 with time step dt, MD subcycling dt/40 near grains).
+ *
+ * Conventions for every call:
+ *   - SI units (m, s, V, m^-3, K, eV where stated).
+ *   - Pointers named *_host are host memory owned by the caller; the library
+ *     copies inputs during the call and writes outputs of the stated length.
+ *   - All device memory is allocated by pic_init and freed by pic_destroy.
+ *   - Work is queued on the stream given to pic_init (NULL: the legacy default
+ *     stream).  Calls that return data to the host synchronise that stream.
+ *   - No call aborts or throws.  A failed call returns a non-zero pic_status
+ *     and pic_last_error() describes it.  Errors that kernels detect
+ *     (capacity overflow, non-finite values, particles faster than one box
+ *     length per step) are latched on the device and returned by the next
+ *     call that synchronises.
+ */
+#ifndef PIC_H
+#define PIC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pic_ctx pic_ctx;
+
+typedef enum {
+    PIC_OK = 0,
+    PIC_EINVAL = 1,      /* invalid argument or length mismatch             */
+    PIC_ENOMEM = 2,      /* device or host allocation failed                */
+    PIC_ECUDA = 3,       /* a CUDA runtime call failed                      */
+    PIC_ECAPACITY = 4,   /* particle, child or fixed-point capacity exceeded */
+    PIC_ENONFINITE = 5,  /* non-finite value or a particle moved > one box  */
+    PIC_ENOTCONV = 6,    /* Poisson solve did not reach its tolerance       */
+    PIC_ETIMEOUT = 7     /* a bounded device wait ran out                   */
+} pic_status;
+
+typedef enum { PIC_FP64 = 0, PIC_MIXED = 1 } pic_precision;
+
+/* run flags (pic_run.flags) */
+#define PIC_F_NO_MCC      1   /* no Monte Carlo collisions                       */
+#define PIC_F_IONS_FROZEN 2   /* ions neither move nor collide (test use)        */
+#define PIC_F_MOMENTS     8   /* accumulate node moments after every step        */
+
+/* Mesh: nx*ny*nz cubic cells of edge dx.  Phi and rho live on the cell corners
+ * (Sec. III): nx*ny*(nz+1) nodes indexed (k*ny + j)*nx + i; x and y periodic,
+ * node planes k = 0 and k = nz are the electrodes.  nx, ny >= 4, nz >= 2. */
+typedef struct { int32_t nx, ny, nz; double dx; } pic_mesh;
+
+/* phi(z=0, t) = v_dc + v_rf sin(2 pi f_rf t + phase); phi(z=nz*dx) = v_top
+ * (Sec. II: 100 V amplitude at 13.56 MHz on the lower electrode, upper grounded). */
+typedef struct { double v_dc, v_rf, f_rf, phase, v_top; } pic_electrodes;
+
+/* Neutral argon (Sec. III, Table I).  xs_host holds 5 tables of n_xs values
+ * (m^2) on uniform energy grids: electron elastic, excitation, ionization
+ * (energy step de_e eV, energy = electron kinetic energy) and ion elastic,
+ * charge exchange (step de_i eV, energy = ion energy relative to the neutral).
+ * Linear interpolation between grid points; the last value beyond the grid.
+ * nu_max_e / nu_max_i bound n_gas * sum(sigma) * v for the null-collision
+ * method; a collision candidate occurs with probability 1 - exp(-nu_max dt). */
+typedef struct {
+    double n_gas, t_gas;          /* m^-3, K */
+    double eps_exc, eps_ion;      /* eV */
+    double nu_max_e, nu_max_i;    /* 1/s */
+    double de_e, de_i;            /* eV */
+    int32_t n_xs;
+    const double* xs_host;        /* 5 * n_xs */
+} pic_gas;
+
+/* Grains (Sec. II-III): n fixed spheres, centres pos_host (3n, metres) and
+ * radii radius_host (n, metres).  Each grain's cell must lie at least one cell
+ * away from both electrodes; no cell may lie in more than 8 grains' MD regions. */
+typedef struct { int32_t n; const double* pos_host; const double* radius_host; } pic_grains;
+
+/* Super-particles and time stepping.  Initial particles are given per species
+ * (0 = electrons, 1 = Ar+): positions x_host (3n, metres, inside the box),
+ * velocities v_host (3n, m/s, taken as v at t = -dt/2) and unique ids (n).
+ * capacity = particle slots per species (>= n; ionization adds particles). */
+typedef struct {
+    int64_t n[2];
+    const double* x_host[2];
+    const double* v_host[2];
+    const uint32_t* id_host[2];
+    int64_t capacity[2];
+    double weight;                /* real particles per super-particle, W */
+    double dt;                    /* s */
+    int32_t md_sub;               /* MD substeps per step (Sec. III: 40) */
+    int32_t sort_every;           /* counting-sort interval in steps (>= 1) */
+    uint64_t seed;
+    uint32_t run_id;
+    int32_t prec;                 /* pic_precision */
+    int32_t flags;                /* PIC_F_* */
+    double tol;                   /* Poisson relative residual tolerance (e.g. 1e-10) */
+    int32_t max_cycles;           /* Poisson refinement iterations per solve */
+} pic_run;
+
+/* Create a run: copies every input to the device, deposits rho_0 (particles
+ * plus grain charges, Sec. III), precomputes each grain's unit-charge mesh
+ * field (Eq. 5) and solves phi_0 at t = 0.  On success *out owns the run. */
+pic_status pic_init(const pic_mesh* mesh, const pic_electrodes* el, const pic_gas* gas,
+                    const pic_grains* grains, const pic_run* run, void* cuda_stream,
+                    pic_ctx** out);
+
+/* n_steps full time steps (Eqs. 1-6, MCC, absorption, deposit, Poisson), queued
+ * on the run's stream.  Returns the status of the previous steps' solves. */
+pic_status pic_step(pic_ctx* ctx, int32_t n_steps);
+
+/* The particle half of one step: CIC gather of -grad phi (Eq. 4), leapfrog push
+ * (Eqs. 1-2) with MD subcycling and the PPPM correction (Eqs. 5-6) near grains,
+ * electrode and grain absorption, null-collision MCC with ionization products,
+ * grain charge update and the fixed-point CIC deposit of rho_{k+1}; then
+ * step += 1.  Does not solve for phi. */
+pic_status pic_advance(pic_ctx* ctx);
+
+/* Solve Eq. 3 for the current rho with the electrode values at t = step*dt,
+ * warm-started from the current phi.  Optional outputs: refinement iterations
+ * used and final relative residual ||b - A phi|| / ||b|| (host pointers). */
+pic_status pic_solve(pic_ctx* ctx, int32_t* iterations, double* rel_residual);
+
+/* Grain state: n_abs_host (2*n: electrons, ions absorbed, cumulative, exact)
+ * and q_host (n: Q = e W (N_ion - N_e), coulomb). Either may be NULL. */
+pic_status pic_grain_charges(pic_ctx* ctx, int64_t* n_abs_host, double* q_host);
+
+/* Live particle counts (2) and event counters (PIC_C_N, cumulative). */
+#define PIC_C_LOST_BOT_E 0
+#define PIC_C_LOST_BOT_I 1
+#define PIC_C_LOST_TOP_E 2
+#define PIC_C_LOST_TOP_I 3
+#define PIC_C_ABS_E      4
+#define PIC_C_ABS_I      5
+#define PIC_C_E_EL       6
+#define PIC_C_E_EXC      7
+#define PIC_C_E_ION      8
+#define PIC_C_I_EL       9
+#define PIC_C_I_CX      10
+#define PIC_C_ERR       11
+#define PIC_C_PUSHED    12   /* live particles processed by the push kernels */
+#define PIC_C_N         13
+pic_status pic_counts(pic_ctx* ctx, int64_t* n_live_host /* 2 */, int64_t* counters_host /* PIC_C_N */);
+
+/* Window averages since the last reset (needs PIC_F_MOMENTS):
+ * what 0 phi (V, nodes), 1 n_e, 2 n_i (m^-3, nodes), 3 flux_e, 4 flux_i
+ * (m^-2 s^-1, 3 per node, node-major).  len = number of doubles in out_host. */
+pic_status pic_moments(pic_ctx* ctx, int32_t what, double* out_host, size_t len, int32_t reset);
+
+/* Parity and inspection hooks (same conventions; lengths are checked). */
+pic_status pic_get_particles(pic_ctx* ctx, int32_t species, double* x_host, double* v_host,
+                             uint32_t* id_host, int64_t cap, int64_t* n_out);
+pic_status pic_get_rho(pic_ctx* ctx, int64_t* rho_q_host, size_t len); /* units e W 2^-42 per node */
+pic_status pic_get_phi(pic_ctx* ctx, double* phi_host, size_t len);
+pic_status pic_set_phi(pic_ctx* ctx, const double* phi_host, size_t len);
+pic_status pic_get_grain_table(pic_ctx* ctx, double* tab_host, size_t len); /* n*64*3 */
+pic_status pic_set_grain_table(pic_ctx* ctx, const double* tab_host, size_t len);
+pic_status pic_set_grain_counts(pic_ctx* ctx, const int64_t* n_abs_host, size_t len);
+int64_t    pic_step_index(const pic_ctx* ctx);
+
+/* Measurement: from pic_profile(ctx, 1) on, CUDA events recorded on the run's
+ * stream bracket every push-kernel launch and every Poisson solve; pic_profile(ctx, 0)
+ * stops recording.  pic_profile_read returns the summed device time (ms) and
+ * counts since recording started, and the number of kernels the library has
+ * launched since pic_init (all kinds).  Any pointer may be NULL. */
+pic_status pic_profile(pic_ctx* ctx, int32_t enable);
+pic_status pic_profile_read(pic_ctx* ctx, double* push_ms, int64_t* push_launches, double* solve_ms,
+                            int64_t* solves, int64_t* solve_iterations, int64_t* kernels_launched);
+
+const char* pic_last_error(const pic_ctx* ctx);   /* NULL ctx: last pic_init failure */
+void pic_destroy(pic_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,1 +1,335 @@
-"""placeholder"""
+"""GB300 PIC-MCC/PPPM particle cycle (arXiv:1801.00972, Sec. III) behind a C ABI.
+
+This module is the thin Python binding of ``libpic.so``: ctypes structures
+that mirror ``include/pic.h`` and one function per C entry point, with the same
+names, doing argument marshalling only.  Every step of the method runs in the
+library's CUDA kernels; there is no CPU fallback.  Importing works without a
+GPU; the first call loads ``libpic.so`` and raises if it is missing.
+
+``Run`` wraps one run context for convenience (numpy in, numpy out).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libpic.so")
+_lock = threading.Lock()
+_lib = None
+
+PIC_OK, PIC_EINVAL, PIC_ENOMEM, PIC_ECUDA, PIC_ECAPACITY, PIC_ENONFINITE, PIC_ENOTCONV, PIC_ETIMEOUT = range(8)
+STATUS = {0: "PIC_OK", 1: "PIC_EINVAL", 2: "PIC_ENOMEM", 3: "PIC_ECUDA", 4: "PIC_ECAPACITY",
+          5: "PIC_ENONFINITE", 6: "PIC_ENOTCONV", 7: "PIC_ETIMEOUT"}
+PIC_FP64, PIC_MIXED = 0, 1
+PIC_F_NO_MCC, PIC_F_IONS_FROZEN, PIC_F_MOMENTS = 1, 2, 8
+COUNTERS = ("lost_bot_e", "lost_bot_i", "lost_top_e", "lost_top_i", "abs_e", "abs_i",
+            "e_el", "e_exc", "e_ion", "i_el", "i_cx", "err", "pushed")
+PIC_C_N = len(COUNTERS)
+
+# every symbol include/pic.h declares
+SYMBOLS = ("pic_init", "pic_step", "pic_advance", "pic_solve", "pic_grain_charges", "pic_counts",
+           "pic_moments", "pic_get_particles", "pic_get_rho", "pic_get_phi", "pic_set_phi",
+           "pic_get_grain_table", "pic_set_grain_table", "pic_set_grain_counts", "pic_step_index",
+           "pic_profile", "pic_profile_read", "pic_last_error", "pic_destroy")
+
+
+class pic_mesh(C.Structure):
+    _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("nz", C.c_int32), ("dx", C.c_double)]
+
+
+class pic_electrodes(C.Structure):
+    _fields_ = [("v_dc", C.c_double), ("v_rf", C.c_double), ("f_rf", C.c_double), ("phase", C.c_double),
+                ("v_top", C.c_double)]
+
+
+class pic_gas(C.Structure):
+    _fields_ = [("n_gas", C.c_double), ("t_gas", C.c_double), ("eps_exc", C.c_double), ("eps_ion", C.c_double),
+                ("nu_max_e", C.c_double), ("nu_max_i", C.c_double), ("de_e", C.c_double), ("de_i", C.c_double),
+                ("n_xs", C.c_int32), ("xs_host", C.POINTER(C.c_double))]
+
+
+class pic_grains(C.Structure):
+    _fields_ = [("n", C.c_int32), ("pos_host", C.POINTER(C.c_double)), ("radius_host", C.POINTER(C.c_double))]
+
+
+class pic_run(C.Structure):
+    _fields_ = [("n", C.c_int64 * 2), ("x_host", C.POINTER(C.c_double) * 2), ("v_host", C.POINTER(C.c_double) * 2),
+                ("id_host", C.POINTER(C.c_uint32) * 2), ("capacity", C.c_int64 * 2), ("weight", C.c_double),
+                ("dt", C.c_double), ("md_sub", C.c_int32), ("sort_every", C.c_int32), ("seed", C.c_uint64),
+                ("run_id", C.c_uint32), ("prec", C.c_int32), ("flags", C.c_int32), ("tol", C.c_double),
+                ("max_cycles", C.c_int32)]
+
+
+class PicError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+def load(path: str | None = None):
+    """Load libpic.so (built by ``paper_1801_00972_gb300.build``); raise if absent."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        p = path or LIB_PATH
+        if not os.path.exists(p):
+            raise RuntimeError(f"{p} is missing: build it with `python -m paper_1801_00972_gb300.build` "
+                               "(there is no CPU fallback)")
+        L = C.CDLL(p)
+        vp, i32, i64, sz, pd = C.c_void_p, C.c_int32, C.c_int64, C.c_size_t, C.POINTER(C.c_double)
+        pi64, pu32 = C.POINTER(C.c_int64), C.POINTER(C.c_uint32)
+        L.pic_init.argtypes = [C.POINTER(pic_mesh), C.POINTER(pic_electrodes), C.POINTER(pic_gas),
+                               C.POINTER(pic_grains), C.POINTER(pic_run), vp, C.POINTER(vp)]
+        sig = {
+            "pic_step": [vp, i32], "pic_advance": [vp], "pic_solve": [vp, C.POINTER(i32), pd],
+            "pic_grain_charges": [vp, pi64, pd], "pic_counts": [vp, pi64, pi64],
+            "pic_moments": [vp, i32, pd, sz, i32],
+            "pic_get_particles": [vp, i32, pd, pd, pu32, i64, pi64],
+            "pic_get_rho": [vp, pi64, sz], "pic_get_phi": [vp, pd, sz], "pic_set_phi": [vp, pd, sz],
+            "pic_get_grain_table": [vp, pd, sz], "pic_set_grain_table": [vp, pd, sz],
+            "pic_set_grain_counts": [vp, pi64, sz],
+            "pic_profile": [vp, i32], "pic_profile_read": [vp, pd, pi64, pd, pi64, pi64, pi64],
+        }
+        for name, args in sig.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = C.c_int
+        L.pic_init.restype = C.c_int
+        L.pic_step_index.argtypes = [vp]
+        L.pic_step_index.restype = i64
+        L.pic_last_error.argtypes = [vp]
+        L.pic_last_error.restype = C.c_char_p
+        L.pic_destroy.argtypes = [vp]
+        L.pic_destroy.restype = None
+        _lib = L
+        return L
+
+
+def _p(a, t):
+    return a.ctypes.data_as(C.POINTER(t))
+
+
+def _check(ctx, st):
+    if st != PIC_OK:
+        msg = load().pic_last_error(ctx)
+        raise PicError(st, msg.decode() if msg else "")
+    return st
+
+
+# ----------------------------------------------------------------- C-ABI mirrors
+def pic_init(mesh, electrodes, gas, grains, run, stream=None):
+    ctx = C.c_void_p()
+    st = load().pic_init(C.byref(mesh), C.byref(electrodes), C.byref(gas), C.byref(grains), C.byref(run),
+                         C.c_void_p(stream or 0), C.byref(ctx))
+    _check(None, st)
+    return ctx
+
+
+def pic_step(ctx, n_steps):
+    return _check(ctx, load().pic_step(ctx, int(n_steps)))
+
+
+def pic_advance(ctx):
+    return _check(ctx, load().pic_advance(ctx))
+
+
+def pic_solve(ctx):
+    it = C.c_int32()
+    res = C.c_double()
+    _check(ctx, load().pic_solve(ctx, C.byref(it), C.byref(res)))
+    return it.value, res.value
+
+
+def pic_grain_charges(ctx, ng):
+    n = np.zeros(2 * max(ng, 1), np.int64)
+    q = np.zeros(max(ng, 1))
+    _check(ctx, load().pic_grain_charges(ctx, _p(n, C.c_int64), _p(q, C.c_double)))
+    return n[: 2 * ng].reshape(ng, 2), q[:ng]
+
+
+def pic_counts(ctx):
+    n = np.zeros(2, np.int64)
+    c = np.zeros(PIC_C_N, np.int64)
+    _check(ctx, load().pic_counts(ctx, _p(n, C.c_int64), _p(c, C.c_int64)))
+    return n, dict(zip(COUNTERS, (int(x) for x in c)))
+
+
+def pic_moments(ctx, what, nodes, reset=False):
+    out = np.zeros(nodes * (3 if what >= 3 else 1))
+    _check(ctx, load().pic_moments(ctx, int(what), _p(out, C.c_double), out.size, int(bool(reset))))
+    return out
+
+
+def pic_get_particles(ctx, species, cap):
+    x = np.zeros((max(cap, 1), 3)); v = np.zeros((max(cap, 1), 3)); ids = np.zeros(max(cap, 1), np.uint32)
+    n = C.c_int64()
+    _check(ctx, load().pic_get_particles(ctx, int(species), _p(x, C.c_double), _p(v, C.c_double),
+                                         _p(ids, C.c_uint32), int(cap), C.byref(n)))
+    return x[: n.value], v[: n.value], ids[: n.value]
+
+
+def pic_get_rho(ctx, nodes):
+    a = np.zeros(nodes, np.int64)
+    _check(ctx, load().pic_get_rho(ctx, _p(a, C.c_int64), nodes))
+    return a
+
+
+def pic_get_phi(ctx, nodes):
+    a = np.zeros(nodes)
+    _check(ctx, load().pic_get_phi(ctx, _p(a, C.c_double), nodes))
+    return a
+
+
+def pic_set_phi(ctx, phi):
+    a = np.ascontiguousarray(phi, dtype=np.float64).reshape(-1)
+    return _check(ctx, load().pic_set_phi(ctx, _p(a, C.c_double), a.size))
+
+
+def pic_get_grain_table(ctx, ng):
+    a = np.zeros(max(ng, 1) * 192)
+    _check(ctx, load().pic_get_grain_table(ctx, _p(a, C.c_double), ng * 192))
+    return a[: ng * 192].reshape(ng, 4, 4, 4, 3)
+
+
+def pic_set_grain_table(ctx, tab):
+    a = np.ascontiguousarray(tab, dtype=np.float64).reshape(-1)
+    return _check(ctx, load().pic_set_grain_table(ctx, _p(a, C.c_double), a.size))
+
+
+def pic_set_grain_counts(ctx, n_abs):
+    a = np.ascontiguousarray(n_abs, dtype=np.int64).reshape(-1)
+    return _check(ctx, load().pic_set_grain_counts(ctx, _p(a, C.c_int64), a.size))
+
+
+def pic_profile(ctx, enable):
+    return _check(ctx, load().pic_profile(ctx, int(bool(enable))))
+
+
+def pic_profile_read(ctx):
+    pm, sm = C.c_double(), C.c_double()
+    pl, ns, it, kl = C.c_int64(), C.c_int64(), C.c_int64(), C.c_int64()
+    _check(ctx, load().pic_profile_read(ctx, C.byref(pm), C.byref(pl), C.byref(sm), C.byref(ns), C.byref(it),
+                                        C.byref(kl)))
+    return dict(push_ms=pm.value, push_launches=pl.value, solve_ms=sm.value, solves=ns.value,
+                solve_iterations=it.value, kernels=kl.value)
+
+
+def pic_step_index(ctx):
+    return load().pic_step_index(ctx)
+
+
+def pic_last_error(ctx=None):
+    m = load().pic_last_error(ctx)
+    return m.decode() if m else ""
+
+
+def pic_destroy(ctx):
+    load().pic_destroy(ctx)
+
+
+# ----------------------------------------------------------------- convenience
+class Run:
+    """One run context built from a workload description (see ``inputs.Workload``)
+    and initial particles [(x, v, id) for electrons, ions] in SI units."""
+
+    def __init__(self, wl, particles, prec=PIC_MIXED, flags=0, stream=None, capacity=None, sort_every=20,
+                 tol=1e-10, max_cycles=60, md_sub=None):
+        keep = []
+        mesh = pic_mesh(wl.nx, wl.ny, wl.nz, wl.dx)
+        el = pic_electrodes(wl.v_dc, wl.v_rf, wl.f_rf, wl.phase, wl.v_top)
+        xs = np.ascontiguousarray(wl.xs, dtype=np.float64)
+        keep.append(xs)
+        gas = pic_gas(wl.n_gas, wl.t_gas, wl.eps_exc, wl.eps_ion, wl.nu_max_e, wl.nu_max_i, wl.de_e, wl.de_i,
+                      xs.shape[1], _p(xs, C.c_double))
+        gp = np.ascontiguousarray(wl.grain_pos, dtype=np.float64).reshape(-1)
+        gr = np.ascontiguousarray(wl.grain_r, dtype=np.float64).reshape(-1)
+        keep += [gp, gr]
+        grains = pic_grains(gr.size, _p(gp, C.c_double), _p(gr, C.c_double))
+        run = pic_run()
+        for sp in range(2):
+            x, v, ids = particles[sp]
+            x = np.ascontiguousarray(x, dtype=np.float64).reshape(-1)
+            v = np.ascontiguousarray(v, dtype=np.float64).reshape(-1)
+            ids = np.ascontiguousarray(ids, dtype=np.uint32).reshape(-1)
+            keep += [x, v, ids]
+            run.n[sp] = ids.size
+            run.x_host[sp] = _p(x, C.c_double)
+            run.v_host[sp] = _p(v, C.c_double)
+            run.id_host[sp] = _p(ids, C.c_uint32)
+            cap = capacity[sp] if capacity is not None else int(ids.size * 1.25) + 4096
+            run.capacity[sp] = cap
+        run.weight, run.dt = wl.weight, wl.dt
+        run.md_sub = wl.md_sub if md_sub is None else md_sub
+        run.sort_every = sort_every
+        run.seed, run.run_id, run.prec, run.flags = wl.seed, wl.run_id, prec, flags
+        run.tol, run.max_cycles = tol, max_cycles
+        self.ctx = pic_init(mesh, el, gas, grains, run, stream)
+        self.wl = wl
+        self.nodes = wl.nx * wl.ny * (wl.nz + 1)
+        self.ng = gr.size
+        self.cap = [int(run.capacity[0]), int(run.capacity[1])]
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            pic_destroy(self.ctx)
+            self.ctx = None
+
+    __del__ = close
+
+    def step(self, n=1):
+        pic_step(self.ctx, n)
+
+    def advance(self):
+        pic_advance(self.ctx)
+
+    def solve(self):
+        return pic_solve(self.ctx)
+
+    def grains(self):
+        return pic_grain_charges(self.ctx, self.ng)
+
+    def counts(self):
+        return pic_counts(self.ctx)
+
+    def particles(self, sp, sort=True):
+        x, v, ids = pic_get_particles(self.ctx, sp, self.cap[sp])
+        if sort:
+            o = np.argsort(ids, kind="stable")
+            x, v, ids = x[o], v[o], ids[o]
+        return x, v, ids
+
+    def rho(self):
+        return pic_get_rho(self.ctx, self.nodes)
+
+    def phi(self):
+        return pic_get_phi(self.ctx, self.nodes)
+
+    def set_phi(self, phi):
+        pic_set_phi(self.ctx, phi)
+
+    def gtab(self):
+        return pic_get_grain_table(self.ctx, self.ng)
+
+    def set_gtab(self, tab):
+        pic_set_grain_table(self.ctx, tab)
+
+    def set_grain_counts(self, n_abs):
+        pic_set_grain_counts(self.ctx, n_abs)
+
+    def moments(self, what, reset=False):
+        return pic_moments(self.ctx, what, self.nodes, reset)
+
+    def profile(self, enable):
+        pic_profile(self.ctx, enable)
+
+    def profile_read(self):
+        return pic_profile_read(self.ctx)
+
+    @property
+    def step_index(self):
+        return pic_step_index(self.ctx)

@@ -1,0 +1,752 @@
+// Host side of libpic: argument checks, device allocation, the step driver and
+// the query calls of the C ABI declared in include/pic.h.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "pic_internal.cuh"
+
+namespace pic {
+
+void* dev_alloc(pic_ctx* c, size_t bytes)
+{
+    void* p = nullptr;
+    if (cudaMalloc(&p, bytes < 16 ? 16 : bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    c->allocs.push_back(p);
+    return p;
+}
+
+cudaEvent_t prof_begin(pic_ctx* c)
+{
+    if (!c->prof) return nullptr;
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    cudaEventRecord(e, c->stream);
+    return e;
+}
+
+void prof_end(pic_ctx* c, cudaEvent_t start, bool push)
+{
+    if (!c->prof || !start) return;
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) return;
+    cudaEventRecord(e, c->stream);
+    (push ? c->ev_push : c->ev_solve).emplace_back(start, e);
+}
+
+int grid_for(int64_t n, int threads, int max_blocks)
+{
+    int64_t b = (n + threads - 1) / threads;
+    if (b < 1) b = 1;
+    if (b > max_blocks) b = max_blocks;
+    return (int)b;
+}
+
+}  // namespace pic
+
+using namespace pic;
+
+namespace {
+
+thread_local std::string g_init_error;
+
+pic_status fail(pic_ctx* c, pic_status s, const std::string& msg)
+{
+    if (c) c->err = msg;
+    else g_init_error = msg;
+    return s;
+}
+
+pic_status cuda_fail(pic_ctx* c, cudaError_t e, const char* what)
+{
+    return fail(c, PIC_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+// cell index and in-cell fraction along one axis, clamped into the mesh
+inline void locate1(double x, double dx, int n, int& i, double& f)
+{
+    const double q = x / dx;
+    i = (int)std::floor(q);
+    if (i > n - 1) i = n - 1;
+    if (i < 0) i = 0;
+    f = q - (double)i;
+}
+
+double v_bottom(const pic_ctx* c)
+{
+    const double t = (double)c->step * c->dt;
+    return c->el.v_dc + c->el.v_rf * std::sin((2.0 * kPI * c->el.f_rf) * t + c->el.phase);
+}
+
+double rho_scale(const pic_ctx* c)
+{
+    const double dx = c->dx;
+    return (((kQE * c->W) / (dx * dx * dx)) * 0x1p-42) / kEPS0;
+}
+
+// device error word and pending solve status
+pic_status check(pic_ctx* c)
+{
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "stream");
+    int err = 0;
+    e = cudaMemcpy(&err, c->d_err, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(c, e, "error word");
+    if (err == PIC_ECAPACITY) return fail(c, PIC_ECAPACITY, "particle or ionization-product capacity exceeded");
+    if (err == PIC_ENONFINITE)
+        return fail(c, PIC_ENONFINITE, "non-finite particle state or a particle moved more than one box length");
+    if (err != 0) return fail(c, PIC_ECUDA, "device error " + std::to_string(err));
+    return PIC_OK;
+}
+
+void deposit_particles(pic_ctx* c)
+{
+    if (c->prec == PIC_MIXED) launch_deposit32(c);
+    else launch_deposit64(c);
+}
+
+pic_status solve_now(pic_ctx* c, double tol, int* iters, double* res)
+{
+    cudaEvent_t ev = prof_begin(c);
+    launch_rhs(c, rho_scale(c), v_bottom(c), c->el.v_top, true);
+    int it = 0;
+    const pic_status s = mg_solve(c, v_bottom(c), c->el.v_top, tol, c->max_cycles, &it, res);
+    prof_end(c, ev, false);
+    if (c->prof) c->prof_iters += it;
+    if (iters) *iters = it;
+    return s;
+}
+
+void drop_events(pic_ctx* c)
+{
+    for (auto* v : {&c->ev_push, &c->ev_solve}) {
+        for (auto& pr : *v) {
+            cudaEventDestroy(pr.first);
+            cudaEventDestroy(pr.second);
+        }
+        v->clear();
+    }
+    c->prof_iters = 0;
+}
+
+void drop_events(pic_ctx* c);
+
+void destroy(pic_ctx* c)
+{
+    if (!c) return;
+    drop_events(c);
+    for (void* p : c->allocs) cudaFree(p);
+    delete c;
+}
+
+bool finite_all(const double* p, size_t n)
+{
+    for (size_t i = 0; i < n; ++i)
+        if (!std::isfinite(p[i])) return false;
+    return true;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* pic_last_error(const pic_ctx* ctx) { return ctx ? ctx->err.c_str() : g_init_error.c_str(); }
+
+void pic_destroy(pic_ctx* ctx)
+{
+    if (ctx) cudaStreamSynchronize(ctx->stream);
+    destroy(ctx);
+}
+
+int64_t pic_step_index(const pic_ctx* ctx) { return ctx ? ctx->step : -1; }
+
+pic_status pic_init(const pic_mesh* mesh, const pic_electrodes* el, const pic_gas* gas, const pic_grains* grains,
+                    const pic_run* run, void* cuda_stream, pic_ctx** out)
+{
+    g_init_error.clear();
+    if (!out) return fail(nullptr, PIC_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!mesh || !el || !gas || !grains || !run) return fail(nullptr, PIC_EINVAL, "NULL argument");
+    const int nx = mesh->nx, ny = mesh->ny, nz = mesh->nz;
+    if (nx < 4 || ny < 4 || nz < 2 || nx % 2 || ny % 2)
+        return fail(nullptr, PIC_EINVAL, "mesh: nx, ny must be even and >= 4, nz >= 2");
+    if ((double)nx * ny * (nz + 1) > 2.0e9) return fail(nullptr, PIC_EINVAL, "mesh too large");
+    if (!(mesh->dx > 0.0) || !std::isfinite(mesh->dx)) return fail(nullptr, PIC_EINVAL, "mesh: dx must be > 0");
+    const double elv[5] = {el->v_dc, el->v_rf, el->f_rf, el->phase, el->v_top};
+    if (!finite_all(elv, 5)) return fail(nullptr, PIC_EINVAL, "electrodes: non-finite value");
+    if (gas->n_xs < 2 || !gas->xs_host || !(gas->de_e > 0) || !(gas->de_i > 0) || !(gas->n_gas >= 0) ||
+        !(gas->t_gas >= 0) || !(gas->nu_max_e >= 0) || !(gas->nu_max_i >= 0))
+        return fail(nullptr, PIC_EINVAL, "gas: need n_xs >= 2, tables, de > 0, non-negative densities and bounds");
+    if (!finite_all(gas->xs_host, 5 * (size_t)gas->n_xs)) return fail(nullptr, PIC_EINVAL, "gas: non-finite table");
+    if (grains->n < 0 || (grains->n > 0 && (!grains->pos_host || !grains->radius_host)))
+        return fail(nullptr, PIC_EINVAL, "grains: bad count or NULL arrays");
+    if (!(run->dt > 0.0) || !(run->weight >= 0.0) || run->md_sub < 1 || run->sort_every < 0 ||
+        (run->prec != PIC_FP64 && run->prec != PIC_MIXED) || !(run->tol > 0.0) || run->max_cycles < 1)
+        return fail(nullptr, PIC_EINVAL, "run: need dt > 0, weight >= 0, md_sub >= 1, sort_every >= 0, prec 0/1, "
+                                         "tol > 0, max_cycles >= 1");
+    const double Lx = nx * mesh->dx, Ly = ny * mesh->dx, Lz = nz * mesh->dx;
+    for (int sp = 0; sp < 2; ++sp) {
+        if (run->n[sp] < 0 || run->capacity[sp] < run->n[sp] || run->capacity[sp] > 0x7fffffffLL)
+            return fail(nullptr, PIC_EINVAL, "run: need 0 <= n <= capacity < 2^31");
+        if (run->n[sp] > 0 && (!run->x_host[sp] || !run->v_host[sp] || !run->id_host[sp]))
+            return fail(nullptr, PIC_EINVAL, "run: NULL particle arrays");
+        for (int64_t q = 0; q < run->n[sp]; ++q) {
+            const double* x = run->x_host[sp] + 3 * q;
+            const double* v = run->v_host[sp] + 3 * q;
+            if (!finite_all(x, 3) || !finite_all(v, 3) || x[0] < 0 || x[0] >= Lx || x[1] < 0 || x[1] >= Ly ||
+                x[2] < 0 || x[2] > Lz)
+                return fail(nullptr, PIC_EINVAL, "run: particle outside the box or non-finite");
+        }
+    }
+    // grains: inside the box, one cell clear of both electrodes, <= 8 per MD cell
+    std::vector<int> gcell(3 * (size_t)grains->n);
+    for (int g = 0; g < grains->n; ++g) {
+        const double* p = grains->pos_host + 3 * g;
+        if (!finite_all(p, 3) || p[0] < 0 || p[0] >= Lx || p[1] < 0 || p[1] >= Ly || p[2] < 0 || p[2] >= Lz ||
+            !(grains->radius_host[g] > 0.0) || !(grains->radius_host[g] < mesh->dx))
+            return fail(nullptr, PIC_EINVAL, "grains: centre outside the box or radius not in (0, dx)");
+        double f;
+        locate1(p[0], mesh->dx, nx, gcell[3 * g], f);
+        locate1(p[1], mesh->dx, ny, gcell[3 * g + 1], f);
+        locate1(p[2], mesh->dx, nz, gcell[3 * g + 2], f);
+        gcell[3 * g] = (int)std::floor(p[0] / mesh->dx);
+        gcell[3 * g + 1] = (int)std::floor(p[1] / mesh->dx);
+        gcell[3 * g + 2] = (int)std::floor(p[2] / mesh->dx);
+        if (gcell[3 * g + 2] < 1 || gcell[3 * g + 2] > nz - 2)
+            return fail(nullptr, PIC_EINVAL, "grains: a grain's cell must be at least one cell from each electrode");
+    }
+    const size_t cells = (size_t)nx * ny * nz, nodes = (size_t)nx * ny * (nz + 1);
+    std::vector<int> cell_ng(cells, 0), cell_g(cells * kMaxG, 0);
+    for (int g = 0; g < grains->n; ++g)
+        for (int dk = -1; dk <= 1; ++dk)
+            for (int dj = -1; dj <= 1; ++dj)
+                for (int di = -1; di <= 1; ++di) {
+                    const int i = (gcell[3 * g] + di + nx) % nx, j = (gcell[3 * g + 1] + dj + ny) % ny,
+                              k = gcell[3 * g + 2] + dk;
+                    const size_t ci = ((size_t)k * ny + j) * nx + i;
+                    if (cell_ng[ci] >= kMaxG) return fail(nullptr, PIC_EINVAL, "grains: more than 8 per MD cell");
+                    cell_g[ci * kMaxG + cell_ng[ci]++] = g;
+                }
+
+    pic_ctx* c = new (std::nothrow) pic_ctx();
+    if (!c) return fail(nullptr, PIC_ENOMEM, "host allocation");
+    c->nx = nx; c->ny = ny; c->nz = nz; c->dx = mesh->dx;
+    c->Lx = Lx; c->Ly = Ly; c->Lz = Lz;
+    c->nodes = nodes; c->cells = cells;
+    c->el = *el;
+    c->n_gas = gas->n_gas; c->t_gas = gas->t_gas; c->eps_exc = gas->eps_exc; c->eps_ion = gas->eps_ion;
+    c->nu_max[0] = gas->nu_max_e; c->nu_max[1] = gas->nu_max_i; c->de[0] = gas->de_e; c->de[1] = gas->de_i;
+    c->n_xs = gas->n_xs;
+    c->ng = grains->n;
+    c->prec = run->prec; c->flags = run->flags; c->md_sub = run->md_sub; c->sort_every = run->sort_every;
+    c->max_cycles = run->max_cycles;
+    c->W = run->weight; c->dt = run->dt; c->tol = run->tol;
+    c->seed = run->seed; c->run_id = run->run_id;
+    c->key = make_uint2((uint32_t)run->seed ^ run->run_id, (uint32_t)(run->seed >> 32));
+    c->qm[0] = -kQE / kME; c->qm[1] = kQE / kMAR;
+    c->hm[0] = (0.5 * kME) / kQE; c->hm[1] = (0.5 * kMAR) / kQE;
+    c->pnull[0] = 1.0 - std::exp(-gas->nu_max_e * run->dt);
+    c->pnull[1] = 1.0 - std::exp(-gas->nu_max_i * run->dt);
+    c->sig_n = std::sqrt(kKB * gas->t_gas / kMAR);
+    c->stream = (cudaStream_t)cuda_stream;
+    c->step = 0;
+    for (int sp = 0; sp < 2; ++sp) c->cap[sp] = std::max<int64_t>(run->capacity[sp], 1);
+    c->child_cap = std::max<int64_t>(4096, std::max(c->cap[0], c->cap[1]) / 64);
+
+    const bool mixed = c->prec == PIC_MIXED;
+    const size_t psz = mixed ? sizeof(float4) : sizeof(double4);
+    bool ok = true;
+    for (int sp = 0; sp < 2; ++sp) {
+        c->pos[sp] = dev_alloc(c, psz * c->cap[sp]);
+        c->vel[sp] = dev_alloc(c, psz * c->cap[sp]);
+        c->pos_alt[sp] = dev_alloc(c, psz * c->cap[sp]);
+        c->vel_alt[sp] = dev_alloc(c, psz * c->cap[sp]);
+        ok = ok && c->pos[sp] && c->vel[sp] && c->pos_alt[sp] && c->vel_alt[sp];
+    }
+    c->d_nslot = (unsigned long long*)dev_alloc(c, 2 * sizeof(unsigned long long));
+    c->d_cnt = (unsigned long long*)dev_alloc(c, PIC_C_N * sizeof(unsigned long long));
+    c->d_err = (int*)dev_alloc(c, sizeof(int));
+    c->d_nch = (unsigned long long*)dev_alloc(c, sizeof(unsigned long long));
+    c->d_next_id = (unsigned int*)dev_alloc(c, sizeof(unsigned int));
+    c->d_child = (ChildRec*)dev_alloc(c, sizeof(ChildRec) * c->child_cap);
+    c->rq = (unsigned long long*)dev_alloc(c, sizeof(unsigned long long) * nodes);
+    c->phi = (double*)dev_alloc(c, sizeof(double) * nodes);
+    c->phi_alt = (double*)dev_alloc(c, sizeof(double) * nodes);
+    c->f64 = (double*)dev_alloc(c, sizeof(double) * nodes);
+    if (mixed) c->e32 = (float4*)dev_alloc(c, sizeof(float4) * nodes);
+    else c->e64 = (double*)dev_alloc(c, sizeof(double) * 3 * nodes);
+    c->d_norm = (double*)dev_alloc(c, 4 * sizeof(double));
+    c->xs64 = (double*)dev_alloc(c, sizeof(double) * 5 * c->n_xs);
+    c->xs32 = (float*)dev_alloc(c, sizeof(float) * 5 * c->n_xs);
+    const int ng1 = std::max(c->ng, 1);
+    c->gpos = (double*)dev_alloc(c, sizeof(double) * 3 * ng1);
+    c->grad = (double*)dev_alloc(c, sizeof(double) * ng1);
+    c->gcell = (int*)dev_alloc(c, sizeof(int) * 3 * ng1);
+    c->gq = (double*)dev_alloc(c, sizeof(double) * ng1);
+    c->gabs = (unsigned long long*)dev_alloc(c, sizeof(unsigned long long) * 2 * ng1);
+    c->gtab = (double*)dev_alloc(c, sizeof(double) * kTab * ng1);
+    c->gtab32 = (float*)dev_alloc(c, sizeof(float) * kTab * ng1);
+    c->gq32 = (float*)dev_alloc(c, sizeof(float) * ng1);
+    c->goff32 = (float*)dev_alloc(c, sizeof(float) * 3 * ng1);
+    c->gr2_32 = (float*)dev_alloc(c, sizeof(float) * ng1);
+    c->cell_ng = (int*)dev_alloc(c, sizeof(int) * cells);
+    c->cell_g = (int*)dev_alloc(c, sizeof(int) * cells * kMaxG);
+    c->cursor = (unsigned int*)dev_alloc(c, sizeof(unsigned int) * (cells + 1));
+    if (c->flags & PIC_F_MOMENTS) {
+        c->mom[0] = (double*)dev_alloc(c, sizeof(double) * 4 * nodes);
+        c->mom[1] = (double*)dev_alloc(c, sizeof(double) * 4 * nodes);
+        c->mphi = (double*)dev_alloc(c, sizeof(double) * nodes);
+        ok = ok && c->mom[0] && c->mom[1] && c->mphi;
+    }
+    ok = ok && c->d_nslot && c->d_cnt && c->d_err && c->d_nch && c->d_next_id && c->d_child && c->rq && c->phi &&
+         c->phi_alt && c->f64 && (c->e32 || c->e64) && c->d_norm && c->xs64 && c->xs32 && c->gpos && c->grad &&
+         c->gcell && c->gq && c->gabs && c->gtab && c->gtab32 && c->gq32 && c->goff32 && c->gr2_32 && c->cell_ng &&
+         c->cell_g && c->cursor;
+    if (!ok || !sort_scratch_setup(c) || mg_setup(c) != PIC_OK) {
+        destroy(c);
+        return fail(nullptr, PIC_ENOMEM, "device allocation failed");
+    }
+
+    // ---- upload inputs
+    std::vector<char> stage;
+    unsigned int max_id = 0;
+    bool any = false;
+    unsigned long long nslot[2] = {(unsigned long long)run->n[0], (unsigned long long)run->n[1]};
+    for (int sp = 0; sp < 2; ++sp) {
+        const int64_t n = run->n[sp];
+        stage.assign(2 * psz * std::max<int64_t>(n, 1), 0);
+        char* P = stage.data();
+        char* V = stage.data() + psz * std::max<int64_t>(n, 1);
+        for (int64_t q = 0; q < n; ++q) {
+            const double* x = run->x_host[sp] + 3 * q;
+            const double* v = run->v_host[sp] + 3 * q;
+            const uint32_t id = run->id_host[sp][q];
+            if (!any || id > max_id) { max_id = id; any = true; }
+            int ci[3];
+            double f[3];
+            const int nn[3] = {nx, ny, nz};
+            for (int a = 0; a < 3; ++a) locate1(x[a], mesh->dx, nn[a], ci[a], f[a]);
+            const int cell = (ci[2] * ny + ci[1]) * nx + ci[0];
+            if (mixed) {
+                float4 p, w;
+                float o[3];
+                for (int a = 0; a < 3; ++a) o[a] = std::min((float)f[a], 0.99999994f);
+                p = make_float4(o[0], o[1], o[2], 0.f);
+                std::memcpy(&p.w, &cell, 4);
+                const double s = run->dt / mesh->dx;
+                w = make_float4((float)(v[0] * s), (float)(v[1] * s), (float)(v[2] * s), 0.f);
+                std::memcpy(&w.w, &id, 4);
+                std::memcpy(P + psz * q, &p, psz);
+                std::memcpy(V + psz * q, &w, psz);
+            } else {
+                const double4 p = make_double4(x[0], x[1], x[2], (double)cell);
+                const double4 w = make_double4(v[0], v[1], v[2], (double)id);
+                std::memcpy(P + psz * q, &p, psz);
+                std::memcpy(V + psz * q, &w, psz);
+            }
+        }
+        cudaError_t e = cudaMemcpy(c->pos[sp], P, psz * n, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(c->vel[sp], V, psz * n, cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) { destroy(c); return cuda_fail(nullptr, e, "particle upload"); }
+    }
+    const unsigned int next_id = any ? max_id + 1 : 0;
+    std::vector<float> xs32(5 * (size_t)c->n_xs);
+    for (size_t i = 0; i < xs32.size(); ++i) xs32[i] = (float)gas->xs_host[i];
+    std::vector<double> gpos(3 * ng1, 0.0), grad(ng1, 0.0);
+    std::vector<float> goff(3 * ng1, 0.f), gr2(ng1, 0.f);
+    for (int g = 0; g < c->ng; ++g) {
+        for (int a = 0; a < 3; ++a) {
+            gpos[3 * g + a] = grains->pos_host[3 * g + a];
+            goff[3 * g + a] = (float)(grains->pos_host[3 * g + a] / mesh->dx - gcell[3 * g + a]);
+        }
+        grad[g] = grains->radius_host[g];
+        gr2[g] = (float)((grad[g] / mesh->dx) * (grad[g] / mesh->dx));
+    }
+    gcell.resize(3 * ng1, 0);
+    cudaError_t e = cudaSuccess;
+    auto up = [&](void* d, const void* h, size_t b) {
+        if (e == cudaSuccess && b) e = cudaMemcpy(d, h, b, cudaMemcpyHostToDevice);
+    };
+    up(c->d_nslot, nslot, sizeof nslot);
+    up(c->d_next_id, &next_id, sizeof next_id);
+    up(c->xs64, gas->xs_host, sizeof(double) * 5 * c->n_xs);
+    up(c->xs32, xs32.data(), sizeof(float) * xs32.size());
+    up(c->gpos, gpos.data(), sizeof(double) * gpos.size());
+    up(c->grad, grad.data(), sizeof(double) * grad.size());
+    up(c->gcell, gcell.data(), sizeof(int) * gcell.size());
+    up(c->goff32, goff.data(), sizeof(float) * goff.size());
+    up(c->gr2_32, gr2.data(), sizeof(float) * gr2.size());
+    up(c->cell_ng, cell_ng.data(), sizeof(int) * cells);
+    up(c->cell_g, cell_g.data(), sizeof(int) * cells * kMaxG);
+    if (e == cudaSuccess) e = cudaMemset(c->d_cnt, 0, PIC_C_N * sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMemset(c->d_err, 0, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(c->d_nch, 0, sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMemset(c->gabs, 0, sizeof(unsigned long long) * 2 * ng1);
+    if (e == cudaSuccess) e = cudaMemset(c->gq, 0, sizeof(double) * ng1);
+    if (e == cudaSuccess) e = cudaMemset(c->gq32, 0, sizeof(float) * ng1);
+    if (e == cudaSuccess) e = cudaMemset(c->phi, 0, sizeof(double) * nodes);
+    if (e == cudaSuccess && c->mphi) e = cudaMemset(c->mphi, 0, sizeof(double) * nodes);
+    if (e == cudaSuccess && c->mom[0]) e = cudaMemset(c->mom[0], 0, sizeof(double) * 4 * nodes);
+    if (e == cudaSuccess && c->mom[1]) e = cudaMemset(c->mom[1], 0, sizeof(double) * 4 * nodes);
+    if (e != cudaSuccess) { destroy(c); return cuda_fail(nullptr, e, "upload"); }
+
+    // ---- unit-charge mesh field of each grain on its region nodes (Eq. 5)
+    {
+        const double dx = mesh->dx;
+        const double scale1 = ((1.0 / (dx * dx * dx)) * 0x1p-42) / kEPS0;
+        std::vector<unsigned long long> one(2 * ng1, 0);
+        for (int g = 0; g < c->ng; ++g) {
+            // deposit a unit charge at grain g alone: set its count so that net = +1
+            std::fill(one.begin(), one.end(), 0ull);
+            one[2 * g + 1] = 1;
+            cudaMemcpyAsync(c->gabs, one.data(), sizeof(unsigned long long) * 2 * ng1, cudaMemcpyHostToDevice,
+                            c->stream);
+            cudaMemsetAsync(c->rq, 0, sizeof(unsigned long long) * nodes, c->stream);
+            launch_grains(c);
+            launch_rhs(c, scale1, 0.0, 0.0, true);
+            cudaMemsetAsync(c->phi, 0, sizeof(double) * nodes, c->stream);
+            int it = 0;
+            double res = 0;
+            const pic_status s = mg_solve(c, 0.0, 0.0, 1e-12, 200, &it, &res);
+            if (s != PIC_OK) {
+                destroy(c);
+                return fail(nullptr, s, "grain field solve did not converge");
+            }
+            launch_grain_table(c, g);
+        }
+        cudaMemsetAsync(c->gabs, 0, sizeof(unsigned long long) * 2 * ng1, c->stream);
+        cudaMemsetAsync(c->phi, 0, sizeof(double) * nodes, c->stream);
+        std::vector<double> tab(kTab * (size_t)ng1);
+        e = cudaMemcpyAsync(tab.data(), c->gtab, sizeof(double) * tab.size(), cudaMemcpyDeviceToHost, c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+        std::vector<float> tab32(tab.size());
+        for (size_t i = 0; i < tab.size(); ++i) tab32[i] = (float)tab[i];
+        if (e == cudaSuccess) e = cudaMemcpy(c->gtab32, tab32.data(), sizeof(float) * tab32.size(),
+                                             cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) { destroy(c); return cuda_fail(nullptr, e, "grain tables"); }
+    }
+
+    // ---- rho_0 and phi_0
+    cudaMemsetAsync(c->rq, 0, sizeof(unsigned long long) * nodes, c->stream);
+    deposit_particles(c);
+    launch_grains(c);
+    const pic_status s = solve_now(c, c->tol, nullptr, nullptr);
+    if (s != PIC_OK && s != PIC_ENOTCONV) {
+        destroy(c);
+        return fail(nullptr, s, "initial solve failed");
+    }
+    const pic_status k = check(c);
+    if (k != PIC_OK) {
+        std::string m = c->err;
+        destroy(c);
+        return fail(nullptr, k, m);
+    }
+    if (s == PIC_ENOTCONV) c->pending = PIC_ENOTCONV;
+    *out = c;
+    return PIC_OK;
+}
+
+pic_status pic_advance(pic_ctx* c)
+{
+    if (!c) return PIC_EINVAL;
+    const bool mixed = c->prec == PIC_MIXED;
+    cudaMemsetAsync(c->rq, 0, sizeof(unsigned long long) * c->nodes, c->stream);
+    if (mixed) {
+        launch_efield32(c);
+        launch_push32(c);
+        launch_children32(c);
+    } else {
+        launch_efield64(c);
+        launch_push64(c);
+        launch_children64(c);
+    }
+    launch_grains(c);
+    c->step += 1;
+    if (c->sort_every > 0 && c->step % c->sort_every == 0) {
+        sort_particles(c, 0);
+        sort_particles(c, 1);
+    }
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(c, e, "advance launch");
+    return PIC_OK;
+}
+
+pic_status pic_solve(pic_ctx* c, int32_t* iterations, double* rel_residual)
+{
+    if (!c) return PIC_EINVAL;
+    int it = 0;
+    double res = 0.0;
+    const pic_status s = solve_now(c, c->tol, &it, &res);
+    if (iterations) *iterations = it;
+    if (rel_residual) *rel_residual = res;
+    const pic_status k = check(c);
+    if (k != PIC_OK) return k;
+    if (s == PIC_ENOTCONV) return fail(c, s, "Poisson solve did not reach the tolerance");
+    if (s != PIC_OK) return fail(c, s, "Poisson solve failed");
+    return PIC_OK;
+}
+
+pic_status pic_step(pic_ctx* c, int32_t n_steps)
+{
+    if (!c || n_steps < 0) return PIC_EINVAL;
+    if (c->pending != PIC_OK) {
+        const pic_status p = c->pending;
+        c->pending = PIC_OK;
+        return fail(c, p, "an earlier solve did not converge");
+    }
+    for (int32_t s = 0; s < n_steps; ++s) {
+        pic_status r = pic_advance(c);
+        if (r != PIC_OK) return r;
+        int it = 0;
+        double res = 0.0;
+        r = solve_now(c, c->tol, &it, &res);
+        if (r == PIC_ENOTCONV) c->pending = PIC_ENOTCONV;
+        else if (r != PIC_OK) return fail(c, r, "Poisson solve failed");
+        if (c->flags & PIC_F_MOMENTS) {
+            if (c->prec == PIC_MIXED) launch_moments32(c);
+            else launch_moments64(c);
+            launch_moments_phi(c);
+            c->msteps += 1;
+        }
+    }
+    return check(c);
+}
+
+pic_status pic_grain_charges(pic_ctx* c, int64_t* n_abs_host, double* q_host)
+{
+    if (!c) return PIC_EINVAL;
+    pic_status k = check(c);
+    if (k != PIC_OK) return k;
+    if (c->ng == 0) return PIC_OK;
+    cudaError_t e = cudaSuccess;
+    if (n_abs_host) e = cudaMemcpy(n_abs_host, c->gabs, sizeof(int64_t) * 2 * c->ng, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && q_host) e = cudaMemcpy(q_host, c->gq, sizeof(double) * c->ng, cudaMemcpyDeviceToHost);
+    return e == cudaSuccess ? PIC_OK : cuda_fail(c, e, "grain copy");
+}
+
+namespace {
+// copy the slots of one species to the host and keep the live ones, in SI
+pic_status fetch(pic_ctx* c, int sp, std::vector<double>& x, std::vector<double>& v, std::vector<uint32_t>& id)
+{
+    unsigned long long ns[2];
+    cudaError_t e = cudaMemcpy(ns, c->d_nslot, sizeof ns, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(c, e, "slot count");
+    const size_t n = (size_t)ns[sp];
+    x.clear(); v.clear(); id.clear();
+    if (c->prec == PIC_MIXED) {
+        std::vector<float4> P(n), V(n);
+        e = cudaMemcpy(P.data(), c->pos[sp], sizeof(float4) * n, cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess) e = cudaMemcpy(V.data(), c->vel[sp], sizeof(float4) * n, cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return cuda_fail(c, e, "particle copy");
+        const double vs = c->dx / c->dt;
+        for (size_t q = 0; q < n; ++q) {
+            int cell;
+            std::memcpy(&cell, &P[q].w, 4);
+            if (cell < 0) continue;
+            const int i = cell % c->nx, j = (cell / c->nx) % c->ny, k = cell / (c->nx * c->ny);
+            x.push_back((i + (double)P[q].x) * c->dx);
+            x.push_back((j + (double)P[q].y) * c->dx);
+            x.push_back((k + (double)P[q].z) * c->dx);
+            v.push_back(V[q].x * vs); v.push_back(V[q].y * vs); v.push_back(V[q].z * vs);
+            uint32_t u;
+            std::memcpy(&u, &V[q].w, 4);
+            id.push_back(u);
+        }
+    } else {
+        std::vector<double4> P(n), V(n);
+        e = cudaMemcpy(P.data(), c->pos[sp], sizeof(double4) * n, cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess) e = cudaMemcpy(V.data(), c->vel[sp], sizeof(double4) * n, cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return cuda_fail(c, e, "particle copy");
+        for (size_t q = 0; q < n; ++q) {
+            if (P[q].w < 0.0) continue;
+            x.push_back(P[q].x); x.push_back(P[q].y); x.push_back(P[q].z);
+            v.push_back(V[q].x); v.push_back(V[q].y); v.push_back(V[q].z);
+            id.push_back((uint32_t)V[q].w);
+        }
+    }
+    return PIC_OK;
+}
+}  // namespace
+
+pic_status pic_counts(pic_ctx* c, int64_t* n_live, int64_t* counters)
+{
+    if (!c) return PIC_EINVAL;
+    pic_status k = check(c);
+    if (k != PIC_OK) return k;
+    if (n_live) {
+        for (int sp = 0; sp < 2; ++sp) {
+            std::vector<double> x, v;
+            std::vector<uint32_t> id;
+            k = fetch(c, sp, x, v, id);
+            if (k != PIC_OK) return k;
+            n_live[sp] = (int64_t)id.size();
+        }
+    }
+    if (counters) {
+        const cudaError_t e = cudaMemcpy(counters, c->d_cnt, sizeof(int64_t) * PIC_C_N, cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return cuda_fail(c, e, "counters");
+    }
+    return PIC_OK;
+}
+
+pic_status pic_get_particles(pic_ctx* c, int32_t sp, double* x_host, double* v_host, uint32_t* id_host, int64_t cap,
+                             int64_t* n_out)
+{
+    if (!c || sp < 0 || sp > 1) return PIC_EINVAL;
+    pic_status k = check(c);
+    if (k != PIC_OK) return k;
+    std::vector<double> x, v;
+    std::vector<uint32_t> id;
+    k = fetch(c, sp, x, v, id);
+    if (k != PIC_OK) return k;
+    if (n_out) *n_out = (int64_t)id.size();
+    if ((int64_t)id.size() > cap) return fail(c, PIC_EINVAL, "particle buffer too small");
+    if (x_host) std::memcpy(x_host, x.data(), sizeof(double) * x.size());
+    if (v_host) std::memcpy(v_host, v.data(), sizeof(double) * v.size());
+    if (id_host) std::memcpy(id_host, id.data(), sizeof(uint32_t) * id.size());
+    return PIC_OK;
+}
+
+pic_status pic_get_rho(pic_ctx* c, int64_t* rq, size_t len)
+{
+    if (!c || !rq || len != c->nodes) return c ? fail(c, PIC_EINVAL, "rho length") : PIC_EINVAL;
+    pic_status k = check(c);
+    if (k != PIC_OK) return k;
+    const cudaError_t e = cudaMemcpy(rq, c->rq, sizeof(int64_t) * len, cudaMemcpyDeviceToHost);
+    return e == cudaSuccess ? PIC_OK : cuda_fail(c, e, "rho copy");
+}
+
+pic_status pic_get_phi(pic_ctx* c, double* phi, size_t len)
+{
+    if (!c || !phi || len != c->nodes) return c ? fail(c, PIC_EINVAL, "phi length") : PIC_EINVAL;
+    pic_status k = check(c);
+    if (k != PIC_OK) return k;
+    const cudaError_t e = cudaMemcpy(phi, c->phi, sizeof(double) * len, cudaMemcpyDeviceToHost);
+    return e == cudaSuccess ? PIC_OK : cuda_fail(c, e, "phi copy");
+}
+
+pic_status pic_set_phi(pic_ctx* c, const double* phi, size_t len)
+{
+    if (!c || !phi || len != c->nodes) return c ? fail(c, PIC_EINVAL, "phi length") : PIC_EINVAL;
+    pic_status k = check(c);
+    if (k != PIC_OK) return k;
+    const cudaError_t e = cudaMemcpy(c->phi, phi, sizeof(double) * len, cudaMemcpyHostToDevice);
+    return e == cudaSuccess ? PIC_OK : cuda_fail(c, e, "phi copy");
+}
+
+pic_status pic_get_grain_table(pic_ctx* c, double* tab, size_t len)
+{
+    if (!c || (len && !tab) || len != (size_t)kTab * c->ng) return c ? fail(c, PIC_EINVAL, "table length") : PIC_EINVAL;
+    pic_status k = check(c);
+    if (k != PIC_OK || !len) return k;
+    const cudaError_t e = cudaMemcpy(tab, c->gtab, sizeof(double) * len, cudaMemcpyDeviceToHost);
+    return e == cudaSuccess ? PIC_OK : cuda_fail(c, e, "table copy");
+}
+
+pic_status pic_set_grain_table(pic_ctx* c, const double* tab, size_t len)
+{
+    if (!c || (len && !tab) || len != (size_t)kTab * c->ng) return c ? fail(c, PIC_EINVAL, "table length") : PIC_EINVAL;
+    pic_status k = check(c);
+    if (k != PIC_OK || !len) return k;
+    std::vector<float> t32(len);
+    for (size_t i = 0; i < len; ++i) t32[i] = (float)tab[i];
+    cudaError_t e = cudaMemcpy(c->gtab, tab, sizeof(double) * len, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(c->gtab32, t32.data(), sizeof(float) * len, cudaMemcpyHostToDevice);
+    return e == cudaSuccess ? PIC_OK : cuda_fail(c, e, "table copy");
+}
+
+pic_status pic_set_grain_counts(pic_ctx* c, const int64_t* n_abs, size_t len)
+{
+    if (!c || (len && !n_abs) || len != (size_t)2 * c->ng) return c ? fail(c, PIC_EINVAL, "count length") : PIC_EINVAL;
+    pic_status k = check(c);
+    if (k != PIC_OK) return k;
+    if (len) {
+        for (size_t i = 0; i < len; ++i)
+            if (n_abs[i] < 0) return fail(c, PIC_EINVAL, "negative count");
+        const cudaError_t e = cudaMemcpy(c->gabs, n_abs, sizeof(int64_t) * len, cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return cuda_fail(c, e, "count copy");
+    }
+    cudaMemsetAsync(c->rq, 0, sizeof(unsigned long long) * c->nodes, c->stream);
+    deposit_particles(c);
+    launch_grains(c);
+    return pic_solve(c, nullptr, nullptr);
+}
+
+pic_status pic_profile(pic_ctx* c, int32_t enable)
+{
+    if (!c) return PIC_EINVAL;
+    const pic_status k = check(c);
+    if (k != PIC_OK) return k;
+    drop_events(c);
+    c->prof = enable ? 1 : 0;
+    return PIC_OK;
+}
+
+pic_status pic_profile_read(pic_ctx* c, double* push_ms, int64_t* push_launches, double* solve_ms, int64_t* solves,
+                            int64_t* solve_iterations, int64_t* kernels_launched)
+{
+    if (!c) return PIC_EINVAL;
+    const pic_status k = check(c);
+    if (k != PIC_OK) return k;
+    double t[2] = {0.0, 0.0};
+    int idx = 0;
+    for (auto* v : {&c->ev_push, &c->ev_solve}) {
+        for (auto& pr : *v) {
+            float ms = 0.f;
+            const cudaError_t e = cudaEventElapsedTime(&ms, pr.first, pr.second);
+            if (e != cudaSuccess) return cuda_fail(c, e, "event time");
+            t[idx] += ms;
+        }
+        ++idx;
+    }
+    if (push_ms) *push_ms = t[0];
+    if (push_launches) *push_launches = (int64_t)c->ev_push.size();
+    if (solve_ms) *solve_ms = t[1];
+    if (solves) *solves = (int64_t)c->ev_solve.size();
+    if (solve_iterations) *solve_iterations = c->prof_iters;
+    if (kernels_launched) *kernels_launched = c->launches;
+    return PIC_OK;
+}
+
+pic_status pic_moments(pic_ctx* c, int32_t what, double* out, size_t len, int32_t reset)
+{
+    if (!c) return PIC_EINVAL;
+    if (!(c->flags & PIC_F_MOMENTS)) return fail(c, PIC_EINVAL, "moments need PIC_F_MOMENTS at init");
+    if (what < 0 || what > 4) return fail(c, PIC_EINVAL, "moments: what in 0..4");
+    const size_t need = (what >= 3 ? 3 : 1) * c->nodes;
+    if (!out || len != need) return fail(c, PIC_EINVAL, "moments length");
+    pic_status k = check(c);
+    if (k != PIC_OK) return k;
+    if (c->msteps == 0) return fail(c, PIC_EINVAL, "moments: empty window");
+    const double norm = c->W / ((c->dx * c->dx * c->dx) * (double)c->msteps);
+    cudaError_t e;
+    if (what == 0) {
+        e = cudaMemcpy(out, c->mphi, sizeof(double) * c->nodes, cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return cuda_fail(c, e, "moments copy");
+        for (size_t q = 0; q < c->nodes; ++q) out[q] /= (double)c->msteps;
+    } else {
+        std::vector<double> m(4 * c->nodes);
+        e = cudaMemcpy(m.data(), c->mom[(what - 1) % 2], sizeof(double) * m.size(), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return cuda_fail(c, e, "moments copy");
+        for (size_t q = 0; q < c->nodes; ++q) {
+            if (what <= 2) out[q] = m[4 * q] * norm;
+            else
+                for (int a = 0; a < 3; ++a) out[3 * q + a] = m[4 * q + 1 + a] * norm;
+        }
+    }
+    if (reset) {
+        cudaMemsetAsync(c->mom[0], 0, sizeof(double) * 4 * c->nodes, c->stream);
+        cudaMemsetAsync(c->mom[1], 0, sizeof(double) * 4 * c->nodes, c->stream);
+        cudaMemsetAsync(c->mphi, 0, sizeof(double) * c->nodes, c->stream);
+        c->msteps = 0;
+    }
+    return check(c);
+}
+
+}  // extern "C"

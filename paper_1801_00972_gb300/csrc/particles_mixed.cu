@@ -1,0 +1,619 @@
+// Mixed-precision particle cycle (Sec. III).  Same steps as the FP64 path
+// (gather of -grad phi, Eqs. 1-2 leapfrog, MD subcycling with Eqs. 5-6 near
+// grains, absorption, null-collision MCC of Table I, fixed-point CIC deposit)
+// on a compact layout:
+//   pos float4 {ox, oy, oz, cell}: in-cell offsets in [0,1) and the linear cell
+//       index (int bits; -1 = dead slot), so positions keep ~6e-8 cell
+//       resolution anywhere in the box;
+//   vel float4 {vx, vy, vz, id}: velocity in cells per step, particle id bits.
+// The push works in cell units: v += (q/m) E dt^2/dx, offset += v, with the
+// integer part carried into the cell index.  Collisions convert to SI.
+#include "pic_internal.cuh"
+
+namespace pic {
+namespace {
+
+struct P32 {
+    int nx, ny, nz, nxy;
+    int M, sp, flags;
+    float kq, kqm, invM;         // (q/m) dt^2/dx, its per-substep value, 1/M
+    float vs, inv_vs;            // dx/dt and its inverse (cells/step <-> m/s)
+    float hm, pnull, nu_max, de, n_gas, sig_n, eps_exc, eps_ion, mr2, qk;
+    int n_xs;
+    const float* xs;
+    uint2 key;
+    uint32_t step;
+    const int* gcell;
+    const float* goff;           // 3 ng: grain centre offsets in its cell
+    const float* gr2;            // ng: (radius/dx)^2
+    const float* gq;             // ng: Q (C)
+    const float* gtab;           // ng * 192: unit-charge node field (V/m per C)
+    unsigned long long* gabs;
+    const int* cell_ng;
+    const int* cell_g;
+    const float4* E;
+    unsigned long long* rq;
+    float4* pos;
+    float4* vel;
+    const unsigned long long* nslot;
+    unsigned long long* cnt;
+    int* err;
+    ChildRec* child;
+    unsigned long long child_cap;
+    unsigned long long* nch;
+};
+
+__device__ __forceinline__ void latch(int* err, int code) { atomicCAS(err, 0, code); }
+
+__device__ __forceinline__ int qa(float o)
+{
+    int a = __float2int_rn(o * (float)kWQ);
+    return min(max(a, 0), kWQ);
+}
+
+__device__ __forceinline__ void split(int cell, int nx, int ny, int& i, int& j, int& k)
+{
+    i = cell % nx;
+    const int t = cell / nx;
+    j = t % ny;
+    k = t / ny;
+}
+
+// CIC gather of the node field with the fixed-point weights a/2^14 per axis
+__device__ __forceinline__ void gather(const float4* __restrict__ E, int nx, int nxy, int i, int j, int k,
+                                       const int a[3], float out[3])
+{
+    const float s = 1.0f / (float)kWQ;
+    const float wx[2] = {(float)(kWQ - a[0]) * s, (float)a[0] * s};
+    const float wy[2] = {(float)(kWQ - a[1]) * s, (float)a[1] * s};
+    const float wz[2] = {(float)(kWQ - a[2]) * s, (float)a[2] * s};
+    const int i1 = (i + 1 == nx) ? 0 : i + 1;
+    const int ny = nxy / nx;
+    const int j1 = (j + 1 == ny) ? 0 : j + 1;
+    const size_t b0 = (size_t)k * nxy, b1 = b0 + nxy;
+    const size_t r00 = b0 + (size_t)j * nx, r01 = b0 + (size_t)j1 * nx, r10 = b1 + (size_t)j * nx,
+                 r11 = b1 + (size_t)j1 * nx;
+    const float4 e000 = __ldg(E + r00 + i), e001 = __ldg(E + r00 + i1);
+    const float4 e010 = __ldg(E + r01 + i), e011 = __ldg(E + r01 + i1);
+    const float4 e100 = __ldg(E + r10 + i), e101 = __ldg(E + r10 + i1);
+    const float4 e110 = __ldg(E + r11 + i), e111 = __ldg(E + r11 + i1);
+    const float w00 = wy[0] * wz[0], w01 = wy[1] * wz[0], w10 = wy[0] * wz[1], w11 = wy[1] * wz[1];
+    out[0] = w00 * (wx[0] * e000.x + wx[1] * e001.x) + w01 * (wx[0] * e010.x + wx[1] * e011.x) +
+             w10 * (wx[0] * e100.x + wx[1] * e101.x) + w11 * (wx[0] * e110.x + wx[1] * e111.x);
+    out[1] = w00 * (wx[0] * e000.y + wx[1] * e001.y) + w01 * (wx[0] * e010.y + wx[1] * e011.y) +
+             w10 * (wx[0] * e100.y + wx[1] * e101.y) + w11 * (wx[0] * e110.y + wx[1] * e111.y);
+    out[2] = w00 * (wx[0] * e000.z + wx[1] * e001.z) + w01 * (wx[0] * e010.z + wx[1] * e011.z) +
+             w10 * (wx[0] * e100.z + wx[1] * e101.z) + w11 * (wx[0] * e110.z + wx[1] * e111.z);
+}
+
+__device__ __forceinline__ void deposit(unsigned long long* rq, int nx, int nxy, int i, int j, int k, const int a[3],
+                                        long long charge)
+{
+    const long long wx[2] = {kWQ - a[0], a[0]}, wy[2] = {kWQ - a[1], a[1]}, wz[2] = {kWQ - a[2], a[2]};
+    const int ny = nxy / nx;
+    const int ii[2] = {i, (i + 1 == nx) ? 0 : i + 1};
+    const int jj[2] = {j, (j + 1 == ny) ? 0 : j + 1};
+#pragma unroll
+    for (int dz = 0; dz < 2; ++dz)
+#pragma unroll
+        for (int dy = 0; dy < 2; ++dy)
+#pragma unroll
+            for (int di = 0; di < 2; ++di) {
+                const long long v = charge * (wx[di] * wy[dy] * wz[dz]);
+                if (v != 0)
+                    atomicAdd(rq + (size_t)(k + dz) * nxy + (size_t)jj[dy] * nx + ii[di], (unsigned long long)v);
+            }
+}
+
+// carry whole cells out of the offsets; 0 alive, 1/2 lost at the bottom/top
+// electrode, 3 invalid (non-finite or more than one box length in a step)
+__device__ __forceinline__ int carry(const P32& p, int& i, int& j, int& k, float o[3])
+{
+    int c[3] = {i, j, k};
+    const int n[3] = {p.nx, p.ny, p.nz};
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        if (!(fabsf(o[a]) < 1e6f)) return 3;
+        const float fl = floorf(o[a]);
+        o[a] -= fl;
+        int cc = c[a] + (int)fl;
+        if (o[a] >= 1.0f) { o[a] -= 1.0f; cc += 1; }
+        if (a < 2) {
+            if (cc < -n[a] || cc >= 2 * n[a]) return 3;
+            if (cc < 0) cc += n[a];
+            else if (cc >= n[a]) cc -= n[a];
+        }
+        c[a] = cc;
+    }
+    if (c[2] < 0) return 1;
+    if (c[2] >= p.nz) return 2;
+    i = c[0]; j = c[1]; k = c[2];
+    return 0;
+}
+
+// separation from grain gi in cell units, minimum image in x and y
+__device__ __forceinline__ void grain_sep(const P32& p, int gi, int i, int j, int k, const float o[3], float d[3])
+{
+    int di = i - p.gcell[3 * gi], dj = j - p.gcell[3 * gi + 1];
+    const int dk = k - p.gcell[3 * gi + 2];
+    if (di > p.nx / 2) di -= p.nx; else if (di < -p.nx / 2) di += p.nx;
+    if (dj > p.ny / 2) dj -= p.ny; else if (dj < -p.ny / 2) dj += p.ny;
+    d[0] = (float)di + (o[0] - p.goff[3 * gi]);
+    d[1] = (float)dj + (o[1] - p.goff[3 * gi + 1]);
+    d[2] = (float)dk + (o[2] - p.goff[3 * gi + 2]);
+}
+
+// Eqs. 5-6: replace each near grain's mesh field by its Coulomb field
+__device__ void md_correct(const P32& p, int i, int j, int k, const float o[3], const int a[3], float E[3])
+{
+    const int cell = (k * p.ny + j) * p.nx + i;
+    const int n = p.cell_ng[cell];
+    const float s = 1.0f / (float)kWQ;
+    const float wx[2] = {(float)(kWQ - a[0]) * s, (float)a[0] * s};
+    const float wy[2] = {(float)(kWQ - a[1]) * s, (float)a[1] * s};
+    const float wz[2] = {(float)(kWQ - a[2]) * s, (float)a[2] * s};
+    for (int t = 0; t < n; ++t) {
+        const int gi = p.cell_g[cell * kMaxG + t];
+        const int gc0 = p.gcell[3 * gi], gc1 = p.gcell[3 * gi + 1], gc2 = p.gcell[3 * gi + 2];
+        float Ed[3] = {0.f, 0.f, 0.f};
+        for (int dz = 0; dz < 2; ++dz)
+            for (int dy = 0; dy < 2; ++dy)
+                for (int di = 0; di < 2; ++di) {
+                    const float wt = wx[di] * wy[dy] * wz[dz];
+                    const int li = ((i + di - gc0 + 1) % p.nx + p.nx) % p.nx;
+                    const int lj = ((j + dy - gc1 + 1) % p.ny + p.ny) % p.ny;
+                    const int lk = k + dz - gc2 + 1;
+                    const float* tv = p.gtab + ((size_t)gi * 64 + (lk * 4 + lj) * 4 + li) * 3;
+                    Ed[0] += wt * tv[0];
+                    Ed[1] += wt * tv[1];
+                    Ed[2] += wt * tv[2];
+                }
+        float d[3];
+        grain_sep(p, gi, i, j, k, o, d);
+        const float r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+        const float Q = p.gq[gi];
+        const float coef = r2 > 0.f ? (Q * p.qk) / (r2 * sqrtf(r2)) : 0.f;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) E[c] = (E[c] - Q * Ed[c]) + coef * d[c];
+    }
+}
+
+__device__ int absorbed_by(const P32& p, int i, int j, int k, const float o[3])
+{
+    const int cell = (k * p.ny + j) * p.nx + i;
+    const int n = p.cell_ng[cell];
+    for (int t = 0; t < n; ++t) {
+        const int gi = p.cell_g[cell * kMaxG + t];
+        float d[3];
+        grain_sep(p, gi, i, j, k, o, d);
+        if (d[0] * d[0] + d[1] * d[1] + d[2] * d[2] <= p.gr2[gi]) return gi;
+    }
+    return -1;
+}
+
+__device__ __forceinline__ float xs_at(const float* tab, int n, float de, float eps)
+{
+    const float t = eps / de;
+    if (t >= (float)(n - 1)) return tab[n - 1];
+    const int i = (int)t;
+    const float fr = t - (float)i;
+    return tab[i] + fr * (tab[i + 1] - tab[i]);
+}
+
+__device__ __forceinline__ void pairf(RStream& r, float& a, float& b)
+{
+    a = 2.0f * u01f(r.next()) - 1.0f;
+    b = 2.0f * u01f(r.next()) - 1.0f;
+}
+
+__device__ void isof(RStream& r, float o[3])
+{
+    for (int t = 0; t < 128; ++t) {
+        float a, b;
+        pairf(r, a, b);
+        const float s = a * a + b * b;
+        if (s < 1.0f) {
+            const float q = 2.0f * sqrtf(1.0f - s);
+            o[0] = a * q; o[1] = b * q; o[2] = 1.0f - 2.0f * s;
+            return;
+        }
+    }
+    o[0] = 0.f; o[1] = 0.f; o[2] = 1.f;
+}
+
+__device__ void gauss3f(RStream& r, float o[3])
+{
+    int got = 0;
+    for (int t = 0; t < 256 && got < 3; ++t) {
+        float a, b;
+        pairf(r, a, b);
+        const float s = a * a + b * b;
+        if (s < 1.0f && s > 0.0f) {
+            const float f = sqrtf(-2.0f * logf(s) / s);
+            o[got++] = a * f;
+            if (got < 3) o[got++] = b * f;
+        }
+    }
+    while (got < 3) o[got++] = 0.f;
+}
+
+// null-collision MCC in SI single precision (Table I)
+__device__ void mcc(const P32& p, int cell, const float o[3], float vc[3], uint32_t id)
+{
+    const uint4 u = philox4x32_10(make_uint4(id, p.step, kPurMCC, 0u), p.key);
+    if (u01f(u.x) >= p.pnull) return;
+    float v[3] = {vc[0] * p.vs, vc[1] * p.vs, vc[2] * p.vs};
+    const int nx = p.n_xs;
+    if (p.sp == 0) {
+        const float v2 = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
+        const float eps = v2 * p.hm;
+        const float vm = sqrtf(v2);
+        const float nu_el = p.n_gas * xs_at(p.xs, nx, p.de, eps) * vm;
+        const float nu_ex = p.n_gas * xs_at(p.xs + nx, nx, p.de, eps) * vm;
+        const float nu_io = p.n_gas * xs_at(p.xs + 2 * nx, nx, p.de, eps) * vm;
+        const float R = u01f(u.y) * p.nu_max;
+        RStream rd(id, p.step, kPurDir, p.key);
+        float dir[3];
+        if (R < nu_el) {
+            isof(rd, dir);
+            const float cosx = (dir[0] * v[0] + dir[1] * v[1] + dir[2] * v[2]) / vm;
+            const float vn = vm * sqrtf(1.0f - p.mr2 * (1.0f - cosx));
+            for (int a = 0; a < 3; ++a) vc[a] = vn * dir[a] * p.inv_vs;
+            atomicAdd(p.cnt + PIC_C_E_EL, 1ull);
+            return;
+        }
+        if (R < nu_el + nu_ex) {
+            const float e2 = fmaxf(eps - p.eps_exc, 0.f);
+            isof(rd, dir);
+            const float vn = sqrtf(e2 / p.hm);
+            for (int a = 0; a < 3; ++a) vc[a] = vn * dir[a] * p.inv_vs;
+            atomicAdd(p.cnt + PIC_C_E_EXC, 1ull);
+            return;
+        }
+        if (R < nu_el + nu_ex + nu_io) {
+            const float e2 = fmaxf(eps - p.eps_ion, 0.f);
+            const float vn = sqrtf(0.5f * e2 / p.hm);
+            isof(rd, dir);
+            float d2[3], gn[3];
+            RStream rc(id, p.step, kPurChildDir, p.key);
+            isof(rc, d2);
+            RStream rn(id, p.step, kPurChildNeutral, p.key);
+            gauss3f(rn, gn);
+            ChildRec cr;
+            cr.parent = id;
+            cr.cell = cell;
+            for (int a = 0; a < 3; ++a) {
+                vc[a] = vn * dir[a] * p.inv_vs;
+                cr.x[a] = o[a];
+                cr.ve[a] = vn * d2[a] * p.inv_vs;
+                cr.vi[a] = p.sig_n * gn[a] * p.inv_vs;
+            }
+            const unsigned long long slot = atomicAdd(p.nch, 1ull);
+            if (slot < p.child_cap) p.child[slot] = cr;
+            else latch(p.err, kErrCapacity);
+            atomicAdd(p.cnt + PIC_C_E_ION, 1ull);
+        }
+        return;
+    }
+    float gn[3];
+    RStream rn(id, p.step, kPurNeutral, p.key);
+    gauss3f(rn, gn);
+    const float vn[3] = {p.sig_n * gn[0], p.sig_n * gn[1], p.sig_n * gn[2]};
+    const float gv[3] = {v[0] - vn[0], v[1] - vn[1], v[2] - vn[2]};
+    const float g2 = gv[0] * gv[0] + gv[1] * gv[1] + gv[2] * gv[2];
+    const float eps = g2 * p.hm;
+    const float gm = sqrtf(g2);
+    const float nu_el = p.n_gas * xs_at(p.xs + 3 * nx, nx, p.de, eps) * gm;
+    const float nu_cx = p.n_gas * xs_at(p.xs + 4 * nx, nx, p.de, eps) * gm;
+    const float R = u01f(u.y) * p.nu_max;
+    if (R < nu_el) {
+        float dir[3];
+        RStream rd(id, p.step, kPurDir, p.key);
+        isof(rd, dir);
+        for (int a = 0; a < 3; ++a) vc[a] = ((v[a] + vn[a]) * 0.5f + 0.5f * gm * dir[a]) * p.inv_vs;
+        atomicAdd(p.cnt + PIC_C_I_EL, 1ull);
+        return;
+    }
+    if (R < nu_el + nu_cx) {
+        for (int a = 0; a < 3; ++a) vc[a] = vn[a] * p.inv_vs;
+        atomicAdd(p.cnt + PIC_C_I_CX, 1ull);
+    }
+}
+
+__global__ void __launch_bounds__(256) k_push32(const P32 p)
+{
+    const unsigned long long n = p.nslot[p.sp];
+    const bool frozen = (p.sp == 1) && (p.flags & PIC_F_IONS_FROZEN);
+    const long long charge = p.sp == 0 ? -1 : 1;
+    unsigned int live = 0;
+    for (unsigned long long q = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; q < n;
+         q += (unsigned long long)gridDim.x * blockDim.x) {
+        const float4 P = p.pos[q];
+        int cell = __float_as_int(P.w);
+        if (cell < 0) continue;
+        ++live;
+        int i, j, k;
+        split(cell, p.nx, p.ny, i, j, k);
+        float o[3] = {P.x, P.y, P.z};
+        int a[3];
+        if (frozen) {
+            a[0] = qa(o[0]); a[1] = qa(o[1]); a[2] = qa(o[2]);
+            deposit(p.rq, p.nx, p.nxy, i, j, k, a, charge);
+            continue;
+        }
+        const float4 V = p.vel[q];
+        float v[3] = {V.x, V.y, V.z};
+        int fate = 0, grain = -1;
+        if (p.cell_ng[cell] == 0) {
+            a[0] = qa(o[0]); a[1] = qa(o[1]); a[2] = qa(o[2]);
+            float E[3];
+            gather(p.E, p.nx, p.nxy, i, j, k, a, E);
+            v[0] += E[0] * p.kq; v[1] += E[1] * p.kq; v[2] += E[2] * p.kq;
+            o[0] += v[0]; o[1] += v[1]; o[2] += v[2];
+            fate = carry(p, i, j, k, o);
+        } else {
+            for (int m = 0; m < p.M; ++m) {
+                a[0] = qa(o[0]); a[1] = qa(o[1]); a[2] = qa(o[2]);
+                float E[3];
+                gather(p.E, p.nx, p.nxy, i, j, k, a, E);
+                md_correct(p, i, j, k, o, a, E);
+                v[0] += E[0] * p.kqm; v[1] += E[1] * p.kqm; v[2] += E[2] * p.kqm;
+                o[0] += v[0] * p.invM; o[1] += v[1] * p.invM; o[2] += v[2] * p.invM;
+                fate = carry(p, i, j, k, o);
+                if (fate) break;
+                grain = absorbed_by(p, i, j, k, o);
+                if (grain >= 0) break;
+            }
+        }
+        if (fate != 0 || grain >= 0) {
+            p.pos[q].w = __int_as_float(-1);
+            if (fate == 1) atomicAdd(p.cnt + (p.sp == 0 ? PIC_C_LOST_BOT_E : PIC_C_LOST_BOT_I), 1ull);
+            else if (fate == 2) atomicAdd(p.cnt + (p.sp == 0 ? PIC_C_LOST_TOP_E : PIC_C_LOST_TOP_I), 1ull);
+            else if (fate == 3) {
+                atomicAdd(p.cnt + PIC_C_ERR, 1ull);
+                latch(p.err, kErrNonFinite);
+            } else {
+                atomicAdd(p.gabs + 2 * grain + p.sp, 1ull);
+                atomicAdd(p.cnt + (p.sp == 0 ? PIC_C_ABS_E : PIC_C_ABS_I), 1ull);
+            }
+            continue;
+        }
+        cell = (k * p.ny + j) * p.nx + i;
+        const uint32_t id = __float_as_uint(V.w);
+        if (!(p.flags & PIC_F_NO_MCC)) mcc(p, cell, o, v, id);
+        p.pos[q] = make_float4(o[0], o[1], o[2], __int_as_float(cell));
+        p.vel[q] = make_float4(v[0], v[1], v[2], V.w);
+        a[0] = qa(o[0]); a[1] = qa(o[1]); a[2] = qa(o[2]);
+        deposit(p.rq, p.nx, p.nxy, i, j, k, a, charge);
+    }
+    live = __reduce_add_sync(0xffffffffu, live);
+    if ((threadIdx.x & 31) == 0 && live) atomicAdd(p.cnt + PIC_C_PUSHED, (unsigned long long)live);
+}
+
+__global__ void k_deposit32(int nx, int ny, const float4* pos, const unsigned long long* nslot, int sp,
+                            unsigned long long* rq)
+{
+    const unsigned long long n = nslot[sp];
+    const long long charge = sp == 0 ? -1 : 1;
+    for (unsigned long long q = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; q < n;
+         q += (unsigned long long)gridDim.x * blockDim.x) {
+        const float4 P = pos[q];
+        const int cell = __float_as_int(P.w);
+        if (cell < 0) continue;
+        int i, j, k;
+        split(cell, nx, ny, i, j, k);
+        const int a[3] = {qa(P.x), qa(P.y), qa(P.z)};
+        deposit(rq, nx, nx * ny, i, j, k, a, charge);
+    }
+}
+
+__global__ void k_efield32(int nx, int ny, int nz, double dx, const double* __restrict__ phi, float4* __restrict__ E)
+{
+    const size_t P = (size_t)nx * ny;
+    const size_t N = P * (nz + 1);
+    const double h2 = 2.0 * dx;
+    for (size_t n = blockIdx.x * (size_t)blockDim.x + threadIdx.x; n < N; n += (size_t)gridDim.x * blockDim.x) {
+        const int i = (int)(n % nx);
+        const int j = (int)((n / nx) % ny);
+        const int k = (int)(n / P);
+        const size_t row = ((size_t)k * ny + j) * nx;
+        const double ex = (phi[row + (i + nx - 1) % nx] - phi[row + (i + 1) % nx]) / h2;
+        const double ey = (phi[((size_t)k * ny + (j + ny - 1) % ny) * nx + i] -
+                           phi[((size_t)k * ny + (j + 1) % ny) * nx + i]) / h2;
+        double ez;
+        if (k == 0) ez = ((3.0 * phi[n] - 4.0 * phi[n + P]) + phi[n + 2 * P]) / h2;
+        else if (k == nz) ez = ((4.0 * phi[n - P] - 3.0 * phi[n]) - phi[n - 2 * P]) / h2;
+        else ez = (phi[n - P] - phi[n + P]) / h2;
+        E[n] = make_float4((float)ex, (float)ey, (float)ez, 0.f);
+    }
+}
+
+__global__ void k_children32(int nx, int ny, ChildRec* rec, const unsigned long long* nch,
+                             unsigned long long child_cap, const unsigned long long* nslot,
+                             const unsigned int* next_id, float4* pos_e, float4* vel_e, float4* pos_i,
+                             float4* vel_i, long long cap_e, long long cap_i, unsigned long long* rq, int* err)
+{
+    __shared__ uint32_t tile[256];
+    const unsigned long long n = min(*nch, child_cap);   // records past the buffer were never written
+    const unsigned long long base_e = nslot[0], base_i = nslot[1];
+    const unsigned int nid = *next_id;
+    for (unsigned long long r0 = blockIdx.x * (unsigned long long)blockDim.x; r0 < n;
+         r0 += (unsigned long long)gridDim.x * blockDim.x) {
+        const unsigned long long r = r0 + threadIdx.x;
+        const uint32_t mine = r < n ? rec[r].parent : 0xFFFFFFFFu;
+        unsigned long long rank = 0;
+        for (unsigned long long t0 = 0; t0 < n; t0 += blockDim.x) {
+            __syncthreads();
+            tile[threadIdx.x] = (t0 + threadIdx.x < n) ? rec[t0 + threadIdx.x].parent : 0xFFFFFFFFu;
+            __syncthreads();
+            const int lim = (int)min((unsigned long long)blockDim.x, n - t0);
+            for (int t = 0; t < lim; ++t) rank += tile[t] < mine;
+        }
+        if (r >= n) continue;
+        const ChildRec cr = rec[r];
+        const unsigned long long se = base_e + rank, si = base_i + rank;
+        if (se >= (unsigned long long)cap_e || si >= (unsigned long long)cap_i) {
+            atomicCAS(err, 0, (int)kErrCapacity);
+            continue;
+        }
+        const float o[3] = {(float)cr.x[0], (float)cr.x[1], (float)cr.x[2]};
+        const float cb = __int_as_float(cr.cell);
+        pos_e[se] = make_float4(o[0], o[1], o[2], cb);
+        vel_e[se] = make_float4((float)cr.ve[0], (float)cr.ve[1], (float)cr.ve[2],
+                                __uint_as_float(nid + (unsigned)(2 * rank)));
+        pos_i[si] = make_float4(o[0], o[1], o[2], cb);
+        vel_i[si] = make_float4((float)cr.vi[0], (float)cr.vi[1], (float)cr.vi[2],
+                                __uint_as_float(nid + (unsigned)(2 * rank + 1)));
+        int i, j, k;
+        split(cr.cell, nx, ny, i, j, k);
+        const int a[3] = {qa(o[0]), qa(o[1]), qa(o[2])};
+        deposit(rq, nx, nx * ny, i, j, k, a, -1);
+        deposit(rq, nx, nx * ny, i, j, k, a, 1);
+    }
+}
+
+__global__ void k_children_finish32(unsigned long long* nch, unsigned long long child_cap,
+                                    unsigned long long* nslot, unsigned int* next_id, long long cap_e, long long cap_i)
+{
+    const unsigned long long n = min(*nch, child_cap);
+    nslot[0] = min(nslot[0] + n, (unsigned long long)cap_e);
+    nslot[1] = min(nslot[1] + n, (unsigned long long)cap_i);
+    *next_id += (unsigned int)(2 * n);
+    *nch = 0;
+}
+
+__global__ void k_moments32(int nx, int ny, float vs, const float4* pos, const float4* vel,
+                            const unsigned long long* nslot, int sp, double* mom)
+{
+    const unsigned long long n = nslot[sp];
+    const int nxy = nx * ny;
+    for (unsigned long long q = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; q < n;
+         q += (unsigned long long)gridDim.x * blockDim.x) {
+        const float4 P = pos[q];
+        const int cell = __float_as_int(P.w);
+        if (cell < 0) continue;
+        const float4 V = vel[q];
+        int i, j, k;
+        split(cell, nx, ny, i, j, k);
+        const int a[3] = {qa(P.x), qa(P.y), qa(P.z)};
+        const long long wx[2] = {kWQ - a[0], a[0]}, wy[2] = {kWQ - a[1], a[1]}, wz[2] = {kWQ - a[2], a[2]};
+        const int ii[2] = {i, (i + 1 == nx) ? 0 : i + 1};
+        const int jj[2] = {j, (j + 1 == ny) ? 0 : j + 1};
+        const double vx = (double)V.x * vs, vy = (double)V.y * vs, vz = (double)V.z * vs;
+        for (int dz = 0; dz < 2; ++dz)
+            for (int dy = 0; dy < 2; ++dy)
+                for (int di = 0; di < 2; ++di) {
+                    const double wt = (double)(wx[di] * wy[dy] * wz[dz]) * 0x1p-42;
+                    if (wt == 0.0) continue;
+                    double* m = mom + 4 * ((size_t)(k + dz) * nxy + (size_t)jj[dy] * nx + ii[di]);
+                    atomicAdd(m, wt);
+                    atomicAdd(m + 1, wt * vx);
+                    atomicAdd(m + 2, wt * vy);
+                    atomicAdd(m + 3, wt * vz);
+                }
+    }
+}
+
+__global__ void k_moments_phi(const double* phi, double* mphi, size_t n)
+{
+    for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < n; q += (size_t)gridDim.x * blockDim.x)
+        mphi[q] += phi[q];
+}
+
+}  // namespace
+
+void launch_push32(pic_ctx* c)
+{
+    for (int sp = 0; sp < 2; ++sp) {
+        P32 p;
+        p.nx = c->nx; p.ny = c->ny; p.nz = c->nz; p.nxy = c->nx * c->ny;
+        p.M = c->md_sub > 0 ? c->md_sub : 1;
+        p.sp = sp;
+        p.flags = c->flags;
+        const double kq = c->qm[sp] * c->dt * c->dt / c->dx;
+        p.kq = (float)kq;
+        p.kqm = (float)(kq / (double)p.M);
+        p.invM = (float)(1.0 / p.M);
+        p.vs = (float)(c->dx / c->dt);
+        p.inv_vs = (float)(c->dt / c->dx);
+        p.hm = (float)c->hm[sp];
+        p.pnull = (float)c->pnull[sp];
+        p.nu_max = (float)c->nu_max[sp];
+        p.de = (float)c->de[sp];
+        p.n_gas = (float)c->n_gas;
+        p.sig_n = (float)c->sig_n;
+        p.eps_exc = (float)c->eps_exc;
+        p.eps_ion = (float)c->eps_ion;
+        p.mr2 = (float)((2.0 * kME) / kMAR);
+        p.qk = (float)(1.0 / (4.0 * kPI * kEPS0) / (c->dx * c->dx));
+        p.n_xs = c->n_xs;
+        p.xs = c->xs32;
+        p.key = c->key;
+        p.step = (uint32_t)c->step;
+        p.gcell = c->gcell;
+        p.goff = c->goff32;
+        p.gr2 = c->gr2_32;
+        p.gq = c->gq32;
+        p.gtab = c->gtab32;
+        p.gabs = c->gabs;
+        p.cell_ng = c->cell_ng;
+        p.cell_g = c->cell_g;
+        p.E = c->e32;
+        p.rq = c->rq;
+        p.pos = (float4*)c->pos[sp];
+        p.vel = (float4*)c->vel[sp];
+        p.nslot = c->d_nslot;
+        p.cnt = c->d_cnt;
+        p.err = c->d_err;
+        p.child = c->d_child;
+        p.child_cap = (unsigned long long)c->child_cap;
+        p.nch = c->d_nch;
+        cudaEvent_t ev = prof_begin(c);
+        k_push32<<<grid_for(c->cap[sp], 256, 152 * 8), 256, 0, c->stream>>>(p);
+        prof_end(c, ev, true);
+        c->launches += 1;
+    }
+}
+
+void launch_deposit32(pic_ctx* c)
+{
+    for (int sp = 0; sp < 2; ++sp)
+        k_deposit32<<<grid_for(c->cap[sp], 256, 152 * 8), 256, 0, c->stream>>>(c->nx, c->ny, (const float4*)c->pos[sp],
+                                                                               c->d_nslot, sp, c->rq);
+    c->launches += 2;
+}
+
+void launch_efield32(pic_ctx* c)
+{
+    k_efield32<<<grid_for((int64_t)c->nodes, 256, 152 * 8), 256, 0, c->stream>>>(c->nx, c->ny, c->nz, c->dx, c->phi,
+                                                                                c->e32);
+    c->launches += 1;
+}
+
+void launch_children32(pic_ctx* c)
+{
+    k_children32<<<64, 256, 0, c->stream>>>(c->nx, c->ny, c->d_child, c->d_nch, (unsigned long long)c->child_cap,
+                                              c->d_nslot, c->d_next_id,
+                                              (float4*)c->pos[0], (float4*)c->vel[0], (float4*)c->pos[1],
+                                              (float4*)c->vel[1], c->cap[0], c->cap[1], c->rq, c->d_err);
+    k_children_finish32<<<1, 1, 0, c->stream>>>(c->d_nch, (unsigned long long)c->child_cap, c->d_nslot,
+                                                c->d_next_id, c->cap[0], c->cap[1]);
+    c->launches += 2;
+}
+
+void launch_moments32(pic_ctx* c)
+{
+    for (int sp = 0; sp < 2; ++sp)
+        k_moments32<<<grid_for(c->cap[sp], 256, 152 * 8), 256, 0, c->stream>>>(
+            c->nx, c->ny, (float)(c->dx / c->dt), (const float4*)c->pos[sp], (const float4*)c->vel[sp], c->d_nslot,
+            sp, c->mom[sp]);
+    c->launches += 2;
+}
+
+void launch_moments_phi(pic_ctx* c)
+{
+    k_moments_phi<<<grid_for((int64_t)c->nodes, 256, 152 * 4), 256, 0, c->stream>>>(c->phi, c->mphi, c->nodes);
+    c->launches += 1;
+}
+
+}  // namespace pic

@@ -1,0 +1,243 @@
+// Internal declarations of libpic: run context, device helpers and the kernel
+// entry points shared between translation units.  Not part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "../../include/pic.h"
+
+namespace pic {
+
+// physical constants (CODATA 2018)
+constexpr double kQE = 1.602176634e-19;
+constexpr double kEPS0 = 8.8541878128e-12;
+constexpr double kME = 9.1093837015e-31;
+constexpr double kAMU = 1.66053906660e-27;
+constexpr double kKB = 1.380649e-23;
+constexpr double kMAR = 39.948 * kAMU;
+constexpr double kPI = 3.14159265358979323846;
+
+constexpr int kWQ = 16384;      // fixed-point CIC weight units per axis
+constexpr int kMaxG = 8;        // grains per MD cell
+constexpr int kTab = 64 * 3;    // doubles per grain field table (4x4x4 nodes x 3)
+
+// Philox counter third word: what the draws are for
+enum Purpose : uint32_t { kPurMCC = 1, kPurDir = 2, kPurNeutral = 3, kPurChildDir = 4, kPurChildNeutral = 5 };
+
+// error codes latched in ctx->d_err (first one wins)
+enum DevErr : int { kErrNone = 0, kErrCapacity = PIC_ECAPACITY, kErrNonFinite = PIC_ENONFINITE };
+
+// ionization product record: written by the push, numbered and appended later
+struct ChildRec {
+    uint32_t parent;
+    int32_t cell;       // mixed: cell of the parent; fp64: unused
+    double x[3];        // fp64: position (m); mixed: in-cell offsets
+    double ve[3];       // new electron velocity (fp64: m/s; mixed: cells/step)
+    double vi[3];       // new ion velocity
+};
+
+// ---------------------------------------------------------------- Philox4x32-10
+// Salmon et al., SC'11: ten rounds of two 32x32->64 multiplies with a Weyl key schedule.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r > 0) { k.x += 0x9E3779B9u; k.y += 0xBB67AE85u; }
+        const uint32_t a0 = 0xD2511F53u * c.x, b0 = __umulhi(0xD2511F53u, c.x);
+        const uint32_t a1 = 0xCD9E8D57u * c.z, b1 = __umulhi(0xCD9E8D57u, c.z);
+        c = make_uint4(b1 ^ c.y ^ k.x, a1, b0 ^ c.w ^ k.y, a0);
+    }
+    return c;
+}
+
+// uniform on (0,1), exact in double
+__device__ __forceinline__ double u01d(uint32_t u) { return ((double)u + 0.5) * 0x1p-32; }
+__device__ __forceinline__ float u01f(uint32_t u) { return ((float)(u >> 8) + 0.5f) * 0x1p-24f; }
+
+// ln x from +,-,*,/: x = m 2^e, m in [sqrt(1/2), sqrt(2)), ln m = 2 atanh((m-1)/(m+1))
+// summed as an odd series to s^23 (Horner, no fused multiply-add in the fp64 unit)
+__device__ __forceinline__ double ln_series(double x)
+{
+    int e;
+    double m = frexp(x, &e);
+    if (m < 0.70710678118654752440) { m = m * 2.0; e = e - 1; }
+    const double s = (m - 1.0) / (m + 1.0);
+    const double s2 = s * s;
+    double p = 1.0 / 23.0;
+    p = p * s2 + 1.0 / 21.0;
+    p = p * s2 + 1.0 / 19.0;
+    p = p * s2 + 1.0 / 17.0;
+    p = p * s2 + 1.0 / 15.0;
+    p = p * s2 + 1.0 / 13.0;
+    p = p * s2 + 1.0 / 11.0;
+    p = p * s2 + 1.0 / 9.0;
+    p = p * s2 + 1.0 / 7.0;
+    p = p * s2 + 1.0 / 5.0;
+    p = p * s2 + 1.0 / 3.0;
+    p = p * s2 + 1.0;
+    const double t1 = (double)e * 0.69314718055994530942;
+    const double t2 = (2.0 * s) * p;
+    return t1 + t2;
+}
+
+// Uniforms for one (particle id, step, purpose): successive Philox calls count
+// in the fourth counter word; each call yields four 32-bit draws.
+struct RStream {
+    uint4 ctr;
+    uint2 key;
+    uint4 buf;
+    int pos;
+    __device__ RStream(uint32_t id, uint32_t step, uint32_t purpose, uint2 k)
+        : ctr(make_uint4(id, step, purpose, 0u)), key(k), buf(make_uint4(0, 0, 0, 0)), pos(4) {}
+    __device__ __forceinline__ uint32_t next()
+    {
+        if (pos == 4) { buf = philox4x32_10(ctr, key); ctr.w += 1u; pos = 0; }
+        const uint32_t v = pos == 0 ? buf.x : pos == 1 ? buf.y : pos == 2 ? buf.z : buf.w;
+        ++pos;
+        return v;
+    }
+};
+
+// ---------------------------------------------------------------- context
+struct MGLevel {
+    int nx, ny, nz;
+    double h;
+    size_t nodes;
+    void* u = nullptr;   // T[nodes]
+    void* f = nullptr;
+    void* r = nullptr;
+};
+
+}  // namespace pic
+
+struct pic_ctx {
+    // mesh and physics
+    int nx, ny, nz;
+    double dx, Lx, Ly, Lz;
+    size_t nodes, cells;
+    pic_electrodes el;
+    double n_gas, t_gas, eps_exc, eps_ion, nu_max[2], de[2];
+    int n_xs;
+    int ng;
+    int prec, flags, md_sub, sort_every, max_cycles;
+    double W, dt, tol;
+    uint64_t seed;
+    uint32_t run_id;
+    uint2 key;
+    double qm[2], hm[2], pnull[2], sig_n;
+    cudaStream_t stream;
+    int64_t step;
+    int64_t cap[2];
+    int64_t child_cap;
+
+    // particles: fp64 double4 {x,y,z,cell} / {vx,vy,vz,id}; mixed float4 {ox,oy,oz,cell bits} / {v (cells/step), id bits}
+    void* pos[2] = {nullptr, nullptr};
+    void* vel[2] = {nullptr, nullptr};
+    void* pos_alt[2] = {nullptr, nullptr};
+    void* vel_alt[2] = {nullptr, nullptr};
+    unsigned long long* d_nslot = nullptr;   // [2] slots in use (live + holes since the last sort)
+    unsigned long long* d_cnt = nullptr;     // [PIC_C_N]
+    int* d_err = nullptr;
+    unsigned long long* d_nch = nullptr;     // children this step
+    unsigned int* d_next_id = nullptr;
+    pic::ChildRec* d_child = nullptr;
+
+    // mesh arrays
+    unsigned long long* rq = nullptr;        // int64 fixed-point charge per node
+    double* phi = nullptr;                   // fp64 master potential
+    double* phi_alt = nullptr;
+    double* f64 = nullptr;                   // rho / eps0
+    double* e64 = nullptr;                   // fp64: ex, ey, ez node arrays (3 * nodes)
+    float4* e32 = nullptr;                   // mixed: {ex, ey, ez, 0} per node (V/m)
+    double* d_norm = nullptr;                // [4] scratch norms
+
+    // gas
+    double* xs64 = nullptr;                  // 5 * n_xs
+    float* xs32 = nullptr;
+
+    // grains
+    double* gpos = nullptr;                  // 3 ng (m)
+    double* grad = nullptr;                  // ng
+    int* gcell = nullptr;                    // 3 ng
+    double* gq = nullptr;                    // ng (C)
+    unsigned long long* gabs = nullptr;      // 2 ng
+    double* gtab = nullptr;                  // ng * 192 (V/m per C)
+    float* gtab32 = nullptr;
+    float* gq32 = nullptr;                   // ng: Q (C)
+    float* goff32 = nullptr;                 // 3 ng: centre offsets inside the grain's cell
+    float* gr2_32 = nullptr;                 // ng: (radius / dx)^2
+    int* cell_ng = nullptr;                  // cells
+    int* cell_g = nullptr;                   // cells * 8
+
+    // sort scratch
+    unsigned int* hist = nullptr;            // cells + 1
+    unsigned int* cursor = nullptr;          // cells
+    std::vector<unsigned int*> scan_tmp;
+    std::vector<size_t> scan_len;
+
+    // multigrid
+    std::vector<pic::MGLevel> mg;
+
+    // moments
+    double* mom[2] = {nullptr, nullptr};     // 4 * nodes each
+    double* mphi = nullptr;
+    int64_t msteps = 0;
+
+    // measurement: events around push launches and solves while prof != 0
+    int prof = 0;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_push, ev_solve;
+    int64_t prof_iters = 0;
+    int64_t launches = 0;                    // kernels launched since pic_init
+
+    // host-side status
+    int64_t last_iters = 0;
+    double last_res = 0.0;
+    pic_status pending = PIC_OK;
+    std::string err;
+    std::vector<void*> allocs;
+};
+
+namespace pic {
+
+// ---------------------------------------------------------------- kernel entry points
+// particles_fp64.cu (built without fused multiply-add)
+void launch_efield64(pic_ctx* c);
+void launch_push64(pic_ctx* c);
+void launch_children64(pic_ctx* c);
+void launch_deposit64(pic_ctx* c);
+void launch_moments64(pic_ctx* c);
+void launch_grains(pic_ctx* c);                  // Q from counts, grain CIC into rq
+void launch_grain_table(pic_ctx* c, int g);      // E of phi on grain g's 4x4x4 region nodes
+
+// particles_mixed.cu
+void launch_efield32(pic_ctx* c);
+void launch_push32(pic_ctx* c);
+void launch_children32(pic_ctx* c);
+void launch_deposit32(pic_ctx* c);
+void launch_moments32(pic_ctx* c);
+void launch_moments_phi(pic_ctx* c);
+
+// sort.cu
+void sort_particles(pic_ctx* c, int sp);
+size_t sort_scratch_setup(pic_ctx* c);
+
+// poisson.cu
+pic_status mg_setup(pic_ctx* c);
+void launch_rhs(pic_ctx* c, double scale, double v_bot, double v_top, bool from_rq);
+pic_status mg_solve(pic_ctx* c, double v_bot, double v_top, double tol, int max_iters, int* iters, double* res);
+
+// api.cu
+void* dev_alloc(pic_ctx* c, size_t bytes);
+int grid_for(int64_t n, int threads, int max_blocks);
+// bracket one launch with events when measuring (begin returns the start event)
+cudaEvent_t prof_begin(pic_ctx* c);
+void prof_end(pic_ctx* c, cudaEvent_t start, bool push);
+
+}  // namespace pic
+
+#define PIC_CUDA_OK(expr) (cudaSuccess == (expr))

@@ -1,0 +1,346 @@
+// Geometric multigrid solve of the discrete Poisson equation (Eq. 3)
+//     (sum of the 6 neighbours - 6 phi) / dx^2 = -rho / eps0
+// on the cell-corner nodes, periodic in x and y, Dirichlet electrode planes
+// k = 0 and k = nz.  The paper factorises the same matrix once with SuperLU
+// and back-solves each step; here the solution comes from iterative
+// refinement in FP64:
+//     r = f - A phi            (FP64, fused with the previous correction)
+//     A e = r                  (one V(2,2) cycle in T = float or double)
+//     phi += e
+// until ||r|| <= tol ||b||, b = f plus the electrode terms.  A V-cycle uses
+// red-black Gauss-Seidel smoothing, full-weighting restriction, trilinear
+// prolongation, the 7-point operator rediscretised on each level (spacing
+// doubling), and many smoothing sweeps on the coarsest level in one block.
+#include <cmath>
+
+#include "pic_internal.cuh"
+
+namespace pic {
+namespace {
+
+struct Dims {
+    int nx, ny, nz;
+};
+
+__device__ __forceinline__ size_t nid(const Dims& d, int i, int j, int k)
+{
+    return ((size_t)k * d.ny + j) * d.nx + i;
+}
+
+template <typename T>
+__global__ void k_rbgs(T* __restrict__ u, const T* __restrict__ f, Dims d, T h2, int color)
+{
+    const int half = d.nx / 2;
+    const size_t total = (size_t)half * d.ny * (d.nz - 1);
+    const size_t P = (size_t)d.nx * d.ny;
+    for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
+        const int i2 = (int)(t % half);
+        const int j = (int)((t / half) % d.ny);
+        const int k = 1 + (int)(t / ((size_t)half * d.ny));
+        const int i = 2 * i2 + ((j + k + color) & 1);
+        const size_t n = nid(d, i, j, k);
+        const int ip = (i + 1 == d.nx) ? 0 : i + 1, im = (i == 0) ? d.nx - 1 : i - 1;
+        const int jp = (j + 1 == d.ny) ? 0 : j + 1, jm = (j == 0) ? d.ny - 1 : j - 1;
+        const size_t row = n - i;
+        const T s = u[row + ip] + u[row + im] + u[nid(d, i, jp, k)] + u[nid(d, i, jm, k)] + u[n + P] + u[n - P];
+        u[n] = (s + h2 * f[n]) * (T)(1.0 / 6.0);
+    }
+}
+
+template <typename T>
+__global__ void k_resid(const T* __restrict__ u, const T* __restrict__ f, T* __restrict__ r, Dims d, T inv_h2)
+{
+    const size_t P = (size_t)d.nx * d.ny;
+    const size_t N = P * (d.nz + 1);
+    for (size_t n = blockIdx.x * (size_t)blockDim.x + threadIdx.x; n < N; n += (size_t)gridDim.x * blockDim.x) {
+        const int k = (int)(n / P);
+        if (k == 0 || k == d.nz) { r[n] = (T)0; continue; }
+        const int i = (int)(n % d.nx), j = (int)((n / d.nx) % d.ny);
+        const int ip = (i + 1 == d.nx) ? 0 : i + 1, im = (i == 0) ? d.nx - 1 : i - 1;
+        const int jp = (j + 1 == d.ny) ? 0 : j + 1, jm = (j == 0) ? d.ny - 1 : j - 1;
+        const size_t row = n - i;
+        const T s = u[row + ip] + u[row + im] + u[nid(d, i, jp, k)] + u[nid(d, i, jm, k)] + u[n + P] + u[n - P];
+        r[n] = f[n] - ((T)6 * u[n] - s) * inv_h2;
+    }
+}
+
+// full weighting: weights (1/4, 1/2, 1/4) per axis around the coincident fine node
+template <typename T>
+__global__ void k_restrict(const T* __restrict__ rf, T* __restrict__ fc, Dims df, Dims dc)
+{
+    const size_t P = (size_t)dc.nx * dc.ny;
+    const size_t N = P * (dc.nz + 1);
+    for (size_t n = blockIdx.x * (size_t)blockDim.x + threadIdx.x; n < N; n += (size_t)gridDim.x * blockDim.x) {
+        const int K = (int)(n / P);
+        if (K == 0 || K == dc.nz) { fc[n] = (T)0; continue; }
+        const int I = (int)(n % dc.nx), J = (int)((n / dc.nx) % dc.ny);
+        T acc = (T)0;
+#pragma unroll
+        for (int dk = -1; dk <= 1; ++dk) {
+            const T wk = dk == 0 ? (T)0.5 : (T)0.25;
+#pragma unroll
+            for (int dj = -1; dj <= 1; ++dj) {
+                const T wj = dj == 0 ? (T)0.5 : (T)0.25;
+                const int j = (2 * J + dj + df.ny) % df.ny;
+#pragma unroll
+                for (int di = -1; di <= 1; ++di) {
+                    const T wi = di == 0 ? (T)0.5 : (T)0.25;
+                    const int i = (2 * I + di + df.nx) % df.nx;
+                    acc += (wk * wj * wi) * rf[nid(df, i, j, 2 * K + dk)];
+                }
+            }
+        }
+        fc[n] = acc;
+    }
+}
+
+// trilinear interpolation of the coarse correction, added on the fine interior
+template <typename T>
+__global__ void k_prolong(T* __restrict__ uf, const T* __restrict__ uc, Dims df, Dims dc)
+{
+    const size_t P = (size_t)df.nx * df.ny;
+    const size_t N = P * (df.nz + 1);
+    for (size_t n = blockIdx.x * (size_t)blockDim.x + threadIdx.x; n < N; n += (size_t)gridDim.x * blockDim.x) {
+        const int k = (int)(n / P);
+        if (k == 0 || k == df.nz) continue;
+        const int i = (int)(n % df.nx), j = (int)((n / df.nx) % df.ny);
+        int I[2], J[2], K[2];
+        T wi[2], wj[2], wk[2];
+        int ni, nj, nk;
+        if (i & 1) { I[0] = i / 2; I[1] = (i / 2 + 1) % dc.nx; wi[0] = wi[1] = (T)0.5; ni = 2; }
+        else { I[0] = i / 2; wi[0] = (T)1; ni = 1; I[1] = 0; wi[1] = (T)0; }
+        if (j & 1) { J[0] = j / 2; J[1] = (j / 2 + 1) % dc.ny; wj[0] = wj[1] = (T)0.5; nj = 2; }
+        else { J[0] = j / 2; wj[0] = (T)1; nj = 1; J[1] = 0; wj[1] = (T)0; }
+        if (k & 1) { K[0] = k / 2; K[1] = k / 2 + 1; wk[0] = wk[1] = (T)0.5; nk = 2; }
+        else { K[0] = k / 2; wk[0] = (T)1; nk = 1; K[1] = 0; wk[1] = (T)0; }
+        T acc = (T)0;
+        for (int a = 0; a < nk; ++a)
+            for (int b = 0; b < nj; ++b)
+                for (int c = 0; c < ni; ++c) acc += (wk[a] * wj[b] * wi[c]) * uc[nid(dc, I[c], J[b], K[a])];
+        uf[n] += acc;
+    }
+}
+
+// coarsest level: red-black sweeps inside one block
+template <typename T>
+__global__ void k_coarse(T* __restrict__ u, const T* __restrict__ f, Dims d, T h2, int sweeps)
+{
+    const int half = d.nx / 2;
+    const int total = half * d.ny * (d.nz - 1);
+    const size_t P = (size_t)d.nx * d.ny;
+    for (int s = 0; s < sweeps; ++s)
+        for (int color = 0; color < 2; ++color) {
+            for (int t = threadIdx.x; t < total; t += blockDim.x) {
+                const int i2 = t % half;
+                const int j = (t / half) % d.ny;
+                const int k = 1 + t / (half * d.ny);
+                const int i = 2 * i2 + ((j + k + color) & 1);
+                const size_t n = nid(d, i, j, k);
+                const int ip = (i + 1 == d.nx) ? 0 : i + 1, im = (i == 0) ? d.nx - 1 : i - 1;
+                const int jp = (j + 1 == d.ny) ? 0 : j + 1, jm = (j == 0) ? d.ny - 1 : j - 1;
+                const size_t row = n - i;
+                const T sum = u[row + ip] + u[row + im] + u[nid(d, i, jp, k)] + u[nid(d, i, jm, k)] + u[n + P] +
+                              u[n - P];
+                u[n] = (sum + h2 * f[n]) * (T)(1.0 / 6.0);
+            }
+            __syncthreads();
+        }
+}
+
+__device__ __forceinline__ double block_sum(double v)
+{
+    __shared__ double part[32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0) part[w] = v;
+    __syncthreads();
+    v = (threadIdx.x < (blockDim.x + 31) / 32) ? part[threadIdx.x] : 0.0;
+    if (w == 0)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// phi_out = phi + e on the interior (e may be null), r = f - A phi_out in FP64,
+// stored as T; ||r||^2 accumulated into *norm2
+template <typename T>
+__global__ void k_resid64(const double* __restrict__ phi, const T* __restrict__ e, const double* __restrict__ f,
+                          double* __restrict__ phi_out, T* __restrict__ r, double* norm2, Dims d, double inv_h2)
+{
+    const size_t P = (size_t)d.nx * d.ny;
+    const size_t N = P * (d.nz + 1);
+    double acc = 0.0;
+    for (size_t n = blockIdx.x * (size_t)blockDim.x + threadIdx.x; n < N; n += (size_t)gridDim.x * blockDim.x) {
+        const int k = (int)(n / P);
+        if (k == 0 || k == d.nz) {
+            if (phi_out) phi_out[n] = phi[n];
+            r[n] = (T)0;
+            continue;
+        }
+        const int i = (int)(n % d.nx), j = (int)((n / d.nx) % d.ny);
+        const int ip = (i + 1 == d.nx) ? 0 : i + 1, im = (i == 0) ? d.nx - 1 : i - 1;
+        const int jp = (j + 1 == d.ny) ? 0 : j + 1, jm = (j == 0) ? d.ny - 1 : j - 1;
+        const size_t row = n - i;
+        const size_t nb[6] = {row + ip, row + im, nid(d, i, jp, k), nid(d, i, jm, k), n + P, n - P};
+        double c = phi[n];
+        if (e) c += (double)e[n];
+        double s = 0.0;
+#pragma unroll
+        for (int q = 0; q < 6; ++q) {
+            double v = phi[nb[q]];
+            if (e) v += (double)e[nb[q]];
+            s += v;
+        }
+        if (phi_out) phi_out[n] = c;
+        const double res = f[n] - (6.0 * c - s) * inv_h2;
+        r[n] = (T)res;
+        acc += res * res;
+    }
+    acc = block_sum(acc);
+    if (threadIdx.x == 0) atomicAdd(norm2, acc);
+}
+
+// f = rho_q * scale; electrode values on both phi buffers; ||b||^2 with the
+// electrode terms of the nodes next to the planes
+__global__ void k_rhs(const unsigned long long* __restrict__ rq, double scale, double* __restrict__ f,
+                      double* __restrict__ phi, double* __restrict__ phi_alt, double vb, double vt, Dims d,
+                      double inv_h2, double* norm2)
+{
+    const size_t P = (size_t)d.nx * d.ny;
+    const size_t N = P * (d.nz + 1);
+    double acc = 0.0;
+    for (size_t n = blockIdx.x * (size_t)blockDim.x + threadIdx.x; n < N; n += (size_t)gridDim.x * blockDim.x) {
+        const int k = (int)(n / P);
+        const double fv = (double)(long long)rq[n] * scale;
+        f[n] = fv;
+        if (k == 0) { phi[n] = vb; phi_alt[n] = vb; continue; }
+        if (k == d.nz) { phi[n] = vt; phi_alt[n] = vt; continue; }
+        double b = fv;
+        if (k == 1) b += vb * inv_h2;
+        if (k == d.nz - 1) b += vt * inv_h2;
+        acc += b * b;
+    }
+    acc = block_sum(acc);
+    if (threadIdx.x == 0) atomicAdd(norm2, acc);
+}
+
+int blocks(size_t n) { return grid_for((int64_t)n, 256, 152 * 8); }
+
+template <typename T>
+void vcycle(pic_ctx* c, int l)
+{
+    MGLevel& L = c->mg[l];
+    const Dims d{L.nx, L.ny, L.nz};
+    const T h2 = (T)(L.h * L.h);
+    T* u = (T*)L.u;
+    T* f = (T*)L.f;
+    cudaMemsetAsync(u, 0, sizeof(T) * L.nodes, c->stream);
+    if (l + 1 == (int)c->mg.size()) {
+        const int m = std::max(std::max(L.nx, L.ny), L.nz);
+        const int sweeps = std::min(4 * m * m + 16, 2000);
+        k_coarse<T><<<1, 1024, 0, c->stream>>>(u, f, d, h2, sweeps);
+        c->launches += 1;
+        return;
+    }
+    const size_t half = (size_t)(L.nx / 2) * L.ny * (L.nz - 1);
+    for (int s = 0; s < 2; ++s)
+        for (int color = 0; color < 2; ++color)
+            k_rbgs<T><<<blocks(half), 256, 0, c->stream>>>(u, f, d, h2, color);
+    k_resid<T><<<blocks(L.nodes), 256, 0, c->stream>>>(u, f, (T*)L.r, d, (T)(1.0 / (L.h * L.h)));
+    MGLevel& C = c->mg[l + 1];
+    const Dims dc{C.nx, C.ny, C.nz};
+    k_restrict<T><<<blocks(C.nodes), 256, 0, c->stream>>>((const T*)L.r, (T*)C.f, d, dc);
+    c->launches += 6;
+    vcycle<T>(c, l + 1);
+    k_prolong<T><<<blocks(L.nodes), 256, 0, c->stream>>>(u, (const T*)C.u, d, dc);
+    c->launches += 5;
+    for (int s = 0; s < 2; ++s)
+        for (int color = 0; color < 2; ++color)
+            k_rbgs<T><<<blocks(half), 256, 0, c->stream>>>(u, f, d, h2, color);
+}
+
+template <typename T>
+pic_status solve_t(pic_ctx* c, double tol, int max_iters, int* iters, double* res)
+{
+    const Dims d{c->nx, c->ny, c->nz};
+    const double inv_h2 = 1.0 / (c->dx * c->dx);
+    MGLevel& L0 = c->mg[0];
+    double h_norm[2];
+    // initial residual (phi unchanged)
+    cudaMemsetAsync(c->d_norm + 1, 0, sizeof(double), c->stream);
+    k_resid64<T><<<blocks(c->nodes), 256, 0, c->stream>>>(c->phi, (const T*)nullptr, c->f64, nullptr, (T*)L0.f,
+                                                          c->d_norm + 1, d, inv_h2);
+    c->launches += 1;
+    if (!PIC_CUDA_OK(cudaMemcpyAsync(h_norm, c->d_norm, 2 * sizeof(double), cudaMemcpyDeviceToHost, c->stream)) ||
+        !PIC_CUDA_OK(cudaStreamSynchronize(c->stream)))
+        return PIC_ECUDA;
+    const double bn = std::sqrt(h_norm[0]);
+    double rn = std::sqrt(h_norm[1]);
+    const double target = tol * (bn > 0.0 ? bn : 1.0);
+    int it = 0;
+    while (!(rn <= target) && it < max_iters) {
+        if (!std::isfinite(rn)) break;
+        vcycle<T>(c, 0);
+        cudaMemsetAsync(c->d_norm + 1, 0, sizeof(double), c->stream);
+        k_resid64<T><<<blocks(c->nodes), 256, 0, c->stream>>>(c->phi, (const T*)L0.u, c->f64, c->phi_alt, (T*)L0.f,
+                                                              c->d_norm + 1, d, inv_h2);
+        c->launches += 1;
+        std::swap(c->phi, c->phi_alt);
+        if (!PIC_CUDA_OK(cudaMemcpyAsync(h_norm + 1, c->d_norm + 1, sizeof(double), cudaMemcpyDeviceToHost,
+                                         c->stream)) ||
+            !PIC_CUDA_OK(cudaStreamSynchronize(c->stream)))
+            return PIC_ECUDA;
+        rn = std::sqrt(h_norm[1]);
+        ++it;
+    }
+    if (iters) *iters = it;
+    const double rel = bn > 0.0 ? rn / bn : rn;
+    if (res) *res = rel;
+    c->last_iters = it;
+    c->last_res = rel;
+    if (!std::isfinite(rn)) return PIC_ENONFINITE;
+    return rn <= target ? PIC_OK : PIC_ENOTCONV;
+}
+
+}  // namespace
+
+pic_status mg_setup(pic_ctx* c)
+{
+    const size_t tsz = c->prec == PIC_MIXED ? sizeof(float) : sizeof(double);
+    int nx = c->nx, ny = c->ny, nz = c->nz;
+    double h = c->dx;
+    c->mg.clear();
+    while (true) {
+        MGLevel L;
+        L.nx = nx; L.ny = ny; L.nz = nz; L.h = h;
+        L.nodes = (size_t)nx * ny * (nz + 1);
+        L.u = dev_alloc(c, tsz * L.nodes);
+        L.f = dev_alloc(c, tsz * L.nodes);
+        L.r = dev_alloc(c, tsz * L.nodes);
+        if (!L.u || !L.f || !L.r) return PIC_ENOMEM;
+        c->mg.push_back(L);
+        const bool can = nx % 2 == 0 && ny % 2 == 0 && nz % 2 == 0 && nx >= 4 && ny >= 4 && nz >= 4 &&
+                         (nx / 2) % 2 == 0 && (ny / 2) % 2 == 0;
+        if (!can) break;
+        nx /= 2; ny /= 2; nz /= 2; h *= 2.0;
+    }
+    return PIC_OK;
+}
+
+void launch_rhs(pic_ctx* c, double scale, double v_bot, double v_top, bool)
+{
+    const Dims d{c->nx, c->ny, c->nz};
+    cudaMemsetAsync(c->d_norm, 0, sizeof(double), c->stream);
+    k_rhs<<<blocks(c->nodes), 256, 0, c->stream>>>(c->rq, scale, c->f64, c->phi, c->phi_alt, v_bot, v_top, d,
+                                                  1.0 / (c->dx * c->dx), c->d_norm);
+    c->launches += 1;
+}
+
+pic_status mg_solve(pic_ctx* c, double, double, double tol, int max_iters, int* iters, double* res)
+{
+    if (c->prec == PIC_MIXED) return solve_t<float>(c, tol, max_iters, iters, res);
+    return solve_t<double>(c, tol, max_iters, iters, res);
+}
+
+}  // namespace pic

@@ -1,0 +1,158 @@
+// Periodic counting sort of one species by linear cell index (histogram,
+// exclusive scan, scatter), dropping dead slots.  Keeps consecutive particles
+// in the same or neighbouring cells so that field gathers and deposits of a
+// warp hit the same cache lines.  The order of particles inside a cell is not
+// fixed (atomic scatter); nothing in a step depends on it: the deposit is an
+// exact integer sum and the random numbers are keyed on particle ids.
+#include "pic_internal.cuh"
+
+namespace pic {
+namespace {
+
+constexpr int kScanThreads = 256;
+constexpr int kScanPer = 4;
+constexpr int kScanBlock = kScanThreads * kScanPer;
+
+__device__ __forceinline__ int key_of(const float4& p) { return __float_as_int(p.w); }
+__device__ __forceinline__ int key_of(const double4& p) { return p.w < 0.0 ? -1 : (int)p.w; }
+
+template <typename T4>
+__global__ void k_hist(const T4* __restrict__ pos, const unsigned long long* nslot, int sp, unsigned int* hist)
+{
+    const unsigned long long n = nslot[sp];
+    for (unsigned long long q = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; q < n;
+         q += (unsigned long long)gridDim.x * blockDim.x) {
+        const int c = key_of(pos[q]);
+        if (c >= 0) atomicAdd(hist + c, 1u);
+    }
+}
+
+// exclusive scan of one block of 1024 values; the block total goes to sums[blockIdx]
+__global__ void k_scan_block(const unsigned int* in, unsigned int* out, unsigned int* sums, size_t n)
+{
+    __shared__ unsigned int warp_tot[kScanThreads / 32];
+    const size_t base = (size_t)blockIdx.x * kScanBlock + (size_t)threadIdx.x * kScanPer;
+    unsigned int v[kScanPer];
+    unsigned int s = 0;
+#pragma unroll
+    for (int t = 0; t < kScanPer; ++t) {
+        v[t] = (base + t < n) ? in[base + t] : 0u;
+        s += v[t];
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    unsigned int incl = s;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const unsigned int y = __shfl_up_sync(0xffffffffu, incl, d);
+        if (lane >= d) incl += y;
+    }
+    if (lane == 31) warp_tot[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        unsigned int w = lane < kScanThreads / 32 ? warp_tot[lane] : 0u;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const unsigned int y = __shfl_up_sync(0xffffffffu, w, d);
+            if (lane >= d) w += y;
+        }
+        if (lane < kScanThreads / 32) warp_tot[lane] = w;
+    }
+    __syncthreads();
+    unsigned int run = (incl - s) + (warp > 0 ? warp_tot[warp - 1] : 0u);
+#pragma unroll
+    for (int t = 0; t < kScanPer; ++t) {
+        if (base + t < n) out[base + t] = run;
+        run += v[t];
+    }
+    if (threadIdx.x == kScanThreads - 1) sums[blockIdx.x] = run;
+}
+
+__global__ void k_scan_add(unsigned int* out, const unsigned int* offs, size_t n)
+{
+    for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < n; q += (size_t)gridDim.x * blockDim.x)
+        out[q] += offs[q / kScanBlock];
+}
+
+template <typename T4>
+__global__ void k_scatter(const T4* __restrict__ pos, const T4* __restrict__ vel, const unsigned long long* nslot,
+                          int sp, unsigned int* cursor, T4* __restrict__ pos_out, T4* __restrict__ vel_out)
+{
+    const unsigned long long n = nslot[sp];
+    for (unsigned long long q = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; q < n;
+         q += (unsigned long long)gridDim.x * blockDim.x) {
+        const T4 p = pos[q];
+        const int c = key_of(p);
+        if (c < 0) continue;
+        const unsigned int d = atomicAdd(cursor + c, 1u);
+        pos_out[d] = p;
+        vel_out[d] = vel[q];
+    }
+}
+
+__global__ void k_set_nslot(unsigned long long* nslot, int sp, const unsigned int* total)
+{
+    nslot[sp] = *total;
+}
+
+// exclusive scan of n values in place through the per-level scratch buffers
+void scan(pic_ctx* c, unsigned int* data, size_t n, int level)
+{
+    const size_t nb = (n + kScanBlock - 1) / kScanBlock;
+    unsigned int* sums = c->scan_tmp[level];
+    k_scan_block<<<(unsigned)nb, kScanThreads, 0, c->stream>>>(data, data, sums, n);
+    c->launches += 1;
+    if (nb > 1) {
+        scan(c, sums, nb, level + 1);
+        k_scan_add<<<grid_for((int64_t)n, 256, 152 * 8), 256, 0, c->stream>>>(data, sums, n);
+        c->launches += 1;
+    }
+}
+
+}  // namespace
+
+// scratch: one block-sum buffer per scan level, plus a final total slot
+size_t sort_scratch_setup(pic_ctx* c)
+{
+    size_t n = c->cells;
+    size_t bytes = 0;
+    c->scan_tmp.clear();
+    c->scan_len.clear();
+    while (true) {
+        const size_t nb = (n + kScanBlock - 1) / kScanBlock;
+        unsigned int* p = (unsigned int*)dev_alloc(c, sizeof(unsigned int) * (nb + 1));
+        if (!p) return 0;
+        c->scan_tmp.push_back(p);
+        c->scan_len.push_back(nb);
+        bytes += sizeof(unsigned int) * (nb + 1);
+        if (nb <= 1) break;
+        n = nb;
+    }
+    return bytes + 1;
+}
+
+void sort_particles(pic_ctx* c, int sp)
+{
+    const size_t nc = c->cells;
+    cudaMemsetAsync(c->cursor, 0, sizeof(unsigned int) * nc, c->stream);
+    const int grid = grid_for(c->cap[sp], 256, 152 * 8);
+    if (c->prec == PIC_MIXED)
+        k_hist<float4><<<grid, 256, 0, c->stream>>>((const float4*)c->pos[sp], c->d_nslot, sp, c->cursor);
+    else
+        k_hist<double4><<<grid, 256, 0, c->stream>>>((const double4*)c->pos[sp], c->d_nslot, sp, c->cursor);
+    scan(c, c->cursor, nc, 0);
+    if (c->prec == PIC_MIXED)
+        k_scatter<float4><<<grid, 256, 0, c->stream>>>((const float4*)c->pos[sp], (const float4*)c->vel[sp],
+                                                       c->d_nslot, sp, c->cursor, (float4*)c->pos_alt[sp],
+                                                       (float4*)c->vel_alt[sp]);
+    else
+        k_scatter<double4><<<grid, 256, 0, c->stream>>>((const double4*)c->pos[sp], (const double4*)c->vel[sp],
+                                                        c->d_nslot, sp, c->cursor, (double4*)c->pos_alt[sp],
+                                                        (double4*)c->vel_alt[sp]);
+    // the last scan level's single block sum is the number of live particles
+    k_set_nslot<<<1, 1, 0, c->stream>>>(c->d_nslot, sp, c->scan_tmp.back());
+    c->launches += 3;
+    void* t = c->pos[sp]; c->pos[sp] = c->pos_alt[sp]; c->pos_alt[sp] = t;
+    t = c->vel[sp]; c->vel[sp] = c->vel_alt[sp]; c->vel_alt[sp] = t;
+}
+
+}  // namespace pic

@@ -1,0 +1,234 @@
+"""Parity of the CUDA path (through the C ABI) with the oracle.
+
+FP64: with the same potential and grain tables fed to both, one step of the
+particle cycle is bit-identical (positions, velocities, ids, fixed-point rho,
+grain counts, event counters).  With each side solving its own Poisson
+equation (multigrid to 1e-10 vs the exact solve), the potential agrees to the
+solver tolerance and the integer outcomes stay identical over a short run.
+Mixed precision agrees within single-precision tolerances.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+import paper_1801_00972_gb300 as P
+from paper_1801_00972_gb300 import build as B
+from paper_1801_00972_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import torch
+    B.build()
+    torch.cuda.set_device(0)
+    P.load()
+
+
+def _stream():
+    import torch
+    return torch.cuda.current_stream().cuda_stream
+
+
+def _pair(wl, prec=P.PIC_FP64, flags=0, parts=None, **kw):
+    parts = parts if parts is not None else I.sample_particles(wl)
+    oflags = (O.NO_MCC if flags & P.PIC_F_NO_MCC else 0) | (O.IONS_FROZEN if flags & P.PIC_F_IONS_FROZEN else 0) \
+        | (O.MOMENTS if flags & P.PIC_F_MOMENTS else 0)
+    ref = O.Sim(wl, parts, flags=oflags)
+    run = P.Run(wl, parts, prec=prec, flags=flags, stream=_stream(), **kw)
+    return ref, run
+
+
+def _same_particles(run, ref):
+    for sp in range(2):
+        xg, vg, ig = run.particles(sp)
+        xo, vo, io = ref.particles(sp)
+        assert np.array_equal(ig, io), f"species {sp}: ids differ ({len(ig)} vs {len(io)})"
+        assert np.array_equal(xg, xo), f"species {sp}: positions differ, max {np.max(np.abs(xg - xo))}"
+        assert np.array_equal(vg, vo), f"species {sp}: velocities differ, max {np.max(np.abs(vg - vo))}"
+
+
+def _counters_equal(run, ref):
+    n, cg = run.counts()
+    cg.pop("pushed")
+    co = ref.counters()
+    assert cg == co, (cg, co)
+    assert n.tolist() == [ref.count(0), ref.count(1)]
+
+
+@pytest.mark.parametrize("shape,ne,ni,grains", [((8, 8, 16), 2000, 2000, 1), ((16, 8, 24), 3001, 2777, 3),
+                                                  ((8, 12, 10), 0, 513, 0), ((4, 4, 4), 37, 0, 0)])
+def test_initial_rho_and_phi(shape, ne, ni, grains):
+    nx, ny, nz = shape
+    wl = I.small(nx=nx, ny=ny, nz=nz, n_e=ne, n_i=ni, grains=grains if nz >= 8 else 0)
+    ref, run = _pair(wl)
+    assert np.array_equal(run.rho(), ref.rho())
+    pg, po = run.phi(), ref.phi()
+    assert np.max(np.abs(pg - po)) <= 1e-8 * max(1.0, np.max(np.abs(po)))
+    if wl.grain_r.size:
+        tg, to = run.gtab(), ref.gtab()
+        assert np.max(np.abs(tg - to)) <= 1e-8 * np.max(np.abs(to))
+
+
+@pytest.mark.parametrize("case", ["dc", "rf_grains", "dense_grain"])
+def test_fp64_steps_bit_exact_given_phi(case):
+    if case == "dc":
+        wl = I.small(nx=8, ny=8, nz=16, n_e=4000, n_i=4000, grains=1, v_dc=-60.0, dt=2e-10)
+    elif case == "rf_grains":
+        wl = I.small(nx=16, ny=16, nz=32, n_e=6000, n_i=6000, grains=4, v_dc=0.0, v_rf=80.0, f_rf=13.56e6,
+                     phase=0.3)
+    else:
+        # many particles around one grain so that absorption happens every step
+        wl = I.small(nx=8, ny=8, nz=16, n_e=0, n_i=0, grains=1)
+        rng = np.random.default_rng(3)
+        g = wl.grain_pos[0]
+        parts = []
+        base = 0
+        for n, s in ((5000, 3e5), (5000, 2e3)):
+            x = g + rng.uniform(-1.4, 1.4, (n, 3)) * wl.dx
+            d = np.linalg.norm(x - g, axis=1, keepdims=True)
+            x = np.where(d < 2 * wl.grain_r[0], g + (x - g) * 3 * wl.grain_r[0] / d, x)
+            v = -(x - g) / np.linalg.norm(x - g, axis=1, keepdims=True) * s + rng.normal(0, s / 3, (n, 3))
+            parts.append((x, v, np.arange(base, base + n, dtype=np.uint32)))
+            base += n
+        wl.n_e = wl.n_i = 5000
+        ref, run = _pair(wl, parts=parts)
+        run.set_gtab(ref.gtab())
+        for _ in range(4):
+            run.set_phi(ref.phi())
+            run.advance()
+            ref.advance()
+            ref.solve()
+            _same_particles(run, ref)
+            assert np.array_equal(run.rho(), ref.rho())
+            assert np.array_equal(run.grains()[0], ref.grains()[0])
+            assert np.array_equal(run.grains()[1], ref.grains()[1])
+            _counters_equal(run, ref)
+        assert ref.grains()[0].sum() > 0
+        return
+    ref, run = _pair(wl)
+    run.set_gtab(ref.gtab())
+    for _ in range(5):
+        run.set_phi(ref.phi())
+        run.advance()
+        ref.advance()
+        ref.solve()
+        _same_particles(run, ref)
+        assert np.array_equal(run.rho(), ref.rho())
+        assert np.array_equal(run.grains()[0], ref.grains()[0])
+        _counters_equal(run, ref)
+
+
+def test_fp64_own_solve_short_run():
+    wl = I.small(nx=16, ny=16, nz=32, n_e=20000, n_i=20000, grains=2, v_dc=-50.0, dt=1e-10)
+    ref, run = _pair(wl)
+    for _ in range(10):
+        ref.step()
+        run.step()
+    pg, po = run.phi(), ref.phi()
+    assert np.max(np.abs(pg - po)) <= 1e-5 * np.max(np.abs(po))
+    assert np.array_equal(run.grains()[0], ref.grains()[0])
+    n, cg = run.counts()
+    cg.pop("pushed")
+    co = ref.counters()
+    for k in cg:
+        assert abs(cg[k] - co[k]) <= 2, (k, cg[k], co[k])
+    for sp in range(2):
+        xg, vg, ig = run.particles(sp)
+        xo, vo, io = ref.particles(sp)
+        common, a, b = np.intersect1d(ig, io, return_indices=True)
+        assert len(common) >= len(io) - 4
+        assert np.max(np.abs(xg[a] - xo[b])) <= 1e-9 * wl.nz * wl.dx
+
+
+def test_sort_does_not_change_results():
+    wl = I.small(nx=16, ny=8, nz=16, n_e=5000, n_i=5000, grains=1, v_dc=-40.0)
+    parts = I.sample_particles(wl)
+    a = P.Run(wl, parts, prec=P.PIC_FP64, stream=_stream(), sort_every=1)
+    b = P.Run(wl, parts, prec=P.PIC_FP64, stream=_stream(), sort_every=0)
+    for _ in range(6):
+        a.step()
+        b.step()
+    for sp in range(2):
+        xa, va, ia = a.particles(sp)
+        xb, vb, ib = b.particles(sp)
+        assert np.array_equal(ia, ib) and np.array_equal(xa, xb) and np.array_equal(va, vb)
+    assert np.array_equal(a.rho(), b.rho())
+    assert np.array_equal(a.phi(), b.phi())
+
+
+@pytest.mark.parametrize("shape", [(8, 8, 16), (16, 16, 32)])
+def test_mixed_step_close_to_oracle(shape):
+    nx, ny, nz = shape
+    wl = I.small(nx=nx, ny=ny, nz=nz, n_e=8000, n_i=8000, grains=1, v_dc=-40.0)
+    ref, run = _pair(wl, prec=P.PIC_MIXED)
+    pg, po = run.phi(), ref.phi()
+    assert np.max(np.abs(pg - po)) <= 1e-4 * max(1.0, np.max(np.abs(po)))
+    run.set_gtab(ref.gtab())
+    run.set_phi(ref.phi())
+    run.advance()
+    ref.advance()
+    for sp in range(2):
+        xg, vg, ig = run.particles(sp)
+        xo, vo, io = ref.particles(sp)
+        common, a, b = np.intersect1d(ig, io, return_indices=True)
+        assert len(common) >= len(io) - 3 and len(common) >= len(ig) - 3
+        dxp = np.abs(xg[a] - xo[b])
+        dxp = np.minimum(dxp, np.array(wl.box) - dxp)
+        assert np.max(dxp) <= 2e-6 * wl.dx * 16
+        vscale = np.sqrt(np.mean(vo ** 2))
+        bad = np.abs(vg[a] - vo[b]).max(axis=1) > 1e-4 * vscale
+        assert bad.sum() <= 3          # a collision decision may flip on a float rounding
+    rg, ro = run.rho(), ref.rho()
+    assert abs(int(rg.sum()) - int(ro.sum())) <= 4 * 2 ** 42
+    assert np.abs(rg - ro).max() <= 2 ** 42 * 8
+
+
+def test_mixed_short_run_statistics():
+    wl = I.small(nx=16, ny=16, nz=32, n_e=20000, n_i=20000, grains=2, v_dc=-50.0)
+    ref, run = _pair(wl, prec=P.PIC_MIXED)
+    for _ in range(10):
+        ref.step()
+        run.step()
+    pg, po = run.phi(), ref.phi()
+    assert np.max(np.abs(pg - po)) <= 2e-2 * np.max(np.abs(po))
+    n, cg = run.counts()
+    co = ref.counters()
+    for k in ("lost_bot_e", "lost_top_e", "e_el"):
+        assert abs(cg[k] - co[k]) <= 5 + 0.05 * co[k], (k, cg[k], co[k])
+
+
+def test_moments_match_oracle():
+    wl = I.small(nx=8, ny=8, nz=16, n_e=3000, n_i=3000, grains=1, v_dc=-20.0)
+    ref, run = _pair(wl, flags=P.PIC_F_MOMENTS)
+    ref.reset_moments()
+    for _ in range(3):
+        ref.step()
+        run.step()
+    for what in range(5):
+        mg, mo = run.moments(what), ref.moments(what)
+        assert np.max(np.abs(mg - mo)) <= 1e-6 * max(np.max(np.abs(mo)), 1e-30), what
+
+
+def test_empty_and_conservation():
+    wl = I.small(nx=8, ny=8, nz=8, n_e=0, n_i=0, grains=0)
+    ref, run = _pair(wl)
+    run.step(3)
+    n, c = run.counts()
+    assert n.tolist() == [0, 0] and not any(c.values())
+    del ref
+    assert not run.rho().any()
+    wl = I.small(nx=8, ny=8, nz=16, n_e=7000, n_i=5000, grains=2, v_dc=-80.0, dt=2e-10)
+    run = P.Run(wl, I.sample_particles(wl), prec=P.PIC_MIXED, stream=_stream())
+    prev, pc = run.counts()
+    for _ in range(5):
+        run.step()
+        n, c = run.counts()
+        ion = c["e_ion"] - pc["e_ion"]
+        for sp, s in ((0, "e"), (1, "i")):
+            lost = sum(c[f"{k}_{s}"] - pc[f"{k}_{s}"] for k in ("lost_bot", "lost_top", "abs"))
+            assert n[sp] == prev[sp] - lost + ion
+        nabs, _ = run.grains()
+        assert int(run.rho().sum()) == 2 ** 42 * int(n[1] - n[0] + nabs[:, 1].sum() - nabs[:, 0].sum())
+        prev, pc = n, c
