@@ -122,7 +122,9 @@ def run_gpu(P, I, wl, parts, prec, steps, warmup, stream, gpu):
             torch.distributed.barrier()
         torch.cuda.synchronize()
         start.record(torch.cuda.current_stream())
+        torch.cuda.nvtx.range_push("timed")
         run.step(steps)
+        torch.cuda.nvtx.range_pop()
         end.record(torch.cuda.current_stream())
         torch.cuda.synchronize()
         if torch.distributed.is_initialized():
