@@ -142,7 +142,7 @@ def test_fp64_own_solve_short_run():
         # the two Poisson solvers agree to ~1e-10; dynamics near grains amplify it
         d = np.abs(xg[a] - xo[b]).max(axis=1)
         assert np.max(d) <= 1e-6 * wl.dx
-        assert np.mean(d <= 1e-9 * wl.dx) >= 0.999
+        assert np.mean(d <= 1e-7 * wl.dx) >= 0.999
 
 
 def test_sort_does_not_change_results():
