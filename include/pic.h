@@ -181,6 +181,37 @@ pic_status pic_profile(pic_ctx* ctx, int32_t enable);
 pic_status pic_profile_read(pic_ctx* ctx, double* push_ms, int64_t* push_launches, double* solve_ms,
                             int64_t* solves, int64_t* solve_iterations, int64_t* kernels_launched);
 
+/* Poisson solve that allocates nothing.  The paper has no counterpart: this is
+ * a service for callers that cannot call cudaMalloc, such as a host application
+ * whose own memory manager has already reserved the device memory (an extra
+ * cudaMalloc fails or escapes its accounting), or a time-critical loop that must
+ * avoid cudaMalloc/cudaFree because they synchronise the whole device.
+ *
+ * It solves the same equation as pic_solve (Eq. 3, periodic x and y, Dirichlet
+ * planes k = 0 and k = nz) with the same multigrid and FP64 refinement, for a
+ * mesh of at most 131072 nodes (nx*ny*(nz+1)); larger meshes return
+ * PIC_EINVAL.  The caller passes device pointers:
+ *   rho_q_dev  int64 fixed-point charge per node, as pic_get_rho returns it;
+ *   scale      factor turning rho_q into rho/eps0 (for a run of weight W:
+ *              e W / dx^3 * 2^-42 / eps0);
+ *   phi_dev    FP64 potential per node: the start value on entry (e.g. zeros or
+ *              the previous solution), the solution on return; the electrode
+ *              planes are set to v_bot and v_top.
+ * prec is PIC_FP64 or PIC_MIXED; tol, max_iters, iterations and rel_residual
+ * mean what they mean for pic_solve.  Work runs on cuda_stream (NULL: default)
+ * and the call returns after the stream has finished it.
+ *
+ * The working set lives in one fixed device array of about 6.3 MB inside the
+ * library, which every GPU that loads the library holds until the process
+ * exits.  The first call on a device looks up that array's device address
+ * (once per device, for the current device); make that first call before any
+ * stream capture.  Every call reuses the same array and overwrites what the
+ * previous call left there, so calls that overlap on the GPU (from several
+ * host threads or streams at once) race and must be serialised by the caller. */
+pic_status pic_solve_noalloc(int32_t nx, int32_t ny, int32_t nz, double dx, const int64_t* rho_q_dev, double scale,
+                             double v_bot, double v_top, double* phi_dev, int32_t prec, double tol,
+                             int32_t max_iters, int32_t* iterations, double* rel_residual, void* cuda_stream);
+
 const char* pic_last_error(const pic_ctx* ctx);   /* NULL ctx: last pic_init failure */
 void pic_destroy(pic_ctx* ctx);
 

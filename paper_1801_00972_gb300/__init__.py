@@ -34,7 +34,7 @@ PIC_C_N = len(COUNTERS)
 SYMBOLS = ("pic_init", "pic_step", "pic_advance", "pic_solve", "pic_grain_charges", "pic_counts",
            "pic_moments", "pic_get_particles", "pic_get_rho", "pic_get_phi", "pic_set_phi",
            "pic_get_grain_table", "pic_set_grain_table", "pic_set_grain_counts", "pic_step_index",
-           "pic_profile", "pic_profile_read", "pic_last_error", "pic_destroy")
+           "pic_profile", "pic_profile_read", "pic_solve_noalloc", "pic_last_error", "pic_destroy")
 
 
 class pic_mesh(C.Structure):
@@ -94,6 +94,8 @@ def load(path: str | None = None):
             "pic_get_grain_table": [vp, pd, sz], "pic_set_grain_table": [vp, pd, sz],
             "pic_set_grain_counts": [vp, pi64, sz],
             "pic_profile": [vp, i32], "pic_profile_read": [vp, pd, pi64, pd, pi64, pi64, pi64],
+            "pic_solve_noalloc": [i32, i32, i32, C.c_double, vp, C.c_double, C.c_double, C.c_double, vp, i32,
+                                  C.c_double, i32, C.POINTER(i32), pd, vp],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -217,6 +219,19 @@ def pic_profile_read(ctx):
                                         C.byref(kl)))
     return dict(push_ms=pm.value, push_launches=pl.value, solve_ms=sm.value, solves=ns.value,
                 solve_iterations=it.value, kernels=kl.value)
+
+
+def pic_solve_noalloc(nx, ny, nz, dx, rho_q_ptr, scale, v_bot, v_top, phi_ptr, prec, tol, max_iters,
+                      stream=None):
+    """Allocation-free Poisson solve on caller-owned device buffers (raw device
+    pointers as ints).  Returns (iterations, relative residual)."""
+    it = C.c_int32()
+    res = C.c_double()
+    st = load().pic_solve_noalloc(int(nx), int(ny), int(nz), float(dx), C.c_void_p(rho_q_ptr), float(scale),
+                                  float(v_bot), float(v_top), C.c_void_p(phi_ptr), int(prec), float(tol),
+                                  int(max_iters), C.byref(it), C.byref(res), C.c_void_p(stream or 0))
+    _check(None, st)
+    return it.value, res.value
 
 
 def pic_step_index(ctx):

@@ -154,6 +154,10 @@ bool finite_all(const double* p, size_t n)
 
 }  // namespace
 
+namespace pic {
+void set_global_error(const char* msg) { g_init_error = msg; }
+}  // namespace pic
+
 extern "C" {
 
 const char* pic_last_error(const pic_ctx* ctx) { return ctx ? ctx->err.c_str() : g_init_error.c_str(); }

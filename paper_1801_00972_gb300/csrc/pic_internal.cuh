@@ -234,6 +234,8 @@ pic_status mg_solve(pic_ctx* c, double v_bot, double v_top, double tol, int max_
 // api.cu
 void* dev_alloc(pic_ctx* c, size_t bytes);
 int grid_for(int64_t n, int threads, int max_blocks);
+// message returned by pic_last_error(NULL) for calls without a run context
+void set_global_error(const char* msg);
 // bracket one launch with events when measuring (begin returns the start event)
 cudaEvent_t prof_begin(pic_ctx* c);
 void prof_end(pic_ctx* c, cudaEvent_t start, bool push);

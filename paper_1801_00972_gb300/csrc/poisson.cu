@@ -11,7 +11,9 @@
 // red-black Gauss-Seidel smoothing, full-weighting restriction, trilinear
 // prolongation, the 7-point operator rediscretised on each level (spacing
 // doubling), and many smoothing sweeps on the coarsest level in one block.
+#include <algorithm>
 #include <cmath>
+#include <mutex>
 
 #include "pic_internal.cuh"
 
@@ -344,3 +346,190 @@ pic_status mg_solve(pic_ctx* c, double, double, double tol, int max_iters, int* 
 }
 
 }  // namespace pic
+
+// ---------------------------------------------------------------------------
+// pic_solve_noalloc: the same multigrid solve for callers that cannot allocate
+// device memory.  Its whole working set (second potential buffer, right-hand
+// side, norms and every level's u, f, r) lives in one file-scope device array
+// of fixed size, which each GPU that loads the library holds until exit.
+namespace pic {
+namespace {
+
+constexpr size_t kNaMaxNodes = 131072;       // largest fine mesh, in nodes
+constexpr size_t kNaAlign = 256;
+// phi_alt + f (16 B/node) + three level arrays summing to at most 4/3 of the
+// fine nodes in doubles (32 B/node) + norms + per-array alignment padding
+constexpr size_t kNaBytes = kNaMaxNodes * 48 + 64 * kNaAlign + 4096;
+constexpr int kNaMaxDevices = 64;
+constexpr int kNaMaxLevels = 24;
+
+static __device__ __align__(256) unsigned char g_na_scratch[kNaBytes];
+
+std::mutex g_na_mu;
+unsigned char* g_na_ptr[kNaMaxDevices] = {};
+
+// Device address of the scratch array on the current device, looked up once
+// per device (the array's name is only a host-side stand-in in host code).
+pic_status na_scratch(unsigned char** out)
+{
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) return PIC_ECUDA;
+    if (dev < 0 || dev >= kNaMaxDevices) return PIC_EINVAL;
+    std::lock_guard<std::mutex> lock(g_na_mu);
+    if (!g_na_ptr[dev]) {
+        void* p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_na_scratch) != cudaSuccess || !p) return PIC_ECUDA;
+        g_na_ptr[dev] = (unsigned char*)p;
+    }
+    *out = g_na_ptr[dev];
+    return PIC_OK;
+}
+
+struct NaCtx {
+    MGLevel lv[kNaMaxLevels];
+    int nl;
+    cudaStream_t s;
+};
+
+template <typename T>
+void na_vcycle(NaCtx& c, int l)
+{
+    MGLevel& L = c.lv[l];
+    const Dims d{L.nx, L.ny, L.nz};
+    const T h2 = (T)(L.h * L.h);
+    T* u = (T*)L.u;
+    T* f = (T*)L.f;
+    cudaMemsetAsync(u, 0, sizeof(T) * L.nodes, c.s);
+    if (l + 1 == c.nl) {
+        const int m = std::max(std::max(L.nx, L.ny), L.nz);
+        k_coarse<T><<<1, 1024, 0, c.s>>>(u, f, d, h2, std::min(4 * m * m + 16, 2000));
+        return;
+    }
+    const size_t half = (size_t)(L.nx / 2) * L.ny * (L.nz - 1);
+    for (int s = 0; s < 2; ++s)
+        for (int color = 0; color < 2; ++color) k_rbgs<T><<<blocks(half), 256, 0, c.s>>>(u, f, d, h2, color);
+    k_resid<T><<<blocks(L.nodes), 256, 0, c.s>>>(u, f, (T*)L.r, d, (T)(1.0 / (L.h * L.h)));
+    MGLevel& C = c.lv[l + 1];
+    const Dims dc{C.nx, C.ny, C.nz};
+    k_restrict<T><<<blocks(C.nodes), 256, 0, c.s>>>((const T*)L.r, (T*)C.f, d, dc);
+    na_vcycle<T>(c, l + 1);
+    k_prolong<T><<<blocks(L.nodes), 256, 0, c.s>>>(u, (const T*)C.u, d, dc);
+    for (int s = 0; s < 2; ++s)
+        for (int color = 0; color < 2; ++color) k_rbgs<T><<<blocks(half), 256, 0, c.s>>>(u, f, d, h2, color);
+}
+
+template <typename T>
+pic_status na_solve(NaCtx& c, double* phi_user, double* phi_alt, const double* f64, double* norm, Dims d,
+                    double dx, double tol, int max_iters, int* iters, double* res)
+{
+    const double inv_h2 = 1.0 / (dx * dx);
+    const size_t nodes = (size_t)d.nx * d.ny * (d.nz + 1);
+    double h_norm[2];
+    double* phi = phi_user;
+    double* alt = phi_alt;
+    cudaMemsetAsync(norm + 1, 0, sizeof(double), c.s);
+    k_resid64<T><<<blocks(nodes), 256, 0, c.s>>>(phi, (const T*)nullptr, f64, nullptr, (T*)c.lv[0].f, norm + 1, d,
+                                                 inv_h2);
+    if (cudaMemcpyAsync(h_norm, norm, 2 * sizeof(double), cudaMemcpyDeviceToHost, c.s) != cudaSuccess ||
+        cudaStreamSynchronize(c.s) != cudaSuccess)
+        return PIC_ECUDA;
+    const double bn = std::sqrt(h_norm[0]);
+    double rn = std::sqrt(h_norm[1]);
+    const double target = tol * (bn > 0.0 ? bn : 1.0);
+    int it = 0;
+    while (!(rn <= target) && it < max_iters && std::isfinite(rn)) {
+        na_vcycle<T>(c, 0);
+        cudaMemsetAsync(norm + 1, 0, sizeof(double), c.s);
+        k_resid64<T><<<blocks(nodes), 256, 0, c.s>>>(phi, (const T*)c.lv[0].u, f64, alt, (T*)c.lv[0].f, norm + 1, d,
+                                                     inv_h2);
+        std::swap(phi, alt);
+        if (cudaMemcpyAsync(h_norm + 1, norm + 1, sizeof(double), cudaMemcpyDeviceToHost, c.s) != cudaSuccess ||
+            cudaStreamSynchronize(c.s) != cudaSuccess)
+            return PIC_ECUDA;
+        rn = std::sqrt(h_norm[1]);
+        ++it;
+    }
+    // the last update may sit in the scratch buffer: return it in the caller's array
+    if (phi != phi_user &&
+        (cudaMemcpyAsync(phi_user, phi, sizeof(double) * nodes, cudaMemcpyDeviceToDevice, c.s) != cudaSuccess ||
+         cudaStreamSynchronize(c.s) != cudaSuccess))
+        return PIC_ECUDA;
+    if (iters) *iters = it;
+    if (res) *res = bn > 0.0 ? rn / bn : rn;
+    if (!std::isfinite(rn)) return PIC_ENONFINITE;
+    return rn <= target ? PIC_OK : PIC_ENOTCONV;
+}
+
+}  // namespace
+}  // namespace pic
+
+extern "C" pic_status pic_solve_noalloc(int32_t nx, int32_t ny, int32_t nz, double dx, const int64_t* rho_q_dev,
+                                        double scale, double v_bot, double v_top, double* phi_dev, int32_t prec,
+                                        double tol, int32_t max_iters, int32_t* iterations, double* rel_residual,
+                                        void* cuda_stream)
+{
+    using namespace pic;
+    if (nx < 4 || ny < 4 || nz < 2 || nx % 2 || ny % 2 || !(dx > 0.0) || !rho_q_dev || !phi_dev ||
+        (prec != PIC_FP64 && prec != PIC_MIXED) || !(tol > 0.0) || max_iters < 1) {
+        set_global_error("pic_solve_noalloc: invalid mesh, pointer, precision, tolerance or iteration limit");
+        return PIC_EINVAL;
+    }
+    const size_t nodes = (size_t)nx * ny * (nz + 1);
+    if (nodes > kNaMaxNodes) {
+        set_global_error("pic_solve_noalloc: mesh has more than 131072 nodes (nx*ny*(nz+1)), the fixed scratch "
+                         "limit; use pic_init/pic_solve for larger meshes");
+        return PIC_EINVAL;
+    }
+    unsigned char* base = nullptr;
+    pic_status st = na_scratch(&base);
+    if (st != PIC_OK) {
+        set_global_error("pic_solve_noalloc: could not look up the scratch array on the current device");
+        return st;
+    }
+    // carve the scratch: phi_alt, f, norms, then the level arrays
+    size_t off = 0;
+    auto take = [&](size_t bytes) -> void* {
+        void* p = base + off;
+        off += (bytes + kNaAlign - 1) / kNaAlign * kNaAlign;
+        return p;
+    };
+    double* phi_alt = (double*)take(sizeof(double) * nodes);
+    double* f64 = (double*)take(sizeof(double) * nodes);
+    double* norm = (double*)take(4 * sizeof(double));
+    NaCtx c;
+    c.s = (cudaStream_t)cuda_stream;
+    c.nl = 0;
+    const size_t tsz = prec == PIC_MIXED ? sizeof(float) : sizeof(double);
+    int lx = nx, ly = ny, lz = nz;
+    double h = dx;
+    while (c.nl < kNaMaxLevels) {
+        MGLevel& L = c.lv[c.nl++];
+        L.nx = lx; L.ny = ly; L.nz = lz; L.h = h;
+        L.nodes = (size_t)lx * ly * (lz + 1);
+        L.u = take(tsz * L.nodes);
+        L.f = take(tsz * L.nodes);
+        L.r = take(tsz * L.nodes);
+        const bool can = lx % 4 == 0 && ly % 4 == 0 && lz % 2 == 0 && lz >= 4;
+        if (!can) break;
+        lx /= 2; ly /= 2; lz /= 2; h *= 2.0;
+    }
+    if (off > kNaBytes) {
+        set_global_error("pic_solve_noalloc: scratch layout exceeds the fixed array");
+        return PIC_EINVAL;
+    }
+    // rhs from the fixed-point charge; electrode values on both potential buffers
+    const Dims d{nx, ny, nz};
+    cudaMemsetAsync(norm, 0, sizeof(double), c.s);
+    k_rhs<<<blocks(nodes), 256, 0, c.s>>>((const unsigned long long*)rho_q_dev, scale, f64, phi_dev, phi_alt, v_bot,
+                                          v_top, d, 1.0 / (dx * dx), norm);
+    int it = 0;
+    double res = 0.0;
+    st = prec == PIC_MIXED ? na_solve<float>(c, phi_dev, phi_alt, f64, norm, d, dx, tol, max_iters, &it, &res)
+                           : na_solve<double>(c, phi_dev, phi_alt, f64, norm, d, dx, tol, max_iters, &it, &res);
+    if (iterations) *iterations = it;
+    if (rel_residual) *rel_residual = res;
+    if (st == PIC_ECUDA) set_global_error("pic_solve_noalloc: a CUDA call failed");
+    else if (st == PIC_ENOTCONV) set_global_error("pic_solve_noalloc: tolerance not reached in max_iters");
+    else if (st == PIC_ENONFINITE) set_global_error("pic_solve_noalloc: non-finite residual");
+    return st;
+}
