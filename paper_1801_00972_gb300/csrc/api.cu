@@ -102,6 +102,14 @@ pic_status check(pic_ctx* c)
     if (err == PIC_ENONFINITE)
         return fail(c, PIC_ENONFINITE, "non-finite particle state or a particle moved more than one box length");
     if (err != 0) return fail(c, PIC_ECUDA, "device error " + std::to_string(err));
+    int sf = 0;
+    e = cudaMemcpy(&sf, c->d_solve_flag, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(c, e, "solve flag");
+    if (sf != 0) {
+        cudaMemset(c->d_solve_flag, 0, sizeof(int));
+        if (sf == PIC_ENONFINITE) return fail(c, PIC_ENONFINITE, "Poisson solve: non-finite residual");
+        return fail(c, PIC_ENOTCONV, "Poisson solve did not reach the tolerance within max_cycles");
+    }
     return PIC_OK;
 }
 
@@ -141,6 +149,10 @@ void destroy(pic_ctx* c)
 {
     if (!c) return;
     drop_events(c);
+    for (cudaGraphExec_t g : {c->g_pre, c->g_push[0], c->g_push[1], c->g_solve, c->g_post[0][0], c->g_post[0][1],
+                              c->g_post[1][0], c->g_post[1][1], c->g_mom[0], c->g_mom[1]})
+        if (g) cudaGraphExecDestroy(g);
+    if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     for (void* p : c->allocs) cudaFree(p);
     delete c;
 }
@@ -262,6 +274,10 @@ pic_status pic_init(const pic_mesh* mesh, const pic_electrodes* el, const pic_ga
     c->step = 0;
     for (int sp = 0; sp < 2; ++sp) c->cap[sp] = std::max<int64_t>(run->capacity[sp], 1);
     c->child_cap = std::max<int64_t>(4096, std::max(c->cap[0], c->cap[1]) / 64);
+    c->sp.scale = rho_scale(c);
+    c->sp.inv_h2 = 1.0 / (mesh->dx * mesh->dx);
+    c->sp.v_dc = el->v_dc; c->sp.v_rf = el->v_rf; c->sp.f_rf = el->f_rf; c->sp.phase = el->phase;
+    c->sp.v_top = el->v_top; c->sp.dt = run->dt;
 
     const bool mixed = c->prec == PIC_MIXED;
     const size_t psz = mixed ? sizeof(float4) : sizeof(double4);
@@ -286,6 +302,11 @@ pic_status pic_init(const pic_mesh* mesh, const pic_electrodes* el, const pic_ga
     if (mixed) c->e32 = (float4*)dev_alloc(c, sizeof(float4) * nodes);
     else c->e64 = (double*)dev_alloc(c, sizeof(double) * 3 * nodes);
     c->d_norm = (double*)dev_alloc(c, 4 * sizeof(double));
+    c->d_step = (uint32_t*)dev_alloc(c, sizeof(uint32_t));
+    c->d_iters = (unsigned int*)dev_alloc(c, sizeof(unsigned int));
+    c->d_res = (double*)dev_alloc(c, sizeof(double));
+    c->d_solve_flag = (int*)dev_alloc(c, sizeof(int));
+    c->d_iter_total = (unsigned long long*)dev_alloc(c, sizeof(unsigned long long));
     c->xs64 = (double*)dev_alloc(c, sizeof(double) * 5 * c->n_xs);
     c->xs32 = (float*)dev_alloc(c, sizeof(float) * 5 * c->n_xs);
     const int ng1 = std::max(c->ng, 1);
@@ -308,6 +329,7 @@ pic_status pic_init(const pic_mesh* mesh, const pic_electrodes* el, const pic_ga
         c->mphi = (double*)dev_alloc(c, sizeof(double) * nodes);
         ok = ok && c->mom[0] && c->mom[1] && c->mphi;
     }
+    ok = ok && c->d_step && c->d_iters && c->d_res && c->d_solve_flag && c->d_iter_total;
     ok = ok && c->d_nslot && c->d_cnt && c->d_err && c->d_nch && c->d_next_id && c->d_child && c->rq && c->phi &&
          c->phi_alt && c->f64 && (c->e32 || c->e64) && c->d_norm && c->xs64 && c->xs32 && c->gpos && c->grad &&
          c->gcell && c->gq && c->gabs && c->gtab && c->gtab32 && c->gq32 && c->goff32 && c->gr2_32 && c->cell_ng &&
@@ -390,6 +412,12 @@ pic_status pic_init(const pic_mesh* mesh, const pic_electrodes* el, const pic_ga
     up(c->cell_g, cell_g.data(), sizeof(int) * cells * kMaxG);
     if (e == cudaSuccess) e = cudaMemset(c->d_cnt, 0, PIC_C_N * sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaMemset(c->d_err, 0, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(c->d_step, 0, sizeof(uint32_t));
+    if (e == cudaSuccess) e = cudaMemset(c->d_iters, 0, sizeof(unsigned int));
+    if (e == cudaSuccess) e = cudaMemset(c->d_res, 0, sizeof(double));
+    if (e == cudaSuccess) e = cudaMemset(c->d_solve_flag, 0, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(c->d_iter_total, 0, sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaMemset(c->d_nch, 0, sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaMemset(c->gabs, 0, sizeof(unsigned long long) * 2 * ng1);
     if (e == cudaSuccess) e = cudaMemset(c->gq, 0, sizeof(double) * ng1);
@@ -461,39 +489,185 @@ pic_status pic_advance(pic_ctx* c)
     if (!c) return PIC_EINVAL;
     const bool mixed = c->prec == PIC_MIXED;
     cudaMemsetAsync(c->rq, 0, sizeof(unsigned long long) * c->nodes, c->stream);
-    if (mixed) {
-        launch_efield32(c);
-        launch_push32(c);
-        launch_children32(c);
-    } else {
-        launch_efield64(c);
-        launch_push64(c);
-        launch_children64(c);
-    }
+    if (mixed) launch_efield32(c);
+    else launch_efield64(c);
+    cudaEvent_t ev = prof_begin(c);
+    if (mixed) launch_push32(c);
+    else launch_push64(c);
+    prof_end(c, ev, true);
+    if (mixed) launch_children32(c);
+    else launch_children64(c);
     launch_grains(c);
     c->step += 1;
     if (c->sort_every > 0 && c->step % c->sort_every == 0) {
         sort_particles(c, 0);
         sort_particles(c, 1);
+        c->parity ^= 1;
     }
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(c, e, "advance launch");
     return PIC_OK;
 }
 
+}  // extern "C"
+
+namespace {
+
+// Capture what `enqueue` queues on c->stream into an executable graph, on the
+// private capture stream; the host-side launch counter and particle buffer
+// pointers are restored, and the graph's kernel count returned in *kernels.
+template <class F>
+cudaGraphExec_t capture(pic_ctx* c, int* kernels, F&& enqueue)
+{
+    cudaStream_t user = c->stream;
+    const int prof = c->prof;
+    const int64_t l0 = c->launches;
+    void* keep[8] = {c->pos[0], c->pos[1], c->vel[0], c->vel[1], c->pos_alt[0], c->pos_alt[1], c->vel_alt[0],
+                     c->vel_alt[1]};
+    c->stream = c->cap_stream;
+    c->prof = 0;
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t ex = nullptr;
+    if (cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+        enqueue();
+        if (cudaStreamEndCapture(c->cap_stream, &g) == cudaSuccess && g) {
+            if (cudaGraphInstantiate(&ex, g, 0) != cudaSuccess) ex = nullptr;
+            cudaGraphDestroy(g);
+        }
+    }
+    *kernels = (int)(c->launches - l0);
+    c->launches = l0;
+    c->stream = user;
+    c->prof = prof;
+    c->pos[0] = (void*)keep[0]; c->pos[1] = keep[1]; c->vel[0] = keep[2]; c->vel[1] = keep[3];
+    c->pos_alt[0] = keep[4]; c->pos_alt[1] = keep[5]; c->vel_alt[0] = keep[6]; c->vel_alt[1] = keep[7];
+    return ex;
+}
+
+// The solve graph: head (rhs, starting residual, first decision) followed by a
+// conditional while node whose body is one refinement iteration.
+cudaGraphExec_t capture_solve(pic_ctx* c)
+{
+    cudaStream_t user = c->stream;
+    const int prof = c->prof;
+    const int64_t l0 = c->launches;
+    c->stream = c->cap_stream;
+    c->prof = 0;
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t ex = nullptr;
+    bool ok = cudaGraphCreate(&g, 0) == cudaSuccess;
+    cudaGraphConditionalHandle h{};
+    ok = ok && cudaGraphConditionalHandleCreate(&h, g, 0, cudaGraphCondAssignDefault) == cudaSuccess;
+    std::vector<cudaGraphNode_t> frontier;
+    if (ok && cudaStreamBeginCaptureToGraph(c->cap_stream, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) ==
+                  cudaSuccess) {
+        enqueue_solve_head(c, c->tol, c->max_cycles, h);
+        cudaStreamCaptureStatus st;
+        const cudaGraphNode_t* deps = nullptr;
+        size_t nd = 0;
+        if (cudaStreamGetCaptureInfo(c->cap_stream, &st, nullptr, nullptr, &deps, nullptr, &nd) == cudaSuccess)
+            frontier.assign(deps, deps + nd);
+        ok = cudaStreamEndCapture(c->cap_stream, &g) == cudaSuccess && !frontier.empty();
+    } else {
+        ok = false;
+    }
+    c->n_solve_head = (int)(c->launches - l0);
+    if (ok) {
+        cudaGraphNodeParams cp{};
+        cp.type = cudaGraphNodeTypeConditional;
+        cp.conditional.handle = h;
+        cp.conditional.type = cudaGraphCondTypeWhile;
+        cp.conditional.size = 1;
+        cudaGraphNode_t cn;
+        ok = cudaGraphAddNode(&cn, g, frontier.data(), nullptr, frontier.size(), &cp) == cudaSuccess;
+        if (ok) {
+            cudaGraph_t body = cp.conditional.phGraph_out[0];
+            const int64_t l1 = c->launches;
+            ok = cudaStreamBeginCaptureToGraph(c->cap_stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) ==
+                 cudaSuccess;
+            if (ok) {
+                enqueue_solve_iteration(c, c->tol, c->max_cycles, h);
+                ok = cudaStreamEndCapture(c->cap_stream, &body) == cudaSuccess;
+            }
+            c->n_solve_body = (int)(c->launches - l1);
+        }
+    }
+    if (ok && cudaGraphInstantiate(&ex, g, 0) != cudaSuccess) ex = nullptr;
+    if (g) cudaGraphDestroy(g);
+    c->launches = l0;
+    c->stream = user;
+    c->prof = prof;
+    return ex;
+}
+
+pic_status ensure_graphs(pic_ctx* c, bool sort)
+{
+    const bool mixed = c->prec == PIC_MIXED;
+    const int p = c->parity, so = sort ? 1 : 0;
+    if (!c->g_pre)
+        c->g_pre = capture(c, &c->n_pre, [&] {
+            cudaMemsetAsync(c->rq, 0, sizeof(unsigned long long) * c->nodes, c->stream);
+            if (mixed) launch_efield32(c);
+            else launch_efield64(c);
+        });
+    if (!c->g_push[p])
+        c->g_push[p] = capture(c, &c->n_push, [&] {
+            if (mixed) launch_push32(c);
+            else launch_push64(c);
+        });
+    if (!c->g_post[p][so])
+        c->g_post[p][so] = capture(c, &c->n_post[so], [&] {
+            if (mixed) launch_children32(c);
+            else launch_children64(c);
+            launch_grains(c);
+            if (sort) {
+                sort_particles(c, 0);
+                sort_particles(c, 1);
+            }
+        });
+    if (!c->g_solve) c->g_solve = capture_solve(c);
+    if ((c->flags & PIC_F_MOMENTS) && !c->g_mom[p])
+        c->g_mom[p] = capture(c, &c->n_mom, [&] {
+            if (mixed) launch_moments32(c);
+            else launch_moments64(c);
+            launch_moments_phi(c);
+        });
+    if (!c->g_pre || !c->g_push[p] || !c->g_post[p][so] || !c->g_solve ||
+        ((c->flags & PIC_F_MOMENTS) && !c->g_mom[p]))
+        return fail(c, PIC_ECUDA, "CUDA graph capture failed");
+    return PIC_OK;
+}
+
+pic_status launch_solve_graph(pic_ctx* c)
+{
+    cudaEvent_t ev = prof_begin(c);
+    const cudaError_t e = cudaGraphLaunch(c->g_solve, c->stream);
+    prof_end(c, ev, false);
+    c->launches += c->n_solve_head;
+    return e == cudaSuccess ? PIC_OK : cuda_fail(c, e, "solve graph launch");
+}
+
+}  // namespace
+
+extern "C" {
+
 pic_status pic_solve(pic_ctx* c, int32_t* iterations, double* rel_residual)
 {
     if (!c) return PIC_EINVAL;
-    int it = 0;
-    double res = 0.0;
-    const pic_status s = solve_now(c, c->tol, &it, &res);
-    if (iterations) *iterations = it;
-    if (rel_residual) *rel_residual = res;
-    const pic_status k = check(c);
+    pic_status k = ensure_graphs(c, false);
     if (k != PIC_OK) return k;
-    if (s == PIC_ENOTCONV) return fail(c, s, "Poisson solve did not reach the tolerance");
-    if (s != PIC_OK) return fail(c, s, "Poisson solve failed");
-    return PIC_OK;
+    k = launch_solve_graph(c);
+    if (k != PIC_OK) return k;
+    unsigned int it = 0;
+    double res = 0.0;
+    const pic_status chk = check(c);
+    cudaMemcpy(&it, c->d_iters, sizeof it, cudaMemcpyDeviceToHost);
+    cudaMemcpy(&res, c->d_res, sizeof res, cudaMemcpyDeviceToHost);
+    if (iterations) *iterations = (int32_t)it;
+    if (rel_residual) *rel_residual = res;
+    c->last_iters = it;
+    c->last_res = res;
+    return chk;
 }
 
 pic_status pic_step(pic_ctx* c, int32_t n_steps)
@@ -505,17 +679,31 @@ pic_status pic_step(pic_ctx* c, int32_t n_steps)
         return fail(c, p, "an earlier solve did not converge");
     }
     for (int32_t s = 0; s < n_steps; ++s) {
-        pic_status r = pic_advance(c);
+        const bool sort = c->sort_every > 0 && (c->step + 1) % c->sort_every == 0;
+        pic_status r = ensure_graphs(c, sort);
         if (r != PIC_OK) return r;
-        int it = 0;
-        double res = 0.0;
-        r = solve_now(c, c->tol, &it, &res);
-        if (r == PIC_ENOTCONV) c->pending = PIC_ENOTCONV;
-        else if (r != PIC_OK) return fail(c, r, "Poisson solve failed");
+        const int p = c->parity;
+        cudaError_t e = cudaGraphLaunch(c->g_pre, c->stream);
+        cudaEvent_t ev = prof_begin(c);
+        if (e == cudaSuccess) e = cudaGraphLaunch(c->g_push[p], c->stream);
+        prof_end(c, ev, true);
+        if (e == cudaSuccess) e = cudaGraphLaunch(c->g_post[p][sort ? 1 : 0], c->stream);
+        if (e != cudaSuccess) return cuda_fail(c, e, "step graph launch");
+        c->launches += c->n_pre + c->n_push + c->n_post[sort ? 1 : 0];
+        c->step += 1;
+        if (sort) {
+            std::swap(c->pos[0], c->pos_alt[0]);
+            std::swap(c->pos[1], c->pos_alt[1]);
+            std::swap(c->vel[0], c->vel_alt[0]);
+            std::swap(c->vel[1], c->vel_alt[1]);
+            c->parity ^= 1;
+        }
+        r = launch_solve_graph(c);
+        if (r != PIC_OK) return r;
         if (c->flags & PIC_F_MOMENTS) {
-            if (c->prec == PIC_MIXED) launch_moments32(c);
-            else launch_moments64(c);
-            launch_moments_phi(c);
+            e = cudaGraphLaunch(c->g_mom[c->parity], c->stream);
+            if (e != cudaSuccess) return cuda_fail(c, e, "moments graph launch");
+            c->launches += c->n_mom;
             c->msteps += 1;
         }
     }
@@ -689,7 +877,9 @@ pic_status pic_profile(pic_ctx* c, int32_t enable)
     if (k != PIC_OK) return k;
     drop_events(c);
     c->prof = enable ? 1 : 0;
-    return PIC_OK;
+    const cudaError_t e = cudaMemcpy(&c->prof_iter0, c->d_iter_total, sizeof(unsigned long long),
+                                     cudaMemcpyDeviceToHost);
+    return e == cudaSuccess ? PIC_OK : cuda_fail(c, e, "iteration counter");
 }
 
 pic_status pic_profile_read(pic_ctx* c, double* push_ms, int64_t* push_launches, double* solve_ms, int64_t* solves,
@@ -709,12 +899,15 @@ pic_status pic_profile_read(pic_ctx* c, double* push_ms, int64_t* push_launches,
         }
         ++idx;
     }
+    unsigned long long tot = 0;
+    const cudaError_t e = cudaMemcpy(&tot, c->d_iter_total, sizeof tot, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(c, e, "iteration counter");
     if (push_ms) *push_ms = t[0];
-    if (push_launches) *push_launches = (int64_t)c->ev_push.size();
+    if (push_launches) *push_launches = (int64_t)c->ev_push.size() * 2;   // one launch per species
     if (solve_ms) *solve_ms = t[1];
     if (solves) *solves = (int64_t)c->ev_solve.size();
-    if (solve_iterations) *solve_iterations = c->prof_iters;
-    if (kernels_launched) *kernels_launched = c->launches;
+    if (solve_iterations) *solve_iterations = (int64_t)(tot - c->prof_iter0);
+    if (kernels_launched) *kernels_launched = c->launches + (int64_t)tot * c->n_solve_body;
     return PIC_OK;
 }
 

@@ -23,7 +23,7 @@ struct P64 {
     int n_xs;
     const double* xs;
     uint2 key;
-    uint32_t step;
+    const uint32_t* step;        // device step counter (Philox counter word 2)
     int flags;
     int ng;
     const double* gpos;
@@ -260,9 +260,9 @@ __device__ void gauss3(RStream& r, double o[3])
 __device__ __forceinline__ void latch(int* err, int code) { atomicCAS(err, 0, code); }
 
 // null-collision MCC after the push (Table I); may record an ionization product
-__device__ void mcc(const P64& p, const double x[3], double v[3], uint32_t id, int cell)
+__device__ void mcc(const P64& p, uint32_t step, const double x[3], double v[3], uint32_t id, int cell)
 {
-    const uint4 u = philox4x32_10(make_uint4(id, p.step, kPurMCC, 0u), p.key);
+    const uint4 u = philox4x32_10(make_uint4(id, step, kPurMCC, 0u), p.key);
     if (u01d(u.x) >= p.pnull) return;
     const double ng = p.n_gas;
     const int nx = p.n_xs;
@@ -275,7 +275,7 @@ __device__ void mcc(const P64& p, const double x[3], double v[3], uint32_t id, i
         const double nu_io = (ng * xs_at(p.xs + 2 * nx, nx, p.de, eps)) * vm;
         const double R = u01d(u.y) * p.nu_max;
         double acc = nu_el;
-        RStream rd(id, p.step, kPurDir, p.key);
+        RStream rd(id, step, kPurDir, p.key);
         double dir[3];
         if (R < acc) {
             iso(rd, dir);
@@ -310,9 +310,9 @@ __device__ void mcc(const P64& p, const double x[3], double v[3], uint32_t id, i
 #pragma unroll
             for (int a = 0; a < 3; ++a) { v[a] = vn * dir[a]; cr.x[a] = x[a]; }
             double d2[3], gn[3];
-            RStream rc(id, p.step, kPurChildDir, p.key);
+            RStream rc(id, step, kPurChildDir, p.key);
             iso(rc, d2);
-            RStream rn(id, p.step, kPurChildNeutral, p.key);
+            RStream rn(id, step, kPurChildNeutral, p.key);
             gauss3(rn, gn);
 #pragma unroll
             for (int a = 0; a < 3; ++a) { cr.ve[a] = vn * d2[a]; cr.vi[a] = p.sig_n * gn[a]; }
@@ -324,7 +324,7 @@ __device__ void mcc(const P64& p, const double x[3], double v[3], uint32_t id, i
         return;
     }
     double gn[3];
-    RStream rn(id, p.step, kPurNeutral, p.key);
+    RStream rn(id, step, kPurNeutral, p.key);
     gauss3(rn, gn);
     const double vn[3] = {p.sig_n * gn[0], p.sig_n * gn[1], p.sig_n * gn[2]};
     const double gv[3] = {v[0] - vn[0], v[1] - vn[1], v[2] - vn[2]};
@@ -337,7 +337,7 @@ __device__ void mcc(const P64& p, const double x[3], double v[3], uint32_t id, i
     double acc = nu_el;
     if (R < acc) {
         double dir[3];
-        RStream rd(id, p.step, kPurDir, p.key);
+        RStream rd(id, step, kPurDir, p.key);
         iso(rd, dir);
 #pragma unroll
         for (int a = 0; a < 3; ++a) v[a] = (v[a] + vn[a]) * 0.5 + (0.5 * gm) * dir[a];
@@ -356,6 +356,7 @@ __global__ void k_push64(const P64 p)
 {
     const Geo g{p.nx, p.ny, p.nz, p.dx, p.Lx, p.Ly, p.Lz};
     const unsigned long long n = p.nslot[p.sp];
+    const uint32_t step = *p.step;
     const bool frozen = (p.sp == 1) && (p.flags & PIC_F_IONS_FROZEN);
     const long long charge = p.sp == 0 ? -1 : 1;
     unsigned int live = 0;
@@ -422,7 +423,7 @@ __global__ void k_push64(const P64 p)
         }
         locate(g, x, c, f);
         const int cell = cell_of(g, c);
-        if (!(p.flags & PIC_F_NO_MCC)) mcc(p, x, v, id, cell);
+        if (!(p.flags & PIC_F_NO_MCC)) mcc(p, step, x, v, id, cell);
         p.pos[q] = make_double4(x[0], x[1], x[2], (double)cell);
         p.vel[q] = make_double4(v[0], v[1], v[2], (double)id);
         qweights(f, w);
@@ -525,8 +526,9 @@ __global__ void k_children64(Geo g, ChildRec* rec, const unsigned long long* nch
 }
 
 __global__ void k_children_finish(unsigned long long* nch, unsigned long long child_cap, unsigned long long* nslot,
-                                  unsigned int* next_id, long long cap_e, long long cap_i)
+                                  unsigned int* next_id, long long cap_e, long long cap_i, uint32_t* step)
 {
+    *step += 1u;   // the step is complete on the particle side
     const unsigned long long n = min(*nch, child_cap);
     nslot[0] = min(nslot[0] + n, (unsigned long long)cap_e);
     nslot[1] = min(nslot[1] + n, (unsigned long long)cap_i);
@@ -638,7 +640,7 @@ void launch_push64(pic_ctx* c)
         p.n_xs = c->n_xs;
         p.xs = c->xs64;
         p.key = c->key;
-        p.step = (uint32_t)c->step;
+        p.step = c->d_step;
         p.flags = c->flags;
         p.ng = c->ng;
         p.gpos = c->gpos; p.grad = c->grad; p.gcell = c->gcell; p.gq = c->gq; p.gtab = c->gtab; p.gabs = c->gabs;
@@ -653,9 +655,7 @@ void launch_push64(pic_ctx* c)
         p.child = c->d_child;
         p.child_cap = (unsigned long long)c->child_cap;
         p.nch = c->d_nch;
-        cudaEvent_t ev = prof_begin(c);
         k_push64<<<grid_for(c->cap[sp], 128, 152 * 16), 128, 0, c->stream>>>(p);
-        prof_end(c, ev, true);
         c->launches += 1;
     }
 }
@@ -667,7 +667,7 @@ void launch_children64(pic_ctx* c)
                                               (double4*)c->pos[0], (double4*)c->vel[0], (double4*)c->pos[1],
                                               (double4*)c->vel[1], c->cap[0], c->cap[1], c->rq, c->d_err);
     k_children_finish<<<1, 1, 0, c->stream>>>(c->d_nch, (unsigned long long)c->child_cap, c->d_nslot, c->d_next_id,
-                                              c->cap[0], c->cap[1]);
+                                              c->cap[0], c->cap[1], c->d_step);
     c->launches += 2;
 }
 

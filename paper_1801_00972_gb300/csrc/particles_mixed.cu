@@ -22,7 +22,7 @@ struct P32 {
     int n_xs;
     const float* xs;
     uint2 key;
-    uint32_t step;
+    const uint32_t* step;        // device step counter (Philox counter word 2)
     const int* gcell;
     const float* goff;           // 3 ng: grain centre offsets in its cell
     const float* gr2;            // ng: (radius/dx)^2
@@ -238,9 +238,9 @@ __device__ void gauss3f(RStream& r, float o[3])
 }
 
 // null-collision MCC in SI single precision (Table I)
-__device__ void mcc(const P32& p, int cell, const float o[3], float vc[3], uint32_t id)
+__device__ void mcc(const P32& p, uint32_t step, int cell, const float o[3], float vc[3], uint32_t id)
 {
-    const uint4 u = philox4x32_10(make_uint4(id, p.step, kPurMCC, 0u), p.key);
+    const uint4 u = philox4x32_10(make_uint4(id, step, kPurMCC, 0u), p.key);
     if (u01f(u.x) >= p.pnull) return;
     float v[3] = {vc[0] * p.vs, vc[1] * p.vs, vc[2] * p.vs};
     const int nx = p.n_xs;
@@ -252,7 +252,7 @@ __device__ void mcc(const P32& p, int cell, const float o[3], float vc[3], uint3
         const float nu_ex = p.n_gas * xs_at(p.xs + nx, nx, p.de, eps) * vm;
         const float nu_io = p.n_gas * xs_at(p.xs + 2 * nx, nx, p.de, eps) * vm;
         const float R = u01f(u.y) * p.nu_max;
-        RStream rd(id, p.step, kPurDir, p.key);
+        RStream rd(id, step, kPurDir, p.key);
         float dir[3];
         if (R < nu_el) {
             isof(rd, dir);
@@ -275,9 +275,9 @@ __device__ void mcc(const P32& p, int cell, const float o[3], float vc[3], uint3
             const float vn = sqrtf(0.5f * e2 / p.hm);
             isof(rd, dir);
             float d2[3], gn[3];
-            RStream rc(id, p.step, kPurChildDir, p.key);
+            RStream rc(id, step, kPurChildDir, p.key);
             isof(rc, d2);
-            RStream rn(id, p.step, kPurChildNeutral, p.key);
+            RStream rn(id, step, kPurChildNeutral, p.key);
             gauss3f(rn, gn);
             ChildRec cr;
             cr.parent = id;
@@ -296,7 +296,7 @@ __device__ void mcc(const P32& p, int cell, const float o[3], float vc[3], uint3
         return;
     }
     float gn[3];
-    RStream rn(id, p.step, kPurNeutral, p.key);
+    RStream rn(id, step, kPurNeutral, p.key);
     gauss3f(rn, gn);
     const float vn[3] = {p.sig_n * gn[0], p.sig_n * gn[1], p.sig_n * gn[2]};
     const float gv[3] = {v[0] - vn[0], v[1] - vn[1], v[2] - vn[2]};
@@ -308,7 +308,7 @@ __device__ void mcc(const P32& p, int cell, const float o[3], float vc[3], uint3
     const float R = u01f(u.y) * p.nu_max;
     if (R < nu_el) {
         float dir[3];
-        RStream rd(id, p.step, kPurDir, p.key);
+        RStream rd(id, step, kPurDir, p.key);
         isof(rd, dir);
         for (int a = 0; a < 3; ++a) vc[a] = ((v[a] + vn[a]) * 0.5f + 0.5f * gm * dir[a]) * p.inv_vs;
         atomicAdd(p.cnt + PIC_C_I_EL, 1ull);
@@ -323,6 +323,7 @@ __device__ void mcc(const P32& p, int cell, const float o[3], float vc[3], uint3
 __global__ void __launch_bounds__(256) k_push32(const P32 p)
 {
     const unsigned long long n = p.nslot[p.sp];
+    const uint32_t step = *p.step;
     const bool frozen = (p.sp == 1) && (p.flags & PIC_F_IONS_FROZEN);
     const long long charge = p.sp == 0 ? -1 : 1;
     unsigned int live = 0;
@@ -380,7 +381,7 @@ __global__ void __launch_bounds__(256) k_push32(const P32 p)
         }
         cell = (k * p.ny + j) * p.nx + i;
         const uint32_t id = __float_as_uint(V.w);
-        if (!(p.flags & PIC_F_NO_MCC)) mcc(p, cell, o, v, id);
+        if (!(p.flags & PIC_F_NO_MCC)) mcc(p, step, cell, o, v, id);
         p.pos[q] = make_float4(o[0], o[1], o[2], __int_as_float(cell));
         p.vel[q] = make_float4(v[0], v[1], v[2], V.w);
         a[0] = qa(o[0]); a[1] = qa(o[1]); a[2] = qa(o[2]);
@@ -473,8 +474,10 @@ __global__ void k_children32(int nx, int ny, ChildRec* rec, const unsigned long 
 }
 
 __global__ void k_children_finish32(unsigned long long* nch, unsigned long long child_cap,
-                                    unsigned long long* nslot, unsigned int* next_id, long long cap_e, long long cap_i)
+                                    unsigned long long* nslot, unsigned int* next_id, long long cap_e, long long cap_i,
+                                    uint32_t* step)
 {
+    *step += 1u;   // the step is complete on the particle side
     const unsigned long long n = min(*nch, child_cap);
     nslot[0] = min(nslot[0] + n, (unsigned long long)cap_e);
     nslot[1] = min(nslot[1] + n, (unsigned long long)cap_i);
@@ -549,7 +552,7 @@ void launch_push32(pic_ctx* c)
         p.n_xs = c->n_xs;
         p.xs = c->xs32;
         p.key = c->key;
-        p.step = (uint32_t)c->step;
+        p.step = c->d_step;
         p.gcell = c->gcell;
         p.goff = c->goff32;
         p.gr2 = c->gr2_32;
@@ -568,9 +571,7 @@ void launch_push32(pic_ctx* c)
         p.child = c->d_child;
         p.child_cap = (unsigned long long)c->child_cap;
         p.nch = c->d_nch;
-        cudaEvent_t ev = prof_begin(c);
         k_push32<<<grid_for(c->cap[sp], 256, 152 * 8), 256, 0, c->stream>>>(p);
-        prof_end(c, ev, true);
         c->launches += 1;
     }
 }
@@ -597,7 +598,7 @@ void launch_children32(pic_ctx* c)
                                               (float4*)c->pos[0], (float4*)c->vel[0], (float4*)c->pos[1],
                                               (float4*)c->vel[1], c->cap[0], c->cap[1], c->rq, c->d_err);
     k_children_finish32<<<1, 1, 0, c->stream>>>(c->d_nch, (unsigned long long)c->child_cap, c->d_nslot,
-                                                c->d_next_id, c->cap[0], c->cap[1]);
+                                                c->d_next_id, c->cap[0], c->cap[1], c->d_step);
     c->launches += 2;
 }
 

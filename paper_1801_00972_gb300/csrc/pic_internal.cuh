@@ -104,6 +104,15 @@ struct RStream {
 };
 
 // ---------------------------------------------------------------- context
+constexpr int kMaxDense = 1024;   // coarsest-level unknowns solved with a dense inverse
+
+// constants of the graph solve's right-hand side and electrode values
+struct SolveParams {
+    double scale;       // rho_q units -> rho / eps0
+    double inv_h2;
+    double v_dc, v_rf, f_rf, phase, v_top, dt;
+};
+
 struct MGLevel {
     int nx, ny, nz;
     double h;
@@ -182,6 +191,22 @@ struct pic_ctx {
 
     // multigrid
     std::vector<pic::MGLevel> mg;
+    void* coarse_inv = nullptr;              // dense inverse of the coarsest level (T)
+    pic::SolveParams sp;
+    unsigned int* d_iters = nullptr;         // graph solve: iterations of the last solve
+    double* d_res = nullptr;                 // graph solve: relative residual of the last solve
+    int* d_solve_flag = nullptr;             // graph solve: PIC_ENOTCONV / PIC_ENONFINITE latch
+    uint32_t* d_step = nullptr;              // device copy of the step counter
+    unsigned long long* d_iter_total = nullptr;  // refinement iterations of all graph solves
+
+    // CUDA graphs of one step, captured lazily on a private stream and
+    // launched on the run's stream; variants by particle-buffer parity
+    cudaStream_t cap_stream = nullptr;
+    int parity = 0;
+    cudaGraphExec_t g_pre = nullptr, g_push[2] = {nullptr, nullptr}, g_solve = nullptr;
+    cudaGraphExec_t g_post[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}}, g_mom[2] = {nullptr, nullptr};
+    int n_pre = 0, n_push = 0, n_post[2] = {0, 0}, n_solve_head = 0, n_solve_body = 0, n_mom = 0;
+    unsigned long long prof_iter0 = 0;
 
     // moments
     double* mom[2] = {nullptr, nullptr};     // 4 * nodes each
@@ -230,6 +255,9 @@ size_t sort_scratch_setup(pic_ctx* c);
 pic_status mg_setup(pic_ctx* c);
 void launch_rhs(pic_ctx* c, double scale, double v_bot, double v_top, bool from_rq);
 pic_status mg_solve(pic_ctx* c, double v_bot, double v_top, double tol, int max_iters, int* iters, double* res);
+// graph solve pieces (enqueued on c->stream during capture)
+void enqueue_solve_head(pic_ctx* c, double tol, int max_iters, cudaGraphConditionalHandle h);
+void enqueue_solve_iteration(pic_ctx* c, double tol, int max_iters, cudaGraphConditionalHandle h);
 
 // api.cu
 void* dev_alloc(pic_ctx* c, size_t bytes);

@@ -14,6 +14,7 @@
 #include <algorithm>
 #include <cmath>
 #include <mutex>
+#include <vector>
 
 #include "pic_internal.cuh"
 
@@ -227,6 +228,84 @@ __global__ void k_rhs(const unsigned long long* __restrict__ rq, double scale, d
     if (threadIdx.x == 0) atomicAdd(norm2, acc);
 }
 
+// coarsest level solved exactly: u = A^-1 f on the interior nodes, with A^-1
+// precomputed on the host for the level (at most kMaxDense unknowns)
+template <typename T>
+__global__ void k_coarse_direct(T* __restrict__ u, const T* __restrict__ f, const T* __restrict__ ainv, Dims d)
+{
+    extern __shared__ unsigned char smem[];
+    T* fi = reinterpret_cast<T*>(smem);
+    const int P = d.nx * d.ny;
+    const int n = P * (d.nz - 1);
+    for (int m = threadIdx.x; m < n; m += blockDim.x) fi[m] = f[P + m];
+    __syncthreads();
+    for (int m = threadIdx.x; m < n; m += blockDim.x) {
+        const T* row = ainv + (size_t)m * n;
+        T acc = (T)0;
+        for (int q = 0; q < n; ++q) acc += row[q] * fi[q];
+        u[P + m] = acc;
+    }
+}
+
+// phi += e on the interior nodes
+template <typename T>
+__global__ void k_add(double* __restrict__ phi, const T* __restrict__ e, Dims d)
+{
+    const size_t P = (size_t)d.nx * d.ny;
+    const size_t lo = P, hi = P * d.nz;
+    for (size_t n = lo + blockIdx.x * (size_t)blockDim.x + threadIdx.x; n < hi; n += (size_t)gridDim.x * blockDim.x)
+        phi[n] += (double)e[n];
+}
+
+// electrode values at t = step * dt from the device step counter
+__device__ __forceinline__ double bottom_potential(const SolveParams& sp, uint32_t step)
+{
+    const double t = (double)step * sp.dt;
+    return sp.v_dc + sp.v_rf * sin((2.0 * kPI * sp.f_rf) * t + sp.phase);
+}
+
+// f = rho_q * scale; electrode values on phi; ||b||^2 added into norm[0]
+__global__ void k_rhs_dev(const unsigned long long* __restrict__ rq, double* __restrict__ f, double* __restrict__ phi,
+                          Dims d, SolveParams sp, const uint32_t* step, double* norm2)
+{
+    const size_t P = (size_t)d.nx * d.ny;
+    const size_t N = P * (d.nz + 1);
+    const double vb = bottom_potential(sp, *step), vt = sp.v_top;
+    double acc = 0.0;
+    for (size_t n = blockIdx.x * (size_t)blockDim.x + threadIdx.x; n < N; n += (size_t)gridDim.x * blockDim.x) {
+        const int k = (int)(n / P);
+        const double fv = (double)(long long)rq[n] * sp.scale;
+        f[n] = fv;
+        if (k == 0) { phi[n] = vb; continue; }
+        if (k == d.nz) { phi[n] = vt; continue; }
+        double b = fv;
+        if (k == 1) b += vb * sp.inv_h2;
+        if (k == d.nz - 1) b += vt * sp.inv_h2;
+        acc += b * b;
+    }
+    acc = block_sum(acc);
+    if (threadIdx.x == 0) atomicAdd(norm2, acc);
+}
+
+// loop control of the graph solve: after each residual, decide whether to run
+// another refinement iteration; record iterations, residual and non-convergence
+__global__ void k_conv(double* norm, unsigned int* iters, double* res_out, int* flag, unsigned long long* total,
+                       double tol2, int max_iters, int first, cudaGraphConditionalHandle h)
+{
+    const double b2 = norm[0], r2 = norm[1];
+    const double target2 = tol2 * (b2 > 0.0 ? b2 : 1.0);
+    unsigned int it = first ? 0u : *iters + 1u;
+    *iters = it;
+    if (!first) *total += 1ull;
+    const bool ok = r2 <= target2;
+    const bool finite = isfinite(r2);
+    const bool more = !ok && finite && (int)it < max_iters;
+    *res_out = b2 > 0.0 ? sqrt(r2 / b2) : sqrt(r2);
+    if (!more && !ok) atomicCAS(flag, 0, finite ? (int)PIC_ENOTCONV : (int)PIC_ENONFINITE);
+    norm[1] = 0.0;
+    cudaGraphSetConditional(h, more ? 1u : 0u);
+}
+
 int blocks(size_t n) { return grid_for((int64_t)n, 256, 152 * 8); }
 
 template <typename T>
@@ -239,9 +318,14 @@ void vcycle(pic_ctx* c, int l)
     T* f = (T*)L.f;
     cudaMemsetAsync(u, 0, sizeof(T) * L.nodes, c->stream);
     if (l + 1 == (int)c->mg.size()) {
-        const int m = std::max(std::max(L.nx, L.ny), L.nz);
-        const int sweeps = std::min(4 * m * m + 16, 2000);
-        k_coarse<T><<<1, 1024, 0, c->stream>>>(u, f, d, h2, sweeps);
+        if (c->coarse_inv) {
+            const int n = L.nx * L.ny * (L.nz - 1);
+            k_coarse_direct<T><<<1, 256, sizeof(T) * n, c->stream>>>(u, f, (const T*)c->coarse_inv, d);
+        } else {
+            const int m = std::max(std::max(L.nx, L.ny), L.nz);
+            const int sweeps = std::min(4 * m * m + 16, 2000);
+            k_coarse<T><<<1, 1024, 0, c->stream>>>(u, f, d, h2, sweeps);
+        }
         c->launches += 1;
         return;
     }
@@ -305,7 +389,51 @@ pic_status solve_t(pic_ctx* c, double tol, int max_iters, int* iters, double* re
     return rn <= target ? PIC_OK : PIC_ENOTCONV;
 }
 
+// One refinement iteration (the body of the graph's while loop):
+// V-cycle on A e = r, phi += e, r = f - A phi, loop decision.
+template <typename T>
+void enqueue_iteration(pic_ctx* c, double tol, int max_iters, cudaGraphConditionalHandle h)
+{
+    const Dims d{c->nx, c->ny, c->nz};
+    vcycle<T>(c, 0);
+    k_add<T><<<blocks(c->nodes), 256, 0, c->stream>>>(c->phi, (const T*)c->mg[0].u, d);
+    k_resid64<T><<<blocks(c->nodes), 256, 0, c->stream>>>(c->phi, (const T*)nullptr, c->f64, nullptr,
+                                                          (T*)c->mg[0].f, c->d_norm + 1, d,
+                                                          1.0 / (c->dx * c->dx));
+    k_conv<<<1, 1, 0, c->stream>>>(c->d_norm, c->d_iters, c->d_res, c->d_solve_flag, c->d_iter_total, tol * tol,
+                                   max_iters, 0, h);
+    c->launches += 3;
+}
+
+// Head of the graph solve: rhs from rho with the electrode values of the
+// device step, the starting residual, and the first loop decision.
+template <typename T>
+void enqueue_head(pic_ctx* c, double tol, int max_iters, cudaGraphConditionalHandle h)
+{
+    const Dims d{c->nx, c->ny, c->nz};
+    cudaMemsetAsync(c->d_norm, 0, 2 * sizeof(double), c->stream);
+    k_rhs_dev<<<blocks(c->nodes), 256, 0, c->stream>>>(c->rq, c->f64, c->phi, d, c->sp, c->d_step, c->d_norm);
+    k_resid64<T><<<blocks(c->nodes), 256, 0, c->stream>>>(c->phi, (const T*)nullptr, c->f64, nullptr,
+                                                          (T*)c->mg[0].f, c->d_norm + 1, d,
+                                                          1.0 / (c->dx * c->dx));
+    k_conv<<<1, 1, 0, c->stream>>>(c->d_norm, c->d_iters, c->d_res, c->d_solve_flag, c->d_iter_total, tol * tol,
+                                   max_iters, 1, h);
+    c->launches += 3;
+}
+
 }  // namespace
+
+void enqueue_solve_head(pic_ctx* c, double tol, int max_iters, cudaGraphConditionalHandle h)
+{
+    if (c->prec == PIC_MIXED) enqueue_head<float>(c, tol, max_iters, h);
+    else enqueue_head<double>(c, tol, max_iters, h);
+}
+
+void enqueue_solve_iteration(pic_ctx* c, double tol, int max_iters, cudaGraphConditionalHandle h)
+{
+    if (c->prec == PIC_MIXED) enqueue_iteration<float>(c, tol, max_iters, h);
+    else enqueue_iteration<double>(c, tol, max_iters, h);
+}
 
 pic_status mg_setup(pic_ctx* c)
 {
@@ -326,6 +454,61 @@ pic_status mg_setup(pic_ctx* c)
                          (nx / 2) % 2 == 0 && (ny / 2) % 2 == 0;
         if (!can) break;
         nx /= 2; ny /= 2; nz /= 2; h *= 2.0;
+    }
+    // exact inverse of the coarsest operator (6 u - neighbour sum) / h^2 with
+    // zero values on the electrode planes, by Gauss-Jordan elimination
+    const MGLevel& L = c->mg.back();
+    const int P = L.nx * L.ny, n = P * (L.nz - 1);
+    c->coarse_inv = nullptr;
+    if (n <= kMaxDense && n > 0) {
+        std::vector<double> a((size_t)n * n, 0.0), inv((size_t)n * n, 0.0);
+        const double ih2 = 1.0 / (L.h * L.h);
+        for (int k = 1; k < L.nz; ++k)
+            for (int j = 0; j < L.ny; ++j)
+                for (int i = 0; i < L.nx; ++i) {
+                    const int m = (k - 1) * P + j * L.nx + i;
+                    a[(size_t)m * n + m] += 6.0 * ih2;
+                    const int nb[6][3] = {{(i + 1) % L.nx, j, k}, {(i + L.nx - 1) % L.nx, j, k},
+                                          {i, (j + 1) % L.ny, k}, {i, (j + L.ny - 1) % L.ny, k},
+                                          {i, j, k + 1}, {i, j, k - 1}};
+                    for (auto& q : nb) {
+                        if (q[2] == 0 || q[2] == L.nz) continue;
+                        a[(size_t)m * n + (q[2] - 1) * P + q[1] * L.nx + q[0]] -= ih2;
+                    }
+                }
+        for (int m = 0; m < n; ++m) inv[(size_t)m * n + m] = 1.0;
+        for (int col = 0; col < n; ++col) {
+            int piv = col;
+            for (int r = col + 1; r < n; ++r)
+                if (std::fabs(a[(size_t)r * n + col]) > std::fabs(a[(size_t)piv * n + col])) piv = r;
+            if (piv != col)
+                for (int q = 0; q < n; ++q) {
+                    std::swap(a[(size_t)piv * n + q], a[(size_t)col * n + q]);
+                    std::swap(inv[(size_t)piv * n + q], inv[(size_t)col * n + q]);
+                }
+            const double dg = a[(size_t)col * n + col];
+            for (int q = 0; q < n; ++q) { a[(size_t)col * n + q] /= dg; inv[(size_t)col * n + q] /= dg; }
+            for (int r = 0; r < n; ++r) {
+                if (r == col) continue;
+                const double fct = a[(size_t)r * n + col];
+                if (fct == 0.0) continue;
+                for (int q = 0; q < n; ++q) {
+                    a[(size_t)r * n + q] -= fct * a[(size_t)col * n + q];
+                    inv[(size_t)r * n + q] -= fct * inv[(size_t)col * n + q];
+                }
+            }
+        }
+        void* d = dev_alloc(c, tsz * (size_t)n * n);
+        if (!d) return PIC_ENOMEM;
+        cudaError_t e;
+        if (c->prec == PIC_MIXED) {
+            std::vector<float> f32(inv.begin(), inv.end());
+            e = cudaMemcpy(d, f32.data(), sizeof(float) * f32.size(), cudaMemcpyHostToDevice);
+        } else {
+            e = cudaMemcpy(d, inv.data(), sizeof(double) * inv.size(), cudaMemcpyHostToDevice);
+        }
+        if (e != cudaSuccess) return PIC_ECUDA;
+        c->coarse_inv = d;
     }
     return PIC_OK;
 }
