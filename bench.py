@@ -30,6 +30,7 @@ sys.path.insert(0, ROOT)
 METRIC = "particle-steps/s and Poisson solves/s, mixed vs FP64, 1 GB300, % HBM roof"
 BYTES_MIXED = 64     # per particle-step: float4 pos + float4 vel, read and written
 BYTES_FP64 = 128     # double4 pos + double4 vel, read and written
+SORT_EVERY = 10      # counting-sort interval (steps)
 
 
 def args():
@@ -43,6 +44,7 @@ def args():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--eager", action="store_true", help="no CUDA graphs (for profilers)")
     return ap.parse_args()
 
 
@@ -108,9 +110,9 @@ class Clocks:
                 "samples": len(sm)}
 
 
-def run_gpu(P, I, wl, parts, prec, steps, warmup, stream, gpu):
+def run_gpu(P, I, wl, parts, prec, steps, warmup, stream, gpu, flags=0):
     import torch
-    run = P.Run(wl, parts, prec=prec, stream=stream, sort_every=20)
+    run = P.Run(wl, parts, prec=prec, stream=stream, sort_every=SORT_EVERY, flags=flags)
     run.step(warmup)
     _, c0 = run.counts()
     run.profile(1)
@@ -145,7 +147,7 @@ def e2e(P, wl, parts, prec, steps, stream):
     import torch
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    run = P.Run(wl, parts, prec=prec, stream=stream, sort_every=20)
+    run = P.Run(wl, parts, prec=prec, stream=stream, sort_every=SORT_EVERY)
     _, c0 = run.counts()
     for _ in range(steps):
         run.step(1)
@@ -233,10 +235,12 @@ def main():
     wl.seed = wl.seed + 1000 * rank
     parts = I.sample_particles(wl)
     stream = torch.cuda.current_stream().cuda_stream
-    mixed = run_gpu(P, I, wl, parts, P.PIC_MIXED, a.steps, a.warmup, stream, local)
+    flags = P.PIC_F_NO_GRAPH if a.eager else 0
+    mixed = run_gpu(P, I, wl, parts, P.PIC_MIXED, a.steps, a.warmup, stream, local, flags)
     fp64 = None
     if not a.no_fp64:
-        fp64 = run_gpu(P, I, wl, parts, P.PIC_FP64, a.fp64_steps or max(a.steps // 4, 10), a.warmup, stream, local)
+        fp64 = run_gpu(P, I, wl, parts, P.PIC_FP64, a.fp64_steps or max(a.steps // 4, 10), a.warmup, stream, local,
+                       flags)
     ee = None if a.no_e2e else e2e(P, wl, parts, P.PIC_MIXED, max(a.steps // 4, 10), stream)
 
     def agg(x):
@@ -279,7 +283,7 @@ def main():
                                f"{wl.n_e + wl.n_i:.0e} macroparticles, 13.56 MHz 100 V, 2 Pa",
                    "parallelism": "replicas only" if world > 1 else "1 GPU",
                    "l2": "inputs larger than L2 (particle arrays 320 MB mixed / 640 MB FP64)",
-                   "sort_every": 20, "tol": 1e-10},
+                   "sort_every": SORT_EVERY, "tol": 1e-10},
         "roofline": {"bound": "hbm", "kernel": "k_push32 (fused gather/push/MD/absorb/MCC/deposit)",
                      "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "peak_kind": peak_kind, "bytes_per_particle_step": BYTES_MIXED, "traffic": None,

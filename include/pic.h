@@ -59,6 +59,9 @@ typedef enum { PIC_FP64 = 0, PIC_MIXED = 1 } pic_precision;
 #define PIC_F_NO_MCC      1   /* no Monte Carlo collisions                       */
 #define PIC_F_IONS_FROZEN 2   /* ions neither move nor collide (test use)        */
 #define PIC_F_MOMENTS     8   /* accumulate node moments after every step        */
+#define PIC_F_NO_GRAPH   16   /* pic_step launches kernels one by one and runs the
+                                 Poisson loop from the host (for profilers that
+                                 cannot see inside CUDA graphs); same results */
 
 /* Mesh: nx*ny*nz cubic cells of edge dx.  Phi and rho live on the cell corners
  * (Sec. III): nx*ny*(nz+1) nodes indexed (k*ny + j)*nx + i; x and y periodic,

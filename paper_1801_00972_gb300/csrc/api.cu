@@ -153,6 +153,9 @@ void destroy(pic_ctx* c)
                               c->g_post[1][0], c->g_post[1][1], c->g_mom[0], c->g_mom[1]})
         if (g) cudaGraphExecDestroy(g);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+    if (c->aux) cudaStreamDestroy(c->aux);
+    if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+    if (c->ev_join) cudaEventDestroy(c->ev_join);
     for (void* p : c->allocs) cudaFree(p);
     delete c;
 }
@@ -206,6 +209,9 @@ pic_status pic_init(const pic_mesh* mesh, const pic_electrodes* el, const pic_ga
         (run->prec != PIC_FP64 && run->prec != PIC_MIXED) || !(run->tol > 0.0) || run->max_cycles < 1)
         return fail(nullptr, PIC_EINVAL, "run: need dt > 0, weight >= 0, md_sub >= 1, sort_every >= 0, prec 0/1, "
                                          "tol > 0, max_cycles >= 1");
+    if (run->prec == PIC_MIXED && (nx > 1024 || ny > 1024 || nz > 2047))
+        return fail(nullptr, PIC_EINVAL, "mesh: mixed precision packs the cell as i | j << 10 | k << 20, so nx, ny "
+                                         "<= 1024 and nz <= 2047");
     const double Lx = nx * mesh->dx, Ly = ny * mesh->dx, Lz = nz * mesh->dx;
     for (int sp = 0; sp < 2; ++sp) {
         if (run->n[sp] < 0 || run->capacity[sp] < run->n[sp] || run->capacity[sp] > 0x7fffffffLL)
@@ -295,6 +301,15 @@ pic_status pic_init(const pic_mesh* mesh, const pic_electrodes* el, const pic_ga
     c->d_nch = (unsigned long long*)dev_alloc(c, sizeof(unsigned long long));
     c->d_next_id = (unsigned int*)dev_alloc(c, sizeof(unsigned int));
     c->d_child = (ChildRec*)dev_alloc(c, sizeof(ChildRec) * c->child_cap);
+    if (mixed) {
+        for (int sp = 0; sp < 2; ++sp) {
+            c->md_list[sp] = (unsigned int*)dev_alloc(c, sizeof(unsigned int) * c->cap[sp]);
+            c->mcc_list[sp] = (unsigned int*)dev_alloc(c, sizeof(unsigned int) * c->cap[sp]);
+            ok = ok && c->md_list[sp] && c->mcc_list[sp];
+        }
+        c->d_lists = (unsigned int*)dev_alloc(c, 4 * sizeof(unsigned int));
+        ok = ok && c->d_lists;
+    }
     c->rq = (unsigned long long*)dev_alloc(c, sizeof(unsigned long long) * nodes);
     c->phi = (double*)dev_alloc(c, sizeof(double) * nodes);
     c->phi_alt = (double*)dev_alloc(c, sizeof(double) * nodes);
@@ -358,7 +373,7 @@ pic_status pic_init(const pic_mesh* mesh, const pic_electrodes* el, const pic_ga
             double f[3];
             const int nn[3] = {nx, ny, nz};
             for (int a = 0; a < 3; ++a) locate1(x[a], mesh->dx, nn[a], ci[a], f[a]);
-            const int cell = (ci[2] * ny + ci[1]) * nx + ci[0];
+            const int cell = mixed ? (ci[0] | (ci[1] << 10) | (ci[2] << 20)) : (ci[2] * ny + ci[1]) * nx + ci[0];
             if (mixed) {
                 float4 p, w;
                 float o[3];
@@ -418,6 +433,9 @@ pic_status pic_init(const pic_mesh* mesh, const pic_electrodes* el, const pic_ga
     if (e == cudaSuccess) e = cudaMemset(c->d_solve_flag, 0, sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(c->d_iter_total, 0, sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->aux, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaMemset(c->d_nch, 0, sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaMemset(c->gabs, 0, sizeof(unsigned long long) * 2 * ng1);
     if (e == cudaSuccess) e = cudaMemset(c->gq, 0, sizeof(double) * ng1);
@@ -464,7 +482,10 @@ pic_status pic_init(const pic_mesh* mesh, const pic_electrodes* el, const pic_ga
         if (e != cudaSuccess) { destroy(c); return cuda_fail(nullptr, e, "grain tables"); }
     }
 
-    // ---- rho_0 and phi_0
+    // ---- cell order for the first steps, then rho_0 and phi_0
+    sort_particles(c, 0);
+    sort_particles(c, 1);
+    c->parity ^= 1;
     cudaMemsetAsync(c->rq, 0, sizeof(unsigned long long) * nodes, c->stream);
     deposit_particles(c);
     launch_grains(c);
@@ -678,6 +699,24 @@ pic_status pic_step(pic_ctx* c, int32_t n_steps)
         c->pending = PIC_OK;
         return fail(c, p, "an earlier solve did not converge");
     }
+    if (c->flags & PIC_F_NO_GRAPH) {
+        for (int32_t s = 0; s < n_steps; ++s) {
+            pic_status r = pic_advance(c);
+            if (r != PIC_OK) return r;
+            int it = 0;
+            double res = 0.0;
+            r = solve_now(c, c->tol, &it, &res);
+            if (r == PIC_ENOTCONV) c->pending = PIC_ENOTCONV;
+            else if (r != PIC_OK) return fail(c, r, "Poisson solve failed");
+            if (c->flags & PIC_F_MOMENTS) {
+                if (c->prec == PIC_MIXED) launch_moments32(c);
+                else launch_moments64(c);
+                launch_moments_phi(c);
+                c->msteps += 1;
+            }
+        }
+        return check(c);
+    }
     for (int32_t s = 0; s < n_steps; ++s) {
         const bool sort = c->sort_every > 0 && (c->step + 1) % c->sort_every == 0;
         pic_status r = ensure_graphs(c, sort);
@@ -741,7 +780,7 @@ pic_status fetch(pic_ctx* c, int sp, std::vector<double>& x, std::vector<double>
             int cell;
             std::memcpy(&cell, &P[q].w, 4);
             if (cell < 0) continue;
-            const int i = cell % c->nx, j = (cell / c->nx) % c->ny, k = cell / (c->nx * c->ny);
+            const int i = cell & 1023, j = (cell >> 10) & 1023, k = cell >> 20;
             x.push_back((i + (double)P[q].x) * c->dx);
             x.push_back((j + (double)P[q].y) * c->dx);
             x.push_back((k + (double)P[q].z) * c->dx);

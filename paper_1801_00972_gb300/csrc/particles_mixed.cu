@@ -2,16 +2,38 @@
 // (gather of -grad phi, Eqs. 1-2 leapfrog, MD subcycling with Eqs. 5-6 near
 // grains, absorption, null-collision MCC of Table I, fixed-point CIC deposit)
 // on a compact layout:
-//   pos float4 {ox, oy, oz, cell}: in-cell offsets in [0,1) and the linear cell
-//       index (int bits; -1 = dead slot), so positions keep ~6e-8 cell
-//       resolution anywhere in the box;
+//   pos float4 {ox, oy, oz, cell}: in-cell offsets in [0,1) and the packed cell
+//       (i | j << 10 | k << 20 as int bits; -1 = dead slot), so positions keep
+//       ~6e-8 cell resolution anywhere in the box;
 //   vel float4 {vx, vy, vz, id}: velocity in cells per step, particle id bits.
 // The push works in cell units: v += (q/m) E dt^2/dx, offset += v, with the
-// integer part carried into the cell index.  Collisions convert to SI.
+// integer part carried into the cell.  Collisions convert to SI.
+//
+// One step runs three kernels per species:
+//   k_push32  every particle outside the MD regions: gather, push, electrode
+//             loss, the null-collision test, deposit.  Deposits are summed in a
+//             shared-memory window of nodes per block and flushed with one
+//             global atomic per touched node.  Particles in MD cells and
+//             collision candidates are appended to lists.
+//   k_md32    the MD-region particles: Dt/40 substeps with the PPPM correction,
+//             grain absorption, MCC, deposit.
+//   k_mcc32   the collision candidates: process selection and kinematics.
+#include <climits>
+
 #include "pic_internal.cuh"
 
 namespace pic {
 namespace {
+
+constexpr int kPushThreads = 256;
+constexpr int kPPT = 2;                          // particles per thread per chunk
+constexpr int kChunk = kPushThreads * kPPT;      // particles per block per chunk
+// deposit window per block: 4 planes (offsets -1..+2 from the anchor particle's
+// plane), each +-kWinR nodes around the anchor's node column; a fixed-point
+// weight w <= 2^42 is summed as two 21-bit halves in 32-bit shared counters
+// (a chunk adds at most kChunk * 2^21 < 2^32 to a slot)
+constexpr int kWinR = 256;
+constexpr int kWinN = 4 * 2 * kWinR;
 
 struct P32 {
     int nx, ny, nz, nxy;
@@ -41,76 +63,119 @@ struct P32 {
     ChildRec* child;
     unsigned long long child_cap;
     unsigned long long* nch;
+    unsigned int* md_list;
+    unsigned int* md_n;
+    unsigned int* mcc_list;
+    unsigned int* mcc_n;
 };
+
+enum Event : int { kEvNone = 0, kEvEEl, kEvEExc, kEvEIon, kEvIEl, kEvICx };
 
 __device__ __forceinline__ void latch(int* err, int code) { atomicCAS(err, 0, code); }
 
+__device__ __forceinline__ int pack(int i, int j, int k) { return i | (j << 10) | (k << 20); }
+__device__ __forceinline__ void unpack(int c, int& i, int& j, int& k)
+{
+    i = c & 1023;
+    j = (c >> 10) & 1023;
+    k = c >> 20;
+}
+
 __device__ __forceinline__ int qa(float o)
 {
-    int a = __float2int_rn(o * (float)kWQ);
+    const int a = __float2int_rn(o * (float)kWQ);
     return min(max(a, 0), kWQ);
 }
 
-__device__ __forceinline__ void split(int cell, int nx, int ny, int& i, int& j, int& k)
+// add `pred` lanes of the active threads of this warp to *ctr with one atomic
+__device__ __forceinline__ void warp_count(unsigned long long* ctr, bool pred)
 {
-    i = cell % nx;
-    const int t = cell / nx;
-    j = t % ny;
-    k = t / ny;
+    const unsigned act = __activemask();
+    const unsigned m = __ballot_sync(act, pred);
+    if (m && (threadIdx.x & 31) == __ffs(act) - 1) atomicAdd(ctr, (unsigned long long)__popc(m));
+}
+
+// append q to a list with one atomic per warp
+__device__ __forceinline__ void warp_append(unsigned int* list, unsigned int* n, unsigned int q, bool pred)
+{
+    const unsigned act = __activemask();
+    const unsigned m = __ballot_sync(act, pred);
+    if (!m) return;
+    const int lane = threadIdx.x & 31;
+    const int leader = __ffs(m) - 1;
+    unsigned int base = 0;
+    if (lane == leader) base = atomicAdd(n, (unsigned int)__popc(m));
+    base = __shfl_sync(act, base, leader);
+    if (pred) list[base + __popc(m & ((1u << lane) - 1u))] = q;
 }
 
 // CIC gather of the node field with the fixed-point weights a/2^14 per axis
-__device__ __forceinline__ void gather(const float4* __restrict__ E, int nx, int nxy, int i, int j, int k,
+__device__ __forceinline__ void gather(const float4* __restrict__ E, int nx, int ny, int i, int j, int k,
                                        const int a[3], float out[3])
 {
     const float s = 1.0f / (float)kWQ;
-    const float wx[2] = {(float)(kWQ - a[0]) * s, (float)a[0] * s};
-    const float wy[2] = {(float)(kWQ - a[1]) * s, (float)a[1] * s};
-    const float wz[2] = {(float)(kWQ - a[2]) * s, (float)a[2] * s};
+    const float wx0 = (float)(kWQ - a[0]) * s, wx1 = (float)a[0] * s;
+    const float wy0 = (float)(kWQ - a[1]) * s, wy1 = (float)a[1] * s;
+    const float wz0 = (float)(kWQ - a[2]) * s, wz1 = (float)a[2] * s;
     const int i1 = (i + 1 == nx) ? 0 : i + 1;
-    const int ny = nxy / nx;
     const int j1 = (j + 1 == ny) ? 0 : j + 1;
-    const size_t b0 = (size_t)k * nxy, b1 = b0 + nxy;
-    const size_t r00 = b0 + (size_t)j * nx, r01 = b0 + (size_t)j1 * nx, r10 = b1 + (size_t)j * nx,
-                 r11 = b1 + (size_t)j1 * nx;
+    const int nxy = nx * ny;
+    const int b0 = k * nxy, b1 = b0 + nxy;
+    const int r00 = b0 + j * nx, r01 = b0 + j1 * nx, r10 = b1 + j * nx, r11 = b1 + j1 * nx;
     const float4 e000 = __ldg(E + r00 + i), e001 = __ldg(E + r00 + i1);
     const float4 e010 = __ldg(E + r01 + i), e011 = __ldg(E + r01 + i1);
     const float4 e100 = __ldg(E + r10 + i), e101 = __ldg(E + r10 + i1);
     const float4 e110 = __ldg(E + r11 + i), e111 = __ldg(E + r11 + i1);
-    const float w00 = wy[0] * wz[0], w01 = wy[1] * wz[0], w10 = wy[0] * wz[1], w11 = wy[1] * wz[1];
-    out[0] = w00 * (wx[0] * e000.x + wx[1] * e001.x) + w01 * (wx[0] * e010.x + wx[1] * e011.x) +
-             w10 * (wx[0] * e100.x + wx[1] * e101.x) + w11 * (wx[0] * e110.x + wx[1] * e111.x);
-    out[1] = w00 * (wx[0] * e000.y + wx[1] * e001.y) + w01 * (wx[0] * e010.y + wx[1] * e011.y) +
-             w10 * (wx[0] * e100.y + wx[1] * e101.y) + w11 * (wx[0] * e110.y + wx[1] * e111.y);
-    out[2] = w00 * (wx[0] * e000.z + wx[1] * e001.z) + w01 * (wx[0] * e010.z + wx[1] * e011.z) +
-             w10 * (wx[0] * e100.z + wx[1] * e101.z) + w11 * (wx[0] * e110.z + wx[1] * e111.z);
+    const float w00 = wy0 * wz0, w01 = wy1 * wz0, w10 = wy0 * wz1, w11 = wy1 * wz1;
+    out[0] = w00 * (wx0 * e000.x + wx1 * e001.x) + w01 * (wx0 * e010.x + wx1 * e011.x) +
+             w10 * (wx0 * e100.x + wx1 * e101.x) + w11 * (wx0 * e110.x + wx1 * e111.x);
+    out[1] = w00 * (wx0 * e000.y + wx1 * e001.y) + w01 * (wx0 * e010.y + wx1 * e011.y) +
+             w10 * (wx0 * e100.y + wx1 * e101.y) + w11 * (wx0 * e110.y + wx1 * e111.y);
+    out[2] = w00 * (wx0 * e000.z + wx1 * e001.z) + w01 * (wx0 * e010.z + wx1 * e011.z) +
+             w10 * (wx0 * e100.z + wx1 * e101.z) + w11 * (wx0 * e110.z + wx1 * e111.z);
 }
 
-__device__ __forceinline__ void deposit(unsigned long long* rq, int nx, int nxy, int i, int j, int k, const int a[3],
-                                        long long charge)
+// the 8 corner nodes and fixed-point weights of a particle
+__device__ __forceinline__ void corners(int nx, int ny, int i, int j, int k, const int a[3], long long charge,
+                                        int node[8], long long val[8])
 {
-    const long long wx[2] = {kWQ - a[0], a[0]}, wy[2] = {kWQ - a[1], a[1]}, wz[2] = {kWQ - a[2], a[2]};
-    const int ny = nxy / nx;
-    const int ii[2] = {i, (i + 1 == nx) ? 0 : i + 1};
-    const int jj[2] = {j, (j + 1 == ny) ? 0 : j + 1};
+    const int i1 = (i + 1 == nx) ? 0 : i + 1;
+    const int j1 = (j + 1 == ny) ? 0 : j + 1;
+    const int nxy = nx * ny;
+    const int r0 = k * nxy + j * nx, r1 = k * nxy + j1 * nx;
+    const int wx[2] = {kWQ - a[0], a[0]}, wy[2] = {kWQ - a[1], a[1]};
+    const long long wz[2] = {charge * (kWQ - a[2]), charge * a[2]};
+    const int ii[2] = {i, i1};
+    const int rr[2] = {r0, r1};
 #pragma unroll
     for (int dz = 0; dz < 2; ++dz)
 #pragma unroll
         for (int dy = 0; dy < 2; ++dy)
 #pragma unroll
             for (int di = 0; di < 2; ++di) {
-                const long long v = charge * (wx[di] * wy[dy] * wz[dz]);
-                if (v != 0)
-                    atomicAdd(rq + (size_t)(k + dz) * nxy + (size_t)jj[dy] * nx + ii[di], (unsigned long long)v);
+                const int c = dz * 4 + dy * 2 + di;
+                node[c] = rr[dy] + dz * nxy + ii[di];
+                val[c] = (long long)(wx[di] * wy[dy]) * wz[dz];
             }
+}
+
+__device__ __forceinline__ void deposit_global(unsigned long long* rq, int nx, int ny, int i, int j, int k,
+                                               const int a[3], long long charge)
+{
+    int node[8];
+    long long val[8];
+    corners(nx, ny, i, j, k, a, charge, node, val);
+#pragma unroll
+    for (int c = 0; c < 8; ++c)
+        if (val[c] != 0) atomicAdd(rq + node[c], (unsigned long long)val[c]);
 }
 
 // carry whole cells out of the offsets; 0 alive, 1/2 lost at the bottom/top
 // electrode, 3 invalid (non-finite or more than one box length in a step)
-__device__ __forceinline__ int carry(const P32& p, int& i, int& j, int& k, float o[3])
+__device__ __forceinline__ int carry(int nx, int ny, int nz, int& i, int& j, int& k, float o[3])
 {
     int c[3] = {i, j, k};
-    const int n[3] = {p.nx, p.ny, p.nz};
+    const int n[3] = {nx, ny, nz};
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         if (!(fabsf(o[a]) < 1e6f)) return 3;
@@ -126,7 +191,7 @@ __device__ __forceinline__ int carry(const P32& p, int& i, int& j, int& k, float
         c[a] = cc;
     }
     if (c[2] < 0) return 1;
-    if (c[2] >= p.nz) return 2;
+    if (c[2] >= nz) return 2;
     i = c[0]; j = c[1]; k = c[2];
     return 0;
 }
@@ -141,54 +206,6 @@ __device__ __forceinline__ void grain_sep(const P32& p, int gi, int i, int j, in
     d[0] = (float)di + (o[0] - p.goff[3 * gi]);
     d[1] = (float)dj + (o[1] - p.goff[3 * gi + 1]);
     d[2] = (float)dk + (o[2] - p.goff[3 * gi + 2]);
-}
-
-// Eqs. 5-6: replace each near grain's mesh field by its Coulomb field
-__device__ void md_correct(const P32& p, int i, int j, int k, const float o[3], const int a[3], float E[3])
-{
-    const int cell = (k * p.ny + j) * p.nx + i;
-    const int n = p.cell_ng[cell];
-    const float s = 1.0f / (float)kWQ;
-    const float wx[2] = {(float)(kWQ - a[0]) * s, (float)a[0] * s};
-    const float wy[2] = {(float)(kWQ - a[1]) * s, (float)a[1] * s};
-    const float wz[2] = {(float)(kWQ - a[2]) * s, (float)a[2] * s};
-    for (int t = 0; t < n; ++t) {
-        const int gi = p.cell_g[cell * kMaxG + t];
-        const int gc0 = p.gcell[3 * gi], gc1 = p.gcell[3 * gi + 1], gc2 = p.gcell[3 * gi + 2];
-        float Ed[3] = {0.f, 0.f, 0.f};
-        for (int dz = 0; dz < 2; ++dz)
-            for (int dy = 0; dy < 2; ++dy)
-                for (int di = 0; di < 2; ++di) {
-                    const float wt = wx[di] * wy[dy] * wz[dz];
-                    const int li = ((i + di - gc0 + 1) % p.nx + p.nx) % p.nx;
-                    const int lj = ((j + dy - gc1 + 1) % p.ny + p.ny) % p.ny;
-                    const int lk = k + dz - gc2 + 1;
-                    const float* tv = p.gtab + ((size_t)gi * 64 + (lk * 4 + lj) * 4 + li) * 3;
-                    Ed[0] += wt * tv[0];
-                    Ed[1] += wt * tv[1];
-                    Ed[2] += wt * tv[2];
-                }
-        float d[3];
-        grain_sep(p, gi, i, j, k, o, d);
-        const float r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
-        const float Q = p.gq[gi];
-        const float coef = r2 > 0.f ? (Q * p.qk) / (r2 * sqrtf(r2)) : 0.f;
-#pragma unroll
-        for (int c = 0; c < 3; ++c) E[c] = (E[c] - Q * Ed[c]) + coef * d[c];
-    }
-}
-
-__device__ int absorbed_by(const P32& p, int i, int j, int k, const float o[3])
-{
-    const int cell = (k * p.ny + j) * p.nx + i;
-    const int n = p.cell_ng[cell];
-    for (int t = 0; t < n; ++t) {
-        const int gi = p.cell_g[cell * kMaxG + t];
-        float d[3];
-        grain_sep(p, gi, i, j, k, o, d);
-        if (d[0] * d[0] + d[1] * d[1] + d[2] * d[2] <= p.gr2[gi]) return gi;
-    }
-    return -1;
 }
 
 __device__ __forceinline__ float xs_at(const float* tab, int n, float de, float eps)
@@ -237,11 +254,10 @@ __device__ void gauss3f(RStream& r, float o[3])
     while (got < 3) o[got++] = 0.f;
 }
 
-// null-collision MCC in SI single precision (Table I)
-__device__ void mcc(const P32& p, uint32_t step, int cell, const float o[3], float vc[3], uint32_t id)
+// process selection and kinematics of a collision candidate (Table I), in SI
+// single precision; u = the candidate's Philox draw (u.y picks the process)
+__device__ int collide(const P32& p, uint32_t step, uint4 u, int cell, const float o[3], float vc[3], uint32_t id)
 {
-    const uint4 u = philox4x32_10(make_uint4(id, step, kPurMCC, 0u), p.key);
-    if (u01f(u.x) >= p.pnull) return;
     float v[3] = {vc[0] * p.vs, vc[1] * p.vs, vc[2] * p.vs};
     const int nx = p.n_xs;
     if (p.sp == 0) {
@@ -259,16 +275,14 @@ __device__ void mcc(const P32& p, uint32_t step, int cell, const float o[3], flo
             const float cosx = (dir[0] * v[0] + dir[1] * v[1] + dir[2] * v[2]) / vm;
             const float vn = vm * sqrtf(1.0f - p.mr2 * (1.0f - cosx));
             for (int a = 0; a < 3; ++a) vc[a] = vn * dir[a] * p.inv_vs;
-            atomicAdd(p.cnt + PIC_C_E_EL, 1ull);
-            return;
+            return kEvEEl;
         }
         if (R < nu_el + nu_ex) {
             const float e2 = fmaxf(eps - p.eps_exc, 0.f);
             isof(rd, dir);
             const float vn = sqrtf(e2 / p.hm);
             for (int a = 0; a < 3; ++a) vc[a] = vn * dir[a] * p.inv_vs;
-            atomicAdd(p.cnt + PIC_C_E_EXC, 1ull);
-            return;
+            return kEvEExc;
         }
         if (R < nu_el + nu_ex + nu_io) {
             const float e2 = fmaxf(eps - p.eps_ion, 0.f);
@@ -291,9 +305,9 @@ __device__ void mcc(const P32& p, uint32_t step, int cell, const float o[3], flo
             const unsigned long long slot = atomicAdd(p.nch, 1ull);
             if (slot < p.child_cap) p.child[slot] = cr;
             else latch(p.err, kErrCapacity);
-            atomicAdd(p.cnt + PIC_C_E_ION, 1ull);
+            return kEvEIon;
         }
-        return;
+        return kEvNone;
     }
     float gn[3];
     RStream rn(id, step, kPurNeutral, p.key);
@@ -311,60 +325,250 @@ __device__ void mcc(const P32& p, uint32_t step, int cell, const float o[3], flo
         RStream rd(id, step, kPurDir, p.key);
         isof(rd, dir);
         for (int a = 0; a < 3; ++a) vc[a] = ((v[a] + vn[a]) * 0.5f + 0.5f * gm * dir[a]) * p.inv_vs;
-        atomicAdd(p.cnt + PIC_C_I_EL, 1ull);
-        return;
+        return kEvIEl;
     }
     if (R < nu_el + nu_cx) {
         for (int a = 0; a < 3; ++a) vc[a] = vn[a] * p.inv_vs;
-        atomicAdd(p.cnt + PIC_C_I_CX, 1ull);
+        return kEvICx;
     }
+    return kEvNone;
 }
 
-__global__ void __launch_bounds__(256) k_push32(const P32 p)
+__device__ __forceinline__ void count_event(const P32& p, int ev)
 {
+    const int slot = ev == kEvEEl ? PIC_C_E_EL : ev == kEvEExc ? PIC_C_E_EXC : ev == kEvEIon ? PIC_C_E_ION
+                   : ev == kEvIEl ? PIC_C_I_EL : PIC_C_I_CX;
+    if (ev != kEvNone) atomicAdd(p.cnt + slot, 1ull);
+}
+
+__global__ void __launch_bounds__(kPushThreads) k_push32(const P32 p)
+{
+    __shared__ unsigned int win_hi[kWinN], win_lo[kWinN];
+    __shared__ unsigned long long s_anchor;
     const unsigned long long n = p.nslot[p.sp];
     const uint32_t step = *p.step;
     const bool frozen = (p.sp == 1) && (p.flags & PIC_F_IONS_FROZEN);
+    const bool no_mcc = p.flags & PIC_F_NO_MCC;
     const long long charge = p.sp == 0 ? -1 : 1;
+    const int nx = p.nx, ny = p.ny, nz = p.nz, nxy = p.nxy;
+    for (int t = threadIdx.x; t < kWinN; t += blockDim.x) { win_hi[t] = 0u; win_lo[t] = 0u; }
+    if (threadIdx.x == 0) s_anchor = 0ull;
+    __syncthreads();
     unsigned int live = 0;
-    for (unsigned long long q = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; q < n;
-         q += (unsigned long long)gridDim.x * blockDim.x) {
-        const float4 P = p.pos[q];
-        int cell = __float_as_int(P.w);
-        if (cell < 0) continue;
-        ++live;
-        int i, j, k;
-        split(cell, p.nx, p.ny, i, j, k);
-        float o[3] = {P.x, P.y, P.z};
-        int a[3];
-        if (frozen) {
-            a[0] = qa(o[0]); a[1] = qa(o[1]); a[2] = qa(o[2]);
-            deposit(p.rq, p.nx, p.nxy, i, j, k, a, charge);
-            continue;
+    for (unsigned long long c0 = (unsigned long long)blockIdx.x * kChunk; c0 < n;
+         c0 += (unsigned long long)gridDim.x * kChunk) {
+        int dcell[kPPT];                 // packed cell of each deposit (-1: none)
+        int da[kPPT][3];
+#pragma unroll
+        for (int u = 0; u < kPPT; ++u) {
+            dcell[u] = -1;
+            const unsigned long long q = c0 + (unsigned long long)u * kPushThreads + threadIdx.x;
+            int lost = 0;
+            bool md = false, cand = false;
+            if (q < n) {
+                const float4 P = p.pos[q];
+                int cell = __float_as_int(P.w);
+                if (cell >= 0) {
+                    ++live;
+                    int i, j, k;
+                    unpack(cell, i, j, k);
+                    float o[3] = {P.x, P.y, P.z};
+                    if (frozen) {
+                        dcell[u] = cell;
+                        da[u][0] = qa(o[0]); da[u][1] = qa(o[1]); da[u][2] = qa(o[2]);
+                    } else if (p.cell_ng[(k * ny + j) * nx + i] != 0) {
+                        md = true;
+                    } else {
+                        const float4 V = p.vel[q];
+                        float v[3] = {V.x, V.y, V.z};
+                        int a[3] = {qa(o[0]), qa(o[1]), qa(o[2])};
+                        float E[3];
+                        gather(p.E, nx, ny, i, j, k, a, E);
+                        v[0] += E[0] * p.kq; v[1] += E[1] * p.kq; v[2] += E[2] * p.kq;
+                        o[0] += v[0]; o[1] += v[1]; o[2] += v[2];
+                        lost = carry(nx, ny, nz, i, j, k, o);
+                        if (lost) {
+                            p.pos[q].w = __int_as_float(-1);
+                        } else {
+                            if (!no_mcc) {
+                                const uint4 r = philox4x32_10(make_uint4(__float_as_uint(V.w), step, kPurMCC, 0u),
+                                                              p.key);
+                                cand = u01f(r.x) < p.pnull;
+                            }
+                            cell = pack(i, j, k);
+                            p.pos[q] = make_float4(o[0], o[1], o[2], __int_as_float(cell));
+                            p.vel[q] = make_float4(v[0], v[1], v[2], V.w);
+                            dcell[u] = cell;
+                            da[u][0] = qa(o[0]); da[u][1] = qa(o[1]); da[u][2] = qa(o[2]);
+                        }
+                    }
+                }
+            }
+            warp_append(p.md_list, p.md_n, (unsigned int)q, md);
+            warp_append(p.mcc_list, p.mcc_n, (unsigned int)q, cand);
+            warp_count(p.cnt + (p.sp == 0 ? PIC_C_LOST_BOT_E : PIC_C_LOST_BOT_I), lost == 1);
+            warp_count(p.cnt + (p.sp == 0 ? PIC_C_LOST_TOP_E : PIC_C_LOST_TOP_I), lost == 2);
+            if (__any_sync(__activemask(), lost == 3)) {
+                warp_count(p.cnt + PIC_C_ERR, lost == 3);
+                if (lost == 3) latch(p.err, kErrNonFinite);
+            }
         }
+        // anchor of the window: a deposit from the middle half of the chunk if there is one
+        {
+            unsigned long long key = 0ull;
+#pragma unroll
+            for (int u = 0; u < kPPT; ++u)
+                if (dcell[u] >= 0) {
+                    const int slot = u * kPushThreads + threadIdx.x;
+                    const unsigned long long prio = (slot >= kChunk / 4 && slot < 3 * kChunk / 4) ? 2ull : 1ull;
+                    const unsigned long long kk = (prio << 32) | (unsigned int)dcell[u];
+                    key = kk > key ? kk : key;
+                }
+            for (int o = 16; o > 0; o >>= 1) {
+                const unsigned long long y = __shfl_xor_sync(0xffffffffu, key, o);
+                key = y > key ? y : key;
+            }
+            if ((threadIdx.x & 31) == 0 && key) atomicMax(&s_anchor, key);
+        }
+        __syncthreads();
+        const unsigned long long ak = s_anchor;
+        int ai = 0, aj = 0, akk = 0;
+        unpack((int)(unsigned int)ak, ai, aj, akk);
+        const int anchor = (akk * ny + aj) * nx + ai;
+        if (ak) {
+#pragma unroll
+            for (int u = 0; u < kPPT; ++u) {
+                if (dcell[u] < 0) continue;
+                int i, j, k;
+                unpack(dcell[u], i, j, k);
+                int node[8];
+                long long val[8];
+                corners(nx, ny, i, j, k, da[u], 1, node, val);
+#pragma unroll
+                for (int c = 0; c < 8; ++c) {
+                    if (val[c] == 0) continue;
+                    const int pl = k + (c >> 2) - akk;               // plane offset from the anchor
+                    const int w = node[c] - anchor - pl * nxy + kWinR;
+                    if (pl >= -1 && pl <= 2 && w >= 0 && w < 2 * kWinR) {
+                        const int slot = (pl + 1) * 2 * kWinR + w;
+                        atomicAdd(win_hi + slot, (unsigned int)(val[c] >> 21));
+                        atomicAdd(win_lo + slot, (unsigned int)(val[c] & 0x1FFFFF));
+                    } else {
+                        atomicAdd(p.rq + node[c], (unsigned long long)(charge * val[c]));
+                    }
+                }
+            }
+        }
+        __syncthreads();
+        if (ak) {
+            for (int t = threadIdx.x; t < kWinN; t += blockDim.x) {
+                const unsigned int hi = win_hi[t], lo = win_lo[t];
+                if (hi | lo) {
+                    const long long v = (((long long)hi << 21) + (long long)lo) * charge;
+                    const int pl = t / (2 * kWinR) - 1, w = t % (2 * kWinR);
+                    atomicAdd(p.rq + (anchor + pl * nxy + w - kWinR), (unsigned long long)v);
+                    win_hi[t] = 0u;
+                    win_lo[t] = 0u;
+                }
+            }
+        }
+        if (threadIdx.x == 0) s_anchor = 0ull;
+        __syncthreads();
+    }
+    live = __reduce_add_sync(0xffffffffu, live);
+    if ((threadIdx.x & 31) == 0 && live) atomicAdd(p.cnt + PIC_C_PUSHED, (unsigned long long)live);
+}
+
+// Field data of one cell for the MD substeps: the 8 corner values of
+// E_PIC - sum_g Q_g g_g (Eq. 5, mesh part) and the cell's near grains, so a
+// substep that stays in its cell touches no memory.
+struct MdCell {
+    float ec[8][3];
+    int ng;
+    int gi[kMaxG];
+};
+
+__device__ void md_load(const P32& p, int i, int j, int k, MdCell& m)
+{
+    const int i1 = (i + 1 == p.nx) ? 0 : i + 1;
+    const int j1 = (j + 1 == p.ny) ? 0 : j + 1;
+    const int ii[2] = {i, i1}, jj[2] = {j, j1};
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+        const float4 e = __ldg(p.E + ((k + (c >> 2)) * p.ny + jj[(c >> 1) & 1]) * p.nx + ii[c & 1]);
+        m.ec[c][0] = e.x; m.ec[c][1] = e.y; m.ec[c][2] = e.z;
+    }
+    const int cell = (k * p.ny + j) * p.nx + i;
+    m.ng = p.cell_ng[cell];
+    for (int t = 0; t < m.ng; ++t) {
+        const int gi = p.cell_g[cell * kMaxG + t];
+        m.gi[t] = gi;
+        const float Q = p.gq[gi];
+        const int gc0 = p.gcell[3 * gi], gc1 = p.gcell[3 * gi + 1], gc2 = p.gcell[3 * gi + 2];
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            const int li = ((i + (c & 1) - gc0 + 1) % p.nx + p.nx) % p.nx;
+            const int lj = ((j + ((c >> 1) & 1) - gc1 + 1) % p.ny + p.ny) % p.ny;
+            const int lk = k + (c >> 2) - gc2 + 1;
+            const float* tv = p.gtab + ((size_t)gi * 64 + (lk * 4 + lj) * 4 + li) * 3;
+            m.ec[c][0] -= Q * tv[0];
+            m.ec[c][1] -= Q * tv[1];
+            m.ec[c][2] -= Q * tv[2];
+        }
+    }
+}
+
+// MD-region particles: md_sub substeps of dt/md_sub with the PPPM correction,
+// absorption after each substep, then MCC and the deposit (Sec. III)
+__global__ void __launch_bounds__(64) k_md32(const P32 p)
+{
+    const unsigned int n = *p.md_n;
+    const uint32_t step = *p.step;
+    const long long charge = p.sp == 0 ? -1 : 1;
+    const float s = 1.0f / (float)kWQ;
+    for (unsigned int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
+        const unsigned int q = p.md_list[t];
+        const float4 P = p.pos[q];
         const float4 V = p.vel[q];
+        int i, j, k;
+        unpack(__float_as_int(P.w), i, j, k);
+        float o[3] = {P.x, P.y, P.z};
         float v[3] = {V.x, V.y, V.z};
         int fate = 0, grain = -1;
-        if (p.cell_ng[cell] == 0) {
-            a[0] = qa(o[0]); a[1] = qa(o[1]); a[2] = qa(o[2]);
-            float E[3];
-            gather(p.E, p.nx, p.nxy, i, j, k, a, E);
-            v[0] += E[0] * p.kq; v[1] += E[1] * p.kq; v[2] += E[2] * p.kq;
-            o[0] += v[0]; o[1] += v[1]; o[2] += v[2];
-            fate = carry(p, i, j, k, o);
-        } else {
-            for (int m = 0; m < p.M; ++m) {
-                a[0] = qa(o[0]); a[1] = qa(o[1]); a[2] = qa(o[2]);
-                float E[3];
-                gather(p.E, p.nx, p.nxy, i, j, k, a, E);
-                md_correct(p, i, j, k, o, a, E);
-                v[0] += E[0] * p.kqm; v[1] += E[1] * p.kqm; v[2] += E[2] * p.kqm;
-                o[0] += v[0] * p.invM; o[1] += v[1] * p.invM; o[2] += v[2] * p.invM;
-                fate = carry(p, i, j, k, o);
-                if (fate) break;
-                grain = absorbed_by(p, i, j, k, o);
-                if (grain >= 0) break;
+        MdCell mc;
+        md_load(p, i, j, k, mc);
+        for (int m = 0; m < p.M; ++m) {
+            const int a0 = qa(o[0]), a1 = qa(o[1]), a2 = qa(o[2]);
+            const float wx[2] = {(float)(kWQ - a0) * s, (float)a0 * s};
+            const float wy[2] = {(float)(kWQ - a1) * s, (float)a1 * s};
+            const float wz[2] = {(float)(kWQ - a2) * s, (float)a2 * s};
+            float E[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {
+                const float w = wx[c & 1] * wy[(c >> 1) & 1] * wz[c >> 2];
+                E[0] += w * mc.ec[c][0];
+                E[1] += w * mc.ec[c][1];
+                E[2] += w * mc.ec[c][2];
             }
+            for (int g = 0; g < mc.ng; ++g) {      // Eq. 6: Coulomb field of the near grains
+                float d[3];
+                grain_sep(p, mc.gi[g], i, j, k, o, d);
+                const float r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+                const float coef = r2 > 0.f ? (p.gq[mc.gi[g]] * p.qk) / (r2 * sqrtf(r2)) : 0.f;
+                E[0] += coef * d[0]; E[1] += coef * d[1]; E[2] += coef * d[2];
+            }
+            v[0] += E[0] * p.kqm; v[1] += E[1] * p.kqm; v[2] += E[2] * p.kqm;
+            o[0] += v[0] * p.invM; o[1] += v[1] * p.invM; o[2] += v[2] * p.invM;
+            const int pi = i, pj = j, pk = k;
+            fate = carry(p.nx, p.ny, p.nz, i, j, k, o);
+            if (fate) break;
+            if (i != pi || j != pj || k != pk) md_load(p, i, j, k, mc);
+            for (int g = 0; g < mc.ng && grain < 0; ++g) {
+                float d[3];
+                grain_sep(p, mc.gi[g], i, j, k, o, d);
+                if (d[0] * d[0] + d[1] * d[1] + d[2] * d[2] <= p.gr2[mc.gi[g]]) grain = mc.gi[g];
+            }
+            if (grain >= 0) break;
         }
         if (fate != 0 || grain >= 0) {
             p.pos[q].w = __int_as_float(-1);
@@ -379,16 +583,47 @@ __global__ void __launch_bounds__(256) k_push32(const P32 p)
             }
             continue;
         }
-        cell = (k * p.ny + j) * p.nx + i;
+        const int cell = pack(i, j, k);
         const uint32_t id = __float_as_uint(V.w);
-        if (!(p.flags & PIC_F_NO_MCC)) mcc(p, step, cell, o, v, id);
+        if (!(p.flags & PIC_F_NO_MCC)) {
+            const uint4 r = philox4x32_10(make_uint4(id, step, kPurMCC, 0u), p.key);
+            if (u01f(r.x) < p.pnull) count_event(p, collide(p, step, r, cell, o, v, id));
+        }
         p.pos[q] = make_float4(o[0], o[1], o[2], __int_as_float(cell));
         p.vel[q] = make_float4(v[0], v[1], v[2], V.w);
-        a[0] = qa(o[0]); a[1] = qa(o[1]); a[2] = qa(o[2]);
-        deposit(p.rq, p.nx, p.nxy, i, j, k, a, charge);
+        const int a[3] = {qa(o[0]), qa(o[1]), qa(o[2])};
+        deposit_global(p.rq, p.nx, p.ny, i, j, k, a, charge);
     }
-    live = __reduce_add_sync(0xffffffffu, live);
-    if ((threadIdx.x & 31) == 0 && live) atomicAdd(p.cnt + PIC_C_PUSHED, (unsigned long long)live);
+}
+
+// collision candidates found by k_push32 (their positions are final)
+__global__ void __launch_bounds__(256) k_mcc32(const P32 p)
+{
+    const unsigned int n = *p.mcc_n;
+    const uint32_t step = *p.step;
+    for (unsigned int t0 = blockIdx.x * blockDim.x; t0 < n; t0 += gridDim.x * blockDim.x) {
+        const unsigned int t = t0 + threadIdx.x;
+        int ev = kEvNone;
+        if (t < n) {
+            const unsigned int q = p.mcc_list[t];
+            const float4 P = p.pos[q];
+            const float4 V = p.vel[q];
+            const uint32_t id = __float_as_uint(V.w);
+            const uint4 r = philox4x32_10(make_uint4(id, step, kPurMCC, 0u), p.key);
+            float v[3] = {V.x, V.y, V.z};
+            const float o[3] = {P.x, P.y, P.z};
+            ev = collide(p, step, r, __float_as_int(P.w), o, v, id);
+            if (ev != kEvNone) p.vel[q] = make_float4(v[0], v[1], v[2], V.w);
+        }
+        if (p.sp == 0) {
+            warp_count(p.cnt + PIC_C_E_EL, ev == kEvEEl);
+            warp_count(p.cnt + PIC_C_E_EXC, ev == kEvEExc);
+            warp_count(p.cnt + PIC_C_E_ION, ev == kEvEIon);
+        } else {
+            warp_count(p.cnt + PIC_C_I_EL, ev == kEvIEl);
+            warp_count(p.cnt + PIC_C_I_CX, ev == kEvICx);
+        }
+    }
 }
 
 __global__ void k_deposit32(int nx, int ny, const float4* pos, const unsigned long long* nslot, int sp,
@@ -402,9 +637,9 @@ __global__ void k_deposit32(int nx, int ny, const float4* pos, const unsigned lo
         const int cell = __float_as_int(P.w);
         if (cell < 0) continue;
         int i, j, k;
-        split(cell, nx, ny, i, j, k);
+        unpack(cell, i, j, k);
         const int a[3] = {qa(P.x), qa(P.y), qa(P.z)};
-        deposit(rq, nx, nx * ny, i, j, k, a, charge);
+        deposit_global(rq, nx, ny, i, j, k, a, charge);
     }
 }
 
@@ -466,10 +701,10 @@ __global__ void k_children32(int nx, int ny, ChildRec* rec, const unsigned long 
         vel_i[si] = make_float4((float)cr.vi[0], (float)cr.vi[1], (float)cr.vi[2],
                                 __uint_as_float(nid + (unsigned)(2 * rank + 1)));
         int i, j, k;
-        split(cr.cell, nx, ny, i, j, k);
+        unpack(cr.cell, i, j, k);
         const int a[3] = {qa(o[0]), qa(o[1]), qa(o[2])};
-        deposit(rq, nx, nx * ny, i, j, k, a, -1);
-        deposit(rq, nx, nx * ny, i, j, k, a, 1);
+        deposit_global(rq, nx, ny, i, j, k, a, -1);
+        deposit_global(rq, nx, ny, i, j, k, a, 1);
     }
 }
 
@@ -489,7 +724,6 @@ __global__ void k_moments32(int nx, int ny, float vs, const float4* pos, const f
                             const unsigned long long* nslot, int sp, double* mom)
 {
     const unsigned long long n = nslot[sp];
-    const int nxy = nx * ny;
     for (unsigned long long q = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; q < n;
          q += (unsigned long long)gridDim.x * blockDim.x) {
         const float4 P = pos[q];
@@ -497,23 +731,21 @@ __global__ void k_moments32(int nx, int ny, float vs, const float4* pos, const f
         if (cell < 0) continue;
         const float4 V = vel[q];
         int i, j, k;
-        split(cell, nx, ny, i, j, k);
+        unpack(cell, i, j, k);
         const int a[3] = {qa(P.x), qa(P.y), qa(P.z)};
-        const long long wx[2] = {kWQ - a[0], a[0]}, wy[2] = {kWQ - a[1], a[1]}, wz[2] = {kWQ - a[2], a[2]};
-        const int ii[2] = {i, (i + 1 == nx) ? 0 : i + 1};
-        const int jj[2] = {j, (j + 1 == ny) ? 0 : j + 1};
+        int node[8];
+        long long val[8];
+        corners(nx, ny, i, j, k, a, 1, node, val);
         const double vx = (double)V.x * vs, vy = (double)V.y * vs, vz = (double)V.z * vs;
-        for (int dz = 0; dz < 2; ++dz)
-            for (int dy = 0; dy < 2; ++dy)
-                for (int di = 0; di < 2; ++di) {
-                    const double wt = (double)(wx[di] * wy[dy] * wz[dz]) * 0x1p-42;
-                    if (wt == 0.0) continue;
-                    double* m = mom + 4 * ((size_t)(k + dz) * nxy + (size_t)jj[dy] * nx + ii[di]);
-                    atomicAdd(m, wt);
-                    atomicAdd(m + 1, wt * vx);
-                    atomicAdd(m + 2, wt * vy);
-                    atomicAdd(m + 3, wt * vz);
-                }
+        for (int c = 0; c < 8; ++c) {
+            const double wt = (double)val[c] * 0x1p-42;
+            if (wt == 0.0) continue;
+            double* m = mom + 4 * (size_t)node[c];
+            atomicAdd(m, wt);
+            atomicAdd(m + 1, wt * vx);
+            atomicAdd(m + 2, wt * vy);
+            atomicAdd(m + 3, wt * vz);
+        }
     }
 }
 
@@ -523,57 +755,77 @@ __global__ void k_moments_phi(const double* phi, double* mphi, size_t n)
         mphi[q] += phi[q];
 }
 
+P32 params(pic_ctx* c, int sp)
+{
+    P32 p;
+    p.nx = c->nx; p.ny = c->ny; p.nz = c->nz; p.nxy = c->nx * c->ny;
+    p.M = c->md_sub > 0 ? c->md_sub : 1;
+    p.sp = sp;
+    p.flags = c->flags;
+    const double kq = c->qm[sp] * c->dt * c->dt / c->dx;
+    p.kq = (float)kq;
+    p.kqm = (float)(kq / (double)p.M);
+    p.invM = (float)(1.0 / p.M);
+    p.vs = (float)(c->dx / c->dt);
+    p.inv_vs = (float)(c->dt / c->dx);
+    p.hm = (float)c->hm[sp];
+    p.pnull = (float)c->pnull[sp];
+    p.nu_max = (float)c->nu_max[sp];
+    p.de = (float)c->de[sp];
+    p.n_gas = (float)c->n_gas;
+    p.sig_n = (float)c->sig_n;
+    p.eps_exc = (float)c->eps_exc;
+    p.eps_ion = (float)c->eps_ion;
+    p.mr2 = (float)((2.0 * kME) / kMAR);
+    p.qk = (float)(1.0 / (4.0 * kPI * kEPS0) / (c->dx * c->dx));
+    p.n_xs = c->n_xs;
+    p.xs = c->xs32;
+    p.key = c->key;
+    p.step = c->d_step;
+    p.gcell = c->gcell;
+    p.goff = c->goff32;
+    p.gr2 = c->gr2_32;
+    p.gq = c->gq32;
+    p.gtab = c->gtab32;
+    p.gabs = c->gabs;
+    p.cell_ng = c->cell_ng;
+    p.cell_g = c->cell_g;
+    p.E = c->e32;
+    p.rq = c->rq;
+    p.pos = (float4*)c->pos[sp];
+    p.vel = (float4*)c->vel[sp];
+    p.nslot = c->d_nslot;
+    p.cnt = c->d_cnt;
+    p.err = c->d_err;
+    p.child = c->d_child;
+    p.child_cap = (unsigned long long)c->child_cap;
+    p.nch = c->d_nch;
+    p.md_list = c->md_list[sp];
+    p.md_n = c->d_lists + 2 * sp;
+    p.mcc_list = c->mcc_list[sp];
+    p.mcc_n = c->d_lists + 2 * sp + 1;
+    return p;
+}
+
 }  // namespace
 
 void launch_push32(pic_ctx* c)
 {
-    for (int sp = 0; sp < 2; ++sp) {
-        P32 p;
-        p.nx = c->nx; p.ny = c->ny; p.nz = c->nz; p.nxy = c->nx * c->ny;
-        p.M = c->md_sub > 0 ? c->md_sub : 1;
-        p.sp = sp;
-        p.flags = c->flags;
-        const double kq = c->qm[sp] * c->dt * c->dt / c->dx;
-        p.kq = (float)kq;
-        p.kqm = (float)(kq / (double)p.M);
-        p.invM = (float)(1.0 / p.M);
-        p.vs = (float)(c->dx / c->dt);
-        p.inv_vs = (float)(c->dt / c->dx);
-        p.hm = (float)c->hm[sp];
-        p.pnull = (float)c->pnull[sp];
-        p.nu_max = (float)c->nu_max[sp];
-        p.de = (float)c->de[sp];
-        p.n_gas = (float)c->n_gas;
-        p.sig_n = (float)c->sig_n;
-        p.eps_exc = (float)c->eps_exc;
-        p.eps_ion = (float)c->eps_ion;
-        p.mr2 = (float)((2.0 * kME) / kMAR);
-        p.qk = (float)(1.0 / (4.0 * kPI * kEPS0) / (c->dx * c->dx));
-        p.n_xs = c->n_xs;
-        p.xs = c->xs32;
-        p.key = c->key;
-        p.step = c->d_step;
-        p.gcell = c->gcell;
-        p.goff = c->goff32;
-        p.gr2 = c->gr2_32;
-        p.gq = c->gq32;
-        p.gtab = c->gtab32;
-        p.gabs = c->gabs;
-        p.cell_ng = c->cell_ng;
-        p.cell_g = c->cell_g;
-        p.E = c->e32;
-        p.rq = c->rq;
-        p.pos = (float4*)c->pos[sp];
-        p.vel = (float4*)c->vel[sp];
-        p.nslot = c->d_nslot;
-        p.cnt = c->d_cnt;
-        p.err = c->d_err;
-        p.child = c->d_child;
-        p.child_cap = (unsigned long long)c->child_cap;
-        p.nch = c->d_nch;
-        k_push32<<<grid_for(c->cap[sp], 256, 152 * 8), 256, 0, c->stream>>>(p);
-        c->launches += 1;
-    }
+    // electrons: fast push on the main stream, then their MD-region and
+    // collision kernels on a second branch, which overlaps the ion push
+    cudaMemsetAsync(c->d_lists, 0, 4 * sizeof(unsigned int), c->stream);
+    const P32 pe = params(c, 0), pi = params(c, 1);
+    k_push32<<<grid_for((c->cap[0] + kPPT - 1) / kPPT, kPushThreads, 152 * 8), kPushThreads, 0, c->stream>>>(pe);
+    cudaEventRecord(c->ev_fork, c->stream);
+    cudaStreamWaitEvent(c->aux, c->ev_fork, 0);
+    k_md32<<<152 * 4, 64, 0, c->aux>>>(pe);
+    k_mcc32<<<152 * 4, 256, 0, c->aux>>>(pe);
+    cudaEventRecord(c->ev_join, c->aux);
+    k_push32<<<grid_for((c->cap[1] + kPPT - 1) / kPPT, kPushThreads, 152 * 8), kPushThreads, 0, c->stream>>>(pi);
+    k_md32<<<152 * 4, 64, 0, c->stream>>>(pi);
+    k_mcc32<<<152 * 4, 256, 0, c->stream>>>(pi);
+    cudaStreamWaitEvent(c->stream, c->ev_join, 0);
+    c->launches += 6;
 }
 
 void launch_deposit32(pic_ctx* c)
@@ -594,9 +846,9 @@ void launch_efield32(pic_ctx* c)
 void launch_children32(pic_ctx* c)
 {
     k_children32<<<64, 256, 0, c->stream>>>(c->nx, c->ny, c->d_child, c->d_nch, (unsigned long long)c->child_cap,
-                                              c->d_nslot, c->d_next_id,
-                                              (float4*)c->pos[0], (float4*)c->vel[0], (float4*)c->pos[1],
-                                              (float4*)c->vel[1], c->cap[0], c->cap[1], c->rq, c->d_err);
+                                              c->d_nslot, c->d_next_id, (float4*)c->pos[0], (float4*)c->vel[0],
+                                              (float4*)c->pos[1], (float4*)c->vel[1], c->cap[0], c->cap[1], c->rq,
+                                              c->d_err);
     k_children_finish32<<<1, 1, 0, c->stream>>>(c->d_nch, (unsigned long long)c->child_cap, c->d_nslot,
                                                 c->d_next_id, c->cap[0], c->cap[1], c->d_step);
     c->launches += 2;

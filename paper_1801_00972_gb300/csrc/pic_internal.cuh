@@ -105,6 +105,7 @@ struct RStream {
 
 // ---------------------------------------------------------------- context
 constexpr int kMaxDense = 1024;   // coarsest-level unknowns solved with a dense inverse
+constexpr size_t kTailNodes = 2500;   // levels this small run together in one block
 
 // constants of the graph solve's right-hand side and electrode values
 struct SolveParams {
@@ -155,6 +156,9 @@ struct pic_ctx {
     unsigned long long* d_nch = nullptr;     // children this step
     unsigned int* d_next_id = nullptr;
     pic::ChildRec* d_child = nullptr;
+    unsigned int* md_list[2] = {nullptr, nullptr};   // mixed: slots of MD-region particles this step
+    unsigned int* mcc_list[2] = {nullptr, nullptr};  // mixed: slots of collision candidates this step
+    unsigned int* d_lists = nullptr;                  // [md_n e, mcc_n e, md_n i, mcc_n i]
 
     // mesh arrays
     unsigned long long* rq = nullptr;        // int64 fixed-point charge per node
@@ -192,6 +196,7 @@ struct pic_ctx {
     // multigrid
     std::vector<pic::MGLevel> mg;
     void* coarse_inv = nullptr;              // dense inverse of the coarsest level (T)
+    int mg_tail = 0;                         // first level handled by the one-block tail kernel
     pic::SolveParams sp;
     unsigned int* d_iters = nullptr;         // graph solve: iterations of the last solve
     double* d_res = nullptr;                 // graph solve: relative residual of the last solve
@@ -202,6 +207,8 @@ struct pic_ctx {
     // CUDA graphs of one step, captured lazily on a private stream and
     // launched on the run's stream; variants by particle-buffer parity
     cudaStream_t cap_stream = nullptr;
+    cudaStream_t aux = nullptr;              // second branch of the particle phase (MD, collisions)
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     int parity = 0;
     cudaGraphExec_t g_pre = nullptr, g_push[2] = {nullptr, nullptr}, g_solve = nullptr;
     cudaGraphExec_t g_post[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}}, g_mom[2] = {nullptr, nullptr};

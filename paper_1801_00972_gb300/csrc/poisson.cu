@@ -30,98 +30,109 @@ __device__ __forceinline__ size_t nid(const Dims& d, int i, int j, int k)
     return ((size_t)k * d.ny + j) * d.nx + i;
 }
 
-template <typename T>
-__global__ void k_rbgs(T* __restrict__ u, const T* __restrict__ f, Dims d, T h2, int color)
+// The stencil kernels run on 3-D grids: threads over (i, j) of a plane, one
+// grid row of blocks per k; all indices are 32-bit (a mesh has < 2^31 nodes).
+struct Grid3 {
+    dim3 grid, block;
+};
+inline Grid3 grid3(int nx, int ny, int planes)
 {
-    const int half = d.nx / 2;
-    const size_t total = (size_t)half * d.ny * (d.nz - 1);
-    const size_t P = (size_t)d.nx * d.ny;
-    for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
-        const int i2 = (int)(t % half);
-        const int j = (int)((t / half) % d.ny);
-        const int k = 1 + (int)(t / ((size_t)half * d.ny));
-        const int i = 2 * i2 + ((j + k + color) & 1);
-        const size_t n = nid(d, i, j, k);
-        const int ip = (i + 1 == d.nx) ? 0 : i + 1, im = (i == 0) ? d.nx - 1 : i - 1;
-        const int jp = (j + 1 == d.ny) ? 0 : j + 1, jm = (j == 0) ? d.ny - 1 : j - 1;
-        const size_t row = n - i;
-        const T s = u[row + ip] + u[row + im] + u[nid(d, i, jp, k)] + u[nid(d, i, jm, k)] + u[n + P] + u[n - P];
-        u[n] = (s + h2 * f[n]) * (T)(1.0 / 6.0);
-    }
+    const int bx = nx >= 32 ? 32 : nx;
+    const int by = std::max(1, std::min(ny, 256 / bx));
+    return Grid3{dim3((unsigned)((nx + bx - 1) / bx), (unsigned)((ny + by - 1) / by), (unsigned)planes),
+                 dim3((unsigned)bx, (unsigned)by, 1)};
 }
 
+__device__ __forceinline__ int tid_flat() { return threadIdx.y * blockDim.x + threadIdx.x; }
+
+// red-black Gauss-Seidel, one colour; thread (i2, j) of plane k = 1 + blockIdx.z
+template <typename T>
+__global__ void k_rbgs(T* __restrict__ u, const T* __restrict__ f, Dims d, T h2, int color, int zero)
+{
+    const int i2 = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    const int k = 1 + blockIdx.z;
+    if (i2 >= d.nx / 2 || j >= d.ny) return;
+    const int i = 2 * i2 + ((j + k + color) & 1);
+    const int P = d.nx * d.ny;
+    const int n = k * P + j * d.nx + i;
+    if (zero) {   // first sweep from a zero guess: the neighbours are still zero
+        u[n] = (h2 * f[n]) * (T)(1.0 / 6.0);
+        return;
+    }
+    const int row = n - i;
+    const int ip = (i + 1 == d.nx) ? 0 : i + 1, im = (i == 0) ? d.nx - 1 : i - 1;
+    const int jp = (j + 1 == d.ny) ? -j * d.nx : d.nx, jm = (j == 0) ? (d.ny - 1) * d.nx : -d.nx;
+    const T s = u[row + ip] + u[row + im] + u[n + jp] + u[n + jm] + u[n + P] + u[n - P];
+    u[n] = (s + h2 * f[n]) * (T)(1.0 / 6.0);
+}
+
+// r = f - A u on the interior planes (the electrode planes of r stay zero)
 template <typename T>
 __global__ void k_resid(const T* __restrict__ u, const T* __restrict__ f, T* __restrict__ r, Dims d, T inv_h2)
 {
-    const size_t P = (size_t)d.nx * d.ny;
-    const size_t N = P * (d.nz + 1);
-    for (size_t n = blockIdx.x * (size_t)blockDim.x + threadIdx.x; n < N; n += (size_t)gridDim.x * blockDim.x) {
-        const int k = (int)(n / P);
-        if (k == 0 || k == d.nz) { r[n] = (T)0; continue; }
-        const int i = (int)(n % d.nx), j = (int)((n / d.nx) % d.ny);
-        const int ip = (i + 1 == d.nx) ? 0 : i + 1, im = (i == 0) ? d.nx - 1 : i - 1;
-        const int jp = (j + 1 == d.ny) ? 0 : j + 1, jm = (j == 0) ? d.ny - 1 : j - 1;
-        const size_t row = n - i;
-        const T s = u[row + ip] + u[row + im] + u[nid(d, i, jp, k)] + u[nid(d, i, jm, k)] + u[n + P] + u[n - P];
-        r[n] = f[n] - ((T)6 * u[n] - s) * inv_h2;
-    }
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    const int k = 1 + blockIdx.z;
+    if (i >= d.nx || j >= d.ny) return;
+    const int P = d.nx * d.ny;
+    const int n = k * P + j * d.nx + i;
+    const int row = n - i;
+    const int ip = (i + 1 == d.nx) ? 0 : i + 1, im = (i == 0) ? d.nx - 1 : i - 1;
+    const int jp = (j + 1 == d.ny) ? -j * d.nx : d.nx, jm = (j == 0) ? (d.ny - 1) * d.nx : -d.nx;
+    const T s = u[row + ip] + u[row + im] + u[n + jp] + u[n + jm] + u[n + P] + u[n - P];
+    r[n] = f[n] - ((T)6 * u[n] - s) * inv_h2;
 }
 
-// full weighting: weights (1/4, 1/2, 1/4) per axis around the coincident fine node
+// full weighting: weights (1/4, 1/2, 1/4) per axis around the coincident fine
+// node; thread (I, J) of coarse plane K = 1 + blockIdx.z
 template <typename T>
 __global__ void k_restrict(const T* __restrict__ rf, T* __restrict__ fc, Dims df, Dims dc)
 {
-    const size_t P = (size_t)dc.nx * dc.ny;
-    const size_t N = P * (dc.nz + 1);
-    for (size_t n = blockIdx.x * (size_t)blockDim.x + threadIdx.x; n < N; n += (size_t)gridDim.x * blockDim.x) {
-        const int K = (int)(n / P);
-        if (K == 0 || K == dc.nz) { fc[n] = (T)0; continue; }
-        const int I = (int)(n % dc.nx), J = (int)((n / dc.nx) % dc.ny);
-        T acc = (T)0;
+    const int I = blockIdx.x * blockDim.x + threadIdx.x;
+    const int J = blockIdx.y * blockDim.y + threadIdx.y;
+    const int K = 1 + blockIdx.z;
+    if (I >= dc.nx || J >= dc.ny) return;
+    const int Pf = df.nx * df.ny;
+    const int i0 = 2 * I, j0 = 2 * J, k0 = 2 * K;
+    const int im = (i0 == 0) ? df.nx - 1 : i0 - 1, ip = i0 + 1;   // i0 + 1 < nx (nx even)
+    const int jm = (j0 == 0) ? df.ny - 1 : j0 - 1, jp = j0 + 1;
+    const int cols[3] = {im, i0, ip};
+    const int rows[3] = {jm * df.nx, j0 * df.nx, jp * df.nx};
+    const T w[3] = {(T)0.25, (T)0.5, (T)0.25};
+    T acc = (T)0;
 #pragma unroll
-        for (int dk = -1; dk <= 1; ++dk) {
-            const T wk = dk == 0 ? (T)0.5 : (T)0.25;
+    for (int a = 0; a < 3; ++a) {
+        const int pl = (k0 - 1 + a) * Pf;
+        T pa = (T)0;
 #pragma unroll
-            for (int dj = -1; dj <= 1; ++dj) {
-                const T wj = dj == 0 ? (T)0.5 : (T)0.25;
-                const int j = (2 * J + dj + df.ny) % df.ny;
-#pragma unroll
-                for (int di = -1; di <= 1; ++di) {
-                    const T wi = di == 0 ? (T)0.5 : (T)0.25;
-                    const int i = (2 * I + di + df.nx) % df.nx;
-                    acc += (wk * wj * wi) * rf[nid(df, i, j, 2 * K + dk)];
-                }
-            }
+        for (int b = 0; b < 3; ++b) {
+            const T* rr = rf + pl + rows[b];
+            pa += w[b] * (w[0] * rr[cols[0]] + w[1] * rr[cols[1]] + w[2] * rr[cols[2]]);
         }
-        fc[n] = acc;
+        acc += w[a] * pa;
     }
+    fc[K * dc.nx * dc.ny + J * dc.nx + I] = acc;
 }
 
 // trilinear interpolation of the coarse correction, added on the fine interior
 template <typename T>
 __global__ void k_prolong(T* __restrict__ uf, const T* __restrict__ uc, Dims df, Dims dc)
 {
-    const size_t P = (size_t)df.nx * df.ny;
-    const size_t N = P * (df.nz + 1);
-    for (size_t n = blockIdx.x * (size_t)blockDim.x + threadIdx.x; n < N; n += (size_t)gridDim.x * blockDim.x) {
-        const int k = (int)(n / P);
-        if (k == 0 || k == df.nz) continue;
-        const int i = (int)(n % df.nx), j = (int)((n / df.nx) % df.ny);
-        int I[2], J[2], K[2];
-        T wi[2], wj[2], wk[2];
-        int ni, nj, nk;
-        if (i & 1) { I[0] = i / 2; I[1] = (i / 2 + 1) % dc.nx; wi[0] = wi[1] = (T)0.5; ni = 2; }
-        else { I[0] = i / 2; wi[0] = (T)1; ni = 1; I[1] = 0; wi[1] = (T)0; }
-        if (j & 1) { J[0] = j / 2; J[1] = (j / 2 + 1) % dc.ny; wj[0] = wj[1] = (T)0.5; nj = 2; }
-        else { J[0] = j / 2; wj[0] = (T)1; nj = 1; J[1] = 0; wj[1] = (T)0; }
-        if (k & 1) { K[0] = k / 2; K[1] = k / 2 + 1; wk[0] = wk[1] = (T)0.5; nk = 2; }
-        else { K[0] = k / 2; wk[0] = (T)1; nk = 1; K[1] = 0; wk[1] = (T)0; }
-        T acc = (T)0;
-        for (int a = 0; a < nk; ++a)
-            for (int b = 0; b < nj; ++b)
-                for (int c = 0; c < ni; ++c) acc += (wk[a] * wj[b] * wi[c]) * uc[nid(dc, I[c], J[b], K[a])];
-        uf[n] += acc;
-    }
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    const int k = 1 + blockIdx.z;
+    if (i >= df.nx || j >= df.ny) return;
+    const int I0 = i >> 1, I1 = (i & 1) ? ((I0 + 1 == dc.nx) ? 0 : I0 + 1) : I0;
+    const int J0 = j >> 1, J1 = (j & 1) ? ((J0 + 1 == dc.ny) ? 0 : J0 + 1) : J0;
+    const int K0 = k >> 1, K1 = (k & 1) ? K0 + 1 : K0;
+    const int Pc = dc.nx * dc.ny;
+    const T* a0 = uc + K0 * Pc;
+    const T* a1 = uc + K1 * Pc;
+    // a coincident axis repeats its node, so the 1/8 weights give 1/2 or 1 per axis
+    const T v = (T)0.125 * (a0[J0 * dc.nx + I0] + a0[J0 * dc.nx + I1] + a0[J1 * dc.nx + I0] + a0[J1 * dc.nx + I1] +
+                            a1[J0 * dc.nx + I0] + a1[J0 * dc.nx + I1] + a1[J1 * dc.nx + I0] + a1[J1 * dc.nx + I1]);
+    uf[k * df.nx * df.ny + j * df.nx + i] += v;
 }
 
 // coarsest level: red-black sweeps inside one block
@@ -153,12 +164,13 @@ __global__ void k_coarse(T* __restrict__ u, const T* __restrict__ f, Dims d, T h
 __device__ __forceinline__ double block_sum(double v)
 {
     __shared__ double part[32];
+    const int t = tid_flat(), nt = blockDim.x * blockDim.y;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int lane = t & 31, w = t >> 5;
     if (lane == 0) part[w] = v;
     __syncthreads();
-    v = (threadIdx.x < (blockDim.x + 31) / 32) ? part[threadIdx.x] : 0.0;
+    v = (t < (nt + 31) / 32) ? part[t] : 0.0;
     if (w == 0)
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
@@ -166,95 +178,92 @@ __device__ __forceinline__ double block_sum(double v)
 }
 
 // phi_out = phi + e on the interior (e may be null), r = f - A phi_out in FP64,
-// stored as T; ||r||^2 accumulated into *norm2
+// stored as T; ||r||^2 accumulated into *norm2.  Thread (i, j) of interior
+// plane k = 1 + blockIdx.z.
 template <typename T>
 __global__ void k_resid64(const double* __restrict__ phi, const T* __restrict__ e, const double* __restrict__ f,
                           double* __restrict__ phi_out, T* __restrict__ r, double* norm2, Dims d, double inv_h2)
 {
-    const size_t P = (size_t)d.nx * d.ny;
-    const size_t N = P * (d.nz + 1);
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
     double acc = 0.0;
-    for (size_t n = blockIdx.x * (size_t)blockDim.x + threadIdx.x; n < N; n += (size_t)gridDim.x * blockDim.x) {
-        const int k = (int)(n / P);
-        if (k == 0 || k == d.nz) {
-            if (phi_out) phi_out[n] = phi[n];
-            r[n] = (T)0;
-            continue;
-        }
-        const int i = (int)(n % d.nx), j = (int)((n / d.nx) % d.ny);
+    if (i < d.nx && j < d.ny) {
+        const int P = d.nx * d.ny;
         const int ip = (i + 1 == d.nx) ? 0 : i + 1, im = (i == 0) ? d.nx - 1 : i - 1;
-        const int jp = (j + 1 == d.ny) ? 0 : j + 1, jm = (j == 0) ? d.ny - 1 : j - 1;
-        const size_t row = n - i;
-        const size_t nb[6] = {row + ip, row + im, nid(d, i, jp, k), nid(d, i, jm, k), n + P, n - P};
-        double c = phi[n];
-        if (e) c += (double)e[n];
-        double s = 0.0;
+        const int jp = (j + 1 == d.ny) ? -j * d.nx : d.nx, jm = (j == 0) ? (d.ny - 1) * d.nx : -d.nx;
+        // planes 1 + blockIdx.z, 1 + blockIdx.z + gridDim.z, ... (few blocks: few norm atomics)
+        for (int k = 1 + blockIdx.z; k < d.nz; k += gridDim.z) {
+            const int n = k * P + j * d.nx + i;
+            const int row = n - i;
+            const int nb[6] = {row + ip, row + im, n + jp, n + jm, n + P, n - P};
+            double c = phi[n];
+            double s = 0.0;
+            if (e) {
+                c += (double)e[n];
 #pragma unroll
-        for (int q = 0; q < 6; ++q) {
-            double v = phi[nb[q]];
-            if (e) v += (double)e[nb[q]];
-            s += v;
+                for (int q = 0; q < 6; ++q) s += phi[nb[q]] + (double)e[nb[q]];
+            } else {
+#pragma unroll
+                for (int q = 0; q < 6; ++q) s += phi[nb[q]];
+            }
+            if (phi_out) phi_out[n] = c;
+            const double res = f[n] - (6.0 * c - s) * inv_h2;
+            r[n] = (T)res;
+            acc += res * res;
         }
-        if (phi_out) phi_out[n] = c;
-        const double res = f[n] - (6.0 * c - s) * inv_h2;
-        r[n] = (T)res;
-        acc += res * res;
     }
     acc = block_sum(acc);
-    if (threadIdx.x == 0) atomicAdd(norm2, acc);
+    if (tid_flat() == 0) atomicAdd(norm2, acc);
 }
 
-// f = rho_q * scale; electrode values on both phi buffers; ||b||^2 with the
-// electrode terms of the nodes next to the planes
+// copy the electrode planes from phi to phi_out (the fused update writes only
+// the interior)
+__global__ void k_copy_planes(const double* __restrict__ phi, double* __restrict__ phi_out, Dims d)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    if (i >= d.nx || j >= d.ny) return;
+    const int P = d.nx * d.ny;
+    const int n = (blockIdx.z ? d.nz : 0) * P + j * d.nx + i;
+    phi_out[n] = phi[n];
+}
+
+// f = rho_q * scale on every node; electrode values on both phi buffers;
+// ||b||^2 with the electrode terms of the nodes next to the planes
 __global__ void k_rhs(const unsigned long long* __restrict__ rq, double scale, double* __restrict__ f,
                       double* __restrict__ phi, double* __restrict__ phi_alt, double vb, double vt, Dims d,
                       double inv_h2, double* norm2)
 {
-    const size_t P = (size_t)d.nx * d.ny;
-    const size_t N = P * (d.nz + 1);
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
     double acc = 0.0;
-    for (size_t n = blockIdx.x * (size_t)blockDim.x + threadIdx.x; n < N; n += (size_t)gridDim.x * blockDim.x) {
-        const int k = (int)(n / P);
-        const double fv = (double)(long long)rq[n] * scale;
-        f[n] = fv;
-        if (k == 0) { phi[n] = vb; phi_alt[n] = vb; continue; }
-        if (k == d.nz) { phi[n] = vt; phi_alt[n] = vt; continue; }
-        double b = fv;
-        if (k == 1) b += vb * inv_h2;
-        if (k == d.nz - 1) b += vt * inv_h2;
-        acc += b * b;
-    }
+    if (i < d.nx && j < d.ny)
+        for (int k = blockIdx.z; k <= d.nz; k += gridDim.z) {
+            const int n = (k * d.ny + j) * d.nx + i;
+            const double fv = (double)(long long)rq[n] * scale;
+            f[n] = fv;
+            if (k == 0) { phi[n] = vb; phi_alt[n] = vb; }
+            else if (k == d.nz) { phi[n] = vt; phi_alt[n] = vt; }
+            else {
+                double b = fv;
+                if (k == 1) b += vb * inv_h2;
+                if (k == d.nz - 1) b += vt * inv_h2;
+                acc += b * b;
+            }
+        }
     acc = block_sum(acc);
-    if (threadIdx.x == 0) atomicAdd(norm2, acc);
-}
-
-// coarsest level solved exactly: u = A^-1 f on the interior nodes, with A^-1
-// precomputed on the host for the level (at most kMaxDense unknowns)
-template <typename T>
-__global__ void k_coarse_direct(T* __restrict__ u, const T* __restrict__ f, const T* __restrict__ ainv, Dims d)
-{
-    extern __shared__ unsigned char smem[];
-    T* fi = reinterpret_cast<T*>(smem);
-    const int P = d.nx * d.ny;
-    const int n = P * (d.nz - 1);
-    for (int m = threadIdx.x; m < n; m += blockDim.x) fi[m] = f[P + m];
-    __syncthreads();
-    for (int m = threadIdx.x; m < n; m += blockDim.x) {
-        const T* row = ainv + (size_t)m * n;
-        T acc = (T)0;
-        for (int q = 0; q < n; ++q) acc += row[q] * fi[q];
-        u[P + m] = acc;
-    }
+    if (tid_flat() == 0) atomicAdd(norm2, acc);
 }
 
 // phi += e on the interior nodes
 template <typename T>
 __global__ void k_add(double* __restrict__ phi, const T* __restrict__ e, Dims d)
 {
-    const size_t P = (size_t)d.nx * d.ny;
-    const size_t lo = P, hi = P * d.nz;
-    for (size_t n = lo + blockIdx.x * (size_t)blockDim.x + threadIdx.x; n < hi; n += (size_t)gridDim.x * blockDim.x)
-        phi[n] += (double)e[n];
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    if (i >= d.nx || j >= d.ny) return;
+    const int n = ((1 + blockIdx.z) * d.ny + j) * d.nx + i;
+    phi[n] += (double)e[n];
 }
 
 // electrode values at t = step * dt from the device step counter
@@ -268,23 +277,26 @@ __device__ __forceinline__ double bottom_potential(const SolveParams& sp, uint32
 __global__ void k_rhs_dev(const unsigned long long* __restrict__ rq, double* __restrict__ f, double* __restrict__ phi,
                           Dims d, SolveParams sp, const uint32_t* step, double* norm2)
 {
-    const size_t P = (size_t)d.nx * d.ny;
-    const size_t N = P * (d.nz + 1);
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
     const double vb = bottom_potential(sp, *step), vt = sp.v_top;
     double acc = 0.0;
-    for (size_t n = blockIdx.x * (size_t)blockDim.x + threadIdx.x; n < N; n += (size_t)gridDim.x * blockDim.x) {
-        const int k = (int)(n / P);
-        const double fv = (double)(long long)rq[n] * sp.scale;
-        f[n] = fv;
-        if (k == 0) { phi[n] = vb; continue; }
-        if (k == d.nz) { phi[n] = vt; continue; }
-        double b = fv;
-        if (k == 1) b += vb * sp.inv_h2;
-        if (k == d.nz - 1) b += vt * sp.inv_h2;
-        acc += b * b;
-    }
+    if (i < d.nx && j < d.ny)
+        for (int k = blockIdx.z; k <= d.nz; k += gridDim.z) {
+            const int n = (k * d.ny + j) * d.nx + i;
+            const double fv = (double)(long long)rq[n] * sp.scale;
+            f[n] = fv;
+            if (k == 0) phi[n] = vb;
+            else if (k == d.nz) phi[n] = vt;
+            else {
+                double b = fv;
+                if (k == 1) b += vb * sp.inv_h2;
+                if (k == d.nz - 1) b += vt * sp.inv_h2;
+                acc += b * b;
+            }
+        }
     acc = block_sum(acc);
-    if (threadIdx.x == 0) atomicAdd(norm2, acc);
+    if (tid_flat() == 0) atomicAdd(norm2, acc);
 }
 
 // loop control of the graph solve: after each residual, decide whether to run
@@ -306,44 +318,257 @@ __global__ void k_conv(double* norm, unsigned int* iters, double* res_out, int* 
     cudaGraphSetConditional(h, more ? 1u : 0u);
 }
 
+// ---- the small levels of a V-cycle in one block --------------------------
+constexpr int kTailMax = 8;
+
+template <typename T>
+struct TailLevels {
+    int n;                        // levels in the tail (the last one is the coarsest)
+    int nx[kTailMax], ny[kTailMax], nz[kTailMax];
+    double h[kTailMax];
+    T* u[kTailMax];
+    T* f[kTailMax];
+    T* r[kTailMax];
+    const T* ainv;                // dense inverse of the coarsest level, or null
+    int sweeps;                   // coarsest-level sweeps when there is no inverse
+};
+
+template <typename T>
+__device__ void tail_rbgs(T* u, const T* f, Dims d, T h2, int color, bool zero)
+{
+    const int half = d.nx / 2;
+    const int total = half * d.ny * (d.nz - 1);
+    const int P = d.nx * d.ny;
+    for (int t = threadIdx.x; t < total; t += blockDim.x) {
+        const int i2 = t % half;
+        const int j = (t / half) % d.ny;
+        const int k = 1 + t / (half * d.ny);
+        const int i = 2 * i2 + ((j + k + color) & 1);
+        const int n = (k * d.ny + j) * d.nx + i;
+        if (zero) {
+            u[n] = (h2 * f[n]) * (T)(1.0 / 6.0);
+            continue;
+        }
+        const int ip = (i + 1 == d.nx) ? 0 : i + 1, im = (i == 0) ? d.nx - 1 : i - 1;
+        const int jp = (j + 1 == d.ny) ? 0 : j + 1, jm = (j == 0) ? d.ny - 1 : j - 1;
+        const int row = n - i;
+        const T s = u[row + ip] + u[row + im] + u[(k * d.ny + jp) * d.nx + i] + u[(k * d.ny + jm) * d.nx + i] +
+                    u[n + P] + u[n - P];
+        u[n] = (s + h2 * f[n]) * (T)(1.0 / 6.0);
+    }
+    __syncthreads();
+}
+
+template <typename T>
+__device__ void tail_resid(const T* u, const T* f, T* r, Dims d, T inv_h2)
+{
+    const int P = d.nx * d.ny;
+    const int N = P * (d.nz + 1);
+    for (int n = threadIdx.x; n < N; n += blockDim.x) {
+        const int k = n / P;
+        if (k == 0 || k == d.nz) { r[n] = (T)0; continue; }
+        const int i = n % d.nx, j = (n / d.nx) % d.ny;
+        const int ip = (i + 1 == d.nx) ? 0 : i + 1, im = (i == 0) ? d.nx - 1 : i - 1;
+        const int jp = (j + 1 == d.ny) ? 0 : j + 1, jm = (j == 0) ? d.ny - 1 : j - 1;
+        const int row = n - i;
+        const T s = u[row + ip] + u[row + im] + u[(k * d.ny + jp) * d.nx + i] + u[(k * d.ny + jm) * d.nx + i] +
+                    u[n + P] + u[n - P];
+        r[n] = f[n] - ((T)6 * u[n] - s) * inv_h2;
+    }
+    __syncthreads();
+}
+
+template <typename T>
+__device__ void tail_restrict(const T* rf, T* fc, Dims df, Dims dc)
+{
+    const int P = dc.nx * dc.ny;
+    const int N = P * (dc.nz + 1);
+    for (int n = threadIdx.x; n < N; n += blockDim.x) {
+        const int K = n / P;
+        if (K == 0 || K == dc.nz) { fc[n] = (T)0; continue; }
+        const int I = n % dc.nx, J = (n / dc.nx) % dc.ny;
+        T acc = (T)0;
+        for (int dk = -1; dk <= 1; ++dk) {
+            const T wk = dk == 0 ? (T)0.5 : (T)0.25;
+            for (int dj = -1; dj <= 1; ++dj) {
+                const T wj = dj == 0 ? (T)0.5 : (T)0.25;
+                const int j = (2 * J + dj + df.ny) % df.ny;
+                for (int di = -1; di <= 1; ++di) {
+                    const T wi = di == 0 ? (T)0.5 : (T)0.25;
+                    const int i = (2 * I + di + df.nx) % df.nx;
+                    acc += (wk * wj * wi) * rf[((2 * K + dk) * df.ny + j) * df.nx + i];
+                }
+            }
+        }
+        fc[n] = acc;
+    }
+    __syncthreads();
+}
+
+template <typename T>
+__device__ void tail_prolong(T* uf, const T* uc, Dims df, Dims dc)
+{
+    const int P = df.nx * df.ny;
+    const int N = P * (df.nz + 1);
+    for (int n = threadIdx.x; n < N; n += blockDim.x) {
+        const int k = n / P;
+        if (k == 0 || k == df.nz) continue;
+        const int i = n % df.nx, j = (n / df.nx) % df.ny;
+        const int I0 = i / 2, I1 = (i & 1) ? (i / 2 + 1) % dc.nx : I0;
+        const int J0 = j / 2, J1 = (j & 1) ? (j / 2 + 1) % dc.ny : J0;
+        const int K0 = k / 2, K1 = (k & 1) ? k / 2 + 1 : K0;
+        const int Pc = dc.nx * dc.ny;
+        // each axis: weights (1/2, 1/2) between two coarse nodes, or (1) on a coincident one
+        const T v = (T)0.125 * (uc[K0 * Pc + J0 * dc.nx + I0] + uc[K0 * Pc + J0 * dc.nx + I1] +
+                                uc[K0 * Pc + J1 * dc.nx + I0] + uc[K0 * Pc + J1 * dc.nx + I1] +
+                                uc[K1 * Pc + J0 * dc.nx + I0] + uc[K1 * Pc + J0 * dc.nx + I1] +
+                                uc[K1 * Pc + J1 * dc.nx + I0] + uc[K1 * Pc + J1 * dc.nx + I1]);
+        uf[n] += v;
+    }
+    __syncthreads();
+}
+
+// pre-smoothing, residual and restriction down the tail, the coarsest solve,
+// then prolongation and post-smoothing back up: the lower part of a V(2,2) cycle
+template <typename T>
+__global__ void __launch_bounds__(1024) k_vcycle_tail(const TailLevels<T> L)
+{
+    extern __shared__ unsigned char smem[];
+    for (int l = 0; l + 1 < L.n; ++l) {
+        const Dims d{L.nx[l], L.ny[l], L.nz[l]};
+        const T h2 = (T)(L.h[l] * L.h[l]);
+        tail_rbgs<T>(L.u[l], L.f[l], d, h2, 0, true);
+        tail_rbgs<T>(L.u[l], L.f[l], d, h2, 1, false);
+        tail_rbgs<T>(L.u[l], L.f[l], d, h2, 0, false);
+        tail_rbgs<T>(L.u[l], L.f[l], d, h2, 1, false);
+        tail_resid<T>(L.u[l], L.f[l], L.r[l], d, (T)(1.0 / (L.h[l] * L.h[l])));
+        tail_restrict<T>(L.r[l], L.f[l + 1], d, Dims{L.nx[l + 1], L.ny[l + 1], L.nz[l + 1]});
+    }
+    {
+        const int c = L.n - 1;
+        const Dims d{L.nx[c], L.ny[c], L.nz[c]};
+        const int P = d.nx * d.ny, n = P * (d.nz - 1);
+        if (L.ainv) {
+            T* fi = reinterpret_cast<T*>(smem);
+            for (int m = threadIdx.x; m < n; m += blockDim.x) fi[m] = L.f[c][P + m];
+            __syncthreads();
+            for (int m = threadIdx.x; m < n; m += blockDim.x) {
+                const T* row = L.ainv + (size_t)m * n;
+                T acc = (T)0;
+                for (int q = 0; q < n; ++q) acc += row[q] * fi[q];
+                L.u[c][P + m] = acc;
+            }
+            __syncthreads();
+        } else {
+            const T h2 = (T)(L.h[c] * L.h[c]);
+            for (int s = 0; s < L.sweeps; ++s) {
+                tail_rbgs<T>(L.u[c], L.f[c], d, h2, 0, s == 0);
+                tail_rbgs<T>(L.u[c], L.f[c], d, h2, 1, false);
+            }
+        }
+    }
+    for (int l = L.n - 2; l >= 0; --l) {
+        const Dims d{L.nx[l], L.ny[l], L.nz[l]};
+        const T h2 = (T)(L.h[l] * L.h[l]);
+        tail_prolong<T>(L.u[l], L.u[l + 1], d, Dims{L.nx[l + 1], L.ny[l + 1], L.nz[l + 1]});
+        tail_rbgs<T>(L.u[l], L.f[l], d, h2, 0, false);
+        tail_rbgs<T>(L.u[l], L.f[l], d, h2, 1, false);
+        tail_rbgs<T>(L.u[l], L.f[l], d, h2, 0, false);
+        tail_rbgs<T>(L.u[l], L.f[l], d, h2, 1, false);
+    }
+}
+
 int blocks(size_t n) { return grid_for((int64_t)n, 256, 152 * 8); }
+
+// grid for kernels that reduce a norm: (x, y) blocks of a plane and just enough
+// z blocks (each looping over planes) to fill the GPU a few times
+inline Grid3 grid_norm(int nx, int ny, int planes)
+{
+    Grid3 g = grid3(nx, ny, 1);
+    const int per_plane = (int)(g.grid.x * g.grid.y);
+    const int zb = std::max(1, std::min(planes, (152 * 4 + per_plane - 1) / per_plane));
+    g.grid.z = (unsigned)zb;
+    return g;
+}
+
+template <typename T>
+void run_rbgs(cudaStream_t s, T* u, const T* f, Dims d, T h2, int color, int zero)
+{
+    const Grid3 g = grid3(d.nx / 2, d.ny, d.nz - 1);
+    k_rbgs<T><<<g.grid, g.block, 0, s>>>(u, f, d, h2, color, zero);
+}
+template <typename T>
+void run_resid(cudaStream_t s, const T* u, const T* f, T* r, Dims d, T inv_h2)
+{
+    const Grid3 g = grid3(d.nx, d.ny, d.nz - 1);
+    k_resid<T><<<g.grid, g.block, 0, s>>>(u, f, r, d, inv_h2);
+}
+template <typename T>
+void run_restrict(cudaStream_t s, const T* rf, T* fc, Dims df, Dims dc)
+{
+    const Grid3 g = grid3(dc.nx, dc.ny, dc.nz - 1);
+    k_restrict<T><<<g.grid, g.block, 0, s>>>(rf, fc, df, dc);
+}
+template <typename T>
+void run_prolong(cudaStream_t s, T* uf, const T* uc, Dims df, Dims dc)
+{
+    const Grid3 g = grid3(df.nx, df.ny, df.nz - 1);
+    k_prolong<T><<<g.grid, g.block, 0, s>>>(uf, uc, df, dc);
+}
+template <typename T>
+void run_resid64(cudaStream_t s, const double* phi, const T* e, const double* f, double* phi_out, T* r, double* norm2,
+                 Dims d, double inv_h2)
+{
+    const Grid3 g = grid_norm(d.nx, d.ny, d.nz - 1);
+    k_resid64<T><<<g.grid, g.block, 0, s>>>(phi, e, f, phi_out, r, norm2, d, inv_h2);
+    if (phi_out) {
+        const Grid3 g2 = grid3(d.nx, d.ny, 2);
+        k_copy_planes<<<g2.grid, g2.block, 0, s>>>(phi, phi_out, d);
+    }
+}
 
 template <typename T>
 void vcycle(pic_ctx* c, int l)
 {
+    const int nl = (int)c->mg.size();
+    if (l >= c->mg_tail) {
+        // every level from here down runs in one block
+        TailLevels<T> t{};
+        t.n = nl - l;
+        for (int q = 0; q < t.n; ++q) {
+            const MGLevel& L = c->mg[l + q];
+            t.nx[q] = L.nx; t.ny[q] = L.ny; t.nz[q] = L.nz; t.h[q] = L.h;
+            t.u[q] = (T*)L.u; t.f[q] = (T*)L.f; t.r[q] = (T*)L.r;
+        }
+        const MGLevel& C = c->mg.back();
+        const int n = C.nx * C.ny * (C.nz - 1);
+        t.ainv = (const T*)c->coarse_inv;
+        const int m = std::max(std::max(C.nx, C.ny), C.nz);
+        t.sweeps = std::min(4 * m * m + 16, 2000);
+        k_vcycle_tail<T><<<1, 1024, c->coarse_inv ? sizeof(T) * n : 0, c->stream>>>(t);
+        c->launches += 1;
+        return;
+    }
     MGLevel& L = c->mg[l];
     const Dims d{L.nx, L.ny, L.nz};
     const T h2 = (T)(L.h * L.h);
     T* u = (T*)L.u;
     T* f = (T*)L.f;
-    cudaMemsetAsync(u, 0, sizeof(T) * L.nodes, c->stream);
-    if (l + 1 == (int)c->mg.size()) {
-        if (c->coarse_inv) {
-            const int n = L.nx * L.ny * (L.nz - 1);
-            k_coarse_direct<T><<<1, 256, sizeof(T) * n, c->stream>>>(u, f, (const T*)c->coarse_inv, d);
-        } else {
-            const int m = std::max(std::max(L.nx, L.ny), L.nz);
-            const int sweeps = std::min(4 * m * m + 16, 2000);
-            k_coarse<T><<<1, 1024, 0, c->stream>>>(u, f, d, h2, sweeps);
-        }
-        c->launches += 1;
-        return;
-    }
-    const size_t half = (size_t)(L.nx / 2) * L.ny * (L.nz - 1);
-    for (int s = 0; s < 2; ++s)
-        for (int color = 0; color < 2; ++color)
-            k_rbgs<T><<<blocks(half), 256, 0, c->stream>>>(u, f, d, h2, color);
-    k_resid<T><<<blocks(L.nodes), 256, 0, c->stream>>>(u, f, (T*)L.r, d, (T)(1.0 / (L.h * L.h)));
+    // pre-smoothing from a zero guess: the first colour-0 pass needs no neighbours
+    run_rbgs<T>(c->stream, u, f, d, h2, 0, 1);
+    run_rbgs<T>(c->stream, u, f, d, h2, 1, 0);
+    run_rbgs<T>(c->stream, u, f, d, h2, 0, 0);
+    run_rbgs<T>(c->stream, u, f, d, h2, 1, 0);
+    run_resid<T>(c->stream, u, f, (T*)L.r, d, (T)(1.0 / (L.h * L.h)));
     MGLevel& C = c->mg[l + 1];
     const Dims dc{C.nx, C.ny, C.nz};
-    k_restrict<T><<<blocks(C.nodes), 256, 0, c->stream>>>((const T*)L.r, (T*)C.f, d, dc);
+    run_restrict<T>(c->stream, (const T*)L.r, (T*)C.f, d, dc);
     c->launches += 6;
     vcycle<T>(c, l + 1);
-    k_prolong<T><<<blocks(L.nodes), 256, 0, c->stream>>>(u, (const T*)C.u, d, dc);
+    run_prolong<T>(c->stream, u, (const T*)C.u, d, dc);
     c->launches += 5;
     for (int s = 0; s < 2; ++s)
-        for (int color = 0; color < 2; ++color)
-            k_rbgs<T><<<blocks(half), 256, 0, c->stream>>>(u, f, d, h2, color);
+        for (int color = 0; color < 2; ++color) run_rbgs<T>(c->stream, u, f, d, h2, color, 0);
 }
 
 template <typename T>
@@ -355,8 +580,7 @@ pic_status solve_t(pic_ctx* c, double tol, int max_iters, int* iters, double* re
     double h_norm[2];
     // initial residual (phi unchanged)
     cudaMemsetAsync(c->d_norm + 1, 0, sizeof(double), c->stream);
-    k_resid64<T><<<blocks(c->nodes), 256, 0, c->stream>>>(c->phi, (const T*)nullptr, c->f64, nullptr, (T*)L0.f,
-                                                          c->d_norm + 1, d, inv_h2);
+    run_resid64<T>(c->stream, c->phi, (const T*)nullptr, c->f64, nullptr, (T*)L0.f, c->d_norm + 1, d, inv_h2);
     c->launches += 1;
     if (!PIC_CUDA_OK(cudaMemcpyAsync(h_norm, c->d_norm, 2 * sizeof(double), cudaMemcpyDeviceToHost, c->stream)) ||
         !PIC_CUDA_OK(cudaStreamSynchronize(c->stream)))
@@ -369,9 +593,8 @@ pic_status solve_t(pic_ctx* c, double tol, int max_iters, int* iters, double* re
         if (!std::isfinite(rn)) break;
         vcycle<T>(c, 0);
         cudaMemsetAsync(c->d_norm + 1, 0, sizeof(double), c->stream);
-        k_resid64<T><<<blocks(c->nodes), 256, 0, c->stream>>>(c->phi, (const T*)L0.u, c->f64, c->phi_alt, (T*)L0.f,
-                                                              c->d_norm + 1, d, inv_h2);
-        c->launches += 1;
+        run_resid64<T>(c->stream, c->phi, (const T*)L0.u, c->f64, c->phi_alt, (T*)L0.f, c->d_norm + 1, d, inv_h2);
+        c->launches += 2;
         std::swap(c->phi, c->phi_alt);
         if (!PIC_CUDA_OK(cudaMemcpyAsync(h_norm + 1, c->d_norm + 1, sizeof(double), cudaMemcpyDeviceToHost,
                                          c->stream)) ||
@@ -396,10 +619,10 @@ void enqueue_iteration(pic_ctx* c, double tol, int max_iters, cudaGraphCondition
 {
     const Dims d{c->nx, c->ny, c->nz};
     vcycle<T>(c, 0);
-    k_add<T><<<blocks(c->nodes), 256, 0, c->stream>>>(c->phi, (const T*)c->mg[0].u, d);
-    k_resid64<T><<<blocks(c->nodes), 256, 0, c->stream>>>(c->phi, (const T*)nullptr, c->f64, nullptr,
-                                                          (T*)c->mg[0].f, c->d_norm + 1, d,
-                                                          1.0 / (c->dx * c->dx));
+    const Grid3 g = grid3(d.nx, d.ny, d.nz - 1);
+    k_add<T><<<g.grid, g.block, 0, c->stream>>>(c->phi, (const T*)c->mg[0].u, d);
+    run_resid64<T>(c->stream, c->phi, (const T*)nullptr, c->f64, nullptr, (T*)c->mg[0].f, c->d_norm + 1, d,
+                   1.0 / (c->dx * c->dx));
     k_conv<<<1, 1, 0, c->stream>>>(c->d_norm, c->d_iters, c->d_res, c->d_solve_flag, c->d_iter_total, tol * tol,
                                    max_iters, 0, h);
     c->launches += 3;
@@ -412,10 +635,10 @@ void enqueue_head(pic_ctx* c, double tol, int max_iters, cudaGraphConditionalHan
 {
     const Dims d{c->nx, c->ny, c->nz};
     cudaMemsetAsync(c->d_norm, 0, 2 * sizeof(double), c->stream);
-    k_rhs_dev<<<blocks(c->nodes), 256, 0, c->stream>>>(c->rq, c->f64, c->phi, d, c->sp, c->d_step, c->d_norm);
-    k_resid64<T><<<blocks(c->nodes), 256, 0, c->stream>>>(c->phi, (const T*)nullptr, c->f64, nullptr,
-                                                          (T*)c->mg[0].f, c->d_norm + 1, d,
-                                                          1.0 / (c->dx * c->dx));
+    const Grid3 g = grid_norm(d.nx, d.ny, d.nz + 1);
+    k_rhs_dev<<<g.grid, g.block, 0, c->stream>>>(c->rq, c->f64, c->phi, d, c->sp, c->d_step, c->d_norm);
+    run_resid64<T>(c->stream, c->phi, (const T*)nullptr, c->f64, nullptr, (T*)c->mg[0].f, c->d_norm + 1, d,
+                   1.0 / (c->dx * c->dx));
     k_conv<<<1, 1, 0, c->stream>>>(c->d_norm, c->d_iters, c->d_res, c->d_solve_flag, c->d_iter_total, tol * tol,
                                    max_iters, 1, h);
     c->launches += 3;
@@ -449,12 +672,21 @@ pic_status mg_setup(pic_ctx* c)
         L.f = dev_alloc(c, tsz * L.nodes);
         L.r = dev_alloc(c, tsz * L.nodes);
         if (!L.u || !L.f || !L.r) return PIC_ENOMEM;
+        // electrode planes of the corrections stay zero: they are never written
+        if (cudaMemset(L.u, 0, tsz * L.nodes) != cudaSuccess || cudaMemset(L.f, 0, tsz * L.nodes) != cudaSuccess ||
+            cudaMemset(L.r, 0, tsz * L.nodes) != cudaSuccess)
+            return PIC_ECUDA;
         c->mg.push_back(L);
         const bool can = nx % 2 == 0 && ny % 2 == 0 && nz % 2 == 0 && nx >= 4 && ny >= 4 && nz >= 4 &&
                          (nx / 2) % 2 == 0 && (ny / 2) % 2 == 0;
         if (!can) break;
         nx /= 2; ny /= 2; nz /= 2; h *= 2.0;
     }
+    // levels of at most kTailNodes nodes (and at most kTailMax of them) run in one block
+    c->mg_tail = (int)c->mg.size() - 1;
+    while (c->mg_tail > 0 && c->mg[c->mg_tail - 1].nodes <= kTailNodes &&
+           (int)c->mg.size() - (c->mg_tail - 1) <= kTailMax)
+        --c->mg_tail;
     // exact inverse of the coarsest operator (6 u - neighbour sum) / h^2 with
     // zero values on the electrode planes, by Gauss-Jordan elimination
     const MGLevel& L = c->mg.back();
@@ -517,8 +749,9 @@ void launch_rhs(pic_ctx* c, double scale, double v_bot, double v_top, bool)
 {
     const Dims d{c->nx, c->ny, c->nz};
     cudaMemsetAsync(c->d_norm, 0, sizeof(double), c->stream);
-    k_rhs<<<blocks(c->nodes), 256, 0, c->stream>>>(c->rq, scale, c->f64, c->phi, c->phi_alt, v_bot, v_top, d,
-                                                  1.0 / (c->dx * c->dx), c->d_norm);
+    const Grid3 g = grid_norm(d.nx, d.ny, d.nz + 1);
+    k_rhs<<<g.grid, g.block, 0, c->stream>>>(c->rq, scale, c->f64, c->phi, c->phi_alt, v_bot, v_top, d,
+                                            1.0 / (c->dx * c->dx), c->d_norm);
     c->launches += 1;
 }
 
@@ -590,15 +823,15 @@ void na_vcycle(NaCtx& c, int l)
     }
     const size_t half = (size_t)(L.nx / 2) * L.ny * (L.nz - 1);
     for (int s = 0; s < 2; ++s)
-        for (int color = 0; color < 2; ++color) k_rbgs<T><<<blocks(half), 256, 0, c.s>>>(u, f, d, h2, color);
-    k_resid<T><<<blocks(L.nodes), 256, 0, c.s>>>(u, f, (T*)L.r, d, (T)(1.0 / (L.h * L.h)));
+        for (int color = 0; color < 2; ++color) run_rbgs<T>(c.s, u, f, d, h2, color, 0);
+    run_resid<T>(c.s, u, f, (T*)L.r, d, (T)(1.0 / (L.h * L.h)));
     MGLevel& C = c.lv[l + 1];
     const Dims dc{C.nx, C.ny, C.nz};
-    k_restrict<T><<<blocks(C.nodes), 256, 0, c.s>>>((const T*)L.r, (T*)C.f, d, dc);
+    run_restrict<T>(c.s, (const T*)L.r, (T*)C.f, d, dc);
     na_vcycle<T>(c, l + 1);
-    k_prolong<T><<<blocks(L.nodes), 256, 0, c.s>>>(u, (const T*)C.u, d, dc);
+    run_prolong<T>(c.s, u, (const T*)C.u, d, dc);
     for (int s = 0; s < 2; ++s)
-        for (int color = 0; color < 2; ++color) k_rbgs<T><<<blocks(half), 256, 0, c.s>>>(u, f, d, h2, color);
+        for (int color = 0; color < 2; ++color) run_rbgs<T>(c.s, u, f, d, h2, color, 0);
 }
 
 template <typename T>
@@ -611,8 +844,7 @@ pic_status na_solve(NaCtx& c, double* phi_user, double* phi_alt, const double* f
     double* phi = phi_user;
     double* alt = phi_alt;
     cudaMemsetAsync(norm + 1, 0, sizeof(double), c.s);
-    k_resid64<T><<<blocks(nodes), 256, 0, c.s>>>(phi, (const T*)nullptr, f64, nullptr, (T*)c.lv[0].f, norm + 1, d,
-                                                 inv_h2);
+    run_resid64<T>(c.s, phi, (const T*)nullptr, f64, nullptr, (T*)c.lv[0].f, norm + 1, d, inv_h2);
     if (cudaMemcpyAsync(h_norm, norm, 2 * sizeof(double), cudaMemcpyDeviceToHost, c.s) != cudaSuccess ||
         cudaStreamSynchronize(c.s) != cudaSuccess)
         return PIC_ECUDA;
@@ -623,8 +855,7 @@ pic_status na_solve(NaCtx& c, double* phi_user, double* phi_alt, const double* f
     while (!(rn <= target) && it < max_iters && std::isfinite(rn)) {
         na_vcycle<T>(c, 0);
         cudaMemsetAsync(norm + 1, 0, sizeof(double), c.s);
-        k_resid64<T><<<blocks(nodes), 256, 0, c.s>>>(phi, (const T*)c.lv[0].u, f64, alt, (T*)c.lv[0].f, norm + 1, d,
-                                                     inv_h2);
+        run_resid64<T>(c.s, phi, (const T*)c.lv[0].u, f64, alt, (T*)c.lv[0].f, norm + 1, d, inv_h2);
         std::swap(phi, alt);
         if (cudaMemcpyAsync(h_norm + 1, norm + 1, sizeof(double), cudaMemcpyDeviceToHost, c.s) != cudaSuccess ||
             cudaStreamSynchronize(c.s) != cudaSuccess)
@@ -703,8 +934,9 @@ extern "C" pic_status pic_solve_noalloc(int32_t nx, int32_t ny, int32_t nz, doub
     // rhs from the fixed-point charge; electrode values on both potential buffers
     const Dims d{nx, ny, nz};
     cudaMemsetAsync(norm, 0, sizeof(double), c.s);
-    k_rhs<<<blocks(nodes), 256, 0, c.s>>>((const unsigned long long*)rho_q_dev, scale, f64, phi_dev, phi_alt, v_bot,
-                                          v_top, d, 1.0 / (dx * dx), norm);
+    const Grid3 g = grid_norm(nx, ny, nz + 1);
+    k_rhs<<<g.grid, g.block, 0, c.s>>>((const unsigned long long*)rho_q_dev, scale, f64, phi_dev, phi_alt, v_bot,
+                                      v_top, d, 1.0 / (dx * dx), norm);
     int it = 0;
     double res = 0.0;
     st = prec == PIC_MIXED ? na_solve<float>(c, phi_dev, phi_alt, f64, norm, d, dx, tol, max_iters, &it, &res)

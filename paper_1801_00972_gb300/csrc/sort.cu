@@ -13,16 +13,23 @@ constexpr int kScanThreads = 256;
 constexpr int kScanPer = 4;
 constexpr int kScanBlock = kScanThreads * kScanPer;
 
-__device__ __forceinline__ int key_of(const float4& p) { return __float_as_int(p.w); }
-__device__ __forceinline__ int key_of(const double4& p) { return p.w < 0.0 ? -1 : (int)p.w; }
+// linear cell index (k*ny + j)*nx + i, or -1 for a dead slot
+__device__ __forceinline__ int key_of(const float4& p, int nx, int ny)
+{
+    const int c = __float_as_int(p.w);   // packed i | j << 10 | k << 20
+    if (c < 0) return -1;
+    return ((c >> 20) * ny + ((c >> 10) & 1023)) * nx + (c & 1023);
+}
+__device__ __forceinline__ int key_of(const double4& p, int, int) { return p.w < 0.0 ? -1 : (int)p.w; }
 
 template <typename T4>
-__global__ void k_hist(const T4* __restrict__ pos, const unsigned long long* nslot, int sp, unsigned int* hist)
+__global__ void k_hist(const T4* __restrict__ pos, const unsigned long long* nslot, int sp, unsigned int* hist, int nx,
+                       int ny)
 {
     const unsigned long long n = nslot[sp];
     for (unsigned long long q = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; q < n;
          q += (unsigned long long)gridDim.x * blockDim.x) {
-        const int c = key_of(pos[q]);
+        const int c = key_of(pos[q], nx, ny);
         if (c >= 0) atomicAdd(hist + c, 1u);
     }
 }
@@ -75,13 +82,14 @@ __global__ void k_scan_add(unsigned int* out, const unsigned int* offs, size_t n
 
 template <typename T4>
 __global__ void k_scatter(const T4* __restrict__ pos, const T4* __restrict__ vel, const unsigned long long* nslot,
-                          int sp, unsigned int* cursor, T4* __restrict__ pos_out, T4* __restrict__ vel_out)
+                          int sp, unsigned int* cursor, T4* __restrict__ pos_out, T4* __restrict__ vel_out, int nx,
+                          int ny)
 {
     const unsigned long long n = nslot[sp];
     for (unsigned long long q = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; q < n;
          q += (unsigned long long)gridDim.x * blockDim.x) {
         const T4 p = pos[q];
-        const int c = key_of(p);
+        const int c = key_of(p, nx, ny);
         if (c < 0) continue;
         const unsigned int d = atomicAdd(cursor + c, 1u);
         pos_out[d] = p;
@@ -136,18 +144,20 @@ void sort_particles(pic_ctx* c, int sp)
     cudaMemsetAsync(c->cursor, 0, sizeof(unsigned int) * nc, c->stream);
     const int grid = grid_for(c->cap[sp], 256, 152 * 8);
     if (c->prec == PIC_MIXED)
-        k_hist<float4><<<grid, 256, 0, c->stream>>>((const float4*)c->pos[sp], c->d_nslot, sp, c->cursor);
+        k_hist<float4><<<grid, 256, 0, c->stream>>>((const float4*)c->pos[sp], c->d_nslot, sp, c->cursor, c->nx,
+                                                    c->ny);
     else
-        k_hist<double4><<<grid, 256, 0, c->stream>>>((const double4*)c->pos[sp], c->d_nslot, sp, c->cursor);
+        k_hist<double4><<<grid, 256, 0, c->stream>>>((const double4*)c->pos[sp], c->d_nslot, sp, c->cursor, c->nx,
+                                                     c->ny);
     scan(c, c->cursor, nc, 0);
     if (c->prec == PIC_MIXED)
         k_scatter<float4><<<grid, 256, 0, c->stream>>>((const float4*)c->pos[sp], (const float4*)c->vel[sp],
                                                        c->d_nslot, sp, c->cursor, (float4*)c->pos_alt[sp],
-                                                       (float4*)c->vel_alt[sp]);
+                                                       (float4*)c->vel_alt[sp], c->nx, c->ny);
     else
         k_scatter<double4><<<grid, 256, 0, c->stream>>>((const double4*)c->pos[sp], (const double4*)c->vel[sp],
                                                         c->d_nslot, sp, c->cursor, (double4*)c->pos_alt[sp],
-                                                        (double4*)c->vel_alt[sp]);
+                                                        (double4*)c->vel_alt[sp], c->nx, c->ny);
     // the last scan level's single block sum is the number of live particles
     k_set_nslot<<<1, 1, 0, c->stream>>>(c->d_nslot, sp, c->scan_tmp.back());
     c->launches += 3;
