@@ -45,6 +45,7 @@ def args():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--eager", action="store_true", help="no CUDA graphs (for profilers)")
+    ap.add_argument("--no-batch", action="store_true")
     return ap.parse_args()
 
 
@@ -164,6 +165,28 @@ def e2e(P, wl, parts, prec, steps, stream):
             "note": "pic_init from host arrays + per-step pic_step(1) and pic_grain_charges"}
 
 
+def batch_bench(P, I, steps, warmup):
+    """The 48-run ensemble stepped concurrently (pic_batch_step).  pic_batch_step
+    returns after every run's stream has finished, so host timestamps around
+    it bracket the device work."""
+    import torch
+    wls = I.ensemble()
+    parts = [I.sample_particles(w) for w in wls]
+    b = P.Batch(wls, parts, prec=P.PIC_MIXED, sort_every=SORT_EVERY)
+    b.step(warmup)
+    c0 = sum(P.pic_counts(r)[1]["pushed"] for r in b.runs)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    b.step(steps)
+    t = time.perf_counter() - t0
+    c1 = sum(P.pic_counts(r)[1]["pushed"] for r in b.runs)
+    b.close()
+    return {"workload": f"{len(wls)} independent runs, meshes 32^3..64x64x128, "
+                        f"{sum(w.n_e + w.n_i for w in wls):.3g} particles in all, 1-10 Pa, 1-19 grains",
+            "value": (c1 - c0) / t, "unit": "particle-steps/s", "steps": steps, "ms_per_step": 1000 * t / steps,
+            "timing": "host clock around pic_batch_step (synchronises all run streams)"}
+
+
 def oracle_sample(wl, n_particles, steps, seed=1):
     """The CPU oracle, as it stands, on a bounded sample of the workload: the same
     mesh, grains and gas with n_particles macroparticles (init excluded)."""
@@ -242,6 +265,7 @@ def main():
         fp64 = run_gpu(P, I, wl, parts, P.PIC_FP64, a.fp64_steps or max(a.steps // 4, 10), a.warmup, stream, local,
                        flags)
     ee = None if a.no_e2e else e2e(P, wl, parts, P.PIC_MIXED, max(a.steps // 4, 10), stream)
+    bb = None if (a.no_batch or world > 1) else batch_bench(P, I, max(a.steps // 4, 10), a.warmup)
 
     def agg(x):
         if x is None:
@@ -307,6 +331,8 @@ def main():
                         "mixed_speedup": (m_tot / m_ms) / (f[1] / f[0])}
     if ee is not None:
         line["e2e"] = ee
+    if bb is not None:
+        line["batch"] = bb
     if not a.no_cpu:
         v, t, n0 = oracle_sample(wl, 400_000, 4)
         line["cpu_baseline"] = {"value": v, "unit": "particle-steps/s", "cores": 1, "kind": "oracle",

@@ -184,6 +184,21 @@ pic_status pic_profile(pic_ctx* ctx, int32_t enable);
 pic_status pic_profile_read(pic_ctx* ctx, double* push_ms, int64_t* push_launches, double* solve_ms,
                             int64_t* solves, int64_t* solve_iterations, int64_t* kernels_launched);
 
+/* Batched ensemble: n independent runs (seeds, rf phases, pressures, grain
+ * clusters, meshes of different sizes), each described by element r of the
+ * argument arrays exactly as for pic_init.  The batch gives every run its own
+ * CUDA stream; pic_batch_step queues each run's step graphs on its stream, so
+ * the runs execute concurrently on the GPU, and returns after all of them
+ * (the first failing run's status).  Results of a run are identical to the
+ * same run made alone with pic_init/pic_step.  pic_batch_run lends run r's
+ * context to the query calls (do not pass it to pic_destroy). */
+typedef struct pic_batch pic_batch;
+pic_status pic_batch_init(int32_t n, const pic_mesh* meshes, const pic_electrodes* els, const pic_gas* gases,
+                          const pic_grains* grains, const pic_run* runs, pic_batch** out);
+pic_status pic_batch_step(pic_batch* b, int32_t n_steps);
+pic_ctx*   pic_batch_run(pic_batch* b, int32_t r);
+void       pic_batch_destroy(pic_batch* b);
+
 /* Poisson solve that allocates nothing.  The paper has no counterpart: this is
  * a service for callers that cannot call cudaMalloc, such as a host application
  * whose own memory manager has already reserved the device memory (an extra

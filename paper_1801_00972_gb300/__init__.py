@@ -34,7 +34,8 @@ PIC_C_N = len(COUNTERS)
 SYMBOLS = ("pic_init", "pic_step", "pic_advance", "pic_solve", "pic_grain_charges", "pic_counts",
            "pic_moments", "pic_get_particles", "pic_get_rho", "pic_get_phi", "pic_set_phi",
            "pic_get_grain_table", "pic_set_grain_table", "pic_set_grain_counts", "pic_step_index",
-           "pic_profile", "pic_profile_read", "pic_solve_noalloc", "pic_last_error", "pic_destroy")
+           "pic_profile", "pic_profile_read", "pic_solve_noalloc", "pic_batch_init", "pic_batch_step",
+           "pic_batch_run", "pic_batch_destroy", "pic_last_error", "pic_destroy")
 
 
 class pic_mesh(C.Structure):
@@ -102,6 +103,15 @@ def load(path: str | None = None):
             f.argtypes = args
             f.restype = C.c_int
         L.pic_init.restype = C.c_int
+        L.pic_batch_init.argtypes = [i32, C.POINTER(pic_mesh), C.POINTER(pic_electrodes), C.POINTER(pic_gas),
+                                     C.POINTER(pic_grains), C.POINTER(pic_run), C.POINTER(vp)]
+        L.pic_batch_init.restype = C.c_int
+        L.pic_batch_step.argtypes = [vp, i32]
+        L.pic_batch_step.restype = C.c_int
+        L.pic_batch_run.argtypes = [vp, i32]
+        L.pic_batch_run.restype = vp
+        L.pic_batch_destroy.argtypes = [vp]
+        L.pic_batch_destroy.restype = None
         L.pic_step_index.argtypes = [vp]
         L.pic_step_index.restype = i64
         L.pic_last_error.argtypes = [vp]
@@ -248,6 +258,67 @@ def pic_destroy(ctx):
 
 
 # ----------------------------------------------------------------- convenience
+def make_args(wl, particles, prec=PIC_MIXED, flags=0, capacity=None, sort_every=20, tol=1e-10, max_cycles=60,
+              md_sub=None):
+    """The pic_init argument structures for a workload; returns them with the
+    numpy arrays they point into (keep those alive while the call runs)."""
+    keep = []
+    mesh = pic_mesh(wl.nx, wl.ny, wl.nz, wl.dx)
+    el = pic_electrodes(wl.v_dc, wl.v_rf, wl.f_rf, wl.phase, wl.v_top)
+    xs = np.ascontiguousarray(wl.xs, dtype=np.float64)
+    keep.append(xs)
+    gas = pic_gas(wl.n_gas, wl.t_gas, wl.eps_exc, wl.eps_ion, wl.nu_max_e, wl.nu_max_i, wl.de_e, wl.de_i,
+                  xs.shape[1], _p(xs, C.c_double))
+    gp = np.ascontiguousarray(wl.grain_pos, dtype=np.float64).reshape(-1)
+    gr = np.ascontiguousarray(wl.grain_r, dtype=np.float64).reshape(-1)
+    keep += [gp, gr]
+    grains = pic_grains(gr.size, _p(gp, C.c_double), _p(gr, C.c_double))
+    run = pic_run()
+    for sp in range(2):
+        x, v, ids = particles[sp]
+        x = np.ascontiguousarray(x, dtype=np.float64).reshape(-1)
+        v = np.ascontiguousarray(v, dtype=np.float64).reshape(-1)
+        ids = np.ascontiguousarray(ids, dtype=np.uint32).reshape(-1)
+        keep += [x, v, ids]
+        run.n[sp] = ids.size
+        run.x_host[sp] = _p(x, C.c_double)
+        run.v_host[sp] = _p(v, C.c_double)
+        run.id_host[sp] = _p(ids, C.c_uint32)
+        run.capacity[sp] = capacity[sp] if capacity is not None else int(ids.size * 1.25) + 4096
+    run.weight, run.dt = wl.weight, wl.dt
+    run.md_sub = wl.md_sub if md_sub is None else md_sub
+    run.sort_every = sort_every
+    run.seed, run.run_id, run.prec, run.flags = wl.seed, wl.run_id, prec, flags
+    run.tol, run.max_cycles = tol, max_cycles
+    return (mesh, el, gas, grains, run), keep
+
+
+class Batch:
+    """An ensemble of independent runs stepped concurrently (pic_batch_*)."""
+
+    def __init__(self, workloads, particles, **kw):
+        n = len(workloads)
+        args = [make_args(w, p, **kw) for w, p in zip(workloads, particles)]
+        arrs = [(t * n)(*[a[0][q] for a in args]) for q, t in
+                enumerate((pic_mesh, pic_electrodes, pic_gas, pic_grains, pic_run))]
+        h = C.c_void_p()
+        _check(None, load().pic_batch_init(n, *arrs, C.byref(h)))
+        self.h = h
+        self.n = n
+        self.workloads = workloads
+        self.runs = [load().pic_batch_run(h, r) for r in range(n)]
+
+    def step(self, n=1):
+        _check(None, load().pic_batch_step(self.h, int(n)))
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().pic_batch_destroy(self.h)
+            self.h = None
+
+    __del__ = close
+
+
 class Run:
     """One run context built from a workload description (see ``inputs.Workload``)
     and initial particles [(x, v, id) for electrons, ions] in SI units."""

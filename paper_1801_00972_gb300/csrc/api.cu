@@ -691,9 +691,13 @@ pic_status pic_solve(pic_ctx* c, int32_t* iterations, double* rel_residual)
     return chk;
 }
 
-pic_status pic_step(pic_ctx* c, int32_t n_steps)
+}  // extern "C"
+
+namespace {
+
+// queue n steps on the run's stream; no final synchronisation
+pic_status step_enqueue(pic_ctx* c, int32_t n_steps)
 {
-    if (!c || n_steps < 0) return PIC_EINVAL;
     if (c->pending != PIC_OK) {
         const pic_status p = c->pending;
         c->pending = PIC_OK;
@@ -715,7 +719,7 @@ pic_status pic_step(pic_ctx* c, int32_t n_steps)
                 c->msteps += 1;
             }
         }
-        return check(c);
+        return PIC_OK;
     }
     for (int32_t s = 0; s < n_steps; ++s) {
         const bool sort = c->sort_every > 0 && (c->step + 1) % c->sort_every == 0;
@@ -746,7 +750,84 @@ pic_status pic_step(pic_ctx* c, int32_t n_steps)
             c->msteps += 1;
         }
     }
+    return PIC_OK;
+}
+
+}  // namespace
+
+struct pic_batch {
+    std::vector<pic_ctx*> runs;
+    std::vector<cudaStream_t> streams;
+};
+
+extern "C" {
+
+pic_status pic_step(pic_ctx* c, int32_t n_steps)
+{
+    if (!c || n_steps < 0) return PIC_EINVAL;
+    const pic_status r = step_enqueue(c, n_steps);
+    if (r != PIC_OK) return r;
     return check(c);
+}
+
+pic_status pic_batch_init(int32_t n, const pic_mesh* meshes, const pic_electrodes* els, const pic_gas* gases,
+                          const pic_grains* grains, const pic_run* runs, pic_batch** out)
+{
+    g_init_error.clear();
+    if (!out || n < 1 || !meshes || !els || !gases || !grains || !runs)
+        return fail(nullptr, PIC_EINVAL, "pic_batch_init: need n >= 1 and the five argument arrays");
+    *out = nullptr;
+    pic_batch* b = new (std::nothrow) pic_batch();
+    if (!b) return fail(nullptr, PIC_ENOMEM, "host allocation");
+    for (int32_t r = 0; r < n; ++r) {
+        cudaStream_t s = nullptr;
+        cudaError_t e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+        pic_ctx* c = nullptr;
+        pic_status st = e == cudaSuccess ? pic_init(meshes + r, els + r, gases + r, grains + r, runs + r, s, &c)
+                                         : PIC_ECUDA;
+        if (st != PIC_OK) {
+            const std::string m = "run " + std::to_string(r) + ": " +
+                                  (e == cudaSuccess ? g_init_error : std::string(cudaGetErrorString(e)));
+            if (s) cudaStreamDestroy(s);
+            pic_batch_destroy(b);
+            return fail(nullptr, st, m);
+        }
+        b->runs.push_back(c);
+        b->streams.push_back(s);
+    }
+    *out = b;
+    return PIC_OK;
+}
+
+pic_status pic_batch_step(pic_batch* b, int32_t n_steps)
+{
+    if (!b || n_steps < 0) return PIC_EINVAL;
+    pic_status first = PIC_OK;
+    // one step of every run at a time, so the runs advance side by side
+    for (int32_t s = 0; s < n_steps && first == PIC_OK; ++s)
+        for (pic_ctx* c : b->runs) {
+            const pic_status r = step_enqueue(c, 1);
+            if (r != PIC_OK && first == PIC_OK) first = r;
+        }
+    for (pic_ctx* c : b->runs) {
+        const pic_status r = check(c);
+        if (r != PIC_OK && first == PIC_OK) first = r;
+    }
+    return first;
+}
+
+pic_ctx* pic_batch_run(pic_batch* b, int32_t r)
+{
+    if (!b || r < 0 || r >= (int32_t)b->runs.size()) return nullptr;
+    return b->runs[r];
+}
+
+void pic_batch_destroy(pic_batch* b)
+{
+    if (!b) return;
+    for (pic_ctx* c : b->runs) pic_destroy(c);
+    for (cudaStream_t s : b->streams) cudaStreamDestroy(s);
+    delete b;
 }
 
 pic_status pic_grain_charges(pic_ctx* c, int64_t* n_abs_host, double* q_host)

@@ -105,7 +105,8 @@ struct RStream {
 
 // ---------------------------------------------------------------- context
 constexpr int kMaxDense = 1024;   // coarsest-level unknowns solved with a dense inverse
-constexpr size_t kTailNodes = 2500;   // levels this small run together in one block
+constexpr size_t kTailSmem = 200 * 1024;   // shared memory of the one-block tail of a V-cycle
+constexpr size_t kTailNodes = 2500;         // largest level in that tail
 
 // constants of the graph solve's right-hand side and electrode values
 struct SolveParams {

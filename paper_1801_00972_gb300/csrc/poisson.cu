@@ -405,6 +405,41 @@ __device__ void tail_restrict(const T* rf, T* fc, Dims df, Dims dc)
     __syncthreads();
 }
 
+// restriction of the residual f - A u computed on the fly at the 27 fine points
+template <typename T>
+__device__ void tail_resid_restrict(const T* u, const T* f, T* fc, Dims df, Dims dc, T inv_h2)
+{
+    const int P = dc.nx * dc.ny;
+    const int N = P * (dc.nz - 1);
+    const int Pf = df.nx * df.ny;
+    for (int t = threadIdx.x; t < N; t += blockDim.x) {
+        const int n = P + t;
+        const int K = n / P;
+        const int I = n % dc.nx, J = (n / dc.nx) % dc.ny;
+        T acc = (T)0;
+        for (int dk = -1; dk <= 1; ++dk) {
+            const T wk = dk == 0 ? (T)0.5 : (T)0.25;
+            const int k = 2 * K + dk;
+            for (int dj = -1; dj <= 1; ++dj) {
+                const T wj = dj == 0 ? (T)0.5 : (T)0.25;
+                const int j = (2 * J + dj + df.ny) % df.ny;
+                const int jp = (j + 1 == df.ny) ? 0 : j + 1, jm = (j == 0) ? df.ny - 1 : j - 1;
+                for (int di = -1; di <= 1; ++di) {
+                    const T wi = di == 0 ? (T)0.5 : (T)0.25;
+                    const int i = (2 * I + di + df.nx) % df.nx;
+                    const int ip = (i + 1 == df.nx) ? 0 : i + 1, im = (i == 0) ? df.nx - 1 : i - 1;
+                    const int m = k * Pf + j * df.nx + i;
+                    const T sum = u[m - i + ip] + u[m - i + im] + u[k * Pf + jp * df.nx + i] +
+                                  u[k * Pf + jm * df.nx + i] + u[m + Pf] + u[m - Pf];
+                    acc += (wk * wj * wi) * (f[m] - ((T)6 * u[m] - sum) * inv_h2);
+                }
+            }
+        }
+        fc[n] = acc;
+    }
+    __syncthreads();
+}
+
 template <typename T>
 __device__ void tail_prolong(T* uf, const T* uc, Dims df, Dims dc)
 {
@@ -428,54 +463,83 @@ __device__ void tail_prolong(T* uf, const T* uc, Dims df, Dims dc)
     __syncthreads();
 }
 
-// pre-smoothing, residual and restriction down the tail, the coarsest solve,
-// then prolongation and post-smoothing back up: the lower part of a V(2,2) cycle
+// The lower part of a V(2,2) cycle in one block with every tail level held in
+// shared memory: pre-smoothing from a zero guess, residual restricted to the
+// next level, the coarsest solve, prolongation and post-smoothing.  Global
+// memory is touched only to read the first tail level's right-hand side and
+// write back its correction.
 template <typename T>
 __global__ void __launch_bounds__(1024) k_vcycle_tail(const TailLevels<T> L)
 {
-    extern __shared__ unsigned char smem[];
+    extern __shared__ __align__(16) unsigned char smem[];
+    T* su[kTailMax];
+    T* sf[kTailMax];
+    {
+        T* p = reinterpret_cast<T*>(smem);
+        for (int l = 0; l < L.n; ++l) {
+            const int nodes = L.nx[l] * L.ny[l] * (L.nz[l] + 1);
+            su[l] = p; p += nodes;
+            sf[l] = p; p += nodes;
+        }
+        // corrections start at zero (electrode planes stay zero); first rhs from global
+        for (int l = 0; l < L.n; ++l) {
+            const int nodes = L.nx[l] * L.ny[l] * (L.nz[l] + 1);
+            for (int t = threadIdx.x; t < nodes; t += blockDim.x) {
+                su[l][t] = (T)0;
+                sf[l][t] = l == 0 ? L.f[0][t] : (T)0;
+            }
+        }
+        __syncthreads();
+    }
     for (int l = 0; l + 1 < L.n; ++l) {
         const Dims d{L.nx[l], L.ny[l], L.nz[l]};
         const T h2 = (T)(L.h[l] * L.h[l]);
-        tail_rbgs<T>(L.u[l], L.f[l], d, h2, 0, true);
-        tail_rbgs<T>(L.u[l], L.f[l], d, h2, 1, false);
-        tail_rbgs<T>(L.u[l], L.f[l], d, h2, 0, false);
-        tail_rbgs<T>(L.u[l], L.f[l], d, h2, 1, false);
-        tail_resid<T>(L.u[l], L.f[l], L.r[l], d, (T)(1.0 / (L.h[l] * L.h[l])));
-        tail_restrict<T>(L.r[l], L.f[l + 1], d, Dims{L.nx[l + 1], L.ny[l + 1], L.nz[l + 1]});
+        tail_rbgs<T>(su[l], sf[l], d, h2, 0, true);
+        tail_rbgs<T>(su[l], sf[l], d, h2, 1, false);
+        tail_rbgs<T>(su[l], sf[l], d, h2, 0, false);
+        tail_rbgs<T>(su[l], sf[l], d, h2, 1, false);
+        tail_resid_restrict<T>(su[l], sf[l], sf[l + 1], d, Dims{L.nx[l + 1], L.ny[l + 1], L.nz[l + 1]},
+                               (T)(1.0 / (L.h[l] * L.h[l])));
     }
     {
         const int c = L.n - 1;
         const Dims d{L.nx[c], L.ny[c], L.nz[c]};
         const int P = d.nx * d.ny, n = P * (d.nz - 1);
         if (L.ainv) {
-            T* fi = reinterpret_cast<T*>(smem);
-            for (int m = threadIdx.x; m < n; m += blockDim.x) fi[m] = L.f[c][P + m];
-            __syncthreads();
             for (int m = threadIdx.x; m < n; m += blockDim.x) {
                 const T* row = L.ainv + (size_t)m * n;
                 T acc = (T)0;
-                for (int q = 0; q < n; ++q) acc += row[q] * fi[q];
-                L.u[c][P + m] = acc;
+                for (int q = 0; q < n; ++q) acc += row[q] * sf[c][P + q];
+                su[c][P + m] = acc;
             }
             __syncthreads();
         } else {
             const T h2 = (T)(L.h[c] * L.h[c]);
             for (int s = 0; s < L.sweeps; ++s) {
-                tail_rbgs<T>(L.u[c], L.f[c], d, h2, 0, s == 0);
-                tail_rbgs<T>(L.u[c], L.f[c], d, h2, 1, false);
+                tail_rbgs<T>(su[c], sf[c], d, h2, 0, s == 0);
+                tail_rbgs<T>(su[c], sf[c], d, h2, 1, false);
             }
         }
     }
     for (int l = L.n - 2; l >= 0; --l) {
         const Dims d{L.nx[l], L.ny[l], L.nz[l]};
         const T h2 = (T)(L.h[l] * L.h[l]);
-        tail_prolong<T>(L.u[l], L.u[l + 1], d, Dims{L.nx[l + 1], L.ny[l + 1], L.nz[l + 1]});
-        tail_rbgs<T>(L.u[l], L.f[l], d, h2, 0, false);
-        tail_rbgs<T>(L.u[l], L.f[l], d, h2, 1, false);
-        tail_rbgs<T>(L.u[l], L.f[l], d, h2, 0, false);
-        tail_rbgs<T>(L.u[l], L.f[l], d, h2, 1, false);
+        tail_prolong<T>(su[l], su[l + 1], d, Dims{L.nx[l + 1], L.ny[l + 1], L.nz[l + 1]});
+        tail_rbgs<T>(su[l], sf[l], d, h2, 0, false);
+        tail_rbgs<T>(su[l], sf[l], d, h2, 1, false);
+        tail_rbgs<T>(su[l], sf[l], d, h2, 0, false);
+        tail_rbgs<T>(su[l], sf[l], d, h2, 1, false);
     }
+    const int nodes0 = L.nx[0] * L.ny[0] * (L.nz[0] + 1);
+    for (int t = threadIdx.x; t < nodes0; t += blockDim.x) L.u[0][t] = su[0][t];
+}
+
+template <typename T>
+size_t tail_smem(const pic_ctx* c, int l0)
+{
+    size_t b = 0;
+    for (size_t l = (size_t)l0; l < c->mg.size(); ++l) b += 2 * sizeof(T) * c->mg[l].nodes;
+    return b;
 }
 
 int blocks(size_t n) { return grid_for((int64_t)n, 256, 152 * 8); }
@@ -545,7 +609,8 @@ void vcycle(pic_ctx* c, int l)
         t.ainv = (const T*)c->coarse_inv;
         const int m = std::max(std::max(C.nx, C.ny), C.nz);
         t.sweeps = std::min(4 * m * m + 16, 2000);
-        k_vcycle_tail<T><<<1, 1024, c->coarse_inv ? sizeof(T) * n : 0, c->stream>>>(t);
+        (void)n;
+        k_vcycle_tail<T><<<1, 1024, tail_smem<T>(c, l), c->stream>>>(t);
         c->launches += 1;
         return;
     }
@@ -682,11 +747,24 @@ pic_status mg_setup(pic_ctx* c)
         if (!can) break;
         nx /= 2; ny /= 2; nz /= 2; h *= 2.0;
     }
-    // levels of at most kTailNodes nodes (and at most kTailMax of them) run in one block
+    // the smallest levels (each at most kTailNodes nodes, at most kTailMax of them,
+    // together at most kTailSmem bytes of u and f) run in one block from shared
+    // memory; larger levels are faster as grid-wide launches
     c->mg_tail = (int)c->mg.size() - 1;
-    while (c->mg_tail > 0 && c->mg[c->mg_tail - 1].nodes <= kTailNodes &&
+    auto smem_from = [&](int l0) {
+        size_t b = 0;
+        for (size_t l = (size_t)l0; l < c->mg.size(); ++l) b += 2 * tsz * c->mg[l].nodes;
+        return b;
+    };
+    while (c->mg_tail > 0 && smem_from(c->mg_tail - 1) <= kTailSmem && c->mg[c->mg_tail - 1].nodes <= kTailNodes &&
            (int)c->mg.size() - (c->mg_tail - 1) <= kTailMax)
         --c->mg_tail;
+    {
+        const cudaError_t e = c->prec == PIC_MIXED
+            ? cudaFuncSetAttribute(k_vcycle_tail<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTailSmem)
+            : cudaFuncSetAttribute(k_vcycle_tail<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTailSmem);
+        if (e != cudaSuccess) return PIC_ECUDA;
+    }
     // exact inverse of the coarsest operator (6 u - neighbour sum) / h^2 with
     // zero values on the electrode planes, by Gauss-Jordan elimination
     const MGLevel& L = c->mg.back();

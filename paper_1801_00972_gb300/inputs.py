@@ -212,6 +212,34 @@ def workload(index: int, **over) -> Workload:
     return Workload(**args)
 
 
+def ensemble(n_runs: int = 48, seed: int = BASE_SEED + 3):
+    """The batched-ensemble workload: independent runs of uneven size.  Per run:
+    mesh from {32^3, 32x32x64, 64x64x64, 64x64x128} cells of 0.2 mm, 1e5..2e6
+    particles (log-uniform), argon at 1..10 Pa, 1..19 grains of 4-5 um in a
+    shell-shaped cluster 5.6 mm above the driven electrode (capped for the
+    smallest meshes), 100 V at 13.56 MHz with a random phase."""
+    rng = np.random.default_rng(seed)
+    shapes = [(32, 32, 32), (32, 32, 64), (64, 64, 64), (64, 64, 128)]
+    dx = 0.2e-3
+    out = []
+    for r in range(n_runs):
+        nx, ny, nz = shapes[int(rng.integers(len(shapes)))]
+        n_p = int(round(10 ** rng.uniform(5.0, math.log10(2e6))))
+        p_pa = float(rng.uniform(1.0, 10.0))
+        n_g = int(rng.integers(1, 20))
+        L = (nx * dx, ny * dx, nz * dx)
+        zc = min(5.6e-3, 0.5 * L[2])
+        gpos, grad = sphere_cluster(n_g, min(0.8e-3, 0.2 * L[0]), (L[0] / 2, L[1] / 2, zc), 4e-6, 5e-6, dx,
+                                    (nx, ny, nz), int(rng.integers(1 << 30)))
+        gas = _gas(p_pa)
+        vol = nx * ny * nz * dx ** 3
+        out.append(Workload(name=f"ens{r}", nx=nx, ny=ny, nz=nz, dx=dx, dt=1e-10, weight=1e15 * vol / (n_p // 2),
+                            md_sub=40, v_dc=0.0, v_rf=100.0, f_rf=13.56e6, phase=float(rng.uniform(0, 2 * math.pi)),
+                            v_top=0.0, grain_pos=gpos, grain_r=grad, seed=seed + 7919 * (r + 1), run_id=r,
+                            n_e=n_p // 2, n_i=n_p - n_p // 2, te_ev=3.0, ti_ev=0.03, steps=100, **gas))
+    return out
+
+
 def small(nx=8, ny=8, nz=16, n_e=2000, n_i=2000, grains=1, seed=7, **over) -> Workload:
     """A small case for tests: a few tiles, a grain near the middle, DC bias."""
     dx = 0.2e-3
