@@ -302,13 +302,17 @@ pic_status pic_init(const pic_mesh* mesh, const pic_electrodes* el, const pic_ga
     c->d_next_id = (unsigned int*)dev_alloc(c, sizeof(unsigned int));
     c->d_child = (ChildRec*)dev_alloc(c, sizeof(ChildRec) * c->child_cap);
     if (mixed) {
+        c->md_rescap = std::max<int64_t>(65536, std::max(c->cap[0], c->cap[1]) / 8);
         for (int sp = 0; sp < 2; ++sp) {
+            c->md_res[sp] = (float4*)dev_alloc(c, sizeof(float4) * 2 * c->md_rescap);
+            ok = ok && c->md_res[sp];
             c->md_list[sp] = (unsigned int*)dev_alloc(c, sizeof(unsigned int) * c->cap[sp]);
+            c->md_next[sp] = (unsigned int*)dev_alloc(c, sizeof(unsigned int) * c->cap[sp]);
             c->mcc_list[sp] = (unsigned int*)dev_alloc(c, sizeof(unsigned int) * c->cap[sp]);
-            ok = ok && c->md_list[sp] && c->mcc_list[sp];
+            ok = ok && c->md_list[sp] && c->md_next[sp] && c->mcc_list[sp];
         }
-        c->d_lists = (unsigned int*)dev_alloc(c, 4 * sizeof(unsigned int));
-        ok = ok && c->d_lists;
+        c->d_lists = (unsigned int*)dev_alloc(c, 6 * sizeof(unsigned int));
+        ok = ok && c->d_lists && cudaMemset(c->d_lists, 0, 6 * sizeof(unsigned int)) == cudaSuccess;
     }
     c->rq = (unsigned long long*)dev_alloc(c, sizeof(unsigned long long) * nodes);
     c->phi = (double*)dev_alloc(c, sizeof(double) * nodes);

@@ -13,10 +13,12 @@
 //   k_push32  every particle outside the MD regions: gather, push, electrode
 //             loss, the null-collision test, deposit.  Deposits are summed in a
 //             shared-memory window of nodes per block and flushed with one
-//             global atomic per touched node.  Particles in MD cells and
-//             collision candidates are appended to lists.
-//   k_md32    the MD-region particles: Dt/40 substeps with the PPPM correction,
-//             grain absorption, MCC, deposit.
+//             global atomic per touched node.  Collision candidates are
+//             appended to a list, particles that end in an MD cell to the next
+//             step's MD list.
+//   k_md32    the MD-region particles (listed during the previous step, so it
+//             runs on a second stream alongside k_push32): Dt/40 substeps with
+//             the PPPM correction, grain absorption, MCC, deposit.
 //   k_mcc32   the collision candidates: process selection and kinematics.
 #include <climits>
 
@@ -25,15 +27,25 @@
 namespace pic {
 namespace {
 
+#ifndef PIC_PUSH_PPT
+#define PIC_PUSH_PPT 2
+#endif
+#ifndef PIC_PUSH_WINR
+#define PIC_PUSH_WINR 128
+#endif
+#ifndef PIC_PUSH_TILE
+#define PIC_PUSH_TILE 0
+#endif
 constexpr int kPushThreads = 256;
-constexpr int kPPT = 2;                          // particles per thread per chunk
+constexpr int kPPT = PIC_PUSH_PPT;               // particles per thread per chunk
 constexpr int kChunk = kPushThreads * kPPT;      // particles per block per chunk
 // deposit window per block: 4 planes (offsets -1..+2 from the anchor particle's
 // plane), each +-kWinR nodes around the anchor's node column; a fixed-point
 // weight w <= 2^42 is summed as two 21-bit halves in 32-bit shared counters
 // (a chunk adds at most kChunk * 2^21 < 2^32 to a slot)
-constexpr int kWinR = 256;
+constexpr int kWinR = PIC_PUSH_WINR;
 constexpr int kWinN = 4 * 2 * kWinR;
+constexpr bool kTile = PIC_PUSH_TILE != 0;       // gather E from a shared-memory tile
 
 struct P32 {
     int nx, ny, nz, nxy;
@@ -63,8 +75,12 @@ struct P32 {
     ChildRec* child;
     unsigned long long child_cap;
     unsigned long long* nch;
-    unsigned int* md_list;
+    unsigned int* md_list;       // MD-region particles of this step (built during the previous one)
     unsigned int* md_n;
+    unsigned int* md_next;       // ... and of the next step
+    unsigned int* md_next_n;
+    float4* md_res;              // MD results (pos, vel) per list entry, committed after the step's join
+    unsigned int md_rescap;
     unsigned int* mcc_list;
     unsigned int* mcc_n;
 };
@@ -341,9 +357,29 @@ __device__ __forceinline__ void count_event(const P32& p, int ev)
     if (ev != kEvNone) atomicAdd(p.cnt + slot, 1ull);
 }
 
-__global__ void __launch_bounds__(kPushThreads) k_push32(const P32 p)
+// Slot of node `node` (in plane k) in a block's tile/window around the anchor
+// node `anchor` in plane `ak`, or -1 when outside.
+__device__ __forceinline__ int tile_slot(int node, int k, int anchor, int ak, int nxy)
 {
-    __shared__ unsigned int win_hi[kWinN], win_lo[kWinN];
+    const int pl = k - ak;
+    const int w = node - anchor - pl * nxy + kWinR;
+    return (pl >= -1 && pl <= 2 && w >= 0 && w < 2 * kWinR) ? (pl + 1) * 2 * kWinR + w : -1;
+}
+
+// Base slot of a particle's 8 corners when they all lie in the tile without a
+// periodic wrap: corners are base + {0, 1, nx, nx + 1} and the same + 2 kWinR.
+__device__ __forceinline__ int block_slot(int i, int j, int k, int nx, int ny, int anchor, int ak)
+{
+    if (i + 1 >= nx || j + 1 >= ny) return -1;
+    const int pl = k - ak;
+    const int w = ((k * ny + j) * nx + i) - anchor - pl * nx * ny + kWinR;
+    return (pl >= -1 && pl <= 1 && w >= 0 && w + nx + 1 < 2 * kWinR) ? (pl + 1) * 2 * kWinR + w : -1;
+}
+
+__global__ void __launch_bounds__(kPushThreads, 4) k_push32(const P32 p)
+{
+    __shared__ float4 tile[kTile ? kWinN : 1];         // E around the chunk (gather)
+    __shared__ unsigned int win_hi[kWinN], win_lo[kWinN];  // deposit sums (two 21-bit halves)
     __shared__ unsigned long long s_anchor;
     const unsigned long long n = p.nslot[p.sp];
     const uint32_t step = *p.step;
@@ -351,13 +387,40 @@ __global__ void __launch_bounds__(kPushThreads) k_push32(const P32 p)
     const bool no_mcc = p.flags & PIC_F_NO_MCC;
     const long long charge = p.sp == 0 ? -1 : 1;
     const int nx = p.nx, ny = p.ny, nz = p.nz, nxy = p.nxy;
+    const int nodes = nxy * (nz + 1);
+    const float s14 = 1.0f / (float)kWQ;
     for (int t = threadIdx.x; t < kWinN; t += blockDim.x) { win_hi[t] = 0u; win_lo[t] = 0u; }
     if (threadIdx.x == 0) s_anchor = 0ull;
     __syncthreads();
     unsigned int live = 0;
     for (unsigned long long c0 = (unsigned long long)blockIdx.x * kChunk; c0 < n;
          c0 += (unsigned long long)gridDim.x * kChunk) {
-        int dcell[kPPT];                 // packed cell of each deposit (-1: none)
+        // ---- anchor: warp 0 samples 32 slots spread over the chunk and takes the
+        // first live one from the middle on (else any live one)
+        if (threadIdx.x < 32) {
+            const unsigned long long q = c0 + (unsigned long long)threadIdx.x * (kChunk / 32) + kChunk / 64;
+            const int cell = q < n ? __float_as_int(p.pos[q].w) : -1;
+            const unsigned m = __ballot_sync(0xffffffffu, cell >= 0);
+            const unsigned mh = m & 0xffff0000u;
+            const int lane = mh ? __ffs(mh) - 1 : (m ? __ffs(m) - 1 : -1);
+            const int ac = lane >= 0 ? __shfl_sync(0xffffffffu, cell, lane) : -1;
+            if (threadIdx.x == 0) s_anchor = ac >= 0 ? (1ull << 32) | (unsigned int)ac : 0ull;
+        }
+        __syncthreads();
+        const unsigned long long ak64 = s_anchor;
+        int ai = 0, aj = 0, akk = 0;
+        unpack((int)(unsigned int)ak64, ai, aj, akk);
+        const int anchor = (akk * ny + aj) * nx + ai;
+        // ---- stage E on the tile: planes akk-1 .. akk+2, +-kWinR nodes around the anchor column
+        if (kTile && ak64) {
+            for (int t = threadIdx.x; t < kWinN; t += blockDim.x) {
+                const int pl = t / (2 * kWinR) - 1, w = t % (2 * kWinR);
+                const int nd = anchor + pl * nxy + w - kWinR;
+                if (nd >= 0 && nd < nodes) tile[t] = __ldg(p.E + nd);
+            }
+        }
+        __syncthreads();
+        int dcell[kPPT];
         int da[kPPT][3];
 #pragma unroll
         for (int u = 0; u < kPPT; ++u) {
@@ -365,102 +428,121 @@ __global__ void __launch_bounds__(kPushThreads) k_push32(const P32 p)
             const unsigned long long q = c0 + (unsigned long long)u * kPushThreads + threadIdx.x;
             int lost = 0;
             bool md = false, cand = false;
-            if (q < n) {
-                const float4 P = p.pos[q];
-                int cell = __float_as_int(P.w);
-                if (cell >= 0) {
-                    ++live;
-                    int i, j, k;
-                    unpack(cell, i, j, k);
-                    float o[3] = {P.x, P.y, P.z};
-                    if (frozen) {
+            const float4 Pu = q < n ? p.pos[q] : make_float4(0.f, 0.f, 0.f, __int_as_float(-1));
+            int cell = __float_as_int(Pu.w);
+            if (cell >= 0) {
+                ++live;
+                int i, j, k;
+                unpack(cell, i, j, k);
+                float o[3] = {Pu.x, Pu.y, Pu.z};
+                if (frozen) {
+                    dcell[u] = cell;
+                    da[u][0] = qa(o[0]); da[u][1] = qa(o[1]); da[u][2] = qa(o[2]);
+                } else if (p.cell_ng[(k * ny + j) * nx + i] != 0) {
+                    // in an MD region: on this step's MD list, advanced by k_md32
+                } else {
+                    const float4 Vu = p.vel[q];
+                    float v[3] = {Vu.x, Vu.y, Vu.z};
+                    int a[3] = {qa(o[0]), qa(o[1]), qa(o[2])};
+                    float E[3];
+                    const int b = (kTile && ak64) ? block_slot(i, j, k, nx, ny, anchor, akk) : -1;
+                    if (b >= 0) {
+                        const float wx0 = (float)(kWQ - a[0]) * s14, wx1 = (float)a[0] * s14;
+                        const float wy0 = (float)(kWQ - a[1]) * s14, wy1 = (float)a[1] * s14;
+                        const float wz0 = (float)(kWQ - a[2]) * s14, wz1 = (float)a[2] * s14;
+                        const float4 e000 = tile[b], e001 = tile[b + 1], e010 = tile[b + nx], e011 = tile[b + nx + 1];
+                        const int b1 = b + 2 * kWinR;
+                        const float4 e100 = tile[b1], e101 = tile[b1 + 1], e110 = tile[b1 + nx],
+                                     e111 = tile[b1 + nx + 1];
+                        const float w00 = wy0 * wz0, w01 = wy1 * wz0, w10 = wy0 * wz1, w11 = wy1 * wz1;
+                        E[0] = w00 * (wx0 * e000.x + wx1 * e001.x) + w01 * (wx0 * e010.x + wx1 * e011.x) +
+                               w10 * (wx0 * e100.x + wx1 * e101.x) + w11 * (wx0 * e110.x + wx1 * e111.x);
+                        E[1] = w00 * (wx0 * e000.y + wx1 * e001.y) + w01 * (wx0 * e010.y + wx1 * e011.y) +
+                               w10 * (wx0 * e100.y + wx1 * e101.y) + w11 * (wx0 * e110.y + wx1 * e111.y);
+                        E[2] = w00 * (wx0 * e000.z + wx1 * e001.z) + w01 * (wx0 * e010.z + wx1 * e011.z) +
+                               w10 * (wx0 * e100.z + wx1 * e101.z) + w11 * (wx0 * e110.z + wx1 * e111.z);
+                    } else {
+                        gather(p.E, nx, ny, i, j, k, a, E);
+                    }
+                    v[0] += E[0] * p.kq; v[1] += E[1] * p.kq; v[2] += E[2] * p.kq;
+                    o[0] += v[0]; o[1] += v[1]; o[2] += v[2];
+                    lost = carry(nx, ny, nz, i, j, k, o);
+                    if (lost) {
+                        p.pos[q].w = __int_as_float(-1);
+                    } else {
+                        if (!no_mcc) {
+                            const uint4 r = philox4x32_10(make_uint4(__float_as_uint(Vu.w), step, kPurMCC, 0u),
+                                                          p.key);
+                            cand = u01f(r.x) < p.pnull;
+                        }
+                        cell = pack(i, j, k);
+                        p.pos[q] = make_float4(o[0], o[1], o[2], __int_as_float(cell));
+                        p.vel[q] = make_float4(v[0], v[1], v[2], Vu.w);
                         dcell[u] = cell;
                         da[u][0] = qa(o[0]); da[u][1] = qa(o[1]); da[u][2] = qa(o[2]);
-                    } else if (p.cell_ng[(k * ny + j) * nx + i] != 0) {
-                        md = true;
-                    } else {
-                        const float4 V = p.vel[q];
-                        float v[3] = {V.x, V.y, V.z};
-                        int a[3] = {qa(o[0]), qa(o[1]), qa(o[2])};
-                        float E[3];
-                        gather(p.E, nx, ny, i, j, k, a, E);
-                        v[0] += E[0] * p.kq; v[1] += E[1] * p.kq; v[2] += E[2] * p.kq;
-                        o[0] += v[0]; o[1] += v[1]; o[2] += v[2];
-                        lost = carry(nx, ny, nz, i, j, k, o);
-                        if (lost) {
-                            p.pos[q].w = __int_as_float(-1);
-                        } else {
-                            if (!no_mcc) {
-                                const uint4 r = philox4x32_10(make_uint4(__float_as_uint(V.w), step, kPurMCC, 0u),
-                                                              p.key);
-                                cand = u01f(r.x) < p.pnull;
-                            }
-                            cell = pack(i, j, k);
-                            p.pos[q] = make_float4(o[0], o[1], o[2], __int_as_float(cell));
-                            p.vel[q] = make_float4(v[0], v[1], v[2], V.w);
-                            dcell[u] = cell;
-                            da[u][0] = qa(o[0]); da[u][1] = qa(o[1]); da[u][2] = qa(o[2]);
-                        }
+                        md = p.cell_ng[(k * ny + j) * nx + i] != 0;    // in an MD region next step
                     }
                 }
             }
-            warp_append(p.md_list, p.md_n, (unsigned int)q, md);
-            warp_append(p.mcc_list, p.mcc_n, (unsigned int)q, cand);
-            warp_count(p.cnt + (p.sp == 0 ? PIC_C_LOST_BOT_E : PIC_C_LOST_BOT_I), lost == 1);
-            warp_count(p.cnt + (p.sp == 0 ? PIC_C_LOST_TOP_E : PIC_C_LOST_TOP_I), lost == 2);
-            if (__any_sync(__activemask(), lost == 3)) {
-                warp_count(p.cnt + PIC_C_ERR, lost == 3);
-                if (lost == 3) latch(p.err, kErrNonFinite);
-            }
-        }
-        // anchor of the window: a deposit from the middle half of the chunk if there is one
-        {
-            unsigned long long key = 0ull;
-#pragma unroll
-            for (int u = 0; u < kPPT; ++u)
-                if (dcell[u] >= 0) {
-                    const int slot = u * kPushThreads + threadIdx.x;
-                    const unsigned long long prio = (slot >= kChunk / 4 && slot < 3 * kChunk / 4) ? 2ull : 1ull;
-                    const unsigned long long kk = (prio << 32) | (unsigned int)dcell[u];
-                    key = kk > key ? kk : key;
+            if (__any_sync(0xffffffffu, md || cand || lost)) {
+                warp_append(p.md_next, p.md_next_n, (unsigned int)q, md);
+                warp_append(p.mcc_list, p.mcc_n, (unsigned int)q, cand);
+                if (__any_sync(0xffffffffu, lost != 0)) {
+                    warp_count(p.cnt + (p.sp == 0 ? PIC_C_LOST_BOT_E : PIC_C_LOST_BOT_I), lost == 1);
+                    warp_count(p.cnt + (p.sp == 0 ? PIC_C_LOST_TOP_E : PIC_C_LOST_TOP_I), lost == 2);
+                    warp_count(p.cnt + PIC_C_ERR, lost == 3);
+                    if (lost == 3) latch(p.err, kErrNonFinite);
                 }
-            for (int o = 16; o > 0; o >>= 1) {
-                const unsigned long long y = __shfl_xor_sync(0xffffffffu, key, o);
-                key = y > key ? y : key;
             }
-            if ((threadIdx.x & 31) == 0 && key) atomicMax(&s_anchor, key);
         }
-        __syncthreads();
-        const unsigned long long ak = s_anchor;
-        int ai = 0, aj = 0, akk = 0;
-        unpack((int)(unsigned int)ak, ai, aj, akk);
-        const int anchor = (akk * ny + aj) * nx + ai;
-        if (ak) {
+        // ---- deposit: shared window for corners near the anchor, global atomics otherwise
+        if (!ak64) {
 #pragma unroll
             for (int u = 0; u < kPPT; ++u) {
                 if (dcell[u] < 0) continue;
                 int i, j, k;
                 unpack(dcell[u], i, j, k);
-                int node[8];
-                long long val[8];
-                corners(nx, ny, i, j, k, da[u], 1, node, val);
+                deposit_global(p.rq, nx, ny, i, j, k, da[u], charge);
+            }
+        } else {
 #pragma unroll
-                for (int c = 0; c < 8; ++c) {
-                    if (val[c] == 0) continue;
-                    const int pl = k + (c >> 2) - akk;               // plane offset from the anchor
-                    const int w = node[c] - anchor - pl * nxy + kWinR;
-                    if (pl >= -1 && pl <= 2 && w >= 0 && w < 2 * kWinR) {
-                        const int slot = (pl + 1) * 2 * kWinR + w;
-                        atomicAdd(win_hi + slot, (unsigned int)(val[c] >> 21));
-                        atomicAdd(win_lo + slot, (unsigned int)(val[c] & 0x1FFFFF));
-                    } else {
-                        atomicAdd(p.rq + node[c], (unsigned long long)(charge * val[c]));
+            for (int u = 0; u < kPPT; ++u) {
+                if (dcell[u] < 0) continue;
+                int i, j, k;
+                unpack(dcell[u], i, j, k);
+                const long long wx[2] = {kWQ - da[u][0], da[u][0]};
+                const int wy[2] = {kWQ - da[u][1], da[u][1]}, wz[2] = {kWQ - da[u][2], da[u][2]};
+                const int b = block_slot(i, j, k, nx, ny, anchor, akk);
+                if (b >= 0) {
+                    const int off[8] = {0, 1, nx, nx + 1, 2 * kWinR, 2 * kWinR + 1, 2 * kWinR + nx,
+                                        2 * kWinR + nx + 1};
+#pragma unroll
+                    for (int c = 0; c < 8; ++c) {
+                        const long long v = wx[c & 1] * (long long)(wy[(c >> 1) & 1] * wz[c >> 2]);
+                        if (v == 0) continue;
+                        atomicAdd(win_hi + b + off[c], (unsigned int)(v >> 21));
+                        atomicAdd(win_lo + b + off[c], (unsigned int)(v & 0x1FFFFF));
+                    }
+                } else {
+                    int node[8];
+                    long long val[8];
+                    corners(nx, ny, i, j, k, da[u], 1, node, val);
+#pragma unroll
+                    for (int c = 0; c < 8; ++c) {
+                        if (val[c] == 0) continue;
+                        const int sl = tile_slot(node[c], k + (c >> 2), anchor, akk, nxy);
+                        if (sl >= 0) {
+                            atomicAdd(win_hi + sl, (unsigned int)(val[c] >> 21));
+                            atomicAdd(win_lo + sl, (unsigned int)(val[c] & 0x1FFFFF));
+                        } else {
+                            atomicAdd(p.rq + node[c], (unsigned long long)(charge * val[c]));
+                        }
                     }
                 }
             }
         }
         __syncthreads();
-        if (ak) {
+        if (ak64) {
             for (int t = threadIdx.x; t < kWinN; t += blockDim.x) {
                 const unsigned int hi = win_hi[t], lo = win_lo[t];
                 if (hi | lo) {
@@ -519,9 +601,12 @@ __device__ void md_load(const P32& p, int i, int j, int k, MdCell& m)
 }
 
 // MD-region particles: md_sub substeps of dt/md_sub with the PPPM correction,
-// absorption after each substep, then MCC and the deposit (Sec. III)
+// absorption after each substep, then MCC and the deposit (Sec. III).  Runs
+// beside k_push32, so the new states go to md_res and reach pos/vel only in
+// k_md_commit, after both have finished (k_push32 reads these slots' cells).
 __global__ void __launch_bounds__(64) k_md32(const P32 p)
 {
+    if (p.sp == 1 && (p.flags & PIC_F_IONS_FROZEN)) return;
     const unsigned int n = *p.md_n;
     const uint32_t step = *p.step;
     const long long charge = p.sp == 0 ? -1 : 1;
@@ -530,6 +615,10 @@ __global__ void __launch_bounds__(64) k_md32(const P32 p)
         const unsigned int q = p.md_list[t];
         const float4 P = p.pos[q];
         const float4 V = p.vel[q];
+        if (t >= p.md_rescap) {            // no room for the result: leave the particle, report
+            latch(p.err, kErrCapacity);
+            continue;
+        }
         int i, j, k;
         unpack(__float_as_int(P.w), i, j, k);
         float o[3] = {P.x, P.y, P.z};
@@ -571,7 +660,8 @@ __global__ void __launch_bounds__(64) k_md32(const P32 p)
             if (grain >= 0) break;
         }
         if (fate != 0 || grain >= 0) {
-            p.pos[q].w = __int_as_float(-1);
+            p.md_res[2 * t] = make_float4(P.x, P.y, P.z, __int_as_float(-1));
+            p.md_res[2 * t + 1] = V;
             if (fate == 1) atomicAdd(p.cnt + (p.sp == 0 ? PIC_C_LOST_BOT_E : PIC_C_LOST_BOT_I), 1ull);
             else if (fate == 2) atomicAdd(p.cnt + (p.sp == 0 ? PIC_C_LOST_TOP_E : PIC_C_LOST_TOP_I), 1ull);
             else if (fate == 3) {
@@ -589,11 +679,49 @@ __global__ void __launch_bounds__(64) k_md32(const P32 p)
             const uint4 r = philox4x32_10(make_uint4(id, step, kPurMCC, 0u), p.key);
             if (u01f(r.x) < p.pnull) count_event(p, collide(p, step, r, cell, o, v, id));
         }
-        p.pos[q] = make_float4(o[0], o[1], o[2], __int_as_float(cell));
-        p.vel[q] = make_float4(v[0], v[1], v[2], V.w);
+        p.md_res[2 * t] = make_float4(o[0], o[1], o[2], __int_as_float(cell));
+        p.md_res[2 * t + 1] = make_float4(v[0], v[1], v[2], V.w);
         const int a[3] = {qa(o[0]), qa(o[1]), qa(o[2])};
         deposit_global(p.rq, p.nx, p.ny, i, j, k, a, charge);
+        if (p.cell_ng[(k * p.ny + j) * p.nx + i] != 0) p.md_next[atomicAdd(p.md_next_n, 1u)] = q;
     }
+}
+
+// write the MD results back once k_push32 and k_md32 have both finished
+__global__ void k_md_commit(float4* pos_e, float4* vel_e, const unsigned int* list_e, const float4* res_e,
+                            float4* pos_i, float4* vel_i, const unsigned int* list_i, const float4* res_i,
+                            const unsigned int* lists, unsigned int rescap, int frozen_ions)
+{
+    const unsigned int ne = min(lists[0], rescap), ni = frozen_ions ? 0u : min(lists[2], rescap);
+    for (unsigned int t = blockIdx.x * blockDim.x + threadIdx.x; t < ne; t += gridDim.x * blockDim.x) {
+        pos_e[list_e[t]] = res_e[2 * t];
+        vel_e[list_e[t]] = res_e[2 * t + 1];
+    }
+    for (unsigned int t = blockIdx.x * blockDim.x + threadIdx.x; t < ni; t += gridDim.x * blockDim.x) {
+        pos_i[list_i[t]] = res_i[2 * t];
+        vel_i[list_i[t]] = res_i[2 * t + 1];
+    }
+}
+
+// start of a step: this step's MD lists are the ones built during the last step
+__global__ void k_md_rotate(unsigned int* md_e, unsigned int* next_e, unsigned int* md_i, unsigned int* next_i,
+                            unsigned int* lists)
+{
+    const unsigned int ne = lists[4], ni = lists[5];
+    for (unsigned int t = blockIdx.x * blockDim.x + threadIdx.x; t < ne; t += gridDim.x * blockDim.x)
+        md_e[t] = next_e[t];
+    for (unsigned int t = blockIdx.x * blockDim.x + threadIdx.x; t < ni; t += gridDim.x * blockDim.x)
+        md_i[t] = next_i[t];
+}
+
+__global__ void k_md_counts(unsigned int* lists)
+{
+    lists[0] = lists[4];     // md_n e
+    lists[2] = lists[5];     // md_n i
+    lists[1] = 0u;           // mcc_n e
+    lists[3] = 0u;           // mcc_n i
+    lists[4] = 0u;
+    lists[5] = 0u;
 }
 
 // collision candidates found by k_push32 (their positions are final)
@@ -667,7 +795,8 @@ __global__ void k_efield32(int nx, int ny, int nz, double dx, const double* __re
 __global__ void k_children32(int nx, int ny, ChildRec* rec, const unsigned long long* nch,
                              unsigned long long child_cap, const unsigned long long* nslot,
                              const unsigned int* next_id, float4* pos_e, float4* vel_e, float4* pos_i,
-                             float4* vel_i, long long cap_e, long long cap_i, unsigned long long* rq, int* err)
+                             float4* vel_i, long long cap_e, long long cap_i, unsigned long long* rq, int* err,
+                             const int* cell_ng, unsigned int* next_e, unsigned int* next_i, unsigned int* lists)
 {
     __shared__ uint32_t tile[256];
     const unsigned long long n = min(*nch, child_cap);   // records past the buffer were never written
@@ -705,6 +834,10 @@ __global__ void k_children32(int nx, int ny, ChildRec* rec, const unsigned long 
         const int a[3] = {qa(o[0]), qa(o[1]), qa(o[2])};
         deposit_global(rq, nx, ny, i, j, k, a, -1);
         deposit_global(rq, nx, ny, i, j, k, a, 1);
+        if (next_e && cell_ng[(k * ny + j) * nx + i] != 0) {
+            next_e[atomicAdd(lists + 4, 1u)] = (unsigned int)se;
+            next_i[atomicAdd(lists + 5, 1u)] = (unsigned int)si;
+        }
     }
 }
 
@@ -802,6 +935,10 @@ P32 params(pic_ctx* c, int sp)
     p.nch = c->d_nch;
     p.md_list = c->md_list[sp];
     p.md_n = c->d_lists + 2 * sp;
+    p.md_next = c->md_next[sp];
+    p.md_next_n = c->d_lists + 4 + sp;
+    p.md_res = c->md_res[sp];
+    p.md_rescap = (unsigned int)c->md_rescap;
     p.mcc_list = c->mcc_list[sp];
     p.mcc_n = c->d_lists + 2 * sp + 1;
     return p;
@@ -811,21 +948,26 @@ P32 params(pic_ctx* c, int sp)
 
 void launch_push32(pic_ctx* c)
 {
-    // electrons: fast push on the main stream, then their MD-region and
-    // collision kernels on a second branch, which overlaps the ion push
-    cudaMemsetAsync(c->d_lists, 0, 4 * sizeof(unsigned int), c->stream);
+    // this step's MD lists come from the last step; both species' MD particles
+    // advance on a second branch while the bulk pushes run on the main stream
+    k_md_rotate<<<64, 256, 0, c->stream>>>(c->md_list[0], c->md_next[0], c->md_list[1], c->md_next[1], c->d_lists);
+    k_md_counts<<<1, 1, 0, c->stream>>>(c->d_lists);
     const P32 pe = params(c, 0), pi = params(c, 1);
-    k_push32<<<grid_for((c->cap[0] + kPPT - 1) / kPPT, kPushThreads, 152 * 8), kPushThreads, 0, c->stream>>>(pe);
     cudaEventRecord(c->ev_fork, c->stream);
     cudaStreamWaitEvent(c->aux, c->ev_fork, 0);
     k_md32<<<152 * 4, 64, 0, c->aux>>>(pe);
-    k_mcc32<<<152 * 4, 256, 0, c->aux>>>(pe);
+    k_md32<<<152 * 4, 64, 0, c->aux>>>(pi);
     cudaEventRecord(c->ev_join, c->aux);
+    k_push32<<<grid_for((c->cap[0] + kPPT - 1) / kPPT, kPushThreads, 152 * 8), kPushThreads, 0, c->stream>>>(pe);
+    k_mcc32<<<152 * 4, 256, 0, c->stream>>>(pe);
     k_push32<<<grid_for((c->cap[1] + kPPT - 1) / kPPT, kPushThreads, 152 * 8), kPushThreads, 0, c->stream>>>(pi);
-    k_md32<<<152 * 4, 64, 0, c->stream>>>(pi);
     k_mcc32<<<152 * 4, 256, 0, c->stream>>>(pi);
     cudaStreamWaitEvent(c->stream, c->ev_join, 0);
-    c->launches += 6;
+    k_md_commit<<<64, 256, 0, c->stream>>>((float4*)c->pos[0], (float4*)c->vel[0], c->md_list[0], c->md_res[0],
+                                           (float4*)c->pos[1], (float4*)c->vel[1], c->md_list[1], c->md_res[1],
+                                           c->d_lists, (unsigned int)c->md_rescap,
+                                           (c->flags & PIC_F_IONS_FROZEN) ? 1 : 0);
+    c->launches += 9;
 }
 
 void launch_deposit32(pic_ctx* c)
@@ -848,7 +990,7 @@ void launch_children32(pic_ctx* c)
     k_children32<<<64, 256, 0, c->stream>>>(c->nx, c->ny, c->d_child, c->d_nch, (unsigned long long)c->child_cap,
                                               c->d_nslot, c->d_next_id, (float4*)c->pos[0], (float4*)c->vel[0],
                                               (float4*)c->pos[1], (float4*)c->vel[1], c->cap[0], c->cap[1], c->rq,
-                                              c->d_err);
+                                              c->d_err, c->cell_ng, c->md_next[0], c->md_next[1], c->d_lists);
     k_children_finish32<<<1, 1, 0, c->stream>>>(c->d_nch, (unsigned long long)c->child_cap, c->d_nslot,
                                                 c->d_next_id, c->cap[0], c->cap[1], c->d_step);
     c->launches += 2;

@@ -158,8 +158,11 @@ struct pic_ctx {
     unsigned int* d_next_id = nullptr;
     pic::ChildRec* d_child = nullptr;
     unsigned int* md_list[2] = {nullptr, nullptr};   // mixed: slots of MD-region particles this step
+    unsigned int* md_next[2] = {nullptr, nullptr};   // mixed: the same list being built for the next step
+    float4* md_res[2] = {nullptr, nullptr};           // mixed: MD results (pos, vel pairs) until the join
+    int64_t md_rescap = 0;
     unsigned int* mcc_list[2] = {nullptr, nullptr};  // mixed: slots of collision candidates this step
-    unsigned int* d_lists = nullptr;                  // [md_n e, mcc_n e, md_n i, mcc_n i]
+    unsigned int* d_lists = nullptr;                  // [md_n e, mcc_n e, md_n i, mcc_n i, next_n e, next_n i]
 
     // mesh arrays
     unsigned long long* rq = nullptr;        // int64 fixed-point charge per node

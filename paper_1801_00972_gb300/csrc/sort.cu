@@ -80,10 +80,12 @@ __global__ void k_scan_add(unsigned int* out, const unsigned int* offs, size_t n
         out[q] += offs[q / kScanBlock];
 }
 
+// (mixed precision also lists the new slots of particles in MD cells for the
+// next step: md_next / next_n, null for FP64)
 template <typename T4>
 __global__ void k_scatter(const T4* __restrict__ pos, const T4* __restrict__ vel, const unsigned long long* nslot,
                           int sp, unsigned int* cursor, T4* __restrict__ pos_out, T4* __restrict__ vel_out, int nx,
-                          int ny)
+                          int ny, const int* cell_ng, unsigned int* md_next, unsigned int* next_n)
 {
     const unsigned long long n = nslot[sp];
     for (unsigned long long q = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; q < n;
@@ -94,6 +96,7 @@ __global__ void k_scatter(const T4* __restrict__ pos, const T4* __restrict__ vel
         const unsigned int d = atomicAdd(cursor + c, 1u);
         pos_out[d] = p;
         vel_out[d] = vel[q];
+        if (md_next && cell_ng[c] != 0) md_next[atomicAdd(next_n, 1u)] = d;
     }
 }
 
@@ -150,14 +153,17 @@ void sort_particles(pic_ctx* c, int sp)
         k_hist<double4><<<grid, 256, 0, c->stream>>>((const double4*)c->pos[sp], c->d_nslot, sp, c->cursor, c->nx,
                                                      c->ny);
     scan(c, c->cursor, nc, 0);
+    if (c->prec == PIC_MIXED) cudaMemsetAsync(c->d_lists + 4 + sp, 0, sizeof(unsigned int), c->stream);
     if (c->prec == PIC_MIXED)
         k_scatter<float4><<<grid, 256, 0, c->stream>>>((const float4*)c->pos[sp], (const float4*)c->vel[sp],
                                                        c->d_nslot, sp, c->cursor, (float4*)c->pos_alt[sp],
-                                                       (float4*)c->vel_alt[sp], c->nx, c->ny);
+                                                       (float4*)c->vel_alt[sp], c->nx, c->ny, c->cell_ng,
+                                                       c->md_next[sp], c->d_lists + 4 + sp);
     else
         k_scatter<double4><<<grid, 256, 0, c->stream>>>((const double4*)c->pos[sp], (const double4*)c->vel[sp],
                                                         c->d_nslot, sp, c->cursor, (double4*)c->pos_alt[sp],
-                                                        (double4*)c->vel_alt[sp], c->nx, c->ny);
+                                                        (double4*)c->vel_alt[sp], c->nx, c->ny, c->cell_ng,
+                                                        (unsigned int*)nullptr, (unsigned int*)nullptr);
     // the last scan level's single block sum is the number of live particles
     k_set_nslot<<<1, 1, 0, c->stream>>>(c->d_nslot, sp, c->scan_tmp.back());
     c->launches += 3;
