@@ -326,6 +326,7 @@ pic_status pic_init(const pic_mesh* mesh, const pic_electrodes* el, const pic_ga
     c->d_res = (double*)dev_alloc(c, sizeof(double));
     c->d_solve_flag = (int*)dev_alloc(c, sizeof(int));
     c->d_iter_total = (unsigned long long*)dev_alloc(c, sizeof(unsigned long long));
+    c->d_vb_last = (double*)dev_alloc(c, sizeof(double));
     c->xs64 = (double*)dev_alloc(c, sizeof(double) * 5 * c->n_xs);
     c->xs32 = (float*)dev_alloc(c, sizeof(float) * 5 * c->n_xs);
     const int ng1 = std::max(c->ng, 1);
@@ -348,7 +349,7 @@ pic_status pic_init(const pic_mesh* mesh, const pic_electrodes* el, const pic_ga
         c->mphi = (double*)dev_alloc(c, sizeof(double) * nodes);
         ok = ok && c->mom[0] && c->mom[1] && c->mphi;
     }
-    ok = ok && c->d_step && c->d_iters && c->d_res && c->d_solve_flag && c->d_iter_total;
+    ok = ok && c->d_step && c->d_iters && c->d_res && c->d_solve_flag && c->d_iter_total && c->d_vb_last;
     ok = ok && c->d_nslot && c->d_cnt && c->d_err && c->d_nch && c->d_next_id && c->d_child && c->rq && c->phi &&
          c->phi_alt && c->f64 && (c->e32 || c->e64) && c->d_norm && c->xs64 && c->xs32 && c->gpos && c->grad &&
          c->gcell && c->gq && c->gabs && c->gtab && c->gtab32 && c->gq32 && c->goff32 && c->gr2_32 && c->cell_ng &&
@@ -436,6 +437,7 @@ pic_status pic_init(const pic_mesh* mesh, const pic_electrodes* el, const pic_ga
     if (e == cudaSuccess) e = cudaMemset(c->d_res, 0, sizeof(double));
     if (e == cudaSuccess) e = cudaMemset(c->d_solve_flag, 0, sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(c->d_iter_total, 0, sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMemset(c->d_vb_last, 0, sizeof(double));
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->aux, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming);

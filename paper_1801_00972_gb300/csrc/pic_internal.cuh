@@ -206,6 +206,7 @@ struct pic_ctx {
     double* d_res = nullptr;                 // graph solve: relative residual of the last solve
     int* d_solve_flag = nullptr;             // graph solve: PIC_ENOTCONV / PIC_ENONFINITE latch
     uint32_t* d_step = nullptr;              // device copy of the step counter
+    double* d_vb_last = nullptr;             // lower electrode value of the last solve
     unsigned long long* d_iter_total = nullptr;  // refinement iterations of all graph solves
 
     // CUDA graphs of one step, captured lazily on a private stream and

@@ -18,8 +18,22 @@
 
 #include "pic_internal.cuh"
 
+#ifndef PIC_MG_PRE
+#define PIC_MG_PRE 2
+#endif
+#ifndef PIC_MG_POST
+#define PIC_MG_POST 2
+#endif
+#ifndef PIC_MG_OMEGA
+#define PIC_MG_OMEGA 1.0
+#endif
+
 namespace pic {
 namespace {
+
+constexpr int kPre = PIC_MG_PRE;         // pre-smoothing sweeps of a V-cycle
+constexpr int kPost = PIC_MG_POST;       // post-smoothing sweeps
+constexpr double kOmega = PIC_MG_OMEGA;  // relaxation factor of the red-black Gauss-Seidel sweeps
 
 struct Dims {
     int nx, ny, nz;
@@ -57,14 +71,15 @@ __global__ void k_rbgs(T* __restrict__ u, const T* __restrict__ f, Dims d, T h2,
     const int P = d.nx * d.ny;
     const int n = k * P + j * d.nx + i;
     if (zero) {   // first sweep from a zero guess: the neighbours are still zero
-        u[n] = (h2 * f[n]) * (T)(1.0 / 6.0);
+        u[n] = (T)kOmega * (h2 * f[n]) * (T)(1.0 / 6.0);
         return;
     }
     const int row = n - i;
     const int ip = (i + 1 == d.nx) ? 0 : i + 1, im = (i == 0) ? d.nx - 1 : i - 1;
     const int jp = (j + 1 == d.ny) ? -j * d.nx : d.nx, jm = (j == 0) ? (d.ny - 1) * d.nx : -d.nx;
     const T s = u[row + ip] + u[row + im] + u[n + jp] + u[n + jm] + u[n + P] + u[n - P];
-    u[n] = (s + h2 * f[n]) * (T)(1.0 / 6.0);
+    const T gs = (s + h2 * f[n]) * (T)(1.0 / 6.0);
+    u[n] = kOmega == 1.0 ? gs : u[n] + (T)kOmega * (gs - u[n]);
 }
 
 // r = f - A u on the interior planes (the electrode planes of r stay zero)
@@ -111,6 +126,43 @@ __global__ void k_restrict(const T* __restrict__ rf, T* __restrict__ fc, Dims df
             pa += w[b] * (w[0] * rr[cols[0]] + w[1] * rr[cols[1]] + w[2] * rr[cols[2]]);
         }
         acc += w[a] * pa;
+    }
+    fc[K * dc.nx * dc.ny + J * dc.nx + I] = acc;
+}
+
+// restriction of the residual f - A u, computed on the fly at the 27 fine
+// points of each coarse interior node (one kernel instead of two)
+template <typename T>
+__global__ void k_resid_restrict(const T* __restrict__ u, const T* __restrict__ f, T* __restrict__ fc, Dims df, Dims dc,
+                                 T inv_h2)
+{
+    const int I = blockIdx.x * blockDim.x + threadIdx.x;
+    const int J = blockIdx.y * blockDim.y + threadIdx.y;
+    const int K = 1 + blockIdx.z;
+    if (I >= dc.nx || J >= dc.ny) return;
+    const int Pf = df.nx * df.ny;
+    const int i0 = 2 * I, j0 = 2 * J, k0 = 2 * K;
+    const int cols[3] = {(i0 == 0) ? df.nx - 1 : i0 - 1, i0, i0 + 1};
+    const int rows[3] = {(j0 == 0) ? df.ny - 1 : j0 - 1, j0, j0 + 1};
+    const T w[3] = {(T)0.25, (T)0.5, (T)0.25};
+    T acc = (T)0;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const int k = k0 - 1 + a;
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+            const int j = rows[b];
+            const int jp = (j + 1 == df.ny) ? 0 : j + 1, jm = (j == 0) ? df.ny - 1 : j - 1;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const int i = cols[c];
+                const int ip = (i + 1 == df.nx) ? 0 : i + 1, im = (i == 0) ? df.nx - 1 : i - 1;
+                const int m = k * Pf + j * df.nx + i;
+                const T sum = u[m - i + ip] + u[m - i + im] + u[k * Pf + jp * df.nx + i] + u[k * Pf + jm * df.nx + i] +
+                              u[m + Pf] + u[m - Pf];
+                acc += (w[a] * w[b] * w[c]) * (f[m] - ((T)6 * u[m] - sum) * inv_h2);
+            }
+        }
     }
     fc[K * dc.nx * dc.ny + J * dc.nx + I] = acc;
 }
@@ -229,13 +281,18 @@ __global__ void k_copy_planes(const double* __restrict__ phi, double* __restrict
 }
 
 // f = rho_q * scale on every node; electrode values on both phi buffers;
-// ||b||^2 with the electrode terms of the nodes next to the planes
+// ||b||^2 with the electrode terms of the nodes next to the planes.  When
+// vb_last (the lower electrode value of the previous solve) is given, the
+// warm start moves by the change of the electrode ramp, (vb - vb_last)(1 - z/Lz),
+// which the 7-point operator maps to zero: the starting residual then holds
+// only the change of rho.
 __global__ void k_rhs(const unsigned long long* __restrict__ rq, double scale, double* __restrict__ f,
                       double* __restrict__ phi, double* __restrict__ phi_alt, double vb, double vt, Dims d,
-                      double inv_h2, double* norm2)
+                      double inv_h2, double* norm2, const double* vb_last)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    const double shift = vb_last ? vb - *vb_last : 0.0;
     double acc = 0.0;
     if (i < d.nx && j < d.ny)
         for (int k = blockIdx.z; k <= d.nz; k += gridDim.z) {
@@ -245,6 +302,7 @@ __global__ void k_rhs(const unsigned long long* __restrict__ rq, double scale, d
             if (k == 0) { phi[n] = vb; phi_alt[n] = vb; }
             else if (k == d.nz) { phi[n] = vt; phi_alt[n] = vt; }
             else {
+                if (shift != 0.0) phi[n] += shift * (1.0 - (double)k / (double)d.nz);
                 double b = fv;
                 if (k == 1) b += vb * inv_h2;
                 if (k == d.nz - 1) b += vt * inv_h2;
@@ -254,6 +312,8 @@ __global__ void k_rhs(const unsigned long long* __restrict__ rq, double scale, d
     acc = block_sum(acc);
     if (tid_flat() == 0) atomicAdd(norm2, acc);
 }
+
+__global__ void k_store(double* dst, double v) { *dst = v; }
 
 // phi += e on the interior nodes
 template <typename T>
@@ -273,13 +333,15 @@ __device__ __forceinline__ double bottom_potential(const SolveParams& sp, uint32
     return sp.v_dc + sp.v_rf * sin((2.0 * kPI * sp.f_rf) * t + sp.phase);
 }
 
-// f = rho_q * scale; electrode values on phi; ||b||^2 added into norm[0]
+// f = rho_q * scale; electrode values on phi; ||b||^2 added into norm[0];
+// warm start moved by the change of the electrode ramp (as in k_rhs)
 __global__ void k_rhs_dev(const unsigned long long* __restrict__ rq, double* __restrict__ f, double* __restrict__ phi,
-                          Dims d, SolveParams sp, const uint32_t* step, double* norm2)
+                          Dims d, SolveParams sp, const uint32_t* step, double* norm2, const double* vb_last)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y * blockDim.y + threadIdx.y;
     const double vb = bottom_potential(sp, *step), vt = sp.v_top;
+    const double shift = vb - *vb_last;
     double acc = 0.0;
     if (i < d.nx && j < d.ny)
         for (int k = blockIdx.z; k <= d.nz; k += gridDim.z) {
@@ -289,6 +351,7 @@ __global__ void k_rhs_dev(const unsigned long long* __restrict__ rq, double* __r
             if (k == 0) phi[n] = vb;
             else if (k == d.nz) phi[n] = vt;
             else {
+                if (shift != 0.0) phi[n] += shift * (1.0 - (double)k / (double)d.nz);
                 double b = fv;
                 if (k == 1) b += vb * sp.inv_h2;
                 if (k == d.nz - 1) b += vt * sp.inv_h2;
@@ -302,8 +365,10 @@ __global__ void k_rhs_dev(const unsigned long long* __restrict__ rq, double* __r
 // loop control of the graph solve: after each residual, decide whether to run
 // another refinement iteration; record iterations, residual and non-convergence
 __global__ void k_conv(double* norm, unsigned int* iters, double* res_out, int* flag, unsigned long long* total,
-                       double tol2, int max_iters, int first, cudaGraphConditionalHandle h)
+                       double tol2, int max_iters, int first, cudaGraphConditionalHandle h, double* vb_last,
+                       SolveParams sp, const uint32_t* step)
 {
+    if (first) *vb_last = bottom_potential(sp, *step);
     const double b2 = norm[0], r2 = norm[1];
     const double target2 = tol2 * (b2 > 0.0 ? b2 : 1.0);
     unsigned int it = first ? 0u : *iters + 1u;
@@ -574,6 +639,12 @@ void run_restrict(cudaStream_t s, const T* rf, T* fc, Dims df, Dims dc)
     k_restrict<T><<<g.grid, g.block, 0, s>>>(rf, fc, df, dc);
 }
 template <typename T>
+void run_resid_restrict(cudaStream_t s, const T* u, const T* f, T* fc, Dims df, Dims dc, T inv_h2)
+{
+    const Grid3 g = grid3(dc.nx, dc.ny, dc.nz - 1);
+    k_resid_restrict<T><<<g.grid, g.block, 0, s>>>(u, f, fc, df, dc, inv_h2);
+}
+template <typename T>
 void run_prolong(cudaStream_t s, T* uf, const T* uc, Dims df, Dims dc)
 {
     const Grid3 g = grid3(df.nx, df.ny, df.nz - 1);
@@ -620,19 +691,16 @@ void vcycle(pic_ctx* c, int l)
     T* u = (T*)L.u;
     T* f = (T*)L.f;
     // pre-smoothing from a zero guess: the first colour-0 pass needs no neighbours
-    run_rbgs<T>(c->stream, u, f, d, h2, 0, 1);
-    run_rbgs<T>(c->stream, u, f, d, h2, 1, 0);
-    run_rbgs<T>(c->stream, u, f, d, h2, 0, 0);
-    run_rbgs<T>(c->stream, u, f, d, h2, 1, 0);
-    run_resid<T>(c->stream, u, f, (T*)L.r, d, (T)(1.0 / (L.h * L.h)));
+    for (int s = 0; s < kPre; ++s)
+        for (int color = 0; color < 2; ++color) run_rbgs<T>(c->stream, u, f, d, h2, color, s == 0 && color == 0);
     MGLevel& C = c->mg[l + 1];
     const Dims dc{C.nx, C.ny, C.nz};
-    run_restrict<T>(c->stream, (const T*)L.r, (T*)C.f, d, dc);
-    c->launches += 6;
+    run_resid_restrict<T>(c->stream, u, f, (T*)C.f, d, dc, (T)(1.0 / (L.h * L.h)));
+    c->launches += 2 * kPre + 1;
     vcycle<T>(c, l + 1);
     run_prolong<T>(c->stream, u, (const T*)C.u, d, dc);
-    c->launches += 5;
-    for (int s = 0; s < 2; ++s)
+    c->launches += 1 + 2 * kPost;
+    for (int s = 0; s < kPost; ++s)
         for (int color = 0; color < 2; ++color) run_rbgs<T>(c->stream, u, f, d, h2, color, 0);
 }
 
@@ -689,7 +757,7 @@ void enqueue_iteration(pic_ctx* c, double tol, int max_iters, cudaGraphCondition
     run_resid64<T>(c->stream, c->phi, (const T*)nullptr, c->f64, nullptr, (T*)c->mg[0].f, c->d_norm + 1, d,
                    1.0 / (c->dx * c->dx));
     k_conv<<<1, 1, 0, c->stream>>>(c->d_norm, c->d_iters, c->d_res, c->d_solve_flag, c->d_iter_total, tol * tol,
-                                   max_iters, 0, h);
+                                   max_iters, 0, h, c->d_vb_last, c->sp, c->d_step);
     c->launches += 3;
 }
 
@@ -701,11 +769,12 @@ void enqueue_head(pic_ctx* c, double tol, int max_iters, cudaGraphConditionalHan
     const Dims d{c->nx, c->ny, c->nz};
     cudaMemsetAsync(c->d_norm, 0, 2 * sizeof(double), c->stream);
     const Grid3 g = grid_norm(d.nx, d.ny, d.nz + 1);
-    k_rhs_dev<<<g.grid, g.block, 0, c->stream>>>(c->rq, c->f64, c->phi, d, c->sp, c->d_step, c->d_norm);
+    k_rhs_dev<<<g.grid, g.block, 0, c->stream>>>(c->rq, c->f64, c->phi, d, c->sp, c->d_step, c->d_norm,
+                                                c->d_vb_last);
     run_resid64<T>(c->stream, c->phi, (const T*)nullptr, c->f64, nullptr, (T*)c->mg[0].f, c->d_norm + 1, d,
                    1.0 / (c->dx * c->dx));
     k_conv<<<1, 1, 0, c->stream>>>(c->d_norm, c->d_iters, c->d_res, c->d_solve_flag, c->d_iter_total, tol * tol,
-                                   max_iters, 1, h);
+                                   max_iters, 1, h, c->d_vb_last, c->sp, c->d_step);
     c->launches += 3;
 }
 
@@ -829,8 +898,9 @@ void launch_rhs(pic_ctx* c, double scale, double v_bot, double v_top, bool)
     cudaMemsetAsync(c->d_norm, 0, sizeof(double), c->stream);
     const Grid3 g = grid_norm(d.nx, d.ny, d.nz + 1);
     k_rhs<<<g.grid, g.block, 0, c->stream>>>(c->rq, scale, c->f64, c->phi, c->phi_alt, v_bot, v_top, d,
-                                            1.0 / (c->dx * c->dx), c->d_norm);
-    c->launches += 1;
+                                            1.0 / (c->dx * c->dx), c->d_norm, c->d_vb_last);
+    k_store<<<1, 1, 0, c->stream>>>(c->d_vb_last, v_bot);
+    c->launches += 2;
 }
 
 pic_status mg_solve(pic_ctx* c, double, double, double tol, int max_iters, int* iters, double* res)
@@ -1014,7 +1084,7 @@ extern "C" pic_status pic_solve_noalloc(int32_t nx, int32_t ny, int32_t nz, doub
     cudaMemsetAsync(norm, 0, sizeof(double), c.s);
     const Grid3 g = grid_norm(nx, ny, nz + 1);
     k_rhs<<<g.grid, g.block, 0, c.s>>>((const unsigned long long*)rho_q_dev, scale, f64, phi_dev, phi_alt, v_bot,
-                                      v_top, d, 1.0 / (dx * dx), norm);
+                                      v_top, d, 1.0 / (dx * dx), norm, (const double*)nullptr);
     int it = 0;
     double res = 0.0;
     st = prec == PIC_MIXED ? na_solve<float>(c, phi_dev, phi_alt, f64, norm, d, dx, tol, max_iters, &it, &res)
