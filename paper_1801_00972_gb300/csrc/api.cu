@@ -465,8 +465,9 @@ pic_status pic_init(const pic_mesh* mesh, const pic_electrodes* el, const pic_ga
                             c->stream);
             cudaMemsetAsync(c->rq, 0, sizeof(unsigned long long) * nodes, c->stream);
             launch_grains(c);
-            launch_rhs(c, scale1, 0.0, 0.0, true);
             cudaMemsetAsync(c->phi, 0, sizeof(double) * nodes, c->stream);
+            if (c->phi2) cudaMemsetAsync(c->phi2, 0, sizeof(float2) * nodes, c->stream);
+            launch_rhs(c, scale1, 0.0, 0.0, false);
             int it = 0;
             double res = 0;
             const pic_status s = mg_solve(c, 0.0, 0.0, 1e-12, 200, &it, &res);
@@ -474,10 +475,12 @@ pic_status pic_init(const pic_mesh* mesh, const pic_electrodes* el, const pic_ga
                 destroy(c);
                 return fail(nullptr, s, "grain field solve did not converge");
             }
+            phi_sync_f64(c);
             launch_grain_table(c, g);
         }
         cudaMemsetAsync(c->gabs, 0, sizeof(unsigned long long) * 2 * ng1, c->stream);
         cudaMemsetAsync(c->phi, 0, sizeof(double) * nodes, c->stream);
+        if (c->phi2) cudaMemsetAsync(c->phi2, 0, sizeof(float2) * 2 * nodes, c->stream);
         std::vector<double> tab(kTab * (size_t)ng1);
         e = cudaMemcpyAsync(tab.data(), c->gtab, sizeof(double) * tab.size(), cudaMemcpyDeviceToHost, c->stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
@@ -617,6 +620,17 @@ cudaGraphExec_t capture_solve(pic_ctx* c)
                 ok = cudaStreamEndCapture(c->cap_stream, &body) == cudaSuccess;
             }
             c->n_solve_body = (int)(c->launches - l1);
+        }
+        // after the loop
+        if (ok) {
+            const int64_t l2 = c->launches;
+            ok = cudaStreamBeginCaptureToGraph(c->cap_stream, g, &cn, nullptr, 1, cudaStreamCaptureModeThreadLocal) ==
+                 cudaSuccess;
+            if (ok) {
+                enqueue_solve_tail(c);
+                ok = cudaStreamEndCapture(c->cap_stream, &g) == cudaSuccess;
+            }
+            c->n_solve_head += (int)(c->launches - l2);
         }
     }
     if (ok && cudaGraphInstantiate(&ex, g, 0) != cudaSuccess) ex = nullptr;
@@ -945,7 +959,9 @@ pic_status pic_get_phi(pic_ctx* c, double* phi, size_t len)
     if (!c || !phi || len != c->nodes) return c ? fail(c, PIC_EINVAL, "phi length") : PIC_EINVAL;
     pic_status k = check(c);
     if (k != PIC_OK) return k;
-    const cudaError_t e = cudaMemcpy(phi, c->phi, sizeof(double) * len, cudaMemcpyDeviceToHost);
+    phi_sync_f64(c);
+    cudaError_t e = cudaMemcpyAsync(phi, c->phi, sizeof(double) * len, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     return e == cudaSuccess ? PIC_OK : cuda_fail(c, e, "phi copy");
 }
 
@@ -954,7 +970,9 @@ pic_status pic_set_phi(pic_ctx* c, const double* phi, size_t len)
     if (!c || !phi || len != c->nodes) return c ? fail(c, PIC_EINVAL, "phi length") : PIC_EINVAL;
     pic_status k = check(c);
     if (k != PIC_OK) return k;
-    const cudaError_t e = cudaMemcpy(c->phi, phi, sizeof(double) * len, cudaMemcpyHostToDevice);
+    cudaError_t e = cudaMemcpyAsync(c->phi, phi, sizeof(double) * len, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) phi_from_f64(c);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     return e == cudaSuccess ? PIC_OK : cuda_fail(c, e, "phi copy");
 }
 

@@ -20,6 +20,7 @@
 //             runs on a second stream alongside k_push32): Dt/40 substeps with
 //             the PPPM correction, grain absorption, MCC, deposit.
 //   k_mcc32   the collision candidates: process selection and kinematics.
+#include <algorithm>
 #include <climits>
 
 #include "pic_internal.cuh"
@@ -771,25 +772,37 @@ __global__ void k_deposit32(int nx, int ny, const float4* pos, const unsigned lo
     }
 }
 
-__global__ void k_efield32(int nx, int ny, int nz, double dx, const double* __restrict__ phi, float4* __restrict__ E)
+// E = -grad phi on every node from the double-float potential: central
+// differences in x, y and between the electrode planes, second-order one-sided
+// differences on the planes.  Each difference of neighbouring values is taken
+// part by part, (hi_a - hi_b) + (lo_a - lo_b), and rounded once to float.
+__global__ void k_efield32(int nx, int ny, int nz, float inv_2dx, const float2* __restrict__ phi,
+                           float4* __restrict__ E)
 {
-    const size_t P = (size_t)nx * ny;
-    const size_t N = P * (nz + 1);
-    const double h2 = 2.0 * dx;
-    for (size_t n = blockIdx.x * (size_t)blockDim.x + threadIdx.x; n < N; n += (size_t)gridDim.x * blockDim.x) {
-        const int i = (int)(n % nx);
-        const int j = (int)((n / nx) % ny);
-        const int k = (int)(n / P);
-        const size_t row = ((size_t)k * ny + j) * nx;
-        const double ex = (phi[row + (i + nx - 1) % nx] - phi[row + (i + 1) % nx]) / h2;
-        const double ey = (phi[((size_t)k * ny + (j + ny - 1) % ny) * nx + i] -
-                           phi[((size_t)k * ny + (j + 1) % ny) * nx + i]) / h2;
-        double ez;
-        if (k == 0) ez = ((3.0 * phi[n] - 4.0 * phi[n + P]) + phi[n + 2 * P]) / h2;
-        else if (k == nz) ez = ((4.0 * phi[n - P] - 3.0 * phi[n]) - phi[n - 2 * P]) / h2;
-        else ez = (phi[n - P] - phi[n + P]) / h2;
-        E[n] = make_float4((float)ex, (float)ey, (float)ez, 0.f);
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    const int k = blockIdx.z;
+    if (i >= nx || j >= ny) return;
+    const int P = nx * ny;
+    const int n = k * P + j * nx + i;
+    const int row = n - i;
+    const float2 xm = phi[row + (i == 0 ? nx - 1 : i - 1)], xp = phi[row + (i + 1 == nx ? 0 : i + 1)];
+    const float2 ym = phi[k * P + (j == 0 ? ny - 1 : j - 1) * nx + i], yp = phi[k * P + (j + 1 == ny ? 0 : j + 1) * nx + i];
+    const float ex = ((xm.x - xp.x) + (xm.y - xp.y)) * inv_2dx;
+    const float ey = ((ym.x - yp.x) + (ym.y - yp.y)) * inv_2dx;
+    float ez;
+    if (k == 0 || k == nz) {
+        // 3 phi_0 - 4 phi_1 + phi_2 = 3 (phi_0 - phi_1) - (phi_1 - phi_2), planes counted inwards
+        const int s = k == 0 ? P : -P;
+        const float2 a = phi[n], b = phi[n + s], c = phi[n + 2 * s];
+        const float d01 = (a.x - b.x) + (a.y - b.y), d12 = (b.x - c.x) + (b.y - c.y);
+        ez = (3.f * d01 - d12) * inv_2dx;
+        if (k == nz) ez = -ez;
+    } else {
+        const float2 zm = phi[n - P], zp = phi[n + P];
+        ez = ((zm.x - zp.x) + (zm.y - zp.y)) * inv_2dx;
     }
+    E[n] = make_float4(ex, ey, ez, 0.f);
 }
 
 __global__ void k_children32(int nx, int ny, ChildRec* rec, const unsigned long long* nch,
@@ -980,8 +993,10 @@ void launch_deposit32(pic_ctx* c)
 
 void launch_efield32(pic_ctx* c)
 {
-    k_efield32<<<grid_for((int64_t)c->nodes, 256, 152 * 8), 256, 0, c->stream>>>(c->nx, c->ny, c->nz, c->dx, c->phi,
-                                                                                c->e32);
+    const int bx = c->nx >= 32 ? 32 : c->nx, by = std::max(1, std::min(c->ny, 256 / bx));
+    const dim3 grid((unsigned)((c->nx + bx - 1) / bx), (unsigned)((c->ny + by - 1) / by), (unsigned)(c->nz + 1));
+    k_efield32<<<grid, dim3((unsigned)bx, (unsigned)by), 0, c->stream>>>(c->nx, c->ny, c->nz,
+                                                                         (float)(1.0 / (2.0 * c->dx)), c->phi2, c->e32);
     c->launches += 1;
 }
 
@@ -1007,6 +1022,7 @@ void launch_moments32(pic_ctx* c)
 
 void launch_moments_phi(pic_ctx* c)
 {
+    phi_sync_f64(c);
     k_moments_phi<<<grid_for((int64_t)c->nodes, 256, 152 * 4), 256, 0, c->stream>>>(c->phi, c->mphi, c->nodes);
     c->launches += 1;
 }

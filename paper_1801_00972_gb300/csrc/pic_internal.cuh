@@ -105,14 +105,22 @@ struct RStream {
 
 // ---------------------------------------------------------------- context
 constexpr int kMaxDense = 1024;   // coarsest-level unknowns solved with a dense inverse
-constexpr size_t kTailSmem = 200 * 1024;   // shared memory of the one-block tail of a V-cycle
-constexpr size_t kTailNodes = 2500;         // largest level in that tail
+constexpr size_t kTailNodes = 2500;         // largest multigrid level held by one CTA
 
 // constants of the graph solve's right-hand side and electrode values
 struct SolveParams {
     double scale;       // rho_q units -> rho / eps0
     double inv_h2;
     double v_dc, v_rf, f_rf, phase, v_top, dt;
+};
+
+// device state of the mixed-precision (double-float) refinement
+struct DfState {
+    unsigned int cnt_head, cnt_res;   // block counters of the grid sums (wrap to 0)
+    int sel;                          // buffer holding the current potential during a solve
+    int more;                         // loop decision of the last residual
+    int status;                       // PIC_OK, PIC_ENOTCONV or PIC_ENONFINITE after the last residual
+    float b2;                         // ||h^2 b||^2 of the current solve
 };
 
 struct MGLevel {
@@ -200,13 +208,18 @@ struct pic_ctx {
     // multigrid
     std::vector<pic::MGLevel> mg;
     void* coarse_inv = nullptr;              // dense inverse of the coarsest level (T)
-    int mg_tail = 0;                         // first level handled by the one-block tail kernel
+    int mg_tail = 0;                         // first level handled by the cluster kernel
+    int cl_size = 1;                         // CTAs in that cluster
     pic::SolveParams sp;
     unsigned int* d_iters = nullptr;         // graph solve: iterations of the last solve
     double* d_res = nullptr;                 // graph solve: relative residual of the last solve
     int* d_solve_flag = nullptr;             // graph solve: PIC_ENOTCONV / PIC_ENONFINITE latch
     uint32_t* d_step = nullptr;              // device copy of the step counter
     double* d_vb_last = nullptr;             // lower electrode value of the last solve
+    float2* phi2 = nullptr;                  // mixed: potential as hi + lo floats, two buffers of nodes
+    float2* f2 = nullptr;                    // mixed: h^2 rho / eps0 as hi + lo floats
+    float* d_part = nullptr;                 // mixed: per-block partial sums
+    pic::DfState* d_dfs = nullptr;
     unsigned long long* d_iter_total = nullptr;  // refinement iterations of all graph solves
 
     // CUDA graphs of one step, captured lazily on a private stream and
@@ -265,11 +278,14 @@ size_t sort_scratch_setup(pic_ctx* c);
 
 // poisson.cu
 pic_status mg_setup(pic_ctx* c);
-void launch_rhs(pic_ctx* c, double scale, double v_bot, double v_top, bool from_rq);
+void launch_rhs(pic_ctx* c, double scale, double v_bot, double v_top, bool warm_shift);
+void phi_sync_f64(pic_ctx* c);       // mixed: write the FP64 copy of the potential
+void phi_from_f64(pic_ctx* c);       // mixed: potential from the FP64 copy
 pic_status mg_solve(pic_ctx* c, double v_bot, double v_top, double tol, int max_iters, int* iters, double* res);
 // graph solve pieces (enqueued on c->stream during capture)
 void enqueue_solve_head(pic_ctx* c, double tol, int max_iters, cudaGraphConditionalHandle h);
 void enqueue_solve_iteration(pic_ctx* c, double tol, int max_iters, cudaGraphConditionalHandle h);
+void enqueue_solve_tail(pic_ctx* c);
 
 // api.cu
 void* dev_alloc(pic_ctx* c, size_t bytes);

@@ -16,6 +16,8 @@
 #include <mutex>
 #include <vector>
 
+#include <cooperative_groups.h>
+
 #include "pic_internal.cuh"
 
 #ifndef PIC_MG_PRE
@@ -24,16 +26,26 @@
 #ifndef PIC_MG_POST
 #define PIC_MG_POST 2
 #endif
-#ifndef PIC_MG_OMEGA
-#define PIC_MG_OMEGA 1.0
+#ifndef PIC_MG_CLUSTER
+#define PIC_MG_CLUSTER 16      // largest cluster (CTAs) for the small levels
+#endif
+#ifndef PIC_MG_CLUSTER_FROM
+#define PIC_MG_CLUSTER_FROM 2  // first level that may run in the cluster
+#endif
+#ifndef PIC_PDL
+#define PIC_PDL 1              // programmatic dependent launch between solver kernels
+#endif
+#ifndef PIC_MG_CL_THREADS
+#define PIC_MG_CL_THREADS 512  // threads per CTA of the cluster
 #endif
 
 namespace pic {
 namespace {
 
+namespace cg = cooperative_groups;
+
 constexpr int kPre = PIC_MG_PRE;         // pre-smoothing sweeps of a V-cycle
 constexpr int kPost = PIC_MG_POST;       // post-smoothing sweeps
-constexpr double kOmega = PIC_MG_OMEGA;  // relaxation factor of the red-black Gauss-Seidel sweeps
 
 struct Dims {
     int nx, ny, nz;
@@ -59,10 +71,38 @@ inline Grid3 grid3(int nx, int ny, int planes)
 
 __device__ __forceinline__ int tid_flat() { return threadIdx.y * blockDim.x + threadIdx.x; }
 
+// Programmatic dependent launch: the solver's kernels are queued with the
+// programmatic-serialization attribute, so the next kernel's blocks can be
+// scheduled while this one drains.  Each kernel waits for its predecessor's
+// completion (and memory) before touching anything, in every thread, so the
+// ordering stays transitive; it then lets its own successor launch.
+__device__ __forceinline__ void pdl_begin()
+{
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+template <typename... KArgs, typename... Args>
+inline void launch_pdl(cudaStream_t s, dim3 grid, dim3 block, void (*kernel)(KArgs...), Args... args)
+{
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = PIC_PDL ? 1 : 0;
+    cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 // red-black Gauss-Seidel, one colour; thread (i2, j) of plane k = 1 + blockIdx.z
 template <typename T>
 __global__ void k_rbgs(T* __restrict__ u, const T* __restrict__ f, Dims d, T h2, int color, int zero)
 {
+    pdl_begin();
     const int i2 = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y * blockDim.y + threadIdx.y;
     const int k = 1 + blockIdx.z;
@@ -71,15 +111,14 @@ __global__ void k_rbgs(T* __restrict__ u, const T* __restrict__ f, Dims d, T h2,
     const int P = d.nx * d.ny;
     const int n = k * P + j * d.nx + i;
     if (zero) {   // first sweep from a zero guess: the neighbours are still zero
-        u[n] = (T)kOmega * (h2 * f[n]) * (T)(1.0 / 6.0);
+        u[n] = (h2 * f[n]) * (T)(1.0 / 6.0);
         return;
     }
     const int row = n - i;
     const int ip = (i + 1 == d.nx) ? 0 : i + 1, im = (i == 0) ? d.nx - 1 : i - 1;
     const int jp = (j + 1 == d.ny) ? -j * d.nx : d.nx, jm = (j == 0) ? (d.ny - 1) * d.nx : -d.nx;
     const T s = u[row + ip] + u[row + im] + u[n + jp] + u[n + jm] + u[n + P] + u[n - P];
-    const T gs = (s + h2 * f[n]) * (T)(1.0 / 6.0);
-    u[n] = kOmega == 1.0 ? gs : u[n] + (T)kOmega * (gs - u[n]);
+    u[n] = (s + h2 * f[n]) * (T)(1.0 / 6.0);
 }
 
 // r = f - A u on the interior planes (the electrode planes of r stay zero)
@@ -130,47 +169,55 @@ __global__ void k_restrict(const T* __restrict__ rf, T* __restrict__ fc, Dims df
     fc[K * dc.nx * dc.ny + J * dc.nx + I] = acc;
 }
 
-// restriction of the residual f - A u, computed on the fly at the 27 fine
-// points of each coarse interior node (one kernel instead of two)
+// residual f - A u at fine node (i, j, k)
 template <typename T>
-__global__ void k_resid_restrict(const T* __restrict__ u, const T* __restrict__ f, T* __restrict__ fc, Dims df, Dims dc,
-                                 T inv_h2)
+__device__ __forceinline__ T res_at(const T* __restrict__ u, const T* __restrict__ f, Dims d, int i, int j, int k,
+                                    T inv_h2)
 {
+    const int P = d.nx * d.ny;
+    const int ip = (i + 1 == d.nx) ? 0 : i + 1, im = (i == 0) ? d.nx - 1 : i - 1;
+    const int jp = (j + 1 == d.ny) ? 0 : j + 1, jm = (j == 0) ? d.ny - 1 : j - 1;
+    const int row = k * P + j * d.nx, n = row + i;
+    const T s = u[row + ip] + u[row + im] + u[k * P + jp * d.nx + i] + u[k * P + jm * d.nx + i] + u[n + P] + u[n - P];
+    return f[n] - ((T)6 * u[n] - s) * inv_h2;
+}
+
+// Full-weighting restriction of the residual f - A u, computed on the fly.
+// After the black half-sweep that ends the pre-smoothing the residual is zero
+// at the black nodes, so only the 13 red points of the 27 enter (weight 1/8
+// at the coincident node, 1/32 at the 12 with two odd offsets).  The coarse
+// correction starts from zero: its first red half-sweep, h^2 f / 6 at the red
+// coarse nodes, is written here as well.  Thread (I, J) of coarse plane
+// K = 1 + blockIdx.z.
+template <typename T>
+__global__ void k_resid_restrict(const T* __restrict__ u, const T* __restrict__ f, T* __restrict__ fc,
+                                 T* __restrict__ uc, Dims df, Dims dc, T inv_h2, T h2c)
+{
+    pdl_begin();
     const int I = blockIdx.x * blockDim.x + threadIdx.x;
     const int J = blockIdx.y * blockDim.y + threadIdx.y;
     const int K = 1 + blockIdx.z;
     if (I >= dc.nx || J >= dc.ny) return;
-    const int Pf = df.nx * df.ny;
     const int i0 = 2 * I, j0 = 2 * J, k0 = 2 * K;
-    const int cols[3] = {(i0 == 0) ? df.nx - 1 : i0 - 1, i0, i0 + 1};
-    const int rows[3] = {(j0 == 0) ? df.ny - 1 : j0 - 1, j0, j0 + 1};
-    const T w[3] = {(T)0.25, (T)0.5, (T)0.25};
-    T acc = (T)0;
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        const int k = k0 - 1 + a;
-#pragma unroll
-        for (int b = 0; b < 3; ++b) {
-            const int j = rows[b];
-            const int jp = (j + 1 == df.ny) ? 0 : j + 1, jm = (j == 0) ? df.ny - 1 : j - 1;
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                const int i = cols[c];
-                const int ip = (i + 1 == df.nx) ? 0 : i + 1, im = (i == 0) ? df.nx - 1 : i - 1;
-                const int m = k * Pf + j * df.nx + i;
-                const T sum = u[m - i + ip] + u[m - i + im] + u[k * Pf + jp * df.nx + i] + u[k * Pf + jm * df.nx + i] +
-                              u[m + Pf] + u[m - Pf];
-                acc += (w[a] * w[b] * w[c]) * (f[m] - ((T)6 * u[m] - sum) * inv_h2);
-            }
-        }
-    }
-    fc[K * dc.nx * dc.ny + J * dc.nx + I] = acc;
+    const int im = (i0 == 0) ? df.nx - 1 : i0 - 1, ip = i0 + 1;
+    const int jm = (j0 == 0) ? df.ny - 1 : j0 - 1, jp = j0 + 1;
+    T e = res_at(u, f, df, im, jm, k0, inv_h2) + res_at(u, f, df, ip, jm, k0, inv_h2) +
+          res_at(u, f, df, im, jp, k0, inv_h2) + res_at(u, f, df, ip, jp, k0, inv_h2);
+    e += res_at(u, f, df, im, j0, k0 - 1, inv_h2) + res_at(u, f, df, ip, j0, k0 - 1, inv_h2) +
+         res_at(u, f, df, im, j0, k0 + 1, inv_h2) + res_at(u, f, df, ip, j0, k0 + 1, inv_h2);
+    e += res_at(u, f, df, i0, jm, k0 - 1, inv_h2) + res_at(u, f, df, i0, jp, k0 - 1, inv_h2) +
+         res_at(u, f, df, i0, jm, k0 + 1, inv_h2) + res_at(u, f, df, i0, jp, k0 + 1, inv_h2);
+    const T v = (T)0.125 * res_at(u, f, df, i0, j0, k0, inv_h2) + (T)0.03125 * e;
+    const int nc = K * dc.nx * dc.ny + J * dc.nx + I;
+    fc[nc] = v;
+    if (((I + J + K) & 1) == 0) uc[nc] = h2c * v * (T)(1.0 / 6.0);
 }
 
 // trilinear interpolation of the coarse correction, added on the fine interior
 template <typename T>
 __global__ void k_prolong(T* __restrict__ uf, const T* __restrict__ uc, Dims df, Dims dc)
 {
+    pdl_begin();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y * blockDim.y + threadIdx.y;
     const int k = 1 + blockIdx.z;
@@ -383,231 +430,445 @@ __global__ void k_conv(double* norm, unsigned int* iters, double* res_out, int* 
     cudaGraphSetConditional(h, more ? 1u : 0u);
 }
 
-// ---- the small levels of a V-cycle in one block --------------------------
+// ---- the levels below the grid-wide ones: one thread-block cluster ---------
+// Every level from mg_tail down is held in the shared memory of the CTAs of
+// one cluster.  A level is cut into z slabs, one per CTA (slab boundaries
+// nested between levels: fine plane 2K and coarse plane K have the same
+// owner); the smallest levels sit in CTA 0 alone.  Neighbour planes owned by
+// another CTA are read through distributed shared memory, and the phases of
+// the V-cycle are separated by cluster barriers (CTA barriers on the levels
+// of CTA 0 alone).  The coarsest level is solved with the dense inverse or by
+// many red-black sweeps.
 constexpr int kTailMax = 8;
+constexpr int kClThreads = PIC_MG_CL_THREADS;
+
+// n / d for 0 <= n < 2^31 by a multiply-high and a shift (Granlund and
+// Montgomery's division by invariant integers, round-up variant)
+struct FastDiv {
+    unsigned int m;
+    int s;
+};
+inline FastDiv fast_div(int d)
+{
+    int l = 0;
+    while ((1u << l) < (unsigned)d) ++l;
+    const unsigned long long m = ((1ull << 32) * ((1ull << l) - (unsigned long long)d)) / (unsigned long long)d + 1;
+    return FastDiv{(unsigned int)m, l};
+}
+__device__ __forceinline__ int fdiv(int n, FastDiv f)
+{
+    return (int)((__umulhi((unsigned)n, f.m) + (unsigned)n) >> f.s);
+}
 
 template <typename T>
-struct TailLevels {
-    int n;                        // levels in the tail (the last one is the coarsest)
+struct ClusterLevels {
+    int n;                            // levels; index 0 is mg_tail, n - 1 the coarsest
+    int single;                       // first level held by CTA 0 alone (<= n - 1)
     int nx[kTailMax], ny[kTailMax], nz[kTailMax];
-    double h[kTailMax];
-    T* u[kTailMax];
-    T* f[kTailMax];
-    T* r[kTailMax];
-    const T* ainv;                // dense inverse of the coarsest level, or null
-    int sweeps;                   // coarsest-level sweeps when there is no inverse
+    T h2[kTailMax], ih2[kTailMax];
+    FastDiv f_hx[kTailMax], f_ph[kTailMax];   // nx / 2 and nx ny / 2
+    FastDiv f_x[kTailMax], f_p[kTailMax];     // nx and nx ny
+    unsigned int off[kTailMax];       // byte offset of the level's u block (its f block follows)
+    int mp[kTailMax];                 // planes reserved per CTA
+    int pbase[kTailMax];              // first entry of the level in the plane pointer tables
+    unsigned int ptr_off;             // byte offset of the tables (u pointers, then f pointers)
+    int nplanes;                      // entries per table
+    T* gu;                            // correction of level 0 (out, interior planes)
+    const T* gf;                      // right-hand side of level 0 (in)
+    const T* ainv;                    // dense inverse of the coarsest operator, or null
+    int sweeps;                       // coarsest-level sweeps without an inverse
 };
 
-template <typename T>
-__device__ void tail_rbgs(T* u, const T* f, Dims d, T h2, int color, bool zero)
+// first plane owned by CTA r of C on a distributed level with planes 0..nz (r = C gives nz + 1)
+__device__ __forceinline__ int cl_kfirst(int r, int C, int nz)
 {
-    const int half = d.nx / 2;
-    const int total = half * d.ny * (d.nz - 1);
-    const int P = d.nx * d.ny;
-    for (int t = threadIdx.x; t < total; t += blockDim.x) {
-        const int i2 = t % half;
-        const int j = (t / half) % d.ny;
-        const int k = 1 + t / (half * d.ny);
-        const int i = 2 * i2 + ((j + k + color) & 1);
-        const int n = (k * d.ny + j) * d.nx + i;
-        if (zero) {
-            u[n] = (h2 * f[n]) * (T)(1.0 / 6.0);
-            continue;
+    if (r >= C) return nz + 1;
+    return (r * nz + C - 1) / C;
+}
+__device__ __forceinline__ int cl_owner(int k, int C, int nz)
+{
+    const int o = (k * C) / nz;
+    return o < C - 1 ? o : C - 1;
+}
+// planes [k0, k1) that CTA r holds: its slab, or all of a level every CTA holds
+__device__ __forceinline__ void cl_planes(int r, int C, int nz, bool single, int& k0, int& k1)
+{
+    if (single) {
+        k0 = 0;
+        k1 = nz + 1;
+    } else {
+        k0 = cl_kfirst(r, C, nz);
+        k1 = cl_kfirst(r + 1, C, nz);
+    }
+}
+
+template <typename T>
+struct ClView {
+    T* const* pu;     // plane pointers (generic addresses, local or in another CTA)
+    T* const* pf;
+    int r, C;
+};
+
+// one level as this CTA sees it: levels held by CTA 0 alone are addressed in
+// its own shared memory (plane k at u + k P), distributed levels through the
+// plane tables
+template <typename T>
+struct Lv {
+    T* const* pu;
+    T* const* pf;
+    T* u;
+    T* f;
+    int nx, ny, nz, P;
+    bool local;
+    __device__ __forceinline__ T* U(int k) const { return local ? u + k * P : pu[k]; }
+    __device__ __forceinline__ T* F(int k) const { return local ? f + k * P : pf[k]; }
+};
+
+// One colour of red-black Gauss-Seidel on the interior planes [klo, khi]
+// (omega = 1: a node's new value does not depend on its old one).  Each
+// thread keeps one half-column (i2, j) of a plane and walks the planes
+// k = klo + g, klo + g + G, ...; the node of the colour in plane k is
+// i = 2 i2 or 2 i2 + 1 by the parity of j + k.
+template <typename T>
+__device__ __forceinline__ void cl_rbgs(const Lv<T> a, T h2, int klo, int khi, int color, FastDiv f_ph, FastDiv f_hx)
+{
+    if (khi < klo) return;
+    const int bd = blockDim.x, t = threadIdx.x;
+    const int hx = a.nx / 2, ph = hx * a.ny;
+    int g = 0, G = 1, c = t, cstep = bd;
+    if (ph <= bd) {
+        g = fdiv(t, f_ph);
+        G = bd / ph;
+        if (g >= G) return;
+        c = t - g * ph;
+        cstep = ph;
+    }
+    for (; c < ph; c += cstep) {
+        const int j = fdiv(c, f_hx), i2 = c - j * hx;
+        const int jr = j * a.nx;
+        const int jpr = (j + 1 == a.ny ? 0 : j + 1) * a.nx, jmr = (j == 0 ? a.ny - 1 : j - 1) * a.nx;
+        const int e0 = 2 * i2, e1 = e0 + 1;
+        const int em0 = (i2 == 0) ? a.nx - 1 : e0 - 1;
+        const int ep1 = (e1 + 1 == a.nx) ? 0 : e1 + 1;
+        for (int k = klo + g; k <= khi; k += G) {
+            const bool odd = ((j + k + color) & 1) != 0;
+            const int i = odd ? e1 : e0, im = odd ? e0 : em0, ip = odd ? ep1 : e1;
+            T* u = a.U(k);
+            const int n = jr + i;
+            const T s = u[jr + im] + u[jr + ip] + u[jpr + i] + u[jmr + i] + a.U(k + 1)[n] + a.U(k - 1)[n];
+            u[n] = (s + h2 * a.F(k)[n]) * (T)(1.0 / 6.0);
         }
-        const int ip = (i + 1 == d.nx) ? 0 : i + 1, im = (i == 0) ? d.nx - 1 : i - 1;
-        const int jp = (j + 1 == d.ny) ? 0 : j + 1, jm = (j == 0) ? d.ny - 1 : j - 1;
-        const int row = n - i;
-        const T s = u[row + ip] + u[row + im] + u[(k * d.ny + jp) * d.nx + i] + u[(k * d.ny + jm) * d.nx + i] +
-                    u[n + P] + u[n - P];
-        u[n] = (s + h2 * f[n]) * (T)(1.0 / 6.0);
     }
-    __syncthreads();
 }
 
+// residual f - A u at node (i, j) of plane k
 template <typename T>
-__device__ void tail_resid(const T* u, const T* f, T* r, Dims d, T inv_h2)
+__device__ __forceinline__ T cl_res(const Lv<T> a, T ih2, int i, int j, int k)
 {
-    const int P = d.nx * d.ny;
-    const int N = P * (d.nz + 1);
-    for (int n = threadIdx.x; n < N; n += blockDim.x) {
-        const int k = n / P;
-        if (k == 0 || k == d.nz) { r[n] = (T)0; continue; }
-        const int i = n % d.nx, j = (n / d.nx) % d.ny;
-        const int ip = (i + 1 == d.nx) ? 0 : i + 1, im = (i == 0) ? d.nx - 1 : i - 1;
-        const int jp = (j + 1 == d.ny) ? 0 : j + 1, jm = (j == 0) ? d.ny - 1 : j - 1;
-        const int row = n - i;
-        const T s = u[row + ip] + u[row + im] + u[(k * d.ny + jp) * d.nx + i] + u[(k * d.ny + jm) * d.nx + i] +
-                    u[n + P] + u[n - P];
-        r[n] = f[n] - ((T)6 * u[n] - s) * inv_h2;
-    }
-    __syncthreads();
+    const T* u = a.U(k);
+    const int ip = (i + 1 == a.nx) ? 0 : i + 1, im = (i == 0) ? a.nx - 1 : i - 1;
+    const int jp = (j + 1 == a.ny) ? 0 : j + 1, jm = (j == 0) ? a.ny - 1 : j - 1;
+    const int n = j * a.nx + i;
+    const T s = u[j * a.nx + ip] + u[j * a.nx + im] + u[jp * a.nx + i] + u[jm * a.nx + i] + a.U(k + 1)[n] +
+                a.U(k - 1)[n];
+    return a.F(k)[n] - ((T)6 * u[n] - s) * ih2;
 }
 
+// Full-weighting restriction of the fine residual to the coarse interior
+// planes [Klo, Khi].  After a black half-sweep the residual is zero at the
+// black nodes, so only the 13 red points of the 27 enter: weight 1/8 at the
+// coincident node and 1/32 at the 12 with two odd offsets.  The coarse
+// correction starts from zero, so its first red half-sweep (h^2 f / 6) is
+// written here too.  With bcast > 0 the coarse level is one that every CTA
+// holds, and the values go to all bcast copies.
 template <typename T>
-__device__ void tail_restrict(const T* rf, T* fc, Dims df, Dims dc)
+__device__ __forceinline__ void cl_restrict(const Lv<T> a, const Lv<T> b, T ih2, T h2c, int Klo, int Khi, FastDiv f_pc,
+                            FastDiv f_xc, int bcast)
 {
-    const int P = dc.nx * dc.ny;
-    const int N = P * (dc.nz + 1);
-    for (int n = threadIdx.x; n < N; n += blockDim.x) {
-        const int K = n / P;
-        if (K == 0 || K == dc.nz) { fc[n] = (T)0; continue; }
-        const int I = n % dc.nx, J = (n / dc.nx) % dc.ny;
-        T acc = (T)0;
-        for (int dk = -1; dk <= 1; ++dk) {
-            const T wk = dk == 0 ? (T)0.5 : (T)0.25;
-            for (int dj = -1; dj <= 1; ++dj) {
-                const T wj = dj == 0 ? (T)0.5 : (T)0.25;
-                const int j = (2 * J + dj + df.ny) % df.ny;
-                for (int di = -1; di <= 1; ++di) {
-                    const T wi = di == 0 ? (T)0.5 : (T)0.25;
-                    const int i = (2 * I + di + df.nx) % df.nx;
-                    acc += (wk * wj * wi) * rf[((2 * K + dk) * df.ny + j) * df.nx + i];
-                }
+    if (Khi < Klo) return;
+    const int pc = b.nx * b.ny;
+    const int total = (Khi - Klo + 1) * pc;
+    for (int m = threadIdx.x; m < total; m += blockDim.x) {
+        const int kk = fdiv(m, f_pc);
+        const int rem = m - kk * pc;
+        const int J = fdiv(rem, f_xc);
+        const int I = rem - J * b.nx;
+        const int K = Klo + kk;
+        const int i0 = 2 * I, j0 = 2 * J, k0 = 2 * K;
+        const int im = (i0 == 0) ? a.nx - 1 : i0 - 1, ip = i0 + 1;
+        const int jm = (j0 == 0) ? a.ny - 1 : j0 - 1, jp = j0 + 1;
+        T e = cl_res(a, ih2, im, jm, k0) + cl_res(a, ih2, ip, jm, k0) + cl_res(a, ih2, im, jp, k0) +
+              cl_res(a, ih2, ip, jp, k0);
+        e += cl_res(a, ih2, im, j0, k0 - 1) + cl_res(a, ih2, ip, j0, k0 - 1) + cl_res(a, ih2, im, j0, k0 + 1) +
+             cl_res(a, ih2, ip, j0, k0 + 1);
+        e += cl_res(a, ih2, i0, jm, k0 - 1) + cl_res(a, ih2, i0, jp, k0 - 1) + cl_res(a, ih2, i0, jm, k0 + 1) +
+             cl_res(a, ih2, i0, jp, k0 + 1);
+        const T fc = (T)0.125 * cl_res(a, ih2, i0, j0, k0) + (T)0.03125 * e;
+        const int nc = J * b.nx + I;
+        const bool red = ((I + J + K) & 1) == 0;
+        const T uc = h2c * fc * (T)(1.0 / 6.0);
+        if (bcast == 0) {
+            b.F(K)[nc] = fc;
+            if (red) b.U(K)[nc] = uc;
+        } else {
+            cg::cluster_group cl = cg::this_cluster();
+            for (int q = 0; q < bcast; ++q) {
+                *cl.map_shared_rank(b.F(K) + nc, q) = fc;
+                if (red) *cl.map_shared_rank(b.U(K) + nc, q) = uc;
             }
         }
-        fc[n] = acc;
     }
-    __syncthreads();
 }
 
-// restriction of the residual f - A u computed on the fly at the 27 fine points
+// trilinear interpolation of the coarse correction added on the fine interior
+// planes [klo, khi]; threads keep a column (i, j) as in cl_rbgs
 template <typename T>
-__device__ void tail_resid_restrict(const T* u, const T* f, T* fc, Dims df, Dims dc, T inv_h2)
+__device__ __forceinline__ void cl_prolong(const Lv<T> a, const Lv<T> b, int klo, int khi, FastDiv f_p, FastDiv f_x)
 {
-    const int P = dc.nx * dc.ny;
-    const int N = P * (dc.nz - 1);
-    const int Pf = df.nx * df.ny;
-    for (int t = threadIdx.x; t < N; t += blockDim.x) {
-        const int n = P + t;
-        const int K = n / P;
-        const int I = n % dc.nx, J = (n / dc.nx) % dc.ny;
-        T acc = (T)0;
-        for (int dk = -1; dk <= 1; ++dk) {
-            const T wk = dk == 0 ? (T)0.5 : (T)0.25;
-            const int k = 2 * K + dk;
-            for (int dj = -1; dj <= 1; ++dj) {
-                const T wj = dj == 0 ? (T)0.5 : (T)0.25;
-                const int j = (2 * J + dj + df.ny) % df.ny;
-                const int jp = (j + 1 == df.ny) ? 0 : j + 1, jm = (j == 0) ? df.ny - 1 : j - 1;
-                for (int di = -1; di <= 1; ++di) {
-                    const T wi = di == 0 ? (T)0.5 : (T)0.25;
-                    const int i = (2 * I + di + df.nx) % df.nx;
-                    const int ip = (i + 1 == df.nx) ? 0 : i + 1, im = (i == 0) ? df.nx - 1 : i - 1;
-                    const int m = k * Pf + j * df.nx + i;
-                    const T sum = u[m - i + ip] + u[m - i + im] + u[k * Pf + jp * df.nx + i] +
-                                  u[k * Pf + jm * df.nx + i] + u[m + Pf] + u[m - Pf];
-                    acc += (wk * wj * wi) * (f[m] - ((T)6 * u[m] - sum) * inv_h2);
-                }
-            }
+    if (khi < klo) return;
+    const int bd = blockDim.x, t = threadIdx.x;
+    int g = 0, G = 1, c = t, cstep = bd;
+    if (a.P <= bd) {
+        g = fdiv(t, f_p);
+        G = bd / a.P;
+        if (g >= G) return;
+        c = t - g * a.P;
+        cstep = a.P;
+    }
+    for (; c < a.P; c += cstep) {
+        const int j = fdiv(c, f_x), i = c - j * a.nx;
+        const int I0 = i >> 1, I1 = (i & 1) ? ((I0 + 1 == b.nx) ? 0 : I0 + 1) : I0;
+        const int J0 = j >> 1, J1 = (j & 1) ? ((J0 + 1 == b.ny) ? 0 : J0 + 1) : J0;
+        const int o00 = J0 * b.nx + I0, o01 = J0 * b.nx + I1, o10 = J1 * b.nx + I0, o11 = J1 * b.nx + I1;
+        for (int k = klo + g; k <= khi; k += G) {
+            const int K0 = k >> 1, K1 = K0 + (k & 1);
+            const T* a0 = b.U(K0);
+            const T* a1 = b.U(K1);
+            // a coincident axis repeats its node, so the 1/8 weights give 1/2 or 1 per axis
+            const T v = (T)0.125 * (a0[o00] + a0[o01] + a0[o10] + a0[o11] + a1[o00] + a1[o01] + a1[o10] + a1[o11]);
+            a.U(k)[c] += v;
         }
-        fc[n] = acc;
     }
-    __syncthreads();
 }
 
 template <typename T>
-__device__ void tail_prolong(T* uf, const T* uc, Dims df, Dims dc)
+__global__ void __launch_bounds__(kClThreads) k_vcycle_cluster(const ClusterLevels<T> Lp)
 {
-    const int P = df.nx * df.ny;
-    const int N = P * (df.nz + 1);
-    for (int n = threadIdx.x; n < N; n += blockDim.x) {
-        const int k = n / P;
-        if (k == 0 || k == df.nz) continue;
-        const int i = n % df.nx, j = (n / df.nx) % df.ny;
-        const int I0 = i / 2, I1 = (i & 1) ? (i / 2 + 1) % dc.nx : I0;
-        const int J0 = j / 2, J1 = (j & 1) ? (j / 2 + 1) % dc.ny : J0;
-        const int K0 = k / 2, K1 = (k & 1) ? k / 2 + 1 : K0;
-        const int Pc = dc.nx * dc.ny;
-        // each axis: weights (1/2, 1/2) between two coarse nodes, or (1) on a coincident one
-        const T v = (T)0.125 * (uc[K0 * Pc + J0 * dc.nx + I0] + uc[K0 * Pc + J0 * dc.nx + I1] +
-                                uc[K0 * Pc + J1 * dc.nx + I0] + uc[K0 * Pc + J1 * dc.nx + I1] +
-                                uc[K1 * Pc + J0 * dc.nx + I0] + uc[K1 * Pc + J0 * dc.nx + I1] +
-                                uc[K1 * Pc + J1 * dc.nx + I0] + uc[K1 * Pc + J1 * dc.nx + I1]);
-        uf[n] += v;
-    }
-    __syncthreads();
-}
-
-// The lower part of a V(2,2) cycle in one block with every tail level held in
-// shared memory: pre-smoothing from a zero guess, residual restricted to the
-// next level, the coarsest solve, prolongation and post-smoothing.  Global
-// memory is touched only to read the first tail level's right-hand side and
-// write back its correction.
-template <typename T>
-__global__ void __launch_bounds__(1024) k_vcycle_tail(const TailLevels<T> L)
-{
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     extern __shared__ __align__(16) unsigned char smem[];
-    T* su[kTailMax];
-    T* sf[kTailMax];
-    {
-        T* p = reinterpret_cast<T*>(smem);
-        for (int l = 0; l < L.n; ++l) {
-            const int nodes = L.nx[l] * L.ny[l] * (L.nz[l] + 1);
-            su[l] = p; p += nodes;
-            sf[l] = p; p += nodes;
-        }
-        // corrections start at zero (electrode planes stay zero); first rhs from global
-        for (int l = 0; l < L.n; ++l) {
-            const int nodes = L.nx[l] * L.ny[l] * (L.nz[l] + 1);
-            for (int t = threadIdx.x; t < nodes; t += blockDim.x) {
-                su[l][t] = (T)0;
-                sf[l][t] = l == 0 ? L.f[0][t] : (T)0;
+    // the level table is indexed by level at run time: keep it in shared memory
+    __shared__ ClusterLevels<T> L;
+    if (threadIdx.x == 0) L = Lp;
+    __syncthreads();
+    cg::cluster_group cl = cg::this_cluster();
+    const int r = (int)cl.block_rank(), C = (int)cl.num_blocks();
+    T** pu = reinterpret_cast<T**>(smem + L.ptr_off);
+    T** pf = pu + L.nplanes;
+    // plane tables of the distributed levels: every plane, wherever it is held
+    for (int e = threadIdx.x; e < L.nplanes; e += blockDim.x) {
+        int l = 0;
+        while (l + 1 < L.n && e >= L.pbase[l + 1]) ++l;
+        const int k = e - L.pbase[l];
+        const bool sg = l >= L.single;
+        const int o = sg ? r : cl_owner(k, C, L.nz[l]);
+        const int P = L.nx[l] * L.ny[l];
+        T* lu = reinterpret_cast<T*>(smem + L.off[l]) + (size_t)(k - (sg ? 0 : cl_kfirst(o, C, L.nz[l]))) * P;
+        T* lf = lu + (size_t)L.mp[l] * P;
+        pu[e] = cl.map_shared_rank(lu, o);
+        pf[e] = cl.map_shared_rank(lf, o);
+    }
+    // this CTA's planes start at zero (the electrode planes of the corrections stay zero)
+    for (int l = 0; l < L.n; ++l) {
+        T* b = reinterpret_cast<T*>(smem + L.off[l]);
+        const int words = 2 * L.mp[l] * L.nx[l] * L.ny[l];
+        for (int t = threadIdx.x; t < words; t += blockDim.x) b[t] = (T)0;
+    }
+    __syncthreads();
+    auto lv = [&](int l) {
+        Lv<T> a;
+        a.pu = pu + L.pbase[l];
+        a.pf = pf + L.pbase[l];
+        a.u = reinterpret_cast<T*>(smem + L.off[l]);
+        a.nx = L.nx[l];
+        a.ny = L.ny[l];
+        a.nz = L.nz[l];
+        a.P = a.nx * a.ny;
+        a.f = a.u + (size_t)L.mp[l] * a.P;
+        a.local = l >= L.single;
+        return a;
+    };
+    auto range = [&](int l, int& klo, int& khi) {
+        int k0, k1;
+        cl_planes(r, C, L.nz[l], l >= L.single, k0, k1);
+        klo = max(1, k0);
+        khi = min(L.nz[l] - 1, k1 - 1);
+    };
+    auto sync_level = [&](int l) {
+        if (l < L.single) cl.sync();
+        else __syncthreads();
+    };
+    {   // right-hand side of the first level on this CTA's planes, and the first
+        // red half-sweep from a zero guess (h^2 f / 6 at the red interior nodes)
+        const Lv<T> a = lv(0);
+        int k0, k1;
+        cl_planes(r, C, a.nz, 0 >= L.single, k0, k1);
+        const T h6 = L.h2[0] * (T)(1.0 / 6.0);
+        for (int k = k0; k < k1; ++k) {
+            T* fk = a.F(k);
+            T* uk = a.U(k);
+            for (int t = threadIdx.x; t < a.P; t += blockDim.x) {
+                const T v = L.gf[(size_t)k * a.P + t];
+                fk[t] = v;
+                const int j = fdiv(t, L.f_x[0]);
+                if (k > 0 && k < a.nz && ((t - j * a.nx + j + k) & 1) == 0) uk[t] = h6 * v;
             }
         }
-        __syncthreads();
     }
+    cl.sync();
+    // down: black, red, black half-sweeps (the first red one is done), residual
+    // restricted to the next level with that level's first red half-sweep
     for (int l = 0; l + 1 < L.n; ++l) {
-        const Dims d{L.nx[l], L.ny[l], L.nz[l]};
-        const T h2 = (T)(L.h[l] * L.h[l]);
-        tail_rbgs<T>(su[l], sf[l], d, h2, 0, true);
-        tail_rbgs<T>(su[l], sf[l], d, h2, 1, false);
-        tail_rbgs<T>(su[l], sf[l], d, h2, 0, false);
-        tail_rbgs<T>(su[l], sf[l], d, h2, 1, false);
-        tail_resid_restrict<T>(su[l], sf[l], sf[l + 1], d, Dims{L.nx[l + 1], L.ny[l + 1], L.nz[l + 1]},
-                               (T)(1.0 / (L.h[l] * L.h[l])));
+        const Lv<T> a = lv(l);
+        int klo, khi;
+        range(l, klo, khi);
+        cl_rbgs(a, L.h2[l], klo, khi, 1, L.f_ph[l], L.f_hx[l]);
+        sync_level(l);
+        cl_rbgs(a, L.h2[l], klo, khi, 0, L.f_ph[l], L.f_hx[l]);
+        sync_level(l);
+        cl_rbgs(a, L.h2[l], klo, khi, 1, L.f_ph[l], L.f_hx[l]);
+        sync_level(l);
+        {   // coarse planes K whose fine plane 2K this CTA holds
+            int f0, f1;
+            cl_planes(r, C, a.nz, l >= L.single, f0, f1);
+            const int Klo = max(1, (f0 + 1) / 2), Khi = min(L.nz[l + 1] - 1, (f1 - 1) / 2);
+            const int bcast = (l < L.single && l + 1 >= L.single) ? C : 0;
+            cl_restrict(a, lv(l + 1), L.ih2[l], L.h2[l + 1], Klo, Khi, L.f_p[l + 1], L.f_x[l + 1], bcast);
+        }
+        sync_level(l);
     }
-    {
+    {   // the coarsest level (held by every CTA, solved by each)
         const int c = L.n - 1;
-        const Dims d{L.nx[c], L.ny[c], L.nz[c]};
-        const int P = d.nx * d.ny, n = P * (d.nz - 1);
+        const Lv<T> a = lv(c);
+        const int nun = a.P * (a.nz - 1);
         if (L.ainv) {
-            for (int m = threadIdx.x; m < n; m += blockDim.x) {
-                const T* row = L.ainv + (size_t)m * n;
+            for (int m = threadIdx.x; m < nun; m += blockDim.x) {
+                const T* row = L.ainv + (size_t)m * nun;
                 T acc = (T)0;
-                for (int q = 0; q < n; ++q) acc += row[q] * sf[c][P + q];
-                su[c][P + m] = acc;
+                for (int q = 0; q < nun; ++q) acc += row[q] * a.f[a.P + q];
+                a.u[a.P + m] = acc;
             }
             __syncthreads();
         } else {
-            const T h2 = (T)(L.h[c] * L.h[c]);
             for (int s = 0; s < L.sweeps; ++s) {
-                tail_rbgs<T>(su[c], sf[c], d, h2, 0, s == 0);
-                tail_rbgs<T>(su[c], sf[c], d, h2, 1, false);
+                cl_rbgs(a, L.h2[c], 1, a.nz - 1, s == 0 ? 1 : 0, L.f_ph[c], L.f_hx[c]);
+                __syncthreads();
+                cl_rbgs(a, L.h2[c], 1, a.nz - 1, s == 0 ? 0 : 1, L.f_ph[c], L.f_hx[c]);
+                __syncthreads();
             }
         }
     }
+    // up: prolongation and four half-sweeps
     for (int l = L.n - 2; l >= 0; --l) {
-        const Dims d{L.nx[l], L.ny[l], L.nz[l]};
-        const T h2 = (T)(L.h[l] * L.h[l]);
-        tail_prolong<T>(su[l], su[l + 1], d, Dims{L.nx[l + 1], L.ny[l + 1], L.nz[l + 1]});
-        tail_rbgs<T>(su[l], sf[l], d, h2, 0, false);
-        tail_rbgs<T>(su[l], sf[l], d, h2, 1, false);
-        tail_rbgs<T>(su[l], sf[l], d, h2, 0, false);
-        tail_rbgs<T>(su[l], sf[l], d, h2, 1, false);
+        const Lv<T> a = lv(l);
+        int klo, khi;
+        range(l, klo, khi);
+        cl_prolong(a, lv(l + 1), klo, khi, L.f_p[l], L.f_x[l]);
+        sync_level(l);
+        for (int h = 0; h < 4; ++h) {
+            cl_rbgs(a, L.h2[l], klo, khi, h & 1, L.f_ph[l], L.f_hx[l]);
+            sync_level(l);
+        }
     }
-    const int nodes0 = L.nx[0] * L.ny[0] * (L.nz[0] + 1);
-    for (int t = threadIdx.x; t < nodes0; t += blockDim.x) L.u[0][t] = su[0][t];
+    {   // the first level's correction back to global memory
+        if (0 >= L.single && r != 0) return;
+        const Lv<T> a = lv(0);
+        int klo, khi;
+        range(0, klo, khi);
+        for (int k = klo; k <= khi; ++k) {
+            const T* uk = a.U(k);
+            for (int t = threadIdx.x; t < a.P; t += blockDim.x) L.gu[(size_t)k * a.P + t] = uk[t];
+        }
+    }
+}
+
+constexpr size_t kClSmemMax = 220 * 1024;
+
+// layout of the levels l0.. for a cluster of C CTAs; false if it does not fit
+template <typename T>
+bool cluster_levels(const pic_ctx* c, int l0, int C, ClusterLevels<T>* out, size_t* smem)
+{
+    ClusterLevels<T> L{};
+    L.n = (int)c->mg.size() - l0;
+    if (L.n < 1 || L.n > kTailMax) return false;
+    L.single = L.n - 1;
+    for (int q = 0; q < L.n; ++q)
+        if (C == 1 || c->mg[l0 + q].nodes <= kTailNodes) {
+            L.single = q;
+            break;
+        }
+    size_t off = 0;
+    int pb = 0;
+    for (int q = 0; q < L.n; ++q) {
+        const MGLevel& M = c->mg[l0 + q];
+        L.nx[q] = M.nx;
+        L.ny[q] = M.ny;
+        L.nz[q] = M.nz;
+        L.h2[q] = (T)(M.h * M.h);
+        L.ih2[q] = (T)(1.0 / (M.h * M.h));
+        L.f_hx[q] = fast_div(M.nx / 2);
+        L.f_ph[q] = fast_div(M.nx * M.ny / 2);
+        L.f_x[q] = fast_div(M.nx);
+        L.f_p[q] = fast_div(M.nx * M.ny);
+        L.mp[q] = q >= L.single ? M.nz + 1 : (M.nz + C - 1) / C + 1;
+        L.off[q] = (unsigned int)off;
+        off += (2 * sizeof(T) * (size_t)L.mp[q] * M.nx * M.ny + 15) / 16 * 16;
+        L.pbase[q] = pb;
+        pb += M.nz + 1;
+    }
+    L.ptr_off = (unsigned int)off;
+    L.nplanes = pb;
+    off += 2 * sizeof(T*) * (size_t)pb;
+    L.gu = (T*)c->mg[l0].u;
+    L.gf = (const T*)c->mg[l0].f;
+    L.ainv = (const T*)c->coarse_inv;
+    const MGLevel& Cl = c->mg.back();
+    const int m = std::max(std::max(Cl.nx, Cl.ny), Cl.nz);
+    L.sweeps = std::min(4 * m * m + 16, 2000);
+    if (off > kClSmemMax) return false;
+    if (out) *out = L;
+    if (smem) *smem = off;
+    return true;
 }
 
 template <typename T>
-size_t tail_smem(const pic_ctx* c, int l0)
+cudaError_t launch_cluster(cudaStream_t s, const ClusterLevels<T>& L, int C, size_t smem, bool query, int* fits)
 {
-    size_t b = 0;
-    for (size_t l = (size_t)l0; l < c->mg.size(); ++l) b += 2 * sizeof(T) * c->mg[l].nodes;
-    return b;
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3((unsigned)C, 1, 1);
+    cfg.blockDim = dim3(kClThreads, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = (unsigned)C;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    if (query) {
+        cudaError_t e = cudaFuncSetAttribute(k_vcycle_cluster<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)kClSmemMax);
+        if (e == cudaSuccess && C > 8)
+            e = cudaFuncSetAttribute(k_vcycle_cluster<T>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        int n = 0;
+        if (e == cudaSuccess) e = cudaOccupancyMaxActiveClusters(&n, k_vcycle_cluster<T>, &cfg);
+        *fits = e == cudaSuccess && n > 0;
+        cudaGetLastError();
+        return cudaSuccess;
+    }
+    return cudaLaunchKernelEx(&cfg, k_vcycle_cluster<T>, L);
 }
 
-int blocks(size_t n) { return grid_for((int64_t)n, 256, 152 * 8); }
 
 // grid for kernels that reduce a norm: (x, y) blocks of a plane and just enough
 // z blocks (each looping over planes) to fill the GPU a few times
@@ -624,7 +885,7 @@ template <typename T>
 void run_rbgs(cudaStream_t s, T* u, const T* f, Dims d, T h2, int color, int zero)
 {
     const Grid3 g = grid3(d.nx / 2, d.ny, d.nz - 1);
-    k_rbgs<T><<<g.grid, g.block, 0, s>>>(u, f, d, h2, color, zero);
+    launch_pdl(s, g.grid, g.block, k_rbgs<T>, u, f, d, h2, color, zero);
 }
 template <typename T>
 void run_resid(cudaStream_t s, const T* u, const T* f, T* r, Dims d, T inv_h2)
@@ -639,16 +900,16 @@ void run_restrict(cudaStream_t s, const T* rf, T* fc, Dims df, Dims dc)
     k_restrict<T><<<g.grid, g.block, 0, s>>>(rf, fc, df, dc);
 }
 template <typename T>
-void run_resid_restrict(cudaStream_t s, const T* u, const T* f, T* fc, Dims df, Dims dc, T inv_h2)
+void run_resid_restrict(cudaStream_t s, const T* u, const T* f, T* fc, T* uc, Dims df, Dims dc, T inv_h2, T h2c)
 {
     const Grid3 g = grid3(dc.nx, dc.ny, dc.nz - 1);
-    k_resid_restrict<T><<<g.grid, g.block, 0, s>>>(u, f, fc, df, dc, inv_h2);
+    launch_pdl(s, g.grid, g.block, k_resid_restrict<T>, u, f, fc, uc, df, dc, inv_h2, h2c);
 }
 template <typename T>
 void run_prolong(cudaStream_t s, T* uf, const T* uc, Dims df, Dims dc)
 {
     const Grid3 g = grid3(df.nx, df.ny, df.nz - 1);
-    k_prolong<T><<<g.grid, g.block, 0, s>>>(uf, uc, df, dc);
+    launch_pdl(s, g.grid, g.block, k_prolong<T>, uf, uc, df, dc);
 }
 template <typename T>
 void run_resid64(cudaStream_t s, const double* phi, const T* e, const double* f, double* phi_out, T* r, double* norm2,
@@ -667,21 +928,12 @@ void vcycle(pic_ctx* c, int l)
 {
     const int nl = (int)c->mg.size();
     if (l >= c->mg_tail) {
-        // every level from here down runs in one block
-        TailLevels<T> t{};
-        t.n = nl - l;
-        for (int q = 0; q < t.n; ++q) {
-            const MGLevel& L = c->mg[l + q];
-            t.nx[q] = L.nx; t.ny[q] = L.ny; t.nz[q] = L.nz; t.h[q] = L.h;
-            t.u[q] = (T*)L.u; t.f[q] = (T*)L.f; t.r[q] = (T*)L.r;
-        }
-        const MGLevel& C = c->mg.back();
-        const int n = C.nx * C.ny * (C.nz - 1);
-        t.ainv = (const T*)c->coarse_inv;
-        const int m = std::max(std::max(C.nx, C.ny), C.nz);
-        t.sweeps = std::min(4 * m * m + 16, 2000);
-        (void)n;
-        k_vcycle_tail<T><<<1, 1024, tail_smem<T>(c, l), c->stream>>>(t);
+        // every level from here down runs in one cluster
+        ClusterLevels<T> L{};
+        size_t smem = 0;
+        cluster_levels<T>(c, l, c->cl_size, &L, &smem);
+        int fits = 0;
+        launch_cluster<T>(c->stream, L, c->cl_size, smem, false, &fits);
         c->launches += 1;
         return;
     }
@@ -690,13 +942,18 @@ void vcycle(pic_ctx* c, int l)
     const T h2 = (T)(L.h * L.h);
     T* u = (T*)L.u;
     T* f = (T*)L.f;
-    // pre-smoothing from a zero guess: the first colour-0 pass needs no neighbours
+    // pre-smoothing from a zero guess: the first red pass needs no neighbours
+    // (on the coarser levels the restriction above has already made it)
     for (int s = 0; s < kPre; ++s)
-        for (int color = 0; color < 2; ++color) run_rbgs<T>(c->stream, u, f, d, h2, color, s == 0 && color == 0);
+        for (int color = 0; color < 2; ++color) {
+            if (s == 0 && color == 0 && l > 0) continue;
+            run_rbgs<T>(c->stream, u, f, d, h2, color, s == 0 && color == 0);
+            c->launches += 1;
+        }
     MGLevel& C = c->mg[l + 1];
     const Dims dc{C.nx, C.ny, C.nz};
-    run_resid_restrict<T>(c->stream, u, f, (T*)C.f, d, dc, (T)(1.0 / (L.h * L.h)));
-    c->launches += 2 * kPre + 1;
+    run_resid_restrict<T>(c->stream, u, f, (T*)C.f, (T*)C.u, d, dc, (T)(1.0 / (L.h * L.h)), (T)(C.h * C.h));
+    c->launches += 1;
     vcycle<T>(c, l + 1);
     run_prolong<T>(c->stream, u, (const T*)C.u, d, dc);
     c->launches += 1 + 2 * kPost;
@@ -778,18 +1035,404 @@ void enqueue_head(pic_ctx* c, double tol, int max_iters, cudaGraphConditionalHan
     c->launches += 3;
 }
 
+// ---- mixed precision: the refinement in double-float arithmetic -----------
+// FP64 instructions issue at about 1/70 of the FP32 rate on this GPU, so the
+// mixed solver keeps the potential and the right-hand side as unevaluated sums
+// hi + lo of two floats (about 48 significant bits) and forms the residual
+// with error-free transformations in FP32: Knuth's TwoSum, Dekker's Fast2Sum
+// and the exact product a*b = p + fma(a, b, -p).  The potential lives in two
+// buffers; an iteration reads one and writes phi + e into the other, so the
+// correction and the residual of the updated potential take one pass.
+
+// s + e == a + b exactly
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e)
+{
+    s = a + b;
+    const float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+// s + e == a + b exactly when |a| >= |b| (or a == 0)
+__device__ __forceinline__ void fast_two_sum(float a, float b, float& s, float& e)
+{
+    s = a + b;
+    e = b - (s - a);
+}
+__device__ __forceinline__ float2 df_add_f(float2 a, float b)
+{
+    float s, e, h, l;
+    two_sum(a.x, b, s, e);
+    e += a.y;
+    fast_two_sum(s, e, h, l);
+    return make_float2(h, l);
+}
+__device__ __forceinline__ float2 df_mul(float2 a, float2 b)
+{
+    const float p = a.x * b.x;
+    float e = fmaf(a.x, b.x, -p);
+    e += a.x * b.y + a.y * b.x;
+    float h, l;
+    fast_two_sum(p, e, h, l);
+    return make_float2(h, l);
+}
+__host__ __device__ inline float2 df_of(double v)
+{
+    const float h = (float)v;
+    return make_float2(h, (float)(v - (double)h));
+}
+// a 64-bit integer as hi + lo: three exact pieces of at most 24 bits
+__device__ __forceinline__ float2 df_of_i64(long long v)
+{
+    const float a = (float)(int)(v >> 40) * 0x1p40f;
+    const float b = (float)(int)((v >> 20) & 0xFFFFF) * 0x1p20f;
+    const float c = (float)(int)(v & 0xFFFFF);
+    float s, e, s2, e2, h, l;
+    two_sum(a, b, s, e);
+    two_sum(s, c, s2, e2);
+    fast_two_sum(s2, e2 + e, h, l);
+    return make_float2(h, l);
+}
+
+__device__ __forceinline__ float block_sum_f(float v)
+{
+    __shared__ float part[32];
+    const int t = tid_flat(), nt = blockDim.x * blockDim.y;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    const int lane = t & 31, w = t >> 5;
+    if (lane == 0) part[w] = v;
+    __syncthreads();
+    v = (t < (nt + 31) / 32) ? part[t] : 0.f;
+    if (w == 0)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Grid-wide sum of one value per thread without atomics on the sum: each
+// block stores its partial, the last block to arrive (one counter increment
+// per block) adds the partials in block order.  Returns true in the last
+// block, whose threads all receive the total.  The counter wraps back to 0.
+__device__ bool grid_sum_last(float v, float* part, unsigned int* count, float& total)
+{
+    __shared__ int s_last;
+    __shared__ float s_tot;
+    v = block_sum_f(v);
+    const int t = tid_flat();
+    const unsigned int nb = gridDim.x * gridDim.y * gridDim.z;
+    const unsigned int b = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+    if (t == 0) {
+        part[b] = v;
+        __threadfence();
+        s_last = atomicInc(count, nb - 1) == nb - 1;
+    }
+    __syncthreads();
+    if (!s_last) return false;
+    __threadfence();
+    float acc = 0.f;
+    for (unsigned int q = t; q < nb; q += blockDim.x * blockDim.y) acc += __ldcg(part + q);
+    acc = block_sum_f(acc);
+    if (t == 0) s_tot = acc;
+    __syncthreads();
+    total = s_tot;
+    return true;
+}
+
+struct RhsDf {
+    float2* phi;                     // two buffers of nodes; buffer 0 holds the warm start
+    float2* F;                       // out: h^2 rho / eps0
+    const unsigned long long* rq;
+    float* part;
+    DfState* st;
+    double* vb_last;                 // lower electrode value of the previous solve (null: no shift)
+    const uint32_t* step;            // device step counter: electrode values from the drive, else vb, vt
+    SolveParams sp;
+    double scale, vb, vt, h2;
+};
+
+// Head of a mixed-precision solve, one thread per node of planes 0..nz:
+// F = h^2 rho / eps0 from the fixed-point charge, electrode values on both
+// buffers, the warm start moved by the change of the electrode ramp
+// (vb - vb_last)(1 - z / Lz), which the 7-point operator maps to zero, and
+// ||h^2 b||^2 (b = f plus the electrode terms next to the planes).
+__global__ void __launch_bounds__(256) k_rhs_df(RhsDf a, Dims d)
+{
+    __shared__ float2 s_vb, s_vt, s_sc;
+    __shared__ float s_shift;
+    __shared__ double s_vbd;
+    if (tid_flat() == 0) {
+        double vb = a.vb, vt = a.vt, sc = a.scale;
+        if (a.step) {
+            vb = bottom_potential(a.sp, *a.step);
+            vt = a.sp.v_top;
+            sc = a.sp.scale;
+        }
+        s_vbd = vb;
+        s_vb = df_of(vb);
+        s_vt = df_of(vt);
+        s_sc = df_of(sc * a.h2);
+        s_shift = a.vb_last ? (float)(vb - *a.vb_last) : 0.f;
+    }
+    __syncthreads();
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    const int k = blockIdx.z;
+    const size_t N = (size_t)d.nx * d.ny * (d.nz + 1);
+    float acc = 0.f;
+    if (i < d.nx && j < d.ny) {
+        const int n = (k * d.ny + j) * d.nx + i;
+        const float2 F = df_mul(df_of_i64((long long)a.rq[n]), s_sc);
+        a.F[n] = F;
+        if (k == 0) {
+            a.phi[n] = s_vb;
+            a.phi[N + n] = s_vb;
+        } else if (k == d.nz) {
+            a.phi[n] = s_vt;
+            a.phi[N + n] = s_vt;
+        } else {
+            if (s_shift != 0.f) a.phi[n] = df_add_f(a.phi[n], s_shift * (1.f - (float)k / (float)d.nz));
+            float b = F.x + F.y;
+            if (k == 1) b += s_vb.x;
+            if (k == d.nz - 1) b += s_vt.x;
+            acc = b * b;
+        }
+    }
+    float b2;
+    if (!grid_sum_last(acc, a.part, &a.st->cnt_head, b2)) return;
+    if (tid_flat() == 0) {
+        a.st->b2 = b2;
+        a.st->sel = 0;
+        if (a.vb_last) *a.vb_last = s_vbd;
+    }
+}
+
+struct ResDf {
+    float2* phi;                     // two buffers of nodes
+    const float* e;                  // V-cycle correction on the fine level (null: none, nothing written)
+    const float2* F;
+    float* r;                        // out: r = R / h^2, the next V-cycle's right-hand side
+    float* part;
+    DfState* st;
+    unsigned int* iters;
+    double* res;
+    int* flag;                       // latch for a failed graph solve (null in host-driven solves)
+    unsigned long long* total;
+    float inv_h2, tol2, h4;
+    int max_iters, first, use_cond;
+    cudaGraphConditionalHandle h;
+};
+
+// One refinement step over the interior nodes: phi' = phi + e (written to the
+// other buffer), R = h^2 f - (6 phi' - sum of the 6 neighbours of phi') with
+// the large parts summed exactly, ||R||^2 over the grid, and in the last block
+// the loop decision of the solve (the same rule as the FP64 solver's).
+__global__ void __launch_bounds__(256) k_resid_df(ResDf a, Dims d)
+{
+    pdl_begin();
+    __shared__ int s_sel;
+    if (tid_flat() == 0) s_sel = a.st->sel;
+    __syncthreads();
+    const size_t N = (size_t)d.nx * d.ny * (d.nz + 1);
+    const float2* cur = a.phi + (s_sel ? N : 0);
+    float2* nxt = a.phi + (s_sel ? 0 : N);
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    const int k = 1 + blockIdx.z;
+    float acc = 0.f;
+    if (i < d.nx && j < d.ny) {
+        const int P = d.nx * d.ny;
+        const int n = k * P + j * d.nx + i;
+        const int row = n - i;
+        const int ip = (i + 1 == d.nx) ? 0 : i + 1, im = (i == 0) ? d.nx - 1 : i - 1;
+        const int jp = (j + 1 == d.ny) ? -j * d.nx : d.nx, jm = (j == 0) ? (d.ny - 1) * d.nx : -d.nx;
+        const int nb[6] = {row + ip, row + im, n + jp, n + jm, n + P, n - P};
+        const float2 pc = cur[n];
+        const float ec = a.e ? a.e[n] : 0.f;
+        // 6 phi'_n - sum phi'_nb: hi parts exactly (s + err), the small parts in float
+        float s = 6.f * pc.x;
+        float err = fmaf(6.f, pc.x, -s);
+        float small = 6.f * (pc.y + ec);
+#pragma unroll
+        for (int q = 0; q < 6; ++q) {
+            const float2 p = cur[nb[q]];
+            const float eq = a.e ? a.e[nb[q]] : 0.f;
+            float s2, t;
+            two_sum(s, -p.x, s2, t);
+            s = s2;
+            err += t;
+            small -= p.y + eq;
+        }
+        const float2 F = a.F[n];
+        float r1, t1;
+        two_sum(F.x, -s, r1, t1);
+        const float R = r1 + ((t1 + F.y) - (err + small));
+        if (a.e) nxt[n] = df_add_f(pc, ec);
+        a.r[n] = R * a.inv_h2;
+        acc = R * R;
+    }
+    float r2;
+    if (!grid_sum_last(acc, a.part, &a.st->cnt_res, r2)) return;
+    if (tid_flat() != 0) return;
+    const float b2 = a.st->b2;
+    const float target2 = a.tol2 * (b2 > 0.f ? b2 : a.h4);
+    const unsigned int it = a.first ? 0u : *a.iters + 1u;
+    *a.iters = it;
+    if (!a.first) *a.total += 1ull;
+    const bool ok = r2 <= target2;
+    const bool finite = isfinite(r2);
+    const bool more = !ok && finite && (int)it < a.max_iters;
+    *a.res = b2 > 0.f ? sqrt((double)r2 / (double)b2) : sqrt((double)r2 / (double)a.h4);
+    const int status = ok ? (int)PIC_OK : finite ? (int)PIC_ENOTCONV : (int)PIC_ENONFINITE;
+    if (!more && !ok && a.flag) atomicCAS(a.flag, 0, status);
+    a.st->status = status;
+    a.st->more = more ? 1 : 0;
+    if (a.e) a.st->sel = s_sel ^ 1;
+    if (a.use_cond) cudaGraphSetConditional(a.h, more ? 1u : 0u);
+}
+
+// after the loop: the current potential back into buffer 0
+__global__ void k_settle_df(float2* phi, const DfState* st, size_t N)
+{
+    pdl_begin();
+    if (st->sel == 0) return;
+    for (size_t n = blockIdx.x * (size_t)blockDim.x + threadIdx.x; n < N; n += (size_t)gridDim.x * blockDim.x)
+        phi[n] = phi[N + n];
+}
+
+__global__ void k_df_to_f64(const float2* __restrict__ phi2, double* __restrict__ phi, size_t N)
+{
+    for (size_t n = blockIdx.x * (size_t)blockDim.x + threadIdx.x; n < N; n += (size_t)gridDim.x * blockDim.x) {
+        const float2 p = phi2[n];
+        phi[n] = (double)p.x + (double)p.y;
+    }
+}
+
+__global__ void k_f64_to_df(const double* __restrict__ phi, float2* __restrict__ phi2, size_t N)
+{
+    for (size_t n = blockIdx.x * (size_t)blockDim.x + threadIdx.x; n < N; n += (size_t)gridDim.x * blockDim.x)
+        phi2[n] = df_of(phi[n]);
+}
+
+// head kernel; step != null takes the electrode values and scale from the device step
+void launch_rhs_df(pic_ctx* c, const uint32_t* step, double scale, double vb, double vt, bool warm_shift)
+{
+    const Dims d{c->nx, c->ny, c->nz};
+    RhsDf a{};
+    a.phi = c->phi2;
+    a.F = c->f2;
+    a.rq = c->rq;
+    a.part = c->d_part;
+    a.st = c->d_dfs;
+    a.vb_last = warm_shift ? c->d_vb_last : nullptr;
+    a.step = step;
+    a.sp = c->sp;
+    a.scale = scale;
+    a.vb = vb;
+    a.vt = vt;
+    a.h2 = c->dx * c->dx;
+    const Grid3 g = grid3(d.nx, d.ny, d.nz + 1);
+    k_rhs_df<<<g.grid, g.block, 0, c->stream>>>(a, d);
+    c->launches += 1;
+}
+
+void launch_resid_df(pic_ctx* c, double tol, int max_iters, bool first, bool graph, cudaGraphConditionalHandle h)
+{
+    const Dims d{c->nx, c->ny, c->nz};
+    ResDf a{};
+    a.phi = c->phi2;
+    a.e = first ? nullptr : (const float*)c->mg[0].u;
+    a.F = c->f2;
+    a.r = (float*)c->mg[0].f;
+    a.part = c->d_part;
+    a.st = c->d_dfs;
+    a.iters = c->d_iters;
+    a.res = c->d_res;
+    a.flag = graph ? c->d_solve_flag : nullptr;
+    a.total = c->d_iter_total;
+    a.inv_h2 = (float)(1.0 / (c->dx * c->dx));
+    a.tol2 = (float)(tol * tol);
+    a.h4 = (float)(c->dx * c->dx * c->dx * c->dx);
+    a.max_iters = max_iters;
+    a.first = first ? 1 : 0;
+    a.use_cond = graph ? 1 : 0;
+    a.h = h;
+    const Grid3 g = grid3(d.nx, d.ny, d.nz - 1);
+    launch_pdl(c->stream, g.grid, g.block, k_resid_df, a, d);
+    c->launches += 1;
+}
+
+void launch_settle_df(pic_ctx* c)
+{
+    k_settle_df<<<grid_for((int64_t)c->nodes, 256, 152 * 4), 256, 0, c->stream>>>(c->phi2, c->d_dfs, c->nodes);
+    c->launches += 1;
+}
+
+// host-driven mixed solve after launch_rhs_df: loop decisions read back each iteration
+pic_status solve_df(pic_ctx* c, double tol, int max_iters, int* iters, double* res)
+{
+    cudaGraphConditionalHandle none{};
+    launch_resid_df(c, tol, max_iters, true, false, none);
+    DfState st{};
+    while (true) {
+        if (!PIC_CUDA_OK(cudaMemcpyAsync(&st, c->d_dfs, sizeof st, cudaMemcpyDeviceToHost, c->stream)) ||
+            !PIC_CUDA_OK(cudaStreamSynchronize(c->stream)))
+            return PIC_ECUDA;
+        if (!st.more) break;
+        vcycle<float>(c, 0);
+        launch_resid_df(c, tol, max_iters, false, false, none);
+    }
+    launch_settle_df(c);
+    unsigned int it = 0;
+    double rel = 0.0;
+    if (!PIC_CUDA_OK(cudaMemcpyAsync(&it, c->d_iters, sizeof it, cudaMemcpyDeviceToHost, c->stream)) ||
+        !PIC_CUDA_OK(cudaMemcpyAsync(&rel, c->d_res, sizeof rel, cudaMemcpyDeviceToHost, c->stream)) ||
+        !PIC_CUDA_OK(cudaStreamSynchronize(c->stream)))
+        return PIC_ECUDA;
+    if (iters) *iters = (int)it;
+    if (res) *res = rel;
+    c->last_iters = it;
+    c->last_res = rel;
+    return (pic_status)st.status;
+}
+
 }  // namespace
 
 void enqueue_solve_head(pic_ctx* c, double tol, int max_iters, cudaGraphConditionalHandle h)
 {
-    if (c->prec == PIC_MIXED) enqueue_head<float>(c, tol, max_iters, h);
-    else enqueue_head<double>(c, tol, max_iters, h);
+    if (c->prec == PIC_MIXED) {
+        launch_rhs_df(c, c->d_step, 0.0, 0.0, 0.0, true);
+        launch_resid_df(c, tol, max_iters, true, true, h);
+    } else {
+        enqueue_head<double>(c, tol, max_iters, h);
+    }
 }
 
 void enqueue_solve_iteration(pic_ctx* c, double tol, int max_iters, cudaGraphConditionalHandle h)
 {
-    if (c->prec == PIC_MIXED) enqueue_iteration<float>(c, tol, max_iters, h);
-    else enqueue_iteration<double>(c, tol, max_iters, h);
+    if (c->prec == PIC_MIXED) {
+        vcycle<float>(c, 0);
+        launch_resid_df(c, tol, max_iters, false, true, h);
+    } else {
+        enqueue_iteration<double>(c, tol, max_iters, h);
+    }
+}
+
+void enqueue_solve_tail(pic_ctx* c)
+{
+    if (c->prec == PIC_MIXED) launch_settle_df(c);
+}
+
+void phi_sync_f64(pic_ctx* c)
+{
+    if (c->prec != PIC_MIXED) return;
+    k_df_to_f64<<<grid_for((int64_t)c->nodes, 256, 152 * 4), 256, 0, c->stream>>>(c->phi2, c->phi, c->nodes);
+    c->launches += 1;
+}
+
+void phi_from_f64(pic_ctx* c)
+{
+    if (c->prec != PIC_MIXED) return;
+    k_f64_to_df<<<grid_for((int64_t)c->nodes, 256, 152 * 4), 256, 0, c->stream>>>(c->phi, c->phi2, c->nodes);
+    c->launches += 1;
 }
 
 pic_status mg_setup(pic_ctx* c)
@@ -816,23 +1459,30 @@ pic_status mg_setup(pic_ctx* c)
         if (!can) break;
         nx /= 2; ny /= 2; nz /= 2; h *= 2.0;
     }
-    // the smallest levels (each at most kTailNodes nodes, at most kTailMax of them,
-    // together at most kTailSmem bytes of u and f) run in one block from shared
-    // memory; larger levels are faster as grid-wide launches
-    c->mg_tail = (int)c->mg.size() - 1;
-    auto smem_from = [&](int l0) {
-        size_t b = 0;
-        for (size_t l = (size_t)l0; l < c->mg.size(); ++l) b += 2 * tsz * c->mg[l].nodes;
-        return b;
-    };
-    while (c->mg_tail > 0 && smem_from(c->mg_tail - 1) <= kTailSmem && c->mg[c->mg_tail - 1].nodes <= kTailNodes &&
-           (int)c->mg.size() - (c->mg_tail - 1) <= kTailMax)
-        --c->mg_tail;
+    // the levels from mg_tail down run in one thread-block cluster from shared
+    // memory: the first level (smallest index) that fits, with the largest
+    // cluster the device can hold; larger levels run as grid-wide launches
     {
-        const cudaError_t e = c->prec == PIC_MIXED
-            ? cudaFuncSetAttribute(k_vcycle_tail<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTailSmem)
-            : cudaFuncSetAttribute(k_vcycle_tail<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTailSmem);
-        if (e != cudaSuccess) return PIC_ECUDA;
+        int sizes[6] = {PIC_MG_CLUSTER, 16, 8, 4, 2, 1};
+        bool found = false;
+        for (int l0 = std::min(std::max(0, PIC_MG_CLUSTER_FROM), (int)c->mg.size() - 1); l0 < (int)c->mg.size() && !found;
+             ++l0)
+            for (int C : sizes) {
+                if (C < 1 || C > 16 || C > PIC_MG_CLUSTER) continue;
+                size_t smem = 0;
+                const bool ok = c->prec == PIC_MIXED ? cluster_levels<float>(c, l0, C, nullptr, &smem)
+                                                     : cluster_levels<double>(c, l0, C, nullptr, &smem);
+                if (!ok) continue;
+                int fits = 0;
+                if (c->prec == PIC_MIXED) launch_cluster<float>(nullptr, ClusterLevels<float>{}, C, smem, true, &fits);
+                else launch_cluster<double>(nullptr, ClusterLevels<double>{}, C, smem, true, &fits);
+                if (!fits) continue;
+                c->mg_tail = l0;
+                c->cl_size = C;
+                found = true;
+                break;
+            }
+        if (!found) return PIC_ECUDA;
     }
     // exact inverse of the coarsest operator (6 u - neighbour sum) / h^2 with
     // zero values on the electrode planes, by Gauss-Jordan elimination
@@ -889,23 +1539,44 @@ pic_status mg_setup(pic_ctx* c)
         if (e != cudaSuccess) return PIC_ECUDA;
         c->coarse_inv = d;
     }
+    if (c->prec == PIC_MIXED) {
+        // double-float potential (two buffers), right-hand side, block partials, state
+        const Grid3 g = grid3(c->nx, c->ny, c->nz + 1);
+        const size_t parts = (size_t)g.grid.x * g.grid.y * g.grid.z;
+        c->phi2 = (float2*)dev_alloc(c, sizeof(float2) * 2 * c->nodes);
+        c->f2 = (float2*)dev_alloc(c, sizeof(float2) * c->nodes);
+        c->d_part = (float*)dev_alloc(c, sizeof(float) * parts);
+        c->d_dfs = (DfState*)dev_alloc(c, sizeof(DfState));
+        if (!c->phi2 || !c->f2 || !c->d_part || !c->d_dfs) return PIC_ENOMEM;
+        if (cudaMemset(c->phi2, 0, sizeof(float2) * 2 * c->nodes) != cudaSuccess ||
+            cudaMemset(c->f2, 0, sizeof(float2) * c->nodes) != cudaSuccess ||
+            cudaMemset(c->d_dfs, 0, sizeof(DfState)) != cudaSuccess)
+            return PIC_ECUDA;
+    }
     return PIC_OK;
 }
 
-void launch_rhs(pic_ctx* c, double scale, double v_bot, double v_top, bool)
+void launch_rhs(pic_ctx* c, double scale, double v_bot, double v_top, bool warm_shift)
 {
+    if (c->prec == PIC_MIXED) {
+        launch_rhs_df(c, nullptr, scale, v_bot, v_top, warm_shift);
+        return;
+    }
     const Dims d{c->nx, c->ny, c->nz};
     cudaMemsetAsync(c->d_norm, 0, sizeof(double), c->stream);
     const Grid3 g = grid_norm(d.nx, d.ny, d.nz + 1);
     k_rhs<<<g.grid, g.block, 0, c->stream>>>(c->rq, scale, c->f64, c->phi, c->phi_alt, v_bot, v_top, d,
-                                            1.0 / (c->dx * c->dx), c->d_norm, c->d_vb_last);
-    k_store<<<1, 1, 0, c->stream>>>(c->d_vb_last, v_bot);
-    c->launches += 2;
+                                            1.0 / (c->dx * c->dx), c->d_norm, warm_shift ? c->d_vb_last : nullptr);
+    c->launches += 1;
+    if (warm_shift) {
+        k_store<<<1, 1, 0, c->stream>>>(c->d_vb_last, v_bot);
+        c->launches += 1;
+    }
 }
 
 pic_status mg_solve(pic_ctx* c, double, double, double tol, int max_iters, int* iters, double* res)
 {
-    if (c->prec == PIC_MIXED) return solve_t<float>(c, tol, max_iters, iters, res);
+    if (c->prec == PIC_MIXED) return solve_df(c, tol, max_iters, iters, res);
     return solve_t<double>(c, tol, max_iters, iters, res);
 }
 
