@@ -210,6 +210,10 @@ struct pic_ctx {
     void* coarse_inv = nullptr;              // dense inverse of the coarsest level (T)
     int mg_tail = 0;                         // first level handled by the cluster kernel
     int cl_size = 1;                         // CTAs in that cluster
+    int ex_level = -1;                       // level solved exactly by one cluster (-1: none)
+    int ex_size = 1;                         // CTAs in that cluster
+    void* ex_q = nullptr;                    // its x and y Fourier bases (T)
+    void* ex_p = nullptr;                    // its Thomas pivots per mode (T)
     pic::SolveParams sp;
     unsigned int* d_iters = nullptr;         // graph solve: iterations of the last solve
     double* d_res = nullptr;                 // graph solve: relative residual of the last solve

@@ -35,6 +35,12 @@
 #ifndef PIC_PDL
 #define PIC_PDL 1              // programmatic dependent launch between solver kernels
 #endif
+#ifndef PIC_MG_EXACT
+#define PIC_MG_EXACT 1         // solve the first level that fits one cluster exactly
+#endif
+#ifndef PIC_MG_EXACT_MAXNODES
+#define PIC_MG_EXACT_MAXNODES 32768  // largest level solved exactly (Fourier transforms cost grows as n^1.5)
+#endif
 #ifndef PIC_MG_CL_THREADS
 #define PIC_MG_CL_THREADS 512  // threads per CTA of the cluster
 #endif
@@ -869,6 +875,259 @@ cudaError_t launch_cluster(cudaStream_t s, const ClusterLevels<T>& L, int C, siz
     return cudaLaunchKernelEx(&cfg, k_vcycle_cluster<T>, L);
 }
 
+// ---- exact solve of one coarse level in one thread-block cluster -----------
+// The rediscretised operator (6 u - neighbour sum) / h^2 with periodic x, y
+// and zero Dirichlet planes separates: an orthonormal real Fourier basis
+// (constant, cos/sin pairs, alternating) diagonalises the periodic second
+// differences in x and y with eigenvalues 2 - 2 cos(2 pi p / n), and each
+// resulting mode (mx, my) leaves a constant-coefficient tridiagonal system in z,
+//     (2 + lx + ly) v_k - v_(k-1) - v_(k+1) = h^2 fhat_k,  v_0 = v_nz = 0,
+// solved by the Thomas recurrence with pivots p_k = 1 / (d - p_(k-1))
+// precomputed per mode.  CTA r of C holds a z slab of planes (transforms in
+// x and y are local) and a block of modes (the z solves are local); the
+// spectral values move between the two layouts through distributed shared
+// memory.
+template <typename T>
+struct ExactLevel {
+    int nx, ny, nz;
+    int rp;              // row pitch of the plane buffers in shared memory (nx + 4)
+    T h2;
+    const T* Q;          // Qx, Qx transposed, Qy, Qy transposed; rows of Qx, Qy are basis vectors
+    const T* p;          // Thomas pivots, (nz - 1) per mode, mode m = my nx + mx
+    const T* gf;         // right-hand side of the level (in)
+    T* gu;               // correction of the level (out, interior planes)
+    int mp;              // planes reserved per CTA
+    int mm;              // modes per CTA
+    unsigned int off_a, off_b, off_g, off_p;   // byte offsets in shared memory (Q at 0)
+    FastDiv f_x, f_n, f_x4, f_y4, f_t2;        // nx, nz - 1, nx / 4, ny / 4, (ny / 4)(nx / 4)
+};
+
+// four consecutive values (16-byte aligned)
+__device__ __forceinline__ void ld4(const float* p, float v[4])
+{
+    const float4 q = *reinterpret_cast<const float4*>(p);
+    v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+}
+__device__ __forceinline__ void ld4(const double* p, double v[4])
+{
+    const double2 a = *reinterpret_cast<const double2*>(p), b = *reinterpret_cast<const double2*>(p + 2);
+    v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+}
+__device__ __forceinline__ void st4(float* p, const float v[4])
+{
+    *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+}
+__device__ __forceinline__ void st4(double* p, const double v[4])
+{
+    *reinterpret_cast<double2*>(p) = make_double2(v[0], v[1]);
+    *reinterpret_cast<double2*>(p + 2) = make_double2(v[2], v[3]);
+}
+
+// Out[r][c] = scale * sum_s X(r, s) Y(s, c) on one 4 x 4 tile, with X read
+// as four rows (one value each per s, rows xp apart) or as a 4-vector per s,
+// and Y as a 4-vector per s.
+template <typename T, bool XVEC>
+__device__ __forceinline__ void tile4(const T* x, int xs, int xp, const T* y, int ys, int n, T acc[4][4])
+{
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = (T)0;
+#pragma unroll 4
+    for (int s = 0; s < n; ++s) {
+        T xv[4], yv[4];
+        if (XVEC) {
+            ld4(x + s * xs, xv);
+        } else {
+#pragma unroll
+            for (int a = 0; a < 4; ++a) xv[a] = x[a * xp + s * xs];
+        }
+        ld4(y + s * ys, yv);
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b) acc[a][b] += xv[a] * yv[b];
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kClThreads) k_coarse_exact(const ExactLevel<T> E)
+{
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    extern __shared__ __align__(16) unsigned char smem[];
+    cg::cluster_group cl = cg::this_cluster();
+    const int r = (int)cl.block_rank(), C = (int)cl.num_blocks();
+    const int nx = E.nx, ny = E.ny, nz = E.nz, P = nx * ny, N = nz - 1, rp = E.rp, pp = ny * E.rp;
+    const int bd = blockDim.x, t = threadIdx.x;
+    T* Qx = reinterpret_cast<T*>(smem);   // [m][i]
+    T* QxT = Qx + nx * nx;                // [i][m]
+    T* Qy = QxT + nx * nx;                // [m][j]
+    T* QyT = Qy + ny * ny;                // [j][m]
+    T* A = reinterpret_cast<T*>(smem + E.off_a);   // planes k0.., row pitch rp, plane pitch pp
+    T* B = reinterpret_cast<T*>(smem + E.off_b);
+    T* G = reinterpret_cast<T*>(smem + E.off_g);   // this CTA's modes, index q N + k - 1
+    T* Pv = reinterpret_cast<T*>(smem + E.off_p);
+    const int k0 = cl_kfirst(r, C, nz), k1 = cl_kfirst(r + 1, C, nz);
+    const int klo = max(1, k0), khi = min(nz - 1, k1 - 1);
+    const int nk = max(0, khi - klo + 1);
+    const int base = (klo - k0) * pp;   // first interior plane in A and B
+    const int m0 = r * E.mm, nm = max(0, min(P, m0 + E.mm) - m0);
+    const int nx4 = nx / 4;
+    for (int q = t; q < 2 * nx * nx + 2 * ny * ny; q += bd) Qx[q] = E.Q[q];
+    for (int q = t; q < nk * P; q += bd) {
+        const int row = fdiv(q, E.f_x);   // kk ny + j
+        A[base + row * rp + (q - row * nx)] = E.gf[(size_t)klo * P + q];
+    }
+    for (int q = t; q < nm * N; q += bd) Pv[q] = E.p[(size_t)m0 * N + q];
+    __syncthreads();
+    const int rows4 = nk * ny / 4;   // 4-row groups over all planes (ny is a multiple of 4)
+    // forward along x: B[row][mx] = sum_i A[row][i] Qx[mx][i]
+    for (int q = t; q < rows4 * nx4; q += bd) {
+        const int rg = fdiv(q, E.f_x4), cg4 = q - rg * nx4;
+        T acc[4][4];
+        tile4<T, false>(A + base + 4 * rg * rp, 1, rp, QxT + 4 * cg4, nx, nx, acc);
+#pragma unroll
+        for (int a = 0; a < 4; ++a) st4(B + base + (4 * rg + a) * rp + 4 * cg4, acc[a]);
+    }
+    __syncthreads();
+    // forward along y, times h^2: A[my][mx] = h^2 sum_j Qy[my][j] B[j][mx]
+    for (int q = t; q < nk * (ny / 4) * nx4; q += bd) {
+        const int kk = fdiv(q, E.f_t2), rem = q - kk * (ny / 4) * nx4;
+        const int mg = fdiv(rem, E.f_x4), cg4 = rem - mg * nx4;
+        T acc[4][4];
+        tile4<T, true>(QyT + 4 * mg, ny, 0, B + base + kk * pp + 4 * cg4, rp, ny, acc);
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+#pragma unroll
+            for (int b = 0; b < 4; ++b) acc[a][b] *= E.h2;
+            st4(A + base + kk * pp + (4 * mg + a) * rp + 4 * cg4, acc[a]);
+        }
+    }
+    cl.sync();
+    // this CTA's modes: spectral right-hand sides from every plane's holder
+    for (int q = t; q < nm * N; q += bd) {
+        const int mq = fdiv(q, E.f_n);
+        const int k = 1 + q - mq * N;
+        const int o = cl_owner(k, C, nz);
+        const int m = m0 + mq, my = fdiv(m, E.f_x);
+        T* src = A + (k - cl_kfirst(o, C, nz)) * pp + my * rp + (m - my * nx);
+        G[q] = *cl.map_shared_rank(src, o);
+    }
+    __syncthreads();
+    for (int mq = t; mq < nm; mq += bd) {
+        T* g = G + mq * N;
+        const T* pv = Pv + mq * N;
+        T acc = (T)0;
+        for (int k = 0; k < N; ++k) {
+            acc = (g[k] + acc) * pv[k];
+            g[k] = acc;
+        }
+        T x = (T)0;
+        for (int k = N - 1; k >= 0; --k) {
+            x = g[k] + pv[k] * x;
+            g[k] = x;
+        }
+    }
+    __syncthreads();
+    for (int q = t; q < nm * N; q += bd) {
+        const int mq = fdiv(q, E.f_n);
+        const int k = 1 + q - mq * N;
+        const int o = cl_owner(k, C, nz);
+        const int m = m0 + mq, my = fdiv(m, E.f_x);
+        T* dst = A + (k - cl_kfirst(o, C, nz)) * pp + my * rp + (m - my * nx);
+        *cl.map_shared_rank(dst, o) = G[q];
+    }
+    cl.sync();
+    // inverse along y: B[j][mx] = sum_my Qy[my][j] A[my][mx]
+    for (int q = t; q < nk * (ny / 4) * nx4; q += bd) {
+        const int kk = fdiv(q, E.f_t2), rem = q - kk * (ny / 4) * nx4;
+        const int jg = fdiv(rem, E.f_x4), cg4 = rem - jg * nx4;
+        T acc[4][4];
+        tile4<T, true>(Qy + 4 * jg, ny, 0, A + base + kk * pp + 4 * cg4, rp, ny, acc);
+#pragma unroll
+        for (int a = 0; a < 4; ++a) st4(B + base + kk * pp + (4 * jg + a) * rp + 4 * cg4, acc[a]);
+    }
+    __syncthreads();
+    // inverse along x: u[row][i] = sum_mx B[row][mx] Qx[mx][i]
+    for (int q = t; q < rows4 * nx4; q += bd) {
+        const int rg = fdiv(q, E.f_x4), cg4 = q - rg * nx4;
+        T acc[4][4];
+        tile4<T, false>(B + base + 4 * rg * rp, 1, rp, Qx + 4 * cg4, nx, nx, acc);
+#pragma unroll
+        for (int a = 0; a < 4; ++a) st4(E.gu + (size_t)klo * P + (size_t)(4 * rg + a) * nx + 4 * cg4, acc[a]);
+    }
+}
+
+// shared-memory layout of the exact solve of level l on C CTAs; false if it does not fit
+template <typename T>
+bool exact_layout(const pic_ctx* c, int l, int C, ExactLevel<T>* out, size_t* smem)
+{
+    const MGLevel& M = c->mg[l];
+    ExactLevel<T> E{};
+    E.nx = M.nx;
+    E.ny = M.ny;
+    E.nz = M.nz;
+    E.rp = M.nx + 4;
+    E.h2 = (T)(M.h * M.h);
+    const int P = M.nx * M.ny, N = M.nz - 1;
+    if (N < 1 || M.nz < C || M.nx % 4 != 0 || M.ny % 4 != 0) return false;
+    E.mp = (M.nz + C - 1) / C + 1;
+    E.mm = (P + C - 1) / C;
+    auto al = [](size_t b) { return (b + 15) / 16 * 16; };
+    const size_t plane = (size_t)M.ny * E.rp;
+    size_t off = al(sizeof(T) * (2 * (size_t)M.nx * M.nx + 2 * (size_t)M.ny * M.ny));
+    E.off_a = (unsigned int)off;
+    off += al(sizeof(T) * (size_t)E.mp * plane);
+    E.off_b = (unsigned int)off;
+    off += al(sizeof(T) * (size_t)E.mp * plane);
+    E.off_g = (unsigned int)off;
+    off += al(sizeof(T) * (size_t)E.mm * N);
+    E.off_p = (unsigned int)off;
+    off += al(sizeof(T) * (size_t)E.mm * N);
+    if (off > kClSmemMax) return false;
+    E.Q = (const T*)c->ex_q;
+    E.p = (const T*)c->ex_p;
+    E.gf = (const T*)M.f;
+    E.gu = (T*)M.u;
+    E.f_x = fast_div(M.nx);
+    E.f_n = fast_div(N);
+    E.f_x4 = fast_div(M.nx / 4);
+    E.f_y4 = fast_div(M.ny / 4);
+    E.f_t2 = fast_div((M.ny / 4) * (M.nx / 4));
+    if (out) *out = E;
+    if (smem) *smem = off;
+    return true;
+}
+
+template <typename T>
+cudaError_t launch_exact(cudaStream_t s, const ExactLevel<T>& E, int C, size_t smem, bool query, int* fits)
+{
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3((unsigned)C, 1, 1);
+    cfg.blockDim = dim3(kClThreads, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = (unsigned)C;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    if (query) {
+        cudaError_t e = cudaFuncSetAttribute(k_coarse_exact<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)kClSmemMax);
+        if (e == cudaSuccess && C > 8)
+            e = cudaFuncSetAttribute(k_coarse_exact<T>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        int n = 0;
+        if (e == cudaSuccess) e = cudaOccupancyMaxActiveClusters(&n, k_coarse_exact<T>, &cfg);
+        *fits = e == cudaSuccess && n > 0;
+        cudaGetLastError();
+        return cudaSuccess;
+    }
+    return cudaLaunchKernelEx(&cfg, k_coarse_exact<T>, E);
+}
+
 
 // grid for kernels that reduce a norm: (x, y) blocks of a plane and just enough
 // z blocks (each looping over planes) to fill the GPU a few times
@@ -927,6 +1186,16 @@ template <typename T>
 void vcycle(pic_ctx* c, int l)
 {
     const int nl = (int)c->mg.size();
+    if (l == c->ex_level) {
+        // this level is solved exactly
+        ExactLevel<T> E{};
+        size_t smem = 0;
+        exact_layout<T>(c, l, c->ex_size, &E, &smem);
+        int fits = 0;
+        launch_exact<T>(c->stream, E, c->ex_size, smem, false, &fits);
+        c->launches += 1;
+        return;
+    }
     if (l >= c->mg_tail) {
         // every level from here down runs in one cluster
         ClusterLevels<T> L{};
@@ -1483,6 +1752,81 @@ pic_status mg_setup(pic_ctx* c)
                 break;
             }
         if (!found) return PIC_ECUDA;
+    }
+    // the finest level below the first that one cluster can solve exactly
+    c->ex_level = -1;
+    for (int l = 1; PIC_MG_EXACT && l < (int)c->mg.size() && c->ex_level < 0; ++l)
+        for (int C : {16, 8, 4, 2, 1}) {
+            if (C > PIC_MG_CLUSTER) continue;
+            if (c->mg[l].nodes > (size_t)PIC_MG_EXACT_MAXNODES) break;
+            size_t smem = 0;
+            const bool ok = c->prec == PIC_MIXED ? exact_layout<float>(c, l, C, nullptr, &smem)
+                                                 : exact_layout<double>(c, l, C, nullptr, &smem);
+            if (!ok) continue;
+            int fits = 0;
+            if (c->prec == PIC_MIXED) launch_exact<float>(nullptr, ExactLevel<float>{}, C, smem, true, &fits);
+            else launch_exact<double>(nullptr, ExactLevel<double>{}, C, smem, true, &fits);
+            if (!fits) continue;
+            c->ex_level = l;
+            c->ex_size = C;
+            break;
+        }
+    if (c->ex_level >= 0) {
+        const MGLevel& M = c->mg[c->ex_level];
+        // orthonormal real Fourier basis of length n (rows) and the eigenvalue of
+        // the periodic second difference on each row
+        auto basis = [](int n, std::vector<double>& q, std::vector<double>& lam) {
+            q.assign((size_t)n * n, 0.0);
+            lam.assign(n, 0.0);
+            for (int i = 0; i < n; ++i) q[i] = 1.0 / std::sqrt((double)n);
+            for (int p = 1; 2 * p < n; ++p) {
+                const double a = 2.0 * kPI * p / n, w = std::sqrt(2.0 / n);
+                for (int i = 0; i < n; ++i) {
+                    q[(size_t)(2 * p - 1) * n + i] = w * std::cos(a * i);
+                    q[(size_t)(2 * p) * n + i] = w * std::sin(a * i);
+                }
+                lam[2 * p - 1] = lam[2 * p] = 2.0 - 2.0 * std::cos(a);
+            }
+            if (n % 2 == 0) {
+                for (int i = 0; i < n; ++i) q[(size_t)(n - 1) * n + i] = (i % 2 ? -1.0 : 1.0) / std::sqrt((double)n);
+                lam[n - 1] = 4.0;
+            }
+        };
+        std::vector<double> qx, lx, qy, ly;
+        basis(M.nx, qx, lx);
+        basis(M.ny, qy, ly);
+        std::vector<double> qall;
+        qall.insert(qall.end(), qx.begin(), qx.end());
+        for (int i = 0; i < M.nx; ++i)
+            for (int m = 0; m < M.nx; ++m) qall.push_back(qx[(size_t)m * M.nx + i]);
+        qall.insert(qall.end(), qy.begin(), qy.end());
+        for (int j = 0; j < M.ny; ++j)
+            for (int m = 0; m < M.ny; ++m) qall.push_back(qy[(size_t)m * M.ny + j]);
+        const int N = M.nz - 1;
+        std::vector<double> piv((size_t)M.nx * M.ny * N);
+        for (int my = 0; my < M.ny; ++my)
+            for (int mx = 0; mx < M.nx; ++mx) {
+                const double d = 2.0 + lx[mx] + ly[my];
+                double pk = 0.0;
+                for (int k = 0; k < N; ++k) {
+                    pk = 1.0 / (d - pk);
+                    piv[((size_t)my * M.nx + mx) * N + k] = pk;
+                }
+            }
+        c->ex_q = dev_alloc(c, tsz * qall.size());
+        c->ex_p = dev_alloc(c, tsz * piv.size());
+        if (!c->ex_q || !c->ex_p) return PIC_ENOMEM;
+        cudaError_t e;
+        if (c->prec == PIC_MIXED) {
+            std::vector<float> a(qall.begin(), qall.end()), b(piv.begin(), piv.end());
+            e = cudaMemcpy(c->ex_q, a.data(), sizeof(float) * a.size(), cudaMemcpyHostToDevice);
+            if (e == cudaSuccess) e = cudaMemcpy(c->ex_p, b.data(), sizeof(float) * b.size(), cudaMemcpyHostToDevice);
+        } else {
+            e = cudaMemcpy(c->ex_q, qall.data(), sizeof(double) * qall.size(), cudaMemcpyHostToDevice);
+            if (e == cudaSuccess)
+                e = cudaMemcpy(c->ex_p, piv.data(), sizeof(double) * piv.size(), cudaMemcpyHostToDevice);
+        }
+        if (e != cudaSuccess) return PIC_ECUDA;
     }
     // exact inverse of the coarsest operator (6 u - neighbour sum) / h^2 with
     // zero values on the electrode planes, by Gauss-Jordan elimination
