@@ -429,7 +429,9 @@ __global__ void __launch_bounds__(kPushThreads, 4) k_push32(const P32 p)
             const unsigned long long q = c0 + (unsigned long long)u * kPushThreads + threadIdx.x;
             int lost = 0;
             bool md = false, cand = false;
-            const float4 Pu = q < n ? p.pos[q] : make_float4(0.f, 0.f, 0.f, __int_as_float(-1));
+            // particle records stream through once: evict-first, so that the charge
+            // and field arrays keep their place in L2
+            const float4 Pu = q < n ? __ldcs(p.pos + q) : make_float4(0.f, 0.f, 0.f, __int_as_float(-1));
             int cell = __float_as_int(Pu.w);
             if (cell >= 0) {
                 ++live;
@@ -442,7 +444,7 @@ __global__ void __launch_bounds__(kPushThreads, 4) k_push32(const P32 p)
                 } else if (p.cell_ng[(k * ny + j) * nx + i] != 0) {
                     // in an MD region: on this step's MD list, advanced by k_md32
                 } else {
-                    const float4 Vu = p.vel[q];
+                    const float4 Vu = __ldcs(p.vel + q);
                     float v[3] = {Vu.x, Vu.y, Vu.z};
                     int a[3] = {qa(o[0]), qa(o[1]), qa(o[2])};
                     float E[3];
@@ -477,8 +479,8 @@ __global__ void __launch_bounds__(kPushThreads, 4) k_push32(const P32 p)
                             cand = u01f(r.x) < p.pnull;
                         }
                         cell = pack(i, j, k);
-                        p.pos[q] = make_float4(o[0], o[1], o[2], __int_as_float(cell));
-                        p.vel[q] = make_float4(v[0], v[1], v[2], Vu.w);
+                        __stcs(p.pos + q, make_float4(o[0], o[1], o[2], __int_as_float(cell)));
+                        __stcs(p.vel + q, make_float4(v[0], v[1], v[2], Vu.w));
                         dcell[u] = cell;
                         da[u][0] = qa(o[0]); da[u][1] = qa(o[1]); da[u][2] = qa(o[2]);
                         md = p.cell_ng[(k * ny + j) * nx + i] != 0;    // in an MD region next step

@@ -1444,27 +1444,27 @@ __global__ void __launch_bounds__(256) k_rhs_df(RhsDf a, Dims d)
     __syncthreads();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y * blockDim.y + threadIdx.y;
-    const int k = blockIdx.z;
     const size_t N = (size_t)d.nx * d.ny * (d.nz + 1);
     float acc = 0.f;
-    if (i < d.nx && j < d.ny) {
-        const int n = (k * d.ny + j) * d.nx + i;
-        const float2 F = df_mul(df_of_i64((long long)a.rq[n]), s_sc);
-        a.F[n] = F;
-        if (k == 0) {
-            a.phi[n] = s_vb;
-            a.phi[N + n] = s_vb;
-        } else if (k == d.nz) {
-            a.phi[n] = s_vt;
-            a.phi[N + n] = s_vt;
-        } else {
-            if (s_shift != 0.f) a.phi[n] = df_add_f(a.phi[n], s_shift * (1.f - (float)k / (float)d.nz));
-            float b = F.x + F.y;
-            if (k == 1) b += s_vb.x;
-            if (k == d.nz - 1) b += s_vt.x;
-            acc = b * b;
+    if (i < d.nx && j < d.ny)
+        for (int k = blockIdx.z; k <= d.nz; k += gridDim.z) {
+            const int n = (k * d.ny + j) * d.nx + i;
+            const float2 F = df_mul(df_of_i64((long long)a.rq[n]), s_sc);
+            a.F[n] = F;
+            if (k == 0) {
+                a.phi[n] = s_vb;
+                a.phi[N + n] = s_vb;
+            } else if (k == d.nz) {
+                a.phi[n] = s_vt;
+                a.phi[N + n] = s_vt;
+            } else {
+                if (s_shift != 0.f) a.phi[n] = df_add_f(a.phi[n], s_shift * (1.f - (float)k / (float)d.nz));
+                float b = F.x + F.y;
+                if (k == 1) b += s_vb.x;
+                if (k == d.nz - 1) b += s_vt.x;
+                acc += b * b;
+            }
         }
-    }
     float b2;
     if (!grid_sum_last(acc, a.part, &a.st->cnt_head, b2)) return;
     if (tid_flat() == 0) {
@@ -1505,38 +1505,40 @@ __global__ void __launch_bounds__(256) k_resid_df(ResDf a, Dims d)
     float2* nxt = a.phi + (s_sel ? 0 : N);
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y * blockDim.y + threadIdx.y;
-    const int k = 1 + blockIdx.z;
     float acc = 0.f;
     if (i < d.nx && j < d.ny) {
         const int P = d.nx * d.ny;
-        const int n = k * P + j * d.nx + i;
-        const int row = n - i;
         const int ip = (i + 1 == d.nx) ? 0 : i + 1, im = (i == 0) ? d.nx - 1 : i - 1;
         const int jp = (j + 1 == d.ny) ? -j * d.nx : d.nx, jm = (j == 0) ? (d.ny - 1) * d.nx : -d.nx;
-        const int nb[6] = {row + ip, row + im, n + jp, n + jm, n + P, n - P};
-        const float2 pc = cur[n];
-        const float ec = a.e ? a.e[n] : 0.f;
-        // 6 phi'_n - sum phi'_nb: hi parts exactly (s + err), the small parts in float
-        float s = 6.f * pc.x;
-        float err = fmaf(6.f, pc.x, -s);
-        float small = 6.f * (pc.y + ec);
+#pragma unroll 2
+        for (int k = 1 + blockIdx.z; k < d.nz; k += gridDim.z) {
+            const int n = k * P + j * d.nx + i;
+            const int row = n - i;
+            const int nb[6] = {row + ip, row + im, n + jp, n + jm, n + P, n - P};
+            const float2 pc = cur[n];
+            const float ec = a.e ? a.e[n] : 0.f;
+            // 6 phi'_n - sum phi'_nb: hi parts exactly (s + err), the small parts in float
+            float s = 6.f * pc.x;
+            float err = fmaf(6.f, pc.x, -s);
+            float small = 6.f * (pc.y + ec);
 #pragma unroll
-        for (int q = 0; q < 6; ++q) {
-            const float2 p = cur[nb[q]];
-            const float eq = a.e ? a.e[nb[q]] : 0.f;
-            float s2, t;
-            two_sum(s, -p.x, s2, t);
-            s = s2;
-            err += t;
-            small -= p.y + eq;
+            for (int q = 0; q < 6; ++q) {
+                const float2 p = cur[nb[q]];
+                const float eq = a.e ? a.e[nb[q]] : 0.f;
+                float s2, t;
+                two_sum(s, -p.x, s2, t);
+                s = s2;
+                err += t;
+                small -= p.y + eq;
+            }
+            const float2 F = a.F[n];
+            float r1, t1;
+            two_sum(F.x, -s, r1, t1);
+            const float R = r1 + ((t1 + F.y) - (err + small));
+            if (a.e) nxt[n] = df_add_f(pc, ec);
+            a.r[n] = R * a.inv_h2;
+            acc += R * R;
         }
-        const float2 F = a.F[n];
-        float r1, t1;
-        two_sum(F.x, -s, r1, t1);
-        const float R = r1 + ((t1 + F.y) - (err + small));
-        if (a.e) nxt[n] = df_add_f(pc, ec);
-        a.r[n] = R * a.inv_h2;
-        acc = R * R;
     }
     float r2;
     if (!grid_sum_last(acc, a.part, &a.st->cnt_res, r2)) return;
@@ -1598,7 +1600,7 @@ void launch_rhs_df(pic_ctx* c, const uint32_t* step, double scale, double vb, do
     a.vb = vb;
     a.vt = vt;
     a.h2 = c->dx * c->dx;
-    const Grid3 g = grid3(d.nx, d.ny, d.nz + 1);
+    const Grid3 g = grid_norm(d.nx, d.ny, d.nz + 1);
     k_rhs_df<<<g.grid, g.block, 0, c->stream>>>(a, d);
     c->launches += 1;
 }
@@ -1624,7 +1626,7 @@ void launch_resid_df(pic_ctx* c, double tol, int max_iters, bool first, bool gra
     a.first = first ? 1 : 0;
     a.use_cond = graph ? 1 : 0;
     a.h = h;
-    const Grid3 g = grid3(d.nx, d.ny, d.nz - 1);
+    const Grid3 g = grid_norm(d.nx, d.ny, d.nz - 1);
     launch_pdl(c->stream, g.grid, g.block, k_resid_df, a, d);
     c->launches += 1;
 }
