@@ -1182,10 +1182,11 @@ void run_resid64(cudaStream_t s, const double* phi, const T* e, const double* f,
     }
 }
 
+// One V-cycle from level l down on A e = f (f in mg[l].f); returns the array
+// that holds the level's correction afterwards.
 template <typename T>
-void vcycle(pic_ctx* c, int l)
+T* vcycle(pic_ctx* c, int l)
 {
-    const int nl = (int)c->mg.size();
     if (l == c->ex_level) {
         // this level is solved exactly
         ExactLevel<T> E{};
@@ -1194,7 +1195,7 @@ void vcycle(pic_ctx* c, int l)
         int fits = 0;
         launch_exact<T>(c->stream, E, c->ex_size, smem, false, &fits);
         c->launches += 1;
-        return;
+        return (T*)c->mg[l].u;
     }
     if (l >= c->mg_tail) {
         // every level from here down runs in one cluster
@@ -1204,7 +1205,7 @@ void vcycle(pic_ctx* c, int l)
         int fits = 0;
         launch_cluster<T>(c->stream, L, c->cl_size, smem, false, &fits);
         c->launches += 1;
-        return;
+        return (T*)c->mg[l].u;
     }
     MGLevel& L = c->mg[l];
     const Dims d{L.nx, L.ny, L.nz};
@@ -1223,11 +1224,12 @@ void vcycle(pic_ctx* c, int l)
     const Dims dc{C.nx, C.ny, C.nz};
     run_resid_restrict<T>(c->stream, u, f, (T*)C.f, (T*)C.u, d, dc, (T)(1.0 / (L.h * L.h)), (T)(C.h * C.h));
     c->launches += 1;
-    vcycle<T>(c, l + 1);
-    run_prolong<T>(c->stream, u, (const T*)C.u, d, dc);
+    T* uc = vcycle<T>(c, l + 1);
+    run_prolong<T>(c->stream, u, (const T*)uc, d, dc);
     c->launches += 1 + 2 * kPost;
     for (int s = 0; s < kPost; ++s)
         for (int color = 0; color < 2; ++color) run_rbgs<T>(c->stream, u, f, d, h2, color, 0);
+    return u;
 }
 
 template <typename T>
@@ -1250,9 +1252,9 @@ pic_status solve_t(pic_ctx* c, double tol, int max_iters, int* iters, double* re
     int it = 0;
     while (!(rn <= target) && it < max_iters) {
         if (!std::isfinite(rn)) break;
-        vcycle<T>(c, 0);
+        const T* e = vcycle<T>(c, 0);
         cudaMemsetAsync(c->d_norm + 1, 0, sizeof(double), c->stream);
-        run_resid64<T>(c->stream, c->phi, (const T*)L0.u, c->f64, c->phi_alt, (T*)L0.f, c->d_norm + 1, d, inv_h2);
+        run_resid64<T>(c->stream, c->phi, e, c->f64, c->phi_alt, (T*)L0.f, c->d_norm + 1, d, inv_h2);
         c->launches += 2;
         std::swap(c->phi, c->phi_alt);
         if (!PIC_CUDA_OK(cudaMemcpyAsync(h_norm + 1, c->d_norm + 1, sizeof(double), cudaMemcpyDeviceToHost,
@@ -1277,9 +1279,9 @@ template <typename T>
 void enqueue_iteration(pic_ctx* c, double tol, int max_iters, cudaGraphConditionalHandle h)
 {
     const Dims d{c->nx, c->ny, c->nz};
-    vcycle<T>(c, 0);
+    const T* e = vcycle<T>(c, 0);
     const Grid3 g = grid3(d.nx, d.ny, d.nz - 1);
-    k_add<T><<<g.grid, g.block, 0, c->stream>>>(c->phi, (const T*)c->mg[0].u, d);
+    k_add<T><<<g.grid, g.block, 0, c->stream>>>(c->phi, e, d);
     run_resid64<T>(c->stream, c->phi, (const T*)nullptr, c->f64, nullptr, (T*)c->mg[0].f, c->d_norm + 1, d,
                    1.0 / (c->dx * c->dx));
     k_conv<<<1, 1, 0, c->stream>>>(c->d_norm, c->d_iters, c->d_res, c->d_solve_flag, c->d_iter_total, tol * tol,
@@ -1605,12 +1607,13 @@ void launch_rhs_df(pic_ctx* c, const uint32_t* step, double scale, double vb, do
     c->launches += 1;
 }
 
-void launch_resid_df(pic_ctx* c, double tol, int max_iters, bool first, bool graph, cudaGraphConditionalHandle h)
+void launch_resid_df(pic_ctx* c, double tol, int max_iters, const float* e, bool graph, cudaGraphConditionalHandle h)
 {
     const Dims d{c->nx, c->ny, c->nz};
     ResDf a{};
     a.phi = c->phi2;
-    a.e = first ? nullptr : (const float*)c->mg[0].u;
+    const bool first = e == nullptr;
+    a.e = e;
     a.F = c->f2;
     a.r = (float*)c->mg[0].f;
     a.part = c->d_part;
@@ -1641,15 +1644,15 @@ void launch_settle_df(pic_ctx* c)
 pic_status solve_df(pic_ctx* c, double tol, int max_iters, int* iters, double* res)
 {
     cudaGraphConditionalHandle none{};
-    launch_resid_df(c, tol, max_iters, true, false, none);
+    launch_resid_df(c, tol, max_iters, nullptr, false, none);
     DfState st{};
     while (true) {
         if (!PIC_CUDA_OK(cudaMemcpyAsync(&st, c->d_dfs, sizeof st, cudaMemcpyDeviceToHost, c->stream)) ||
             !PIC_CUDA_OK(cudaStreamSynchronize(c->stream)))
             return PIC_ECUDA;
         if (!st.more) break;
-        vcycle<float>(c, 0);
-        launch_resid_df(c, tol, max_iters, false, false, none);
+        const float* e = vcycle<float>(c, 0);
+        launch_resid_df(c, tol, max_iters, e, false, none);
     }
     launch_settle_df(c);
     unsigned int it = 0;
@@ -1671,7 +1674,7 @@ void enqueue_solve_head(pic_ctx* c, double tol, int max_iters, cudaGraphConditio
 {
     if (c->prec == PIC_MIXED) {
         launch_rhs_df(c, c->d_step, 0.0, 0.0, 0.0, true);
-        launch_resid_df(c, tol, max_iters, true, true, h);
+        launch_resid_df(c, tol, max_iters, nullptr, true, h);
     } else {
         enqueue_head<double>(c, tol, max_iters, h);
     }
@@ -1680,8 +1683,8 @@ void enqueue_solve_head(pic_ctx* c, double tol, int max_iters, cudaGraphConditio
 void enqueue_solve_iteration(pic_ctx* c, double tol, int max_iters, cudaGraphConditionalHandle h)
 {
     if (c->prec == PIC_MIXED) {
-        vcycle<float>(c, 0);
-        launch_resid_df(c, tol, max_iters, false, true, h);
+        const float* e = vcycle<float>(c, 0);
+        launch_resid_df(c, tol, max_iters, e, true, h);
     } else {
         enqueue_iteration<double>(c, tol, max_iters, h);
     }
