@@ -30,7 +30,28 @@ sys.path.insert(0, ROOT)
 METRIC = "particle-steps/s and Poisson solves/s, mixed vs FP64, 1 GB300, % HBM roof"
 BYTES_MIXED = 64     # per particle-step: float4 pos + float4 vel, read and written
 BYTES_FP64 = 128     # double4 pos + double4 vel, read and written
-SORT_EVERY = 10      # counting-sort interval (steps)
+SORT_EVERY = 5       # counting-sort interval (steps) when not autotuned
+TUNE_STEPS = 20      # steps per candidate interval of the sort autotuner
+
+
+# Poisson: algorithmic bytes per mesh node per refinement iteration: the
+# V(2,2) cycle (4 red-black sweeps x 12 B + residual/restriction 8.5 B +
+# prolongation 8.5 B, x 8/7 for the coarser levels) plus the refinement's
+# residual and update (40 B)
+BYTES_NODE_MIXED = 74 + 40
+BYTES_NODE_FP64 = 148 + 40
+
+
+def poisson_block(pr, cold, wl, bytes_node, peak, peak_kind, precision):
+    solves = max(pr["solves"], 1)
+    ms = pr["solve_ms"] / solves
+    iters = pr["solve_iterations"] / solves
+    nodes = wl.nx * wl.ny * (wl.nz + 1)
+    gbs = iters * bytes_node * nodes / (ms / 1000.0) / 1e9 if ms > 0 else 0.0
+    return {"solves_per_s": 1000.0 / ms if ms > 0 else None, "iterations_per_solve": iters, "ms_per_solve": ms,
+            "bytes_per_node_iteration": bytes_node, "achieved_gbs": gbs, "frac": gbs / peak, "peak_kind": peak_kind,
+            "precision": precision, "warm": "from the previous step's potential, inside the step loop",
+            "cold": cold}
 
 
 def args():
@@ -46,6 +67,7 @@ def args():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--eager", action="store_true", help="no CUDA graphs (for profilers)")
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-tune", action="store_true", help="fixed sort interval (no autotuning)")
     return ap.parse_args()
 
 
@@ -111,10 +133,12 @@ class Clocks:
                 "samples": len(sm)}
 
 
-def run_gpu(P, I, wl, parts, prec, steps, warmup, stream, gpu, flags=0):
+def run_gpu(P, I, wl, parts, prec, steps, warmup, stream, gpu, flags=0, tune=True):
     import torch
     run = P.Run(wl, parts, prec=prec, stream=stream, sort_every=SORT_EVERY, flags=flags)
     run.step(warmup)
+    # sort interval autotuned on the run itself before the timed region
+    sort_every = run.tune_sort(TUNE_STEPS) if tune else SORT_EVERY
     _, c0 = run.counts()
     run.profile(1)
     k0 = run.profile_read()["kernels"]
@@ -135,12 +159,52 @@ def run_gpu(P, I, wl, parts, prec, steps, warmup, stream, gpu, flags=0):
     ms = start.elapsed_time(end)
     prof = run.profile_read()
     n, c1 = run.counts()
+    cold = cold_solves(run)
     run.close()
     return dict(ms=ms, pushed=c1["pushed"] - c0["pushed"], prof=prof, kernels=prof["kernels"] - k0,
-                live=[int(x) for x in n], clocks=clk.summary(), counters=c1)
+                live=[int(x) for x in n], clocks=clk.summary(), counters=c1, cold=cold, sort_every=sort_every)
 
 
-def e2e(P, wl, parts, prec, steps, stream):
+def cold_solves(run, reps=3):
+    """Solve-only loop from a zero potential on the last step's charge density
+    (the warm solves are the ones inside the timed step loop)."""
+    import numpy as np
+    import torch
+    zero = np.zeros_like(run.phi())
+    times, iters = [], []
+    for _ in range(reps):
+        run.set_phi(zero)
+        torch.cuda.synchronize()
+        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s.record(torch.cuda.current_stream())
+        it, _ = run.solve()
+        e.record(torch.cuda.current_stream())
+        torch.cuda.synchronize()
+        times.append(s.elapsed_time(e))
+        iters.append(it)
+    return {"ms_per_solve": statistics.median(times), "iterations_per_solve": statistics.median(iters)}
+
+
+def traffic_from_profile(kernel_source, name):
+    """DRAM bytes per launch of the push kernel from its committed ncu summary,
+    or None when the kernel's source has changed since that capture."""
+    import hashlib
+    try:
+        text = open(os.path.join(ROOT, "profiles", name)).read()
+        src = open(os.path.join(ROOT, "paper_1801_00972_gb300", "csrc", kernel_source), "rb").read()
+    except OSError:
+        return None
+    vals = dict(line.split(":", 1) for line in text.splitlines() if line.startswith(("traffic_bytes_per_launch:",
+                                                                                    "source_sha256:")))
+    if vals.get("source_sha256", "").strip() != hashlib.sha256(src).hexdigest():
+        return None
+    try:
+        return float(vals["traffic_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+def e2e(P, wl, parts, prec, steps, stream, sort_every):
     """Through the public API from host buffers: init (host->device copy of the
     particles), then each step followed by a device->host read of the grain
     charges (the step's result)."""
@@ -148,7 +212,7 @@ def e2e(P, wl, parts, prec, steps, stream):
     import torch
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    run = P.Run(wl, parts, prec=prec, stream=stream, sort_every=SORT_EVERY)
+    run = P.Run(wl, parts, prec=prec, stream=stream, sort_every=sort_every)
     _, c0 = run.counts()
     for _ in range(steps):
         run.step(1)
@@ -259,12 +323,12 @@ def main():
     parts = I.sample_particles(wl)
     stream = torch.cuda.current_stream().cuda_stream
     flags = P.PIC_F_NO_GRAPH if a.eager else 0
-    mixed = run_gpu(P, I, wl, parts, P.PIC_MIXED, a.steps, a.warmup, stream, local, flags)
+    mixed = run_gpu(P, I, wl, parts, P.PIC_MIXED, a.steps, a.warmup, stream, local, flags, tune=not a.no_tune)
     fp64 = None
     if not a.no_fp64:
         fp64 = run_gpu(P, I, wl, parts, P.PIC_FP64, a.fp64_steps or max(a.steps // 4, 10), a.warmup, stream, local,
-                       flags)
-    ee = None if a.no_e2e else e2e(P, wl, parts, P.PIC_MIXED, max(a.steps // 4, 10), stream)
+                       flags, tune=False)
+    ee = None if a.no_e2e else e2e(P, wl, parts, P.PIC_MIXED, max(a.steps // 4, 10), stream, mixed["sort_every"])
     bb = None if (a.no_batch or world > 1) else batch_bench(P, I, max(a.steps // 4, 10), a.warmup)
 
     def agg(x):
@@ -307,14 +371,16 @@ def main():
                                f"{wl.n_e + wl.n_i:.0e} macroparticles, 13.56 MHz 100 V, 2 Pa",
                    "parallelism": "replicas only" if world > 1 else "1 GPU",
                    "l2": "inputs larger than L2 (particle arrays 320 MB mixed / 640 MB FP64)",
-                   "sort_every": SORT_EVERY, "tol": 1e-10},
+                   "sort_every": mixed["sort_every"],
+                   "sort_interval": "fixed" if a.no_tune else "autotuned (pic_tune_sort)",
+                   "tol": 1e-10},
         "roofline": {"bound": "hbm", "kernel": "k_push32 (fused gather/push/MD/absorb/MCC/deposit)",
                      "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                     "peak_kind": peak_kind, "bytes_per_particle_step": BYTES_MIXED, "traffic": None,
+                     "peak_kind": peak_kind, "bytes_per_particle_step": BYTES_MIXED,
+                     "traffic": traffic_from_profile("particles_mixed.cu", "k_push32_w1_64x64x256_1e7.md"),
                      "avg_launch_ms": pr["push_ms"] / max(pr["push_launches"], 1),
                      "launches": pr["push_launches"]},
-        "poisson": {"solves_per_s": solves_s, "iterations_per_solve": pr["solve_iterations"] / max(pr["solves"], 1),
-                    "ms_per_solve": pr["solve_ms"] / max(pr["solves"], 1), "precision": "mixed"},
+        "poisson": poisson_block(pr, mixed["cold"], wl, BYTES_NODE_MIXED, peak, peak_kind, "mixed"),
         "gpu_launches": mixed["kernels"],
         "clocks": mixed["clocks"],
         "live_particles_end": mixed["live"],
@@ -326,8 +392,7 @@ def main():
         line["fp64"] = {"value": f[1] / (f[0] / 1000.0), "unit": "particle-steps/s", "steps": fp64_steps(a),
                         "ms_per_step": f[0] / fp64_steps(a),
                         "push_achieved_gbs": fach, "push_frac": fach / peak,
-                        "poisson_solves_per_s": fp["solves"] / (fp["solve_ms"] / 1000.0) if fp["solve_ms"] else None,
-                        "poisson_iterations_per_solve": fp["solve_iterations"] / max(fp["solves"], 1),
+                        "poisson": poisson_block(fp, fp64["cold"], wl, BYTES_NODE_FP64, peak, peak_kind, "fp64"),
                         "mixed_speedup": (m_tot / m_ms) / (f[1] / f[0])}
     if ee is not None:
         line["e2e"] = ee

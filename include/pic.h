@@ -126,6 +126,16 @@ pic_status pic_init(const pic_mesh* mesh, const pic_electrodes* el, const pic_ga
  * on the run's stream.  Returns the status of the previous steps' solves. */
 pic_status pic_step(pic_ctx* ctx, int32_t n_steps);
 
+/* Autotune the counting-sort interval (the paper is silent on particle order;
+ * it only affects speed: the deposit is an exact integer sum and the random
+ * numbers are keyed on particle ids, so the physics does not depend on it).
+ * Steps the run by at least steps_per_candidate steps (rounded up to whole
+ * sort periods, at least two) for each interval in {2, 3, 4, 5, 6, 8, 10, 14,
+ * 20}, timing each with CUDA events, and keeps the fastest.  The run advances
+ * by all of these steps.  *chosen (may be NULL) receives the interval.
+ * PIC_EINVAL for steps_per_candidate < 1; errors of the steps as pic_step. */
+pic_status pic_tune_sort(pic_ctx* ctx, int32_t steps_per_candidate, int32_t* chosen);
+
 /* The particle half of one step: CIC gather of -grad phi (Eq. 4), leapfrog push
  * (Eqs. 1-2) with MD subcycling and the PPPM correction (Eqs. 5-6) near grains,
  * electrode and grain absorption, null-collision MCC with ionization products,

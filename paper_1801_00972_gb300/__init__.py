@@ -31,7 +31,7 @@ COUNTERS = ("lost_bot_e", "lost_bot_i", "lost_top_e", "lost_top_i", "abs_e", "ab
 PIC_C_N = len(COUNTERS)
 
 # every symbol include/pic.h declares
-SYMBOLS = ("pic_init", "pic_step", "pic_advance", "pic_solve", "pic_grain_charges", "pic_counts",
+SYMBOLS = ("pic_init", "pic_step", "pic_tune_sort", "pic_advance", "pic_solve", "pic_grain_charges", "pic_counts",
            "pic_moments", "pic_get_particles", "pic_get_rho", "pic_get_phi", "pic_set_phi",
            "pic_get_grain_table", "pic_set_grain_table", "pic_set_grain_counts", "pic_step_index",
            "pic_profile", "pic_profile_read", "pic_solve_noalloc", "pic_batch_init", "pic_batch_step",
@@ -87,7 +87,7 @@ def load(path: str | None = None):
         L.pic_init.argtypes = [C.POINTER(pic_mesh), C.POINTER(pic_electrodes), C.POINTER(pic_gas),
                                C.POINTER(pic_grains), C.POINTER(pic_run), vp, C.POINTER(vp)]
         sig = {
-            "pic_step": [vp, i32], "pic_advance": [vp], "pic_solve": [vp, C.POINTER(i32), pd],
+            "pic_step": [vp, i32], "pic_tune_sort": [vp, i32, C.POINTER(i32)], "pic_advance": [vp], "pic_solve": [vp, C.POINTER(i32), pd],
             "pic_grain_charges": [vp, pi64, pd], "pic_counts": [vp, pi64, pi64],
             "pic_moments": [vp, i32, pd, sz, i32],
             "pic_get_particles": [vp, i32, pd, pd, pu32, i64, pi64],
@@ -144,6 +144,12 @@ def pic_init(mesh, electrodes, gas, grains, run, stream=None):
 
 def pic_step(ctx, n_steps):
     return _check(ctx, load().pic_step(ctx, int(n_steps)))
+
+
+def pic_tune_sort(ctx, steps_per_candidate):
+    chosen = C.c_int32()
+    _check(ctx, load().pic_tune_sort(ctx, int(steps_per_candidate), C.byref(chosen)))
+    return chosen.value
 
 
 def pic_advance(ctx):
@@ -369,6 +375,9 @@ class Run:
 
     def step(self, n=1):
         pic_step(self.ctx, n)
+
+    def tune_sort(self, steps_per_candidate=20):
+        return pic_tune_sort(self.ctx, steps_per_candidate)
 
     def advance(self):
         pic_advance(self.ctx)

@@ -790,6 +790,44 @@ pic_status pic_step(pic_ctx* c, int32_t n_steps)
     return check(c);
 }
 
+pic_status pic_tune_sort(pic_ctx* c, int32_t steps_per_candidate, int32_t* chosen)
+{
+    if (!c || steps_per_candidate < 1) return PIC_EINVAL;
+    const int32_t cand[] = {2, 3, 4, 5, 6, 8, 10, 14, 20};
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (!PIC_CUDA_OK(cudaEventCreate(&e0)) || !PIC_CUDA_OK(cudaEventCreate(&e1))) {
+        if (e0) cudaEventDestroy(e0);
+        return cuda_fail(c, cudaGetLastError(), "tune events");
+    }
+    int32_t best = c->sort_every;
+    float best_ms = 0.f;
+    pic_status st = PIC_OK;
+    for (int32_t s : cand) {
+        c->sort_every = s;
+        const int32_t whole = std::max(steps_per_candidate, 2 * s);
+        const int32_t n = (whole + s - 1) / s * s;
+        // start on a sort boundary so that every candidate covers whole periods
+        const int32_t lead = (int32_t)((s - c->step % s) % s);
+        if (lead > 0 && (st = step_enqueue(c, lead)) != PIC_OK) break;
+        cudaEventRecord(e0, c->stream);
+        if ((st = step_enqueue(c, n)) != PIC_OK) break;
+        cudaEventRecord(e1, c->stream);
+        if ((st = check(c)) != PIC_OK) break;
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        ms /= (float)n;
+        if (best_ms == 0.f || ms < best_ms) {
+            best_ms = ms;
+            best = s;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    c->sort_every = best;
+    if (chosen) *chosen = best;
+    return st;
+}
+
 pic_status pic_batch_init(int32_t n, const pic_mesh* meshes, const pic_electrodes* els, const pic_gas* gases,
                           const pic_grains* grains, const pic_run* runs, pic_batch** out)
 {

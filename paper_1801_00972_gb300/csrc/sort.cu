@@ -27,10 +27,13 @@ __global__ void k_hist(const T4* __restrict__ pos, const unsigned long long* nsl
                        int ny)
 {
     const unsigned long long n = nslot[sp];
+    const int lane = threadIdx.x & 31;
     for (unsigned long long q = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; q < n;
          q += (unsigned long long)gridDim.x * blockDim.x) {
         const int c = key_of(pos[q], nx, ny);
-        if (c >= 0) atomicAdd(hist + c, 1u);
+        // lanes with the same cell (common in nearly sorted input) add once
+        const unsigned m = __match_any_sync(__activemask(), c);
+        if (c >= 0 && lane == __ffs(m) - 1) atomicAdd(hist + c, (unsigned int)__popc(m));
     }
 }
 
@@ -88,12 +91,20 @@ __global__ void k_scatter(const T4* __restrict__ pos, const T4* __restrict__ vel
                           int ny, const int* cell_ng, unsigned int* md_next, unsigned int* next_n)
 {
     const unsigned long long n = nslot[sp];
+    const int lane = threadIdx.x & 31;
     for (unsigned long long q = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; q < n;
          q += (unsigned long long)gridDim.x * blockDim.x) {
         const T4 p = pos[q];
         const int c = key_of(p, nx, ny);
+        // one cursor atomic per group of lanes with the same cell; the group's
+        // lanes take consecutive slots in lane order
+        const unsigned m = __match_any_sync(__activemask(), c);
+        const int leader = __ffs(m) - 1;
+        unsigned int base = 0;
+        if (c >= 0 && lane == leader) base = atomicAdd(cursor + c, (unsigned int)__popc(m));
+        base = __shfl_sync(m, base, leader);
         if (c < 0) continue;
-        const unsigned int d = atomicAdd(cursor + c, 1u);
+        const unsigned int d = base + (unsigned int)__popc(m & ((1u << lane) - 1u));
         pos_out[d] = p;
         vel_out[d] = vel[q];
         if (md_next && cell_ng[c] != 0) md_next[atomicAdd(next_n, 1u)] = d;

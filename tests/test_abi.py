@@ -89,3 +89,10 @@ def test_invalid_arguments_rejected(lib, bad):
         P.pic_init(mesh, el, gas, grains, run)
     assert e.value.status == P.PIC_EINVAL
     assert P.pic_last_error(None)
+
+
+def test_null_context_rejected(lib):
+    # entry points that take a run context refuse a null one without touching the GPU
+    assert lib.pic_step(None, 1) == P.PIC_EINVAL
+    assert lib.pic_tune_sort(None, 5, None) == P.PIC_EINVAL
+    assert lib.pic_advance(None) == P.PIC_EINVAL

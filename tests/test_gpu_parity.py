@@ -161,6 +161,28 @@ def test_sort_does_not_change_results():
     assert np.array_equal(a.phi(), b.phi())
 
 
+@pytest.mark.parametrize("prec", [P.PIC_FP64, P.PIC_MIXED])
+def test_sort_autotune_does_not_change_results(prec):
+    # pic_tune_sort steps the run with every candidate interval; particle order
+    # never enters the physics, so the state equals that of plain steps
+    wl = I.small(nx=16, ny=8, nz=16, n_e=4000, n_i=4000, grains=1, v_dc=-40.0)
+    parts = I.sample_particles(wl)
+    a = P.Run(wl, parts, prec=prec, stream=_stream(), sort_every=7)
+    b = P.Run(wl, parts, prec=prec, stream=_stream(), sort_every=7)
+    chosen = a.tune_sort(2)
+    assert chosen in (2, 3, 4, 5, 6, 8, 10, 14, 20)
+    n = a.step_index
+    assert n >= 9 * 4
+    b.step(n)
+    a.step(3)
+    b.step(3)
+    for sp in range(2):
+        xa, va, ia = a.particles(sp)
+        xb, vb, ib = b.particles(sp)
+        assert np.array_equal(ia, ib) and np.array_equal(xa, xb) and np.array_equal(va, vb)
+    assert np.array_equal(a.rho(), b.rho())
+
+
 @pytest.mark.parametrize("shape", [(8, 8, 16), (16, 16, 32)])
 def test_mixed_step_close_to_oracle(shape):
     nx, ny, nz = shape
