@@ -29,10 +29,10 @@ namespace pic {
 namespace {
 
 #ifndef PIC_PUSH_PPT
-#define PIC_PUSH_PPT 2
+#define PIC_PUSH_PPT 4
 #endif
 #ifndef PIC_PUSH_WINR
-#define PIC_PUSH_WINR 128
+#define PIC_PUSH_WINR 256
 #endif
 #ifndef PIC_PUSH_TILE
 #define PIC_PUSH_TILE 0
@@ -46,6 +46,7 @@ constexpr int kChunk = kPushThreads * kPPT;      // particles per block per chun
 // (a chunk adds at most kChunk * 2^21 < 2^32 to a slot)
 constexpr int kWinR = PIC_PUSH_WINR;
 constexpr int kWinN = 4 * 2 * kWinR;
+static_assert(kChunk < 2048, "a chunk's window counters would overflow");
 constexpr bool kTile = PIC_PUSH_TILE != 0;       // gather E from a shared-memory tile
 
 struct P32 {

@@ -41,6 +41,9 @@
 #ifndef PIC_MG_EXACT_MAXNODES
 #define PIC_MG_EXACT_MAXNODES 32768  // largest level solved exactly (Fourier transforms cost grows as n^1.5)
 #endif
+#ifndef PIC_NORM_BLOCKS
+#define PIC_NORM_BLOCKS 1216   // blocks of the plane-looping kernels that reduce a norm
+#endif
 #ifndef PIC_MG_CL_THREADS
 #define PIC_MG_CL_THREADS 512  // threads per CTA of the cluster
 #endif
@@ -1135,7 +1138,7 @@ inline Grid3 grid_norm(int nx, int ny, int planes)
 {
     Grid3 g = grid3(nx, ny, 1);
     const int per_plane = (int)(g.grid.x * g.grid.y);
-    const int zb = std::max(1, std::min(planes, (152 * 4 + per_plane - 1) / per_plane));
+    const int zb = std::max(1, std::min(planes, (PIC_NORM_BLOCKS + per_plane - 1) / per_plane));
     g.grid.z = (unsigned)zb;
     return g;
 }
