@@ -26,6 +26,7 @@ _lib = None
 NO_MCC = 1
 IONS_FROZEN = 2
 MOMENTS = 8
+COULOMB = 32
 
 # counter slots of orc_get_counters
 C_NAMES = ("lost_bot_e", "lost_bot_i", "lost_top_e", "lost_top_i", "abs_e", "abs_i",
@@ -64,6 +65,7 @@ class Cfg(C.Structure):
         ("x_init", C.POINTER(C.c_double) * 2),
         ("v_init", C.POINTER(C.c_double) * 2),
         ("id_init", C.POINTER(C.c_uint32) * 2),
+        ("coulomb_log", C.c_double),
     ]
 
 
@@ -81,6 +83,8 @@ def lib():
             for f in ("orc_advance", "orc_solve", "orc_step"):
                 getattr(L, f).argtypes = [vp]
                 getattr(L, f).restype = i32
+            L.orc_coulomb.argtypes = [vp]
+            L.orc_coulomb.restype = None
             L.orc_count.argtypes = [vp, i32]; L.orc_count.restype = i64
             L.orc_get_particles.argtypes = [vp, i32, pd, pd, pu32]
             L.orc_get_rho.argtypes = [vp, pi64]
@@ -161,7 +165,7 @@ class Sim:
     ``paper_1801_00972_gb300.inputs.Workload`` (duck-typed; this module does not
     import the package)."""
 
-    def __init__(self, wl, particles, flags: int = 0, md_sub: int | None = None):
+    def __init__(self, wl, particles, flags: int = 0, md_sub: int | None = None, coulomb_log: float = 10.0):
         L = lib()
         self._keep = []
         cfg = Cfg()
@@ -182,6 +186,7 @@ class Sim:
         cfg.gpos = _p(g, C.c_double) if r.size else None
         cfg.grad = _p(r, C.c_double) if r.size else None
         cfg.seed, cfg.run_id, cfg.flags = wl.seed, wl.run_id, flags
+        cfg.coulomb_log = coulomb_log
         self._keep += [xs, g, r]
         for sp in range(2):
             x, v, ids = particles[sp]
@@ -212,6 +217,10 @@ class Sim:
 
     def solve(self):
         assert lib().orc_solve(self.h) == 0
+
+    def coulomb(self):
+        """One Coulomb collision pass on the current particles (as at the end of a step)."""
+        lib().orc_coulomb(self.h)
 
     def step(self, n: int = 1):
         for _ in range(n):

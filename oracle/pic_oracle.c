@@ -44,7 +44,8 @@
 #define WQ    16384                /* fixed-point CIC weight units per axis (2^14) */
 #define MAXG  8                    /* grains per MD cell */
 
-enum { PUR_MCC = 1, PUR_DIR = 2, PUR_NEUTRAL = 3, PUR_CHILD_DIR = 4, PUR_CHILD_NEUTRAL = 5 };
+enum { PUR_MCC = 1, PUR_DIR = 2, PUR_NEUTRAL = 3, PUR_CHILD_DIR = 4, PUR_CHILD_NEUTRAL = 5,
+       PUR_COUL_ORDER = 6, PUR_COUL_EE = 7, PUR_COUL_II = 8, PUR_COUL_EI = 9 };
 
 /* ------------------------------------------------------------------------ */
 /* Philox4x32-10 counter-based generator (Salmon, Moraes, Dror, Shaw, SC'11) */
@@ -633,6 +634,160 @@ static void moments_accumulate(orc_sim* s)
     s->msteps++;
 }
 
+/* ---------------------------------------------------------------------------
+ * Binary Coulomb collisions (Table I, "Coulomb collision e+e, e+Ar+, Ar+ +Ar+";
+ * the paper's cited binary-collision model of Takizuka and Abe, 1977), applied
+ * once per step to the particles alive at its end, cell by cell:
+ *   - the particles of a cell are put in the order of the key
+ *     (Philox(id, step, PUR_COUL_ORDER) word 0, then id): a random pairing that
+ *     does not depend on array order;
+ *   - like particles pair as (0,1), (2,3), ...; an odd count makes the first
+ *     three a triplet (0,1), (1,2), (2,0), each with half the time step;
+ *   - e-i: every particle of the larger group A (electrons on a tie) meets
+ *     B[k mod |B|]; the density is that of the smaller group;
+ *   - order inside a cell: e-e, i-i, e-i.
+ * One collision of A and B with relative velocity u (|u| > 0) over dt:
+ *   mu = mA mB / (mA + mB),
+ *   sigma^2 = qA^2 qB^2 lnL / (8 pi eps0^2 mu^2) * n * dt / |u|^3,
+ *   delta = sigma * N(0,1) = tan(Theta/2): sin Theta = 2 delta / (1 + delta^2),
+ *   1 - cos Theta = 2 delta^2 / (1 + delta^2), azimuth Phi from a uniform point
+ *   (a, b) of the unit disk: cos Phi = (a^2 - b^2)/s, sin Phi = 2ab/s;
+ *   u' = u rotated by (Theta, Phi) about the frame of u, Du = u' - u,
+ *   vA += (mu/mA) Du, vB -= (mu/mB) Du  (momentum and energy are conserved).
+ * Random numbers: the stream (id of the pair's first particle, step, purpose). */
+static void coul_pair(double* va, double* vb, double ma, double mb, double cfac, double n, double dt, uint32_t id,
+                      uint32_t step, uint32_t purpose, const uint32_t key[2])
+{
+    const double u[3] = { va[0] - vb[0], va[1] - vb[1], va[2] - vb[2] };
+    const double u2 = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+    if (!(u2 > 0.0)) return;
+    const double um = sqrt(u2);
+    const double sig2 = ((cfac * n) * dt) / (u2 * um);
+    rstream r; rs_init(&r, id, step, purpose, key);
+    double g, g2;
+    rs_gauss2(&r, &g, &g2);
+    const double d = sqrt(sig2) * g;
+    const double den = 1.0 + d * d;
+    const double sn = (2.0 * d) / den, omc = (2.0 * (d * d)) / den;
+    double a = 0.0, b = 0.0, s2 = 0.0;
+    int t;
+    for (t = 0; t < 128; ++t) {
+        rs_pair(&r, &a, &b);
+        s2 = a * a + b * b;
+        if (s2 < 1.0 && s2 > 0.0) break;
+    }
+    double cp = 1.0, sp = 0.0;
+    if (t < 128) { cp = (a * a - b * b) / s2; sp = (2.0 * (a * b)) / s2; }
+    const double up = sqrt(u[0] * u[0] + u[1] * u[1]);
+    double du[3];
+    if (up > 0.0) {
+        du[0] = (u[0] / up) * u[2] * sn * cp - (u[1] / up) * um * sn * sp - u[0] * omc;
+        du[1] = (u[1] / up) * u[2] * sn * cp + (u[0] / up) * um * sn * sp - u[1] * omc;
+        du[2] = -up * sn * cp - u[2] * omc;
+    } else {
+        du[0] = um * sn * cp;
+        du[1] = um * sn * sp;
+        du[2] = -u[2] * omc;
+    }
+    const double mu = (ma * mb) / (ma + mb);
+    const double fa = mu / ma, fb = mu / mb;
+    for (int q = 0; q < 3; ++q) { va[q] = va[q] + fa * du[q]; vb[q] = vb[q] - fb * du[q]; }
+}
+
+typedef struct { uint64_t key; int64_t idx; } coul_ent;
+static int cmp_coul(const void* a, const void* b)
+{
+    const uint64_t x = ((const coul_ent*)a)->key, y = ((const coul_ent*)b)->key;
+    return x < y ? -1 : (x > y ? 1 : 0);
+}
+
+void orc_coulomb(orc_sim* s)
+{
+    const size_t nc = cells_of(s);
+    const double vol = s->c.dx * s->c.dx * s->c.dx;
+    const double w = s->c.weight, lnl = s->c.coulomb_log, dt = s->c.dt;
+    const uint32_t step = (uint32_t)s->step;
+    const double m[2] = { ME, MAR };
+    /* qA^2 qB^2 lnL / (8 pi eps0^2 mu^2) for e-e, i-i, e-i */
+    double cf[3];
+    for (int k = 0; k < 3; ++k) {
+        const double ma = k == 1 ? MAR : ME, mb = k == 0 ? ME : MAR;
+        const double mu = (ma * mb) / (ma + mb);
+        cf[k] = ((((QE * QE) * (QE * QE)) * lnl) / (((8.0 * PI_D) * (EPS0 * EPS0)) * (mu * mu)));
+    }
+    /* particles of each species grouped by cell, in key order inside a cell */
+    coul_ent* ent[2];
+    size_t* start[2];
+    for (int sp = 0; sp < 2; ++sp) {
+        ent[sp] = (coul_ent*)malloc(sizeof(coul_ent) * (size_t)(s->n[sp] + 1));
+        start[sp] = (size_t*)calloc(nc + 1, sizeof(size_t));
+        int64_t* cellof = (int64_t*)malloc(sizeof(int64_t) * (size_t)(s->n[sp] + 1));
+        for (int64_t q = 0; q < s->n[sp]; ++q) {
+            int c[3]; double f[3];
+            locate(s, s->x[sp] + 3 * q, c, f);
+            cellof[q] = (int64_t)cell_index(s, c);
+            start[sp][cellof[q] + 1]++;
+        }
+        for (size_t c = 0; c < nc; ++c) start[sp][c + 1] += start[sp][c];
+        size_t* fill = (size_t*)malloc(sizeof(size_t) * (nc + 1));
+        memcpy(fill, start[sp], sizeof(size_t) * (nc + 1));
+        for (int64_t q = 0; q < s->n[sp]; ++q) {
+            const uint32_t id = s->id[sp][q];
+            const uint32_t ctr[4] = { id, step, PUR_COUL_ORDER, 0 };
+            uint32_t o[4];
+            orc_philox4x32_10(ctr, s->key, o);
+            coul_ent e; e.key = ((uint64_t)o[0] << 32) | id; e.idx = q;
+            ent[sp][fill[cellof[q]]++] = e;
+        }
+        for (size_t c = 0; c < nc; ++c)
+            qsort(ent[sp] + start[sp][c], start[sp][c + 1] - start[sp][c], sizeof(coul_ent), cmp_coul);
+        free(fill);
+        free(cellof);
+    }
+    for (size_t c = 0; c < nc; ++c) {
+        const int64_t n0 = (int64_t)(start[0][c + 1] - start[0][c]), n1 = (int64_t)(start[1][c + 1] - start[1][c]);
+        const coul_ent* E = ent[0] + start[0][c];
+        const coul_ent* I = ent[1] + start[1][c];
+        /* like particles */
+        for (int sp = 0; sp < 2; ++sp) {
+            const int64_t n = sp == 0 ? n0 : n1;
+            const coul_ent* L = sp == 0 ? E : I;
+            if (n < 2) continue;
+            const double dens = ((double)n * w) / vol;
+            double* v = s->v[sp];
+            const uint32_t pur = sp == 0 ? PUR_COUL_EE : PUR_COUL_II;
+            int64_t j = 0;
+            if (n % 2 == 1) {
+                const double h = 0.5 * dt;
+                for (int t = 0; t < 3; ++t) {
+                    const int64_t a = L[t].idx, b = L[(t + 1) % 3].idx;
+                    coul_pair(v + 3 * a, v + 3 * b, m[sp], m[sp], cf[sp], dens, h, s->id[sp][a], step, pur, s->key);
+                }
+                j = 3;
+            }
+            for (; j + 1 < n; j += 2) {
+                const int64_t a = L[j].idx, b = L[j + 1].idx;
+                coul_pair(v + 3 * a, v + 3 * b, m[sp], m[sp], cf[sp], dens, dt, s->id[sp][a], step, pur, s->key);
+            }
+        }
+        /* electrons and ions */
+        if (n0 > 0 && n1 > 0) {
+            const int big = n0 >= n1 ? 0 : 1;
+            const int64_t na = big == 0 ? n0 : n1, nb = big == 0 ? n1 : n0;
+            const coul_ent* A = big == 0 ? E : I;
+            const coul_ent* B = big == 0 ? I : E;
+            const double dens = ((double)nb * w) / vol;
+            for (int64_t k = 0; k < na; ++k) {
+                const int64_t a = A[k].idx, b = B[k % nb].idx;
+                double* va = s->v[big] + 3 * a;
+                double* vb = s->v[1 - big] + 3 * b;
+                coul_pair(va, vb, m[big], m[1 - big], cf[2], dens, dt, s->id[big][a], step, PUR_COUL_EI, s->key);
+            }
+        }
+    }
+    for (int sp = 0; sp < 2; ++sp) { free(ent[sp]); free(start[sp]); }
+}
+
 int orc_advance(orc_sim* s)
 {
     const size_t N = nodes_of(s);
@@ -709,6 +864,7 @@ int orc_advance(orc_sim* s)
         s->id[1][s->n[1]++] = s->next_id + (uint32_t)(2 * r + 1);
     }
     s->next_id += (uint32_t)(2 * s->nch);
+    if (s->c.flags & ORC_COULOMB) orc_coulomb(s);
     deposit_all(s);
     s->step++;
     (void)N;

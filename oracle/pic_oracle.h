@@ -23,6 +23,7 @@ extern "C" {
 #define ORC_NO_MCC      1   /* skip Monte Carlo collisions                     */
 #define ORC_IONS_FROZEN 2   /* ions neither move nor collide (test-only)       */
 #define ORC_MOMENTS     8   /* accumulate node moments every step              */
+#define ORC_COULOMB    32   /* binary Coulomb collisions e-e, i-i, e-i (Table I) */
 
 typedef struct {
     int32_t nx, ny, nz, md_sub;      /* cells; MD subcycles per step (Sec. III: 40) */
@@ -43,6 +44,7 @@ typedef struct {
     const double*   x_init[2];       /* 3*n per species */
     const double*   v_init[2];       /* 3*n per species */
     const uint32_t* id_init[2];      /* n per species */
+    double   coulomb_log;            /* Coulomb logarithm of the binary collisions (ORC_COULOMB) */
 } orc_cfg;
 
 typedef struct orc_sim orc_sim;
@@ -57,6 +59,7 @@ void     orc_destroy(orc_sim* s);
 int      orc_advance(orc_sim* s);                   /* particles, grains, children, deposit; step += 1 */
 int      orc_solve(orc_sim* s);                     /* phi from rho at t = step*dt */
 int      orc_step(orc_sim* s);                      /* advance + solve */
+void     orc_coulomb(orc_sim* s);                   /* one Coulomb collision pass at the current step */
 
 int64_t  orc_count(const orc_sim* s, int sp);
 void     orc_get_particles(const orc_sim* s, int sp, double* x, double* v, uint32_t* id);
