@@ -59,6 +59,15 @@ typedef enum { PIC_FP64 = 0, PIC_MIXED = 1 } pic_precision;
 #define PIC_F_NO_MCC      1   /* no Monte Carlo collisions                       */
 #define PIC_F_IONS_FROZEN 2   /* ions neither move nor collide (test use)        */
 #define PIC_F_MOMENTS     8   /* accumulate node moments after every step        */
+#define PIC_F_COULOMB    32   /* binary Coulomb collisions e-e, e-Ar+, Ar+-Ar+ (Table I)
+                                 once per step, cell by cell, after the ionization
+                                 products join: in-cell pairs in the order of a Philox
+                                 key of (id, step), like pairs (0,1),(2,3),... with an odd
+                                 count's first three as a triplet at half the time step,
+                                 e-i pairs A[k] with B[k mod |B|] (A the larger group) at
+                                 the smaller group's density; per pair tan(Theta/2) is
+                                 normal with variance q^4 lnL n dt / (8 pi eps0^2 mu^2 u^3),
+                                 the binary-collision model the paper cites (Sec. III) */
 #define PIC_F_NO_GRAPH   16   /* pic_step launches kernels one by one and runs the
                                  Poisson loop from the host (for profilers that
                                  cannot see inside CUDA graphs); same results */
@@ -113,6 +122,7 @@ typedef struct {
     int32_t flags;                /* PIC_F_* */
     double tol;                   /* Poisson relative residual tolerance (e.g. 1e-10) */
     int32_t max_cycles;           /* Poisson refinement iterations per solve */
+    double coulomb_log;           /* Coulomb logarithm lnL (> 0 with PIC_F_COULOMB) */
 } pic_run;
 
 /* Create a run: copies every input to the device, deposits rho_0 (particles

@@ -25,7 +25,7 @@ PIC_OK, PIC_EINVAL, PIC_ENOMEM, PIC_ECUDA, PIC_ECAPACITY, PIC_ENONFINITE, PIC_EN
 STATUS = {0: "PIC_OK", 1: "PIC_EINVAL", 2: "PIC_ENOMEM", 3: "PIC_ECUDA", 4: "PIC_ECAPACITY",
           5: "PIC_ENONFINITE", 6: "PIC_ENOTCONV", 7: "PIC_ETIMEOUT"}
 PIC_FP64, PIC_MIXED = 0, 1
-PIC_F_NO_MCC, PIC_F_IONS_FROZEN, PIC_F_MOMENTS, PIC_F_NO_GRAPH = 1, 2, 8, 16
+PIC_F_NO_MCC, PIC_F_IONS_FROZEN, PIC_F_MOMENTS, PIC_F_NO_GRAPH, PIC_F_COULOMB = 1, 2, 8, 16, 32
 COUNTERS = ("lost_bot_e", "lost_bot_i", "lost_top_e", "lost_top_i", "abs_e", "abs_i",
             "e_el", "e_exc", "e_ion", "i_el", "i_cx", "err", "pushed")
 PIC_C_N = len(COUNTERS)
@@ -62,7 +62,7 @@ class pic_run(C.Structure):
                 ("id_host", C.POINTER(C.c_uint32) * 2), ("capacity", C.c_int64 * 2), ("weight", C.c_double),
                 ("dt", C.c_double), ("md_sub", C.c_int32), ("sort_every", C.c_int32), ("seed", C.c_uint64),
                 ("run_id", C.c_uint32), ("prec", C.c_int32), ("flags", C.c_int32), ("tol", C.c_double),
-                ("max_cycles", C.c_int32)]
+                ("max_cycles", C.c_int32), ("coulomb_log", C.c_double)]
 
 
 class PicError(RuntimeError):
@@ -265,7 +265,7 @@ def pic_destroy(ctx):
 
 # ----------------------------------------------------------------- convenience
 def make_args(wl, particles, prec=PIC_MIXED, flags=0, capacity=None, sort_every=20, tol=1e-10, max_cycles=60,
-              md_sub=None):
+              md_sub=None, coulomb_log=10.0):
     """The pic_init argument structures for a workload; returns them with the
     numpy arrays they point into (keep those alive while the call runs)."""
     keep = []
@@ -295,7 +295,7 @@ def make_args(wl, particles, prec=PIC_MIXED, flags=0, capacity=None, sort_every=
     run.md_sub = wl.md_sub if md_sub is None else md_sub
     run.sort_every = sort_every
     run.seed, run.run_id, run.prec, run.flags = wl.seed, wl.run_id, prec, flags
-    run.tol, run.max_cycles = tol, max_cycles
+    run.tol, run.max_cycles, run.coulomb_log = tol, max_cycles, coulomb_log
     return (mesh, el, gas, grains, run), keep
 
 
@@ -330,7 +330,7 @@ class Run:
     and initial particles [(x, v, id) for electrons, ions] in SI units."""
 
     def __init__(self, wl, particles, prec=PIC_MIXED, flags=0, stream=None, capacity=None, sort_every=20,
-                 tol=1e-10, max_cycles=60, md_sub=None):
+                 tol=1e-10, max_cycles=60, md_sub=None, coulomb_log=10.0):
         keep = []
         mesh = pic_mesh(wl.nx, wl.ny, wl.nz, wl.dx)
         el = pic_electrodes(wl.v_dc, wl.v_rf, wl.f_rf, wl.phase, wl.v_top)
@@ -359,7 +359,7 @@ class Run:
         run.md_sub = wl.md_sub if md_sub is None else md_sub
         run.sort_every = sort_every
         run.seed, run.run_id, run.prec, run.flags = wl.seed, wl.run_id, prec, flags
-        run.tol, run.max_cycles = tol, max_cycles
+        run.tol, run.max_cycles, run.coulomb_log = tol, max_cycles, coulomb_log
         self.ctx = pic_init(mesh, el, gas, grains, run, stream)
         self.wl = wl
         self.nodes = wl.nx * wl.ny * (wl.nz + 1)

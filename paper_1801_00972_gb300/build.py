@@ -1,7 +1,8 @@
 """Build libpic.so (the C-ABI library) in-tree with nvcc for sm_103a.
 
-Each translation unit compiles in parallel; the FP64 particle unit is built
-with --fmad=false so that its arithmetic rounds exactly as written.
+Each translation unit compiles in parallel; the FP64 particle unit
+and the Coulomb-collision unit are built with --fmad=false so that their
+arithmetic rounds exactly as written.
 """
 from __future__ import annotations
 
@@ -23,6 +24,7 @@ UNITS = {
     "particles_mixed.cu": [],
     "sort.cu": [],
     "poisson.cu": [],
+    "coulomb.cu": ["--fmad=false"],
 }
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",

@@ -209,6 +209,8 @@ pic_status pic_init(const pic_mesh* mesh, const pic_electrodes* el, const pic_ga
         (run->prec != PIC_FP64 && run->prec != PIC_MIXED) || !(run->tol > 0.0) || run->max_cycles < 1)
         return fail(nullptr, PIC_EINVAL, "run: need dt > 0, weight >= 0, md_sub >= 1, sort_every >= 0, prec 0/1, "
                                          "tol > 0, max_cycles >= 1");
+    if ((run->flags & PIC_F_COULOMB) && !(run->coulomb_log > 0.0 && run->coulomb_log < 1e3))
+        return fail(nullptr, PIC_EINVAL, "run: PIC_F_COULOMB needs a Coulomb logarithm in (0, 1000)");
     if (run->prec == PIC_MIXED && (nx > 1024 || ny > 1024 || nz > 2047))
         return fail(nullptr, PIC_EINVAL, "mesh: mixed precision packs the cell as i | j << 10 | k << 20, so nx, ny "
                                          "<= 1024 and nz <= 2047");
@@ -267,6 +269,7 @@ pic_status pic_init(const pic_mesh* mesh, const pic_electrodes* el, const pic_ga
     c->n_xs = gas->n_xs;
     c->ng = grains->n;
     c->prec = run->prec; c->flags = run->flags; c->md_sub = run->md_sub; c->sort_every = run->sort_every;
+    c->coul_log = run->coulomb_log;
     c->max_cycles = run->max_cycles;
     c->W = run->weight; c->dt = run->dt; c->tol = run->tol;
     c->seed = run->seed; c->run_id = run->run_id;
@@ -343,6 +346,14 @@ pic_status pic_init(const pic_mesh* mesh, const pic_electrodes* el, const pic_ga
     c->cell_ng = (int*)dev_alloc(c, sizeof(int) * cells);
     c->cell_g = (int*)dev_alloc(c, sizeof(int) * cells * kMaxG);
     c->cursor = (unsigned int*)dev_alloc(c, sizeof(unsigned int) * (cells + 1));
+    if (c->flags & PIC_F_COULOMB)
+        for (int sp = 0; sp < 2; ++sp) {
+            c->cs_end[sp] = (unsigned int*)dev_alloc(c, sizeof(unsigned int) * (cells + 1));
+            c->cs_idx[sp] = (unsigned int*)dev_alloc(c, sizeof(unsigned int) * (size_t)std::max<int64_t>(c->cap[sp], 1));
+            c->cs_key[sp] =
+                (unsigned long long*)dev_alloc(c, sizeof(unsigned long long) * (size_t)std::max<int64_t>(c->cap[sp], 1));
+            ok = ok && c->cs_end[sp] && c->cs_idx[sp] && c->cs_key[sp];
+        }
     if (c->flags & PIC_F_MOMENTS) {
         c->mom[0] = (double*)dev_alloc(c, sizeof(double) * 4 * nodes);
         c->mom[1] = (double*)dev_alloc(c, sizeof(double) * 4 * nodes);
@@ -527,6 +538,7 @@ pic_status pic_advance(pic_ctx* c)
     prof_end(c, ev, true);
     if (mixed) launch_children32(c);
     else launch_children64(c);
+    if (c->flags & PIC_F_COULOMB) launch_coulomb(c);
     launch_grains(c);
     c->step += 1;
     if (c->sort_every > 0 && c->step % c->sort_every == 0) {
@@ -660,6 +672,7 @@ pic_status ensure_graphs(pic_ctx* c, bool sort)
         c->g_post[p][so] = capture(c, &c->n_post[so], [&] {
             if (mixed) launch_children32(c);
             else launch_children64(c);
+            if (c->flags & PIC_F_COULOMB) launch_coulomb(c);
             launch_grains(c);
             if (sort) {
                 sort_particles(c, 0);

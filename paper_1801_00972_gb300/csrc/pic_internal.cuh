@@ -199,6 +199,12 @@ struct pic_ctx {
     int* cell_ng = nullptr;                  // cells
     int* cell_g = nullptr;                   // cells * 8
 
+    // Coulomb collisions (PIC_F_COULOMB): per species, cell groups of slot indices
+    double coul_log = 0.0;
+    unsigned int* cs_end[2] = {nullptr, nullptr};        // cells: end of each cell's group
+    unsigned int* cs_idx[2] = {nullptr, nullptr};        // capacity: slots grouped by cell
+    unsigned long long* cs_key[2] = {nullptr, nullptr};  // capacity: pairing keys
+
     // sort scratch
     unsigned int* hist = nullptr;            // cells + 1
     unsigned int* cursor = nullptr;          // cells
@@ -278,6 +284,10 @@ void launch_moments_phi(pic_ctx* c);
 
 // sort.cu
 void sort_particles(pic_ctx* c, int sp);
+void scan_cells(pic_ctx* c, unsigned int* data);   // exclusive scan of one value per cell, in place
+
+// coulomb.cu (built without fused multiply-add)
+void launch_coulomb(pic_ctx* c);                    // binary Coulomb collisions of the step's particles
 size_t sort_scratch_setup(pic_ctx* c);
 
 // poisson.cu

@@ -132,6 +132,8 @@ void scan(pic_ctx* c, unsigned int* data, size_t n, int level)
 
 }  // namespace
 
+void scan_cells(pic_ctx* c, unsigned int* data) { scan(c, data, c->cells, 0); }
+
 // scratch: one block-sum buffer per scan level, plus a final total slot
 size_t sort_scratch_setup(pic_ctx* c)
 {

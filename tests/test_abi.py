@@ -62,7 +62,7 @@ def _args(wl, n=10):
 
 
 @pytest.mark.parametrize("bad", ["nx_odd", "dx", "dt", "tol", "capacity", "grain_at_electrode", "particle_out",
-                                 "xs_nan", "prec"])
+                                 "xs_nan", "prec", "coulomb_log"])
 def test_invalid_arguments_rejected(lib, bad):
     wl = I.small(n_e=10, n_i=10)
     mesh, el, gas, grains, run, keep = _args(wl)
@@ -85,6 +85,9 @@ def test_invalid_arguments_rejected(lib, bad):
         keep[0][0, 3] = np.nan
     elif bad == "prec":
         run.prec = 7
+    elif bad == "coulomb_log":
+        run.flags = P.PIC_F_COULOMB
+        run.coulomb_log = 0.0
     with pytest.raises(P.PicError) as e:
         P.pic_init(mesh, el, gas, grains, run)
     assert e.value.status == P.PIC_EINVAL

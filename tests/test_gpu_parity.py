@@ -34,8 +34,8 @@ def _stream():
 def _pair(wl, prec=P.PIC_FP64, flags=0, parts=None, **kw):
     parts = parts if parts is not None else I.sample_particles(wl)
     oflags = (O.NO_MCC if flags & P.PIC_F_NO_MCC else 0) | (O.IONS_FROZEN if flags & P.PIC_F_IONS_FROZEN else 0) \
-        | (O.MOMENTS if flags & P.PIC_F_MOMENTS else 0)
-    ref = O.Sim(wl, parts, flags=oflags)
+        | (O.MOMENTS if flags & P.PIC_F_MOMENTS else 0) | (O.COULOMB if flags & P.PIC_F_COULOMB else 0)
+    ref = O.Sim(wl, parts, flags=oflags, coulomb_log=kw.get("coulomb_log", 10.0))
     run = P.Run(wl, parts, prec=prec, flags=flags, stream=_stream(), **kw)
     return ref, run
 
@@ -257,3 +257,54 @@ def test_empty_and_conservation():
         nabs, _ = run.grains()
         assert int(run.rho().sum()) == 2 ** 42 * int(n[1] - n[0] + nabs[:, 1].sum() - nabs[:, 0].sum())
         prev, pc = n, c
+
+
+def _dense(nx=8, ny=8, nz=16, n=6000):
+    # n ~ 4e15 m^-3 keeps the Debye length near one cell; the Coulomb logarithm
+    # passed with it (200) makes the collisions change velocities visibly per step
+    wl = I.small(nx=nx, ny=ny, nz=nz, n_e=n, n_i=n, grains=1, v_dc=-30.0, dt=2e-10)
+    wl.weight = wl.weight * 4.0
+    parts = I.sample_particles(wl)
+    parts[1] = (parts[1][0], parts[1][1] * 5.0, parts[1][2])      # warmer ions: i-i collisions matter
+    return wl, parts
+
+
+def test_fp64_coulomb_bit_exact_given_phi():
+    wl, parts = _dense()
+    ref, run = _pair(wl, flags=P.PIC_F_COULOMB, parts=parts, coulomb_log=200.0)
+    run.set_gtab(ref.gtab())
+    for _ in range(4):
+        run.set_phi(ref.phi())
+        run.advance()
+        ref.advance()
+        ref.solve()
+        _same_particles(run, ref)
+        assert np.array_equal(run.rho(), ref.rho())
+        _counters_equal(run, ref)
+    # and the collisions did act: the same steps without them end elsewhere
+    ref2, run2 = _pair(wl, parts=parts)
+    run2.set_gtab(ref2.gtab())
+    for _ in range(4):
+        run2.set_phi(ref2.phi())
+        run2.advance()
+        ref2.advance()
+        ref2.solve()
+    assert not np.array_equal(run.particles(0)[1], run2.particles(0)[1])
+
+
+def test_mixed_coulomb_close_to_oracle():
+    wl, parts = _dense(nx=16, ny=16, nz=32, n=20000)
+    ref, run = _pair(wl, prec=P.PIC_MIXED, flags=P.PIC_F_COULOMB, parts=parts, coulomb_log=200.0)
+    run.set_gtab(ref.gtab())
+    run.set_phi(ref.phi())
+    run.advance()
+    ref.advance()
+    for sp in range(2):
+        xg, vg, ig = run.particles(sp)
+        xo, vo, io = ref.particles(sp)
+        common, a, b = np.intersect1d(ig, io, return_indices=True)
+        assert len(common) >= len(io) - 3
+        vscale = np.sqrt(np.mean(vo ** 2))
+        dv = np.abs(vg[a] - vo[b]).max(axis=1)
+        # float vs double: a rejection draw or a collision decision may flip on a rounding
+        assert np.mean(dv <= 1e-4 * vscale) >= 0.998, np.quantile(dv / vscale, [0.5, 0.99, 0.999])
