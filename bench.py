@@ -68,6 +68,7 @@ def args():
     ap.add_argument("--eager", action="store_true", help="no CUDA graphs (for profilers)")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="fixed sort interval (no autotuning)")
+    ap.add_argument("--no-coulomb", action="store_true", help="skip the run with Coulomb collisions")
     return ap.parse_args()
 
 
@@ -133,12 +134,12 @@ class Clocks:
                 "samples": len(sm)}
 
 
-def run_gpu(P, I, wl, parts, prec, steps, warmup, stream, gpu, flags=0, tune=True):
+def run_gpu(P, I, wl, parts, prec, steps, warmup, stream, gpu, flags=0, tune=True, sort_every=SORT_EVERY):
     import torch
-    run = P.Run(wl, parts, prec=prec, stream=stream, sort_every=SORT_EVERY, flags=flags)
+    run = P.Run(wl, parts, prec=prec, stream=stream, sort_every=sort_every, flags=flags)
     run.step(warmup)
     # sort interval autotuned on the run itself before the timed region
-    sort_every = run.tune_sort(TUNE_STEPS) if tune else SORT_EVERY
+    sort_every = run.tune_sort(TUNE_STEPS) if tune else sort_every
     _, c0 = run.counts()
     run.profile(1)
     k0 = run.profile_read()["kernels"]
@@ -329,6 +330,11 @@ def main():
         fp64 = run_gpu(P, I, wl, parts, P.PIC_FP64, a.fp64_steps or max(a.steps // 4, 10), a.warmup, stream, local,
                        flags, tune=False)
     ee = None if a.no_e2e else e2e(P, wl, parts, P.PIC_MIXED, max(a.steps // 4, 10), stream, mixed["sort_every"])
+    coul = None
+    if not a.no_coulomb:
+        # the same step with the binary Coulomb collisions of Table I switched on
+        coul = run_gpu(P, I, wl, parts, P.PIC_MIXED, max(a.steps // 4, 20), a.warmup, stream, local,
+                       flags | P.PIC_F_COULOMB, tune=False, sort_every=mixed["sort_every"])
     bb = None if (a.no_batch or world > 1) else batch_bench(P, I, max(a.steps // 4, 10), a.warmup)
 
     def agg(x):
@@ -396,6 +402,12 @@ def main():
                         "mixed_speedup": (m_tot / m_ms) / (f[1] / f[0])}
     if ee is not None:
         line["e2e"] = ee
+    if coul is not None:
+        cs = max(a.steps // 4, 20)
+        line["coulomb"] = {"value": coul["pushed"] / (coul["ms"] / 1000.0), "unit": "particle-steps/s",
+                           "steps": cs, "ms_per_step": coul["ms"] / cs,
+                           "extra_ms_per_step": coul["ms"] / cs - m_ms / a.steps,
+                           "note": "mixed, PIC_F_COULOMB (e-e, e-Ar+, Ar+-Ar+ binary collisions, lnL = 10)"}
     if bb is not None:
         line["batch"] = bb
     if not a.no_cpu:

@@ -268,13 +268,11 @@ __device__ __forceinline__ void collide(const CoulArgs& a, int sa, unsigned int 
     store_v(a, sb, qb, vb);
 }
 
-// one thread per cell: its groups in key order, then e-e, i-i and e-i collisions
+// Form for a cell with more than kCoulLocal particles of a species: the groups
+// put in key order in place in global memory.
 template <typename T>
-__global__ void k_coul_cells(const CoulArgs a)
+__device__ void cell_serial(const CoulArgs& a, int c, uint32_t step)
 {
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= a.cells) return;
-    const uint32_t step = *a.step - 1u;
     unsigned int b0[2], b1[2];
     for (int sp = 0; sp < 2; ++sp) {
         b0[sp] = c == 0 ? 0u : a.end[sp][c - 1];
@@ -301,6 +299,68 @@ __global__ void k_coul_cells(const CoulArgs a)
         const unsigned int na = big == 0 ? ne : ni, nb = big == 0 ? ni : ne;
         const unsigned int* A = a.idx[big] + b0[big];
         const unsigned int* B = a.idx[1 - big] + b0[1 - big];
+        const double dens = ((double)nb * a.w) / a.vol;
+        for (unsigned int k = 0; k < na; ++k)
+            collide(a, big, A[k], 1 - big, B[k % nb], 2, dens, false, step, kPurCoulEI, tag);
+    }
+}
+
+// One thread per cell.  A group of at most kCoulLocal particles is put in key
+// order in a local array (insertion sort on cached memory) and collided from
+// there; a larger cell takes the serial form above, in place.
+constexpr int kCoulLocal = 32;
+
+template <typename T>
+__global__ void __launch_bounds__(128) k_coul_cells(const CoulArgs a)
+{
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= a.cells) return;
+    const uint32_t step = *a.step - 1u;
+    unsigned int b0[2], n[2];
+    for (int sp = 0; sp < 2; ++sp) {
+        b0[sp] = c == 0 ? 0u : a.end[sp][c - 1];
+        n[sp] = a.end[sp][c] - b0[sp];
+    }
+    if (n[0] + n[1] < 2) return;
+    if (n[0] > kCoulLocal || n[1] > kCoulLocal) {
+        cell_serial<T>(a, c, step);
+        return;
+    }
+    unsigned int list[2][kCoulLocal];
+    for (int sp = 0; sp < 2; ++sp) {
+        unsigned long long key[kCoulLocal];
+        for (unsigned int i = 0; i < n[sp]; ++i) {
+            const unsigned long long k = a.key[sp][b0[sp] + i];
+            const unsigned int q = a.idx[sp][b0[sp] + i];
+            unsigned int j = i;
+            while (j > 0 && key[j - 1] > k) {
+                key[j] = key[j - 1];
+                list[sp][j] = list[sp][j - 1];
+                --j;
+            }
+            key[j] = k;
+            list[sp][j] = q;
+        }
+    }
+    T* tag = nullptr;
+    for (int sp = 0; sp < 2; ++sp) {
+        const unsigned int m = n[sp];
+        if (m < 2) continue;
+        const unsigned int* L = list[sp];
+        const double dens = ((double)m * a.w) / a.vol;
+        const uint32_t pur = sp == 0 ? kPurCoulEE : kPurCoulII;
+        unsigned int j = 0;
+        if (m % 2 == 1) {
+            for (int t = 0; t < 3; ++t) collide(a, sp, L[t], sp, L[(t + 1) % 3], sp, dens, true, step, pur, tag);
+            j = 3;
+        }
+        for (; j + 1 < m; j += 2) collide(a, sp, L[j], sp, L[j + 1], sp, dens, false, step, pur, tag);
+    }
+    if (n[0] > 0 && n[1] > 0) {
+        const int big = n[0] >= n[1] ? 0 : 1;
+        const unsigned int na = n[big], nb = n[1 - big];
+        const unsigned int* A = list[big];
+        const unsigned int* B = list[1 - big];
         const double dens = ((double)nb * a.w) / a.vol;
         for (unsigned int k = 0; k < na; ++k)
             collide(a, big, A[k], 1 - big, B[k % nb], 2, dens, false, step, kPurCoulEI, tag);
