@@ -123,6 +123,8 @@ typedef struct {
     double tol;                   /* Poisson relative residual tolerance (e.g. 1e-10) */
     int32_t max_cycles;           /* Poisson refinement iterations per solve */
     double coulomb_log;           /* Coulomb logarithm lnL (> 0 with PIC_F_COULOMB) */
+    int32_t eepf_bins;            /* > 0: accumulate the electron energy histogram of pic_eepf */
+    double eepf_de_ev;            /* its bin width (eV) */
 } pic_run;
 
 /* Create a run: copies every input to the device, deposits rho_0 (particles
@@ -178,6 +180,28 @@ pic_status pic_grain_charges(pic_ctx* ctx, int64_t* n_abs_host, double* q_host);
 #define PIC_C_PUSHED    12   /* live particles processed by the push kernels */
 #define PIC_C_N         13
 pic_status pic_counts(pic_ctx* ctx, int64_t* n_live_host /* 2 */, int64_t* counters_host /* PIC_C_N */);
+
+/* Electron energy histogram for the EEPF (Sec. IV.A, Fig. 3), accumulated
+ * every step after the collisions when run->eepf_bins > 0: counts[k][b] is the
+ * number of electron super-particles in cell plane k (z from k dx to (k+1) dx)
+ * with energy eps = (m_e/2)|v|^2/e in [b de, (b+1) de) eV, b < eepf_bins, and
+ * column eepf_bins counts the energies beyond, summed over the steps since
+ * pic_init or the last reset.  len = nz * (eepf_bins + 1); *steps (may be NULL)
+ * receives the number of steps summed.  reset != 0 clears after reading.
+ * The EEPF of a slab is g(eps) = sum_k counts[k][b] W / (V de sqrt(eps)) at
+ * the bin centres (V the slab volume, W the weight).
+ * PIC_EINVAL for a wrong len or when the histogram is off. */
+pic_status pic_eepf(pic_ctx* ctx, int64_t* counts, size_t len, int64_t* steps, int32_t reset);
+
+/* Two-Maxwellian fit of an EEPF histogram (one slab, nbins counts without the
+ * overflow column): g(eps) = A_l exp(-eps/T_l) + A_h exp(-eps/T_h) over the bin
+ * centres in [e_lo_ev, e_hi_ev], g_b = counts_b / (de sqrt(eps_b)), as the
+ * paper fits its bulk EEPF (Sec. IV.A: T_l = 0.31 eV, T_h = 2.32 eV there).
+ * fit[4] receives T_l, T_h (eV), A_l, A_h; a single temperature gives T_l =
+ * T_h and A_l = 0.  Host only, touches no GPU.  PIC_EINVAL for bad arguments
+ * or fewer than 4 non-empty bins in range. */
+pic_status pic_eepf_fit(const int64_t* counts, int32_t nbins, double de_ev, double e_lo_ev, double e_hi_ev,
+                        double* fit);
 
 /* Window averages since the last reset (needs PIC_F_MOMENTS):
  * what 0 phi (V, nodes), 1 n_e, 2 n_i (m^-3, nodes), 3 flux_e, 4 flux_i

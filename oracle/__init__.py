@@ -27,6 +27,7 @@ NO_MCC = 1
 IONS_FROZEN = 2
 MOMENTS = 8
 COULOMB = 32
+EEPF = 64
 
 # counter slots of orc_get_counters
 C_NAMES = ("lost_bot_e", "lost_bot_i", "lost_top_e", "lost_top_i", "abs_e", "abs_i",
@@ -66,6 +67,8 @@ class Cfg(C.Structure):
         ("v_init", C.POINTER(C.c_double) * 2),
         ("id_init", C.POINTER(C.c_uint32) * 2),
         ("coulomb_log", C.c_double),
+        ("eepf_bins", C.c_int32),
+        ("eepf_de_ev", C.c_double),
     ]
 
 
@@ -85,6 +88,8 @@ def lib():
                 getattr(L, f).restype = i32
             L.orc_coulomb.argtypes = [vp]
             L.orc_coulomb.restype = None
+            L.orc_get_eepf.argtypes = [vp, pi64]
+            L.orc_get_eepf.restype = i64
             L.orc_count.argtypes = [vp, i32]; L.orc_count.restype = i64
             L.orc_get_particles.argtypes = [vp, i32, pd, pd, pu32]
             L.orc_get_rho.argtypes = [vp, pi64]
@@ -165,7 +170,8 @@ class Sim:
     ``paper_1801_00972_gb300.inputs.Workload`` (duck-typed; this module does not
     import the package)."""
 
-    def __init__(self, wl, particles, flags: int = 0, md_sub: int | None = None, coulomb_log: float = 10.0):
+    def __init__(self, wl, particles, flags: int = 0, md_sub: int | None = None, coulomb_log: float = 10.0,
+                 eepf_bins: int = 0, eepf_de_ev: float = 0.0):
         L = lib()
         self._keep = []
         cfg = Cfg()
@@ -187,6 +193,8 @@ class Sim:
         cfg.grad = _p(r, C.c_double) if r.size else None
         cfg.seed, cfg.run_id, cfg.flags = wl.seed, wl.run_id, flags
         cfg.coulomb_log = coulomb_log
+        cfg.eepf_bins, cfg.eepf_de_ev = eepf_bins, eepf_de_ev
+        self.eepf_bins = eepf_bins
         self._keep += [xs, g, r]
         for sp in range(2):
             x, v, ids = particles[sp]
@@ -217,6 +225,12 @@ class Sim:
 
     def solve(self):
         assert lib().orc_solve(self.h) == 0
+
+    def eepf(self):
+        """(counts per (cell plane, energy bin) summed over the steps, number of steps)."""
+        out = np.zeros(self.wl.nz * (self.eepf_bins + 1), np.int64)
+        n = lib().orc_get_eepf(self.h, _p(out, C.c_int64))
+        return out.reshape(self.wl.nz, self.eepf_bins + 1), int(n)
 
     def coulomb(self):
         """One Coulomb collision pass on the current particles (as at the end of a step)."""

@@ -321,6 +321,8 @@ struct orc_sim {
     double* mom[2];                /* [node][4]: count, count*vx, count*vy, count*vz */
     double* mphi;
     int64_t msteps;
+    int64_t* eepf;                 /* [k][bin] electron counts */
+    int64_t eepf_steps;
 };
 
 static size_t nodes_of(const orc_sim* s) { return (size_t)s->c.nx * s->c.ny * (s->c.nz + 1); }
@@ -788,6 +790,34 @@ void orc_coulomb(orc_sim* s)
     for (int sp = 0; sp < 2; ++sp) { free(ent[sp]); free(start[sp]); }
 }
 
+/* Electron energy histogram (for the EEPF of Sec. IV.A): after a step's
+ * collisions, each electron adds one count to (its cell plane k, bin
+ * floor(eps / de)), eps = (m_e/2) |v|^2 / e in eV; energies beyond the last bin
+ * go to an overflow bin. */
+static void eepf_accumulate(orc_sim* s)
+{
+    const int nb = s->c.eepf_bins;
+    const double de = s->c.eepf_de_ev;
+    for (int64_t q = 0; q < s->n[0]; ++q) {
+        const double* v = s->v[0] + 3 * q;
+        int c[3]; double f[3];
+        locate(s, s->x[0] + 3 * q, c, f);
+        const double v2 = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
+        const double eps = v2 * s->hm[0];
+        const double t = eps / de;
+        const int b = t < (double)nb ? (int)t : nb;
+        s->eepf[(size_t)c[2] * (size_t)(nb + 1) + (size_t)b]++;
+    }
+    s->eepf_steps++;
+}
+
+int64_t orc_get_eepf(const orc_sim* s, int64_t* counts)
+{
+    if (!s->eepf) return 0;
+    memcpy(counts, s->eepf, sizeof(int64_t) * (size_t)s->c.nz * (size_t)(s->c.eepf_bins + 1));
+    return s->eepf_steps;
+}
+
 int orc_advance(orc_sim* s)
 {
     const size_t N = nodes_of(s);
@@ -865,6 +895,7 @@ int orc_advance(orc_sim* s)
     }
     s->next_id += (uint32_t)(2 * s->nch);
     if (s->c.flags & ORC_COULOMB) orc_coulomb(s);
+    if ((s->c.flags & ORC_EEPF) && s->eepf) eepf_accumulate(s);
     deposit_all(s);
     s->step++;
     (void)N;
@@ -902,6 +933,8 @@ orc_sim* orc_create(const orc_cfg* cfg)
     s->mom[0] = (double*)calloc(4 * N, sizeof(double));
     s->mom[1] = (double*)calloc(4 * N, sizeof(double));
     s->mphi = (double*)calloc(N, sizeof(double));
+    if ((cfg->flags & ORC_EEPF) && cfg->eepf_bins > 0 && cfg->eepf_de_ev > 0.0)
+        s->eepf = (int64_t*)calloc((size_t)cfg->nz * (size_t)(cfg->eepf_bins + 1), sizeof(int64_t));
     if (cfg->n_xs > 0) {
         s->xs = (double*)malloc(sizeof(double) * 5 * cfg->n_xs);
         memcpy(s->xs, cfg->xs, sizeof(double) * 5 * cfg->n_xs);
@@ -980,7 +1013,7 @@ void orc_destroy(orc_sim* s)
     for (int sp = 0; sp < 2; ++sp) { free(s->x[sp]); free(s->v[sp]); free(s->id[sp]); free(s->mom[sp]); }
     free(s->rq); free(s->phi); free(s->ex); free(s->ey); free(s->ez); free(s->xs);
     free(s->gpos); free(s->grad); free(s->gq); free(s->gabs); free(s->gtab);
-    free(s->cell_ng); free(s->cell_g); free(s->ch); free(s->mphi);
+    free(s->cell_ng); free(s->cell_g); free(s->ch); free(s->mphi); free(s->eepf);
     free(s);
 }
 

@@ -24,6 +24,7 @@ extern "C" {
 #define ORC_IONS_FROZEN 2   /* ions neither move nor collide (test-only)       */
 #define ORC_MOMENTS     8   /* accumulate node moments every step              */
 #define ORC_COULOMB    32   /* binary Coulomb collisions e-e, i-i, e-i (Table I) */
+#define ORC_EEPF       64   /* electron energy histogram per cell plane, every step */
 
 typedef struct {
     int32_t nx, ny, nz, md_sub;      /* cells; MD subcycles per step (Sec. III: 40) */
@@ -45,6 +46,8 @@ typedef struct {
     const double*   v_init[2];       /* 3*n per species */
     const uint32_t* id_init[2];      /* n per species */
     double   coulomb_log;            /* Coulomb logarithm of the binary collisions (ORC_COULOMB) */
+    int32_t  eepf_bins;              /* ORC_EEPF: energy bins of width eepf_de_ev, plus one overflow bin */
+    double   eepf_de_ev;
 } orc_cfg;
 
 typedef struct orc_sim orc_sim;
@@ -60,6 +63,9 @@ int      orc_advance(orc_sim* s);                   /* particles, grains, childr
 int      orc_solve(orc_sim* s);                     /* phi from rho at t = step*dt */
 int      orc_step(orc_sim* s);                      /* advance + solve */
 void     orc_coulomb(orc_sim* s);                   /* one Coulomb collision pass at the current step */
+/* electron counts per (cell plane k, energy bin), nz * (eepf_bins + 1), summed over the steps since
+ * creation; returns the number of steps summed */
+int64_t  orc_get_eepf(const orc_sim* s, int64_t* counts);
 
 int64_t  orc_count(const orc_sim* s, int sp);
 void     orc_get_particles(const orc_sim* s, int sp, double* x, double* v, uint32_t* id);

@@ -32,7 +32,7 @@ PIC_C_N = len(COUNTERS)
 
 # every symbol include/pic.h declares
 SYMBOLS = ("pic_init", "pic_step", "pic_tune_sort", "pic_advance", "pic_solve", "pic_grain_charges", "pic_counts",
-           "pic_moments", "pic_get_particles", "pic_get_rho", "pic_get_phi", "pic_set_phi",
+           "pic_moments", "pic_eepf", "pic_eepf_fit", "pic_get_particles", "pic_get_rho", "pic_get_phi", "pic_set_phi",
            "pic_get_grain_table", "pic_set_grain_table", "pic_set_grain_counts", "pic_step_index",
            "pic_profile", "pic_profile_read", "pic_solve_noalloc", "pic_batch_init", "pic_batch_step",
            "pic_batch_run", "pic_batch_destroy", "pic_last_error", "pic_destroy")
@@ -62,7 +62,8 @@ class pic_run(C.Structure):
                 ("id_host", C.POINTER(C.c_uint32) * 2), ("capacity", C.c_int64 * 2), ("weight", C.c_double),
                 ("dt", C.c_double), ("md_sub", C.c_int32), ("sort_every", C.c_int32), ("seed", C.c_uint64),
                 ("run_id", C.c_uint32), ("prec", C.c_int32), ("flags", C.c_int32), ("tol", C.c_double),
-                ("max_cycles", C.c_int32), ("coulomb_log", C.c_double)]
+                ("max_cycles", C.c_int32), ("coulomb_log", C.c_double), ("eepf_bins", C.c_int32),
+                ("eepf_de_ev", C.c_double)]
 
 
 class PicError(RuntimeError):
@@ -90,6 +91,7 @@ def load(path: str | None = None):
             "pic_step": [vp, i32], "pic_tune_sort": [vp, i32, C.POINTER(i32)], "pic_advance": [vp], "pic_solve": [vp, C.POINTER(i32), pd],
             "pic_grain_charges": [vp, pi64, pd], "pic_counts": [vp, pi64, pi64],
             "pic_moments": [vp, i32, pd, sz, i32],
+            "pic_eepf": [vp, pi64, sz, pi64, i32], "pic_eepf_fit": [pi64, i32, C.c_double, C.c_double, C.c_double, pd],
             "pic_get_particles": [vp, i32, pd, pd, pu32, i64, pi64],
             "pic_get_rho": [vp, pi64, sz], "pic_get_phi": [vp, pd, sz], "pic_set_phi": [vp, pd, sz],
             "pic_get_grain_table": [vp, pd, sz], "pic_set_grain_table": [vp, pd, sz],
@@ -175,6 +177,24 @@ def pic_counts(ctx):
     c = np.zeros(PIC_C_N, np.int64)
     _check(ctx, load().pic_counts(ctx, _p(n, C.c_int64), _p(c, C.c_int64)))
     return n, dict(zip(COUNTERS, (int(x) for x in c)))
+
+
+def pic_eepf(ctx, nz, bins, reset=False):
+    """(counts[nz][bins + 1] summed over the steps, number of steps)."""
+    out = np.zeros(nz * (bins + 1), np.int64)
+    steps = C.c_int64()
+    _check(ctx, load().pic_eepf(ctx, _p(out, C.c_int64), out.size, C.byref(steps), int(bool(reset))))
+    return out.reshape(nz, bins + 1), steps.value
+
+
+def pic_eepf_fit(counts, de_ev, e_lo_ev, e_hi_ev):
+    """Two-Maxwellian fit of one slab's histogram (bins without the overflow
+    column): (T_l, T_h, A_l, A_h)."""
+    c = np.ascontiguousarray(counts, dtype=np.int64)
+    out = np.zeros(4)
+    _check(None, load().pic_eepf_fit(_p(c, C.c_int64), int(c.size), float(de_ev), float(e_lo_ev), float(e_hi_ev),
+                                     _p(out, C.c_double)))
+    return tuple(float(x) for x in out)
 
 
 def pic_moments(ctx, what, nodes, reset=False):
@@ -265,7 +285,7 @@ def pic_destroy(ctx):
 
 # ----------------------------------------------------------------- convenience
 def make_args(wl, particles, prec=PIC_MIXED, flags=0, capacity=None, sort_every=20, tol=1e-10, max_cycles=60,
-              md_sub=None, coulomb_log=10.0):
+              md_sub=None, coulomb_log=10.0, eepf_bins=0, eepf_de_ev=0.0):
     """The pic_init argument structures for a workload; returns them with the
     numpy arrays they point into (keep those alive while the call runs)."""
     keep = []
@@ -296,6 +316,7 @@ def make_args(wl, particles, prec=PIC_MIXED, flags=0, capacity=None, sort_every=
     run.sort_every = sort_every
     run.seed, run.run_id, run.prec, run.flags = wl.seed, wl.run_id, prec, flags
     run.tol, run.max_cycles, run.coulomb_log = tol, max_cycles, coulomb_log
+    run.eepf_bins, run.eepf_de_ev = eepf_bins, eepf_de_ev
     return (mesh, el, gas, grains, run), keep
 
 
@@ -330,7 +351,7 @@ class Run:
     and initial particles [(x, v, id) for electrons, ions] in SI units."""
 
     def __init__(self, wl, particles, prec=PIC_MIXED, flags=0, stream=None, capacity=None, sort_every=20,
-                 tol=1e-10, max_cycles=60, md_sub=None, coulomb_log=10.0):
+                 tol=1e-10, max_cycles=60, md_sub=None, coulomb_log=10.0, eepf_bins=0, eepf_de_ev=0.0):
         keep = []
         mesh = pic_mesh(wl.nx, wl.ny, wl.nz, wl.dx)
         el = pic_electrodes(wl.v_dc, wl.v_rf, wl.f_rf, wl.phase, wl.v_top)
@@ -360,6 +381,8 @@ class Run:
         run.sort_every = sort_every
         run.seed, run.run_id, run.prec, run.flags = wl.seed, wl.run_id, prec, flags
         run.tol, run.max_cycles, run.coulomb_log = tol, max_cycles, coulomb_log
+        run.eepf_bins, run.eepf_de_ev = eepf_bins, eepf_de_ev
+        self.eepf_bins = eepf_bins
         self.ctx = pic_init(mesh, el, gas, grains, run, stream)
         self.wl = wl
         self.nodes = wl.nx * wl.ny * (wl.nz + 1)
@@ -418,6 +441,9 @@ class Run:
 
     def moments(self, what, reset=False):
         return pic_moments(self.ctx, what, self.nodes, reset)
+
+    def eepf(self, reset=False):
+        return pic_eepf(self.ctx, self.wl.nz, self.eepf_bins, reset)
 
     def profile(self, enable):
         pic_profile(self.ctx, enable)

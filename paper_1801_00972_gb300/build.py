@@ -1,7 +1,7 @@
 """Build libpic.so (the C-ABI library) in-tree with nvcc for sm_103a.
 
-Each translation unit compiles in parallel; the FP64 particle unit
-and the Coulomb-collision unit are built with --fmad=false so that their
+Each translation unit compiles in parallel; the FP64 particle unit, the
+Coulomb-collision unit and the diagnostics unit are built with --fmad=false so that their
 arithmetic rounds exactly as written.
 """
 from __future__ import annotations
@@ -25,6 +25,7 @@ UNITS = {
     "sort.cu": [],
     "poisson.cu": [],
     "coulomb.cu": ["--fmad=false"],
+    "diagnostics.cu": ["--fmad=false"],
 }
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",

@@ -209,6 +209,8 @@ pic_status pic_init(const pic_mesh* mesh, const pic_electrodes* el, const pic_ga
         (run->prec != PIC_FP64 && run->prec != PIC_MIXED) || !(run->tol > 0.0) || run->max_cycles < 1)
         return fail(nullptr, PIC_EINVAL, "run: need dt > 0, weight >= 0, md_sub >= 1, sort_every >= 0, prec 0/1, "
                                          "tol > 0, max_cycles >= 1");
+    if (run->eepf_bins < 0 || run->eepf_bins > 65536 || (run->eepf_bins > 0 && !(run->eepf_de_ev > 0.0)))
+        return fail(nullptr, PIC_EINVAL, "run: eepf_bins in [0, 65536] and eepf_de_ev > 0 when bins > 0");
     if ((run->flags & PIC_F_COULOMB) && !(run->coulomb_log > 0.0 && run->coulomb_log < 1e3))
         return fail(nullptr, PIC_EINVAL, "run: PIC_F_COULOMB needs a Coulomb logarithm in (0, 1000)");
     if (run->prec == PIC_MIXED && (nx > 1024 || ny > 1024 || nz > 2047))
@@ -270,6 +272,8 @@ pic_status pic_init(const pic_mesh* mesh, const pic_electrodes* el, const pic_ga
     c->ng = grains->n;
     c->prec = run->prec; c->flags = run->flags; c->md_sub = run->md_sub; c->sort_every = run->sort_every;
     c->coul_log = run->coulomb_log;
+    c->eepf_bins = run->eepf_bins;
+    c->eepf_de = run->eepf_de_ev;
     c->max_cycles = run->max_cycles;
     c->W = run->weight; c->dt = run->dt; c->tol = run->tol;
     c->seed = run->seed; c->run_id = run->run_id;
@@ -354,6 +358,11 @@ pic_status pic_init(const pic_mesh* mesh, const pic_electrodes* el, const pic_ga
                 (unsigned long long*)dev_alloc(c, sizeof(unsigned long long) * (size_t)std::max<int64_t>(c->cap[sp], 1));
             ok = ok && c->cs_end[sp] && c->cs_idx[sp] && c->cs_key[sp];
         }
+    if (c->eepf_bins > 0) {
+        c->eepf = (unsigned long long*)dev_alloc(c, sizeof(unsigned long long) * (size_t)nz * (c->eepf_bins + 1));
+        ok = ok && c->eepf;
+        if (c->eepf) cudaMemset(c->eepf, 0, sizeof(unsigned long long) * (size_t)nz * (c->eepf_bins + 1));
+    }
     if (c->flags & PIC_F_MOMENTS) {
         c->mom[0] = (double*)dev_alloc(c, sizeof(double) * 4 * nodes);
         c->mom[1] = (double*)dev_alloc(c, sizeof(double) * 4 * nodes);
@@ -539,6 +548,10 @@ pic_status pic_advance(pic_ctx* c)
     if (mixed) launch_children32(c);
     else launch_children64(c);
     if (c->flags & PIC_F_COULOMB) launch_coulomb(c);
+    if (c->eepf) {
+        launch_eepf(c);
+        c->eepf_steps += 1;
+    }
     launch_grains(c);
     c->step += 1;
     if (c->sort_every > 0 && c->step % c->sort_every == 0) {
@@ -673,6 +686,7 @@ pic_status ensure_graphs(pic_ctx* c, bool sort)
             if (mixed) launch_children32(c);
             else launch_children64(c);
             if (c->flags & PIC_F_COULOMB) launch_coulomb(c);
+            if (c->eepf) launch_eepf(c);
             launch_grains(c);
             if (sort) {
                 sort_particles(c, 0);
@@ -766,6 +780,7 @@ pic_status step_enqueue(pic_ctx* c, int32_t n_steps)
         if (e == cudaSuccess) e = cudaGraphLaunch(c->g_post[p][sort ? 1 : 0], c->stream);
         if (e != cudaSuccess) return cuda_fail(c, e, "step graph launch");
         c->launches += c->n_pre + c->n_push + c->n_post[sort ? 1 : 0];
+        if (c->eepf) c->eepf_steps += 1;
         c->step += 1;
         if (sort) {
             std::swap(c->pos[0], c->pos_alt[0]);
@@ -1103,6 +1118,22 @@ pic_status pic_profile_read(pic_ctx* c, double* push_ms, int64_t* push_launches,
     if (solves) *solves = (int64_t)c->ev_solve.size();
     if (solve_iterations) *solve_iterations = (int64_t)(tot - c->prof_iter0);
     if (kernels_launched) *kernels_launched = c->launches + (int64_t)tot * c->n_solve_body;
+    return PIC_OK;
+}
+
+pic_status pic_eepf(pic_ctx* c, int64_t* counts, size_t len, int64_t* steps, int32_t reset)
+{
+    if (!c) return PIC_EINVAL;
+    if (!c->eepf) return fail(c, PIC_EINVAL, "the energy histogram is off (eepf_bins = 0)");
+    if (!counts || len != (size_t)c->nz * (c->eepf_bins + 1)) return fail(c, PIC_EINVAL, "eepf length");
+    pic_status k = check(c);
+    if (k != PIC_OK) return k;
+    cudaError_t e = cudaMemcpyAsync(counts, c->eepf, sizeof(int64_t) * len, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess && reset) e = cudaMemsetAsync(c->eepf, 0, sizeof(int64_t) * len, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "eepf copy");
+    if (steps) *steps = c->eepf_steps;
+    if (reset) c->eepf_steps = 0;
     return PIC_OK;
 }
 

@@ -205,6 +205,12 @@ struct pic_ctx {
     unsigned int* cs_idx[2] = {nullptr, nullptr};        // capacity: slots grouped by cell
     unsigned long long* cs_key[2] = {nullptr, nullptr};  // capacity: pairing keys
 
+    // electron energy histogram (eepf_bins > 0): [k][bin], bins of eepf_de eV plus overflow
+    unsigned long long* eepf = nullptr;
+    int eepf_bins = 0;
+    double eepf_de = 0.0;
+    int64_t eepf_steps = 0;
+
     // sort scratch
     unsigned int* hist = nullptr;            // cells + 1
     unsigned int* cursor = nullptr;          // cells
@@ -285,6 +291,9 @@ void launch_moments_phi(pic_ctx* c);
 // sort.cu
 void sort_particles(pic_ctx* c, int sp);
 void scan_cells(pic_ctx* c, unsigned int* data);   // exclusive scan of one value per cell, in place
+
+// diagnostics.cu (built without fused multiply-add)
+void launch_eepf(pic_ctx* c);                       // add this step's electrons to the energy histogram
 
 // coulomb.cu (built without fused multiply-add)
 void launch_coulomb(pic_ctx* c);                    // binary Coulomb collisions of the step's particles

@@ -308,3 +308,31 @@ def test_mixed_coulomb_close_to_oracle():
         dv = np.abs(vg[a] - vo[b]).max(axis=1)
         # float vs double: a rejection draw or a collision decision may flip on a rounding
         assert np.mean(dv <= 1e-4 * vscale) >= 0.998, np.quantile(dv / vscale, [0.5, 0.99, 0.999])
+
+
+@pytest.mark.parametrize("prec", [P.PIC_FP64, P.PIC_MIXED])
+def test_eepf_histogram_matches_oracle(prec):
+    wl = I.small(nx=8, ny=8, nz=16, n_e=6000, n_i=6000, grains=1, v_dc=-40.0, dt=2e-10)
+    parts = I.sample_particles(wl)
+    bins, de = 100, 0.2
+    ref = O.Sim(wl, parts, flags=O.EEPF, eepf_bins=bins, eepf_de_ev=de)
+    run = P.Run(wl, parts, prec=prec, stream=_stream(), eepf_bins=bins, eepf_de_ev=de)
+    run.set_gtab(ref.gtab())
+    for _ in range(3):
+        run.set_phi(ref.phi())
+        run.advance()
+        ref.advance()
+        ref.solve()
+    hg, sg = run.eepf()
+    ho, so = ref.eepf()
+    assert sg == so == 3
+    if prec == P.PIC_FP64:
+        assert np.array_equal(hg, ho)
+    else:
+        # float energies may fall into the neighbouring bin; totals per plane agree
+        assert abs(int(hg.sum()) - int(ho.sum())) <= 9
+        assert np.abs(hg - ho).sum() <= 0.01 * ho.sum()
+    hr, _ = run.eepf(reset=True)
+    assert np.array_equal(hr, hg)
+    h0, s0 = run.eepf()
+    assert s0 == 0 and h0.sum() == 0
