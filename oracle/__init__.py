@@ -69,6 +69,10 @@ class Cfg(C.Structure):
         ("coulomb_log", C.c_double),
         ("eepf_bins", C.c_int32),
         ("eepf_de_ev", C.c_double),
+        ("mom_phases", C.c_int32),
+        ("fine_n", C.c_int32 * 3),
+        ("fine_h", C.c_double),
+        ("fine_origin", C.c_double * 3),
     ]
 
 
@@ -102,6 +106,8 @@ def lib():
             L.orc_step_index.argtypes = [vp]; L.orc_step_index.restype = i64
             L.orc_next_id.argtypes = [vp]; L.orc_next_id.restype = u32
             L.orc_moments.argtypes = [vp, i32, pd]; L.orc_moments.restype = i32
+            L.orc_moments_phase.argtypes = [vp, i32, i32, pd, pi64]; L.orc_moments_phase.restype = i32
+            L.orc_fine_moments.argtypes = [vp, i32, pd]; L.orc_fine_moments.restype = i32
             L.orc_reset_moments.argtypes = [vp]
             L.orc_field_at.argtypes = [vp, pd, pd]; L.orc_field_at.restype = i32
             L.orc_set_grain_counts.argtypes = [vp, pi64]
@@ -171,7 +177,8 @@ class Sim:
     import the package)."""
 
     def __init__(self, wl, particles, flags: int = 0, md_sub: int | None = None, coulomb_log: float = 10.0,
-                 eepf_bins: int = 0, eepf_de_ev: float = 0.0):
+                 eepf_bins: int = 0, eepf_de_ev: float = 0.0, mom_phases: int = 0, fine_n=(0, 0, 0),
+                 fine_h: float = 0.0, fine_origin=(0.0, 0.0, 0.0)):
         L = lib()
         self._keep = []
         cfg = Cfg()
@@ -195,6 +202,11 @@ class Sim:
         cfg.coulomb_log = coulomb_log
         cfg.eepf_bins, cfg.eepf_de_ev = eepf_bins, eepf_de_ev
         self.eepf_bins = eepf_bins
+        cfg.mom_phases = mom_phases
+        for a in range(3):
+            cfg.fine_n[a], cfg.fine_origin[a] = int(fine_n[a]), float(fine_origin[a])
+        cfg.fine_h = fine_h
+        self.fine_n = tuple(int(n) for n in fine_n)
         self._keep += [xs, g, r]
         for sp in range(2):
             x, v, ids = particles[sp]
@@ -312,6 +324,21 @@ class Sim:
         a = np.ascontiguousarray(n_abs, dtype=np.int64).reshape(-1)
         assert a.size == 2 * self.ng
         lib().orc_set_grain_counts(self.h, _p(a, C.c_int64))
+
+    def moments_phase(self, what: int, bin: int):
+        """(window average of rf phase bin ``bin``, samples in that bin)."""
+        n = self.nodes * (3 if what >= 3 else 1)
+        a = np.zeros(n)
+        st = C.c_int64(0)
+        assert lib().orc_moments_phase(self.h, what, bin, _p(a, C.c_double), C.byref(st)) == 0
+        return a, st.value
+
+    def fine_moments(self, what: int):
+        """Fine-grid window average, what 1 n_e, 2 n_i (nz, ny, nx), 3/4 fluxes (nz, ny, nx, 3)."""
+        nx, ny, nz = self.fine_n
+        a = np.zeros(nx * ny * nz * (3 if what >= 3 else 1))
+        assert lib().orc_fine_moments(self.h, what, _p(a, C.c_double)) == 0
+        return a.reshape((nz, ny, nx, 3) if what >= 3 else (nz, ny, nx))
 
     def reset_moments(self):
         lib().orc_reset_moments(self.h)

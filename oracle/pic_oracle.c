@@ -318,9 +318,13 @@ struct orc_sim {
     uint32_t next_id;
     int64_t cnt[ORC_C_N];
     child_rec* ch; int64_t nch, capch;
-    double* mom[2];                /* [node][4]: count, count*vx, count*vy, count*vz */
-    double* mphi;
+    double* mom[2];                /* [phase bin][node][4]: count, count*vx, count*vy, count*vz */
+    double* mphi;                  /* [phase bin][node] */
     int64_t msteps;
+    int64_t* bsteps;               /* samples per phase bin */
+    int nph;                       /* phase bins (1 without phase resolution) */
+    double* fine[2];               /* [fine cell][4]: count, sum vx, sum vy, sum vz */
+    size_t nfine;
     int64_t* eepf;                 /* [k][bin] electron counts */
     int64_t eepf_steps;
 };
@@ -614,9 +618,44 @@ int orc_solve(orc_sim* s)
     return rc;
 }
 
+/* rf phase bin of the samples taken after the current step (t = step dt): the
+ * argument 2 pi f t + phase of the electrode voltage, taken modulo 2 pi and
+ * cut into nph equal bins starting at phase 0 (Sec. IV.C: electron fluxes
+ * resolved in rf phase, ion fluxes averaged over the period) */
+static int phase_bin(const orc_sim* s)
+{
+    if (s->nph == 1) return 0;
+    const double t = (double)s->step * s->c.dt;
+    const double u = s->c.f_rf * t + s->c.phase / (2.0 * PI_D);
+    const double fr = u - floor(u);
+    const int b = (int)(fr * (double)s->nph);
+    return b < s->nph ? b : s->nph - 1;
+}
+
+/* Sec. IV.C: inside the MD region the paper samples densities and fluxes on
+ * a grid of cubes of edge 0.08 dx instead of the PIC cells.  A particle adds
+ * 1 and its velocity to the fine cell that holds it (an average over the
+ * cell's volume); particles outside the box add nothing. */
+static void fine_accumulate(orc_sim* s, int sp, const double* p, const double* vv)
+{
+    int f[3];
+    for (int a = 0; a < 3; ++a) {
+        const double q = (p[a] - s->c.fine_origin[a]) / s->c.fine_h;
+        if (!(q >= 0.0) || !(q < (double)s->c.fine_n[a])) return;
+        f[a] = (int)q;
+    }
+    const size_t cell = ((size_t)f[2] * (size_t)s->c.fine_n[1] + (size_t)f[1]) * (size_t)s->c.fine_n[0] + (size_t)f[0];
+    double* m = s->fine[sp] + 4 * cell;
+    m[0] += 1.0; m[1] += vv[0]; m[2] += vv[1]; m[3] += vv[2];
+}
+
+/* node moments (Sec. IV: time averages): CIC weights of every particle at the
+ * end of a step, summed with the weight times its velocity, and phi; into the
+ * phase bin of the step */
 static void moments_accumulate(orc_sim* s)
 {
     const size_t N = nodes_of(s);
+    const int b = phase_bin(s);
     for (int sp = 0; sp < 2; ++sp)
         for (int64_t q = 0; q < s->n[sp]; ++q) {
             int c[3]; double f[3]; int64_t w[3][2];
@@ -628,11 +667,13 @@ static void moments_accumulate(orc_sim* s)
                 for (int dy = 0; dy < 2; ++dy)
                     for (int dxi = 0; dxi < 2; ++dxi) {
                         double wt = (double)(w[0][dxi] * w[1][dy] * w[2][dz]) * 0x1p-42;
-                        double* m = s->mom[sp] + 4 * node_at(s, c[0] + dxi, c[1] + dy, c[2] + dz);
+                        double* m = s->mom[sp] + 4 * ((size_t)b * N + node_at(s, c[0] + dxi, c[1] + dy, c[2] + dz));
                         m[0] += wt; m[1] += wt * vv[0]; m[2] += wt * vv[1]; m[3] += wt * vv[2];
                     }
+            if (s->nfine) fine_accumulate(s, sp, p, vv);
         }
-    for (size_t q = 0; q < N; ++q) s->mphi[q] += s->phi[q];
+    for (size_t q = 0; q < N; ++q) s->mphi[(size_t)b * N + q] += s->phi[q];
+    s->bsteps[b]++;
     s->msteps++;
 }
 
@@ -930,9 +971,16 @@ orc_sim* orc_create(const orc_cfg* cfg)
     s->ex = (double*)calloc(N, sizeof(double));
     s->ey = (double*)calloc(N, sizeof(double));
     s->ez = (double*)calloc(N, sizeof(double));
-    s->mom[0] = (double*)calloc(4 * N, sizeof(double));
-    s->mom[1] = (double*)calloc(4 * N, sizeof(double));
-    s->mphi = (double*)calloc(N, sizeof(double));
+    s->nph = cfg->mom_phases > 1 ? cfg->mom_phases : 1;
+    s->mom[0] = (double*)calloc(4 * N * (size_t)s->nph, sizeof(double));
+    s->mom[1] = (double*)calloc(4 * N * (size_t)s->nph, sizeof(double));
+    s->mphi = (double*)calloc(N * (size_t)s->nph, sizeof(double));
+    s->bsteps = (int64_t*)calloc((size_t)s->nph, sizeof(int64_t));
+    if (cfg->fine_n[0] > 0 && cfg->fine_n[1] > 0 && cfg->fine_n[2] > 0 && cfg->fine_h > 0.0) {
+        s->nfine = (size_t)cfg->fine_n[0] * (size_t)cfg->fine_n[1] * (size_t)cfg->fine_n[2];
+        s->fine[0] = (double*)calloc(4 * s->nfine, sizeof(double));
+        s->fine[1] = (double*)calloc(4 * s->nfine, sizeof(double));
+    }
     if ((cfg->flags & ORC_EEPF) && cfg->eepf_bins > 0 && cfg->eepf_de_ev > 0.0)
         s->eepf = (int64_t*)calloc((size_t)cfg->nz * (size_t)(cfg->eepf_bins + 1), sizeof(int64_t));
     if (cfg->n_xs > 0) {
@@ -1014,6 +1062,7 @@ void orc_destroy(orc_sim* s)
     free(s->rq); free(s->phi); free(s->ex); free(s->ey); free(s->ez); free(s->xs);
     free(s->gpos); free(s->grad); free(s->gq); free(s->gabs); free(s->gtab);
     free(s->cell_ng); free(s->cell_g); free(s->ch); free(s->mphi); free(s->eepf);
+    free(s->bsteps); free(s->fine[0]); free(s->fine[1]);
     free(s);
 }
 
@@ -1038,27 +1087,56 @@ void orc_get_counters(const orc_sim* s, int64_t* c) { memcpy(c, s->cnt, sizeof(i
 int64_t orc_step_index(const orc_sim* s) { return s->step; }
 uint32_t orc_next_id(const orc_sim* s) { return s->next_id; }
 
-int orc_moments(const orc_sim* s, int what, double* out)
+/* window averages of bins [b0, b1): sums over the bins' samples divided by their count */
+static int moments_of(const orc_sim* s, int what, int b0, int b1, int64_t steps, double* out)
 {
     const size_t N = nodes_of(s);
-    if (s->msteps == 0) return -1;
+    if (steps == 0 || what < 0 || what > 4) return -1;
     const double dx = s->c.dx;
-    const double norm = s->c.weight / ((dx * dx * dx) * (double)s->msteps);
-    switch (what) {
-    case 0: for (size_t q = 0; q < N; ++q) out[q] = s->mphi[q] / (double)s->msteps; return 0;
-    case 1: case 2: {
-        const double* m = s->mom[what - 1];
-        for (size_t q = 0; q < N; ++q) out[q] = m[4 * q] * norm;
-        return 0;
+    const double norm = s->c.weight / ((dx * dx * dx) * (double)steps);
+    const size_t len = what >= 3 ? 3 * N : N;
+    for (size_t q = 0; q < len; ++q) out[q] = 0.0;
+    for (int b = b0; b < b1; ++b) {
+        if (what == 0) {
+            for (size_t q = 0; q < N; ++q) out[q] += s->mphi[(size_t)b * N + q];
+        } else {
+            const double* m = s->mom[(what - 1) % 2] + 4 * (size_t)b * N;
+            for (size_t q = 0; q < N; ++q) {
+                if (what <= 2) out[q] += m[4 * q];
+                else
+                    for (int a = 0; a < 3; ++a) out[3 * q + a] += m[4 * q + 1 + a];
+            }
+        }
     }
-    case 3: case 4: {
-        const double* m = s->mom[what - 3];
-        for (size_t q = 0; q < N; ++q)
+    const double scale = what == 0 ? 1.0 / (double)steps : norm;
+    for (size_t q = 0; q < len; ++q) out[q] *= scale;
+    return 0;
+}
+
+int orc_moments(const orc_sim* s, int what, double* out)
+{
+    return moments_of(s, what, 0, s->nph, s->msteps, out);
+}
+
+int orc_moments_phase(const orc_sim* s, int what, int bin, double* out, int64_t* steps)
+{
+    if (bin < 0 || bin >= s->nph) return -1;
+    if (steps) *steps = s->bsteps[bin];
+    return moments_of(s, what, bin, bin + 1, s->bsteps[bin], out);
+}
+
+int orc_fine_moments(const orc_sim* s, int what, double* out)
+{
+    if (!s->nfine || s->msteps == 0 || what < 1 || what > 4) return -1;
+    const double h = s->c.fine_h;
+    const double norm = s->c.weight / ((h * h * h) * (double)s->msteps);
+    const double* m = s->fine[(what - 1) % 2];
+    for (size_t q = 0; q < s->nfine; ++q) {
+        if (what <= 2) out[q] = m[4 * q] * norm;
+        else
             for (int a = 0; a < 3; ++a) out[3 * q + a] = m[4 * q + 1 + a] * norm;
-        return 0;
     }
-    }
-    return -1;
+    return 0;
 }
 
 int orc_field_at(orc_sim* s, const double p[3], double E[3])
@@ -1084,9 +1162,14 @@ void orc_set_grain_counts(orc_sim* s, const int64_t* n_abs)
 
 void orc_reset_moments(orc_sim* s)
 {
-    const size_t N = nodes_of(s);
+    const size_t N = nodes_of(s) * (size_t)s->nph;
     memset(s->mom[0], 0, sizeof(double) * 4 * N);
     memset(s->mom[1], 0, sizeof(double) * 4 * N);
     memset(s->mphi, 0, sizeof(double) * N);
+    memset(s->bsteps, 0, sizeof(int64_t) * (size_t)s->nph);
+    if (s->nfine) {
+        memset(s->fine[0], 0, sizeof(double) * 4 * s->nfine);
+        memset(s->fine[1], 0, sizeof(double) * 4 * s->nfine);
+    }
     s->msteps = 0;
 }

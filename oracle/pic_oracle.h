@@ -48,6 +48,10 @@ typedef struct {
     double   coulomb_log;            /* Coulomb logarithm of the binary collisions (ORC_COULOMB) */
     int32_t  eepf_bins;              /* ORC_EEPF: energy bins of width eepf_de_ev, plus one overflow bin */
     double   eepf_de_ev;
+    int32_t  mom_phases;             /* ORC_MOMENTS: > 1 also bins the node moments by rf phase */
+    int32_t  fine_n[3];              /* ORC_MOMENTS: fine diagnostic grid of fine_n[0..2] cells of */
+    double   fine_h;                 /*   edge fine_h (all three > 0 switch it on), lower corner  */
+    double   fine_origin[3];         /*   fine_origin (metres); not periodic                       */
 } orc_cfg;
 
 typedef struct orc_sim orc_sim;
@@ -80,6 +84,10 @@ int64_t  orc_step_index(const orc_sim* s);
 uint32_t orc_next_id(const orc_sim* s);
 /* what: 0 phi, 1 n_e, 2 n_i, 3 flux_e (3 per node), 4 flux_i; window averages */
 int      orc_moments(const orc_sim* s, int what, double* out);
+/* the same for the samples of rf phase bin `bin` only; *steps = samples in that bin */
+int      orc_moments_phase(const orc_sim* s, int what, int bin, double* out, int64_t* steps);
+/* fine grid, what: 1 n_e, 2 n_i (per fine cell), 3 flux_e, 4 flux_i (3 per fine cell) */
+int      orc_fine_moments(const orc_sim* s, int what, double* out);
 void     orc_reset_moments(orc_sim* s);
 /* test helpers: field acting on a particle at p (Eqs. 4-6, with the MD
  * correction when p's cell is in an MD region); set the grains' absorbed
