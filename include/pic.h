@@ -125,6 +125,14 @@ typedef struct {
     double coulomb_log;           /* Coulomb logarithm lnL (> 0 with PIC_F_COULOMB) */
     int32_t eepf_bins;            /* > 0: accumulate the electron energy histogram of pic_eepf */
     double eepf_de_ev;            /* its bin width (eV) */
+    int32_t mom_phases;           /* PIC_F_MOMENTS: > 1 also bins the moments by rf phase
+                                     (pic_moments_phase); 0 or 1: rf averages only, in [0, 1024] */
+    int32_t fine_n[3];            /* PIC_F_MOMENTS: fine diagnostic grid of fine_n[0] x fine_n[1] x
+                                     fine_n[2] cubes of edge fine_h (Sec. IV.C: 200^3 cubes of
+                                     0.08 dx over the MD region), lower corner fine_origin
+                                     (metres), not periodic; all three 0 = off, else in [1, 1024] */
+    double fine_h;
+    double fine_origin[3];
 } pic_run;
 
 /* Create a run: copies every input to the device, deposits rho_0 (particles
@@ -203,10 +211,27 @@ pic_status pic_eepf(pic_ctx* ctx, int64_t* counts, size_t len, int64_t* steps, i
 pic_status pic_eepf_fit(const int64_t* counts, int32_t nbins, double de_ev, double e_lo_ev, double e_hi_ev,
                         double* fit);
 
-/* Window averages since the last reset (needs PIC_F_MOMENTS):
- * what 0 phi (V, nodes), 1 n_e, 2 n_i (m^-3, nodes), 3 flux_e, 4 flux_i
- * (m^-2 s^-1, 3 per node, node-major).  len = number of doubles in out_host. */
+/* Window averages since the last reset (needs PIC_F_MOMENTS), sampled after
+ * every step (positions at t = step dt, the velocities of the step, phi of the
+ * step's solve): what 0 phi (V, nodes), 1 n_e, 2 n_i (m^-3, nodes, CIC
+ * weights), 3 flux_e, 4 flux_i (m^-2 s^-1, 3 per node, node-major).  len =
+ * number of doubles in out_host.  reset != 0 then clears every moment window
+ * (rf average, phase bins and the fine grid). */
 pic_status pic_moments(pic_ctx* ctx, int32_t what, double* out_host, size_t len, int32_t reset);
+
+/* The same averages over the samples of one rf phase bin (Sec. IV.C: electron
+ * fluxes resolved in rf phase).  The sample after step s falls in bin
+ * floor(frac(f_rf s dt + phase / 2 pi) * mom_phases), i.e. the electrode phase
+ * modulo 2 pi cut into mom_phases equal bins from 0.  *steps_out (optional) =
+ * samples in that bin.  PIC_EINVAL for a bin out of range or an empty bin. */
+pic_status pic_moments_phase(pic_ctx* ctx, int32_t what, int32_t bin, double* out_host, size_t len,
+                             int64_t* steps_out);
+
+/* Window averages on the fine grid (needs fine_n): what 1 n_e, 2 n_i (m^-3 per
+ * fine cube), 3 flux_e, 4 flux_i (m^-2 s^-1, 3 per cube); cube (i, j, k) at
+ * index (k * fine_n[1] + j) * fine_n[0] + i holds the particles with
+ * fine_origin + (i, j, k) fine_h <= x < fine_origin + (i+1, j+1, k+1) fine_h. */
+pic_status pic_fine_moments(pic_ctx* ctx, int32_t what, double* out_host, size_t len);
 
 /* Parity and inspection hooks (same conventions; lengths are checked). */
 pic_status pic_get_particles(pic_ctx* ctx, int32_t species, double* x_host, double* v_host,

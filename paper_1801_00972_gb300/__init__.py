@@ -32,7 +32,7 @@ PIC_C_N = len(COUNTERS)
 
 # every symbol include/pic.h declares
 SYMBOLS = ("pic_init", "pic_step", "pic_tune_sort", "pic_advance", "pic_solve", "pic_grain_charges", "pic_counts",
-           "pic_moments", "pic_eepf", "pic_eepf_fit", "pic_get_particles", "pic_get_rho", "pic_get_phi", "pic_set_phi",
+           "pic_moments", "pic_moments_phase", "pic_fine_moments", "pic_eepf", "pic_eepf_fit", "pic_get_particles", "pic_get_rho", "pic_get_phi", "pic_set_phi",
            "pic_get_grain_table", "pic_set_grain_table", "pic_set_grain_counts", "pic_step_index",
            "pic_profile", "pic_profile_read", "pic_solve_noalloc", "pic_batch_init", "pic_batch_step",
            "pic_batch_run", "pic_batch_destroy", "pic_last_error", "pic_destroy")
@@ -63,7 +63,8 @@ class pic_run(C.Structure):
                 ("dt", C.c_double), ("md_sub", C.c_int32), ("sort_every", C.c_int32), ("seed", C.c_uint64),
                 ("run_id", C.c_uint32), ("prec", C.c_int32), ("flags", C.c_int32), ("tol", C.c_double),
                 ("max_cycles", C.c_int32), ("coulomb_log", C.c_double), ("eepf_bins", C.c_int32),
-                ("eepf_de_ev", C.c_double)]
+                ("eepf_de_ev", C.c_double), ("mom_phases", C.c_int32), ("fine_n", C.c_int32 * 3),
+                ("fine_h", C.c_double), ("fine_origin", C.c_double * 3)]
 
 
 class PicError(RuntimeError):
@@ -90,7 +91,8 @@ def load(path: str | None = None):
         sig = {
             "pic_step": [vp, i32], "pic_tune_sort": [vp, i32, C.POINTER(i32)], "pic_advance": [vp], "pic_solve": [vp, C.POINTER(i32), pd],
             "pic_grain_charges": [vp, pi64, pd], "pic_counts": [vp, pi64, pi64],
-            "pic_moments": [vp, i32, pd, sz, i32],
+            "pic_moments": [vp, i32, pd, sz, i32], "pic_moments_phase": [vp, i32, i32, pd, sz, pi64],
+            "pic_fine_moments": [vp, i32, pd, sz],
             "pic_eepf": [vp, pi64, sz, pi64, i32], "pic_eepf_fit": [pi64, i32, C.c_double, C.c_double, C.c_double, pd],
             "pic_get_particles": [vp, i32, pd, pd, pu32, i64, pi64],
             "pic_get_rho": [vp, pi64, sz], "pic_get_phi": [vp, pd, sz], "pic_set_phi": [vp, pd, sz],
@@ -203,6 +205,22 @@ def pic_moments(ctx, what, nodes, reset=False):
     return out
 
 
+def pic_moments_phase(ctx, what, bin, nodes):
+    """(window average over the samples of rf phase bin ``bin``, samples in it)."""
+    out = np.zeros(nodes * (3 if what >= 3 else 1))
+    steps = C.c_int64()
+    _check(ctx, load().pic_moments_phase(ctx, int(what), int(bin), _p(out, C.c_double), out.size, C.byref(steps)))
+    return out, int(steps.value)
+
+
+def pic_fine_moments(ctx, what, fine_n):
+    """Fine-grid window average, shaped (nz, ny, nx) or (nz, ny, nx, 3) for the fluxes."""
+    nx, ny, nz = fine_n
+    out = np.zeros(nx * ny * nz * (3 if what >= 3 else 1))
+    _check(ctx, load().pic_fine_moments(ctx, int(what), _p(out, C.c_double), out.size))
+    return out.reshape((nz, ny, nx, 3) if what >= 3 else (nz, ny, nx))
+
+
 def pic_get_particles(ctx, species, cap):
     x = np.zeros((max(cap, 1), 3)); v = np.zeros((max(cap, 1), 3)); ids = np.zeros(max(cap, 1), np.uint32)
     n = C.c_int64()
@@ -285,7 +303,8 @@ def pic_destroy(ctx):
 
 # ----------------------------------------------------------------- convenience
 def make_args(wl, particles, prec=PIC_MIXED, flags=0, capacity=None, sort_every=20, tol=1e-10, max_cycles=60,
-              md_sub=None, coulomb_log=10.0, eepf_bins=0, eepf_de_ev=0.0):
+              md_sub=None, coulomb_log=10.0, eepf_bins=0, eepf_de_ev=0.0, mom_phases=0, fine_n=(0, 0, 0),
+              fine_h=0.0, fine_origin=(0.0, 0.0, 0.0)):
     """The pic_init argument structures for a workload; returns them with the
     numpy arrays they point into (keep those alive while the call runs)."""
     keep = []
@@ -317,6 +336,9 @@ def make_args(wl, particles, prec=PIC_MIXED, flags=0, capacity=None, sort_every=
     run.seed, run.run_id, run.prec, run.flags = wl.seed, wl.run_id, prec, flags
     run.tol, run.max_cycles, run.coulomb_log = tol, max_cycles, coulomb_log
     run.eepf_bins, run.eepf_de_ev = eepf_bins, eepf_de_ev
+    run.mom_phases, run.fine_h = mom_phases, fine_h
+    for a in range(3):
+        run.fine_n[a], run.fine_origin[a] = int(fine_n[a]), float(fine_origin[a])
     return (mesh, el, gas, grains, run), keep
 
 
@@ -351,38 +373,15 @@ class Run:
     and initial particles [(x, v, id) for electrons, ions] in SI units."""
 
     def __init__(self, wl, particles, prec=PIC_MIXED, flags=0, stream=None, capacity=None, sort_every=20,
-                 tol=1e-10, max_cycles=60, md_sub=None, coulomb_log=10.0, eepf_bins=0, eepf_de_ev=0.0):
-        keep = []
-        mesh = pic_mesh(wl.nx, wl.ny, wl.nz, wl.dx)
-        el = pic_electrodes(wl.v_dc, wl.v_rf, wl.f_rf, wl.phase, wl.v_top)
-        xs = np.ascontiguousarray(wl.xs, dtype=np.float64)
-        keep.append(xs)
-        gas = pic_gas(wl.n_gas, wl.t_gas, wl.eps_exc, wl.eps_ion, wl.nu_max_e, wl.nu_max_i, wl.de_e, wl.de_i,
-                      xs.shape[1], _p(xs, C.c_double))
-        gp = np.ascontiguousarray(wl.grain_pos, dtype=np.float64).reshape(-1)
-        gr = np.ascontiguousarray(wl.grain_r, dtype=np.float64).reshape(-1)
-        keep += [gp, gr]
-        grains = pic_grains(gr.size, _p(gp, C.c_double), _p(gr, C.c_double))
-        run = pic_run()
-        for sp in range(2):
-            x, v, ids = particles[sp]
-            x = np.ascontiguousarray(x, dtype=np.float64).reshape(-1)
-            v = np.ascontiguousarray(v, dtype=np.float64).reshape(-1)
-            ids = np.ascontiguousarray(ids, dtype=np.uint32).reshape(-1)
-            keep += [x, v, ids]
-            run.n[sp] = ids.size
-            run.x_host[sp] = _p(x, C.c_double)
-            run.v_host[sp] = _p(v, C.c_double)
-            run.id_host[sp] = _p(ids, C.c_uint32)
-            cap = capacity[sp] if capacity is not None else int(ids.size * 1.25) + 4096
-            run.capacity[sp] = cap
-        run.weight, run.dt = wl.weight, wl.dt
-        run.md_sub = wl.md_sub if md_sub is None else md_sub
-        run.sort_every = sort_every
-        run.seed, run.run_id, run.prec, run.flags = wl.seed, wl.run_id, prec, flags
-        run.tol, run.max_cycles, run.coulomb_log = tol, max_cycles, coulomb_log
-        run.eepf_bins, run.eepf_de_ev = eepf_bins, eepf_de_ev
+                 tol=1e-10, max_cycles=60, md_sub=None, coulomb_log=10.0, eepf_bins=0, eepf_de_ev=0.0,
+                 mom_phases=0, fine_n=(0, 0, 0), fine_h=0.0, fine_origin=(0.0, 0.0, 0.0)):
+        (mesh, el, gas, grains, run), keep = make_args(
+            wl, particles, prec=prec, flags=flags, capacity=capacity, sort_every=sort_every, tol=tol,
+            max_cycles=max_cycles, md_sub=md_sub, coulomb_log=coulomb_log, eepf_bins=eepf_bins,
+            eepf_de_ev=eepf_de_ev, mom_phases=mom_phases, fine_n=fine_n, fine_h=fine_h, fine_origin=fine_origin)
+        gr = np.asarray(wl.grain_r).reshape(-1)
         self.eepf_bins = eepf_bins
+        self.fine_n = tuple(int(n) for n in fine_n)
         self.ctx = pic_init(mesh, el, gas, grains, run, stream)
         self.wl = wl
         self.nodes = wl.nx * wl.ny * (wl.nz + 1)
@@ -441,6 +440,12 @@ class Run:
 
     def moments(self, what, reset=False):
         return pic_moments(self.ctx, what, self.nodes, reset)
+
+    def moments_phase(self, what, bin):
+        return pic_moments_phase(self.ctx, what, bin, self.nodes)
+
+    def fine_moments(self, what):
+        return pic_fine_moments(self.ctx, what, self.fine_n)
 
     def eepf(self, reset=False):
         return pic_eepf(self.ctx, self.wl.nz, self.eepf_bins, reset)

@@ -68,6 +68,55 @@ pic_status cuda_fail(pic_ctx* c, cudaError_t e, const char* what)
     return fail(c, PIC_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
 }
 
+// zero every moment window (rf average, phase bins, fine grid) on `st`
+// (synchronous memsets when st is null)
+cudaError_t clear_moments(pic_ctx* c, cudaStream_t st)
+{
+    const size_t nb = (size_t)c->nph;
+    const size_t sz[6] = {sizeof(double) * 4 * c->nodes * nb, sizeof(double) * 4 * c->nodes * nb,
+                          sizeof(double) * c->nodes * nb, sizeof(unsigned long long) * nb,
+                          sizeof(double) * 4 * c->nfine, sizeof(double) * 4 * c->nfine};
+    void* p[6] = {c->mom[0], c->mom[1], c->mphi, c->d_bsteps, c->fine[0], c->fine[1]};
+    cudaError_t e = cudaSuccess;
+    for (int q = 0; q < 6 && e == cudaSuccess; ++q)
+        if (p[q]) e = st ? cudaMemsetAsync(p[q], 0, sz[q], st) : cudaMemset(p[q], 0, sz[q]);
+    return e;
+}
+
+// one moment sample after the step's solve: the phase bin, node moments and phi, fine grid
+void launch_moments_all(pic_ctx* c)
+{
+    if (c->nph > 1) launch_phase_bin(c);
+    if (c->prec == PIC_MIXED) launch_moments32(c);
+    else launch_moments64(c);
+    launch_moments_phi(c);
+    if (c->nfine) launch_fine(c);
+}
+
+// averages of phase bins [b0, b1) over `steps` samples into out (layout of pic_moments)
+pic_status moments_window(pic_ctx* c, int what, int b0, int b1, int64_t steps, double* out)
+{
+    const size_t N = c->nodes, len = (what >= 3 ? 3 : 1) * N, w = what == 0 ? 1 : 4;
+    std::vector<double> m(w * N * (size_t)(b1 - b0));
+    const double* src = what == 0 ? c->mphi : c->mom[(what - 1) % 2];
+    const cudaError_t e = cudaMemcpy(m.data(), src + w * N * (size_t)b0, sizeof(double) * m.size(),
+                                     cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(c, e, "moments copy");
+    for (size_t q = 0; q < len; ++q) out[q] = 0.0;
+    for (int b = 0; b < b1 - b0; ++b) {
+        const double* mb = m.data() + w * N * (size_t)b;
+        for (size_t q = 0; q < N; ++q) {
+            if (what == 0) out[q] += mb[q];
+            else if (what <= 2) out[q] += mb[4 * q];
+            else
+                for (int a = 0; a < 3; ++a) out[3 * q + a] += mb[4 * q + 1 + a];
+        }
+    }
+    const double scale = what == 0 ? 1.0 / (double)steps : c->W / ((c->dx * c->dx * c->dx) * (double)steps);
+    for (size_t q = 0; q < len; ++q) out[q] *= scale;
+    return PIC_OK;
+}
+
 // cell index and in-cell fraction along one axis, clamped into the mesh
 inline void locate1(double x, double dx, int n, int& i, double& f)
 {
@@ -211,6 +260,18 @@ pic_status pic_init(const pic_mesh* mesh, const pic_electrodes* el, const pic_ga
                                          "tol > 0, max_cycles >= 1");
     if (run->eepf_bins < 0 || run->eepf_bins > 65536 || (run->eepf_bins > 0 && !(run->eepf_de_ev > 0.0)))
         return fail(nullptr, PIC_EINVAL, "run: eepf_bins in [0, 65536] and eepf_de_ev > 0 when bins > 0");
+    {
+        const bool any = run->fine_n[0] != 0 || run->fine_n[1] != 0 || run->fine_n[2] != 0;
+        bool fine_ok = true;
+        for (int a = 0; a < 3; ++a)
+            fine_ok = fine_ok && (any ? run->fine_n[a] >= 1 && run->fine_n[a] <= 1024 : true);
+        if (any)
+            fine_ok = fine_ok && run->fine_h > 0.0 && std::isfinite(run->fine_h) && finite_all(run->fine_origin, 3);
+        if (run->mom_phases < 0 || run->mom_phases > 1024 || !fine_ok ||
+            ((run->mom_phases > 1 || any) && !(run->flags & PIC_F_MOMENTS)))
+            return fail(nullptr, PIC_EINVAL, "run: mom_phases in [0, 1024]; fine_n all 0 or all in [1, 1024] with "
+                                             "fine_h > 0 and a finite origin; both need PIC_F_MOMENTS");
+    }
     if ((run->flags & PIC_F_COULOMB) && !(run->coulomb_log > 0.0 && run->coulomb_log < 1e3))
         return fail(nullptr, PIC_EINVAL, "run: PIC_F_COULOMB needs a Coulomb logarithm in (0, 1000)");
     if (run->prec == PIC_MIXED && (nx > 1024 || ny > 1024 || nz > 2047))
@@ -274,6 +335,14 @@ pic_status pic_init(const pic_mesh* mesh, const pic_electrodes* el, const pic_ga
     c->coul_log = run->coulomb_log;
     c->eepf_bins = run->eepf_bins;
     c->eepf_de = run->eepf_de_ev;
+    c->nph = run->mom_phases > 1 ? run->mom_phases : 1;
+    c->f_rf = el->f_rf;
+    c->rf_phase = el->phase;
+    if (run->fine_n[0] > 0) {
+        for (int a = 0; a < 3; ++a) { c->fine_n[a] = run->fine_n[a]; c->fine_o[a] = run->fine_origin[a]; }
+        c->fine_h = run->fine_h;
+        c->nfine = (size_t)run->fine_n[0] * (size_t)run->fine_n[1] * (size_t)run->fine_n[2];
+    }
     c->max_cycles = run->max_cycles;
     c->W = run->weight; c->dt = run->dt; c->tol = run->tol;
     c->seed = run->seed; c->run_id = run->run_id;
@@ -364,10 +433,18 @@ pic_status pic_init(const pic_mesh* mesh, const pic_electrodes* el, const pic_ga
         if (c->eepf) cudaMemset(c->eepf, 0, sizeof(unsigned long long) * (size_t)nz * (c->eepf_bins + 1));
     }
     if (c->flags & PIC_F_MOMENTS) {
-        c->mom[0] = (double*)dev_alloc(c, sizeof(double) * 4 * nodes);
-        c->mom[1] = (double*)dev_alloc(c, sizeof(double) * 4 * nodes);
-        c->mphi = (double*)dev_alloc(c, sizeof(double) * nodes);
-        ok = ok && c->mom[0] && c->mom[1] && c->mphi;
+        const size_t nb = (size_t)c->nph;
+        c->mom[0] = (double*)dev_alloc(c, sizeof(double) * 4 * nodes * nb);
+        c->mom[1] = (double*)dev_alloc(c, sizeof(double) * 4 * nodes * nb);
+        c->mphi = (double*)dev_alloc(c, sizeof(double) * nodes * nb);
+        c->d_bin = (int*)dev_alloc(c, sizeof(int));
+        c->d_bsteps = (unsigned long long*)dev_alloc(c, sizeof(unsigned long long) * nb);
+        ok = ok && c->mom[0] && c->mom[1] && c->mphi && c->d_bin && c->d_bsteps;
+        if (c->nfine) {
+            c->fine[0] = (double*)dev_alloc(c, sizeof(double) * 4 * c->nfine);
+            c->fine[1] = (double*)dev_alloc(c, sizeof(double) * 4 * c->nfine);
+            ok = ok && c->fine[0] && c->fine[1];
+        }
     }
     ok = ok && c->d_step && c->d_iters && c->d_res && c->d_solve_flag && c->d_iter_total && c->d_vb_last;
     ok = ok && c->d_nslot && c->d_cnt && c->d_err && c->d_nch && c->d_next_id && c->d_child && c->rq && c->phi &&
@@ -467,9 +544,11 @@ pic_status pic_init(const pic_mesh* mesh, const pic_electrodes* el, const pic_ga
     if (e == cudaSuccess) e = cudaMemset(c->gq, 0, sizeof(double) * ng1);
     if (e == cudaSuccess) e = cudaMemset(c->gq32, 0, sizeof(float) * ng1);
     if (e == cudaSuccess) e = cudaMemset(c->phi, 0, sizeof(double) * nodes);
-    if (e == cudaSuccess && c->mphi) e = cudaMemset(c->mphi, 0, sizeof(double) * nodes);
-    if (e == cudaSuccess && c->mom[0]) e = cudaMemset(c->mom[0], 0, sizeof(double) * 4 * nodes);
-    if (e == cudaSuccess && c->mom[1]) e = cudaMemset(c->mom[1], 0, sizeof(double) * 4 * nodes);
+    if (e == cudaSuccess && (c->flags & PIC_F_MOMENTS)) {
+        e = cudaMemset(c->d_bin, 0, sizeof(int));
+        if (e == cudaSuccess) e = clear_moments(c, nullptr);
+        if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    }
     if (e != cudaSuccess) { destroy(c); return cuda_fail(nullptr, e, "upload"); }
 
     // ---- unit-charge mesh field of each grain on its region nodes (Eq. 5)
@@ -696,9 +775,7 @@ pic_status ensure_graphs(pic_ctx* c, bool sort)
     if (!c->g_solve) c->g_solve = capture_solve(c);
     if ((c->flags & PIC_F_MOMENTS) && !c->g_mom[p])
         c->g_mom[p] = capture(c, &c->n_mom, [&] {
-            if (mixed) launch_moments32(c);
-            else launch_moments64(c);
-            launch_moments_phi(c);
+            launch_moments_all(c);
         });
     if (!c->g_pre || !c->g_push[p] || !c->g_post[p][so] || !c->g_solve ||
         ((c->flags & PIC_F_MOMENTS) && !c->g_mom[p]))
@@ -760,9 +837,7 @@ pic_status step_enqueue(pic_ctx* c, int32_t n_steps)
             if (r == PIC_ENOTCONV) c->pending = PIC_ENOTCONV;
             else if (r != PIC_OK) return fail(c, r, "Poisson solve failed");
             if (c->flags & PIC_F_MOMENTS) {
-                if (c->prec == PIC_MIXED) launch_moments32(c);
-                else launch_moments64(c);
-                launch_moments_phi(c);
+                launch_moments_all(c);
                 c->msteps += 1;
             }
         }
@@ -1142,34 +1217,62 @@ pic_status pic_moments(pic_ctx* c, int32_t what, double* out, size_t len, int32_
     if (!c) return PIC_EINVAL;
     if (!(c->flags & PIC_F_MOMENTS)) return fail(c, PIC_EINVAL, "moments need PIC_F_MOMENTS at init");
     if (what < 0 || what > 4) return fail(c, PIC_EINVAL, "moments: what in 0..4");
-    const size_t need = (what >= 3 ? 3 : 1) * c->nodes;
-    if (!out || len != need) return fail(c, PIC_EINVAL, "moments length");
+    if (!out || len != (what >= 3 ? 3 : 1) * c->nodes) return fail(c, PIC_EINVAL, "moments length");
     pic_status k = check(c);
     if (k != PIC_OK) return k;
     if (c->msteps == 0) return fail(c, PIC_EINVAL, "moments: empty window");
-    const double norm = c->W / ((c->dx * c->dx * c->dx) * (double)c->msteps);
-    cudaError_t e;
-    if (what == 0) {
-        e = cudaMemcpy(out, c->mphi, sizeof(double) * c->nodes, cudaMemcpyDeviceToHost);
-        if (e != cudaSuccess) return cuda_fail(c, e, "moments copy");
-        for (size_t q = 0; q < c->nodes; ++q) out[q] /= (double)c->msteps;
-    } else {
-        std::vector<double> m(4 * c->nodes);
-        e = cudaMemcpy(m.data(), c->mom[(what - 1) % 2], sizeof(double) * m.size(), cudaMemcpyDeviceToHost);
-        if (e != cudaSuccess) return cuda_fail(c, e, "moments copy");
-        for (size_t q = 0; q < c->nodes; ++q) {
-            if (what <= 2) out[q] = m[4 * q] * norm;
-            else
-                for (int a = 0; a < 3; ++a) out[3 * q + a] = m[4 * q + 1 + a] * norm;
-        }
-    }
+    k = moments_window(c, what, 0, c->nph, c->msteps, out);
+    if (k != PIC_OK) return k;
     if (reset) {
-        cudaMemsetAsync(c->mom[0], 0, sizeof(double) * 4 * c->nodes, c->stream);
-        cudaMemsetAsync(c->mom[1], 0, sizeof(double) * 4 * c->nodes, c->stream);
-        cudaMemsetAsync(c->mphi, 0, sizeof(double) * c->nodes, c->stream);
+        const cudaError_t e = clear_moments(c, c->stream);
+        if (e != cudaSuccess) return cuda_fail(c, e, "moments reset");
         c->msteps = 0;
     }
     return check(c);
+}
+
+pic_status pic_moments_phase(pic_ctx* c, int32_t what, int32_t bin, double* out, size_t len, int64_t* steps_out)
+{
+    if (!c) return PIC_EINVAL;
+    if (!(c->flags & PIC_F_MOMENTS)) return fail(c, PIC_EINVAL, "moments need PIC_F_MOMENTS at init");
+    if (what < 0 || what > 4 || bin < 0 || bin >= c->nph)
+        return fail(c, PIC_EINVAL, "moments_phase: what in 0..4, bin in [0, mom_phases)");
+    if (!out || len != (what >= 3 ? 3 : 1) * c->nodes) return fail(c, PIC_EINVAL, "moments length");
+    pic_status k = check(c);
+    if (k != PIC_OK) return k;
+    int64_t steps = c->msteps;
+    if (c->nph > 1) {
+        unsigned long long n = 0;
+        const cudaError_t e = cudaMemcpy(&n, c->d_bsteps + bin, sizeof n, cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return cuda_fail(c, e, "moments copy");
+        steps = (int64_t)n;
+    }
+    if (steps_out) *steps_out = steps;
+    if (steps == 0) return fail(c, PIC_EINVAL, "moments_phase: no samples in this bin");
+    return moments_window(c, what, bin, bin + 1, steps, out);
+}
+
+pic_status pic_fine_moments(pic_ctx* c, int32_t what, double* out, size_t len)
+{
+    if (!c) return PIC_EINVAL;
+    if (!c->nfine) return fail(c, PIC_EINVAL, "the fine grid is off (fine_n = 0)");
+    if (what < 1 || what > 4) return fail(c, PIC_EINVAL, "fine_moments: what in 1..4");
+    if (!out || len != (what >= 3 ? 3 : 1) * c->nfine) return fail(c, PIC_EINVAL, "fine_moments length");
+    pic_status k = check(c);
+    if (k != PIC_OK) return k;
+    if (c->msteps == 0) return fail(c, PIC_EINVAL, "moments: empty window");
+    std::vector<double> m(4 * c->nfine);
+    const cudaError_t e = cudaMemcpy(m.data(), c->fine[(what - 1) % 2], sizeof(double) * m.size(),
+                                     cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(c, e, "fine moments copy");
+    const double h = c->fine_h;
+    const double norm = c->W / ((h * h * h) * (double)c->msteps);
+    for (size_t q = 0; q < c->nfine; ++q) {
+        if (what <= 2) out[q] = m[4 * q] * norm;
+        else
+            for (int a = 0; a < 3; ++a) out[3 * q + a] = m[4 * q + 1 + a] * norm;
+    }
+    return PIC_OK;
 }
 
 }  // extern "C"

@@ -1,3 +1,5 @@
+// Diagnostics beyond the step.
+//
 // Electron energy probability function (Sec. IV.A, Fig. 3): an exact integer
 // histogram of electron energies per cell plane, accumulated every step after
 // the collisions, and the two-Maxwellian fit the paper applies to it.
@@ -7,6 +9,11 @@
 // to an overflow bin.  The FP64 kernel takes the bin decision in FP64 exactly
 // as the oracle does (this unit is built without fused multiply-add); the mixed
 // kernel takes it in float from the cells/step velocities.
+//
+// Phase-resolved moments and the fine MD-region grid (Sec. IV.C): each moment
+// sample goes into the rf phase bin of its time (the bin index is taken in
+// FP64 as the oracle takes it), and every particle inside the fine box adds 1
+// and its velocity to the cube that holds it.
 #include <algorithm>
 #include <cmath>
 #include <vector>
@@ -59,6 +66,81 @@ __global__ void k_eepf32(const float4* __restrict__ pos, const float4* __restric
     }
 }
 
+// bin = floor(frac(f_rf t + phase / 2 pi) * nph) of the sample at t = step dt
+__global__ void k_phase_bin(const uint32_t* step, double f_rf, double dt, double phase, int nph, int* bin,
+                            unsigned long long* bsteps)
+{
+    const double t = (double)*step * dt;
+    const double u = f_rf * t + phase / (2.0 * 3.14159265358979323846);
+    const double fr = u - floor(u);
+    int b = (int)(fr * (double)nph);
+    b = b < nph ? b : nph - 1;
+    *bin = b;
+    bsteps[b] += 1ull;
+}
+
+struct FineBox {
+    double o[3], h;
+    int n[3];
+};
+
+// the cube of the box holding x, or -1
+__device__ __forceinline__ long long fine_cube(const FineBox& f, const double x[3])
+{
+    int c[3];
+    for (int a = 0; a < 3; ++a) {
+        const double q = (x[a] - f.o[a]) / f.h;
+        if (!(q >= 0.0) || !(q < (double)f.n[a])) return -1;
+        c[a] = (int)q;
+    }
+    return ((long long)c[2] * f.n[1] + c[1]) * f.n[0] + c[0];
+}
+
+__device__ __forceinline__ void fine_add(double* m, double vx, double vy, double vz)
+{
+    atomicAdd(m, 1.0);
+    atomicAdd(m + 1, vx);
+    atomicAdd(m + 2, vy);
+    atomicAdd(m + 3, vz);
+}
+
+__global__ void k_fine64(FineBox f, const double4* __restrict__ pos, const double4* __restrict__ vel,
+                         const unsigned long long* nslot, int sp, double* fine)
+{
+    const unsigned long long n = nslot[sp];
+    for (unsigned long long q = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; q < n;
+         q += (unsigned long long)gridDim.x * blockDim.x) {
+        const double4 p = pos[q];
+        if (p.w < 0.0) continue;
+        const double x[3] = {p.x, p.y, p.z};
+        const long long cube = fine_cube(f, x);
+        if (cube < 0) continue;
+        const double4 v = vel[q];
+        fine_add(fine + 4 * cube, v.x, v.y, v.z);
+    }
+}
+
+// mixed layout: integer cell packed as i | j << 10 | k << 20, float offsets in
+// cells, velocities in cells per step
+__global__ void k_fine32(FineBox f, double dx, double vs, const float4* __restrict__ pos,
+                         const float4* __restrict__ vel, const unsigned long long* nslot, int sp, double* fine)
+{
+    const unsigned long long n = nslot[sp];
+    for (unsigned long long q = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; q < n;
+         q += (unsigned long long)gridDim.x * blockDim.x) {
+        const float4 p = pos[q];
+        const int cell = __float_as_int(p.w);
+        if (cell < 0) continue;
+        const double x[3] = {((double)(cell & 1023) + (double)p.x) * dx,
+                             ((double)((cell >> 10) & 1023) + (double)p.y) * dx,
+                             ((double)(cell >> 20) + (double)p.z) * dx};
+        const long long cube = fine_cube(f, x);
+        if (cube < 0) continue;
+        const float4 v = vel[q];
+        fine_add(fine + 4 * cube, (double)v.x * vs, (double)v.y * vs, (double)v.z * vs);
+    }
+}
+
 // weighted least squares y = a + s x; false without two distinct abscissae
 bool line_fit(const std::vector<double>& x, const std::vector<double>& y, const std::vector<double>& w, size_t lo,
               size_t hi, double& a, double& s)
@@ -89,6 +171,29 @@ void launch_eepf(pic_ctx* c)
                                               c->eepf, c->nx * c->ny, c->eepf_bins, c->eepf_de, c->hm[0]);
     }
     c->launches += 1;
+}
+
+void launch_phase_bin(pic_ctx* c)
+{
+    k_phase_bin<<<1, 1, 0, c->stream>>>(c->d_step, c->f_rf, c->dt, c->rf_phase, c->nph, c->d_bin, c->d_bsteps);
+    c->launches += 1;
+}
+
+void launch_fine(pic_ctx* c)
+{
+    FineBox f;
+    for (int a = 0; a < 3; ++a) { f.o[a] = c->fine_o[a]; f.n[a] = c->fine_n[a]; }
+    f.h = c->fine_h;
+    for (int sp = 0; sp < 2; ++sp) {
+        const int grid = grid_for(c->cap[sp], 256, 152 * 8);
+        if (c->prec == PIC_MIXED)
+            k_fine32<<<grid, 256, 0, c->stream>>>(f, c->dx, c->dx / c->dt, (const float4*)c->pos[sp],
+                                                  (const float4*)c->vel[sp], c->d_nslot, sp, c->fine[sp]);
+        else
+            k_fine64<<<grid, 256, 0, c->stream>>>(f, (const double4*)c->pos[sp], (const double4*)c->vel[sp],
+                                                  c->d_nslot, sp, c->fine[sp]);
+    }
+    c->launches += 2;
 }
 
 }  // namespace pic

@@ -581,11 +581,13 @@ __global__ void k_grain_table(int nx, int ny, int nz, double dx, const double* p
         o[2] = (phi[n - P] - phi[n + P]) / h2;
 }
 
-// node moments: CIC sums of 1 and v per species (double atomics)
+// node moments: CIC sums of 1 and v per species (double atomics), into the
+// slice of the sample's rf phase bin
 __global__ void k_moments64(Geo g, const double4* pos, const double4* vel, const unsigned long long* nslot, int sp,
-                            double* mom)
+                            double* mom, const int* bin, size_t stride)
 {
     const unsigned long long n = nslot[sp];
+    mom += (size_t)*bin * stride;
     for (unsigned long long q = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; q < n;
          q += (unsigned long long)gridDim.x * blockDim.x) {
         const double4 P = pos[q];
@@ -691,7 +693,8 @@ void launch_moments64(pic_ctx* c)
 {
     for (int sp = 0; sp < 2; ++sp)
         k_moments64<<<grid_for(c->cap[sp], 256, 152 * 8), 256, 0, c->stream>>>(
-            geo(c), (const double4*)c->pos[sp], (const double4*)c->vel[sp], c->d_nslot, sp, c->mom[sp]);
+            geo(c), (const double4*)c->pos[sp], (const double4*)c->vel[sp], c->d_nslot, sp, c->mom[sp], c->d_bin,
+            4 * c->nodes);
     c->launches += 2;
 }
 

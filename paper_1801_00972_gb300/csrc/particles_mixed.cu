@@ -870,9 +870,10 @@ __global__ void k_children_finish32(unsigned long long* nch, unsigned long long 
 }
 
 __global__ void k_moments32(int nx, int ny, float vs, const float4* pos, const float4* vel,
-                            const unsigned long long* nslot, int sp, double* mom)
+                            const unsigned long long* nslot, int sp, double* mom, const int* bin, size_t stride)
 {
     const unsigned long long n = nslot[sp];
+    mom += (size_t)*bin * stride;   // the sample's rf phase bin
     for (unsigned long long q = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; q < n;
          q += (unsigned long long)gridDim.x * blockDim.x) {
         const float4 P = pos[q];
@@ -898,8 +899,9 @@ __global__ void k_moments32(int nx, int ny, float vs, const float4* pos, const f
     }
 }
 
-__global__ void k_moments_phi(const double* phi, double* mphi, size_t n)
+__global__ void k_moments_phi(const double* phi, double* mphi, size_t n, const int* bin)
 {
+    mphi += (size_t)*bin * n;
     for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < n; q += (size_t)gridDim.x * blockDim.x)
         mphi[q] += phi[q];
 }
@@ -1019,14 +1021,15 @@ void launch_moments32(pic_ctx* c)
     for (int sp = 0; sp < 2; ++sp)
         k_moments32<<<grid_for(c->cap[sp], 256, 152 * 8), 256, 0, c->stream>>>(
             c->nx, c->ny, (float)(c->dx / c->dt), (const float4*)c->pos[sp], (const float4*)c->vel[sp], c->d_nslot,
-            sp, c->mom[sp]);
+            sp, c->mom[sp], c->d_bin, 4 * c->nodes);
     c->launches += 2;
 }
 
 void launch_moments_phi(pic_ctx* c)
 {
     phi_sync_f64(c);
-    k_moments_phi<<<grid_for((int64_t)c->nodes, 256, 152 * 4), 256, 0, c->stream>>>(c->phi, c->mphi, c->nodes);
+    k_moments_phi<<<grid_for((int64_t)c->nodes, 256, 152 * 4), 256, 0, c->stream>>>(c->phi, c->mphi, c->nodes,
+                                                                                  c->d_bin);
     c->launches += 1;
 }
 

@@ -250,9 +250,17 @@ struct pic_ctx {
     unsigned long long prof_iter0 = 0;
 
     // moments
-    double* mom[2] = {nullptr, nullptr};     // 4 * nodes each
-    double* mphi = nullptr;
+    double* mom[2] = {nullptr, nullptr};     // nph * 4 * nodes each: [phase bin][node][n, n vx, n vy, n vz]
+    double* mphi = nullptr;                  // nph * nodes
     int64_t msteps = 0;
+    int nph = 1;                             // rf phase bins of the moments
+    double f_rf = 0.0, rf_phase = 0.0;
+    int* d_bin = nullptr;                    // phase bin of the current sample
+    unsigned long long* d_bsteps = nullptr;  // samples per phase bin
+    int fine_n[3] = {0, 0, 0};
+    size_t nfine = 0;
+    double fine_h = 0.0, fine_o[3] = {0.0, 0.0, 0.0};
+    double* fine[2] = {nullptr, nullptr};    // nfine * 4 each: [cube][count, sum vx, sum vy, sum vz]
 
     // measurement: events around push launches and solves while prof != 0
     int prof = 0;
@@ -294,6 +302,8 @@ void scan_cells(pic_ctx* c, unsigned int* data);   // exclusive scan of one valu
 
 // diagnostics.cu (built without fused multiply-add)
 void launch_eepf(pic_ctx* c);                       // add this step's electrons to the energy histogram
+void launch_phase_bin(pic_ctx* c);                  // phase bin of this step's moment sample
+void launch_fine(pic_ctx* c);                       // add this step's particles to the fine grid
 
 // coulomb.cu (built without fused multiply-add)
 void launch_coulomb(pic_ctx* c);                    // binary Coulomb collisions of the step's particles

@@ -62,7 +62,8 @@ def _args(wl, n=10):
 
 
 @pytest.mark.parametrize("bad", ["nx_odd", "dx", "dt", "tol", "capacity", "grain_at_electrode", "particle_out",
-                                 "xs_nan", "prec", "coulomb_log"])
+                                 "xs_nan", "prec", "coulomb_log", "phases_without_moments", "fine_partial",
+                                 "fine_h"])
 def test_invalid_arguments_rejected(lib, bad):
     wl = I.small(n_e=10, n_i=10)
     mesh, el, gas, grains, run, keep = _args(wl)
@@ -88,6 +89,14 @@ def test_invalid_arguments_rejected(lib, bad):
     elif bad == "coulomb_log":
         run.flags = P.PIC_F_COULOMB
         run.coulomb_log = 0.0
+    elif bad == "phases_without_moments":
+        run.mom_phases = 8
+    elif bad == "fine_partial":
+        run.flags = P.PIC_F_MOMENTS
+        run.fine_n[0], run.fine_n[2], run.fine_h = 10, 10, 1e-5
+    elif bad == "fine_h":
+        run.flags = P.PIC_F_MOMENTS
+        run.fine_n[0] = run.fine_n[1] = run.fine_n[2] = 10
     with pytest.raises(P.PicError) as e:
         P.pic_init(mesh, el, gas, grains, run)
     assert e.value.status == P.PIC_EINVAL
@@ -99,3 +108,5 @@ def test_null_context_rejected(lib):
     assert lib.pic_step(None, 1) == P.PIC_EINVAL
     assert lib.pic_tune_sort(None, 5, None) == P.PIC_EINVAL
     assert lib.pic_advance(None) == P.PIC_EINVAL
+    assert lib.pic_moments_phase(None, 0, 0, None, 0, None) == P.PIC_EINVAL
+    assert lib.pic_fine_moments(None, 1, None, 0) == P.PIC_EINVAL

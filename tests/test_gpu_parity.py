@@ -336,3 +336,77 @@ def test_eepf_histogram_matches_oracle(prec):
     assert np.array_equal(hr, hg)
     h0, s0 = run.eepf()
     assert s0 == 0 and h0.sum() == 0
+
+
+def _rf_wl(**over):
+    # 8 steps per rf period (f dt = 1/8), so 8 steps put two samples in each of 4 bins
+    args = dict(nx=8, ny=8, nz=16, n_e=20000, n_i=20000, grains=1, v_dc=-20.0, v_rf=40.0, f_rf=1.25e9, phase=0.3)
+    args.update(over)
+    return I.small(**args)
+
+
+def _fine_box(wl):
+    h = 0.08 * wl.dx
+    n = (50, 40, 30)
+    o = np.asarray(wl.grain_pos[0]) - 0.5 * h * np.array(n)
+    return dict(fine_n=n, fine_h=h, fine_origin=tuple(o))
+
+
+@pytest.mark.parametrize("prec", [P.PIC_FP64, P.PIC_MIXED])
+def test_phase_moments_and_fine_grid_match_oracle(prec):
+    wl = _rf_wl()
+    parts = I.sample_particles(wl)
+    box = _fine_box(wl)
+    ref = O.Sim(wl, parts, flags=O.MOMENTS, mom_phases=4, **box)
+    run = P.Run(wl, parts, prec=prec, flags=P.PIC_F_MOMENTS, stream=_stream(), mom_phases=4, **box)
+    for _ in range(8):
+        ref.step()
+        run.step()
+    fp64 = prec == P.PIC_FP64
+    for b in range(4):
+        for what in range(5):
+            mg, sg = run.moments_phase(what, b)
+            mo, so = ref.moments_phase(what, b)
+            assert sg == so == 2
+            scale = max(np.max(np.abs(mo)), 1e-30)
+            if what == 0:
+                # phi: two solvers stopped at 1e-10 relative residual
+                assert np.max(np.abs(mg - mo)) <= (1e-6 if fp64 else 1e-4) * scale, (b, what)
+            elif fp64:
+                assert np.max(np.abs(mg - mo)) <= 1e-6 * scale, (b, what)
+            else:
+                # float positions and solve: node densities and fluxes agree statistically
+                assert np.abs(mg - mo).sum() <= 2e-2 * np.abs(mo).sum(), (b, what)
+    # the rf average over the bins
+    for what in range(5):
+        mg, mo = run.moments(what), ref.moments(what)
+        tol = 1e-6 if fp64 else 2e-2
+        assert np.abs(mg - mo).sum() <= tol * np.abs(mo).sum() + 1e-300, what
+    # fine grid: cube counts are integers of the samples; positions that differ by
+    # rounding may put a sample in the neighbouring cube
+    nw = wl.weight / (box["fine_h"] ** 3 * 8)
+    for sp in range(2):
+        cg = np.rint(run.fine_moments(1 + sp) / nw)
+        co = np.rint(ref.fine_moments(1 + sp) / nw)
+        assert co.sum() > 1000
+        flips = np.abs(cg - co).sum()
+        assert flips <= (4 if fp64 else 0.02 * co.sum()), (sp, flips)
+        fg, fo = run.fine_moments(3 + sp), ref.fine_moments(3 + sp)
+        same = (cg == co)
+        vs = np.max(np.abs(fo))
+        if fp64:
+            # velocities follow phi, which two solvers give to about 1e-8 relative
+            assert np.max(np.abs(fg - fo)[same]) <= 1e-7 * vs
+        else:
+            assert np.abs(fg - fo).sum() <= 5e-2 * np.abs(fo).sum()
+    # a reset clears every window: one more step is one sample in one bin
+    run.moments(1, reset=True)
+    run.step()
+    got = []
+    for b in range(4):
+        try:
+            got.append(run.moments_phase(1, b)[1])
+        except P.PicError:
+            got.append(0)
+    assert sorted(got) == [0, 0, 0, 1]
+    assert run.fine_moments(2).sum() > 0
