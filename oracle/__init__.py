@@ -108,6 +108,8 @@ def lib():
             L.orc_moments.argtypes = [vp, i32, pd]; L.orc_moments.restype = i32
             L.orc_moments_phase.argtypes = [vp, i32, i32, pd, pi64]; L.orc_moments_phase.restype = i32
             L.orc_fine_moments.argtypes = [vp, i32, pd]; L.orc_fine_moments.restype = i32
+            L.orc_oml_potential.argtypes = [dbl] * 5; L.orc_oml_potential.restype = dbl
+            L.orc_oml_charges.argtypes = [vp, i32, pd]; L.orc_oml_charges.restype = i32
             L.orc_reset_moments.argtypes = [vp]
             L.orc_field_at.argtypes = [vp, pd, pd]; L.orc_field_at.restype = i32
             L.orc_set_grain_counts.argtypes = [vp, pi64]
@@ -119,6 +121,11 @@ def lib():
             L.orc_gauss3.argtypes = [u32, u32, u32, pu32, pd]
             _lib = L
     return _lib
+
+
+def oml_potential(ne, ni, te, ti, lam_over_l=0.0):
+    """OML surface potential (V) of an isolated sphere; see orc_oml_potential."""
+    return lib().orc_oml_potential(float(ne), float(ni), float(te), float(ti), float(lam_over_l))
 
 
 def _p(a, t):
@@ -309,7 +316,7 @@ class Sim:
         return dict(zip(C_NAMES, (int(x) for x in c)))
 
     def moments(self, what: int):
-        n = self.nodes * (3 if what >= 3 else 1)
+        n = self.nodes * (3 if what in (3, 4) else 1)
         a = np.zeros(n)
         assert lib().orc_moments(self.h, what, _p(a, C.c_double)) == 0
         return a
@@ -327,7 +334,7 @@ class Sim:
 
     def moments_phase(self, what: int, bin: int):
         """(window average of rf phase bin ``bin``, samples in that bin)."""
-        n = self.nodes * (3 if what >= 3 else 1)
+        n = self.nodes * (3 if what in (3, 4) else 1)
         a = np.zeros(n)
         st = C.c_int64(0)
         assert lib().orc_moments_phase(self.h, what, bin, _p(a, C.c_double), C.byref(st)) == 0
@@ -339,6 +346,12 @@ class Sim:
         a = np.zeros(nx * ny * nz * (3 if what >= 3 else 1))
         assert lib().orc_fine_moments(self.h, what, _p(a, C.c_double)) == 0
         return a.reshape((nz, ny, nx, 3) if what >= 3 else (nz, ny, nx))
+
+    def oml_charges(self, with_cx: bool = True):
+        """Per grain (Q [C], phi [V], n_e, n_i [m^-3], T_e, T_i [eV]) from the moment window."""
+        out = np.zeros(6 * max(self.ng, 1))
+        assert lib().orc_oml_charges(self.h, int(bool(with_cx)), _p(out, C.c_double)) == 0
+        return out[: 6 * self.ng].reshape(self.ng, 6)
 
     def reset_moments(self):
         lib().orc_reset_moments(self.h)

@@ -320,6 +320,7 @@ struct orc_sim {
     child_rec* ch; int64_t nch, capch;
     double* mom[2];                /* [phase bin][node][4]: count, count*vx, count*vy, count*vz */
     double* mphi;                  /* [phase bin][node] */
+    double* mke[2];                /* [phase bin][node]: count * |v|^2 */
     int64_t msteps;
     int64_t* bsteps;               /* samples per phase bin */
     int nph;                       /* phase bins (1 without phase resolution) */
@@ -661,6 +662,7 @@ static void moments_accumulate(orc_sim* s)
             int c[3]; double f[3]; int64_t w[3][2];
             const double* p = s->x[sp] + 3 * q;
             const double* vv = s->v[sp] + 3 * q;
+            const double v2 = (vv[0] * vv[0] + vv[1] * vv[1]) + vv[2] * vv[2];
             locate(s, p, c, f);
             qweights(f, w);
             for (int dz = 0; dz < 2; ++dz)
@@ -669,6 +671,7 @@ static void moments_accumulate(orc_sim* s)
                         double wt = (double)(w[0][dxi] * w[1][dy] * w[2][dz]) * 0x1p-42;
                         double* m = s->mom[sp] + 4 * ((size_t)b * N + node_at(s, c[0] + dxi, c[1] + dy, c[2] + dz));
                         m[0] += wt; m[1] += wt * vv[0]; m[2] += wt * vv[1]; m[3] += wt * vv[2];
+                        s->mke[sp][(size_t)b * N + node_at(s, c[0] + dxi, c[1] + dy, c[2] + dz)] += wt * v2;
                     }
             if (s->nfine) fine_accumulate(s, sp, p, vv);
         }
@@ -975,6 +978,8 @@ orc_sim* orc_create(const orc_cfg* cfg)
     s->mom[0] = (double*)calloc(4 * N * (size_t)s->nph, sizeof(double));
     s->mom[1] = (double*)calloc(4 * N * (size_t)s->nph, sizeof(double));
     s->mphi = (double*)calloc(N * (size_t)s->nph, sizeof(double));
+    s->mke[0] = (double*)calloc(N * (size_t)s->nph, sizeof(double));
+    s->mke[1] = (double*)calloc(N * (size_t)s->nph, sizeof(double));
     s->bsteps = (int64_t*)calloc((size_t)s->nph, sizeof(int64_t));
     if (cfg->fine_n[0] > 0 && cfg->fine_n[1] > 0 && cfg->fine_n[2] > 0 && cfg->fine_h > 0.0) {
         s->nfine = (size_t)cfg->fine_n[0] * (size_t)cfg->fine_n[1] * (size_t)cfg->fine_n[2];
@@ -1062,7 +1067,7 @@ void orc_destroy(orc_sim* s)
     free(s->rq); free(s->phi); free(s->ex); free(s->ey); free(s->ez); free(s->xs);
     free(s->gpos); free(s->grad); free(s->gq); free(s->gabs); free(s->gtab);
     free(s->cell_ng); free(s->cell_g); free(s->ch); free(s->mphi); free(s->eepf);
-    free(s->bsteps); free(s->fine[0]); free(s->fine[1]);
+    free(s->bsteps); free(s->fine[0]); free(s->fine[1]); free(s->mke[0]); free(s->mke[1]);
     free(s);
 }
 
@@ -1087,11 +1092,41 @@ void orc_get_counters(const orc_sim* s, int64_t* c) { memcpy(c, s->cnt, sizeof(i
 int64_t orc_step_index(const orc_sim* s) { return s->step; }
 uint32_t orc_next_id(const orc_sim* s) { return s->next_id; }
 
+/* window sums of bins [b0, b1) at node q for species sp: count, count v, count |v|^2 */
+static void node_sums(const orc_sim* s, int sp, int b0, int b1, size_t q, double out[5])
+{
+    const size_t N = nodes_of(s);
+    for (int a = 0; a < 5; ++a) out[a] = 0.0;
+    for (int b = b0; b < b1; ++b) {
+        const double* m = s->mom[sp] + 4 * ((size_t)b * N + q);
+        for (int a = 0; a < 4; ++a) out[a] += m[a];
+        out[4] += s->mke[sp][(size_t)b * N + q];
+    }
+}
+
+/* temperature (eV) of a species from window sums: (m / 3e) (<v^2> - |<v>|^2) */
+static double temperature(const double sum[5], double m)
+{
+    if (!(sum[0] > 0.0)) return 0.0;
+    const double u[3] = { sum[1] / sum[0], sum[2] / sum[0], sum[3] / sum[0] };
+    const double var = sum[4] / sum[0] - ((u[0] * u[0] + u[1] * u[1]) + u[2] * u[2]);
+    return (m / (3.0 * QE)) * var;
+}
+
 /* window averages of bins [b0, b1): sums over the bins' samples divided by their count */
 static int moments_of(const orc_sim* s, int what, int b0, int b1, int64_t steps, double* out)
 {
     const size_t N = nodes_of(s);
-    if (steps == 0 || what < 0 || what > 4) return -1;
+    if (steps == 0 || what < 0 || what > 6) return -1;
+    if (what >= 5) {
+        const int sp = what - 5;
+        for (size_t q = 0; q < N; ++q) {
+            double sum[5];
+            node_sums(s, sp, b0, b1, q, sum);
+            out[q] = temperature(sum, sp == 0 ? ME : MAR);
+        }
+        return 0;
+    }
     const double dx = s->c.dx;
     const double norm = s->c.weight / ((dx * dx * dx) * (double)steps);
     const size_t len = what >= 3 ? 3 * N : N;
@@ -1110,6 +1145,81 @@ static int moments_of(const orc_sim* s, int what, int b0, int b1, int64_t steps,
     }
     const double scale = what == 0 ? 1.0 / (double)steps : norm;
     for (size_t q = 0; q < len; ++q) out[q] *= scale;
+    return 0;
+}
+
+/* ---------------------------------------------------------------------------
+ * Hypothetical grain charge from local plasma moments (Sec. IV.B: the charge a
+ * grain would carry with no other grains around, from the orbital-motion-
+ * limited balance of electron and ion fluxes including the charge-exchange ion
+ * flux, with the local densities and temperatures).  Currents per pi a^2 with
+ * the mean speeds vbar_s = sqrt(8 e T_s / (pi m_s)):
+ *   phi <= 0:  J_e = n_e vbar_e exp(phi/T_e),
+ *              J_i = n_i vbar_i (1 - phi/T_i + 0.1 (phi/T_i)^2 lambda_D/l_i)
+ *   phi >  0:  J_e = n_e vbar_e (1 + phi/T_e),  J_i = n_i vbar_i exp(-phi/T_i)
+ * (the quadratic term is the weakly collisional charge-exchange correction of
+ * Khrapak et al., Phys. Rev. E 72, 016406 (2005)); J_e - J_i increases with
+ * phi and has one root, found here by bisection. */
+double orc_oml_potential(double ne, double ni, double te, double ti, double lam_over_l)
+{
+    if (!(ne > 0.0) || !(ni > 0.0) || !(te > 0.0) || !(ti > 0.0)) return NAN;
+    const double ve = sqrt((8.0 * QE * te) / (PI_D * ME));
+    const double vi = sqrt((8.0 * QE * ti) / (PI_D * MAR));
+    const double A = (ne * ve) / (ni * vi);
+    double lo, hi;
+    if (A > 1.0) { lo = -200.0 * te; hi = 0.0; }
+    else if (A < 1.0) { lo = 0.0; hi = 200.0 * ti; }
+    else return 0.0;
+    for (int it = 0; it < 400; ++it) {
+        const double mid = 0.5 * (lo + hi);
+        if (mid <= lo || mid >= hi) break;
+        double f;
+        if (mid <= 0.0) {
+            const double x = mid / ti;
+            f = A * exp(mid / te) - (1.0 - x + 0.1 * x * x * lam_over_l);
+        } else {
+            f = A * (1.0 + mid / te) - exp(-mid / ti);
+        }
+        if (f > 0.0) hi = mid; else lo = mid;
+    }
+    return 0.5 * (lo + hi);
+}
+
+int orc_oml_charges(const orc_sim* s, int with_cx, double* out)
+{
+    if (s->msteps == 0) return -1;
+    const double dx = s->c.dx;
+    const double norm = s->c.weight / ((dx * dx * dx) * (double)s->msteps);
+    for (int g = 0; g < s->c.n_grains; ++g) {
+        const double* p = s->gpos + 3 * g;
+        int c[3]; double f[3];
+        locate(s, p, c, f);
+        double sum[2][5] = {{0}};
+        for (int dz = 0; dz < 2; ++dz)
+            for (int dy = 0; dy < 2; ++dy)
+                for (int dxi = 0; dxi < 2; ++dxi) {
+                    const double w = (dxi ? f[0] : 1.0 - f[0]) * (dy ? f[1] : 1.0 - f[1]) * (dz ? f[2] : 1.0 - f[2]);
+                    const size_t q = node_at(s, c[0] + dxi, c[1] + dy, c[2] + dz);
+                    for (int sp = 0; sp < 2; ++sp) {
+                        double ns[5];
+                        node_sums(s, sp, 0, s->nph, q, ns);
+                        for (int a = 0; a < 5; ++a) sum[sp][a] += w * ns[a];
+                    }
+                }
+        const double ne = sum[0][0] * norm, ni = sum[1][0] * norm;
+        const double te = temperature(sum[0], ME), ti = temperature(sum[1], MAR);
+        double lam_l = 0.0;
+        if (with_cx && ne > 0.0 && ni > 0.0 && te > 0.0 && ti > 0.0 && s->c.n_xs > 0) {
+            const double lde2 = (EPS0 * te) / (ne * QE), ldi2 = (EPS0 * ti) / (ni * QE);
+            const double lam = 1.0 / sqrt(1.0 / lde2 + 1.0 / ldi2);
+            const double sig = xs_at(s->xs + 4 * s->c.n_xs, s->c.n_xs, s->c.de_i, 1.5 * ti);
+            lam_l = lam * (s->c.n_gas * sig);
+        }
+        const double phi = orc_oml_potential(ne, ni, te, ti, lam_l);
+        double* o = out + 6 * g;
+        o[0] = 4.0 * PI_D * EPS0 * s->grad[g] * phi;
+        o[1] = phi; o[2] = ne; o[3] = ni; o[4] = te; o[5] = ti;
+    }
     return 0;
 }
 
@@ -1166,6 +1276,8 @@ void orc_reset_moments(orc_sim* s)
     memset(s->mom[0], 0, sizeof(double) * 4 * N);
     memset(s->mom[1], 0, sizeof(double) * 4 * N);
     memset(s->mphi, 0, sizeof(double) * N);
+    memset(s->mke[0], 0, sizeof(double) * N);
+    memset(s->mke[1], 0, sizeof(double) * N);
     memset(s->bsteps, 0, sizeof(int64_t) * (size_t)s->nph);
     if (s->nfine) {
         memset(s->fine[0], 0, sizeof(double) * 4 * s->nfine);

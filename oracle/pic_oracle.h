@@ -82,13 +82,24 @@ void     orc_set_gtab(orc_sim* s, const double* tab);
 void     orc_get_counters(const orc_sim* s, int64_t* c /* ORC_C_N */);
 int64_t  orc_step_index(const orc_sim* s);
 uint32_t orc_next_id(const orc_sim* s);
-/* what: 0 phi, 1 n_e, 2 n_i, 3 flux_e (3 per node), 4 flux_i; window averages */
+/* what: 0 phi, 1 n_e, 2 n_i, 3 flux_e (3 per node), 4 flux_i, 5 T_e, 6 T_i (eV, the
+ * temperature of the window's node-weighted velocity distribution); window averages */
 int      orc_moments(const orc_sim* s, int what, double* out);
 /* the same for the samples of rf phase bin `bin` only; *steps = samples in that bin */
 int      orc_moments_phase(const orc_sim* s, int what, int bin, double* out, int64_t* steps);
 /* fine grid, what: 1 n_e, 2 n_i (per fine cell), 3 flux_e, 4 flux_i (3 per fine cell) */
 int      orc_fine_moments(const orc_sim* s, int what, double* out);
 void     orc_reset_moments(orc_sim* s);
+/* OML surface potential (V) of an isolated sphere in a plasma of densities ne,
+ * ni (m^-3) and temperatures te, ti (eV) of electrons and Ar+, with the
+ * charge-exchange ion flux term 0.1 (e phi / T_i)^2 lambda_D / l_i given by
+ * lam_over_l = lambda_D / l_i (0: collisionless OML); NaN if a density or a
+ * temperature is not positive */
+double   orc_oml_potential(double ne, double ni, double te, double ti, double lam_over_l);
+/* per grain 6 values from the moment window: Q = 4 pi eps0 a phi (C), phi (V),
+ * and the local n_e, n_i (m^-3), T_e, T_i (eV) at the grain centre; with_cx
+ * adds the charge-exchange ion flux.  Returns -1 without ORC_MOMENTS samples. */
+int      orc_oml_charges(const orc_sim* s, int with_cx, double* out);
 /* test helpers: field acting on a particle at p (Eqs. 4-6, with the MD
  * correction when p's cell is in an MD region); set the grains' absorbed
  * counts, which redeposits rho and re-solves phi at the current time */
