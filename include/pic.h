@@ -214,8 +214,10 @@ pic_status pic_eepf_fit(const int64_t* counts, int32_t nbins, double de_ev, doub
 /* Window averages since the last reset (needs PIC_F_MOMENTS), sampled after
  * every step (positions at t = step dt, the velocities of the step, phi of the
  * step's solve): what 0 phi (V, nodes), 1 n_e, 2 n_i (m^-3, nodes, CIC
- * weights), 3 flux_e, 4 flux_i (m^-2 s^-1, 3 per node, node-major).  len =
- * number of doubles in out_host.  reset != 0 then clears every moment window
+ * weights), 3 flux_e, 4 flux_i (m^-2 s^-1, 3 per node, node-major), 5 T_e,
+ * 6 T_i (eV per node: (m/3e)(<v^2> - |<v>|^2) of the window's CIC-weighted
+ * velocities, 0 where no particle reached the node).  len = number of doubles
+ * in out_host.  reset != 0 then clears every moment window
  * (rf average, phase bins and the fine grid). */
 pic_status pic_moments(pic_ctx* ctx, int32_t what, double* out_host, size_t len, int32_t reset);
 
@@ -226,6 +228,17 @@ pic_status pic_moments(pic_ctx* ctx, int32_t what, double* out_host, size_t len,
  * samples in that bin.  PIC_EINVAL for a bin out of range or an empty bin. */
 pic_status pic_moments_phase(pic_ctx* ctx, int32_t what, int32_t bin, double* out_host, size_t len,
                              int64_t* steps_out);
+
+/* Hypothetical charge of every grain with no other grains around (Sec. IV.B,
+ * Fig. 7): the orbital-motion-limited balance of electron and ion currents,
+ * with (with_cx != 0) the charge-exchange ion current 0.1 (e phi/T_i)^2
+ * lambda_D/l_i of the weakly collisional model of Khrapak et al. (2005), from
+ * the window's n, <v>, <v^2> CIC-interpolated to the grain centre; l_i from
+ * n_gas and the charge-exchange table at 3/2 T_i.  out_host: 6 doubles per
+ * grain, Q = 4 pi eps0 a phi (C), phi (V), n_e, n_i (m^-3), T_e, T_i (eV); Q
+ * and phi are NaN where a local density or temperature is not positive.
+ * Needs PIC_F_MOMENTS and a non-empty window; len = 6 * grains. */
+pic_status pic_oml_charges(pic_ctx* ctx, int32_t with_cx, double* out_host, size_t len);
 
 /* Window averages on the fine grid (needs fine_n): what 1 n_e, 2 n_i (m^-3 per
  * fine cube), 3 flux_e, 4 flux_i (m^-2 s^-1, 3 per cube); cube (i, j, k) at

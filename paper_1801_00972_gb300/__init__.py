@@ -32,7 +32,7 @@ PIC_C_N = len(COUNTERS)
 
 # every symbol include/pic.h declares
 SYMBOLS = ("pic_init", "pic_step", "pic_tune_sort", "pic_advance", "pic_solve", "pic_grain_charges", "pic_counts",
-           "pic_moments", "pic_moments_phase", "pic_fine_moments", "pic_eepf", "pic_eepf_fit", "pic_get_particles", "pic_get_rho", "pic_get_phi", "pic_set_phi",
+           "pic_moments", "pic_moments_phase", "pic_fine_moments", "pic_oml_charges", "pic_eepf", "pic_eepf_fit", "pic_get_particles", "pic_get_rho", "pic_get_phi", "pic_set_phi",
            "pic_get_grain_table", "pic_set_grain_table", "pic_set_grain_counts", "pic_step_index",
            "pic_profile", "pic_profile_read", "pic_solve_noalloc", "pic_batch_init", "pic_batch_step",
            "pic_batch_run", "pic_batch_destroy", "pic_last_error", "pic_destroy")
@@ -92,7 +92,7 @@ def load(path: str | None = None):
             "pic_step": [vp, i32], "pic_tune_sort": [vp, i32, C.POINTER(i32)], "pic_advance": [vp], "pic_solve": [vp, C.POINTER(i32), pd],
             "pic_grain_charges": [vp, pi64, pd], "pic_counts": [vp, pi64, pi64],
             "pic_moments": [vp, i32, pd, sz, i32], "pic_moments_phase": [vp, i32, i32, pd, sz, pi64],
-            "pic_fine_moments": [vp, i32, pd, sz],
+            "pic_fine_moments": [vp, i32, pd, sz], "pic_oml_charges": [vp, i32, pd, sz],
             "pic_eepf": [vp, pi64, sz, pi64, i32], "pic_eepf_fit": [pi64, i32, C.c_double, C.c_double, C.c_double, pd],
             "pic_get_particles": [vp, i32, pd, pd, pu32, i64, pi64],
             "pic_get_rho": [vp, pi64, sz], "pic_get_phi": [vp, pd, sz], "pic_set_phi": [vp, pd, sz],
@@ -200,17 +200,24 @@ def pic_eepf_fit(counts, de_ev, e_lo_ev, e_hi_ev):
 
 
 def pic_moments(ctx, what, nodes, reset=False):
-    out = np.zeros(nodes * (3 if what >= 3 else 1))
+    out = np.zeros(nodes * (3 if what in (3, 4) else 1))
     _check(ctx, load().pic_moments(ctx, int(what), _p(out, C.c_double), out.size, int(bool(reset))))
     return out
 
 
 def pic_moments_phase(ctx, what, bin, nodes):
     """(window average over the samples of rf phase bin ``bin``, samples in it)."""
-    out = np.zeros(nodes * (3 if what >= 3 else 1))
+    out = np.zeros(nodes * (3 if what in (3, 4) else 1))
     steps = C.c_int64()
     _check(ctx, load().pic_moments_phase(ctx, int(what), int(bin), _p(out, C.c_double), out.size, C.byref(steps)))
     return out, int(steps.value)
+
+
+def pic_oml_charges(ctx, ng, with_cx=True):
+    """Per grain (Q [C], phi [V], n_e, n_i [m^-3], T_e, T_i [eV]) from the moment window."""
+    out = np.zeros(6 * max(ng, 1))
+    _check(ctx, load().pic_oml_charges(ctx, int(bool(with_cx)), _p(out, C.c_double), 6 * ng))
+    return out[: 6 * ng].reshape(ng, 6)
 
 
 def pic_fine_moments(ctx, what, fine_n):
@@ -443,6 +450,9 @@ class Run:
 
     def moments_phase(self, what, bin):
         return pic_moments_phase(self.ctx, what, bin, self.nodes)
+
+    def oml_charges(self, with_cx=True):
+        return pic_oml_charges(self.ctx, self.ng, with_cx)
 
     def fine_moments(self, what):
         return pic_fine_moments(self.ctx, what, self.fine_n)

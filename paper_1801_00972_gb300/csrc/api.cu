@@ -73,12 +73,13 @@ pic_status cuda_fail(pic_ctx* c, cudaError_t e, const char* what)
 cudaError_t clear_moments(pic_ctx* c, cudaStream_t st)
 {
     const size_t nb = (size_t)c->nph;
-    const size_t sz[6] = {sizeof(double) * 4 * c->nodes * nb, sizeof(double) * 4 * c->nodes * nb,
+    const size_t sz[8] = {sizeof(double) * 4 * c->nodes * nb, sizeof(double) * 4 * c->nodes * nb,
                           sizeof(double) * c->nodes * nb, sizeof(unsigned long long) * nb,
-                          sizeof(double) * 4 * c->nfine, sizeof(double) * 4 * c->nfine};
-    void* p[6] = {c->mom[0], c->mom[1], c->mphi, c->d_bsteps, c->fine[0], c->fine[1]};
+                          sizeof(double) * 4 * c->nfine, sizeof(double) * 4 * c->nfine,
+                          sizeof(double) * c->nodes * nb, sizeof(double) * c->nodes * nb};
+    void* p[8] = {c->mom[0], c->mom[1], c->mphi, c->d_bsteps, c->fine[0], c->fine[1], c->mke[0], c->mke[1]};
     cudaError_t e = cudaSuccess;
-    for (int q = 0; q < 6 && e == cudaSuccess; ++q)
+    for (int q = 0; q < 8 && e == cudaSuccess; ++q)
         if (p[q]) e = st ? cudaMemsetAsync(p[q], 0, sz[q], st) : cudaMemset(p[q], 0, sz[q]);
     return e;
 }
@@ -96,6 +97,29 @@ void launch_moments_all(pic_ctx* c)
 // averages of phase bins [b0, b1) over `steps` samples into out (layout of pic_moments)
 pic_status moments_window(pic_ctx* c, int what, int b0, int b1, int64_t steps, double* out)
 {
+    if (what >= 5) {
+        // temperature (eV) of the window's node-weighted velocities: (m / 3e) (<v^2> - |<v>|^2)
+        const int sp = what - 5;
+        const size_t N = c->nodes, nb = (size_t)(b1 - b0);
+        std::vector<double> m(4 * N * nb), k(N * nb);
+        cudaError_t e = cudaMemcpy(m.data(), c->mom[sp] + 4 * N * (size_t)b0, sizeof(double) * m.size(),
+                                   cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess)
+            e = cudaMemcpy(k.data(), c->mke[sp] + N * (size_t)b0, sizeof(double) * k.size(), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return cuda_fail(c, e, "moments copy");
+        const double m3e = (2.0 / 3.0) * c->hm[sp];
+        for (size_t q = 0; q < N; ++q) {
+            double s[5] = {0, 0, 0, 0, 0};
+            for (size_t b = 0; b < nb; ++b) {
+                for (int a = 0; a < 4; ++a) s[a] += m[4 * (b * N + q) + a];
+                s[4] += k[b * N + q];
+            }
+            if (!(s[0] > 0.0)) { out[q] = 0.0; continue; }
+            const double u0 = s[1] / s[0], u1 = s[2] / s[0], u2 = s[3] / s[0];
+            out[q] = m3e * (s[4] / s[0] - ((u0 * u0 + u1 * u1) + u2 * u2));
+        }
+        return PIC_OK;
+    }
     const size_t N = c->nodes, len = (what >= 3 ? 3 : 1) * N, w = what == 0 ? 1 : 4;
     std::vector<double> m(w * N * (size_t)(b1 - b0));
     const double* src = what == 0 ? c->mphi : c->mom[(what - 1) % 2];
@@ -437,9 +461,12 @@ pic_status pic_init(const pic_mesh* mesh, const pic_electrodes* el, const pic_ga
         c->mom[0] = (double*)dev_alloc(c, sizeof(double) * 4 * nodes * nb);
         c->mom[1] = (double*)dev_alloc(c, sizeof(double) * 4 * nodes * nb);
         c->mphi = (double*)dev_alloc(c, sizeof(double) * nodes * nb);
+        c->mke[0] = (double*)dev_alloc(c, sizeof(double) * nodes * nb);
+        c->mke[1] = (double*)dev_alloc(c, sizeof(double) * nodes * nb);
         c->d_bin = (int*)dev_alloc(c, sizeof(int));
         c->d_bsteps = (unsigned long long*)dev_alloc(c, sizeof(unsigned long long) * nb);
-        ok = ok && c->mom[0] && c->mom[1] && c->mphi && c->d_bin && c->d_bsteps;
+        c->d_oml = (double*)dev_alloc(c, sizeof(double) * 6 * (size_t)std::max(c->ng, 1));
+        ok = ok && c->mom[0] && c->mom[1] && c->mphi && c->mke[0] && c->mke[1] && c->d_bin && c->d_bsteps && c->d_oml;
         if (c->nfine) {
             c->fine[0] = (double*)dev_alloc(c, sizeof(double) * 4 * c->nfine);
             c->fine[1] = (double*)dev_alloc(c, sizeof(double) * 4 * c->nfine);
@@ -1216,8 +1243,8 @@ pic_status pic_moments(pic_ctx* c, int32_t what, double* out, size_t len, int32_
 {
     if (!c) return PIC_EINVAL;
     if (!(c->flags & PIC_F_MOMENTS)) return fail(c, PIC_EINVAL, "moments need PIC_F_MOMENTS at init");
-    if (what < 0 || what > 4) return fail(c, PIC_EINVAL, "moments: what in 0..4");
-    if (!out || len != (what >= 3 ? 3 : 1) * c->nodes) return fail(c, PIC_EINVAL, "moments length");
+    if (what < 0 || what > 6) return fail(c, PIC_EINVAL, "moments: what in 0..6");
+    if (!out || len != (what == 3 || what == 4 ? 3 : 1) * c->nodes) return fail(c, PIC_EINVAL, "moments length");
     pic_status k = check(c);
     if (k != PIC_OK) return k;
     if (c->msteps == 0) return fail(c, PIC_EINVAL, "moments: empty window");
@@ -1235,9 +1262,9 @@ pic_status pic_moments_phase(pic_ctx* c, int32_t what, int32_t bin, double* out,
 {
     if (!c) return PIC_EINVAL;
     if (!(c->flags & PIC_F_MOMENTS)) return fail(c, PIC_EINVAL, "moments need PIC_F_MOMENTS at init");
-    if (what < 0 || what > 4 || bin < 0 || bin >= c->nph)
-        return fail(c, PIC_EINVAL, "moments_phase: what in 0..4, bin in [0, mom_phases)");
-    if (!out || len != (what >= 3 ? 3 : 1) * c->nodes) return fail(c, PIC_EINVAL, "moments length");
+    if (what < 0 || what > 6 || bin < 0 || bin >= c->nph)
+        return fail(c, PIC_EINVAL, "moments_phase: what in 0..6, bin in [0, mom_phases)");
+    if (!out || len != (what == 3 || what == 4 ? 3 : 1) * c->nodes) return fail(c, PIC_EINVAL, "moments length");
     pic_status k = check(c);
     if (k != PIC_OK) return k;
     int64_t steps = c->msteps;
@@ -1250,6 +1277,22 @@ pic_status pic_moments_phase(pic_ctx* c, int32_t what, int32_t bin, double* out,
     if (steps_out) *steps_out = steps;
     if (steps == 0) return fail(c, PIC_EINVAL, "moments_phase: no samples in this bin");
     return moments_window(c, what, bin, bin + 1, steps, out);
+}
+
+pic_status pic_oml_charges(pic_ctx* c, int32_t with_cx, double* out, size_t len)
+{
+    if (!c) return PIC_EINVAL;
+    if (!(c->flags & PIC_F_MOMENTS)) return fail(c, PIC_EINVAL, "oml_charges needs PIC_F_MOMENTS at init");
+    if ((c->ng > 0 && !out) || len != 6 * (size_t)c->ng) return fail(c, PIC_EINVAL, "oml_charges length");
+    pic_status k = check(c);
+    if (k != PIC_OK) return k;
+    if (c->msteps == 0) return fail(c, PIC_EINVAL, "moments: empty window");
+    if (c->ng == 0) return PIC_OK;
+    launch_oml(c, with_cx != 0, c->d_oml);
+    cudaError_t e = cudaMemcpyAsync(out, c->d_oml, sizeof(double) * len, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "oml_charges");
+    return check(c);
 }
 
 pic_status pic_fine_moments(pic_ctx* c, int32_t what, double* out, size_t len)

@@ -141,6 +141,123 @@ __global__ void k_fine32(FineBox f, double dx, double vs, const float4* __restri
     }
 }
 
+// Hypothetical charge of each grain with no other grains around (Sec. IV.B):
+// the orbital-motion-limited balance of electron and ion currents with the
+// charge-exchange ion current, from the local moments.  Currents per pi a^2,
+// mean speeds vbar = sqrt(8 e T / (pi m)), x = phi / T_i:
+//   phi <= 0: J_e = n_e vbar_e exp(phi/T_e),  J_i = n_i vbar_i (1 - x + 0.1 x^2 lambda_D / l_i)
+//   phi >  0: J_e = n_e vbar_e (1 + phi/T_e), J_i = n_i vbar_i exp(-x)
+// (the quadratic term: weakly collisional charge exchange, Khrapak et al.,
+// Phys. Rev. E 72, 016406 (2005)); lambda_D = (lambda_De^-2 + lambda_Di^-2)^-1/2,
+// l_i = 1 / (n_gas sigma_cx(3/2 T_i)).  The local n, <v>, <v^2> are the
+// window sums CIC-interpolated to the grain centre; phi solves J_e = J_i by a
+// bracketed Newton iteration; Q = 4 pi eps0 a phi.
+struct OmlArgs {
+    const double* mom[2];
+    const double* mke[2];
+    const double* gpos;
+    const double* grad;
+    const double* xs_cx;
+    int n_xs, ng, nph, nx, ny, nz;
+    size_t nodes;
+    double dx, norm, de_i, n_gas, m3e[2];
+    int with_cx;
+};
+
+// J_e - J_i over n_i vbar_i and its derivative in phi
+__device__ void oml_balance(double phi, double A, double te, double ti, double lam_l, double& f, double& df)
+{
+    if (phi <= 0.0) {
+        const double x = phi / ti;
+        const double ee = A * exp(phi / te);
+        f = ee - (1.0 - x + 0.1 * x * x * lam_l);
+        df = ee / te + (1.0 - 0.2 * x * lam_l) / ti;
+    } else {
+        const double ei = exp(-phi / ti);
+        f = A * (1.0 + phi / te) - ei;
+        df = A / te + ei / ti;
+    }
+}
+
+__global__ void k_oml(OmlArgs a, double* out)
+{
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= a.ng) return;
+    const double p[3] = {a.gpos[3 * g], a.gpos[3 * g + 1], a.gpos[3 * g + 2]};
+    const int nn[3] = {a.nx, a.ny, a.nz};
+    int c[3];
+    double f[3];
+    for (int d = 0; d < 3; ++d) {
+        const double q = p[d] / a.dx;
+        int i = (int)floor(q);
+        i = i > nn[d] - 1 ? nn[d] - 1 : (i < 0 ? 0 : i);
+        c[d] = i;
+        f[d] = q - (double)i;
+    }
+    double s[2][5] = {{0, 0, 0, 0, 0}, {0, 0, 0, 0, 0}};
+    for (int dz = 0; dz < 2; ++dz)
+        for (int dy = 0; dy < 2; ++dy)
+            for (int di = 0; di < 2; ++di) {
+                const double w = (di ? f[0] : 1.0 - f[0]) * (dy ? f[1] : 1.0 - f[1]) * (dz ? f[2] : 1.0 - f[2]);
+                const int i = (c[0] + di) % a.nx, j = (c[1] + dy) % a.ny, k = c[2] + dz;
+                const size_t node = ((size_t)k * a.ny + j) * a.nx + i;
+                for (int sp = 0; sp < 2; ++sp) {
+                    double t[5] = {0, 0, 0, 0, 0};
+                    for (int b = 0; b < a.nph; ++b) {
+                        const double* m = a.mom[sp] + 4 * ((size_t)b * a.nodes + node);
+                        t[0] += m[0]; t[1] += m[1]; t[2] += m[2]; t[3] += m[3];
+                        t[4] += a.mke[sp][(size_t)b * a.nodes + node];
+                    }
+                    for (int q = 0; q < 5; ++q) s[sp][q] += w * t[q];
+                }
+            }
+    double n[2], T[2];
+    for (int sp = 0; sp < 2; ++sp) {
+        n[sp] = s[sp][0] * a.norm;
+        if (s[sp][0] > 0.0) {
+            const double u0 = s[sp][1] / s[sp][0], u1 = s[sp][2] / s[sp][0], u2 = s[sp][3] / s[sp][0];
+            T[sp] = a.m3e[sp] * (s[sp][4] / s[sp][0] - ((u0 * u0 + u1 * u1) + u2 * u2));
+        } else {
+            T[sp] = 0.0;
+        }
+    }
+    double phi = nan("");
+    if (n[0] > 0.0 && n[1] > 0.0 && T[0] > 0.0 && T[1] > 0.0) {
+        double lam_l = 0.0;
+        if (a.with_cx && a.n_xs > 1) {
+            const double lde2 = (kEPS0 * T[0]) / (n[0] * kQE), ldi2 = (kEPS0 * T[1]) / (n[1] * kQE);
+            const double lam = 1.0 / sqrt(1.0 / lde2 + 1.0 / ldi2);
+            const double t = (1.5 * T[1]) / a.de_i;
+            double sig;
+            if (t >= (double)(a.n_xs - 1)) {
+                sig = a.xs_cx[a.n_xs - 1];
+            } else {
+                const int i = (int)t;
+                sig = a.xs_cx[i] + (t - (double)i) * (a.xs_cx[i + 1] - a.xs_cx[i]);
+            }
+            lam_l = lam * (a.n_gas * sig);
+        }
+        const double ve = sqrt((8.0 * kQE * T[0]) / (kPI * kME));
+        const double vi = sqrt((8.0 * kQE * T[1]) / (kPI * kMAR));
+        const double A = (n[0] * ve) / (n[1] * vi);
+        double lo = A > 1.0 ? -200.0 * T[0] : 0.0, hi = A > 1.0 ? 0.0 : 200.0 * T[1];
+        phi = A == 1.0 ? 0.0 : 0.5 * (lo + hi);
+        for (int it = 0; it < 200 && A != 1.0; ++it) {
+            double fv, dfv;
+            oml_balance(phi, A, T[0], T[1], lam_l, fv, dfv);
+            if (fv > 0.0) hi = phi; else lo = phi;
+            double nxt = phi - fv / dfv;
+            if (!(nxt > lo && nxt < hi)) nxt = 0.5 * (lo + hi);   // outside the bracket: bisect
+            if (nxt == phi || hi - lo <= 4e-16 * fmax(fabs(lo), fabs(hi))) { phi = nxt; break; }
+            phi = nxt;
+        }
+    }
+    double* o = out + 6 * g;
+    o[0] = 4.0 * kPI * kEPS0 * a.grad[g] * phi;
+    o[1] = phi;
+    o[2] = n[0]; o[3] = n[1]; o[4] = T[0]; o[5] = T[1];
+}
+
 // weighted least squares y = a + s x; false without two distinct abscissae
 bool line_fit(const std::vector<double>& x, const std::vector<double>& y, const std::vector<double>& w, size_t lo,
               size_t hi, double& a, double& s)
@@ -176,6 +293,23 @@ void launch_eepf(pic_ctx* c)
 void launch_phase_bin(pic_ctx* c)
 {
     k_phase_bin<<<1, 1, 0, c->stream>>>(c->d_step, c->f_rf, c->dt, c->rf_phase, c->nph, c->d_bin, c->d_bsteps);
+    c->launches += 1;
+}
+
+void launch_oml(pic_ctx* c, int with_cx, double* out)
+{
+    OmlArgs a;
+    for (int sp = 0; sp < 2; ++sp) {
+        a.mom[sp] = c->mom[sp];
+        a.mke[sp] = c->mke[sp];
+        a.m3e[sp] = (2.0 / 3.0) * c->hm[sp];
+    }
+    a.gpos = c->gpos; a.grad = c->grad; a.xs_cx = c->xs64 + 4 * (size_t)c->n_xs;
+    a.n_xs = c->n_xs; a.ng = c->ng; a.nph = c->nph; a.nx = c->nx; a.ny = c->ny; a.nz = c->nz;
+    a.nodes = c->nodes; a.dx = c->dx;
+    a.norm = c->W / ((c->dx * c->dx * c->dx) * (double)c->msteps);
+    a.de_i = c->de[1]; a.n_gas = c->n_gas; a.with_cx = with_cx;
+    k_oml<<<(c->ng + 127) / 128, 128, 0, c->stream>>>(a, out);
     c->launches += 1;
 }
 

@@ -584,15 +584,17 @@ __global__ void k_grain_table(int nx, int ny, int nz, double dx, const double* p
 // node moments: CIC sums of 1 and v per species (double atomics), into the
 // slice of the sample's rf phase bin
 __global__ void k_moments64(Geo g, const double4* pos, const double4* vel, const unsigned long long* nslot, int sp,
-                            double* mom, const int* bin, size_t stride)
+                            double* mom, double* mke, const int* bin, size_t nodes)
 {
     const unsigned long long n = nslot[sp];
-    mom += (size_t)*bin * stride;
+    mom += (size_t)*bin * 4 * nodes;
+    mke += (size_t)*bin * nodes;
     for (unsigned long long q = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; q < n;
          q += (unsigned long long)gridDim.x * blockDim.x) {
         const double4 P = pos[q];
         if (P.w < 0.0) continue;
         const double4 V = vel[q];
+        const double v2 = (V.x * V.x + V.y * V.y) + V.z * V.z;
         const double x[3] = {P.x, P.y, P.z};
         int c[3];
         double f[3];
@@ -604,11 +606,13 @@ __global__ void k_moments64(Geo g, const double4* pos, const double4* vel, const
                 for (int di = 0; di < 2; ++di) {
                     const double wt = (double)(w[0][di] * w[1][dy] * w[2][dz]) * 0x1p-42;
                     if (wt == 0.0) continue;
-                    double* m = mom + 4 * node_at(g, c[0] + di, c[1] + dy, c[2] + dz);
+                    const size_t node = node_at(g, c[0] + di, c[1] + dy, c[2] + dz);
+                    double* m = mom + 4 * node;
                     atomicAdd(m, wt);
                     atomicAdd(m + 1, wt * V.x);
                     atomicAdd(m + 2, wt * V.y);
                     atomicAdd(m + 3, wt * V.z);
+                    atomicAdd(mke + node, wt * v2);
                 }
     }
 }
@@ -693,8 +697,8 @@ void launch_moments64(pic_ctx* c)
 {
     for (int sp = 0; sp < 2; ++sp)
         k_moments64<<<grid_for(c->cap[sp], 256, 152 * 8), 256, 0, c->stream>>>(
-            geo(c), (const double4*)c->pos[sp], (const double4*)c->vel[sp], c->d_nslot, sp, c->mom[sp], c->d_bin,
-            4 * c->nodes);
+            geo(c), (const double4*)c->pos[sp], (const double4*)c->vel[sp], c->d_nslot, sp, c->mom[sp], c->mke[sp],
+            c->d_bin, c->nodes);
     c->launches += 2;
 }
 

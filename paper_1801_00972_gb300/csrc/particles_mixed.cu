@@ -870,10 +870,12 @@ __global__ void k_children_finish32(unsigned long long* nch, unsigned long long 
 }
 
 __global__ void k_moments32(int nx, int ny, float vs, const float4* pos, const float4* vel,
-                            const unsigned long long* nslot, int sp, double* mom, const int* bin, size_t stride)
+                            const unsigned long long* nslot, int sp, double* mom, double* mke, const int* bin,
+                            size_t nodes)
 {
     const unsigned long long n = nslot[sp];
-    mom += (size_t)*bin * stride;   // the sample's rf phase bin
+    mom += (size_t)*bin * 4 * nodes;   // the sample's rf phase bin
+    mke += (size_t)*bin * nodes;
     for (unsigned long long q = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; q < n;
          q += (unsigned long long)gridDim.x * blockDim.x) {
         const float4 P = pos[q];
@@ -887,6 +889,7 @@ __global__ void k_moments32(int nx, int ny, float vs, const float4* pos, const f
         long long val[8];
         corners(nx, ny, i, j, k, a, 1, node, val);
         const double vx = (double)V.x * vs, vy = (double)V.y * vs, vz = (double)V.z * vs;
+        const double v2 = (vx * vx + vy * vy) + vz * vz;
         for (int c = 0; c < 8; ++c) {
             const double wt = (double)val[c] * 0x1p-42;
             if (wt == 0.0) continue;
@@ -895,6 +898,7 @@ __global__ void k_moments32(int nx, int ny, float vs, const float4* pos, const f
             atomicAdd(m + 1, wt * vx);
             atomicAdd(m + 2, wt * vy);
             atomicAdd(m + 3, wt * vz);
+            atomicAdd(mke + node[c], wt * v2);
         }
     }
 }
@@ -1021,7 +1025,7 @@ void launch_moments32(pic_ctx* c)
     for (int sp = 0; sp < 2; ++sp)
         k_moments32<<<grid_for(c->cap[sp], 256, 152 * 8), 256, 0, c->stream>>>(
             c->nx, c->ny, (float)(c->dx / c->dt), (const float4*)c->pos[sp], (const float4*)c->vel[sp], c->d_nslot,
-            sp, c->mom[sp], c->d_bin, 4 * c->nodes);
+            sp, c->mom[sp], c->mke[sp], c->d_bin, c->nodes);
     c->launches += 2;
 }
 

@@ -252,6 +252,8 @@ struct pic_ctx {
     // moments
     double* mom[2] = {nullptr, nullptr};     // nph * 4 * nodes each: [phase bin][node][n, n vx, n vy, n vz]
     double* mphi = nullptr;                  // nph * nodes
+    double* mke[2] = {nullptr, nullptr};     // nph * nodes each: sum of n |v|^2
+    double* d_oml = nullptr;                 // 6 per grain: hypothetical-charge estimate
     int64_t msteps = 0;
     int nph = 1;                             // rf phase bins of the moments
     double f_rf = 0.0, rf_phase = 0.0;
@@ -304,6 +306,7 @@ void scan_cells(pic_ctx* c, unsigned int* data);   // exclusive scan of one valu
 void launch_eepf(pic_ctx* c);                       // add this step's electrons to the energy histogram
 void launch_phase_bin(pic_ctx* c);                  // phase bin of this step's moment sample
 void launch_fine(pic_ctx* c);                       // add this step's particles to the fine grid
+void launch_oml(pic_ctx* c, int with_cx, double* out);   // 6 values per grain from the moment window
 
 // coulomb.cu (built without fused multiply-add)
 void launch_coulomb(pic_ctx* c);                    // binary Coulomb collisions of the step's particles

@@ -110,3 +110,4 @@ def test_null_context_rejected(lib):
     assert lib.pic_advance(None) == P.PIC_EINVAL
     assert lib.pic_moments_phase(None, 0, 0, None, 0, None) == P.PIC_EINVAL
     assert lib.pic_fine_moments(None, 1, None, 0) == P.PIC_EINVAL
+    assert lib.pic_oml_charges(None, 1, None, 0) == P.PIC_EINVAL

@@ -410,3 +410,39 @@ def test_phase_moments_and_fine_grid_match_oracle(prec):
             got.append(0)
     assert sorted(got) == [0, 0, 0, 1]
     assert run.fine_moments(2).sum() > 0
+
+
+@pytest.mark.parametrize("prec", [P.PIC_FP64, P.PIC_MIXED])
+def test_temperatures_and_oml_charges_match_oracle(prec):
+    # 6 steps per rf period: two samples in each of 3 phase bins
+    wl = I.small(nx=8, ny=8, nz=16, n_e=30000, n_i=30000, grains=3, v_dc=-20.0, v_rf=15.0, f_rf=1.0 / 6e-10,
+                 phase=0.1, te_ev=2.0, ti_ev=0.05)
+    parts = I.sample_particles(wl)
+    ref = O.Sim(wl, parts, flags=O.MOMENTS, mom_phases=3)
+    run = P.Run(wl, parts, prec=prec, flags=P.PIC_F_MOMENTS, stream=_stream(), mom_phases=3)
+    for _ in range(6):
+        ref.step()
+        run.step()
+    fp64 = prec == P.PIC_FP64
+    for what in (5, 6):
+        tg, to = run.moments(what), ref.moments(what)
+        n = ref.moments(what - 4)
+        w = n / n.sum()
+        # node temperatures weighted by density (empty nodes carry no temperature)
+        err = np.sum(w * np.abs(tg - to)) / np.sum(w * np.abs(to))
+        assert err <= (1e-6 if fp64 else 2e-2), (what, err)
+        for b in range(3):
+            tb, _ = run.moments_phase(what, b)
+            tob, _ = ref.moments_phase(what, b)
+            err = np.sum(w * np.abs(tb - tob)) / np.sum(w * np.abs(tob))
+            assert err <= (1e-6 if fp64 else 5e-2), (what, b, err)
+    for cx in (False, True):
+        qg = run.oml_charges(with_cx=cx)
+        qo = ref.oml_charges(with_cx=cx)
+        assert qg.shape == qo.shape == (3, 6)
+        assert np.all(np.isfinite(qo))
+        tol = 1e-6 if fp64 else 5e-2
+        assert np.allclose(qg, qo, rtol=tol, atol=0), (cx, qg, qo)
+        assert np.all(qg[:, 0] < 0)        # negative grains in this electron-rich bulk
+    # the charge-exchange current makes the estimate less negative
+    assert np.all(run.oml_charges(True)[:, 1] > run.oml_charges(False)[:, 1])
