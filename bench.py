@@ -40,6 +40,7 @@ TUNE_STEPS = 20      # steps per candidate interval of the sort autotuner
 # residual and update (40 B)
 BYTES_NODE_MIXED = 74 + 40
 BYTES_NODE_FP64 = 148 + 40
+DIAG_PHASES = 16           # rf phase bins of the diagnostics run
 
 
 def poisson_block(pr, cold, wl, bytes_node, peak, peak_kind, precision):
@@ -69,6 +70,7 @@ def args():
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="fixed sort interval (no autotuning)")
     ap.add_argument("--no-coulomb", action="store_true", help="skip the run with Coulomb collisions")
+    ap.add_argument("--no-diag", action="store_true", help="skip the run with every diagnostic on")
     return ap.parse_args()
 
 
@@ -134,9 +136,9 @@ class Clocks:
                 "samples": len(sm)}
 
 
-def run_gpu(P, I, wl, parts, prec, steps, warmup, stream, gpu, flags=0, tune=True, sort_every=SORT_EVERY):
+def run_gpu(P, I, wl, parts, prec, steps, warmup, stream, gpu, flags=0, tune=True, sort_every=SORT_EVERY, **run_kw):
     import torch
-    run = P.Run(wl, parts, prec=prec, stream=stream, sort_every=sort_every, flags=flags)
+    run = P.Run(wl, parts, prec=prec, stream=stream, sort_every=sort_every, flags=flags, **run_kw)
     run.step(warmup)
     # sort interval autotuned on the run itself before the timed region
     sort_every = run.tune_sort(TUNE_STEPS) if tune else sort_every
@@ -335,6 +337,18 @@ def main():
         # the same step with the binary Coulomb collisions of Table I switched on
         coul = run_gpu(P, I, wl, parts, P.PIC_MIXED, max(a.steps // 4, 20), a.warmup, stream, local,
                        flags | P.PIC_F_COULOMB, tune=False, sort_every=mixed["sort_every"])
+    diag = None
+    if not a.no_diag:
+        # the same step with every diagnostic of Sec. IV on: node moments with
+        # temperatures in 16 rf phase bins, the 200^3 fine grid of 0.08 dx cubes
+        # on the grain cluster, and the per-plane EEPF
+        import numpy as np
+        h = 0.08 * wl.dx
+        centre = np.asarray(wl.grain_pos).mean(0)
+        diag = run_gpu(P, I, wl, parts, P.PIC_MIXED, max(a.steps // 4, 20), a.warmup, stream, local,
+                       flags | P.PIC_F_MOMENTS, tune=False, sort_every=mixed["sort_every"], mom_phases=DIAG_PHASES,
+                       fine_n=(200, 200, 200), fine_h=h, fine_origin=tuple(centre - 100 * h), eepf_bins=200,
+                       eepf_de_ev=0.1)
     bb = None if (a.no_batch or world > 1) else batch_bench(P, I, max(a.steps // 4, 10), a.warmup)
 
     def agg(x):
@@ -408,6 +422,14 @@ def main():
                            "steps": cs, "ms_per_step": coul["ms"] / cs,
                            "extra_ms_per_step": coul["ms"] / cs - m_ms / a.steps,
                            "note": "mixed, PIC_F_COULOMB (e-e, e-Ar+, Ar+-Ar+ binary collisions, lnL = 10)"}
+    if diag is not None:
+        ds = max(a.steps // 4, 20)
+        line["diagnostics"] = {"value": diag["pushed"] / (diag["ms"] / 1000.0), "unit": "particle-steps/s",
+                               "steps": ds, "ms_per_step": diag["ms"] / ds,
+                               "extra_ms_per_step": diag["ms"] / ds - m_ms / a.steps,
+                               "note": f"mixed, PIC_F_MOMENTS with T_e/T_i, {DIAG_PHASES} rf phase bins, 200^3 fine "
+                                       "grid (0.08 dx) on the cluster, EEPF 200 x 0.1 eV per cell plane, sampled "
+                                       "every step"}
     if bb is not None:
         line["batch"] = bb
     if not a.no_cpu:

@@ -800,14 +800,18 @@ pic_status ensure_graphs(pic_ctx* c, bool sort)
             }
         });
     if (!c->g_solve) c->g_solve = capture_solve(c);
-    if ((c->flags & PIC_F_MOMENTS) && !c->g_mom[p])
-        c->g_mom[p] = capture(c, &c->n_mom, [&] {
-            launch_moments_all(c);
-        });
-    if (!c->g_pre || !c->g_push[p] || !c->g_post[p][so] || !c->g_solve ||
-        ((c->flags & PIC_F_MOMENTS) && !c->g_mom[p]))
+    if (!c->g_pre || !c->g_push[p] || !c->g_post[p][so] || !c->g_solve)
         return fail(c, PIC_ECUDA, "CUDA graph capture failed");
     return PIC_OK;
+}
+
+// the moment sample reads the particle buffers of the parity after the step's
+// sort, so its graph is captured for that parity when it is first needed
+pic_status ensure_mom_graph(pic_ctx* c)
+{
+    const int p = c->parity;
+    if (!c->g_mom[p]) c->g_mom[p] = capture(c, &c->n_mom, [&] { launch_moments_all(c); });
+    return c->g_mom[p] ? PIC_OK : fail(c, PIC_ECUDA, "CUDA graph capture failed");
 }
 
 pic_status launch_solve_graph(pic_ctx* c)
@@ -894,6 +898,8 @@ pic_status step_enqueue(pic_ctx* c, int32_t n_steps)
         r = launch_solve_graph(c);
         if (r != PIC_OK) return r;
         if (c->flags & PIC_F_MOMENTS) {
+            r = ensure_mom_graph(c);
+            if (r != PIC_OK) return r;
             e = cudaGraphLaunch(c->g_mom[c->parity], c->stream);
             if (e != cudaSuccess) return cuda_fail(c, e, "moments graph launch");
             c->launches += c->n_mom;

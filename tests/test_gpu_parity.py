@@ -446,3 +446,15 @@ def test_temperatures_and_oml_charges_match_oracle(prec):
         assert np.all(qg[:, 0] < 0)        # negative grains in this electron-rich bulk
     # the charge-exchange current makes the estimate less negative
     assert np.all(run.oml_charges(True)[:, 1] > run.oml_charges(False)[:, 1])
+
+
+def test_moments_across_sorts():
+    # sorting swaps the particle buffers; the moment sample must read the new ones
+    wl = I.small(nx=8, ny=8, nz=16, n_e=3000, n_i=3000, grains=1, v_dc=-20.0)
+    ref, run = _pair(wl, flags=P.PIC_F_MOMENTS, sort_every=2)
+    for _ in range(5):
+        ref.step()
+        run.step()
+    for what in range(7):
+        mg, mo = run.moments(what), ref.moments(what)
+        assert np.max(np.abs(mg - mo)) <= 1e-6 * max(np.max(np.abs(mo)), 1e-30), what
