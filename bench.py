@@ -188,18 +188,27 @@ def cold_solves(run, reps=3):
     return {"ms_per_solve": statistics.median(times), "iterations_per_solve": statistics.median(iters)}
 
 
-def traffic_from_profile(kernel_source, name):
+def kernel_source_hash(kernel_source, kernel):
+    """sha256 of a source file from its start to the end of `kernel`'s body: the
+    kernel and every helper defined above it (shared headers are not included)."""
+    import hashlib
+    src = open(os.path.join(ROOT, "paper_1801_00972_gb300", "csrc", kernel_source)).read()
+    start = src.index(kernel + "(")
+    end = src.index("\n}\n", start) + 3
+    return hashlib.sha256(src[:end].encode()).hexdigest()
+
+
+def traffic_from_profile(kernel_source, name, kernel="k_push32"):
     """DRAM bytes per launch of the push kernel from its committed ncu summary,
     or None when the kernel's source has changed since that capture."""
-    import hashlib
     try:
         text = open(os.path.join(ROOT, "profiles", name)).read()
-        src = open(os.path.join(ROOT, "paper_1801_00972_gb300", "csrc", kernel_source), "rb").read()
-    except OSError:
+        digest = kernel_source_hash(kernel_source, kernel)
+    except (OSError, ValueError):
         return None
     vals = dict(line.split(":", 1) for line in text.splitlines() if line.startswith(("traffic_bytes_per_launch:",
                                                                                     "source_sha256:")))
-    if vals.get("source_sha256", "").strip() != hashlib.sha256(src).hexdigest():
+    if vals.get("source_sha256", "").strip() != digest:
         return None
     try:
         return float(vals["traffic_bytes_per_launch"])
