@@ -227,8 +227,10 @@ void destroy(pic_ctx* c)
         if (g) cudaGraphExecDestroy(g);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     if (c->aux) cudaStreamDestroy(c->aux);
+    if (c->aux2) cudaStreamDestroy(c->aux2);
     if (c->ev_fork) cudaEventDestroy(c->ev_fork);
     if (c->ev_join) cudaEventDestroy(c->ev_join);
+    if (c->ev_join2) cudaEventDestroy(c->ev_join2);
     for (void* p : c->allocs) cudaFree(p);
     delete c;
 }
@@ -564,8 +566,10 @@ pic_status pic_init(const pic_mesh* mesh, const pic_electrodes* el, const pic_ga
     if (e == cudaSuccess) e = cudaMemset(c->d_vb_last, 0, sizeof(double));
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->aux, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->aux2, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_join2, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaMemset(c->d_nch, 0, sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaMemset(c->gabs, 0, sizeof(unsigned long long) * 2 * ng1);
     if (e == cudaSuccess) e = cudaMemset(c->gq, 0, sizeof(double) * ng1);

@@ -20,6 +20,9 @@
 //             runs on a second stream alongside k_push32): Dt/40 substeps with
 //             the PPPM correction, grain absorption, MCC, deposit.
 //   k_mcc32   the collision candidates: process selection and kinematics.
+// The ion push and its collisions run on a third stream beside the electron
+// push: the species share only the charge array and the counters, both summed
+// with atomics, so the overlap hides each launch's last partial wave.
 #include <algorithm>
 #include <climits>
 
@@ -33,6 +36,9 @@ namespace {
 #endif
 #ifndef PIC_PUSH_WINR
 #define PIC_PUSH_WINR 256
+#endif
+#ifndef PIC_PUSH_CONC
+#define PIC_PUSH_CONC 1                           // the ion push on a third stream beside the electron push
 #endif
 #ifndef PIC_PUSH_TILE
 #define PIC_PUSH_TILE 0
@@ -980,10 +986,18 @@ void launch_push32(pic_ctx* c)
     k_md32<<<152 * 4, 64, 0, c->aux>>>(pe);
     k_md32<<<152 * 4, 64, 0, c->aux>>>(pi);
     cudaEventRecord(c->ev_join, c->aux);
+    // the two species share only the charge array and counters (both atomic), so
+    // the ion push may run beside the electron push
+    cudaStream_t si = PIC_PUSH_CONC ? c->aux2 : c->stream;
+    if (PIC_PUSH_CONC) cudaStreamWaitEvent(c->aux2, c->ev_fork, 0);
     k_push32<<<grid_for((c->cap[0] + kPPT - 1) / kPPT, kPushThreads, 152 * 8), kPushThreads, 0, c->stream>>>(pe);
     k_mcc32<<<152 * 4, 256, 0, c->stream>>>(pe);
-    k_push32<<<grid_for((c->cap[1] + kPPT - 1) / kPPT, kPushThreads, 152 * 8), kPushThreads, 0, c->stream>>>(pi);
-    k_mcc32<<<152 * 4, 256, 0, c->stream>>>(pi);
+    k_push32<<<grid_for((c->cap[1] + kPPT - 1) / kPPT, kPushThreads, 152 * 8), kPushThreads, 0, si>>>(pi);
+    k_mcc32<<<152 * 4, 256, 0, si>>>(pi);
+    if (PIC_PUSH_CONC) {
+        cudaEventRecord(c->ev_join2, c->aux2);
+        cudaStreamWaitEvent(c->stream, c->ev_join2, 0);
+    }
     cudaStreamWaitEvent(c->stream, c->ev_join, 0);
     k_md_commit<<<64, 256, 0, c->stream>>>((float4*)c->pos[0], (float4*)c->vel[0], c->md_list[0], c->md_res[0],
                                            (float4*)c->pos[1], (float4*)c->vel[1], c->md_list[1], c->md_res[1],

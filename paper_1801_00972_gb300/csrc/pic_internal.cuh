@@ -242,7 +242,8 @@ struct pic_ctx {
     // launched on the run's stream; variants by particle-buffer parity
     cudaStream_t cap_stream = nullptr;
     cudaStream_t aux = nullptr;              // second branch of the particle phase (MD, collisions)
-    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    cudaStream_t aux2 = nullptr;             // third branch (the ion push beside the electron push)
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_join2 = nullptr;
     int parity = 0;
     cudaGraphExec_t g_pre = nullptr, g_push[2] = {nullptr, nullptr}, g_solve = nullptr;
     cudaGraphExec_t g_post[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}}, g_mom[2] = {nullptr, nullptr};
