@@ -32,7 +32,7 @@ namespace pic {
 namespace {
 
 #ifndef PIC_PUSH_PPT
-#define PIC_PUSH_PPT 4
+#define PIC_PUSH_PPT 2
 #endif
 #ifndef PIC_PUSH_WINR
 #define PIC_PUSH_WINR 256
@@ -42,6 +42,9 @@ namespace {
 #endif
 #ifndef PIC_PUSH_TILE
 #define PIC_PUSH_TILE 0
+#endif
+#ifndef PIC_PUSH_MINB
+#define PIC_PUSH_MINB 6                           // resident blocks per SM the register budget is set for
 #endif
 constexpr int kPushThreads = 256;
 constexpr int kPPT = PIC_PUSH_PPT;               // particles per thread per chunk
@@ -384,7 +387,7 @@ __device__ __forceinline__ int block_slot(int i, int j, int k, int nx, int ny, i
     return (pl >= -1 && pl <= 1 && w >= 0 && w + nx + 1 < 2 * kWinR) ? (pl + 1) * 2 * kWinR + w : -1;
 }
 
-__global__ void __launch_bounds__(kPushThreads, 4) k_push32(const P32 p)
+__global__ void __launch_bounds__(kPushThreads, PIC_PUSH_MINB) k_push32(const P32 p)
 {
     __shared__ float4 tile[kTile ? kWinN : 1];         // E around the chunk (gather)
     __shared__ unsigned int win_hi[kWinN], win_lo[kWinN];  // deposit sums (two 21-bit halves)
