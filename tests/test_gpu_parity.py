@@ -458,3 +458,28 @@ def test_moments_across_sorts():
     for what in range(7):
         mg, mo = run.moments(what), ref.moments(what)
         assert np.max(np.abs(mg - mo)) <= 1e-6 * max(np.max(np.abs(mo)), 1e-30), what
+
+
+@pytest.mark.parametrize("prec", [P.PIC_FP64, P.PIC_MIXED])
+def test_diagnostics_of_an_empty_plasma(prec):
+    # no particles: every diagnostic is zero, the hypothetical charge undefined (NaN) on both sides
+    wl = _rf_wl(n_e=0, n_i=0)
+    parts = I.sample_particles(wl)
+    box = _fine_box(wl)
+    ref = O.Sim(wl, parts, flags=O.MOMENTS | O.EEPF, mom_phases=4, eepf_bins=20, eepf_de_ev=0.5, **box)
+    run = P.Run(wl, parts, prec=prec, flags=P.PIC_F_MOMENTS, stream=_stream(), mom_phases=4, eepf_bins=20,
+                eepf_de_ev=0.5, **box)
+    for _ in range(4):
+        ref.step()
+        run.step()
+    for what in range(1, 7):
+        assert not np.any(run.moments(what)) and not np.any(ref.moments(what)), what
+    assert not np.any(run.fine_moments(1)) and not np.any(run.fine_moments(4))
+    h, st = run.eepf()
+    assert st == 4 and not h.any()
+    qg, qo = run.oml_charges(), ref.oml_charges()
+    assert np.all(np.isnan(qg[:, :2])) and np.all(np.isnan(qo[:, :2]))
+    assert not np.any(qg[:, 2:]) and not np.any(qo[:, 2:])
+    # phi still follows the electrodes
+    pg, po = run.moments(0), ref.moments(0)
+    assert np.max(np.abs(pg - po)) <= 1e-6 * np.max(np.abs(po))
