@@ -209,6 +209,33 @@ def test_electron_collision_rates(energy):
         assert abs(c[name] - want) <= 4.5 * sd, (name, c[name], want)
 
 
+def test_electron_collision_rates_maxwellian():
+    # a Maxwellian at T_e = 8 eV: per-process counts against N P_null n_g <sigma_j v> / nu_max,
+    # <sigma v> by quadrature of the tabulated cross sections over the Maxwellian
+    # energy density 2 sqrt(E / pi) T^-3/2 exp(-E / T)
+    te, n = 8.0, 150000
+    wl = I.small(grains=0, n_e=n, n_i=0, weight=0.0, v_dc=0.0, v_top=0.0, dt=5e-10, nx=32, ny=32, nz=64,
+                 te_ev=te)
+    x, v, ids = I.sample_particles(wl)[0]
+    s = O.Sim(wl, _parts(xe=x, ve=v))
+    s.step(1)
+    c = s.counters()
+    assert c["err"] == 0
+    pnull = 1 - math.exp(-wl.nu_max_e * wl.dt)
+    e = np.linspace(0.0, 40.0 * te, 400001)
+    f = 2.0 * np.sqrt(e / math.pi) * te ** -1.5 * np.exp(-e / te)
+    vel = np.sqrt(2.0 * e * QE / ME)
+    grid = np.arange(wl.xs.shape[1]) * wl.de_e
+    for name, row in (("e_el", 0), ("e_exc", 1), ("e_ion", 2)):
+        sig = np.interp(e, grid, wl.xs[row])
+        sv = np.trapezoid(sig * vel * f, e)
+        p = pnull * wl.n_gas * sv / wl.nu_max_e
+        want = p * n
+        sd = math.sqrt(max(n * p * (1 - p), 1.0))
+        assert abs(c[name] - want) <= 4.5 * sd + 0.01 * want, (name, c[name], want)
+    assert c["e_exc"] > 50 and c["e_ion"] > 50
+
+
 def test_ion_collision_rates():
     n = 60000
     energy = 40.0     # ion speed far above the neutral thermal speed: relative speed ~ ion speed
