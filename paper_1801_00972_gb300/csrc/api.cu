@@ -73,13 +73,15 @@ pic_status cuda_fail(pic_ctx* c, cudaError_t e, const char* what)
 cudaError_t clear_moments(pic_ctx* c, cudaStream_t st)
 {
     const size_t nb = (size_t)c->nph;
-    const size_t sz[8] = {sizeof(double) * 4 * c->nodes * nb, sizeof(double) * 4 * c->nodes * nb,
-                          sizeof(double) * c->nodes * nb, sizeof(unsigned long long) * nb,
-                          sizeof(double) * 4 * c->nfine, sizeof(double) * 4 * c->nfine,
-                          sizeof(double) * c->nodes * nb, sizeof(double) * c->nodes * nb};
-    void* p[8] = {c->mom[0], c->mom[1], c->mphi, c->d_bsteps, c->fine[0], c->fine[1], c->mke[0], c->mke[1]};
+    const size_t sz[10] = {sizeof(double) * 4 * c->nodes * nb, sizeof(double) * 4 * c->nodes * nb,
+                           sizeof(double) * c->nodes * nb, sizeof(unsigned long long) * nb,
+                           sizeof(double) * 4 * c->nfine, sizeof(double) * 4 * c->nfine,
+                           sizeof(double) * c->nodes * nb, sizeof(double) * c->nodes * nb,
+                           sizeof(float) * 5 * c->nodes, sizeof(float) * 5 * c->nodes};
+    void* p[10] = {c->mom[0], c->mom[1], c->mphi, c->d_bsteps, c->fine[0], c->fine[1], c->mke[0], c->mke[1],
+                   c->mom32[0], c->mom32[1]};
     cudaError_t e = cudaSuccess;
-    for (int q = 0; q < 8 && e == cudaSuccess; ++q)
+    for (int q = 0; q < 10 && e == cudaSuccess; ++q)
         if (p[q]) e = st ? cudaMemsetAsync(p[q], 0, sz[q], st) : cudaMemset(p[q], 0, sz[q]);
     return e;
 }
@@ -468,6 +470,11 @@ pic_status pic_init(const pic_mesh* mesh, const pic_electrodes* el, const pic_ga
         c->d_bin = (int*)dev_alloc(c, sizeof(int));
         c->d_bsteps = (unsigned long long*)dev_alloc(c, sizeof(unsigned long long) * nb);
         c->d_oml = (double*)dev_alloc(c, sizeof(double) * 6 * (size_t)std::max(c->ng, 1));
+        if (c->prec == PIC_MIXED) {
+            c->mom32[0] = (float*)dev_alloc(c, sizeof(float) * 5 * nodes);
+            c->mom32[1] = (float*)dev_alloc(c, sizeof(float) * 5 * nodes);
+            ok = ok && c->mom32[0] && c->mom32[1];
+        }
         ok = ok && c->mom[0] && c->mom[1] && c->mphi && c->mke[0] && c->mke[1] && c->d_bin && c->d_bsteps && c->d_oml;
         if (c->nfine) {
             c->fine[0] = (double*)dev_alloc(c, sizeof(double) * 4 * c->nfine);

@@ -878,13 +878,18 @@ __global__ void k_children_finish32(unsigned long long* nch, unsigned long long 
     *nch = 0;
 }
 
+// Node moments of one sample, in float: FP64 arithmetic issues at a small
+// fraction of the FP32 rate on this GPU, so the CIC weights, weight x v and
+// weight x |v|^2 are formed and summed in float (a node takes tens of adds per
+// sample: about 1e-7 relative rounding), the first four as one float4
+// reduction; k_mom_fold then adds them once per node to the FP64 window of the
+// sample's phase bin.
 __global__ void k_moments32(int nx, int ny, float vs, const float4* pos, const float4* vel,
-                            const unsigned long long* nslot, int sp, double* mom, double* mke, const int* bin,
-                            size_t nodes)
+                            const unsigned long long* nslot, int sp, float4* m4, float* mk)
 {
     const unsigned long long n = nslot[sp];
-    mom += (size_t)*bin * 4 * nodes;   // the sample's rf phase bin
-    mke += (size_t)*bin * nodes;
+    const float s = 1.0f / (float)kWQ;
+    const int nxy = nx * ny;
     for (unsigned long long q = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; q < n;
          q += (unsigned long long)gridDim.x * blockDim.x) {
         const float4 P = pos[q];
@@ -893,22 +898,45 @@ __global__ void k_moments32(int nx, int ny, float vs, const float4* pos, const f
         const float4 V = vel[q];
         int i, j, k;
         unpack(cell, i, j, k);
-        const int a[3] = {qa(P.x), qa(P.y), qa(P.z)};
-        int node[8];
-        long long val[8];
-        corners(nx, ny, i, j, k, a, 1, node, val);
-        const double vx = (double)V.x * vs, vy = (double)V.y * vs, vz = (double)V.z * vs;
-        const double v2 = (vx * vx + vy * vy) + vz * vz;
-        for (int c = 0; c < 8; ++c) {
-            const double wt = (double)val[c] * 0x1p-42;
-            if (wt == 0.0) continue;
-            double* m = mom + 4 * (size_t)node[c];
-            atomicAdd(m, wt);
-            atomicAdd(m + 1, wt * vx);
-            atomicAdd(m + 2, wt * vy);
-            atomicAdd(m + 3, wt * vz);
-            atomicAdd(mke + node[c], wt * v2);
-        }
+        const int ax = qa(P.x), ay = qa(P.y), az = qa(P.z);
+        const float wx[2] = {(float)(kWQ - ax) * s, (float)ax * s};
+        const float wy[2] = {(float)(kWQ - ay) * s, (float)ay * s};
+        const float wz[2] = {(float)(kWQ - az) * s, (float)az * s};
+        const int ii[2] = {i, (i + 1 == nx) ? 0 : i + 1};
+        const int rr[2] = {j * nx, ((j + 1 == ny) ? 0 : j + 1) * nx};
+        const float vx = V.x * vs, vy = V.y * vs, vz = V.z * vs;
+        const float v2 = (vx * vx + vy * vy) + vz * vz;
+#pragma unroll
+        for (int dz = 0; dz < 2; ++dz)
+#pragma unroll
+            for (int dy = 0; dy < 2; ++dy)
+#pragma unroll
+                for (int di = 0; di < 2; ++di) {
+                    const float w = (wx[di] * wy[dy]) * wz[dz];
+                    if (w == 0.f) continue;
+                    const size_t nd = (size_t)((k + dz) * nxy + rr[dy] + ii[di]);
+                    atomicAdd(m4 + nd, make_float4(w, w * vx, w * vy, w * vz));   // one vector reduction
+                    atomicAdd(mk + nd, w * v2);
+                }
+    }
+}
+
+// add one sample's float sums to the FP64 window of its phase bin and clear them
+__global__ void k_mom_fold(float4* __restrict__ m4, float* __restrict__ mk, double* __restrict__ mom,
+                           double* __restrict__ mke, const int* bin, size_t nodes)
+{
+    const size_t b = (size_t)*bin;
+    for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < nodes; q += (size_t)gridDim.x * blockDim.x) {
+        const float4 m = m4[q];
+        if (m.x == 0.f) continue;
+        double* d = mom + 4 * (b * nodes + q);
+        d[0] += (double)m.x;
+        d[1] += (double)m.y;
+        d[2] += (double)m.z;
+        d[3] += (double)m.w;
+        mke[b * nodes + q] += (double)mk[q];
+        m4[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+        mk[q] = 0.f;
     }
 }
 
@@ -1039,11 +1067,14 @@ void launch_children32(pic_ctx* c)
 
 void launch_moments32(pic_ctx* c)
 {
-    for (int sp = 0; sp < 2; ++sp)
+    for (int sp = 0; sp < 2; ++sp) {
         k_moments32<<<grid_for(c->cap[sp], 256, 152 * 8), 256, 0, c->stream>>>(
             c->nx, c->ny, (float)(c->dx / c->dt), (const float4*)c->pos[sp], (const float4*)c->vel[sp], c->d_nslot,
-            sp, c->mom[sp], c->mke[sp], c->d_bin, c->nodes);
-    c->launches += 2;
+            sp, (float4*)c->mom32[sp], c->mom32[sp] + 4 * c->nodes);
+        k_mom_fold<<<grid_for((int64_t)c->nodes, 256, 152 * 8), 256, 0, c->stream>>>(
+            (float4*)c->mom32[sp], c->mom32[sp] + 4 * c->nodes, c->mom[sp], c->mke[sp], c->d_bin, c->nodes);
+    }
+    c->launches += 4;
 }
 
 void launch_moments_phi(pic_ctx* c)

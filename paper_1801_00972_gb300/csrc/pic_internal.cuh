@@ -254,6 +254,7 @@ struct pic_ctx {
     double* mom[2] = {nullptr, nullptr};     // nph * 4 * nodes each: [phase bin][node][n, n vx, n vy, n vz]
     double* mphi = nullptr;                  // nph * nodes
     double* mke[2] = {nullptr, nullptr};     // nph * nodes each: sum of n |v|^2
+    float* mom32[2] = {nullptr, nullptr};    // mixed: one sample's float sums: float4 [node] {n, n v}, then float [node] n |v|^2
     double* d_oml = nullptr;                 // 6 per grain: hypothetical-charge estimate
     int64_t msteps = 0;
     int nph = 1;                             // rf phase bins of the moments

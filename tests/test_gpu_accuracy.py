@@ -18,6 +18,15 @@ from paper_1801_00972_gb300 import inputs as I
 STEPS = 2000
 
 
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import torch
+    from paper_1801_00972_gb300 import build as B
+    B.build()
+    torch.cuda.set_device(0)
+    P.load()
+
+
 def _run(prec, seed):
     import torch
     wl = I.workload(1)

@@ -24,6 +24,15 @@ sp = pytest.importorskip("scipy.special")
 EPS0 = 8.8541878128e-12
 
 
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import torch
+    from paper_1801_00972_gb300 import build as B
+    B.build()
+    torch.cuda.set_device(0)
+    P.load()
+
+
 def _stream():
     import torch
     return torch.cuda.current_stream().cuda_stream
