@@ -286,6 +286,25 @@ def oracle_sample(wl, n_particles, steps, seed=1):
     return done / t, t, n0
 
 
+def replica_seed(seed, rank):
+    """Replicas: every rank runs the same workload from its own seed."""
+    return seed + 1000 * rank
+
+
+def aggregate(ms, units, device):
+    """Whole-job figures of a replicas run: the slowest rank's time and the
+    units (particle-steps) of all ranks; the values themselves on one rank."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return ms, units
+    m = torch.tensor([float(ms)], device=device, dtype=torch.float64)
+    u = torch.tensor([float(units)], device=device, dtype=torch.float64)
+    dist.all_reduce(m, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(m[0]), float(u[0])
+
+
 def reference_arm(a):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -333,7 +352,7 @@ def main():
     P.load()
     wl = I.workload(a.workload)
     # replicas: each rank runs its own independent run (different seed)
-    wl.seed = wl.seed + 1000 * rank
+    wl.seed = replica_seed(wl.seed, rank)
     parts = I.sample_particles(wl)
     stream = torch.cuda.current_stream().cuda_stream
     flags = P.PIC_F_NO_GRAPH if a.eager else 0
@@ -363,17 +382,7 @@ def main():
     bb = None if (a.no_batch or world > 1) else batch_bench(P, I, max(a.steps // 4, 10), a.warmup)
 
     def agg(x):
-        if x is None:
-            return None
-        ms = x["ms"]
-        tot = x["pushed"]
-        if world > 1:
-            t = torch.tensor([ms, float(tot)], device="cuda", dtype=torch.float64)
-            m = t.clone()
-            torch.distributed.all_reduce(m[:1], op=torch.distributed.ReduceOp.MAX)
-            torch.distributed.all_reduce(t[1:], op=torch.distributed.ReduceOp.SUM)
-            ms, tot = float(m[0]), float(t[1])
-        return ms, tot
+        return None if x is None else aggregate(x["ms"], x["pushed"], "cuda")
 
     m_ms, m_tot = agg(mixed)
     f = agg(fp64)
