@@ -1992,7 +1992,6 @@ void na_vcycle(NaCtx& c, int l)
         k_coarse<T><<<1, 1024, 0, c.s>>>(u, f, d, h2, std::min(4 * m * m + 16, 2000));
         return;
     }
-    const size_t half = (size_t)(L.nx / 2) * L.ny * (L.nz - 1);
     for (int s = 0; s < 2; ++s)
         for (int color = 0; color < 2; ++color) run_rbgs<T>(c.s, u, f, d, h2, color, 0);
     run_resid<T>(c.s, u, f, (T*)L.r, d, (T)(1.0 / (L.h * L.h)));
