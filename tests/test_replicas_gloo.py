@@ -1,4 +1,4 @@
-"""The multi-rank path of the benchmark (replicas only: one independent run per
+"""The host side of the benchmark.  The multi-rank path (replicas only: one independent run per
 rank, no data-path collective) on CPU with two gloo ranks: the whole-job time
 is the slowest rank's, the particle-steps are summed over the ranks, every rank
 draws its own seed, and only rank 0 prints the reference arm's line."""
@@ -59,3 +59,21 @@ def test_reference_arm_prints_on_rank_zero_only(monkeypatch, capsys):
     monkeypatch.setattr(sys, "argv", ["bench.py", "--impl", "reference", "--gpus", "2", "--steps", "1", "--warmup", "0"])
     bench.reference_arm(bench.args())
     assert capsys.readouterr().out == ""
+
+
+def test_reference_arm_line(tmp_path):
+    # the oracle arm of the benchmark: one JSON line with the contract's keys
+    import json as _json
+    import subprocess
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
+                        "--warmup", "0"], capture_output=True, text=True, cwd=ROOT, timeout=600,
+                       env={**os.environ, "RANK": "0"})
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [l for l in r.stdout.splitlines() if l.startswith("{")]
+    assert len(lines) == 1
+    d = _json.loads(lines[0])
+    assert d["impl"] == "reference" and d["value"] > 0 and d["unit"] == "particle-steps/s"
+    for k in ("metric", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better", "config"):
+        assert k in d, k
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
+    assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
