@@ -1,7 +1,8 @@
 """The host side of the benchmark.  The multi-rank path (replicas only: one independent run per
 rank, no data-path collective) on CPU with two gloo ranks: the whole-job time
 is the slowest rank's, the particle-steps are summed over the ranks, every rank
-draws its own seed, and only rank 0 prints the reference arm's line."""
+draws its own seed, and only rank 0 prints the reference (oracle) arm's line,
+which carries the keys the benchmark's contract asks for."""
 import json
 import os
 import socket
