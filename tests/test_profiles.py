@@ -1,0 +1,25 @@
+"""The committed ncu summaries stay tied to the code they describe: each gives
+the full command that produced it (with --clock-control none), and the push
+kernel's traffic figure, which the benchmark reports as roofline.traffic, is
+keyed on the current source text of that kernel and its helpers."""
+import glob
+import os
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def test_every_summary_has_its_command():
+    files = sorted(glob.glob(os.path.join(ROOT, "profiles", "*.md")))
+    assert files
+    for f in files:
+        text = open(f).read()
+        assert "ncu " in text and "--clock-control none" in text, os.path.basename(f)
+        assert "python bench.py" in text, os.path.basename(f)
+
+
+def test_push_traffic_matches_the_current_kernel():
+    sys.path.insert(0, ROOT)
+    import bench
+    t = bench.traffic_from_profile("particles_mixed.cu", "k_push32_w1_64x64x256_1e7.md")
+    assert t is not None and 2.5e8 < t < 4e8, t
