@@ -95,9 +95,11 @@ void     orc_reset_moments(orc_sim* s);
  * charge-exchange ion flux term 0.1 (e phi / T_i)^2 lambda_D / l_i given by
  * lam_over_l = lambda_D / l_i (0: collisionless OML); NaN if a density or a
  * temperature is not positive.  Parity partially pinned: the collisionless
- * balance against its closed forms, the charge-exchange term only through the
- * potential a chosen lam_over_l balances and its sign (its 0.1 coefficient is
- * the cited model's, with no independent check here) */
+ * balance against its closed forms, and the charge-exchange term through the
+ * potential a chosen lam_over_l balances and its sign.  Its 0.1 coefficient
+ * is the cited model's, with no independent check here (parity unpinned for
+ * that coefficient).  orc_oml_charges' lambda_D / l_i is pinned against the
+ * textbook Debye length and sigma_cx at 3/2 T_i. */
 double   orc_oml_potential(double ne, double ni, double te, double ti, double lam_over_l);
 /* per grain 6 values from the moment window: Q = 4 pi eps0 a phi (C), phi (V),
  * and the local n_e, n_i (m^-3), T_e, T_i (eV) at the grain centre; with_cx

@@ -100,3 +100,47 @@ def test_cold_beam_has_zero_temperature():
     t = s.moments(5)
     drift_ev = 0.5 * I.ME * (9e8 + 1e8 + 4e8) / I.QE
     assert np.max(np.abs(t)) <= 1e-12 * drift_ev
+
+
+def _debye_length(ne, ni, te_ev, ti_ev):
+    """Linearised Debye length from the textbook definition with temperatures in
+    kelvin: lambda_D^-2 = e^2 n_e / (eps0 k_B T_e) + e^2 n_i / (eps0 k_B T_i)."""
+    qe, kb, eps0 = 1.602176634e-19, 1.380649e-23, 8.8541878128e-12
+    te_k, ti_k = te_ev * qe / kb, ti_ev * qe / kb
+    return 1.0 / math.sqrt(qe * qe * ne / (eps0 * kb * te_k) + qe * qe * ni / (eps0 * kb * ti_k))
+
+
+def test_debye_length_by_hand():
+    # n = 1e15 m^-3, T_e = 3 eV, T_i = 0.03 eV:
+    # lambda_De = sqrt(eps0 * 3 V / (1e15 m^-3 * e)) = 4.0717e-4 m, lambda_Di = 4.0717e-5 m,
+    # lambda_D = (lambda_De^-2 + lambda_Di^-2)^-1/2 = lambda_Di / sqrt(1.01) = 4.0515e-5 m
+    assert _debye_length(1e15, 1e15, 3.0, 0.03) == pytest.approx(4.0515e-5, rel=1e-4)
+
+
+@pytest.mark.parametrize("table", ["flat", "linear"])
+def test_cx_term_uses_debye_length_over_cx_mean_free_path(table):
+    """The estimator's lambda_D / l_i with l_i = 1 / (n_gas sigma_cx(3/2 T_i)):
+    a uniform plasma sampled into the moment window, a charge-exchange table
+    chosen so that sigma_cx(3/2 T_i) is known exactly (a constant, or a line
+    that linear interpolation reproduces), and the potential compared with the
+    balance at the hand-computed ratio."""
+    wl = I.small(nx=8, ny=8, nz=16, n_e=200000, n_i=200000, grains=1, v_dc=0.0, te_ev=2.5, ti_ev=0.05,
+                 weight=1e-3)
+    wl.grain_r[:] = 1e-7
+    a, b = 3.0e-19, 4.0e-18            # sigma_cx = a (flat) or a + b E[eV] (linear)
+    e_grid = np.arange(wl.xs.shape[1]) * wl.de_i
+    wl.xs = wl.xs.copy()
+    wl.xs[4] = a if table == "flat" else a + b * e_grid
+    parts = I.sample_particles(wl)
+    s = O.Sim(wl, parts, flags=O.MOMENTS | O.NO_MCC | O.IONS_FROZEN)
+    s.step(2)
+    q = s.oml_charges(with_cx=True)[0]
+    ne, ni, te, ti = q[2:6]
+    sig = a if table == "flat" else a + b * 1.5 * ti
+    ratio = _debye_length(ne, ni, te, ti) * wl.n_gas * sig
+    assert q[1] == pytest.approx(O.oml_potential(ne, ni, te, ti, ratio), rel=1e-9)
+    if table == "linear":
+        # the cross section is taken at 3/2 T_i, not at T_i or 3 T_i
+        for t in (ti, 3 * ti):
+            wrong = _debye_length(ne, ni, te, ti) * wl.n_gas * (a + b * t)
+            assert abs(O.oml_potential(ne, ni, te, ti, wrong) - q[1]) > 1e-4 * abs(q[1])
