@@ -142,6 +142,23 @@ pic_status pic_init(const pic_mesh* mesh, const pic_electrodes* el, const pic_ga
                     const pic_grains* grains, const pic_run* run, void* cuda_stream,
                     pic_ctx** out);
 
+/* pic_init with the initial plasma drawn on the device from the run's seed
+ * instead of host arrays (Sec. III starts from a plasma of given density and
+ * electron and ion temperatures; the sampling rule is this library's):
+ * run->n[0] electrons with ids 0 .. n[0]-1 and run->n[1] Ar+ ions with ids
+ * n[0] .. n[0]+n[1]-1; run->x_host, v_host and id_host are ignored.  Particle
+ * id p takes three uniforms at a time from its Philox stream (counter p,
+ * step 0, purpose 10) for a point (u_x Lx, u_y Ly, u_z Lz), redrawn while it
+ * lies within 1.5 radii of a grain (minimum image in x and y; at most 64
+ * tries, then the last point is kept), and three standard normals (Marsaglia
+ * polar method, purpose 11) times sqrt(t_ev[sp] e / m) for its velocity,
+ * which is taken as v at t = -dt/2.  t_ev: 2 temperatures in eV (electrons,
+ * ions), host memory.  Needs 1.5 * radius < dx for every grain and
+ * n[0] + n[1] < 2^32; PIC_EINVAL otherwise.  Everything else as pic_init. */
+pic_status pic_init_plasma(const pic_mesh* mesh, const pic_electrodes* el, const pic_gas* gas,
+                           const pic_grains* grains, const pic_run* run, const double* t_ev, void* cuda_stream,
+                           pic_ctx** out);
+
 /* n_steps full time steps (Eqs. 1-6, MCC, absorption, deposit, Poisson), queued
  * on the run's stream.  Returns the status of the previous steps' solves. */
 pic_status pic_step(pic_ctx* ctx, int32_t n_steps);
@@ -287,27 +304,36 @@ void       pic_batch_destroy(pic_batch* b);
  * cudaMalloc fails or escapes its accounting), or a time-critical loop that must
  * avoid cudaMalloc/cudaFree because they synchronise the whole device.
  *
- * It solves the same equation as pic_solve (Eq. 3, periodic x and y, Dirichlet
- * planes k = 0 and k = nz) with the same multigrid and FP64 refinement, for a
- * mesh of at most 131072 nodes (nx*ny*(nz+1)); larger meshes return
- * PIC_EINVAL.  The caller passes device pointers:
+ * It solves the discrete Poisson equation of pic_solve, -lap(phi) = rho/eps0
+ * with the 7-point stencil, periodic in x and y, Dirichlet node planes k = 0
+ * (v_bot) and k = nz (v_top), by multigrid V(2,2) cycles inside FP64 residual
+ * refinement (mixed: FP32 cycles; FP64: FP64 cycles), for a mesh of at most
+ * 131072 nodes (nx*ny*(nz+1)).  Its coarse levels differ from pic_solve's:
+ * the mesh is halved while nx and ny are divisible by 4 and nz is even and
+ * at least 4, and the coarsest level is smoothed by up to 2000 red-black
+ * Gauss-Seidel sweeps in one thread block (pic_solve solves its coarse level
+ * exactly).  Meshes larger than 131072 nodes, or whose coarsest level has
+ * more than 4096 nodes, return PIC_EINVAL.  The caller passes device
+ * pointers:
  *   rho_q_dev  int64 fixed-point charge per node, as pic_get_rho returns it;
  *   scale      factor turning rho_q into rho/eps0 (for a run of weight W:
  *              e W / dx^3 * 2^-42 / eps0);
  *   phi_dev    FP64 potential per node: the start value on entry (e.g. zeros or
- *              the previous solution), the solution on return; the electrode
- *              planes are set to v_bot and v_top.
+ *              the previous solution, even one with other electrode values),
+ *              the solution on return; the electrode planes are set to v_bot
+ *              and v_top.
  * prec is PIC_FP64 or PIC_MIXED; tol, max_iters, iterations and rel_residual
- * mean what they mean for pic_solve.  Work runs on cuda_stream (NULL: default)
- * and the call returns after the stream has finished it.
+ * mean what they mean for pic_solve.  Work runs on cuda_stream (NULL: default).
+ * Every call reads norms back to the host and synchronises cuda_stream, so it
+ * must not be made while that stream is being captured into a CUDA graph.
  *
  * The working set lives in one fixed device array of about 6.3 MB inside the
  * library, which every GPU that loads the library holds until the process
  * exits.  The first call on a device looks up that array's device address
- * (once per device, for the current device); make that first call before any
- * stream capture.  Every call reuses the same array and overwrites what the
- * previous call left there, so calls that overlap on the GPU (from several
- * host threads or streams at once) race and must be serialised by the caller. */
+ * (once per device, for the current device).  Every call reuses the same
+ * array and overwrites what the previous call left there, so calls that
+ * overlap on the GPU (from several host threads or streams at once) race and
+ * must be serialised by the caller. */
 pic_status pic_solve_noalloc(int32_t nx, int32_t ny, int32_t nz, double dx, const int64_t* rho_q_dev, double scale,
                              double v_bot, double v_top, double* phi_dev, int32_t prec, double tol,
                              int32_t max_iters, int32_t* iterations, double* rel_residual, void* cuda_stream);

@@ -73,6 +73,7 @@ class Cfg(C.Structure):
         ("fine_n", C.c_int32 * 3),
         ("fine_h", C.c_double),
         ("fine_origin", C.c_double * 3),
+        ("t_init_ev", C.c_double * 2),
     ]
 
 
@@ -181,7 +182,9 @@ def efield(nx, ny, nz, dx, phi):
 class Sim:
     """One oracle run.  ``wl`` is a workload description with the attributes of
     ``paper_1801_00972_gb300.inputs.Workload`` (duck-typed; this module does not
-    import the package)."""
+    import the package).  ``particles`` = [(x, v, id) per species], or None to
+    let the oracle draw wl.n_e electrons and wl.n_i ions at wl.te_ev / wl.ti_ev
+    from the seed."""
 
     def __init__(self, wl, particles, flags: int = 0, md_sub: int | None = None, coulomb_log: float = 10.0,
                  eepf_bins: int = 0, eepf_de_ev: float = 0.0, mom_phases: int = 0, fine_n=(0, 0, 0),
@@ -216,6 +219,11 @@ class Sim:
         self.fine_n = tuple(int(n) for n in fine_n)
         self._keep += [xs, g, r]
         for sp in range(2):
+            if particles is None:
+                # the oracle draws the initial plasma from the seed itself
+                cfg.n_init[sp] = (wl.n_e, wl.n_i)[sp]
+                cfg.t_init_ev[sp] = (wl.te_ev, wl.ti_ev)[sp]
+                continue
             x, v, ids = particles[sp]
             x = np.ascontiguousarray(x, dtype=np.float64).reshape(-1)
             v = np.ascontiguousarray(v, dtype=np.float64).reshape(-1)

@@ -45,7 +45,8 @@
 #define MAXG  8                    /* grains per MD cell */
 
 enum { PUR_MCC = 1, PUR_DIR = 2, PUR_NEUTRAL = 3, PUR_CHILD_DIR = 4, PUR_CHILD_NEUTRAL = 5,
-       PUR_COUL_ORDER = 6, PUR_COUL_EE = 7, PUR_COUL_II = 8, PUR_COUL_EI = 9 };
+       PUR_COUL_ORDER = 6, PUR_COUL_EE = 7, PUR_COUL_II = 8, PUR_COUL_EI = 9,
+       PUR_INIT_POS = 10, PUR_INIT_VEL = 11 };
 
 /* ------------------------------------------------------------------------ */
 /* Philox4x32-10 counter-based generator (Salmon, Moraes, Dror, Shaw, SC'11) */
@@ -956,6 +957,44 @@ int orc_step(orc_sim* s)
     return 0;
 }
 
+/* Initial plasma drawn from the run's seed (the paper starts from a uniform
+ * plasma of given density and temperatures, Sec. III; the draw itself is this
+ * build's reading): particle id p takes three uniforms at a time from its
+ * stream (p, step 0, PUR_INIT_POS) for a point u L in the box until the point
+ * lies farther than 1.5 radii from every grain (minimum image in x and y; at
+ * most 64 tries, else the last point), and three normals from (p, 0,
+ * PUR_INIT_VEL) times the thermal speed sqrt(T e / m) for its velocity. */
+static void sample_plasma(orc_sim* s, int sp, int64_t n, uint32_t id0, double t_ev)
+{
+    const double m = sp == 0 ? ME : MAR;
+    const double vth = sqrt((t_ev * QE) / m);
+    const double L[3] = { s->Lx, s->Ly, s->Lz };
+    for (int64_t q = 0; q < n; ++q) {
+        const uint32_t id = id0 + (uint32_t)q;
+        double* x = s->x[sp] + 3 * q;
+        rstream rp; rs_init(&rp, id, 0, PUR_INIT_POS, s->key);
+        for (int t = 0; t < 64; ++t) {
+            for (int a = 0; a < 3; ++a) x[a] = u01(rs_next(&rp)) * L[a];
+            int near = 0;
+            for (int g = 0; g < s->c.n_grains && !near; ++g) {
+                double d[3];
+                for (int a = 0; a < 3; ++a) {
+                    d[a] = x[a] - s->gpos[3 * g + a];
+                    if (a < 2 && d[a] > 0.5 * L[a]) d[a] = d[a] - L[a];
+                    else if (a < 2 && d[a] < -0.5 * L[a]) d[a] = d[a] + L[a];
+                }
+                const double rx = 1.5 * s->grad[g];
+                near = ((d[0] * d[0] + d[1] * d[1]) + d[2] * d[2]) <= rx * rx;
+            }
+            if (!near) break;
+        }
+        double nv[3];
+        rstream rv; rs_init(&rv, id, 0, PUR_INIT_VEL, s->key); rs_gauss3(&rv, nv);
+        for (int a = 0; a < 3; ++a) s->v[sp][3 * q + a] = vth * nv[a];
+        s->id[sp][q] = id;
+    }
+}
+
 orc_sim* orc_create(const orc_cfg* cfg)
 {
     orc_sim* s = (orc_sim*)calloc(1, sizeof(orc_sim));
@@ -1045,7 +1084,11 @@ orc_sim* orc_create(const orc_cfg* cfg)
     for (int sp = 0; sp < 2; ++sp) {
         grow(s, sp, cfg->n_init[sp] > 0 ? cfg->n_init[sp] : 1);
         s->n[sp] = cfg->n_init[sp];
-        if (cfg->n_init[sp] > 0) {
+        if (cfg->n_init[sp] > 0 && !cfg->x_init[sp]) {
+            sample_plasma(s, sp, cfg->n_init[sp], sp == 0 ? 0u : (uint32_t)cfg->n_init[0], cfg->t_init_ev[sp]);
+            for (int64_t q = 0; q < cfg->n_init[sp]; ++q)
+                if (!any || s->id[sp][q] > maxid) { maxid = s->id[sp][q]; any = 1; }
+        } else if (cfg->n_init[sp] > 0) {
             memcpy(s->x[sp], cfg->x_init[sp], sizeof(double) * 3 * cfg->n_init[sp]);
             memcpy(s->v[sp], cfg->v_init[sp], sizeof(double) * 3 * cfg->n_init[sp]);
             memcpy(s->id[sp], cfg->id_init[sp], sizeof(uint32_t) * cfg->n_init[sp]);

@@ -52,6 +52,9 @@ typedef struct {
     int32_t  fine_n[3];              /* ORC_MOMENTS: fine diagnostic grid of fine_n[0..2] cells of */
     double   fine_h;                 /*   edge fine_h (all three > 0 switch it on), lower corner  */
     double   fine_origin[3];         /*   fine_origin (metres); not periodic                       */
+    double   t_init_ev[2];           /* species with n_init > 0 and x_init NULL: sampled here from the
+                                        seed (uniform in the box outside 1.5 grain radii, Maxwellian at
+                                        t_init_ev), ids 0..n_e-1 for electrons, n_e.. for ions */
 } orc_cfg;
 
 typedef struct orc_sim orc_sim;

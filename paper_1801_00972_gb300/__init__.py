@@ -31,7 +31,7 @@ COUNTERS = ("lost_bot_e", "lost_bot_i", "lost_top_e", "lost_top_i", "abs_e", "ab
 PIC_C_N = len(COUNTERS)
 
 # every symbol include/pic.h declares
-SYMBOLS = ("pic_init", "pic_step", "pic_tune_sort", "pic_advance", "pic_solve", "pic_grain_charges", "pic_counts",
+SYMBOLS = ("pic_init", "pic_init_plasma", "pic_step", "pic_tune_sort", "pic_advance", "pic_solve", "pic_grain_charges", "pic_counts",
            "pic_moments", "pic_moments_phase", "pic_fine_moments", "pic_oml_charges", "pic_eepf", "pic_eepf_fit", "pic_get_particles", "pic_get_rho", "pic_get_phi", "pic_set_phi",
            "pic_get_grain_table", "pic_set_grain_table", "pic_set_grain_counts", "pic_step_index",
            "pic_profile", "pic_profile_read", "pic_solve_noalloc", "pic_batch_init", "pic_batch_step",
@@ -107,6 +107,9 @@ def load(path: str | None = None):
             f.argtypes = args
             f.restype = C.c_int
         L.pic_init.restype = C.c_int
+        L.pic_init_plasma.argtypes = [C.POINTER(pic_mesh), C.POINTER(pic_electrodes), C.POINTER(pic_gas),
+                                      C.POINTER(pic_grains), C.POINTER(pic_run), pd, vp, C.POINTER(vp)]
+        L.pic_init_plasma.restype = C.c_int
         L.pic_batch_init.argtypes = [i32, C.POINTER(pic_mesh), C.POINTER(pic_electrodes), C.POINTER(pic_gas),
                                      C.POINTER(pic_grains), C.POINTER(pic_run), C.POINTER(vp)]
         L.pic_batch_init.restype = C.c_int
@@ -142,6 +145,15 @@ def pic_init(mesh, electrodes, gas, grains, run, stream=None):
     ctx = C.c_void_p()
     st = load().pic_init(C.byref(mesh), C.byref(electrodes), C.byref(gas), C.byref(grains), C.byref(run),
                          C.c_void_p(stream or 0), C.byref(ctx))
+    _check(None, st)
+    return ctx
+
+
+def pic_init_plasma(mesh, electrodes, gas, grains, run, t_ev, stream=None):
+    ctx = C.c_void_p()
+    t = (C.c_double * 2)(float(t_ev[0]), float(t_ev[1]))
+    st = load().pic_init_plasma(C.byref(mesh), C.byref(electrodes), C.byref(gas), C.byref(grains), C.byref(run),
+                                t, C.c_void_p(stream or 0), C.byref(ctx))
     _check(None, st)
     return ctx
 
@@ -313,7 +325,8 @@ def make_args(wl, particles, prec=PIC_MIXED, flags=0, capacity=None, sort_every=
               md_sub=None, coulomb_log=10.0, eepf_bins=0, eepf_de_ev=0.0, mom_phases=0, fine_n=(0, 0, 0),
               fine_h=0.0, fine_origin=(0.0, 0.0, 0.0)):
     """The pic_init argument structures for a workload; returns them with the
-    numpy arrays they point into (keep those alive while the call runs)."""
+    numpy arrays they point into (keep those alive while the call runs).
+    particles=None leaves the particle arrays NULL for pic_init_plasma."""
     keep = []
     mesh = pic_mesh(wl.nx, wl.ny, wl.nz, wl.dx)
     el = pic_electrodes(wl.v_dc, wl.v_rf, wl.f_rf, wl.phase, wl.v_top)
@@ -327,6 +340,12 @@ def make_args(wl, particles, prec=PIC_MIXED, flags=0, capacity=None, sort_every=
     grains = pic_grains(gr.size, _p(gp, C.c_double), _p(gr, C.c_double))
     run = pic_run()
     for sp in range(2):
+        if particles is None:
+            # drawn on the device from the seed (pic_init_plasma)
+            n = (wl.n_e, wl.n_i)[sp]
+            run.n[sp] = n
+            run.capacity[sp] = capacity[sp] if capacity is not None else int(n * 1.25) + 4096
+            continue
         x, v, ids = particles[sp]
         x = np.ascontiguousarray(x, dtype=np.float64).reshape(-1)
         v = np.ascontiguousarray(v, dtype=np.float64).reshape(-1)
@@ -377,7 +396,9 @@ class Batch:
 
 class Run:
     """One run context built from a workload description (see ``inputs.Workload``)
-    and initial particles [(x, v, id) for electrons, ions] in SI units."""
+    and initial particles [(x, v, id) for electrons, ions] in SI units, or
+    particles=None to draw wl.n_e electrons and wl.n_i ions at wl.te_ev and
+    wl.ti_ev on the device (pic_init_plasma)."""
 
     def __init__(self, wl, particles, prec=PIC_MIXED, flags=0, stream=None, capacity=None, sort_every=20,
                  tol=1e-10, max_cycles=60, md_sub=None, coulomb_log=10.0, eepf_bins=0, eepf_de_ev=0.0,
@@ -389,7 +410,10 @@ class Run:
         gr = np.asarray(wl.grain_r).reshape(-1)
         self.eepf_bins = eepf_bins
         self.fine_n = tuple(int(n) for n in fine_n)
-        self.ctx = pic_init(mesh, el, gas, grains, run, stream)
+        if particles is None:
+            self.ctx = pic_init_plasma(mesh, el, gas, grains, run, (wl.te_ev, wl.ti_ev), stream)
+        else:
+            self.ctx = pic_init(mesh, el, gas, grains, run, stream)
         self.wl = wl
         self.nodes = wl.nx * wl.ny * (wl.nz + 1)
         self.ng = gr.size

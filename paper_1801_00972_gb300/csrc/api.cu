@@ -262,8 +262,15 @@ void pic_destroy(pic_ctx* ctx)
 
 int64_t pic_step_index(const pic_ctx* ctx) { return ctx ? ctx->step : -1; }
 
-pic_status pic_init(const pic_mesh* mesh, const pic_electrodes* el, const pic_gas* gas, const pic_grains* grains,
-                    const pic_run* run, void* cuda_stream, pic_ctx** out)
+}  // extern "C"
+
+namespace {
+
+// pic_init and pic_init_plasma: t_ev == nullptr takes the particles from the
+// host arrays of `run`, else draws run->n[sp] particles of species sp at
+// temperature t_ev[sp] on the device
+pic_status init_run(const pic_mesh* mesh, const pic_electrodes* el, const pic_gas* gas, const pic_grains* grains,
+                    const pic_run* run, const double* t_ev, void* cuda_stream, pic_ctx** out)
 {
     g_init_error.clear();
     if (!out) return fail(nullptr, PIC_EINVAL, "out is NULL");
@@ -309,6 +316,11 @@ pic_status pic_init(const pic_mesh* mesh, const pic_electrodes* el, const pic_ga
     for (int sp = 0; sp < 2; ++sp) {
         if (run->n[sp] < 0 || run->capacity[sp] < run->n[sp] || run->capacity[sp] > 0x7fffffffLL)
             return fail(nullptr, PIC_EINVAL, "run: need 0 <= n <= capacity < 2^31");
+        if (t_ev) {
+            if (!(t_ev[sp] >= 0.0) || !std::isfinite(t_ev[sp]))
+                return fail(nullptr, PIC_EINVAL, "plasma: temperatures must be finite and >= 0");
+            continue;
+        }
         if (run->n[sp] > 0 && (!run->x_host[sp] || !run->v_host[sp] || !run->id_host[sp]))
             return fail(nullptr, PIC_EINVAL, "run: NULL particle arrays");
         for (int64_t q = 0; q < run->n[sp]; ++q) {
@@ -319,6 +331,8 @@ pic_status pic_init(const pic_mesh* mesh, const pic_electrodes* el, const pic_ga
                 return fail(nullptr, PIC_EINVAL, "run: particle outside the box or non-finite");
         }
     }
+    if (t_ev && run->n[0] + run->n[1] > 0xFFFFFFFFLL)
+        return fail(nullptr, PIC_EINVAL, "plasma: n_e + n_i must fit the 32-bit particle ids");
     // grains: inside the box, one cell clear of both electrodes, <= 8 per MD cell
     std::vector<int> gcell(3 * (size_t)grains->n);
     for (int g = 0; g < grains->n; ++g) {
@@ -335,6 +349,9 @@ pic_status pic_init(const pic_mesh* mesh, const pic_electrodes* el, const pic_ga
         gcell[3 * g + 2] = (int)std::floor(p[2] / mesh->dx);
         if (gcell[3 * g + 2] < 1 || gcell[3 * g + 2] > nz - 2)
             return fail(nullptr, PIC_EINVAL, "grains: a grain's cell must be at least one cell from each electrode");
+        if (t_ev && !(1.5 * grains->radius_host[g] < mesh->dx))
+            return fail(nullptr, PIC_EINVAL, "plasma: the sampler keeps 1.5 grain radii clear, so radii must be "
+                                             "below dx / 1.5");
     }
     const size_t cells = (size_t)nx * ny * nz, nodes = (size_t)nx * ny * (nz + 1);
     std::vector<int> cell_ng(cells, 0), cell_g(cells * kMaxG, 0);
@@ -497,7 +514,7 @@ pic_status pic_init(const pic_mesh* mesh, const pic_electrodes* el, const pic_ga
     unsigned int max_id = 0;
     bool any = false;
     unsigned long long nslot[2] = {(unsigned long long)run->n[0], (unsigned long long)run->n[1]};
-    for (int sp = 0; sp < 2; ++sp) {
+    for (int sp = 0; sp < 2 && !t_ev; ++sp) {
         const int64_t n = run->n[sp];
         stage.assign(2 * psz * std::max<int64_t>(n, 1), 0);
         char* P = stage.data();
@@ -534,7 +551,7 @@ pic_status pic_init(const pic_mesh* mesh, const pic_electrodes* el, const pic_ga
         if (e == cudaSuccess) e = cudaMemcpy(c->vel[sp], V, psz * n, cudaMemcpyHostToDevice);
         if (e != cudaSuccess) { destroy(c); return cuda_fail(nullptr, e, "particle upload"); }
     }
-    const unsigned int next_id = any ? max_id + 1 : 0;
+    const unsigned int next_id = t_ev ? (unsigned int)(run->n[0] + run->n[1]) : any ? max_id + 1 : 0;
     std::vector<float> xs32(5 * (size_t)c->n_xs);
     for (size_t i = 0; i < xs32.size(); ++i) xs32[i] = (float)gas->xs_host[i];
     std::vector<double> gpos(3 * ng1, 0.0), grad(ng1, 0.0);
@@ -586,6 +603,12 @@ pic_status pic_init(const pic_mesh* mesh, const pic_electrodes* el, const pic_ga
         e = cudaMemset(c->d_bin, 0, sizeof(int));
         if (e == cudaSuccess) e = clear_moments(c, nullptr);
         if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    }
+    if (e == cudaSuccess && t_ev) {
+        // electrons take ids 0 .. n_e - 1, ions n_e .. n_e + n_i - 1
+        launch_init_plasma(c, 0, run->n[0], 0u, t_ev[0]);
+        launch_init_plasma(c, 1, run->n[1], (uint32_t)run->n[0], t_ev[1]);
+        e = cudaGetLastError();
     }
     if (e != cudaSuccess) { destroy(c); return cuda_fail(nullptr, e, "upload"); }
 
@@ -649,6 +672,28 @@ pic_status pic_init(const pic_mesh* mesh, const pic_electrodes* el, const pic_ga
     if (s == PIC_ENOTCONV) c->pending = PIC_ENOTCONV;
     *out = c;
     return PIC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+pic_status pic_init(const pic_mesh* mesh, const pic_electrodes* el, const pic_gas* gas, const pic_grains* grains,
+                    const pic_run* run, void* cuda_stream, pic_ctx** out)
+{
+    return init_run(mesh, el, gas, grains, run, nullptr, cuda_stream, out);
+}
+
+pic_status pic_init_plasma(const pic_mesh* mesh, const pic_electrodes* el, const pic_gas* gas,
+                           const pic_grains* grains, const pic_run* run, const double* t_ev, void* cuda_stream,
+                           pic_ctx** out)
+{
+    g_init_error.clear();
+    if (!t_ev) {
+        if (out) *out = nullptr;
+        return fail(nullptr, PIC_EINVAL, "t_ev is NULL");
+    }
+    return init_run(mesh, el, gas, grains, run, t_ev, cuda_stream, out);
 }
 
 pic_status pic_advance(pic_ctx* c)

@@ -619,6 +619,85 @@ __global__ void k_moments64(Geo g, const double4* pos, const double4* vel, const
 
 Geo geo(const pic_ctx* c) { return Geo{c->nx, c->ny, c->nz, c->dx, c->Lx, c->Ly, c->Lz}; }
 
+
+// Initial plasma drawn from the run's seed, the same definition the oracle
+// states: particle id p takes three uniforms at a time from its stream (p,
+// step 0, kPurInitPos) for a point u L until it lies farther than 1.5 radii
+// from every grain (minimum image in x and y; at most 64 tries, else the last
+// point), and three normals from (p, 0, kPurInitVel) times sqrt(T e / m).
+// Only the grains listed for the point's cell are tested: a point within
+// 1.5 r < dx of a grain lies in the grain's 3x3x3 region, whose cells list it.
+// The FP64 result is converted to the mixed layout exactly as the host upload
+// converts host arrays.
+struct InitP {
+    Geo g;
+    uint2 key;
+    int64_t n;
+    uint32_t id0;
+    double vth, vs;              // thermal speed (m/s); dt/dx (mixed velocities in cells/step)
+    const int* cell_ng;
+    const int* cell_g;
+    const double* gpos;
+    const double* grad;
+    double4* pos64;
+    double4* vel64;
+    float4* pos32;
+    float4* vel32;
+};
+
+__device__ bool near_grain(const InitP& p, const double x[3])
+{
+    int c[3];
+    double f[3];
+    locate(p.g, x, c, f);
+    const int cell = cell_of(p.g, c);
+    const int ng = p.cell_ng[cell];
+    const double L[3] = {p.g.Lx, p.g.Ly, p.g.Lz};
+    for (int t = 0; t < ng; ++t) {
+        const int gi = p.cell_g[cell * kMaxG + t];
+        double d[3];
+        for (int a = 0; a < 3; ++a) {
+            d[a] = x[a] - p.gpos[3 * gi + a];
+            if (a < 2 && d[a] > 0.5 * L[a]) d[a] = d[a] - L[a];
+            else if (a < 2 && d[a] < -0.5 * L[a]) d[a] = d[a] + L[a];
+        }
+        const double rx = 1.5 * p.grad[gi];
+        if (((d[0] * d[0] + d[1] * d[1]) + d[2] * d[2]) <= rx * rx) return true;
+    }
+    return false;
+}
+
+__global__ void k_init_plasma(const InitP p)
+{
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < p.n; q += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t id = p.id0 + (uint32_t)q;
+        const double L[3] = {p.g.Lx, p.g.Ly, p.g.Lz};
+        double x[3];
+        RStream rp(id, 0u, kPurInitPos, p.key);
+        for (int t = 0; t < 64; ++t) {
+            for (int a = 0; a < 3; ++a) x[a] = u01d(rp.next()) * L[a];
+            if (!near_grain(p, x)) break;
+        }
+        double nv[3], v[3];
+        RStream rv(id, 0u, kPurInitVel, p.key);
+        gauss3(rv, nv);
+        for (int a = 0; a < 3; ++a) v[a] = p.vth * nv[a];
+        int c[3];
+        double f[3];
+        locate(p.g, x, c, f);
+        if (p.pos64) {
+            p.pos64[q] = make_double4(x[0], x[1], x[2], (double)cell_of(p.g, c));
+            p.vel64[q] = make_double4(v[0], v[1], v[2], (double)id);
+        } else {
+            float o[3];
+            for (int a = 0; a < 3; ++a) o[a] = fminf((float)f[a], 0.99999994f);
+            const int cell = c[0] | (c[1] << 10) | (c[2] << 20);
+            p.pos32[q] = make_float4(o[0], o[1], o[2], __int_as_float(cell));
+            p.vel32[q] = make_float4((float)(v[0] * p.vs), (float)(v[1] * p.vs), (float)(v[2] * p.vs),
+                                     __uint_as_float(id));
+        }
+    }
+}
 }  // namespace
 
 void launch_push64(pic_ctx* c)
@@ -715,4 +794,27 @@ void launch_grain_table(pic_ctx* c, int gi)
     k_grain_table<<<1, 64, 0, c->stream>>>(c->nx, c->ny, c->nz, c->dx, c->phi, c->gcell, gi, c->gtab);
     c->launches += 1;
 }
+void launch_init_plasma(pic_ctx* c, int sp, int64_t n, uint32_t id0, double t_ev)
+{
+    if (n <= 0) return;
+    InitP p;
+    p.g = Geo{c->nx, c->ny, c->nz, c->dx, c->Lx, c->Ly, c->Lz};
+    p.key = c->key;
+    p.n = n;
+    p.id0 = id0;
+    p.vth = sqrt((t_ev * kQE) / (sp == 0 ? kME : kMAR));
+    p.vs = c->dt / c->dx;
+    p.cell_ng = c->cell_ng;
+    p.cell_g = c->cell_g;
+    p.gpos = c->gpos;
+    p.grad = c->grad;
+    const bool mixed = c->prec == PIC_MIXED;
+    p.pos64 = mixed ? nullptr : (double4*)c->pos[sp];
+    p.vel64 = mixed ? nullptr : (double4*)c->vel[sp];
+    p.pos32 = mixed ? (float4*)c->pos[sp] : nullptr;
+    p.vel32 = mixed ? (float4*)c->vel[sp] : nullptr;
+    k_init_plasma<<<grid_for(n, 256, 152 * 16), 256, 0, c->stream>>>(p);
+    c->launches += 1;
+}
+
 }  // namespace pic

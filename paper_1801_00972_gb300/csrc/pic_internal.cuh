@@ -27,7 +27,10 @@ constexpr int kMaxG = 8;        // grains per MD cell
 constexpr int kTab = 64 * 3;    // doubles per grain field table (4x4x4 nodes x 3)
 
 // Philox counter third word: what the draws are for
-enum Purpose : uint32_t { kPurMCC = 1, kPurDir = 2, kPurNeutral = 3, kPurChildDir = 4, kPurChildNeutral = 5 };
+enum Purpose : uint32_t {
+    kPurMCC = 1, kPurDir = 2, kPurNeutral = 3, kPurChildDir = 4, kPurChildNeutral = 5,
+    kPurInitPos = 10, kPurInitVel = 11   // the initial plasma (6-9: Coulomb pairing and scattering)
+};
 
 // error codes latched in ctx->d_err (first one wins)
 enum DevErr : int { kErrNone = 0, kErrCapacity = PIC_ECAPACITY, kErrNonFinite = PIC_ENONFINITE };
@@ -291,6 +294,8 @@ void launch_deposit64(pic_ctx* c);
 void launch_moments64(pic_ctx* c);
 void launch_grains(pic_ctx* c);                  // Q from counts, grain CIC into rq
 void launch_grain_table(pic_ctx* c, int g);      // E of phi on grain g's 4x4x4 region nodes
+// the initial plasma of species sp drawn from the seed (ids id0 ..), either layout
+void launch_init_plasma(pic_ctx* c, int sp, int64_t n, uint32_t id0, double t_ev);
 
 // particles_mixed.cu
 void launch_efield32(pic_ctx* c);

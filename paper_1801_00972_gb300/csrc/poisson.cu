@@ -1943,6 +1943,7 @@ namespace pic {
 namespace {
 
 constexpr size_t kNaMaxNodes = 131072;       // largest fine mesh, in nodes
+constexpr size_t kNaMaxCoarse = 4096;        // largest coarsest level (red-black sweeps in one block)
 constexpr size_t kNaAlign = 256;
 // phi_alt + f (16 B/node) + three level arrays summing to at most 4/3 of the
 // fine nodes in doubles (32 B/node) + norms + per-array alignment padding
@@ -2099,6 +2100,13 @@ extern "C" pic_status pic_solve_noalloc(int32_t nx, int32_t ny, int32_t nz, doub
     }
     if (off > kNaBytes) {
         set_global_error("pic_solve_noalloc: scratch layout exceeds the fixed array");
+        return PIC_EINVAL;
+    }
+    if (c.lv[c.nl - 1].nodes > kNaMaxCoarse) {
+        // halving stops at the first level with nx or ny not divisible by 4, or nz odd or below 4; the
+        // one-block smoother of the coarsest level is only exact enough on a small level
+        set_global_error("pic_solve_noalloc: the mesh coarsens only to a level of more than 4096 nodes; halving "
+                         "needs nx, ny divisible by 4 and nz even and >= 4 at each level");
         return PIC_EINVAL;
     }
     // rhs from the fixed-point charge; electrode values on both potential buffers
