@@ -42,9 +42,18 @@ def build(force: bool = False) -> str:
     tmp = _LIB + f".{os.getpid()}.tmp"
     cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off", "-fno-fast-math",
            "-o", tmp, _SRC, "-lm"]
-    subprocess.check_call(cmd)
+    # OpenMP shares independent planes, modes and particles among the host
+    # cores (results do not depend on the thread count); without it, one thread
+    r = subprocess.run(cmd[:1] + ["-fopenmp"] + cmd[1:], capture_output=True, text=True)
+    if r.returncode != 0:
+        subprocess.check_call(cmd)
     os.replace(tmp, _LIB)
     return _LIB
+
+
+def threads() -> int:
+    """Host threads the oracle's parallel loops use."""
+    return lib().orc_threads()
 
 
 class Cfg(C.Structure):
@@ -120,6 +129,8 @@ def lib():
             L.orc_efield.argtypes = [i32, i32, i32, dbl, pd, pd, pd, pd]
             L.orc_iso_dir.argtypes = [u32, u32, u32, pu32, pd]
             L.orc_gauss3.argtypes = [u32, u32, u32, pu32, pd]
+            L.orc_threads.argtypes = []
+            L.orc_threads.restype = i32
             _lib = L
     return _lib
 

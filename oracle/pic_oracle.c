@@ -33,6 +33,18 @@
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+int orc_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
 
 #define QE    1.602176634e-19      /* elementary charge, C          */
 #define EPS0  8.8541878128e-12     /* vacuum permittivity, F/m      */
@@ -166,7 +178,10 @@ void orc_gauss3(uint32_t id, uint32_t step, uint32_t purpose, const uint32_t key
 /* ------------------------------------------------------------------------ */
 /* Exact discrete Poisson solve (Eq. 3) on the node mesh                     */
 /* ------------------------------------------------------------------------ */
-/* 2-D DFT of one plane (nx fastest), sign -1 forward, +1 backward (no 1/n). */
+/* 2-D DFT of one plane (nx fastest), sign -1 forward, +1 backward (no 1/n):
+ * X(m, m2) = sum_{i,j} x(i, j) exp(sign 2 pi i (m i / nx + m2 j / ny)).
+ * Plain O(n^2) sums for any size; planes whose sides are both powers of two
+ * use the radix-2 fast transform below, which computes the same sums. */
 static void dft2(int nx, int ny, const double* cx, const double* sx, const double* cy,
                  const double* sy, double sign, const double* ire, const double* iim,
                  double* ore, double* oim, double* tre, double* tim)
@@ -197,9 +212,77 @@ static void dft2(int nx, int ny, const double* cx, const double* sx, const doubl
         }
 }
 
+static int pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
+
+/* Radix-2 Cooley-Tukey fast Fourier transform of n = 2^q complex values at
+ * stride `st`, in place: the bit-reversal permutation, then q passes of
+ * butterflies (a, b) -> (a + w b, a - w b) over blocks of length 2, 4, ..., n
+ * with w = exp(sign 2 pi i t / len); c[t], s[t] = cos, sin(2 pi t / n). */
+static void fft1(int n, double* re, double* im, size_t st, double sign, const double* c, const double* s)
+{
+    for (int i = 1, j = 0; i < n; ++i) {
+        int bit = n >> 1;
+        for (; j & bit; bit >>= 1) j ^= bit;
+        j ^= bit;
+        if (i < j) {
+            double t = re[i * st]; re[i * st] = re[j * st]; re[j * st] = t;
+            t = im[i * st]; im[i * st] = im[j * st]; im[j * st] = t;
+        }
+    }
+    for (int len = 2; len <= n; len <<= 1) {
+        const int half = len >> 1, step = n / len;
+        for (int b = 0; b < n; b += len)
+            for (int k = 0; k < half; ++k) {
+                const double wr = c[k * step], wi = sign * s[k * step];
+                const size_t ia = (size_t)(b + k) * st, ib = (size_t)(b + k + half) * st;
+                const double xr = re[ib] * wr - im[ib] * wi;
+                const double xi = re[ib] * wi + im[ib] * wr;
+                re[ib] = re[ia] - xr; im[ib] = im[ia] - xi;
+                re[ia] = re[ia] + xr; im[ia] = im[ia] + xi;
+            }
+    }
+}
+
+/* the 2-D transform of one plane in place: rows (x), then columns (y) */
+static void plane_transform(int nx, int ny, const double* cx, const double* sx, const double* cy,
+                            const double* sy, double sign, double* re, double* im, double* tre, double* tim)
+{
+    if (pow2(nx) && pow2(ny)) {
+        for (int j = 0; j < ny; ++j) fft1(nx, re + (size_t)j * nx, im + (size_t)j * nx, 1, sign, cx, sx);
+        for (int i = 0; i < nx; ++i) fft1(ny, re + i, im + i, (size_t)nx, sign, cy, sy);
+        return;
+    }
+    dft2(nx, ny, cx, sx, cy, sy, sign, re, im, tre, tim, tre + (size_t)nx * ny, tim + (size_t)nx * ny);
+    memcpy(re, tre, sizeof(double) * (size_t)nx * ny);
+    memcpy(im, tim, sizeof(double) * (size_t)nx * ny);
+}
+
+/* Tridiagonal solve of one Fourier mode (Thomas): u_{k-1} + d u_k + u_{k+1} = r_k
+ * for k = 1..n with u_0 = u_{n+1} = 0 (electrode terms already moved into r);
+ * cp, rr, ri are scratch of n + 1 values. */
+static void thomas_mode(int n, double d, double* rr, double* ri, double* cp)
+{
+    cp[1] = 1.0 / d;
+    rr[1] = rr[1] / d; ri[1] = ri[1] / d;
+    for (int k = 2; k <= n; ++k) {
+        double mm = d - cp[k - 1];
+        cp[k] = 1.0 / mm;
+        rr[k] = (rr[k] - rr[k - 1]) / mm;
+        ri[k] = (ri[k] - ri[k - 1]) / mm;
+    }
+    for (int k = n - 1; k >= 1; --k) {
+        rr[k] = rr[k] - cp[k] * rr[k + 1];
+        ri[k] = ri[k] - cp[k] * ri[k + 1];
+    }
+}
+
 /* Solve (sum of the six neighbours - 6 phi)/dx^2 = -f on the interior nodes
  * k = 1..nz-1, periodic in x,y, phi(k=0) = v_bot, phi(k=nz) = v_top.
- * f and phi are node arrays indexed (k*ny + j)*nx + i. */
+ * f and phi are node arrays indexed (k*ny + j)*nx + i.  The discrete Fourier
+ * transform in x and y diagonalises the periodic part, leaving one
+ * tridiagonal system in z per mode.  Planes and modes are independent, so
+ * they are shared among OpenMP threads; the result does not depend on the
+ * thread count. */
 int orc_poisson(int nx, int ny, int nz, double dx, const double* f, double v_bot,
                 double v_top, double* phi)
 {
@@ -211,28 +294,38 @@ int orc_poisson(int nx, int ny, int nz, double dx, const double* f, double v_bot
     double* sx = (double*)malloc(sizeof(double) * nx);
     double* cy = (double*)malloc(sizeof(double) * ny);
     double* sy = (double*)malloc(sizeof(double) * ny);
-    double* tre = (double*)malloc(sizeof(double) * P);
-    double* tim = (double*)malloc(sizeof(double) * P);
-    double* cp = (double*)malloc(sizeof(double) * (nz + 1));
-    double* rr = (double*)malloc(sizeof(double) * (nz + 1));
-    double* ri = (double*)malloc(sizeof(double) * (nz + 1));
-    if (!re || !im || !cx || !sx || !cy || !sy || !tre || !tim || !cp || !rr || !ri) return -1;
+    if (!re || !im || !cx || !sx || !cy || !sy) return -1;
     for (int t = 0; t < nx; ++t) { cx[t] = cos(2.0 * PI_D * t / nx); sx[t] = sin(2.0 * PI_D * t / nx); }
     for (int t = 0; t < ny; ++t) { cy[t] = cos(2.0 * PI_D * t / ny); sy[t] = sin(2.0 * PI_D * t / ny); }
+    int bad = 0;
 
     /* right-hand side -dx^2 f, transformed plane by plane */
-    double* g = (double*)malloc(sizeof(double) * P);
-    for (int k = 1; k < nz; ++k) {
-        for (int p = 0; p < P; ++p) g[p] = -(dx * dx) * f[(size_t)k * P + p];
-        dft2(nx, ny, cx, sx, cy, sy, -1.0, g, NULL, re + (size_t)k * P, im + (size_t)k * P, tre, tim);
+    #pragma omp parallel reduction(|:bad)
+    {
+        double* t2 = (double*)malloc(sizeof(double) * 4 * (size_t)P);
+        if (!t2) bad = 1;
+        #pragma omp for schedule(static)
+        for (int k = 1; k < nz; ++k) {
+            if (!t2) continue;
+            double* pr = re + (size_t)k * P;
+            for (int p = 0; p < P; ++p) pr[p] = -(dx * dx) * f[(size_t)k * P + p];
+            plane_transform(nx, ny, cx, sx, cy, sy, -1.0, pr, im + (size_t)k * P, t2, t2 + 2 * (size_t)P);
+        }
+        free(t2);
     }
-    free(g);
 
     /* one tridiagonal system per Fourier mode:
      * u_{k-1} + d u_k + u_{k+1} = r_k,  d = 2 cos(th1) + 2 cos(th2) - 6 */
-    for (int m2 = 0; m2 < ny; ++m2)
-        for (int m1 = 0; m1 < nx; ++m1) {
-            const int p = m2 * nx + m1;
+    #pragma omp parallel reduction(|:bad)
+    {
+        double* cp = (double*)malloc(sizeof(double) * (nz + 1));
+        double* rr = (double*)malloc(sizeof(double) * (nz + 1));
+        double* ri = (double*)malloc(sizeof(double) * (nz + 1));
+        if (!cp || !rr || !ri) bad = 1;
+        #pragma omp for schedule(static)
+        for (int p = 0; p < P; ++p) {
+            if (!cp || !rr || !ri) continue;
+            const int m1 = p % nx, m2 = p / nx;
             const double d = (2.0 * cx[m1] + 2.0 * cy[m2]) - 6.0;
             const double b0 = (p == 0) ? (double)P * v_bot : 0.0;
             const double bn = (p == 0) ? (double)P * v_top : 0.0;
@@ -240,34 +333,29 @@ int orc_poisson(int nx, int ny, int nz, double dx, const double* f, double v_bot
             for (int k = 1; k <= n; ++k) { rr[k] = re[(size_t)k * P + p]; ri[k] = im[(size_t)k * P + p]; }
             rr[1] -= b0;
             rr[n] -= bn;
-            /* forward elimination */
-            cp[1] = 1.0 / d;
-            rr[1] = rr[1] / d; ri[1] = ri[1] / d;
-            for (int k = 2; k <= n; ++k) {
-                double mm = d - cp[k - 1];
-                cp[k] = 1.0 / mm;
-                rr[k] = (rr[k] - rr[k - 1]) / mm;
-                ri[k] = (ri[k] - ri[k - 1]) / mm;
-            }
-            for (int k = n - 1; k >= 1; --k) {
-                rr[k] = rr[k] - cp[k] * rr[k + 1];
-                ri[k] = ri[k] - cp[k] * ri[k + 1];
-            }
+            thomas_mode(n, d, rr, ri, cp);
             for (int k = 1; k <= n; ++k) { re[(size_t)k * P + p] = rr[k]; im[(size_t)k * P + p] = ri[k]; }
         }
+        free(cp); free(rr); free(ri);
+    }
 
     /* back to space */
-    double* ore = (double*)malloc(sizeof(double) * P);
-    double* oim = (double*)malloc(sizeof(double) * P);
-    for (int k = 1; k < nz; ++k) {
-        dft2(nx, ny, cx, sx, cy, sy, +1.0, re + (size_t)k * P, im + (size_t)k * P, ore, oim, tre, tim);
-        for (int q = 0; q < P; ++q) phi[(size_t)k * P + q] = ore[q] / (double)P;
+    #pragma omp parallel reduction(|:bad)
+    {
+        double* t2 = (double*)malloc(sizeof(double) * 4 * (size_t)P);
+        if (!t2) bad = 1;
+        #pragma omp for schedule(static)
+        for (int k = 1; k < nz; ++k) {
+            if (!t2) continue;
+            double* pr = re + (size_t)k * P;
+            plane_transform(nx, ny, cx, sx, cy, sy, +1.0, pr, im + (size_t)k * P, t2, t2 + 2 * (size_t)P);
+            for (int q = 0; q < P; ++q) phi[(size_t)k * P + q] = pr[q] / (double)P;
+        }
+        free(t2);
     }
     for (int q = 0; q < P; ++q) { phi[q] = v_bot; phi[(size_t)nz * P + q] = v_top; }
-    free(ore); free(oim);
-    free(re); free(im); free(cx); free(sx); free(cy); free(sy); free(tre); free(tim);
-    free(cp); free(rr); free(ri);
-    return 0;
+    free(re); free(im); free(cx); free(sx); free(cy); free(sy);
+    return bad ? -1 : 0;
 }
 
 /* E = -grad phi at the nodes (Eq. 4): central differences, periodic in x,y;
@@ -275,6 +363,7 @@ int orc_poisson(int nx, int ny, int nz, double dx, const double* f, double v_bot
 void orc_efield(int nx, int ny, int nz, double dx, const double* phi, double* ex, double* ey, double* ez)
 {
     const double h2 = 2.0 * dx;
+    #pragma omp parallel for schedule(static)
     for (int k = 0; k <= nz; ++k)
         for (int j = 0; j < ny; ++j)
             for (int i = 0; i < nx; ++i) {
@@ -375,7 +464,12 @@ static void deposit_one(const orc_sim* s, int64_t* rq, const double* p, int64_t 
     for (int dz = 0; dz < 2; ++dz)
         for (int dy = 0; dy < 2; ++dy)
             for (int dxi = 0; dxi < 2; ++dxi)
-                rq[node_at(s, c[0] + dxi, c[1] + dy, c[2] + dz)] += charge * (w[0][dxi] * w[1][dy] * w[2][dz]);
+            {
+                const int64_t add = charge * (w[0][dxi] * w[1][dy] * w[2][dz]);
+                int64_t* r = rq + node_at(s, c[0] + dxi, c[1] + dy, c[2] + dz);
+                #pragma omp atomic
+                *r += add;
+            }
 }
 
 /* CIC gather of a node vector field with the same fixed-point weights */
@@ -479,17 +573,30 @@ static double xs_at(const double* tab, int n, double de, double eps)
     return tab[i] + fr * (tab[i + 1] - tab[i]);
 }
 
-static void push_child(orc_sim* s, const child_rec* r)
+/* what one thread's particles did during a step: event counts and ionization
+ * products, merged after the particle loop */
+typedef struct { int64_t cnt[ORC_C_N]; child_rec* ch; int64_t nch, capch; } step_log;
+
+static void push_child(step_log* t, const child_rec* r)
 {
-    if (s->nch == s->capch) {
-        s->capch = s->capch ? 2 * s->capch : 64;
-        s->ch = (child_rec*)realloc(s->ch, sizeof(child_rec) * s->capch);
+    if (t->nch == t->capch) {
+        t->capch = t->capch ? 2 * t->capch : 64;
+        t->ch = (child_rec*)realloc(t->ch, sizeof(child_rec) * t->capch);
     }
-    s->ch[s->nch++] = *r;
+    t->ch[t->nch++] = *r;
+}
+
+static int thread_id(void)
+{
+#ifdef _OPENMP
+    return omp_get_thread_num();
+#else
+    return 0;
+#endif
 }
 
 /* null-collision MCC for one particle after its push (Table I) */
-static void mcc(orc_sim* s, int sp, double* p, double* v, uint32_t id)
+static void mcc(const orc_sim* s, step_log* t, int sp, double* p, double* v, uint32_t id)
 {
     const uint32_t step = (uint32_t)s->step;
     uint32_t ctr[4] = { id, step, PUR_MCC, 0 }, u[4];
@@ -516,7 +623,7 @@ static void mcc(orc_sim* s, int sp, double* p, double* v, uint32_t id)
             double fac = 1.0 - ((2.0 * ME) / MAR) * (1.0 - cosx);
             double vn = vm * sqrt(fac);
             for (int a = 0; a < 3; ++a) v[a] = vn * dir[a];
-            s->cnt[ORC_C_E_EL]++;
+            t->cnt[ORC_C_E_EL]++;
             return;
         }
         acc = acc + nu_ex;
@@ -526,7 +633,7 @@ static void mcc(orc_sim* s, int sp, double* p, double* v, uint32_t id)
             rs_iso(&rd, dir);
             double vn = sqrt(e2 / s->hm[0]);
             for (int a = 0; a < 3; ++a) v[a] = vn * dir[a];
-            s->cnt[ORC_C_E_EXC]++;
+            t->cnt[ORC_C_E_EXC]++;
             return;
         }
         acc = acc + nu_io;
@@ -542,8 +649,8 @@ static void mcc(orc_sim* s, int sp, double* p, double* v, uint32_t id)
             rstream rc; rs_init(&rc, id, step, PUR_CHILD_DIR, s->key); rs_iso(&rc, d2);
             rstream rn; rs_init(&rn, id, step, PUR_CHILD_NEUTRAL, s->key); rs_gauss3(&rn, gn);
             for (int a = 0; a < 3; ++a) { cr.ve[a] = vn * d2[a]; cr.vi[a] = sig_n * gn[a]; }
-            push_child(s, &cr);
-            s->cnt[ORC_C_E_ION]++;
+            push_child(t, &cr);
+            t->cnt[ORC_C_E_ION]++;
         }
         return;
     }
@@ -564,13 +671,13 @@ static void mcc(orc_sim* s, int sp, double* p, double* v, uint32_t id)
         double dir[3];
         rstream rd; rs_init(&rd, id, step, PUR_DIR, s->key); rs_iso(&rd, dir);
         for (int a = 0; a < 3; ++a) v[a] = (v[a] + vn[a]) * 0.5 + (0.5 * gm) * dir[a];
-        s->cnt[ORC_C_I_EL]++;
+        t->cnt[ORC_C_I_EL]++;
         return;
     }
     acc = acc + nu_cx;
     if (R < acc) {
         for (int a = 0; a < 3; ++a) v[a] = vn[a];
-        s->cnt[ORC_C_I_CX]++;
+        t->cnt[ORC_C_I_CX]++;
     }
 }
 
@@ -594,8 +701,10 @@ static void grow(orc_sim* s, int sp, int64_t need)
 static void deposit_all(orc_sim* s)
 {
     memset(s->rq, 0, sizeof(int64_t) * nodes_of(s));
+    /* integer sums: any order of the additions gives the same result */
     for (int sp = 0; sp < 2; ++sp) {
         const int64_t charge = sp == 0 ? -1 : 1;
+        #pragma omp parallel for schedule(static)
         for (int64_t q = 0; q < s->n[sp]; ++q) deposit_one(s, s->rq, s->x[sp] + 3 * q, charge);
     }
     for (int g = 0; g < s->c.n_grains; ++g)
@@ -871,56 +980,91 @@ int orc_advance(orc_sim* s)
     const int M = s->c.md_sub > 0 ? s->c.md_sub : 1;
     const double dt = s->c.dt;
     const double dtm = dt / (double)M;
+    /* particles are independent within a step: OpenMP threads take ranges of
+     * them, each with its own counters and product list; survivors are then
+     * compacted in their original order, so nothing depends on the threads */
+    const int nt = orc_threads();
+    step_log* T = (step_log*)calloc((size_t)nt, sizeof(step_log));
     for (int sp = 0; sp < 2; ++sp) {
         if (sp == 1 && (s->c.flags & ORC_IONS_FROZEN)) continue;
         const double qmdt = s->qm[sp] * dt;
         const double qmdtm = s->qm[sp] * dtm;
-        int64_t keep = 0;
-        for (int64_t q = 0; q < s->n[sp]; ++q) {
-            double p[3], v[3];
-            memcpy(p, s->x[sp] + 3 * q, sizeof p);
-            memcpy(v, s->v[sp] + 3 * q, sizeof v);
-            const uint32_t id = s->id[sp][q];
-            int c[3]; double f[3]; int64_t w[3][2];
-            locate(s, p, c, f);
-            qweights(f, w);
-            int fate = 0, grain = -1;
-            if (s->cell_ng[cell_index(s, c)] == 0) {
-                double E[3];
-                gather(s, s->ex, s->ey, s->ez, c, w, E);
-                for (int a = 0; a < 3; ++a) v[a] = v[a] + qmdt * E[a];
-                for (int a = 0; a < 3; ++a) p[a] = p[a] + v[a] * dt;
-                fate = boundary(s, p);
-            } else {
-                for (int m = 0; m < M; ++m) {
+        const int64_t n = s->n[sp];
+        unsigned char* keep_it = (unsigned char*)malloc((size_t)(n > 0 ? n : 1));
+        #pragma omp parallel
+        {
+            step_log* t = &T[thread_id()];
+            #pragma omp for schedule(static)
+            for (int64_t q = 0; q < n; ++q) {
+                double p[3], v[3];
+                memcpy(p, s->x[sp] + 3 * q, sizeof p);
+                memcpy(v, s->v[sp] + 3 * q, sizeof v);
+                const uint32_t id = s->id[sp][q];
+                int c[3]; double f[3]; int64_t w[3][2];
+                locate(s, p, c, f);
+                qweights(f, w);
+                int fate = 0, grain = -1;
+                keep_it[q] = 0;
+                if (s->cell_ng[cell_index(s, c)] == 0) {
                     double E[3];
-                    if (m > 0) { locate(s, p, c, f); qweights(f, w); }
                     gather(s, s->ex, s->ey, s->ez, c, w, E);
-                    md_correct(s, p, c, w, E);
-                    for (int a = 0; a < 3; ++a) v[a] = v[a] + qmdtm * E[a];
-                    for (int a = 0; a < 3; ++a) p[a] = p[a] + v[a] * dtm;
+                    for (int a = 0; a < 3; ++a) v[a] = v[a] + qmdt * E[a];
+                    for (int a = 0; a < 3; ++a) p[a] = p[a] + v[a] * dt;
                     fate = boundary(s, p);
-                    if (fate) break;
-                    grain = absorbed_by(s, p);
-                    if (grain >= 0) break;
+                } else {
+                    for (int m = 0; m < M; ++m) {
+                        double E[3];
+                        if (m > 0) { locate(s, p, c, f); qweights(f, w); }
+                        gather(s, s->ex, s->ey, s->ez, c, w, E);
+                        md_correct(s, p, c, w, E);
+                        for (int a = 0; a < 3; ++a) v[a] = v[a] + qmdtm * E[a];
+                        for (int a = 0; a < 3; ++a) p[a] = p[a] + v[a] * dtm;
+                        fate = boundary(s, p);
+                        if (fate) break;
+                        grain = absorbed_by(s, p);
+                        if (grain >= 0) break;
+                    }
                 }
+                if (fate == 1) { t->cnt[sp == 0 ? ORC_C_LOST_BOT_E : ORC_C_LOST_BOT_I]++; continue; }
+                if (fate == 2) { t->cnt[sp == 0 ? ORC_C_LOST_TOP_E : ORC_C_LOST_TOP_I]++; continue; }
+                if (fate == 3) { t->cnt[ORC_C_ERR]++; continue; }
+                if (grain >= 0) {
+                    #pragma omp atomic
+                    s->gabs[2 * grain + sp]++;
+                    t->cnt[sp == 0 ? ORC_C_ABS_E : ORC_C_ABS_I]++;
+                    continue;
+                }
+                if (!(s->c.flags & ORC_NO_MCC)) mcc(s, t, sp, p, v, id);
+                memcpy(s->x[sp] + 3 * q, p, sizeof p);
+                memcpy(s->v[sp] + 3 * q, v, sizeof v);
+                keep_it[q] = 1;
             }
-            if (fate == 1) { s->cnt[sp == 0 ? ORC_C_LOST_BOT_E : ORC_C_LOST_BOT_I]++; continue; }
-            if (fate == 2) { s->cnt[sp == 0 ? ORC_C_LOST_TOP_E : ORC_C_LOST_TOP_I]++; continue; }
-            if (fate == 3) { s->cnt[ORC_C_ERR]++; continue; }
-            if (grain >= 0) {
-                s->gabs[2 * grain + sp]++;
-                s->cnt[sp == 0 ? ORC_C_ABS_E : ORC_C_ABS_I]++;
-                continue;
+        }
+        int64_t keep = 0;
+        for (int64_t q = 0; q < n; ++q) {
+            if (!keep_it[q]) continue;
+            if (keep != q) {
+                memcpy(s->x[sp] + 3 * keep, s->x[sp] + 3 * q, 3 * sizeof(double));
+                memcpy(s->v[sp] + 3 * keep, s->v[sp] + 3 * q, 3 * sizeof(double));
+                s->id[sp][keep] = s->id[sp][q];
             }
-            if (!(s->c.flags & ORC_NO_MCC)) mcc(s, sp, p, v, id);
-            memcpy(s->x[sp] + 3 * keep, p, sizeof p);
-            memcpy(s->v[sp] + 3 * keep, v, sizeof v);
-            s->id[sp][keep] = id;
             keep++;
         }
+        free(keep_it);
         s->n[sp] = keep;
     }
+    for (int t = 0; t < nt; ++t) {
+        for (int a = 0; a < ORC_C_N; ++a) s->cnt[a] += T[t].cnt[a];
+        for (int64_t r = 0; r < T[t].nch; ++r) {
+            if (s->nch == s->capch) {
+                s->capch = s->capch ? 2 * s->capch : 64;
+                s->ch = (child_rec*)realloc(s->ch, sizeof(child_rec) * s->capch);
+            }
+            s->ch[s->nch++] = T[t].ch[r];
+        }
+        free(T[t].ch);
+    }
+    free(T);
     /* grain charges after this step's absorptions */
     for (int g = 0; g < s->c.n_grains; ++g)
         s->gq[g] = (QE * s->c.weight) * (double)(s->gabs[2 * g + 1] - s->gabs[2 * g + 0]);
@@ -955,6 +1099,91 @@ int orc_step(orc_sim* s)
     if (rc) return rc;
     if (s->c.flags & ORC_MOMENTS) moments_accumulate(s);
     return 0;
+}
+
+/* Unit-charge mesh field of grain g on the 4x4x4 nodes of its MD region
+ * (Eq. 5: E_PIC^dust per coulomb of grain charge): the exact solution of the
+ * discrete Poisson equation (Eq. 3) with grounded electrodes for one coulomb
+ * deposited by CIC at the grain centre, then E by the differences of Eq. 4.
+ * It is the same discrete solution orc_poisson gives for that source,
+ * evaluated only where the region's differences need it: the source sits on
+ * 8 nodes, so each Fourier mode's right-hand side is a sum of 8 terms; one
+ * tridiagonal solve per mode; the inverse transform is summed on the 6x6x6
+ * nodes around the region (clipped to the electrode planes, where phi = 0).
+ * tab: [(lk*4 + lj)*4 + li][3], region node (gc - 1 + (li, lj, lk)). */
+static void grain_table(const orc_sim* s, int g, double* tab)
+{
+    const int nx = s->c.nx, ny = s->c.ny, nz = s->c.nz, P = nx * ny;
+    const double dx = s->c.dx;
+    const double scale1 = ((1.0 / (dx * dx * dx)) * 0x1p-42) / EPS0;
+    int gc[3]; double fr[3]; int64_t w[3][2];
+    locate(s, s->gpos + 3 * g, gc, fr);
+    qweights(fr, w);
+    double* cx = (double*)malloc(sizeof(double) * nx);
+    double* sx = (double*)malloc(sizeof(double) * nx);
+    double* cy = (double*)malloc(sizeof(double) * ny);
+    double* sy = (double*)malloc(sizeof(double) * ny);
+    double* cp = (double*)malloc(sizeof(double) * (nz + 1));
+    double* rr = (double*)malloc(sizeof(double) * (nz + 1));
+    double* ri = (double*)malloc(sizeof(double) * (nz + 1));
+    for (int t = 0; t < nx; ++t) { cx[t] = cos(2.0 * PI_D * t / nx); sx[t] = sin(2.0 * PI_D * t / nx); }
+    for (int t = 0; t < ny; ++t) { cy[t] = cos(2.0 * PI_D * t / ny); sy[t] = sin(2.0 * PI_D * t / ny); }
+    /* the 6x6x6 block of nodes gc - 2 .. gc + 3: phi summed over the modes */
+    double blk[6][6][6];
+    memset(blk, 0, sizeof blk);
+    for (int p = 0; p < P; ++p) {
+        const int m1 = p % nx, m2 = p / nx;
+        for (int k = 0; k <= nz; ++k) { rr[k] = 0.0; ri[k] = 0.0; }
+        /* forward transform of the right-hand side -dx^2 f of the 8 source nodes */
+        for (int dz = 0; dz < 2; ++dz)
+            for (int dy = 0; dy < 2; ++dy)
+                for (int di = 0; di < 2; ++di) {
+                    const int i = (gc[0] + di) % nx, j = (gc[1] + dy) % ny, k = gc[2] + dz;
+                    const double v = -(dx * dx) * ((double)(w[0][di] * w[1][dy] * w[2][dz]) * scale1);
+                    const int t1 = (int)(((long)m1 * i) % nx), t2 = (int)(((long)m2 * j) % ny);
+                    const double er = cx[t1] * cy[t2] - sx[t1] * sy[t2];     /* cos(a + b) */
+                    const double ei = -(sx[t1] * cy[t2] + cx[t1] * sy[t2]);  /* -sin(a + b) */
+                    rr[k] += v * er;
+                    ri[k] += v * ei;
+                }
+        thomas_mode(nz - 1, (2.0 * cx[m1] + 2.0 * cy[m2]) - 6.0, rr, ri, cp);
+        /* inverse transform at the block nodes (interior planes only) */
+        for (int b = 0; b < 6; ++b) {
+            const int k = gc[2] - 2 + b;
+            if (k < 1 || k > nz - 1) continue;
+            for (int bj = 0; bj < 6; ++bj) {
+                const int j = ((gc[1] - 2 + bj) % ny + ny) % ny;
+                const int t2 = (int)(((long)m2 * j) % ny);
+                for (int bi = 0; bi < 6; ++bi) {
+                    const int i = ((gc[0] - 2 + bi) % nx + nx) % nx;
+                    const int t1 = (int)(((long)m1 * i) % nx);
+                    const double er = cx[t1] * cy[t2] - sx[t1] * sy[t2];
+                    const double ei = sx[t1] * cy[t2] + cx[t1] * sy[t2];
+                    blk[b][bj][bi] += rr[k] * er - ri[k] * ei;
+                }
+            }
+        }
+    }
+    for (int b = 0; b < 6; ++b)
+        for (int bj = 0; bj < 6; ++bj)
+            for (int bi = 0; bi < 6; ++bi) blk[b][bj][bi] = blk[b][bj][bi] / (double)P;
+    /* E = -grad phi at the region nodes (orc_efield's formulas) */
+    const double h2 = 2.0 * dx;
+    for (int lk = 0; lk < 4; ++lk)
+        for (int lj = 0; lj < 4; ++lj)
+            for (int li = 0; li < 4; ++li) {
+                const int bi = li + 1, bj = lj + 1, b = lk + 1, k = gc[2] - 1 + lk;
+                double* tv = tab + ((lk * 4 + lj) * 4 + li) * 3;
+                tv[0] = (blk[b][bj][bi - 1] - blk[b][bj][bi + 1]) / h2;
+                tv[1] = (blk[b][bj - 1][bi] - blk[b][bj + 1][bi]) / h2;
+                if (k == 0)
+                    tv[2] = ((3.0 * blk[b][bj][bi] - 4.0 * blk[b + 1][bj][bi]) + blk[b + 2][bj][bi]) / h2;
+                else if (k == nz)
+                    tv[2] = ((4.0 * blk[b - 1][bj][bi] - 3.0 * blk[b][bj][bi]) - blk[b - 2][bj][bi]) / h2;
+                else
+                    tv[2] = (blk[b - 1][bj][bi] - blk[b + 1][bj][bi]) / h2;
+            }
+    free(cx); free(sx); free(cy); free(sy); free(cp); free(rr); free(ri);
 }
 
 /* Initial plasma drawn from the run's seed (the paper starts from a uniform
@@ -1054,32 +1283,11 @@ orc_sim* orc_create(const orc_cfg* cfg)
                     else s->cnt[ORC_C_ERR]++;
                 }
     }
-    /* unit-charge mesh field of each grain on the 4x4x4 nodes of its region */
-    if (ng) {
-        double* f = (double*)calloc(N, sizeof(double));
-        double* ph = (double*)calloc(N, sizeof(double));
-        double *ex = (double*)calloc(N, sizeof(double)), *ey = (double*)calloc(N, sizeof(double)),
-               *ez = (double*)calloc(N, sizeof(double));
-        int64_t* rq = (int64_t*)calloc(N, sizeof(int64_t));
-        const double scale1 = ((1.0 / (dx * dx * dx)) * 0x1p-42) / EPS0;
-        for (int g = 0; g < ng; ++g) {
-            memset(rq, 0, sizeof(int64_t) * N);
-            deposit_one(s, rq, s->gpos + 3 * g, 1);
-            for (size_t q = 0; q < N; ++q) f[q] = (double)rq[q] * scale1;
-            orc_poisson(cfg->nx, cfg->ny, cfg->nz, dx, f, 0.0, 0.0, ph);
-            orc_efield(cfg->nx, cfg->ny, cfg->nz, dx, ph, ex, ey, ez);
-            const int gc[3] = { (int)floor(s->gpos[3 * g] / dx), (int)floor(s->gpos[3 * g + 1] / dx),
-                                (int)floor(s->gpos[3 * g + 2] / dx) };
-            for (int lk = 0; lk < 4; ++lk)
-                for (int lj = 0; lj < 4; ++lj)
-                    for (int li = 0; li < 4; ++li) {
-                        size_t n = node_at(s, gc[0] - 1 + li + cfg->nx, gc[1] - 1 + lj + cfg->ny, gc[2] - 1 + lk);
-                        double* tv = s->gtab + ((size_t)g * 64 + (lk * 4 + lj) * 4 + li) * 3;
-                        tv[0] = ex[n]; tv[1] = ey[n]; tv[2] = ez[n];
-                    }
-        }
-        free(f); free(ph); free(ex); free(ey); free(ez); free(rq);
-    }
+    /* unit-charge mesh field of each grain on the 4x4x4 nodes of its region;
+     * grains are independent (one thread per grain, so the rounding does not
+     * depend on the thread count) */
+    #pragma omp parallel for schedule(dynamic, 1)
+    for (int g = 0; g < ng; ++g) grain_table(s, g, s->gtab + (size_t)g * 64 * 3);
     uint32_t maxid = 0; int any = 0;
     for (int sp = 0; sp < 2; ++sp) {
         grow(s, sp, cfg->n_init[sp] > 0 ? cfg->n_init[sp] : 1);

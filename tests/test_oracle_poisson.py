@@ -54,8 +54,10 @@ def _assemble(nx, ny, nz, dx):
     return A
 
 
-def test_dense_lu_small():
-    nx, ny, nz, dx = 4, 4, 6, 0.3e-3
+@pytest.mark.parametrize("nx,ny,nz", [(4, 4, 6), (8, 16, 5), (6, 4, 6), (12, 10, 4)])
+def test_dense_lu_small(nx, ny, nz):
+    # power-of-two planes take the fast transform, the others the plain DFT sums
+    dx = 0.3e-3
     rng = np.random.default_rng(3)
     f = rng.standard_normal((nz + 1, ny, nx)) * 1e7
     vb, vt = -13.0, 4.0
@@ -101,3 +103,37 @@ def test_efield_polynomials():
     phi = 5e7 * z ** 2
     ex, ey, ez = O.efield(nx, ny, nz, dx, phi)
     assert np.allclose(ez, -1e8 * z, rtol=1e-11, atol=1e-7)
+
+
+@pytest.mark.parametrize("shape,grains", [((8, 8, 16), 1), ((16, 8, 12), 3), ((12, 10, 14), 2)])
+def test_grain_tables_equal_a_full_solve(shape, grains):
+    """The oracle's unit-charge grain tables (Eq. 5), computed mode by mode at
+    the region nodes only, equal the full exact solve of the same source: the
+    CIC deposit of one coulomb (fixed-point weights round(f 2^14), half to
+    even) solved with grounded electrodes, differenced by orc_efield."""
+    from paper_1801_00972_gb300 import inputs as I
+    nx, ny, nz = shape
+    wl = I.small(nx=nx, ny=ny, nz=nz, n_e=0, n_i=0, grains=grains, seed=5)
+    s = O.Sim(wl, [(np.zeros((0, 3)), np.zeros((0, 3)), np.zeros(0, np.uint32))] * 2)
+    tab = s.gtab()
+    eps0, dx = 8.8541878128e-12, wl.dx
+    for g, p in enumerate(wl.grain_pos):
+        q = p / dx
+        c = np.floor(q).astype(int)
+        a = np.clip(np.rint((q - c) * 16384).astype(np.int64), 0, 16384)
+        f = np.zeros((nz + 1, ny, nx))
+        for dz in (0, 1):
+            for dy in (0, 1):
+                for di in (0, 1):
+                    wgt = ((a[0] if di else 16384 - a[0]) * (a[1] if dy else 16384 - a[1])
+                           * (a[2] if dz else 16384 - a[2]))
+                    f[c[2] + dz, (c[1] + dy) % ny, (c[0] + di) % nx] += wgt * 2.0 ** -42 / dx ** 3 / eps0
+        phi = O.poisson(nx, ny, nz, dx, f, 0.0, 0.0)
+        ex, ey, ez = O.efield(nx, ny, nz, dx, phi)
+        want = np.zeros((4, 4, 4, 3))
+        for lk in range(4):
+            for lj in range(4):
+                for li in range(4):
+                    k, j, i = c[2] - 1 + lk, (c[1] - 1 + lj) % ny, (c[0] - 1 + li) % nx
+                    want[lk, lj, li] = ex[k, j, i], ey[k, j, i], ez[k, j, i]
+        assert np.max(np.abs(tab[g] - want)) <= 1e-11 * np.max(np.abs(want)), g
