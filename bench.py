@@ -2,15 +2,18 @@
 """Benchmark of the PIC-MCC/PPPM step on one GB300 (or N independent replicas).
 
 One bench step = one full time step of the particle cycle (gather, push with
-MD subcycling near grains, absorption, MCC, deposit, Poisson solve) of the rf
-sheath workload with a 7-grain cluster: 64x64x256 cells of 0.2 mm, 100 V at
-13.56 MHz, argon at 2 Pa, 1e7 macroparticles (5e6 e + 5e6 Ar+), synthetic
-seeded inputs.  Particle arrays (320 MB mixed, 640 MB FP64) exceed the 129 MB L2.
+MD subcycling near grains, absorption, MCC, deposit, Poisson solve).  The
+headline workload is the large mixed-precision case: 256x256x1024 cells of
+0.2 mm, 5e8 macroparticles (2.5e8 e + 2.5e8 Ar+, drawn on the device from the
+seed), a 100-grain seeded cluster, 100 V at 13.56 MHz, argon at 2 Pa.
+Particle arrays (16 GB mixed, 32 GB FP64) far exceed the 129 MB L2.
 
 Prints one JSON line.  ``value`` is mixed-precision particle-steps/s summed
-over ranks; the FP64 path, Poisson solves/s, the push kernel's roofline, an
-end-to-end figure through the C ABI with host buffers and the CPU oracle's
-figure on a bounded sample ride along.
+over ranks; the FP64 path on the same workload, Poisson solves/s, the push
+kernel's roofline, an end-to-end figure through the C ABI from host arrays,
+the paper-scale 128x128x512 cluster (2e8 particles) and the 64x64x256 rf
+sheath (1e7 particles, with Coulomb collisions, diagnostics and the 48-run
+ensemble as extra legs), and the CPU oracle on a bounded sample ride along.
 ``--impl reference`` times the CPU oracle alone (rank 0) on the same workload.
 """
 from __future__ import annotations
@@ -41,6 +44,8 @@ TUNE_STEPS = 20      # steps per candidate interval of the sort autotuner
 BYTES_NODE_MIXED = 74 + 40
 BYTES_NODE_FP64 = 148 + 40
 DIAG_PHASES = 16           # rf phase bins of the diagnostics run
+# committed ncu summary of the push kernel on the headline workload (DRAM traffic per launch)
+PUSH_PROFILE = "k_push32_w4_256x256x1024_5e8.md"
 
 
 def poisson_block(pr, cold, wl, bytes_node, peak, peak_kind, precision):
@@ -58,11 +63,12 @@ def poisson_block(pr, cold, wl, bytes_node, peak, peak_kind, precision):
 def args():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", type=int, default=1)
-    ap.add_argument("--fp64-steps", type=int, default=None)
+    ap.add_argument("--workload", type=int, default=4, help="headline workload (inputs.workload index)")
+    ap.add_argument("--fp64-steps", type=int, default=6)
+    ap.add_argument("--e2e-steps", type=int, default=100)
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -71,6 +77,8 @@ def args():
     ap.add_argument("--no-tune", action="store_true", help="fixed sort interval (no autotuning)")
     ap.add_argument("--no-coulomb", action="store_true", help="skip the run with Coulomb collisions")
     ap.add_argument("--no-diag", action="store_true", help="skip the run with every diagnostic on")
+    ap.add_argument("--no-extra", action="store_true", help="headline workload only (no 128x128x512 and "
+                                                            "64x64x256 legs)")
     return ap.parse_args()
 
 
@@ -167,7 +175,8 @@ def run_gpu(P, I, wl, parts, prec, steps, warmup, stream, gpu, flags=0, tune=Tru
     cold = cold_solves(run)
     run.close()
     return dict(ms=ms, pushed=c1["pushed"] - c0["pushed"], prof=prof, kernels=prof["kernels"] - k0,
-                live=[int(x) for x in n], clocks=clk.summary(), counters=c1, cold=cold, sort_every=sort_every)
+                live=[int(x) for x in n], clocks=clk.summary(), counters=c1, cold=cold, sort_every=sort_every,
+                steps=steps)
 
 
 def cold_solves(run, reps=3):
@@ -218,29 +227,35 @@ def traffic_from_profile(kernel_source, name, kernel="k_push32"):
         return None
 
 
-def e2e(P, wl, parts, prec, steps, stream, sort_every):
-    """Through the public API from host buffers: init (host->device copy of the
-    particles), then each step followed by a device->host read of the grain
-    charges (the step's result)."""
-    import numpy as np
+def e2e(P, I, wl, prec, steps, stream, sort_every):
+    """Through the public API from host buffers: pic_init from host particle
+    arrays (validation, conversion and the host->device copy), then each step
+    followed by a device->host read of the grain charges (the step's result).
+    The host arrays are drawn before the timed region."""
     import torch
+    parts = I.sample_particles(wl)
+    h2d = sum(p[0].nbytes + p[1].nbytes + p[2].nbytes for p in parts)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     run = P.Run(wl, parts, prec=prec, stream=stream, sort_every=sort_every)
+    t_init = time.perf_counter() - t0
+    del parts
     _, c0 = run.counts()
+    t1 = time.perf_counter()
     for _ in range(steps):
         run.step(1)
         run.grains()
     _, c1 = run.counts()
     torch.cuda.synchronize()
-    t = time.perf_counter() - t0
+    t2 = time.perf_counter()
     run.close()
-    h2d = sum(p[0].nbytes + p[1].nbytes + p[2].nbytes for p in parts)
     d2h = (2 * 8 + 8) * len(wl.grain_r)
     ps = c1["pushed"] - c0["pushed"]
-    return {"value": ps / t, "unit": "particle-steps/s", "h2d_bytes_per_step": int(h2d // steps),
-            "d2h_bytes_per_step": int(d2h), "seconds": t,
-            "note": "pic_init from host arrays + per-step pic_step(1) and pic_grain_charges"}
+    return {"value": ps / (t2 - t0), "unit": "particle-steps/s", "h2d_bytes_per_step": int(h2d // steps),
+            "d2h_bytes_per_step": int(d2h), "seconds": t2 - t0, "steps": steps, "init_s": t_init,
+            "steps_value": ps / (t2 - t1),
+            "note": "pic_init from host arrays (timed, its H2D bytes spread over the steps) + per step "
+                    "pic_step(1) and a pic_grain_charges read; steps_value excludes pic_init"}
 
 
 def batch_bench(P, I, steps, warmup):
@@ -265,9 +280,10 @@ def batch_bench(P, I, steps, warmup):
             "timing": "host clock around pic_batch_step (synchronises all run streams)"}
 
 
-def oracle_sample(wl, n_particles, steps, seed=1):
+def oracle_sample(wl, n_particles, steps, seed=1, threads=None):
     """The CPU oracle, as it stands, on a bounded sample of the workload: the same
-    mesh, grains and gas with n_particles macroparticles (init excluded)."""
+    mesh, grains and gas with n_particles macroparticles (init excluded), on
+    `threads` host threads (None: all)."""
     import dataclasses
 
     import oracle as O
@@ -275,6 +291,7 @@ def oracle_sample(wl, n_particles, steps, seed=1):
     half = n_particles // 2
     w = dataclasses.replace(wl, n_e=half, n_i=half, weight=wl.weight * wl.n_e / max(half, 1))
     parts = I.sample_particles(w, seed=seed)
+    O.set_threads(threads or 0)
     s = O.Sim(w, parts)
     n0 = s.count(0) + s.count(1)
     t0 = time.perf_counter()
@@ -283,7 +300,10 @@ def oracle_sample(wl, n_particles, steps, seed=1):
         done += s.count(0) + s.count(1)
         s.step()
     t = time.perf_counter() - t0
-    return done / t, t, n0
+    cores = O.threads()
+    del s
+    O.set_threads(0)
+    return done / t, t, n0, cores
 
 
 def replica_seed(seed, rank):
@@ -311,23 +331,52 @@ def reference_arm(a):
         return
     from paper_1801_00972_gb300 import inputs as I
     wl = I.workload(a.workload)
-    n = 600_000
-    steps = a.steps + a.warmup
-    # keep the whole run to a few minutes: ~0.6 s per oracle step on this mesh
-    budget = 150.0
-    if steps * 0.6 > budget:
-        n = 100_000
-    value, t, n0 = oracle_sample(wl, n, a.warmup + a.steps)
+    # a bounded sample: each oracle step also solves the whole mesh exactly
+    n = 2_000_000 if wl.nodes > 10_000_000 else 600_000
+    steps = a.warmup + a.steps
+    if wl.nodes > 10_000_000:
+        steps = min(steps, 12)
+    value, t, n0, cores = oracle_sample(wl, n, steps)
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "particle-steps/s", "n_gpus": a.gpus,
-            "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1000 * t / (a.warmup + a.steps),
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1000 * t / steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": wl.name + f" {wl.nx}x{wl.ny}x{wl.nz} cells, {len(wl.grain_r)} grains, rf",
-                       "sample_particles": n0},
-            "cpu_baseline": {"value": value, "unit": "particle-steps/s", "cores": 1, "kind": "oracle",
-                             "sample": f"{n0} particles of the workload's 1e7 on its full mesh, "
-                                       f"{a.warmup + a.steps} steps, init excluded"},
+            "config": {"workload": describe(wl), "sample_particles": n0, "oracle_steps": steps},
+            "cpu_baseline": {"value": value, "unit": "particle-steps/s", "cores": cores, "kind": "oracle",
+                             "sample": f"{n0} particles (the workload's {wl.n_e + wl.n_i:.0e}) on its full mesh "
+                                       f"and grains, {steps} steps incl. the exact Poisson solve, init excluded"},
             "e2e": {"value": value, "unit": "particle-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def describe(wl):
+    return (f"{wl.nx}x{wl.ny}x{wl.nz} cells of {wl.dx * 1e3:.1f} mm, {wl.n_e + wl.n_i:.0e} macroparticles, "
+            f"{len(wl.grain_r)} grains, {wl.v_rf:.0f} V at {wl.f_rf / 1e6:.2f} MHz, "
+            f"argon {wl.n_gas * 1.380649e-23 * wl.t_gas:.0f} Pa")
+
+
+def push_roofline(res, peak, peak_kind, profile_name):
+    pr = res["prof"]
+    push_s = pr["push_ms"] / 1000.0
+    achieved = res["pushed"] * BYTES_MIXED / push_s / 1e9 if push_s > 0 else 0.0
+    return {"bound": "hbm", "kernel": "k_push32 (fused gather/push/absorb/MCC test/deposit)",
+            "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak, "peak_kind": peak_kind,
+            "bytes_per_particle_step": BYTES_MIXED,
+            "traffic": traffic_from_profile("particles_mixed.cu", profile_name) if profile_name else None,
+            "timing": "CUDA events around each step's push phase, in which the electron and ion launches "
+                      "overlap on two streams (the MD-region kernel on a third); achieved = both launches' "
+                      "algorithmic bytes / the phase time",
+            "phase_ms_per_step": pr["push_ms"] / max(res["steps"], 1),
+            "launches": pr["push_launches"]}
+
+
+def leg(P, I, wl, peak, peak_kind, steps, warmup, stream, gpu, flags, tune, profile_name=None, parts=None):
+    """One mixed-precision workload: value, push roofline and Poisson figures."""
+    r = run_gpu(P, I, wl, parts, P.PIC_MIXED, steps, warmup, stream, gpu, flags, tune=tune)
+    return r, {"workload": describe(wl), "value": r["pushed"] / (r["ms"] / 1000.0), "unit": "particle-steps/s",
+               "steps": steps, "ms_per_step": r["ms"] / steps, "sort_every": r["sort_every"],
+               "roofline": push_roofline(r, peak, peak_kind, profile_name),
+               "poisson": poisson_block(r["prof"], r["cold"], wl, BYTES_NODE_MIXED, peak, peak_kind, "mixed"),
+               "gpu_launches": r["kernels"], "clocks": r["clocks"]}
 
 
 def main():
@@ -350,36 +399,55 @@ def main():
     import paper_1801_00972_gb300 as P
     from paper_1801_00972_gb300 import inputs as I
     P.load()
+    peak, peak_kind = peaks()
     wl = I.workload(a.workload)
     # replicas: each rank runs its own independent run (different seed)
     wl.seed = replica_seed(wl.seed, rank)
-    parts = I.sample_particles(wl)
     stream = torch.cuda.current_stream().cuda_stream
     flags = P.PIC_F_NO_GRAPH if a.eager else 0
-    mixed = run_gpu(P, I, wl, parts, P.PIC_MIXED, a.steps, a.warmup, stream, local, flags, tune=not a.no_tune)
+    # the headline: the initial plasma drawn on the device from the seed (pic_init_plasma)
+    mixed = run_gpu(P, I, wl, None, P.PIC_MIXED, a.steps, a.warmup, stream, local, flags, tune=not a.no_tune)
     fp64 = None
     if not a.no_fp64:
-        fp64 = run_gpu(P, I, wl, parts, P.PIC_FP64, a.fp64_steps or max(a.steps // 4, 10), a.warmup, stream, local,
-                       flags, tune=False)
-    ee = None if a.no_e2e else e2e(P, wl, parts, P.PIC_MIXED, max(a.steps // 4, 10), stream, mixed["sort_every"])
-    coul = None
-    if not a.no_coulomb:
-        # the same step with the binary Coulomb collisions of Table I switched on
-        coul = run_gpu(P, I, wl, parts, P.PIC_MIXED, max(a.steps // 4, 20), a.warmup, stream, local,
-                       flags | P.PIC_F_COULOMB, tune=False, sort_every=mixed["sort_every"])
-    diag = None
-    if not a.no_diag:
-        # the same step with every diagnostic of Sec. IV on: node moments with
-        # temperatures in 16 rf phase bins, the 200^3 fine grid of 0.08 dx cubes
-        # on the grain cluster, and the per-plane EEPF
-        import numpy as np
-        h = 0.08 * wl.dx
-        centre = np.asarray(wl.grain_pos).mean(0)
-        diag = run_gpu(P, I, wl, parts, P.PIC_MIXED, max(a.steps // 4, 20), a.warmup, stream, local,
-                       flags | P.PIC_F_MOMENTS, tune=False, sort_every=mixed["sort_every"], mom_phases=DIAG_PHASES,
-                       fine_n=(200, 200, 200), fine_h=h, fine_origin=tuple(centre - 100 * h), eepf_bins=200,
-                       eepf_de_ev=0.1)
-    bb = None if (a.no_batch or world > 1) else batch_bench(P, I, max(a.steps // 4, 10), a.warmup)
+        fp64 = run_gpu(P, I, wl, None, P.PIC_FP64, a.fp64_steps, min(a.warmup, 3), stream, local, flags,
+                       tune=False, sort_every=mixed["sort_every"])
+    ee = None
+    if not a.no_e2e and world == 1:
+        ee = e2e(P, I, wl, P.PIC_MIXED, a.e2e_steps, stream, mixed["sort_every"])
+    extra = {}
+    if not a.no_extra and world == 1:
+        # the paper-scale cluster: 128x128x512 cells, 50 grains, 2e8 particles
+        w2 = I.workload(2)
+        _, extra["config_128x128x512"] = leg(P, I, w2, peak, peak_kind, max(a.steps // 2, 20), a.warmup, stream,
+                                             local, flags, not a.no_tune)
+        # the rf sheath with the 7-grain cluster: 64x64x256 cells, 1e7 particles, with its extra legs
+        w1 = I.workload(1)
+        r1, extra["config_64x64x256"] = leg(P, I, w1, peak, peak_kind, 200, a.warmup, stream, local, flags,
+                                            not a.no_tune)
+        c2 = extra["config_64x64x256"]
+        base_ms = r1["ms"] / 200
+        if not a.no_coulomb:
+            coul = run_gpu(P, I, w1, None, P.PIC_MIXED, 50, a.warmup, stream, local, flags | P.PIC_F_COULOMB,
+                           tune=False, sort_every=r1["sort_every"])
+            c2["coulomb"] = {"value": coul["pushed"] / (coul["ms"] / 1000.0), "unit": "particle-steps/s",
+                             "steps": 50, "ms_per_step": coul["ms"] / 50,
+                             "extra_ms_per_step": coul["ms"] / 50 - base_ms,
+                             "note": "mixed, PIC_F_COULOMB (e-e, e-Ar+, Ar+-Ar+ binary collisions, lnL = 10)"}
+        if not a.no_diag:
+            import numpy as np
+            h = 0.08 * w1.dx
+            centre = np.asarray(w1.grain_pos).mean(0)
+            diag = run_gpu(P, I, w1, None, P.PIC_MIXED, 50, a.warmup, stream, local, flags | P.PIC_F_MOMENTS,
+                           tune=False, sort_every=r1["sort_every"], mom_phases=DIAG_PHASES, fine_n=(200, 200, 200),
+                           fine_h=h, fine_origin=tuple(centre - 100 * h), eepf_bins=200, eepf_de_ev=0.1)
+            c2["diagnostics"] = {"value": diag["pushed"] / (diag["ms"] / 1000.0), "unit": "particle-steps/s",
+                                 "steps": 50, "ms_per_step": diag["ms"] / 50,
+                                 "extra_ms_per_step": diag["ms"] / 50 - base_ms,
+                                 "note": f"mixed, PIC_F_MOMENTS with T_e/T_i, {DIAG_PHASES} rf phase bins, 200^3 "
+                                         "fine grid (0.08 dx) on the cluster, EEPF 200 x 0.1 eV per cell plane, "
+                                         "sampled every step"}
+        if not a.no_batch:
+            extra["batch"] = batch_bench(P, I, 20, a.warmup)
 
     def agg(x):
         return None if x is None else aggregate(x["ms"], x["pushed"], "cuda")
@@ -389,11 +457,6 @@ def main():
     if rank != 0:
         torch.distributed.destroy_process_group()
         return
-    peak, peak_kind = peaks()
-    pr = mixed["prof"]
-    push_s = pr["push_ms"] / 1000.0
-    achieved = mixed["pushed"] * BYTES_MIXED / push_s / 1e9 if push_s > 0 else 0.0
-    solves_s = pr["solves"] / (pr["solve_ms"] / 1000.0) if pr["solve_ms"] > 0 else None
     line = {
         "metric": METRIC,
         "value": m_tot / (m_ms / 1000.0),
@@ -405,25 +468,19 @@ def main():
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "f32 particles + f64 Poisson refinement (mixed)",
+        "dtype": "mixed: f32 particle offsets and velocities with int cells, f32 multigrid V-cycles with "
+                 "double-float (two-f32, about 48-bit) residual refinement and an f32 exact coarse-level "
+                 "solve, int64 fixed-point charge",
         "data": "synthetic",
-        "config": {"workload": f"rf sheath, 7-grain cluster, {wl.nx}x{wl.ny}x{wl.nz} cells, "
-                               f"{wl.n_e + wl.n_i:.0e} macroparticles, 13.56 MHz 100 V, 2 Pa",
+        "config": {"workload": describe(wl) + ", 100-grain seeded cluster, initial plasma drawn on the device "
+                                              "from the seed",
                    "parallelism": "replicas only" if world > 1 else "1 GPU",
-                   "l2": "inputs larger than L2 (particle arrays 320 MB mixed / 640 MB FP64)",
+                   "l2": "inputs larger than L2 (particle arrays 16 GB mixed / 32 GB FP64)",
                    "sort_every": mixed["sort_every"],
                    "sort_interval": "fixed" if a.no_tune else "autotuned (pic_tune_sort)",
                    "tol": 1e-10},
-        "roofline": {"bound": "hbm", "kernel": "k_push32 (fused gather/push/MD/absorb/MCC/deposit)",
-                     "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                     "peak_kind": peak_kind, "bytes_per_particle_step": BYTES_MIXED,
-                     "traffic": traffic_from_profile("particles_mixed.cu", "k_push32_w1_64x64x256_1e7.md"),
-                     "timing": "CUDA events around each step's push phase, in which the electron and ion "
-                               "launches overlap on two streams; achieved = both launches' algorithmic bytes "
-                               "/ the phase time",
-                     "phase_ms_per_step": pr["push_ms"] / max(pr["push_launches"] // 2, 1),
-                     "launches": pr["push_launches"]},
-        "poisson": poisson_block(pr, mixed["cold"], wl, BYTES_NODE_MIXED, peak, peak_kind, "mixed"),
+        "roofline": push_roofline(mixed, peak, peak_kind, PUSH_PROFILE),
+        "poisson": poisson_block(mixed["prof"], mixed["cold"], wl, BYTES_NODE_MIXED, peak, peak_kind, "mixed"),
         "gpu_launches": mixed["kernels"],
         "clocks": mixed["clocks"],
         "live_particles_end": mixed["live"],
@@ -432,41 +489,26 @@ def main():
         fp = fp64["prof"]
         fpush = fp["push_ms"] / 1000.0
         fach = fp64["pushed"] * BYTES_FP64 / fpush / 1e9 if fpush > 0 else 0.0
-        line["fp64"] = {"value": f[1] / (f[0] / 1000.0), "unit": "particle-steps/s", "steps": fp64_steps(a),
-                        "ms_per_step": f[0] / fp64_steps(a),
+        line["fp64"] = {"value": f[1] / (f[0] / 1000.0), "unit": "particle-steps/s", "steps": a.fp64_steps,
+                        "ms_per_step": f[0] / a.fp64_steps,
                         "push_achieved_gbs": fach, "push_frac": fach / peak,
                         "poisson": poisson_block(fp, fp64["cold"], wl, BYTES_NODE_FP64, peak, peak_kind, "fp64"),
                         "mixed_speedup": (m_tot / m_ms) / (f[1] / f[0])}
     if ee is not None:
         line["e2e"] = ee
-    if coul is not None:
-        cs = max(a.steps // 4, 20)
-        line["coulomb"] = {"value": coul["pushed"] / (coul["ms"] / 1000.0), "unit": "particle-steps/s",
-                           "steps": cs, "ms_per_step": coul["ms"] / cs,
-                           "extra_ms_per_step": coul["ms"] / cs - m_ms / a.steps,
-                           "note": "mixed, PIC_F_COULOMB (e-e, e-Ar+, Ar+-Ar+ binary collisions, lnL = 10)"}
-    if diag is not None:
-        ds = max(a.steps // 4, 20)
-        line["diagnostics"] = {"value": diag["pushed"] / (diag["ms"] / 1000.0), "unit": "particle-steps/s",
-                               "steps": ds, "ms_per_step": diag["ms"] / ds,
-                               "extra_ms_per_step": diag["ms"] / ds - m_ms / a.steps,
-                               "note": f"mixed, PIC_F_MOMENTS with T_e/T_i, {DIAG_PHASES} rf phase bins, 200^3 fine "
-                                       "grid (0.08 dx) on the cluster, EEPF 200 x 0.1 eV per cell plane, sampled "
-                                       "every step"}
-    if bb is not None:
-        line["batch"] = bb
+    line.update(extra)
     if not a.no_cpu:
-        v, t, n0 = oracle_sample(wl, 400_000, 4)
-        line["cpu_baseline"] = {"value": v, "unit": "particle-steps/s", "cores": 1, "kind": "oracle",
-                                "sample": f"{n0} of the 1e7 particles on the full 64x64x256 mesh with its 7 grains, "
-                                          f"4 steps incl. the exact Poisson solve, init excluded ({t:.1f} s)"}
+        v, t, n0, cores = oracle_sample(wl, 2_000_000, 2)
+        line["cpu_baseline"] = {"value": v, "unit": "particle-steps/s", "cores": cores, "kind": "oracle",
+                                "sample": f"{n0} of the {wl.n_e + wl.n_i:.0e} particles on the full "
+                                          f"{wl.nx}x{wl.ny}x{wl.nz} mesh with its {len(wl.grain_r)} grains, "
+                                          f"2 steps incl. the exact Poisson solve, init excluded ({t:.1f} s)"}
+        v1, t1, n1, _ = oracle_sample(wl, 500_000, 1, threads=1)
+        line["cpu_baseline"]["one_core"] = {"value": v1, "cores": 1,
+                                            "sample": f"{n1} particles, 1 step incl. the exact solve ({t1:.1f} s)"}
     print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
-
-
-def fp64_steps(a):
-    return a.fp64_steps or max(a.steps // 4, 10)
 
 
 if __name__ == "__main__":

@@ -56,6 +56,11 @@ def threads() -> int:
     return lib().orc_threads()
 
 
+def set_threads(n: int) -> None:
+    """Use n host threads from now on (0: all of them)."""
+    lib().orc_set_threads(int(n))
+
+
 class Cfg(C.Structure):
     _fields_ = [
         ("nx", C.c_int32), ("ny", C.c_int32), ("nz", C.c_int32), ("md_sub", C.c_int32),
@@ -131,6 +136,8 @@ def lib():
             L.orc_gauss3.argtypes = [u32, u32, u32, pu32, pd]
             L.orc_threads.argtypes = []
             L.orc_threads.restype = i32
+            L.orc_set_threads.argtypes = [i32]
+            L.orc_set_threads.restype = None
             _lib = L
     return _lib
 

@@ -46,6 +46,15 @@ int orc_threads(void)
 #endif
 }
 
+void orc_set_threads(int n)
+{
+#ifdef _OPENMP
+    omp_set_num_threads(n > 0 ? n : omp_get_num_procs());
+#else
+    (void)n;
+#endif
+}
+
 #define QE    1.602176634e-19      /* elementary charge, C          */
 #define EPS0  8.8541878128e-12     /* vacuum permittivity, F/m      */
 #define ME    9.1093837015e-31     /* electron mass, kg             */

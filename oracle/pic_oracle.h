@@ -114,8 +114,9 @@ int      orc_oml_charges(const orc_sim* s, int with_cx, double* out);
 int      orc_field_at(orc_sim* s, const double p[3], double E[3]);
 void     orc_set_grain_counts(orc_sim* s, const int64_t* n_abs /* 2*ng */);
 
-/* host threads of the parallel loops (1 without OpenMP) */
+/* host threads of the parallel loops (1 without OpenMP); set n (0: all cores) */
 int      orc_threads(void);
+void     orc_set_threads(int n);
 
 /* stand-alone pieces, used by the tests that pin the oracle */
 void     orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);

@@ -264,10 +264,82 @@ def small(nx=8, ny=8, nz=16, n_e=2000, n_i=2000, grains=1, seed=7, **over) -> Wo
     return Workload(**args)
 
 
+def _near_grains(x, wl, chunk=1 << 22):
+    """Mask of the points within 1.5 radii of a grain centre (plain distance).
+    Only points whose cell lies in a grain's 3x3x3 cell block can be that close
+    (1.5 r < dx), so the distances are taken for those alone."""
+    dx = wl.dx
+    flag = np.zeros((wl.nz, wl.ny, wl.nx), bool)
+    for p, r in zip(wl.grain_pos, wl.grain_r):
+        assert 1.5 * r < dx
+        c = np.floor(np.asarray(p) / dx).astype(int)
+        for dk in (-1, 0, 1):
+            k = c[2] + dk
+            if 0 <= k < wl.nz:
+                for dj in (-1, 0, 1):
+                    for di in (-1, 0, 1):
+                        flag[k, (c[1] + dj) % wl.ny, (c[0] + di) % wl.nx] = True
+    bad = np.zeros(len(x), bool)
+    for a in range(0, len(x), chunk):
+        xs = x[a:a + chunk]
+        c = np.minimum(np.floor(xs / dx).astype(np.int64), np.array([wl.nx - 1, wl.ny - 1, wl.nz - 1]))
+        cand = np.nonzero(flag[c[:, 2], c[:, 1], c[:, 0]])[0]
+        if cand.size == 0:
+            continue
+        xc = xs[cand]
+        near = np.zeros(cand.size, bool)
+        for p, r in zip(wl.grain_pos, wl.grain_r):
+            near |= np.sum((xc - p) ** 2, 1) <= (1.5 * r) ** 2
+        bad[a + cand[near]] = True
+    return bad
+
+
+_BIG = 1 << 25          # species above this many particles are drawn in parallel chunks
+
+
+def _sample_chunk(wl, n, t_ev, m, ss, x, v):
+    rng = np.random.default_rng(ss)
+    L = np.array(wl.box)
+    x[:] = rng.random((n, 3)) * L
+    if len(wl.grain_r):
+        for _ in range(10):
+            bad = _near_grains(x, wl)
+            if not bad.any():
+                break
+            x[bad] = rng.random((int(bad.sum()), 3)) * L
+    np.minimum(x, np.nextafter(L, 0), out=x)
+    v[:] = rng.standard_normal((n, 3)) * math.sqrt(t_ev * QE / m)
+
+
+def _sample_big(wl, seed, chunk=1 << 23):
+    """Large species: chunks of 2^23 particles, each from its own child seed of
+    the workload seed, drawn on the host cores in parallel."""
+    import concurrent.futures as cf
+    import os
+    out = []
+    base = 0
+    root = np.random.SeedSequence(seed)
+    for sp, (n, t_ev, m) in enumerate(((wl.n_e, wl.te_ev, ME), (wl.n_i, wl.ti_ev, MAR))):
+        x = np.empty((n, 3))
+        v = np.empty((n, 3))
+        starts = list(range(0, n, chunk))
+        seqs = root.spawn(len(starts))
+        with cf.ThreadPoolExecutor(max_workers=min(32, os.cpu_count() or 1)) as ex:
+            list(ex.map(lambda a: _sample_chunk(wl, min(chunk, n - a[1]), t_ev, m, a[0], x[a[1]:a[1] + chunk],
+                                                v[a[1]:a[1] + chunk]), zip(seqs, starts)))
+        out.append((x, v, np.arange(base, base + n, dtype=np.uint32)))
+        base += n
+    return out
+
+
 def sample_particles(wl: Workload, seed: int | None = None):
     """Uniform positions in the box (outside the grains), Maxwellian velocities.
     Returns [(x (n,3), v (n,3), id (n,) uint32) for electrons, ions]; electron ids
-    are 0..n_e-1 and ion ids n_e..n_e+n_i-1."""
+    are 0..n_e-1 and ion ids n_e..n_e+n_i-1.  Workloads with more than 2^25
+    particles of a species are drawn in parallel chunks (another random stream,
+    the same distributions)."""
+    if max(wl.n_e, wl.n_i) > _BIG:
+        return _sample_big(wl, wl.seed if seed is None else seed)
     rng = np.random.default_rng(wl.seed if seed is None else seed)
     L = np.array(wl.box)
     out = []
@@ -276,9 +348,7 @@ def sample_particles(wl: Workload, seed: int | None = None):
         x = rng.random((n, 3)) * L
         if len(wl.grain_r):
             for _ in range(10):
-                bad = np.zeros(n, bool)
-                for p, r in zip(wl.grain_pos, wl.grain_r):
-                    bad |= np.sum((x - p) ** 2, 1) <= (1.5 * r) ** 2
+                bad = _near_grains(x, wl)
                 if not bad.any():
                     break
                 x[bad] = rng.random((int(bad.sum()), 3)) * L

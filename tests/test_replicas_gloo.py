@@ -67,7 +67,7 @@ def test_reference_arm_line(tmp_path):
     import json as _json
     import subprocess
     r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
-                        "--warmup", "0"], capture_output=True, text=True, cwd=ROOT, timeout=600,
+                        "--warmup", "0", "--workload", "1"], capture_output=True, text=True, cwd=ROOT, timeout=600,
                        env={**os.environ, "RANK": "0"})
     assert r.returncode == 0, r.stderr[-2000:]
     lines = [l for l in r.stdout.splitlines() if l.startswith("{")]
