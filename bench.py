@@ -34,7 +34,8 @@ METRIC = "particle-steps/s and Poisson solves/s, mixed vs FP64, 1 GB300, % HBM r
 BYTES_MIXED = 64     # per particle-step: float4 pos + float4 vel, read and written
 BYTES_FP64 = 128     # double4 pos + double4 vel, read and written
 SORT_EVERY = 5       # counting-sort interval (steps) when not autotuned
-TUNE_STEPS = 20      # steps per candidate interval of the sort autotuner
+TUNE_STEPS = 12      # steps per candidate of the autotuner (tile shape, window margin, sort interval)
+TUNE_CACHE = os.path.join(tempfile.gettempdir(), "pic_tune_cache.json")
 
 
 # Poisson: algorithmic bytes per mesh node per refinement iteration: the
@@ -79,6 +80,9 @@ def args():
     ap.add_argument("--no-diag", action="store_true", help="skip the run with every diagnostic on")
     ap.add_argument("--no-extra", action="store_true", help="headline workload only (no 128x128x512 and "
                                                             "64x64x256 legs)")
+    ap.add_argument("--particles", type=float, default=None,
+                    help="macroparticles of the headline workload (both species; the weight keeps the density); "
+                         "for profiling a smaller case")
     return ap.parse_args()
 
 
@@ -144,14 +148,20 @@ class Clocks:
                 "samples": len(sm)}
 
 
-def run_gpu(P, I, wl, parts, prec, steps, warmup, stream, gpu, flags=0, tune=True, sort_every=SORT_EVERY, **run_kw):
+def run_gpu(P, I, wl, parts, prec, steps, warmup, stream, gpu, flags=0, tune=True, sort_every=SORT_EVERY,
+            tuning=None, **run_kw):
     import torch
     run = P.Run(wl, parts, prec=prec, stream=stream, sort_every=sort_every, flags=flags, **run_kw)
+    if tuning is not None and not tune:
+        run.set_tuning(tuning)
+        sort_every = tuning["sort_every"]
+    # tile shape, deposit-window margin and sort interval autotuned on the run
+    # itself before the timed region (pic_tune; fixed choices otherwise)
+    tuning = run.tune(TUNE_STEPS, cache_path=TUNE_CACHE) if tune else run.tuning()
+    sort_every = tuning["sort_every"]
     # warm-up covers two sorts, so that the step graphs of both particle-buffer
     # parities are captured before the timed region
-    run.step(max(warmup, 2 * sort_every + 1) if not tune else warmup)
-    # sort interval autotuned on the run itself before the timed region
-    sort_every = run.tune_sort(TUNE_STEPS) if tune else sort_every
+    run.step(max(warmup, 2 * sort_every + 1))
     _, c0 = run.counts()
     run.profile(1)
     k0 = run.profile_read()["kernels"]
@@ -176,7 +186,7 @@ def run_gpu(P, I, wl, parts, prec, steps, warmup, stream, gpu, flags=0, tune=Tru
     run.close()
     return dict(ms=ms, pushed=c1["pushed"] - c0["pushed"], prof=prof, kernels=prof["kernels"] - k0,
                 live=[int(x) for x in n], clocks=clk.summary(), counters=c1, cold=cold, sort_every=sort_every,
-                steps=steps)
+                steps=steps, tuning=tuning)
 
 
 def cold_solves(run, reps=3):
@@ -373,7 +383,7 @@ def leg(P, I, wl, peak, peak_kind, steps, warmup, stream, gpu, flags, tune, prof
     """One mixed-precision workload: value, push roofline and Poisson figures."""
     r = run_gpu(P, I, wl, parts, P.PIC_MIXED, steps, warmup, stream, gpu, flags, tune=tune)
     return r, {"workload": describe(wl), "value": r["pushed"] / (r["ms"] / 1000.0), "unit": "particle-steps/s",
-               "steps": steps, "ms_per_step": r["ms"] / steps, "sort_every": r["sort_every"],
+               "steps": steps, "ms_per_step": r["ms"] / steps, "tuning": r["tuning"],
                "roofline": push_roofline(r, peak, peak_kind, profile_name),
                "poisson": poisson_block(r["prof"], r["cold"], wl, BYTES_NODE_MIXED, peak, peak_kind, "mixed"),
                "gpu_launches": r["kernels"], "clocks": r["clocks"]}
@@ -401,6 +411,9 @@ def main():
     P.load()
     peak, peak_kind = peaks()
     wl = I.workload(a.workload)
+    if a.particles:
+        half = int(a.particles) // 2
+        wl = I.workload(a.workload, n_e=half, n_i=half, weight=wl.weight * wl.n_e / half)
     # replicas: each rank runs its own independent run (different seed)
     wl.seed = replica_seed(wl.seed, rank)
     stream = torch.cuda.current_stream().cuda_stream
@@ -428,7 +441,7 @@ def main():
         base_ms = r1["ms"] / 200
         if not a.no_coulomb:
             coul = run_gpu(P, I, w1, None, P.PIC_MIXED, 50, a.warmup, stream, local, flags | P.PIC_F_COULOMB,
-                           tune=False, sort_every=r1["sort_every"])
+                           tune=False, tuning=r1["tuning"])
             c2["coulomb"] = {"value": coul["pushed"] / (coul["ms"] / 1000.0), "unit": "particle-steps/s",
                              "steps": 50, "ms_per_step": coul["ms"] / 50,
                              "extra_ms_per_step": coul["ms"] / 50 - base_ms,
@@ -438,7 +451,7 @@ def main():
             h = 0.08 * w1.dx
             centre = np.asarray(w1.grain_pos).mean(0)
             diag = run_gpu(P, I, w1, None, P.PIC_MIXED, 50, a.warmup, stream, local, flags | P.PIC_F_MOMENTS,
-                           tune=False, sort_every=r1["sort_every"], mom_phases=DIAG_PHASES, fine_n=(200, 200, 200),
+                           tune=False, tuning=r1["tuning"], mom_phases=DIAG_PHASES, fine_n=(200, 200, 200),
                            fine_h=h, fine_origin=tuple(centre - 100 * h), eepf_bins=200, eepf_de_ev=0.1)
             c2["diagnostics"] = {"value": diag["pushed"] / (diag["ms"] / 1000.0), "unit": "particle-steps/s",
                                  "steps": 50, "ms_per_step": diag["ms"] / 50,
@@ -476,8 +489,8 @@ def main():
                                               "from the seed",
                    "parallelism": "replicas only" if world > 1 else "1 GPU",
                    "l2": "inputs larger than L2 (particle arrays 16 GB mixed / 32 GB FP64)",
-                   "sort_every": mixed["sort_every"],
-                   "sort_interval": "fixed" if a.no_tune else "autotuned (pic_tune_sort)",
+                   "tuning": mixed["tuning"],
+                   "tuned": "fixed" if a.no_tune else "autotuned (pic_tune: tile shape, window margin, sort interval)",
                    "tol": 1e-10},
         "roofline": push_roofline(mixed, peak, peak_kind, PUSH_PROFILE),
         "poisson": poisson_block(mixed["prof"], mixed["cold"], wl, BYTES_NODE_MIXED, peak, peak_kind, "mixed"),

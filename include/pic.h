@@ -173,6 +173,55 @@ pic_status pic_step(pic_ctx* ctx, int32_t n_steps);
  * PIC_EINVAL for steps_per_candidate < 1; errors of the steps as pic_step. */
 pic_status pic_tune_sort(pic_ctx* ctx, int32_t steps_per_candidate, int32_t* chosen);
 
+/* Launch and layout choices of a run.  None of them changes a result: the
+ * deposit is an exact integer sum and the random numbers are keyed on
+ * particle ids, so any choice gives the same particles, charge and potential
+ * bit for bit (the paper is silent on particle order and data layout).
+ *   sort_every  counting-sort interval in steps (>= 1);
+ *   tile        mixed precision: cells per tile along x, y, z; particles are
+ *               sorted by tile and one thread block of the push takes a
+ *               tile's particles (each edge in [1, min(mesh edge, 64)]);
+ *   halo        mixed precision: margin in cells of the push's shared-memory
+ *               deposit window around its tile, for the particles that drift
+ *               out of the tile between sorts (in [0, 8]); the window of
+ *               (tile + 1 + 2 halo) nodes per axis, 8 bytes each, must fit
+ *               48 KB.
+ * The FP64 path uses sort_every only. */
+typedef struct {
+    int32_t sort_every;
+    int32_t tile[3];
+    int32_t halo;
+} pic_tuning;
+
+/* Current choices of a run (out: host). */
+pic_status pic_get_tuning(const pic_ctx* ctx, pic_tuning* out);
+
+/* Apply choices (in: host).  A new tile shape or margin synchronises the
+ * run's stream, re-sorts both species at once and rebuilds the step graphs
+ * at the next step.  PIC_EINVAL for values out of range. */
+pic_status pic_set_tuning(pic_ctx* ctx, const pic_tuning* t);
+
+/* Autotuner: times candidate choices on the run itself with CUDA events and
+ * keeps the fastest, by coordinate search: tile shapes {8x8x8, 16x8x4, 8x8x4,
+ * 16x8x8, 16x16x4, 32x8x4} (clipped to the mesh), then margins {1, 2, 3},
+ * then sort intervals {2, 3, 4, 5, 6, 8, 10, 14, 20}; each candidate runs at
+ * least steps_per_candidate steps over whole sort periods after one warm-up
+ * period, and the run advances by all of them.  With cache_path (may be NULL)
+ * a cached entry for this (device name, mesh, particle count to two digits,
+ * precision) is applied without timing; otherwise the result is added to the
+ * cache file (see pic_tune_cache_store).  chosen (may be NULL, host) receives
+ * the choices.  Errors of the steps as pic_step. */
+pic_status pic_tune(pic_ctx* ctx, int32_t steps_per_candidate, const char* cache_path, pic_tuning* chosen);
+
+/* The autotuner's cache file, host only (no GPU): a JSON object with one
+ * member per line, "key": {"sort_every": S, "tile": [X, Y, Z], "halo": H}.
+ * load: PIC_OK and *out when the file holds `key`, else PIC_EINVAL.  store:
+ * adds or replaces `key` (no '"' or newline in it) and rewrites the file
+ * through a temporary file in the same directory; PIC_EINVAL when it cannot
+ * be written. */
+pic_status pic_tune_cache_load(const char* path, const char* key, pic_tuning* out);
+pic_status pic_tune_cache_store(const char* path, const char* key, const pic_tuning* t);
+
 /* The particle half of one step: CIC gather of -grad phi (Eq. 4), leapfrog push
  * (Eqs. 1-2) with MD subcycling and the PPPM correction (Eqs. 5-6) near grains,
  * electrode and grain absorption, null-collision MCC with ionization products,

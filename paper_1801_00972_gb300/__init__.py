@@ -31,7 +31,8 @@ COUNTERS = ("lost_bot_e", "lost_bot_i", "lost_top_e", "lost_top_i", "abs_e", "ab
 PIC_C_N = len(COUNTERS)
 
 # every symbol include/pic.h declares
-SYMBOLS = ("pic_init", "pic_init_plasma", "pic_step", "pic_tune_sort", "pic_advance", "pic_solve", "pic_grain_charges", "pic_counts",
+SYMBOLS = ("pic_init", "pic_init_plasma", "pic_step", "pic_tune_sort", "pic_get_tuning", "pic_set_tuning", "pic_tune",
+           "pic_tune_cache_load", "pic_tune_cache_store", "pic_advance", "pic_solve", "pic_grain_charges", "pic_counts",
            "pic_moments", "pic_moments_phase", "pic_fine_moments", "pic_oml_charges", "pic_eepf", "pic_eepf_fit", "pic_get_particles", "pic_get_rho", "pic_get_phi", "pic_set_phi",
            "pic_get_grain_table", "pic_set_grain_table", "pic_set_grain_counts", "pic_step_index",
            "pic_profile", "pic_profile_read", "pic_solve_noalloc", "pic_batch_init", "pic_batch_step",
@@ -67,6 +68,13 @@ class pic_run(C.Structure):
                 ("fine_h", C.c_double), ("fine_origin", C.c_double * 3)]
 
 
+class pic_tuning(C.Structure):
+    _fields_ = [("sort_every", C.c_int32), ("tile", C.c_int32 * 3), ("halo", C.c_int32)]
+
+    def as_dict(self):
+        return {"sort_every": self.sort_every, "tile": [int(x) for x in self.tile], "halo": self.halo}
+
+
 class PicError(RuntimeError):
     def __init__(self, status, msg):
         super().__init__(f"{STATUS.get(status, status)}: {msg}")
@@ -89,7 +97,11 @@ def load(path: str | None = None):
         L.pic_init.argtypes = [C.POINTER(pic_mesh), C.POINTER(pic_electrodes), C.POINTER(pic_gas),
                                C.POINTER(pic_grains), C.POINTER(pic_run), vp, C.POINTER(vp)]
         sig = {
-            "pic_step": [vp, i32], "pic_tune_sort": [vp, i32, C.POINTER(i32)], "pic_advance": [vp], "pic_solve": [vp, C.POINTER(i32), pd],
+            "pic_step": [vp, i32], "pic_tune_sort": [vp, i32, C.POINTER(i32)],
+            "pic_get_tuning": [vp, C.POINTER(pic_tuning)], "pic_set_tuning": [vp, C.POINTER(pic_tuning)],
+            "pic_tune": [vp, i32, C.c_char_p, C.POINTER(pic_tuning)],
+            "pic_tune_cache_load": [C.c_char_p, C.c_char_p, C.POINTER(pic_tuning)],
+            "pic_tune_cache_store": [C.c_char_p, C.c_char_p, C.POINTER(pic_tuning)], "pic_advance": [vp], "pic_solve": [vp, C.POINTER(i32), pd],
             "pic_grain_charges": [vp, pi64, pd], "pic_counts": [vp, pi64, pi64],
             "pic_moments": [vp, i32, pd, sz, i32], "pic_moments_phase": [vp, i32, i32, pd, sz, pi64],
             "pic_fine_moments": [vp, i32, pd, sz], "pic_oml_charges": [vp, i32, pd, sz],
@@ -166,6 +178,44 @@ def pic_tune_sort(ctx, steps_per_candidate):
     chosen = C.c_int32()
     _check(ctx, load().pic_tune_sort(ctx, int(steps_per_candidate), C.byref(chosen)))
     return chosen.value
+
+
+def pic_get_tuning(ctx):
+    t = pic_tuning()
+    _check(ctx, load().pic_get_tuning(ctx, C.byref(t)))
+    return t.as_dict()
+
+
+def _tuning(d):
+    t = pic_tuning()
+    t.sort_every, t.halo = int(d["sort_every"]), int(d["halo"])
+    for a in range(3):
+        t.tile[a] = int(d["tile"][a])
+    return t
+
+
+def pic_set_tuning(ctx, d):
+    t = _tuning(d)
+    return _check(ctx, load().pic_set_tuning(ctx, C.byref(t)))
+
+
+def pic_tune(ctx, steps_per_candidate, cache_path=None):
+    t = pic_tuning()
+    path = cache_path.encode() if cache_path else None
+    _check(ctx, load().pic_tune(ctx, int(steps_per_candidate), path, C.byref(t)))
+    return t.as_dict()
+
+
+def pic_tune_cache_load(path, key):
+    """The cached choices for `key`, or None."""
+    t = pic_tuning()
+    st = load().pic_tune_cache_load(path.encode(), key.encode(), C.byref(t))
+    return t.as_dict() if st == PIC_OK else None
+
+
+def pic_tune_cache_store(path, key, d):
+    t = _tuning(d)
+    return _check(None, load().pic_tune_cache_store(path.encode(), key.encode(), C.byref(t)))
 
 
 def pic_advance(ctx):
@@ -431,6 +481,15 @@ class Run:
 
     def tune_sort(self, steps_per_candidate=20):
         return pic_tune_sort(self.ctx, steps_per_candidate)
+
+    def tune(self, steps_per_candidate=20, cache_path=None):
+        return pic_tune(self.ctx, steps_per_candidate, cache_path)
+
+    def tuning(self):
+        return pic_get_tuning(self.ctx)
+
+    def set_tuning(self, d):
+        pic_set_tuning(self.ctx, d)
 
     def advance(self):
         pic_advance(self.ctx)

@@ -2,6 +2,7 @@
 // the query calls of the C ABI declared in include/pic.h.
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
 #include <cstring>
 #include <new>
 #include <string>
@@ -463,7 +464,23 @@ pic_status init_run(const pic_mesh* mesh, const pic_electrodes* el, const pic_ga
     c->gr2_32 = (float*)dev_alloc(c, sizeof(float) * ng1);
     c->cell_ng = (int*)dev_alloc(c, sizeof(int) * cells);
     c->cell_g = (int*)dev_alloc(c, sizeof(int) * cells * kMaxG);
-    c->cursor = (unsigned int*)dev_alloc(c, sizeof(unsigned int) * (cells + 1));
+    // sort keys: the mixed path sorts by tiles of up to 8 x 8 x 8 cells (the push's
+    // unit of work), the FP64 path by cell
+    for (int a = 0; a < 3; ++a) {
+        const int n = a == 0 ? nx : a == 1 ? ny : nz;
+        c->tile[a] = mixed ? std::min(8, n) : 1;
+        c->ntile[a] = (n + c->tile[a] - 1) / c->tile[a];
+    }
+    c->ntiles = (int64_t)c->ntile[0] * c->ntile[1] * c->ntile[2];
+    c->nkeys = mixed ? (size_t)c->ntiles * (size_t)(c->tile[0] * c->tile[1] * c->tile[2]) : cells;
+    c->cursor = (unsigned int*)dev_alloc(c, sizeof(unsigned int) * (c->nkeys + 1));
+    c->nkeys_cap = c->nkeys;
+    c->ntiles_cap = c->ntiles;
+    if (mixed)
+        for (int sp = 0; sp < 2; ++sp) {
+            c->tstart[sp] = (unsigned int*)dev_alloc(c, sizeof(unsigned int) * (size_t)(c->ntiles + 1));
+            ok = ok && c->tstart[sp];
+        }
     if (c->flags & PIC_F_COULOMB)
         for (int sp = 0; sp < 2; ++sp) {
             c->cs_end[sp] = (unsigned int*)dev_alloc(c, sizeof(unsigned int) * (cells + 1));
@@ -965,6 +982,43 @@ pic_status step_enqueue(pic_ctx* c, int32_t n_steps)
     return PIC_OK;
 }
 
+// the step graphs (not the solve): rebuilt on the next step
+void drop_graphs(pic_ctx* c)
+{
+    cudaGraphExec_t* gs[] = {&c->g_push[0], &c->g_push[1], &c->g_post[0][0], &c->g_post[0][1], &c->g_post[1][0],
+                             &c->g_post[1][1], &c->g_mom[0], &c->g_mom[1]};
+    for (cudaGraphExec_t* g : gs)
+        if (*g) {
+            cudaGraphExecDestroy(*g);
+            *g = nullptr;
+        }
+}
+
+constexpr size_t kMaxWindowBytes = 48 * 1024;
+
+size_t tuning_window_bytes(const int32_t tile[3], int32_t halo)
+{
+    return sizeof(unsigned long long) * (size_t)(tile[0] + 1 + 2 * halo) * (size_t)(tile[1] + 1 + 2 * halo) *
+           (size_t)(tile[2] + 1 + 2 * halo);
+}
+
+// cache key: device name, mesh, particle count (2 significant digits), precision
+std::string tuning_key(const pic_ctx* c)
+{
+    cudaDeviceProp prop{};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::string name = cudaGetDeviceProperties(&prop, dev) == cudaSuccess ? prop.name : "unknown";
+    for (char& ch : name)
+        if (ch == '"' || ch == '|' || ch == '\\') ch = '_';
+    unsigned long long ns[2] = {0, 0};
+    cudaMemcpy(ns, c->d_nslot, sizeof ns, cudaMemcpyDeviceToHost);
+    char buf[256];
+    std::snprintf(buf, sizeof buf, "%s|%dx%dx%d|%.1e|%s", name.c_str(), c->nx, c->ny, c->nz,
+                  (double)(ns[0] + ns[1]), c->prec == PIC_MIXED ? "mixed" : "fp64");
+    return buf;
+}
+
 }  // namespace
 
 struct pic_batch {
@@ -1018,6 +1072,149 @@ pic_status pic_tune_sort(pic_ctx* c, int32_t steps_per_candidate, int32_t* chose
     c->sort_every = best;
     if (chosen) *chosen = best;
     return st;
+}
+
+pic_status pic_get_tuning(const pic_ctx* c, pic_tuning* out)
+{
+    if (!c || !out) return PIC_EINVAL;
+    out->sort_every = c->sort_every;
+    for (int a = 0; a < 3; ++a) out->tile[a] = c->tile[a];
+    out->halo = c->halo;
+    return PIC_OK;
+}
+
+pic_status pic_set_tuning(pic_ctx* c, const pic_tuning* t)
+{
+    if (!c || !t) return PIC_EINVAL;
+    if (t->sort_every < 1 || t->sort_every > 1000) return fail(c, PIC_EINVAL, "tuning: sort_every in [1, 1000]");
+    if (c->prec != PIC_MIXED) {
+        c->sort_every = t->sort_every;
+        return PIC_OK;
+    }
+    const int n[3] = {c->nx, c->ny, c->nz};
+    for (int a = 0; a < 3; ++a)
+        if (t->tile[a] < 1 || t->tile[a] > n[a] || t->tile[a] > 64)
+            return fail(c, PIC_EINVAL, "tuning: tile edges in [1, min(mesh, 64)]");
+    if (t->halo < 0 || t->halo > 8) return fail(c, PIC_EINVAL, "tuning: halo in [0, 8]");
+    if (tuning_window_bytes(t->tile, t->halo) > kMaxWindowBytes)
+        return fail(c, PIC_EINVAL, "tuning: the deposit window (tile + 1 + 2 halo nodes per axis, 8 B each) "
+                                   "exceeds 48 KB");
+    c->sort_every = t->sort_every;
+    const bool same = t->tile[0] == c->tile[0] && t->tile[1] == c->tile[1] && t->tile[2] == c->tile[2] &&
+                      t->halo == c->halo;
+    if (same) return PIC_OK;
+    // new sort keys: wait for queued work, size the key buffers, re-sort both
+    // species now (the tile ranges must describe the new order), drop the step
+    // graphs (grid and window size are baked into them)
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "tuning sync");
+    int ntile[3];
+    for (int a = 0; a < 3; ++a) ntile[a] = (n[a] + t->tile[a] - 1) / t->tile[a];
+    const int64_t ntiles = (int64_t)ntile[0] * ntile[1] * ntile[2];
+    const size_t nkeys = (size_t)ntiles * (size_t)(t->tile[0] * t->tile[1] * t->tile[2]);
+    if (nkeys > c->nkeys_cap || ntiles > c->ntiles_cap) {
+        unsigned int* cur = nkeys > c->nkeys_cap ? (unsigned int*)dev_alloc(c, sizeof(unsigned int) * (nkeys + 1))
+                                                 : c->cursor;
+        unsigned int* ts0 = ntiles > c->ntiles_cap ? (unsigned int*)dev_alloc(c, sizeof(unsigned int) * (ntiles + 1))
+                                                   : c->tstart[0];
+        unsigned int* ts1 = ntiles > c->ntiles_cap ? (unsigned int*)dev_alloc(c, sizeof(unsigned int) * (ntiles + 1))
+                                                   : c->tstart[1];
+        if (!cur || !ts0 || !ts1) return fail(c, PIC_ENOMEM, "tuning: key buffers");
+        c->cursor = cur;
+        c->tstart[0] = ts0;
+        c->tstart[1] = ts1;
+        c->nkeys_cap = std::max(c->nkeys_cap, nkeys);
+        c->ntiles_cap = std::max(c->ntiles_cap, ntiles);
+        const size_t old_keys = c->nkeys;
+        c->nkeys = nkeys;
+        if (nkeys > old_keys && !sort_scratch_setup(c)) return fail(c, PIC_ENOMEM, "tuning: scan scratch");
+    }
+    for (int a = 0; a < 3; ++a) { c->tile[a] = t->tile[a]; c->ntile[a] = ntile[a]; }
+    c->ntiles = ntiles;
+    c->nkeys = nkeys;
+    c->halo = t->halo;
+    drop_graphs(c);
+    sort_particles(c, 0);
+    sort_particles(c, 1);
+    c->parity ^= 1;
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(c, e, "tuning re-sort");
+    return check(c);
+}
+
+pic_status pic_tune(pic_ctx* c, int32_t steps_per_candidate, const char* cache_path, pic_tuning* chosen)
+{
+    if (!c || steps_per_candidate < 1) return PIC_EINVAL;
+    const std::string key = tuning_key(c);
+    pic_tuning best{};
+    pic_get_tuning(c, &best);
+    if (cache_path && pic_tune_cache_load(cache_path, key.c_str(), &best) == PIC_OK) {
+        const pic_status st = pic_set_tuning(c, &best);
+        if (st == PIC_OK && chosen) *chosen = best;
+        return st;
+    }
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (!PIC_CUDA_OK(cudaEventCreate(&e0)) || !PIC_CUDA_OK(cudaEventCreate(&e1))) {
+        if (e0) cudaEventDestroy(e0);
+        return cuda_fail(c, cudaGetLastError(), "tune events");
+    }
+    // ms per step of one candidate over whole sort periods, after a warm-up period
+    pic_status st = PIC_OK;
+    auto time_it = [&](const pic_tuning& t, float* ms) -> pic_status {
+        pic_status r = pic_set_tuning(c, &t);
+        if (r != PIC_OK) return r;
+        const int32_t s = t.sort_every;
+        const int32_t lead = (int32_t)((s - c->step % s) % s) + s;
+        if ((r = step_enqueue(c, lead)) != PIC_OK) return r;
+        const int32_t n = (std::max(steps_per_candidate, 2 * s) + s - 1) / s * s;
+        cudaEventRecord(e0, c->stream);
+        if ((r = step_enqueue(c, n)) != PIC_OK) return r;
+        cudaEventRecord(e1, c->stream);
+        if ((r = check(c)) != PIC_OK) return r;
+        cudaEventElapsedTime(ms, e0, e1);
+        *ms /= (float)n;
+        return PIC_OK;
+    };
+    float best_ms = 0.f;
+    // coordinate search: tile shape, then window margin, then sort interval
+    if (c->prec == PIC_MIXED) {
+        const int shapes[][3] = {{8, 8, 8}, {16, 8, 4}, {8, 8, 4}, {16, 8, 8}, {16, 16, 4}, {32, 8, 4}};
+        for (const auto& sh : shapes) {
+            pic_tuning t = best;
+            for (int a = 0; a < 3; ++a) t.tile[a] = std::min(sh[a], a == 0 ? c->nx : a == 1 ? c->ny : c->nz);
+            if (tuning_window_bytes(t.tile, t.halo) > kMaxWindowBytes) continue;
+            float ms = 0.f;
+            if ((st = time_it(t, &ms)) != PIC_OK) break;
+            if (best_ms == 0.f || ms < best_ms) { best_ms = ms; best = t; }
+        }
+        for (int h = 1; h <= 3 && st == PIC_OK; ++h) {
+            if (h == best.halo) continue;
+            pic_tuning t = best;
+            t.halo = h;
+            if (tuning_window_bytes(t.tile, t.halo) > kMaxWindowBytes) continue;
+            float ms = 0.f;
+            if ((st = time_it(t, &ms)) != PIC_OK) break;
+            if (ms < best_ms) { best_ms = ms; best = t; }
+        }
+    }
+    const int32_t sorts[] = {2, 3, 4, 5, 6, 8, 10, 14, 20};
+    for (int32_t sv : sorts) {
+        if (st != PIC_OK) break;
+        pic_tuning t = best;
+        t.sort_every = sv;
+        float ms = 0.f;
+        if ((st = time_it(t, &ms)) != PIC_OK) break;
+        if (best_ms == 0.f || ms < best_ms) { best_ms = ms; best = t; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st != PIC_OK) return st;
+    st = pic_set_tuning(c, &best);
+    if (st != PIC_OK) return st;
+    if (chosen) *chosen = best;
+    if (cache_path && pic_tune_cache_store(cache_path, key.c_str(), &best) != PIC_OK)
+        return fail(c, PIC_EINVAL, std::string("tuning cache not writable: ") + cache_path);
+    return PIC_OK;
 }
 
 pic_status pic_batch_init(int32_t n, const pic_mesh* meshes, const pic_electrodes* els, const pic_gas* gases,
@@ -1381,3 +1578,58 @@ pic_status pic_fine_moments(pic_ctx* c, int32_t what, double* out, size_t len)
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Tuning cache: a JSON object with one member per line,
+//   "<device>|<nx>x<ny>x<nz>|<particles>|<precision>": {"sort_every": S, "tile": [X, Y, Z], "halo": H},
+// read and rewritten whole by pic_tune_cache_store (last write wins).
+extern "C" pic_status pic_tune_cache_load(const char* path, const char* key, pic_tuning* out)
+{
+    if (!path || !key || !out) return PIC_EINVAL;
+    std::FILE* f = std::fopen(path, "r");
+    if (!f) return PIC_EINVAL;
+    const std::string want = std::string("\"") + key + "\":";
+    char line[1024];
+    pic_status st = PIC_EINVAL;
+    while (std::fgets(line, sizeof line, f)) {
+        const char* at = std::strstr(line, want.c_str());
+        if (!at) continue;
+        pic_tuning t{};
+        if (std::sscanf(at + want.size(), " {\"sort_every\": %d, \"tile\": [%d, %d, %d], \"halo\": %d}",
+                        &t.sort_every, &t.tile[0], &t.tile[1], &t.tile[2], &t.halo) == 5) {
+            *out = t;
+            st = PIC_OK;
+        }
+    }
+    std::fclose(f);
+    return st;
+}
+
+extern "C" pic_status pic_tune_cache_store(const char* path, const char* key, const pic_tuning* t)
+{
+    if (!path || !key || !t || std::strchr(key, '"') || std::strchr(key, '\n')) return PIC_EINVAL;
+    std::vector<std::string> keep;
+    const std::string mine = std::string("\"") + key + "\":";
+    if (std::FILE* f = std::fopen(path, "r")) {
+        char line[1024];
+        while (std::fgets(line, sizeof line, f)) {
+            std::string l(line);
+            while (!l.empty() && (l.back() == '\n' || l.back() == ',' || l.back() == '\r')) l.pop_back();
+            if (l.size() < 2 || l[0] != '"' || l.compare(0, mine.size(), mine) == 0) continue;
+            keep.push_back(l);
+        }
+        std::fclose(f);
+    }
+    char buf[512];
+    std::snprintf(buf, sizeof buf, "%s {\"sort_every\": %d, \"tile\": [%d, %d, %d], \"halo\": %d}", mine.c_str(),
+                  t->sort_every, t->tile[0], t->tile[1], t->tile[2], t->halo);
+    keep.push_back(buf);
+    const std::string tmp = std::string(path) + ".tmp";
+    std::FILE* f = std::fopen(tmp.c_str(), "w");
+    if (!f) return PIC_EINVAL;
+    std::fputs("{\n", f);
+    for (size_t i = 0; i < keep.size(); ++i) std::fprintf(f, "%s%s\n", keep[i].c_str(), i + 1 < keep.size() ? "," : "");
+    std::fputs("}\n", f);
+    const bool ok = std::fclose(f) == 0 && std::rename(tmp.c_str(), path) == 0;
+    return ok ? PIC_OK : PIC_EINVAL;
+}

@@ -11,11 +11,16 @@
 //
 // One step runs three kernels per species:
 //   k_push32  every particle outside the MD regions: gather, push, electrode
-//             loss, the null-collision test, deposit.  Deposits are summed in a
-//             shared-memory window of nodes per block and flushed with one
-//             global atomic per touched node.  Collision candidates are
-//             appended to a list, particles that end in an MD cell to the next
-//             step's MD list.
+//             loss, the null-collision test, deposit.  The particles are
+//             sorted by tile (8 x 8 x 8 cells); one thread block takes the slot
+//             range of one tile as it stood at the last sort and sums its
+//             deposits in a shared-memory window over the tile's nodes plus a
+//             margin of `halo` cells (particles drift between sorts), flushed
+//             with one global atomic per touched node.  Corners outside the
+//             window, and the ionization products appended since the sort
+//             (taken by extra blocks), go to global atomics.  Collision
+//             candidates are appended to a list, particles that end in an MD
+//             cell to the next step's MD list.
 //   k_md32    the MD-region particles (listed during the previous step, so it
 //             runs on a second stream alongside k_push32): Dt/40 substeps with
 //             the PPPM correction, grain absorption, MCC, deposit.
@@ -34,29 +39,18 @@ namespace {
 #ifndef PIC_PUSH_PPT
 #define PIC_PUSH_PPT 2
 #endif
-#ifndef PIC_PUSH_WINR
-#define PIC_PUSH_WINR 256
-#endif
 #ifndef PIC_PUSH_CONC
 #define PIC_PUSH_CONC 1                           // the ion push on a third stream beside the electron push
-#endif
-#ifndef PIC_PUSH_TILE
-#define PIC_PUSH_TILE 0
 #endif
 #ifndef PIC_PUSH_MINB
 #define PIC_PUSH_MINB 6                           // resident blocks per SM the register budget is set for
 #endif
+#ifndef PIC_PUSH_TAIL
+#define PIC_PUSH_TAIL 76                          // blocks for the particles appended since the last sort
+#endif
 constexpr int kPushThreads = 256;
-constexpr int kPPT = PIC_PUSH_PPT;               // particles per thread per chunk
-constexpr int kChunk = kPushThreads * kPPT;      // particles per block per chunk
-// deposit window per block: 4 planes (offsets -1..+2 from the anchor particle's
-// plane), each +-kWinR nodes around the anchor's node column; a fixed-point
-// weight w <= 2^42 is summed as two 21-bit halves in 32-bit shared counters
-// (a chunk adds at most kChunk * 2^21 < 2^32 to a slot)
-constexpr int kWinR = PIC_PUSH_WINR;
-constexpr int kWinN = 4 * 2 * kWinR;
-static_assert(kChunk < 2048, "a chunk's window counters would overflow");
-constexpr bool kTile = PIC_PUSH_TILE != 0;       // gather E from a shared-memory tile
+constexpr int kPPT = PIC_PUSH_PPT;               // particles per thread per loop trip
+constexpr int kTailBlocks = PIC_PUSH_TAIL;
 
 struct P32 {
     int nx, ny, nz, nxy;
@@ -94,6 +88,11 @@ struct P32 {
     unsigned int md_rescap;
     unsigned int* mcc_list;
     unsigned int* mcc_n;
+    const unsigned int* tstart;  // first slot of each tile at the last sort (ntiles + 1)
+    int tx, ty, tz, ntx, nty;    // tile edge (cells) and tiles per axis in x and y
+    long long ntiles;
+    int halo;                    // deposit window margin (cells)
+    int wx, wy, wz;              // deposit window extent (nodes): tile + 1 + 2 halo per axis
 };
 
 enum Event : int { kEvNone = 0, kEvEEl, kEvEExc, kEvEIon, kEvIEl, kEvICx };
@@ -368,80 +367,63 @@ __device__ __forceinline__ void count_event(const P32& p, int ev)
     if (ev != kEvNone) atomicAdd(p.cnt + slot, 1ull);
 }
 
-// Slot of node `node` (in plane k) in a block's tile/window around the anchor
-// node `anchor` in plane `ak`, or -1 when outside.
-__device__ __forceinline__ int tile_slot(int node, int k, int anchor, int ak, int nxy)
+// Window-relative coordinate of node index `n` along a periodic axis of
+// length `len`, for a window starting at `o` (o may be negative): in [0, len).
+__device__ __forceinline__ int wrel(int n, int o, int len)
 {
-    const int pl = k - ak;
-    const int w = node - anchor - pl * nxy + kWinR;
-    return (pl >= -1 && pl <= 2 && w >= 0 && w < 2 * kWinR) ? (pl + 1) * 2 * kWinR + w : -1;
+    int d = n - o;
+    if (d < 0) d += len;
+    else if (d >= len) d -= len;
+    return d;
 }
 
-// Base slot of a particle's 8 corners when they all lie in the tile without a
-// periodic wrap: corners are base + {0, 1, nx, nx + 1} and the same + 2 kWinR.
-__device__ __forceinline__ int block_slot(int i, int j, int k, int nx, int ny, int anchor, int ak)
-{
-    if (i + 1 >= nx || j + 1 >= ny) return -1;
-    const int pl = k - ak;
-    const int w = ((k * ny + j) * nx + i) - anchor - pl * nx * ny + kWinR;
-    return (pl >= -1 && pl <= 1 && w >= 0 && w + nx + 1 < 2 * kWinR) ? (pl + 1) * 2 * kWinR + w : -1;
-}
-
+// Blocks [0, ntiles): the particles of one tile (slot range at the last sort),
+// deposits summed in a shared window of wx x wy x wz nodes from the tile's
+// lower corner minus `halo` cells, flushed once.  Blocks [ntiles, grid): the
+// ionization products appended since the sort, deposited with global atomics.
 __global__ void __launch_bounds__(kPushThreads, PIC_PUSH_MINB) k_push32(const P32 p)
 {
-    __shared__ float4 tile[kTile ? kWinN : 1];         // E around the chunk (gather)
-    __shared__ unsigned int win_hi[kWinN], win_lo[kWinN];  // deposit sums (two 21-bit halves)
-    __shared__ unsigned long long s_anchor;
-    const unsigned long long n = p.nslot[p.sp];
+    extern __shared__ unsigned long long win[];
     const uint32_t step = *p.step;
     const bool frozen = (p.sp == 1) && (p.flags & PIC_F_IONS_FROZEN);
     const bool no_mcc = p.flags & PIC_F_NO_MCC;
     const long long charge = p.sp == 0 ? -1 : 1;
-    const int nx = p.nx, ny = p.ny, nz = p.nz, nxy = p.nxy;
-    const int nodes = nxy * (nz + 1);
-    const float s14 = 1.0f / (float)kWQ;
-    for (int t = threadIdx.x; t < kWinN; t += blockDim.x) { win_hi[t] = 0u; win_lo[t] = 0u; }
-    if (threadIdx.x == 0) s_anchor = 0ull;
-    __syncthreads();
+    const int nx = p.nx, ny = p.ny, nz = p.nz;
+    const int wx = p.wx, wy = p.wy, wz = p.wz, wxy = wx * wy, wn = wxy * wz;
+    const long long b = blockIdx.x;
+    const bool tiled = b < p.ntiles;
+    // block-uniform loop bounds: every lane of a warp takes every trip (warp votes below)
+    unsigned long long first, end, stride;
+    int ox = 0, oy = 0, oz = 0;
+    if (tiled) {
+        first = p.tstart[b];
+        end = p.tstart[b + 1];
+        if (first == end) return;                // the whole block leaves together
+        const int ti = (int)(b % p.ntx), tj = (int)((b / p.ntx) % p.nty), tk = (int)(b / ((long long)p.ntx * p.nty));
+        ox = ti * p.tx - p.halo;
+        oy = tj * p.ty - p.halo;
+        oz = tk * p.tz - p.halo;
+        for (int t = threadIdx.x; t < wn; t += blockDim.x) win[t] = 0ull;
+        __syncthreads();
+        stride = (unsigned long long)kPushThreads * kPPT;
+    } else {
+        first = p.tstart[p.ntiles] + (unsigned long long)(b - p.ntiles) * kPushThreads * kPPT;
+        end = p.nslot[p.sp];
+        stride = (unsigned long long)(gridDim.x - p.ntiles) * kPushThreads * kPPT;
+    }
     unsigned int live = 0;
-    for (unsigned long long c0 = (unsigned long long)blockIdx.x * kChunk; c0 < n;
-         c0 += (unsigned long long)gridDim.x * kChunk) {
-        // ---- anchor: warp 0 samples 32 slots spread over the chunk and takes the
-        // first live one from the middle on (else any live one)
-        if (threadIdx.x < 32) {
-            const unsigned long long q = c0 + (unsigned long long)threadIdx.x * (kChunk / 32) + kChunk / 64;
-            const int cell = q < n ? __float_as_int(p.pos[q].w) : -1;
-            const unsigned m = __ballot_sync(0xffffffffu, cell >= 0);
-            const unsigned mh = m & 0xffff0000u;
-            const int lane = mh ? __ffs(mh) - 1 : (m ? __ffs(m) - 1 : -1);
-            const int ac = lane >= 0 ? __shfl_sync(0xffffffffu, cell, lane) : -1;
-            if (threadIdx.x == 0) s_anchor = ac >= 0 ? (1ull << 32) | (unsigned int)ac : 0ull;
-        }
-        __syncthreads();
-        const unsigned long long ak64 = s_anchor;
-        int ai = 0, aj = 0, akk = 0;
-        unpack((int)(unsigned int)ak64, ai, aj, akk);
-        const int anchor = (akk * ny + aj) * nx + ai;
-        // ---- stage E on the tile: planes akk-1 .. akk+2, +-kWinR nodes around the anchor column
-        if (kTile && ak64) {
-            for (int t = threadIdx.x; t < kWinN; t += blockDim.x) {
-                const int pl = t / (2 * kWinR) - 1, w = t % (2 * kWinR);
-                const int nd = anchor + pl * nxy + w - kWinR;
-                if (nd >= 0 && nd < nodes) tile[t] = __ldg(p.E + nd);
-            }
-        }
-        __syncthreads();
+    for (unsigned long long q0 = first; q0 < end; q0 += stride) {
         int dcell[kPPT];
         int da[kPPT][3];
 #pragma unroll
         for (int u = 0; u < kPPT; ++u) {
             dcell[u] = -1;
-            const unsigned long long q = c0 + (unsigned long long)u * kPushThreads + threadIdx.x;
+            const unsigned long long q = q0 + (unsigned long long)u * kPushThreads + threadIdx.x;
             int lost = 0;
             bool md = false, cand = false;
             // particle records stream through once: evict-first, so that the charge
             // and field arrays keep their place in L2
-            const float4 Pu = q < n ? __ldcs(p.pos + q) : make_float4(0.f, 0.f, 0.f, __int_as_float(-1));
+            const float4 Pu = q < end ? __ldcs(p.pos + q) : make_float4(0.f, 0.f, 0.f, __int_as_float(-1));
             int cell = __float_as_int(Pu.w);
             if (cell >= 0) {
                 ++live;
@@ -458,25 +440,7 @@ __global__ void __launch_bounds__(kPushThreads, PIC_PUSH_MINB) k_push32(const P3
                     float v[3] = {Vu.x, Vu.y, Vu.z};
                     int a[3] = {qa(o[0]), qa(o[1]), qa(o[2])};
                     float E[3];
-                    const int b = (kTile && ak64) ? block_slot(i, j, k, nx, ny, anchor, akk) : -1;
-                    if (b >= 0) {
-                        const float wx0 = (float)(kWQ - a[0]) * s14, wx1 = (float)a[0] * s14;
-                        const float wy0 = (float)(kWQ - a[1]) * s14, wy1 = (float)a[1] * s14;
-                        const float wz0 = (float)(kWQ - a[2]) * s14, wz1 = (float)a[2] * s14;
-                        const float4 e000 = tile[b], e001 = tile[b + 1], e010 = tile[b + nx], e011 = tile[b + nx + 1];
-                        const int b1 = b + 2 * kWinR;
-                        const float4 e100 = tile[b1], e101 = tile[b1 + 1], e110 = tile[b1 + nx],
-                                     e111 = tile[b1 + nx + 1];
-                        const float w00 = wy0 * wz0, w01 = wy1 * wz0, w10 = wy0 * wz1, w11 = wy1 * wz1;
-                        E[0] = w00 * (wx0 * e000.x + wx1 * e001.x) + w01 * (wx0 * e010.x + wx1 * e011.x) +
-                               w10 * (wx0 * e100.x + wx1 * e101.x) + w11 * (wx0 * e110.x + wx1 * e111.x);
-                        E[1] = w00 * (wx0 * e000.y + wx1 * e001.y) + w01 * (wx0 * e010.y + wx1 * e011.y) +
-                               w10 * (wx0 * e100.y + wx1 * e101.y) + w11 * (wx0 * e110.y + wx1 * e111.y);
-                        E[2] = w00 * (wx0 * e000.z + wx1 * e001.z) + w01 * (wx0 * e010.z + wx1 * e011.z) +
-                               w10 * (wx0 * e100.z + wx1 * e101.z) + w11 * (wx0 * e110.z + wx1 * e111.z);
-                    } else {
-                        gather(p.E, nx, ny, i, j, k, a, E);
-                    }
+                    gather(p.E, nx, ny, i, j, k, a, E);
                     v[0] += E[0] * p.kq; v[1] += E[1] * p.kq; v[2] += E[2] * p.kq;
                     o[0] += v[0]; o[1] += v[1]; o[2] += v[2];
                     lost = carry(nx, ny, nz, i, j, k, o);
@@ -508,67 +472,44 @@ __global__ void __launch_bounds__(kPushThreads, PIC_PUSH_MINB) k_push32(const P3
                 }
             }
         }
-        // ---- deposit: shared window for corners near the anchor, global atomics otherwise
-        if (!ak64) {
+        // ---- deposit: the block's window when all 8 corners fall inside it, else global atomics
 #pragma unroll
-            for (int u = 0; u < kPPT; ++u) {
-                if (dcell[u] < 0) continue;
-                int i, j, k;
-                unpack(dcell[u], i, j, k);
+        for (int u = 0; u < kPPT; ++u) {
+            if (dcell[u] < 0) continue;
+            int i, j, k;
+            unpack(dcell[u], i, j, k);
+            const int di = wrel(i, ox, nx), dj = wrel(j, oy, ny), dk = k - oz;
+            if (tiled && di + 1 < wx && dj + 1 < wy && dk >= 0 && dk + 1 < wz) {
+                const int s0 = (dk * wy + dj) * wx + di;
+                const unsigned long long wxs[2] = {(unsigned long long)(kWQ - da[u][0]), (unsigned long long)da[u][0]};
+                const unsigned long long wyz[4] = {
+                    (unsigned long long)((kWQ - da[u][1]) * (kWQ - da[u][2])),
+                    (unsigned long long)(da[u][1] * (kWQ - da[u][2])),
+                    (unsigned long long)((kWQ - da[u][1]) * da[u][2]),
+                    (unsigned long long)(da[u][1] * da[u][2])};
+                const int off[4] = {0, wx, wxy, wxy + wx};
+#pragma unroll
+                for (int c = 0; c < 8; ++c) {
+                    const unsigned long long v = wxs[c & 1] * wyz[c >> 1];
+                    if (v != 0ull) atomicAdd(win + s0 + off[c >> 1] + (c & 1), v);
+                }
+            } else {
                 deposit_global(p.rq, nx, ny, i, j, k, da[u], charge);
             }
-        } else {
-#pragma unroll
-            for (int u = 0; u < kPPT; ++u) {
-                if (dcell[u] < 0) continue;
-                int i, j, k;
-                unpack(dcell[u], i, j, k);
-                const long long wx[2] = {kWQ - da[u][0], da[u][0]};
-                const int wy[2] = {kWQ - da[u][1], da[u][1]}, wz[2] = {kWQ - da[u][2], da[u][2]};
-                const int b = block_slot(i, j, k, nx, ny, anchor, akk);
-                if (b >= 0) {
-                    const int off[8] = {0, 1, nx, nx + 1, 2 * kWinR, 2 * kWinR + 1, 2 * kWinR + nx,
-                                        2 * kWinR + nx + 1};
-#pragma unroll
-                    for (int c = 0; c < 8; ++c) {
-                        const long long v = wx[c & 1] * (long long)(wy[(c >> 1) & 1] * wz[c >> 2]);
-                        if (v == 0) continue;
-                        atomicAdd(win_hi + b + off[c], (unsigned int)(v >> 21));
-                        atomicAdd(win_lo + b + off[c], (unsigned int)(v & 0x1FFFFF));
-                    }
-                } else {
-                    int node[8];
-                    long long val[8];
-                    corners(nx, ny, i, j, k, da[u], 1, node, val);
-#pragma unroll
-                    for (int c = 0; c < 8; ++c) {
-                        if (val[c] == 0) continue;
-                        const int sl = tile_slot(node[c], k + (c >> 2), anchor, akk, nxy);
-                        if (sl >= 0) {
-                            atomicAdd(win_hi + sl, (unsigned int)(val[c] >> 21));
-                            atomicAdd(win_lo + sl, (unsigned int)(val[c] & 0x1FFFFF));
-                        } else {
-                            atomicAdd(p.rq + node[c], (unsigned long long)(charge * val[c]));
-                        }
-                    }
-                }
-            }
         }
+    }
+    if (tiled) {
         __syncthreads();
-        if (ak64) {
-            for (int t = threadIdx.x; t < kWinN; t += blockDim.x) {
-                const unsigned int hi = win_hi[t], lo = win_lo[t];
-                if (hi | lo) {
-                    const long long v = (((long long)hi << 21) + (long long)lo) * charge;
-                    const int pl = t / (2 * kWinR) - 1, w = t % (2 * kWinR);
-                    atomicAdd(p.rq + (anchor + pl * nxy + w - kWinR), (unsigned long long)v);
-                    win_hi[t] = 0u;
-                    win_lo[t] = 0u;
-                }
-            }
+        for (int t = threadIdx.x; t < wn; t += blockDim.x) {
+            const unsigned long long v = win[t];
+            if (v == 0ull) continue;
+            const int dz = t / wxy, r = t - dz * wxy, dy = r / wx, dxi = r - dy * wx;
+            int I = (ox + dxi) % nx, J = (oy + dy) % ny;
+            if (I < 0) I += nx;
+            if (J < 0) J += ny;
+            const int K = oz + dz;
+            atomicAdd(p.rq + ((size_t)K * ny + J) * nx + I, (unsigned long long)((long long)v * charge));
         }
-        if (threadIdx.x == 0) s_anchor = 0ull;
-        __syncthreads();
     }
     live = __reduce_add_sync(0xffffffffu, live);
     if ((threadIdx.x & 31) == 0 && live) atomicAdd(p.cnt + PIC_C_PUSHED, (unsigned long long)live);
@@ -1000,6 +941,14 @@ P32 params(pic_ctx* c, int sp)
     p.md_rescap = (unsigned int)c->md_rescap;
     p.mcc_list = c->mcc_list[sp];
     p.mcc_n = c->d_lists + 2 * sp + 1;
+    p.tstart = c->tstart[sp];
+    p.tx = c->tile[0]; p.ty = c->tile[1]; p.tz = c->tile[2];
+    p.ntx = c->ntile[0]; p.nty = c->ntile[1];
+    p.ntiles = (long long)c->ntiles;
+    p.halo = c->halo;
+    p.wx = c->tile[0] + 1 + 2 * c->halo;
+    p.wy = c->tile[1] + 1 + 2 * c->halo;
+    p.wz = c->tile[2] + 1 + 2 * c->halo;
     return p;
 }
 
@@ -1021,9 +970,11 @@ void launch_push32(pic_ctx* c)
     // the ion push may run beside the electron push
     cudaStream_t si = PIC_PUSH_CONC ? c->aux2 : c->stream;
     if (PIC_PUSH_CONC) cudaStreamWaitEvent(c->aux2, c->ev_fork, 0);
-    k_push32<<<grid_for((c->cap[0] + kPPT - 1) / kPPT, kPushThreads, 152 * 8), kPushThreads, 0, c->stream>>>(pe);
+    const unsigned grid = (unsigned)(c->ntiles + kTailBlocks);
+    const size_t win = sizeof(unsigned long long) * (size_t)pe.wx * pe.wy * pe.wz;
+    k_push32<<<grid, kPushThreads, win, c->stream>>>(pe);
     k_mcc32<<<152 * 4, 256, 0, c->stream>>>(pe);
-    k_push32<<<grid_for((c->cap[1] + kPPT - 1) / kPPT, kPushThreads, 152 * 8), kPushThreads, 0, si>>>(pi);
+    k_push32<<<grid, kPushThreads, win, si>>>(pi);
     k_mcc32<<<152 * 4, 256, 0, si>>>(pi);
     if (PIC_PUSH_CONC) {
         cudaEventRecord(c->ev_join2, c->aux2);

@@ -214,9 +214,19 @@ struct pic_ctx {
     double eepf_de = 0.0;
     int64_t eepf_steps = 0;
 
-    // sort scratch
-    unsigned int* hist = nullptr;            // cells + 1
-    unsigned int* cursor = nullptr;          // cells
+    // sort scratch; the mixed path sorts by tile (tile[0] x tile[1] x tile[2]
+    // cells, tile-major, cells row-major inside a tile), the FP64 path by cell
+    unsigned int* hist = nullptr;            // nkeys + 1
+    unsigned int* cursor = nullptr;          // nkeys + 1
+    size_t nkeys = 0;                        // sort key range
+    size_t nkeys_cap = 0;                    // keys the cursor buffer holds
+    int64_t ntiles_cap = 0;                  // tiles the tstart buffers hold
+    int tile[3] = {1, 1, 1};                 // mixed: tile edge in cells
+    int ntile[3] = {1, 1, 1};                // mixed: tiles per axis
+    int64_t ntiles = 0;
+    int halo = 2;                            // mixed: deposit window margin around a tile, in cells
+    unsigned int* tstart[2] = {nullptr, nullptr};   // mixed: first slot of each tile after the last sort
+                                                    // (ntiles + 1 entries; the last = particles sorted)
     std::vector<unsigned int*> scan_tmp;
     std::vector<size_t> scan_len;
 

@@ -1,9 +1,13 @@
-// Periodic counting sort of one species by linear cell index (histogram,
-// exclusive scan, scatter), dropping dead slots.  Keeps consecutive particles
-// in the same or neighbouring cells so that field gathers and deposits of a
-// warp hit the same cache lines.  The order of particles inside a cell is not
-// fixed (atomic scatter); nothing in a step depends on it: the deposit is an
-// exact integer sum and the random numbers are keyed on particle ids.
+// Periodic counting sort of one species (histogram, exclusive scan, scatter),
+// dropping dead slots.  The FP64 path sorts by linear cell index; the mixed
+// path by tile (blocks of tile[0] x tile[1] x tile[2] cells, tile-major, the
+// cells of a tile row-major inside it), so that each tile's particles occupy
+// one contiguous slot range, which the push hands to one thread block.  The
+// order of particles inside a cell is not fixed (atomic scatter); nothing in a
+// step depends on it: the deposit is an exact integer sum and the random
+// numbers are keyed on particle ids.
+#include <algorithm>
+
 #include "pic_internal.cuh"
 
 namespace pic {
@@ -13,25 +17,35 @@ constexpr int kScanThreads = 256;
 constexpr int kScanPer = 4;
 constexpr int kScanBlock = kScanThreads * kScanPer;
 
-// linear cell index (k*ny + j)*nx + i, or -1 for a dead slot
-__device__ __forceinline__ int key_of(const float4& p, int nx, int ny)
+// sort key geometry: tiles of tx x ty x tz cells, ntx x nty tiles per plane
+struct KeyGeo {
+    int tx, ty, tz, ntx, nty;
+};
+
+// mixed: tile index * (cells per tile) + the cell's row-major index inside its
+// tile, or -1 for a dead slot
+__device__ __forceinline__ int key_of(const float4& p, const KeyGeo& g)
 {
     const int c = __float_as_int(p.w);   // packed i | j << 10 | k << 20
     if (c < 0) return -1;
-    return ((c >> 20) * ny + ((c >> 10) & 1023)) * nx + (c & 1023);
+    const int i = c & 1023, j = (c >> 10) & 1023, k = c >> 20;
+    const int ti = i / g.tx, tj = j / g.ty, tk = k / g.tz;
+    const int tile = (tk * g.nty + tj) * g.ntx + ti;
+    return tile * (g.tx * g.ty * g.tz) + ((k - tk * g.tz) * g.ty + (j - tj * g.ty)) * g.tx + (i - ti * g.tx);
 }
-__device__ __forceinline__ int key_of(const double4& p, int, int) { return p.w < 0.0 ? -1 : (int)p.w; }
+// FP64: the linear cell index (k*ny + j)*nx + i held in w
+__device__ __forceinline__ int key_of(const double4& p, const KeyGeo&) { return p.w < 0.0 ? -1 : (int)p.w; }
 
 template <typename T4>
-__global__ void k_hist(const T4* __restrict__ pos, const unsigned long long* nslot, int sp, unsigned int* hist, int nx,
-                       int ny)
+__global__ void k_hist(const T4* __restrict__ pos, const unsigned long long* nslot, int sp, unsigned int* hist,
+                       KeyGeo kg)
 {
     const unsigned long long n = nslot[sp];
     const int lane = threadIdx.x & 31;
     for (unsigned long long q = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; q < n;
          q += (unsigned long long)gridDim.x * blockDim.x) {
-        const int c = key_of(pos[q], nx, ny);
-        // lanes with the same cell (common in nearly sorted input) add once
+        const int c = key_of(pos[q], kg);
+        // lanes with the same key (common in nearly sorted input) add once
         const unsigned m = __match_any_sync(__activemask(), c);
         if (c >= 0 && lane == __ffs(m) - 1) atomicAdd(hist + c, (unsigned int)__popc(m));
     }
@@ -87,16 +101,16 @@ __global__ void k_scan_add(unsigned int* out, const unsigned int* offs, size_t n
 // next step: md_next / next_n, null for FP64)
 template <typename T4>
 __global__ void k_scatter(const T4* __restrict__ pos, const T4* __restrict__ vel, const unsigned long long* nslot,
-                          int sp, unsigned int* cursor, T4* __restrict__ pos_out, T4* __restrict__ vel_out, int nx,
-                          int ny, const int* cell_ng, unsigned int* md_next, unsigned int* next_n)
+                          int sp, unsigned int* cursor, T4* __restrict__ pos_out, T4* __restrict__ vel_out, KeyGeo kg,
+                          int nx, int ny, const int* cell_ng, unsigned int* md_next, unsigned int* next_n)
 {
     const unsigned long long n = nslot[sp];
     const int lane = threadIdx.x & 31;
     for (unsigned long long q = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; q < n;
          q += (unsigned long long)gridDim.x * blockDim.x) {
         const T4 p = pos[q];
-        const int c = key_of(p, nx, ny);
-        // one cursor atomic per group of lanes with the same cell; the group's
+        const int c = key_of(p, kg);
+        // one cursor atomic per group of lanes with the same key; the group's
         // lanes take consecutive slots in lane order
         const unsigned m = __match_any_sync(__activemask(), c);
         const int leader = __ffs(m) - 1;
@@ -107,13 +121,26 @@ __global__ void k_scatter(const T4* __restrict__ pos, const T4* __restrict__ vel
         const unsigned int d = base + (unsigned int)__popc(m & ((1u << lane) - 1u));
         pos_out[d] = p;
         vel_out[d] = vel[q];
-        if (md_next && cell_ng[c] != 0) md_next[atomicAdd(next_n, 1u)] = d;
+        if (md_next) {
+            const int pc = __float_as_int(p.w);   // mixed: packed cell
+            if (cell_ng[((pc >> 20) * ny + ((pc >> 10) & 1023)) * nx + (pc & 1023)] != 0)
+                md_next[atomicAdd(next_n, 1u)] = d;
+        }
     }
 }
 
 __global__ void k_set_nslot(unsigned long long* nslot, int sp, const unsigned int* total)
 {
     nslot[sp] = *total;
+}
+
+// first slot of every tile after a scatter, which leaves cursor[key] at the end
+// of the key's range: tile t starts where key t * per_tile - 1 ends
+__global__ void k_tile_ranges(const unsigned int* cursor, unsigned int* tstart, long long ntiles, int per_tile)
+{
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t <= ntiles;
+         t += (long long)gridDim.x * blockDim.x)
+        tstart[t] = t == 0 ? 0u : cursor[t * per_tile - 1];
 }
 
 // exclusive scan of n values in place through the per-level scratch buffers
@@ -135,9 +162,10 @@ void scan(pic_ctx* c, unsigned int* data, size_t n, int level)
 void scan_cells(pic_ctx* c, unsigned int* data) { scan(c, data, c->cells, 0); }
 
 // scratch: one block-sum buffer per scan level, plus a final total slot
+// (sized for the sort keys, which are at least as many as the cells)
 size_t sort_scratch_setup(pic_ctx* c)
 {
-    size_t n = c->cells;
+    size_t n = std::max(c->nkeys, c->cells);
     size_t bytes = 0;
     c->scan_tmp.clear();
     c->scan_len.clear();
@@ -156,30 +184,34 @@ size_t sort_scratch_setup(pic_ctx* c)
 
 void sort_particles(pic_ctx* c, int sp)
 {
-    const size_t nc = c->cells;
-    cudaMemsetAsync(c->cursor, 0, sizeof(unsigned int) * nc, c->stream);
+    const size_t nk = c->nkeys;
+    const KeyGeo kg{c->tile[0], c->tile[1], c->tile[2], c->ntile[0], c->ntile[1]};
+    cudaMemsetAsync(c->cursor, 0, sizeof(unsigned int) * nk, c->stream);
     const int grid = grid_for(c->cap[sp], 256, 152 * 8);
     if (c->prec == PIC_MIXED)
-        k_hist<float4><<<grid, 256, 0, c->stream>>>((const float4*)c->pos[sp], c->d_nslot, sp, c->cursor, c->nx,
-                                                    c->ny);
+        k_hist<float4><<<grid, 256, 0, c->stream>>>((const float4*)c->pos[sp], c->d_nslot, sp, c->cursor, kg);
     else
-        k_hist<double4><<<grid, 256, 0, c->stream>>>((const double4*)c->pos[sp], c->d_nslot, sp, c->cursor, c->nx,
-                                                     c->ny);
-    scan(c, c->cursor, nc, 0);
+        k_hist<double4><<<grid, 256, 0, c->stream>>>((const double4*)c->pos[sp], c->d_nslot, sp, c->cursor, kg);
+    scan(c, c->cursor, nk, 0);
     if (c->prec == PIC_MIXED) cudaMemsetAsync(c->d_lists + 4 + sp, 0, sizeof(unsigned int), c->stream);
     if (c->prec == PIC_MIXED)
         k_scatter<float4><<<grid, 256, 0, c->stream>>>((const float4*)c->pos[sp], (const float4*)c->vel[sp],
                                                        c->d_nslot, sp, c->cursor, (float4*)c->pos_alt[sp],
-                                                       (float4*)c->vel_alt[sp], c->nx, c->ny, c->cell_ng,
+                                                       (float4*)c->vel_alt[sp], kg, c->nx, c->ny, c->cell_ng,
                                                        c->md_next[sp], c->d_lists + 4 + sp);
     else
         k_scatter<double4><<<grid, 256, 0, c->stream>>>((const double4*)c->pos[sp], (const double4*)c->vel[sp],
                                                         c->d_nslot, sp, c->cursor, (double4*)c->pos_alt[sp],
-                                                        (double4*)c->vel_alt[sp], c->nx, c->ny, c->cell_ng,
+                                                        (double4*)c->vel_alt[sp], kg, c->nx, c->ny, c->cell_ng,
                                                         (unsigned int*)nullptr, (unsigned int*)nullptr);
     // the last scan level's single block sum is the number of live particles
     k_set_nslot<<<1, 1, 0, c->stream>>>(c->d_nslot, sp, c->scan_tmp.back());
     c->launches += 3;
+    if (c->prec == PIC_MIXED) {
+        k_tile_ranges<<<grid_for(c->ntiles + 1, 256, 152 * 4), 256, 0, c->stream>>>(
+            c->cursor, c->tstart[sp], (long long)c->ntiles, c->tile[0] * c->tile[1] * c->tile[2]);
+        c->launches += 1;
+    }
     void* t = c->pos[sp]; c->pos[sp] = c->pos_alt[sp]; c->pos_alt[sp] = t;
     t = c->vel[sp]; c->vel[sp] = c->vel_alt[sp]; c->vel_alt[sp] = t;
 }

@@ -107,6 +107,9 @@ def test_null_context_rejected(lib):
     # entry points that take a run context refuse a null one without touching the GPU
     assert lib.pic_step(None, 1) == P.PIC_EINVAL
     assert lib.pic_tune_sort(None, 5, None) == P.PIC_EINVAL
+    assert lib.pic_tune(None, 5, None, None) == P.PIC_EINVAL
+    assert lib.pic_get_tuning(None, None) == P.PIC_EINVAL
+    assert lib.pic_set_tuning(None, None) == P.PIC_EINVAL
     assert lib.pic_advance(None) == P.PIC_EINVAL
     assert lib.pic_moments_phase(None, 0, 0, None, 0, None) == P.PIC_EINVAL
     assert lib.pic_fine_moments(None, 1, None, 0) == P.PIC_EINVAL

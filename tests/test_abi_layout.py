@@ -51,7 +51,7 @@ def _check(got, structs):
 def test_library_structs_match_pic_h(tmp_path):
     structs = [("pic_mesh", "pic_mesh", P.pic_mesh), ("pic_electrodes", "pic_electrodes", P.pic_electrodes),
                ("pic_gas", "pic_gas", P.pic_gas), ("pic_grains", "pic_grains", P.pic_grains),
-               ("pic_run", "pic_run", P.pic_run)]
+               ("pic_run", "pic_run", P.pic_run), ("pic_tuning", "pic_tuning", P.pic_tuning)]
     _check(_measure(tmp_path, "pic.h", os.path.join(ROOT, "include"), structs), structs)
 
 

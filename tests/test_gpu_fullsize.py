@@ -1,15 +1,24 @@
-"""Parity at the benchmark's full size (the rf sheath with the 7-grain cluster:
-64x64x256 cells, 1e7 particles), on what the oracle can compute at that size:
+"""Parity at the benchmark's full sizes, on what the oracle can compute there,
+with the oracle's own results driving the GPU (oracle -> GPU):
 
-  - the Poisson solve: the oracle's exact DFT-Thomas solution of the GPU's own
-    charge density after 3 steps in the benchmark's launch configuration (CUDA
-    graphs, sort every 8 steps); two solutions each within a relative residual
-    of 1e-10 differ by at most cond(A) x 1e-10, cond(A) ~ 12 (nz / pi)^2 for the
-    7-point operator with Dirichlet z and periodic x, y;
-  - sampled particles: 2000 electrons and 2000 ions drawn at random plus every
-    particle of the sample within 1.2 dx of a grain (the MD regions), stepped
-    once by the oracle from the GPU's phi_0 and grain tables: bit-exact in
-    FP64, within the mixed path's stated tolerances in mixed precision."""
+  - the 64x64x256 rf sheath with the 7-grain cluster and 1e7 particles:
+    * the oracle's own rho_0, unit-charge grain tables and phi_0 of the initial
+      plasma against the GPU's: rho_0 bit for bit (FP64), the tables and phi_0
+      within the two solvers' tolerances;
+    * the GPU's rho after 3 steps (CUDA graphs, sort every 8 steps) against the
+      oracle's deposit of the GPU's particles and grain counts (FP64: bit for
+      bit), and the GPU's phi against the oracle's exact DFT-Thomas solution of
+      that rho: two solutions each within a relative residual of 1e-10 differ
+      by at most cond(A) x 1e-10, cond(A) ~ 12 (nz / pi)^2 for the 7-point
+      operator with Dirichlet z and periodic x, y;
+    * one step of every particle on the GPU from the oracle's phi_0 and grain
+      tables, against the oracle stepping a sample (2000 random particles per
+      species plus every one within 1.2 dx of a grain) from the same phi_0:
+      bit-exact in FP64, within the mixed path's tolerances in mixed precision;
+  - the 256x256x1024 headline mesh with its 100-grain cluster (mixed, device-drawn
+    plasma of 5e8 particles): the GPU's phi_0 against the oracle's exact
+    solution of the GPU's rho_0, and rho_0's exact total charge.
+"""
 import ctypes as C
 import math
 
@@ -54,17 +63,47 @@ def _oracle_poisson(wl, rq, vb):
     return phi
 
 
+@pytest.fixture(scope="module")
+def oracle_full(full):
+    """The oracle's own initial state of the whole 1e7-particle plasma."""
+    wl, parts = full
+    ref = O.Sim(wl, parts)
+    return ref.rho(), ref.gtab(), ref.phi()
+
+
+def test_oracle_initial_state_matches_gpu(full, oracle_full):
+    wl, parts = full
+    rho_o, tab_o, phi_o = oracle_full
+    run = P.Run(wl, parts, prec=P.PIC_FP64, stream=_stream(), sort_every=8)
+    assert np.array_equal(run.rho(), rho_o)                       # rho_0: exact integer deposit
+    tab_g = run.gtab()
+    assert np.max(np.abs(tab_g - tab_o)) <= 1e-8 * np.max(np.abs(tab_o))   # GPU tables solved to 1e-12
+    cond = 12.0 * (wl.nz / math.pi) ** 2
+    assert np.max(np.abs(run.phi() - phi_o)) <= cond * 1e-10 * np.max(np.abs(phi_o))
+    run.close()
+    run = P.Run(wl, parts, prec=P.PIC_MIXED, stream=_stream(), sort_every=8)
+    assert np.max(np.abs(run.gtab() - tab_o)) <= 1e-8 * np.max(np.abs(tab_o))
+    assert np.max(np.abs(run.phi() - phi_o)) <= cond * 1e-10 * np.max(np.abs(phi_o))
+    run.close()
+
+
 @pytest.mark.parametrize("prec", [P.PIC_MIXED, P.PIC_FP64])
 def test_poisson_at_full_size_matches_oracle(full, prec):
     wl, parts = full
     run = P.Run(wl, parts, prec=prec, stream=_stream(), sort_every=8)
     run.step(3)
     rq, phi = run.rho(), run.phi()
+    if prec == P.PIC_FP64:
+        # the oracle's own deposit of the GPU's particles and grain counts
+        gp = [run.particles(0), run.particles(1)]
+        ref = O.Sim(wl, gp)
+        ref.set_grain_counts(run.grains()[0])
+        assert np.array_equal(ref.rho(), rq)
     t = 3 * wl.dt
     vb = wl.v_dc + wl.v_rf * math.sin(2.0 * math.pi * wl.f_rf * t + wl.phase)
-    ref = _oracle_poisson(wl, rq, vb)
+    want = _oracle_poisson(wl, rq, vb)
     cond = 12.0 * (wl.nz / math.pi) ** 2
-    err = np.max(np.abs(phi - ref)) / np.max(np.abs(ref))
+    err = np.max(np.abs(phi - want)) / np.max(np.abs(want))
     assert err <= cond * 1e-10, err
     run.close()
 
@@ -84,21 +123,25 @@ def _sample(wl, parts, n_rand=2000, seed=12):
     return out
 
 
-def _stepped_pair(wl, parts, prec):
-    """The GPU run and the oracle on the sample, both after one step from the GPU's phi_0."""
+def _stepped_pair(wl, parts, prec, oracle_full):
+    """The GPU run (all particles) and the oracle on the sample, both after one
+    step from the oracle's own phi_0 and grain tables."""
+    _, tab_o, phi_o = oracle_full
     sample = _sample(wl, parts)
     run = P.Run(wl, parts, prec=prec, stream=_stream(), sort_every=8)
+    run.set_gtab(tab_o)
+    run.set_phi(phi_o)
     ref = O.Sim(wl, sample)
-    ref.set_gtab(run.gtab())
-    ref.set_phi(run.phi())
+    ref.set_gtab(tab_o)
+    ref.set_phi(phi_o)
     run.advance()
     ref.advance()
     return run, ref, sample
 
 
-def test_fp64_sampled_particles_bit_exact_at_full_size(full):
+def test_fp64_sampled_particles_bit_exact_at_full_size(full, oracle_full):
     wl, parts = full
-    run, ref, sample = _stepped_pair(wl, parts, P.PIC_FP64)
+    run, ref, sample = _stepped_pair(wl, parts, P.PIC_FP64, oracle_full)
     for sp in range(2):
         sid = sample[sp][2]
         xg, vg, ig = run.particles(sp)
@@ -111,9 +154,9 @@ def test_fp64_sampled_particles_bit_exact_at_full_size(full):
     run.close()
 
 
-def test_mixed_sampled_particles_at_full_size(full):
+def test_mixed_sampled_particles_at_full_size(full, oracle_full):
     wl, parts = full
-    run, ref, sample = _stepped_pair(wl, parts, P.PIC_MIXED)
+    run, ref, sample = _stepped_pair(wl, parts, P.PIC_MIXED, oracle_full)
     for sp in range(2):
         sid = sample[sp][2]
         xg, vg, ig = run.particles(sp)
@@ -130,4 +173,19 @@ def test_mixed_sampled_particles_at_full_size(full):
         vscale = np.sqrt(np.mean(vo ** 2))
         bad = np.abs(vg[a] - vo[b]).max(axis=1) > 1e-4 * vscale
         assert bad.sum() <= 3 + n // 1000, (sp, int(bad.sum()))   # collision decisions that flip on a rounding
+    run.close()
+
+
+def test_headline_mesh_initial_state():
+    """256x256x1024 cells, 100 grains, 5e8 particles drawn on the device (mixed,
+    the benchmark's headline): the GPU's phi_0 against the oracle's exact
+    solution of the GPU's rho_0; the total charge of rho_0 is exactly zero."""
+    wl = I.workload(4)
+    run = P.Run(wl, None, prec=P.PIC_MIXED, stream=_stream(), sort_every=8)
+    rq = run.rho()
+    assert int(rq.sum()) == 0                                  # e and Ar+ in equal numbers, grains neutral
+    want = _oracle_poisson(wl, rq, wl.v_dc + wl.v_rf * math.sin(wl.phase))
+    cond = 12.0 * (wl.nz / math.pi) ** 2
+    err = np.max(np.abs(run.phi() - want)) / np.max(np.abs(want))
+    assert err <= cond * 1e-10, err
     run.close()

@@ -183,6 +183,40 @@ def test_sort_autotune_does_not_change_results(prec):
     assert np.array_equal(a.rho(), b.rho())
 
 
+def test_tuned_run_is_bit_identical_to_untuned(tmp_path):
+    """pic_tune (tile shape, deposit-window margin, sort interval) changes speed
+    only: a run with the tuned choices, and one with other explicit choices,
+    reach the same particles, charge and grain counts bit for bit as a run
+    with the defaults; a second tuning with the cache file applies the cached
+    entry without stepping the run."""
+    wl = I.small(nx=32, ny=32, nz=64, n_e=150000, n_i=150000, grains=3, v_dc=-40.0)
+    parts = I.sample_particles(wl)
+    cache = str(tmp_path / "tune.json")
+    probe = P.Run(wl, parts, prec=P.PIC_MIXED, stream=_stream())
+    chosen = probe.tune(4, cache_path=cache)
+    probe.close()
+    again = P.Run(wl, parts, prec=P.PIC_MIXED, stream=_stream())
+    assert again.tune(4, cache_path=cache) == chosen
+    assert again.step_index == 0
+    again.close()
+    runs = [P.Run(wl, parts, prec=P.PIC_MIXED, stream=_stream(), sort_every=5) for _ in range(3)]
+    runs[1].set_tuning(chosen)
+    runs[2].set_tuning({"sort_every": 3, "tile": [16, 8, 4], "halo": 1})
+    assert runs[2].tuning() == {"sort_every": 3, "tile": [16, 8, 4], "halo": 1}
+    for r in runs:
+        r.step(13)
+    a = runs[0]
+    for b in runs[1:]:
+        for sp in range(2):
+            xa, va, ia = a.particles(sp)
+            xb, vb, ib = b.particles(sp)
+            assert np.array_equal(ia, ib) and np.array_equal(xa, xb) and np.array_equal(va, vb)
+        assert np.array_equal(a.rho(), b.rho())
+        assert np.array_equal(a.grains()[0], b.grains()[0])
+    for r in runs:
+        r.close()
+
+
 @pytest.mark.parametrize("shape", [(8, 8, 16), (16, 16, 32)])
 def test_mixed_step_close_to_oracle(shape):
     nx, ny, nz = shape
