@@ -80,6 +80,9 @@ def args():
     ap.add_argument("--no-diag", action="store_true", help="skip the run with every diagnostic on")
     ap.add_argument("--no-extra", action="store_true", help="headline workload only (no 128x128x512 and "
                                                             "64x64x256 legs)")
+    ap.add_argument("--grains", type=int, default=None,
+                    help="keep only the first N grains of the headline workload (for profiling: fewer launches "
+                         "for the grain tables at init)")
     ap.add_argument("--particles", type=float, default=None,
                     help="macroparticles of the headline workload (both species; the weight keeps the density); "
                          "for profiling a smaller case")
@@ -414,6 +417,8 @@ def main():
     if a.particles:
         half = int(a.particles) // 2
         wl = I.workload(a.workload, n_e=half, n_i=half, weight=wl.weight * wl.n_e / half)
+    if a.grains is not None:
+        wl.grain_pos, wl.grain_r = wl.grain_pos[: a.grains], wl.grain_r[: a.grains]
     # replicas: each rank runs its own independent run (different seed)
     wl.seed = replica_seed(wl.seed, rank)
     stream = torch.cuda.current_stream().cuda_stream

@@ -4,8 +4,12 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <atomic>
+#include <memory>
+#include <mutex>
 #include <new>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "pic_internal.cuh"
@@ -56,6 +60,23 @@ using namespace pic;
 namespace {
 
 thread_local std::string g_init_error;
+
+// fn(lo, hi) over [0, n) in contiguous chunks on the host's cores (the host
+// side of pic_init touches every particle: validation and layout conversion)
+template <class F>
+void host_parallel(int64_t n, F&& fn)
+{
+    const int64_t hw = std::max<int64_t>(1, std::min<int64_t>(64, (int64_t)std::thread::hardware_concurrency()));
+    const int64_t nt = std::max<int64_t>(1, std::min<int64_t>(hw, n / 65536));
+    if (nt <= 1) {
+        fn((int64_t)0, n);
+        return;
+    }
+    std::vector<std::thread> th;
+    th.reserve((size_t)nt);
+    for (int64_t t = 0; t < nt; ++t) th.emplace_back([&fn, t, nt, n] { fn(n * t / nt, n * (t + 1) / nt); });
+    for (auto& x : th) x.join();
+}
 
 pic_status fail(pic_ctx* c, pic_status s, const std::string& msg)
 {
@@ -324,13 +345,17 @@ pic_status init_run(const pic_mesh* mesh, const pic_electrodes* el, const pic_ga
         }
         if (run->n[sp] > 0 && (!run->x_host[sp] || !run->v_host[sp] || !run->id_host[sp]))
             return fail(nullptr, PIC_EINVAL, "run: NULL particle arrays");
-        for (int64_t q = 0; q < run->n[sp]; ++q) {
-            const double* x = run->x_host[sp] + 3 * q;
-            const double* v = run->v_host[sp] + 3 * q;
-            if (!finite_all(x, 3) || !finite_all(v, 3) || x[0] < 0 || x[0] >= Lx || x[1] < 0 || x[1] >= Ly ||
-                x[2] < 0 || x[2] > Lz)
-                return fail(nullptr, PIC_EINVAL, "run: particle outside the box or non-finite");
-        }
+        std::atomic<bool> bad{false};
+        host_parallel(run->n[sp], [&](int64_t lo, int64_t hi) {
+            for (int64_t q = lo; q < hi && !bad.load(std::memory_order_relaxed); ++q) {
+                const double* x = run->x_host[sp] + 3 * q;
+                const double* v = run->v_host[sp] + 3 * q;
+                if (!finite_all(x, 3) || !finite_all(v, 3) || x[0] < 0 || x[0] >= Lx || x[1] < 0 || x[1] >= Ly ||
+                    x[2] < 0 || x[2] > Lz)
+                    bad.store(true, std::memory_order_relaxed);
+            }
+        });
+        if (bad.load()) return fail(nullptr, PIC_EINVAL, "run: particle outside the box or non-finite");
     }
     if (t_ev && run->n[0] + run->n[1] > 0xFFFFFFFFLL)
         return fail(nullptr, PIC_EINVAL, "plasma: n_e + n_i must fit the 32-bit particle ids");
@@ -527,20 +552,24 @@ pic_status init_run(const pic_mesh* mesh, const pic_electrodes* el, const pic_ga
     }
 
     // ---- upload inputs
-    std::vector<char> stage;
     unsigned int max_id = 0;
     bool any = false;
     unsigned long long nslot[2] = {(unsigned long long)run->n[0], (unsigned long long)run->n[1]};
     for (int sp = 0; sp < 2 && !t_ev; ++sp) {
         const int64_t n = run->n[sp];
-        stage.assign(2 * psz * std::max<int64_t>(n, 1), 0);
-        char* P = stage.data();
-        char* V = stage.data() + psz * std::max<int64_t>(n, 1);
-        for (int64_t q = 0; q < n; ++q) {
+        std::unique_ptr<char[]> buf(new (std::nothrow) char[2 * psz * (size_t)std::max<int64_t>(n, 1)]);
+        if (!buf) { destroy(c); return fail(nullptr, PIC_ENOMEM, "host staging buffer"); }
+        char* P = buf.get();
+        char* V = buf.get() + psz * std::max<int64_t>(n, 1);
+        std::mutex id_mu;
+        host_parallel(n, [&](int64_t lo, int64_t hi) {
+          uint32_t mx = 0;
+          bool got = false;
+          for (int64_t q = lo; q < hi; ++q) {
             const double* x = run->x_host[sp] + 3 * q;
             const double* v = run->v_host[sp] + 3 * q;
             const uint32_t id = run->id_host[sp][q];
-            if (!any || id > max_id) { max_id = id; any = true; }
+            if (!got || id > mx) { mx = id; got = true; }
             int ci[3];
             double f[3];
             const int nn[3] = {nx, ny, nz};
@@ -563,7 +592,12 @@ pic_status init_run(const pic_mesh* mesh, const pic_electrodes* el, const pic_ga
                 std::memcpy(P + psz * q, &p, psz);
                 std::memcpy(V + psz * q, &w, psz);
             }
-        }
+          }
+          if (got) {
+              std::lock_guard<std::mutex> lk(id_mu);
+              if (!any || mx > max_id) { max_id = mx; any = true; }
+          }
+        });
         cudaError_t e = cudaMemcpy(c->pos[sp], P, psz * n, cudaMemcpyHostToDevice);
         if (e == cudaSuccess) e = cudaMemcpy(c->vel[sp], V, psz * n, cudaMemcpyHostToDevice);
         if (e != cudaSuccess) { destroy(c); return cuda_fail(nullptr, e, "particle upload"); }

@@ -37,13 +37,10 @@ namespace pic {
 namespace {
 
 #ifndef PIC_PUSH_PPT
-#define PIC_PUSH_PPT 2
-#endif
-#ifndef PIC_PUSH_CONC
-#define PIC_PUSH_CONC 1                           // the ion push on a third stream beside the electron push
+#define PIC_PUSH_PPT 1
 #endif
 #ifndef PIC_PUSH_MINB
-#define PIC_PUSH_MINB 6                           // resident blocks per SM the register budget is set for
+#define PIC_PUSH_MINB 5                           // resident blocks per SM the register budget is set for
 #endif
 #ifndef PIC_PUSH_TAIL
 #define PIC_PUSH_TAIL 76                          // blocks for the particles appended since the last sort
@@ -133,6 +130,48 @@ __device__ __forceinline__ void warp_append(unsigned int* list, unsigned int* n,
     if (lane == leader) base = atomicAdd(n, (unsigned int)__popc(m));
     base = __shfl_sync(act, base, leader);
     if (pred) list[base + __popc(m & ((1u << lane) - 1u))] = q;
+}
+
+// Collision candidates of one block, staged in shared memory so that the
+// global list counter takes one atomic per block instead of one per warp (the
+// counter is shared by the whole grid and serialises in L2); entries beyond
+// the stage go to the global list directly.
+constexpr int kCandStage = 512;
+struct CandStage {
+    unsigned int n[2];
+    unsigned int q[2][kCandStage];
+};
+
+__device__ __forceinline__ void stage_append(CandStage& st, int sp, unsigned int* list, unsigned int* n,
+                                             unsigned int q, bool pred)
+{
+    const unsigned act = __activemask();
+    const unsigned m = __ballot_sync(act, pred);
+    if (!m) return;
+    const int lane = threadIdx.x & 31;
+    const int leader = __ffs(m) - 1;
+    unsigned int base = 0;
+    if (lane == leader) base = atomicAdd(&st.n[sp], (unsigned int)__popc(m));
+    base = __shfl_sync(act, base, leader);
+    if (!pred) return;
+    const unsigned int slot = base + (unsigned int)__popc(m & ((1u << lane) - 1u));
+    if (slot < kCandStage) st.q[sp][slot] = q;
+    else list[atomicAdd(n, 1u)] = q;
+}
+
+// the staged candidates of both species to the global lists (after a barrier)
+__device__ __forceinline__ void stage_flush(CandStage& st, unsigned int* list_e, unsigned int* n_e,
+                                            unsigned int* list_i, unsigned int* n_i)
+{
+    __shared__ unsigned int s_base[2];
+    if (threadIdx.x < 2) {
+        const unsigned int k = min(st.n[threadIdx.x], (unsigned int)kCandStage);
+        s_base[threadIdx.x] = k ? atomicAdd(threadIdx.x == 0 ? n_e : n_i, k) : 0u;
+    }
+    __syncthreads();
+    const unsigned int ke = min(st.n[0], (unsigned int)kCandStage), ki = min(st.n[1], (unsigned int)kCandStage);
+    for (unsigned int t = threadIdx.x; t < ke; t += blockDim.x) list_e[s_base[0] + t] = st.q[0][t];
+    for (unsigned int t = threadIdx.x; t < ki; t += blockDim.x) list_i[s_base[1] + t] = st.q[1][t];
 }
 
 // CIC gather of the node field with the fixed-point weights a/2^14 per axis
@@ -377,53 +416,52 @@ __device__ __forceinline__ int wrel(int n, int o, int len)
     return d;
 }
 
-// Blocks [0, ntiles): the particles of one tile (slot range at the last sort),
-// deposits summed in a shared window of wx x wy x wz nodes from the tile's
-// lower corner minus `halo` cells, flushed once.  Blocks [ntiles, grid): the
-// ionization products appended since the sort, deposited with global atomics.
-__global__ void __launch_bounds__(kPushThreads, PIC_PUSH_MINB) k_push32(const P32 p)
+// Exact 64-bit sums in the shared window from 32-bit shared atomics (a native
+// 32-bit add is far cheaper than a 64-bit one): the low words at win32[s], the
+// high words at win32[wn + s]; the carry out of the low word is detected from
+// the value the low add returned.  Sums are modulo 2^64, so two's-complement
+// (negative) contributions add correctly.
+__device__ __forceinline__ void win_add(unsigned int* win32, int wn, int s, unsigned long long v)
 {
-    extern __shared__ unsigned long long win[];
-    const uint32_t step = *p.step;
+    const unsigned int lo = (unsigned int)v, hi = (unsigned int)(v >> 32);
+    const unsigned int old = atomicAdd(win32 + s, lo);
+    atomicAdd(win32 + wn + s, hi + (old + lo < old ? 1u : 0u));
+}
+
+// The particles of one species in slots [first, end) with block-uniform trips
+// of kPPT x kPushThreads (every lane of a warp takes every trip: warp votes
+// below).  Deposits go to the block's window (signed sums) when all 8 corners
+// fall inside it, else to global atomics.
+__device__ __forceinline__ void push_range(const P32& p, unsigned long long first, unsigned long long end,
+                                           unsigned long long stride, bool tiled, int ox, int oy, int oz,
+                                           unsigned int* win, CandStage& cst, uint32_t step,
+                                           unsigned int& live)
+{
+    const int wn = p.wx * p.wy * p.wz;
     const bool frozen = (p.sp == 1) && (p.flags & PIC_F_IONS_FROZEN);
     const bool no_mcc = p.flags & PIC_F_NO_MCC;
     const long long charge = p.sp == 0 ? -1 : 1;
     const int nx = p.nx, ny = p.ny, nz = p.nz;
-    const int wx = p.wx, wy = p.wy, wz = p.wz, wxy = wx * wy, wn = wxy * wz;
-    const long long b = blockIdx.x;
-    const bool tiled = b < p.ntiles;
-    // block-uniform loop bounds: every lane of a warp takes every trip (warp votes below)
-    unsigned long long first, end, stride;
-    int ox = 0, oy = 0, oz = 0;
-    if (tiled) {
-        first = p.tstart[b];
-        end = p.tstart[b + 1];
-        if (first == end) return;                // the whole block leaves together
-        const int ti = (int)(b % p.ntx), tj = (int)((b / p.ntx) % p.nty), tk = (int)(b / ((long long)p.ntx * p.nty));
-        ox = ti * p.tx - p.halo;
-        oy = tj * p.ty - p.halo;
-        oz = tk * p.tz - p.halo;
-        for (int t = threadIdx.x; t < wn; t += blockDim.x) win[t] = 0ull;
-        __syncthreads();
-        stride = (unsigned long long)kPushThreads * kPPT;
-    } else {
-        first = p.tstart[p.ntiles] + (unsigned long long)(b - p.ntiles) * kPushThreads * kPPT;
-        end = p.nslot[p.sp];
-        stride = (unsigned long long)(gridDim.x - p.ntiles) * kPushThreads * kPPT;
-    }
-    unsigned int live = 0;
+    const int wx = p.wx, wy = p.wy, wz = p.wz, wxy = wx * wy;
     for (unsigned long long q0 = first; q0 < end; q0 += stride) {
         int dcell[kPPT];
         int da[kPPT][3];
+        float4 Pr[kPPT], Vr[kPPT];
+        // both records of every particle of the trip in flight at once; they stream
+        // through once (evict-first), so the charge and field arrays keep L2
+#pragma unroll
+        for (int u = 0; u < kPPT; ++u) {
+            const unsigned long long q = q0 + (unsigned long long)u * kPushThreads + threadIdx.x;
+            Pr[u] = q < end ? __ldcs(p.pos + q) : make_float4(0.f, 0.f, 0.f, __int_as_float(-1));
+            Vr[u] = q < end ? __ldcs(p.vel + q) : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
 #pragma unroll
         for (int u = 0; u < kPPT; ++u) {
             dcell[u] = -1;
             const unsigned long long q = q0 + (unsigned long long)u * kPushThreads + threadIdx.x;
             int lost = 0;
             bool md = false, cand = false;
-            // particle records stream through once: evict-first, so that the charge
-            // and field arrays keep their place in L2
-            const float4 Pu = q < end ? __ldcs(p.pos + q) : make_float4(0.f, 0.f, 0.f, __int_as_float(-1));
+            const float4 Pu = Pr[u];
             int cell = __float_as_int(Pu.w);
             if (cell >= 0) {
                 ++live;
@@ -436,7 +474,7 @@ __global__ void __launch_bounds__(kPushThreads, PIC_PUSH_MINB) k_push32(const P3
                 } else if (p.cell_ng[(k * ny + j) * nx + i] != 0) {
                     // in an MD region: on this step's MD list, advanced by k_md32
                 } else {
-                    const float4 Vu = __ldcs(p.vel + q);
+                    const float4 Vu = Vr[u];
                     float v[3] = {Vu.x, Vu.y, Vu.z};
                     int a[3] = {qa(o[0]), qa(o[1]), qa(o[2])};
                     float E[3];
@@ -463,7 +501,7 @@ __global__ void __launch_bounds__(kPushThreads, PIC_PUSH_MINB) k_push32(const P3
             }
             if (__any_sync(0xffffffffu, md || cand || lost)) {
                 warp_append(p.md_next, p.md_next_n, (unsigned int)q, md);
-                warp_append(p.mcc_list, p.mcc_n, (unsigned int)q, cand);
+                stage_append(cst, p.sp, p.mcc_list, p.mcc_n, (unsigned int)q, cand);
                 if (__any_sync(0xffffffffu, lost != 0)) {
                     warp_count(p.cnt + (p.sp == 0 ? PIC_C_LOST_BOT_E : PIC_C_LOST_BOT_I), lost == 1);
                     warp_count(p.cnt + (p.sp == 0 ? PIC_C_LOST_TOP_E : PIC_C_LOST_TOP_I), lost == 2);
@@ -472,7 +510,6 @@ __global__ void __launch_bounds__(kPushThreads, PIC_PUSH_MINB) k_push32(const P3
                 }
             }
         }
-        // ---- deposit: the block's window when all 8 corners fall inside it, else global atomics
 #pragma unroll
         for (int u = 0; u < kPPT; ++u) {
             if (dcell[u] < 0) continue;
@@ -481,38 +518,86 @@ __global__ void __launch_bounds__(kPushThreads, PIC_PUSH_MINB) k_push32(const P3
             const int di = wrel(i, ox, nx), dj = wrel(j, oy, ny), dk = k - oz;
             if (tiled && di + 1 < wx && dj + 1 < wy && dk >= 0 && dk + 1 < wz) {
                 const int s0 = (dk * wy + dj) * wx + di;
-                const unsigned long long wxs[2] = {(unsigned long long)(kWQ - da[u][0]), (unsigned long long)da[u][0]};
-                const unsigned long long wyz[4] = {
-                    (unsigned long long)((kWQ - da[u][1]) * (kWQ - da[u][2])),
-                    (unsigned long long)(da[u][1] * (kWQ - da[u][2])),
-                    (unsigned long long)((kWQ - da[u][1]) * da[u][2]),
-                    (unsigned long long)(da[u][1] * da[u][2])};
+                // corner weight wx (< 2^15) x wy wz (< 2^29): one 32 x 32 -> 64-bit product;
+                // electrons add the two's complement (the window holds signed sums)
+                const unsigned int wxs[2] = {(unsigned int)(kWQ - da[u][0]), (unsigned int)da[u][0]};
+                const unsigned int wyz[4] = {(unsigned int)((kWQ - da[u][1]) * (kWQ - da[u][2])),
+                                             (unsigned int)(da[u][1] * (kWQ - da[u][2])),
+                                             (unsigned int)((kWQ - da[u][1]) * da[u][2]),
+                                             (unsigned int)(da[u][1] * da[u][2])};
                 const int off[4] = {0, wx, wxy, wxy + wx};
 #pragma unroll
                 for (int c = 0; c < 8; ++c) {
-                    const unsigned long long v = wxs[c & 1] * wyz[c >> 1];
-                    if (v != 0ull) atomicAdd(win + s0 + off[c >> 1] + (c & 1), v);
+                    const unsigned long long v = (unsigned long long)wxs[c & 1] * wyz[c >> 1];
+                    win_add(win, wn, s0 + off[c >> 1] + (c & 1), charge < 0 ? 0ull - v : v);
                 }
             } else {
                 deposit_global(p.rq, nx, ny, i, j, k, da[u], charge);
             }
         }
     }
+}
+
+// Blocks [0, ntiles): the electrons, then the ions, of one tile (their slot
+// ranges at the last sort), deposits of both summed in one shared window of
+// wx x wy x wz nodes from the tile's lower corner minus `halo` cells, flushed
+// once.  Blocks [ntiles, grid): the ionization products appended since the
+// sort, deposited with global atomics.
+__global__ void __launch_bounds__(kPushThreads, PIC_PUSH_MINB) k_push32(const P32 pe, const P32 pi)
+{
+    extern __shared__ unsigned int win[];          // low words [0, wn), high words [wn, 2 wn)
+    __shared__ CandStage cst;
+    __shared__ unsigned int s_live;
+    const uint32_t step = *pe.step;
+    const int nx = pe.nx, ny = pe.ny;
+    const int wx = pe.wx, wy = pe.wy, wz = pe.wz, wxy = wx * wy, wn = wxy * wz;
+    const long long b = blockIdx.x;
+    const bool tiled = b < pe.ntiles;
+    unsigned int live = 0;
     if (tiled) {
+        const unsigned long long e0 = pe.tstart[b], e1 = pe.tstart[b + 1];
+        const unsigned long long i0 = pi.tstart[b], i1 = pi.tstart[b + 1];
+        if (e0 == e1 && i0 == i1) return;                       // the whole block leaves together
+        const int ti = (int)(b % pe.ntx), tj = (int)((b / pe.ntx) % pe.nty),
+                  tk = (int)(b / ((long long)pe.ntx * pe.nty));
+        const int ox = ti * pe.tx - pe.halo, oy = tj * pe.ty - pe.halo, oz = tk * pe.tz - pe.halo;
+        for (int t = threadIdx.x; t < 2 * wn; t += blockDim.x) win[t] = 0u;
+        if (threadIdx.x < 2) cst.n[threadIdx.x] = 0u;
+        if (threadIdx.x == 0) s_live = 0u;
         __syncthreads();
-        for (int t = threadIdx.x; t < wn; t += blockDim.x) {
-            const unsigned long long v = win[t];
-            if (v == 0ull) continue;
-            const int dz = t / wxy, r = t - dz * wxy, dy = r / wx, dxi = r - dy * wx;
-            int I = (ox + dxi) % nx, J = (oy + dy) % ny;
-            if (I < 0) I += nx;
-            if (J < 0) J += ny;
-            const int K = oz + dz;
-            atomicAdd(p.rq + ((size_t)K * ny + J) * nx + I, (unsigned long long)((long long)v * charge));
-        }
+        const unsigned long long stride = (unsigned long long)kPushThreads * kPPT;
+        push_range(pe, e0, e1, stride, true, ox, oy, oz, win, cst, step, live);
+        push_range(pi, i0, i1, stride, true, ox, oy, oz, win, cst, step, live);
+        __syncthreads();
+        // flush: each pass takes blockDim / wx whole window rows, one thread per node
+        const int rows_per_pass = blockDim.x / wx;
+        const int dxi = threadIdx.x - (threadIdx.x / wx) * wx;
+        const int I = ((ox + dxi) % nx + nx) % nx;
+        if ((int)threadIdx.x < rows_per_pass * wx)
+            for (int row = threadIdx.x / wx; row < wy * wz; row += rows_per_pass) {
+                const int t = row * wx + dxi;
+                const unsigned long long v = ((unsigned long long)win[wn + t] << 32) | win[t];
+                if (v == 0ull) continue;
+                const int dz = row / wy, dy = row - dz * wy;
+                const int J = ((oy + dy) % ny + ny) % ny;
+                atomicAdd(pe.rq + ((size_t)(oz + dz) * ny + J) * nx + I, v);
+            }
+    } else {
+        if (threadIdx.x < 2) cst.n[threadIdx.x] = 0u;
+        if (threadIdx.x == 0) s_live = 0u;
+        __syncthreads();
+        const unsigned long long tb = (unsigned long long)(b - pe.ntiles) * kPushThreads * kPPT;
+        const unsigned long long stride = (unsigned long long)(gridDim.x - pe.ntiles) * kPushThreads * kPPT;
+        push_range(pe, pe.tstart[pe.ntiles] + tb, pe.nslot[0], stride, false, 0, 0, 0, win, cst, step, live);
+        push_range(pi, pi.tstart[pi.ntiles] + tb, pi.nslot[1], stride, false, 0, 0, 0, win, cst, step, live);
+        __syncthreads();
     }
+    // one global atomic per block for the candidates of each species and the live count
+    stage_flush(cst, pe.mcc_list, pe.mcc_n, pi.mcc_list, pi.mcc_n);
     live = __reduce_add_sync(0xffffffffu, live);
-    if ((threadIdx.x & 31) == 0 && live) atomicAdd(p.cnt + PIC_C_PUSHED, (unsigned long long)live);
+    if ((threadIdx.x & 31) == 0 && live) atomicAdd(&s_live, live);
+    __syncthreads();
+    if (threadIdx.x == 0 && s_live) atomicAdd(pe.cnt + PIC_C_PUSHED, (unsigned long long)s_live);
 }
 
 // Field data of one cell for the MD substeps: the 8 corner values of
@@ -966,26 +1051,23 @@ void launch_push32(pic_ctx* c)
     k_md32<<<152 * 4, 64, 0, c->aux>>>(pe);
     k_md32<<<152 * 4, 64, 0, c->aux>>>(pi);
     cudaEventRecord(c->ev_join, c->aux);
-    // the two species share only the charge array and counters (both atomic), so
-    // the ion push may run beside the electron push
-    cudaStream_t si = PIC_PUSH_CONC ? c->aux2 : c->stream;
-    if (PIC_PUSH_CONC) cudaStreamWaitEvent(c->aux2, c->ev_fork, 0);
+    // both species of a tile in one block: one window, one flush
     const unsigned grid = (unsigned)(c->ntiles + kTailBlocks);
     const size_t win = sizeof(unsigned long long) * (size_t)pe.wx * pe.wy * pe.wz;
-    k_push32<<<grid, kPushThreads, win, c->stream>>>(pe);
+    k_push32<<<grid, kPushThreads, win, c->stream>>>(pe, pi);
+    // the collision candidates of the two species, side by side
+    cudaEventRecord(c->ev_fork, c->stream);
+    cudaStreamWaitEvent(c->aux2, c->ev_fork, 0);
     k_mcc32<<<152 * 4, 256, 0, c->stream>>>(pe);
-    k_push32<<<grid, kPushThreads, win, si>>>(pi);
-    k_mcc32<<<152 * 4, 256, 0, si>>>(pi);
-    if (PIC_PUSH_CONC) {
-        cudaEventRecord(c->ev_join2, c->aux2);
-        cudaStreamWaitEvent(c->stream, c->ev_join2, 0);
-    }
+    k_mcc32<<<152 * 4, 256, 0, c->aux2>>>(pi);
+    cudaEventRecord(c->ev_join2, c->aux2);
+    cudaStreamWaitEvent(c->stream, c->ev_join2, 0);
     cudaStreamWaitEvent(c->stream, c->ev_join, 0);
     k_md_commit<<<64, 256, 0, c->stream>>>((float4*)c->pos[0], (float4*)c->vel[0], c->md_list[0], c->md_res[0],
                                            (float4*)c->pos[1], (float4*)c->vel[1], c->md_list[1], c->md_res[1],
                                            c->d_lists, (unsigned int)c->md_rescap,
                                            (c->flags & PIC_F_IONS_FROZEN) ? 1 : 0);
-    c->launches += 9;
+    c->launches += 8;
 }
 
 void launch_deposit32(pic_ctx* c)

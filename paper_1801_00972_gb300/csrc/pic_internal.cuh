@@ -51,8 +51,11 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k)
 #pragma unroll
     for (int r = 0; r < 10; ++r) {
         if (r > 0) { k.x += 0x9E3779B9u; k.y += 0xBB67AE85u; }
-        const uint32_t a0 = 0xD2511F53u * c.x, b0 = __umulhi(0xD2511F53u, c.x);
-        const uint32_t a1 = 0xCD9E8D57u * c.z, b1 = __umulhi(0xCD9E8D57u, c.z);
+        // each 32 x 32 -> 64-bit product once, its low and high words
+        const unsigned long long p0 = (unsigned long long)0xD2511F53u * c.x;
+        const unsigned long long p1 = (unsigned long long)0xCD9E8D57u * c.z;
+        const uint32_t a0 = (uint32_t)p0, b0 = (uint32_t)(p0 >> 32);
+        const uint32_t a1 = (uint32_t)p1, b1 = (uint32_t)(p1 >> 32);
         c = make_uint4(b1 ^ c.y ^ k.x, a1, b0 ^ c.w ^ k.y, a0);
     }
     return c;

@@ -21,7 +21,7 @@
 #include "pic_internal.cuh"
 
 #ifndef PIC_MG_FUSED
-#define PIC_MG_FUSED 1            // fused 2.5-D smoothing passes on the large grid-wide levels
+#define PIC_MG_FUSED 0            // fused 2.5-D smoothing passes on the large grid-wide levels (measured slower)
 #endif
 #ifndef PIC_MG_PRE
 #define PIC_MG_PRE 2
@@ -290,9 +290,19 @@ template <bool kPost>
 struct SmoothShape {
     static constexpr int H = kPost ? 4 : 3;
     static constexpr int S = kPost ? 4 : 3;      // last stage
-    static constexpr int RU = S + 2, RF = S + 1;
+    // ring depths: the planes the stages read at step t (t - S - 1 .. t) plus the
+    // next plane, which is already on its way (asynchronous copy)
+    static constexpr int RU = S + 3, RF = S + 2;
     static constexpr int WX = kSmTX + 2 * H, WY = kSmTY + 2 * H, PW = WX * WY;
 };
+
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem)
+{
+    const unsigned int a = (unsigned int)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(a), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_prev() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
 
 template <typename T, bool kPost>
 __global__ void __launch_bounds__(256) k_smooth_fused(const T* __restrict__ u_in, const T* __restrict__ f,
@@ -309,18 +319,38 @@ __global__ void __launch_bounds__(256) k_smooth_fused(const T* __restrict__ u_in
     const int k0 = 1 + blockIdx.z * tz, k1 = min(d.nz, k0 + tz);           // output planes [k0, k1)
     const int P = d.nx * d.ny, Pc = dc.nx * dc.ny;
     const int tid = threadIdx.x;
-    for (int t = k0 - H; t <= k1 - 1 + S; ++t) {
-        // ---- plane t into the rings (zeros on and beyond the electrode planes)
+    const int t_last = k1 - 1 + S;
+    // plane t into the rings: asynchronous copies of f (and u_in), zeros on and
+    // beyond the electrode planes
+    auto fetch = [&](int t) {
         T* ut = su + ((t % RU) + RU) % RU * PW;
         T* ft = sf + ((t % RF) + RF) % RF * PW;
         const bool inner = t >= 1 && t <= d.nz - 1;
         for (int q = tid; q < PW; q += blockDim.x) {
             const int ly = q / WX, lx = q - ly * WX;
+            if (!inner) {
+                ft[q] = (T)0;
+                ut[q] = (T)0;
+                continue;
+            }
             const int n = t * P + wrap_idx(Y0 + ly, d.ny) * d.nx + wrap_idx(X0 + lx, d.nx);
-            ft[q] = inner ? f[n] : (T)0;
-            if (kPost) ut[q] = inner ? u_in[n] : (T)0;
-            else if (!inner) ut[q] = (T)0;
+            if (sizeof(T) == 4) {
+                cp_async4(ft + q, f + n);
+                if (kPost) cp_async4(ut + q, u_in + n);
+            } else {
+                ft[q] = f[n];
+                if (kPost) ut[q] = u_in[n];
+            }
         }
+        cp_async_commit();
+    };
+    fetch(k0 - H);
+    for (int t = k0 - H; t <= t_last; ++t) {
+        // the next plane goes out before this one is used; its ring slots are
+        // those of planes the stages of this step no longer read
+        if (t < t_last) fetch(t + 1);
+        else cp_async_commit();
+        cp_async_wait_prev();
         __syncthreads();
         // ---- stages: stage s on plane t - s, region [s, WX - s) x [s, WY - s)
 #pragma unroll 1
@@ -376,6 +406,50 @@ __global__ void __launch_bounds__(256) k_smooth_fused(const T* __restrict__ u_in
             for (int q = tid; q < kSmTX * kSmTY; q += blockDim.x) {
                 const int ly = q / kSmTX, lx = q - ly * kSmTX;
                 u_out[qo * P + (Y0 + H + ly) * d.nx + (X0 + H + lx)] = uq[(H + ly) * WX + (H + lx)];
+            }
+        }
+    }
+}
+
+// The same interpolation, one thread per coarse cell (I, J, K): its 8 corner
+// values are loaded once and give the 2 x 2 x 2 fine nodes (2I + a, 2J + b,
+// 2K + c), each summed exactly as in k_prolong (a coincident axis repeats its
+// corner), so the result is bit-identical with 8 times fewer coarse loads.
+template <typename T>
+__global__ void k_prolong_cell(T* __restrict__ uf, const T* __restrict__ uc, Dims df, Dims dc)
+{
+    pdl_begin();
+    const int I = blockIdx.x * blockDim.x + threadIdx.x;
+    const int J = blockIdx.y * blockDim.y + threadIdx.y;
+    const int K = blockIdx.z;
+    if (I >= dc.nx || J >= dc.ny) return;
+    const int I1 = (I + 1 == dc.nx) ? 0 : I + 1, J1 = (J + 1 == dc.ny) ? 0 : J + 1;
+    const int Pc = dc.nx * dc.ny;
+    const T* a0 = uc + K * Pc;
+    const T* a1 = a0 + Pc;
+    // c[z][y][x]: corners at (I or I1, J or J1, K or K + 1)
+    const T c000 = a0[J * dc.nx + I], c001 = a0[J * dc.nx + I1], c010 = a0[J1 * dc.nx + I], c011 = a0[J1 * dc.nx + I1];
+    const T c100 = a1[J * dc.nx + I], c101 = a1[J * dc.nx + I1], c110 = a1[J1 * dc.nx + I], c111 = a1[J1 * dc.nx + I1];
+    const int P = df.nx * df.ny;
+#pragma unroll
+    for (int cz = 0; cz < 2; ++cz) {
+        const int k = 2 * K + cz;
+        if (k < 1 || k > df.nz - 1) continue;
+        // K1 = K + cz: the second plane term repeats the first when cz = 0
+        const T z0[4] = {c000, c001, c010, c011};
+        const T z1[4] = {cz ? c100 : c000, cz ? c101 : c001, cz ? c110 : c010, cz ? c111 : c011};
+#pragma unroll
+        for (int by = 0; by < 2; ++by) {
+            const int j = 2 * J + by;
+#pragma unroll
+            for (int bx = 0; bx < 2; ++bx) {
+                const int i = 2 * I + bx;
+                // terms in k_prolong's order: a0[J0 I0], a0[J0 I1], a0[J1 I0], a0[J1 I1], then a1 likewise,
+                // with I1 = I0 and J1 = J0 on the even axes
+                const T p00 = z0[0], p01 = z0[bx ? 1 : 0], p10 = z0[by ? 2 : 0], p11 = z0[(by ? 2 : 0) + (bx ? 1 : 0)];
+                const T q00 = z1[0], q01 = z1[bx ? 1 : 0], q10 = z1[by ? 2 : 0], q11 = z1[(by ? 2 : 0) + (bx ? 1 : 0)];
+                const T v = (T)0.125 * (p00 + p01 + p10 + p11 + q00 + q01 + q10 + q11);
+                uf[k * P + j * df.nx + i] += v;
             }
         }
     }
@@ -1276,7 +1350,9 @@ inline Grid3 grid_norm(int nx, int ny, int planes)
 {
     Grid3 g = grid3(nx, ny, 1);
     const int per_plane = (int)(g.grid.x * g.grid.y);
-    const int zb = std::max(1, std::min(planes, (PIC_NORM_BLOCKS + per_plane - 1) / per_plane));
+    // whole planes per block row, never more blocks than one resident wave: a
+    // partial second wave of plane-looping blocks would double the kernel's time
+    const int zb = std::max(1, std::min(planes, PIC_NORM_BLOCKS / per_plane));
     g.grid.z = (unsigned)zb;
     return g;
 }
@@ -1308,6 +1384,11 @@ void run_resid_restrict(cudaStream_t s, const T* u, const T* f, T* fc, T* uc, Di
 template <typename T>
 void run_prolong(cudaStream_t s, T* uf, const T* uc, Dims df, Dims dc)
 {
+    if (df.nx == 2 * dc.nx && df.ny == 2 * dc.ny && df.nz == 2 * dc.nz) {
+        const Grid3 g = grid3(dc.nx, dc.ny, dc.nz);
+        launch_pdl(s, g.grid, g.block, k_prolong_cell<T>, uf, uc, df, dc);
+        return;
+    }
     const Grid3 g = grid3(df.nx, df.ny, df.nz - 1);
     launch_pdl(s, g.grid, g.block, k_prolong<T>, uf, uc, df, dc);
 }
