@@ -185,7 +185,7 @@ pic_status pic_tune_sort(pic_ctx* ctx, int32_t steps_per_candidate, int32_t* cho
  *               deposit window around its tile, for the particles that drift
  *               out of the tile between sorts (in [0, 8]); the window of
  *               (tile + 1 + 2 halo) nodes per axis, 8 bytes each, must fit
- *               48 KB.
+ *               96 KB.
  * The FP64 path uses sort_every only. */
 typedef struct {
     int32_t sort_every;

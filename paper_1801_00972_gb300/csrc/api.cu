@@ -550,6 +550,10 @@ pic_status init_run(const pic_mesh* mesh, const pic_electrodes* el, const pic_ga
         destroy(c);
         return fail(nullptr, PIC_ENOMEM, "device allocation failed");
     }
+    if (mixed && push32_set_window(c) != cudaSuccess) {
+        destroy(c);
+        return fail(nullptr, PIC_ECUDA, "push window size");
+    }
 
     // ---- upload inputs
     unsigned int max_id = 0;
@@ -1028,7 +1032,7 @@ void drop_graphs(pic_ctx* c)
         }
 }
 
-constexpr size_t kMaxWindowBytes = 48 * 1024;
+constexpr size_t kMaxWindowBytes = 96 * 1024;
 
 size_t tuning_window_bytes(const int32_t tile[3], int32_t halo)
 {
@@ -1132,7 +1136,7 @@ pic_status pic_set_tuning(pic_ctx* c, const pic_tuning* t)
     if (t->halo < 0 || t->halo > 8) return fail(c, PIC_EINVAL, "tuning: halo in [0, 8]");
     if (tuning_window_bytes(t->tile, t->halo) > kMaxWindowBytes)
         return fail(c, PIC_EINVAL, "tuning: the deposit window (tile + 1 + 2 halo nodes per axis, 8 B each) "
-                                   "exceeds 48 KB");
+                                   "exceeds 96 KB");
     c->sort_every = t->sort_every;
     const bool same = t->tile[0] == c->tile[0] && t->tile[1] == c->tile[1] && t->tile[2] == c->tile[2] &&
                       t->halo == c->halo;
@@ -1167,6 +1171,8 @@ pic_status pic_set_tuning(pic_ctx* c, const pic_tuning* t)
     c->ntiles = ntiles;
     c->nkeys = nkeys;
     c->halo = t->halo;
+    e = push32_set_window(c);
+    if (e != cudaSuccess) return cuda_fail(c, e, "tuning: push window size");
     drop_graphs(c);
     sort_particles(c, 0);
     sort_particles(c, 1);

@@ -1070,6 +1070,13 @@ void launch_push32(pic_ctx* c)
     c->launches += 8;
 }
 
+cudaError_t push32_set_window(pic_ctx* c)
+{
+    const size_t win = sizeof(unsigned long long) * (size_t)(c->tile[0] + 1 + 2 * c->halo) *
+                       (size_t)(c->tile[1] + 1 + 2 * c->halo) * (size_t)(c->tile[2] + 1 + 2 * c->halo);
+    return cudaFuncSetAttribute(k_push32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)win);
+}
+
 void launch_deposit32(pic_ctx* c)
 {
     for (int sp = 0; sp < 2; ++sp)

@@ -313,6 +313,7 @@ void launch_init_plasma(pic_ctx* c, int sp, int64_t n, uint32_t id0, double t_ev
 // particles_mixed.cu
 void launch_efield32(pic_ctx* c);
 void launch_push32(pic_ctx* c);
+cudaError_t push32_set_window(pic_ctx* c);     // dynamic shared memory of the push for the current tiling
 void launch_children32(pic_ctx* c);
 void launch_deposit32(pic_ctx* c);
 void launch_moments32(pic_ctx* c);

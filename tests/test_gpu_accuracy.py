@@ -63,3 +63,50 @@ def test_mixed_within_fp64_noise_on_the_rf_cluster():
     spread = max(np.std(qa), np.std(qb)) + w_e
     assert abs(np.mean(qm) - np.mean(qa)) <= spread, (qm / I.QE, qa / I.QE)
     assert np.all(qm <= 0) and np.all(qa <= 0)
+
+
+def _cluster_run(prec, seed, steps, phases):
+    """The 64x64x256 rf sheath with a 40-grain cluster drawn from a seed (a
+    1.2 mm sphere 5.6 mm above the driven electrode), 1e7 particles."""
+    import torch
+    wl = I.workload(1)
+    L = wl.box
+    wl.grain_pos, wl.grain_r = I.sphere_cluster(40, 1.2e-3, (L[0] / 2, L[1] / 2, 5.6e-3), 4e-6, 5e-6, wl.dx,
+                                                (wl.nx, wl.ny, wl.nz), 4242)
+    wl.seed = seed
+    run = P.Run(wl, None, prec=prec, flags=P.PIC_F_MOMENTS, mom_phases=phases,
+                stream=torch.cuda.current_stream().cuda_stream, sort_every=6)
+    run.step(steps // 2)
+    run.moments(1, reset=True)
+    run.step(steps - steps // 2)
+    prof = []
+    for b in range(phases):
+        f, n = run.moments_phase(3, b)
+        prof.append(f.reshape(wl.nz + 1, wl.ny, wl.nx, 3)[..., 2].sum(axis=(1, 2)))
+    q = run.grains()[1] / (wl.weight * I.QE)        # charge in units of one super-particle charge
+    run.close()
+    return np.array(prof), q
+
+
+@pytest.mark.gpu
+def test_grain_charge_distribution_and_phase_resolved_electron_flux():
+    """Over 4000 steps (0.4 us, 5.4 rf periods): the 40 grain charges of the
+    mixed run and of the FP64 run of the same seed are one distribution (a
+    two-sample KS test does not separate them, and their means agree within
+    the FP64 seed-to-seed spread), and the electron flux toward the electrodes,
+    resolved in 8 rf phase bins and summed over each node plane, differs from
+    the FP64 run by no more than the FP64 seed-to-seed noise (which the plane
+    sums bring below 10 %)."""
+    from scipy import stats
+    steps, phases = 4000, 8
+    fa, qa = _cluster_run(P.PIC_FP64, 7, steps, phases)
+    fb, qb = _cluster_run(P.PIC_FP64, 8, steps, phases)
+    fm, qm = _cluster_run(P.PIC_MIXED, 7, steps, phases)
+    noise = _rel(fb, fa)
+    err = _rel(fm, fa)
+    assert noise < 0.10, noise
+    assert err <= 1.5 * noise, (err, noise)
+    assert stats.ks_2samp(qm, qa).pvalue > 0.01, (np.sort(qm), np.sort(qa))
+    spread = max(np.std(qa), np.std(qb)) / np.sqrt(len(qa)) + 1.0
+    assert abs(np.mean(qm) - np.mean(qa)) <= 3 * spread + abs(np.mean(qb) - np.mean(qa)), (qm.mean(), qa.mean(),
+                                                                                             qb.mean())

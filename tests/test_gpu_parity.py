@@ -201,8 +201,9 @@ def test_tuned_run_is_bit_identical_to_untuned(tmp_path):
     again.close()
     runs = [P.Run(wl, parts, prec=P.PIC_MIXED, stream=_stream(), sort_every=5) for _ in range(3)]
     runs[1].set_tuning(chosen)
-    runs[2].set_tuning({"sort_every": 3, "tile": [16, 8, 4], "halo": 1})
-    assert runs[2].tuning() == {"sort_every": 3, "tile": [16, 8, 4], "halo": 1}
+    # a window of 23 x 23 x 11 nodes (46.5 KB, past the 48 KB default with the static shared memory)
+    runs[2].set_tuning({"sort_every": 3, "tile": [16, 16, 4], "halo": 3})
+    assert runs[2].tuning() == {"sort_every": 3, "tile": [16, 16, 4], "halo": 3}
     for r in runs:
         r.step(13)
     a = runs[0]
