@@ -1,8 +1,9 @@
 """Build libpic.so (the C-ABI library) in-tree with nvcc for sm_103a.
 
-Each translation unit compiles in parallel; the FP64 particle unit, the
+Each translation unit compiles in parallel; the FP64 particle unit, the FP64
 Coulomb-collision unit and the diagnostics unit are built with --fmad=false so that their
-arithmetic rounds exactly as written.
+arithmetic rounds exactly as written (the float Coulomb unit, coulomb_mixed.cu, is the same
+source built with fused multiply-add).
 """
 from __future__ import annotations
 
@@ -25,6 +26,7 @@ UNITS = {
     "sort.cu": [],
     "poisson.cu": [],
     "coulomb.cu": ["--fmad=false"],
+    "coulomb_mixed.cu": [],
     "diagnostics.cu": ["--fmad=false"],
 }
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

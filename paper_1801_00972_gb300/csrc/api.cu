@@ -512,7 +512,9 @@ pic_status init_run(const pic_mesh* mesh, const pic_electrodes* el, const pic_ga
             c->cs_idx[sp] = (unsigned int*)dev_alloc(c, sizeof(unsigned int) * (size_t)std::max<int64_t>(c->cap[sp], 1));
             c->cs_key[sp] =
                 (unsigned long long*)dev_alloc(c, sizeof(unsigned long long) * (size_t)std::max<int64_t>(c->cap[sp], 1));
-            ok = ok && c->cs_end[sp] && c->cs_idx[sp] && c->cs_key[sp];
+            c->cs_cell[sp] = (unsigned int*)dev_alloc(c, sizeof(unsigned int) * (size_t)std::max<int64_t>(c->cap[sp], 1));
+            c->cs_ord[sp] = (unsigned int*)dev_alloc(c, sizeof(unsigned int) * (size_t)std::max<int64_t>(c->cap[sp], 1));
+            ok = ok && c->cs_end[sp] && c->cs_idx[sp] && c->cs_key[sp] && c->cs_cell[sp] && c->cs_ord[sp];
         }
     if (c->eepf_bins > 0) {
         c->eepf = (unsigned long long*)dev_alloc(c, sizeof(unsigned long long) * (size_t)nz * (c->eepf_bins + 1));

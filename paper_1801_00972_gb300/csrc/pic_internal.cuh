@@ -210,6 +210,8 @@ struct pic_ctx {
     unsigned int* cs_end[2] = {nullptr, nullptr};        // cells: end of each cell's group
     unsigned int* cs_idx[2] = {nullptr, nullptr};        // capacity: slots grouped by cell
     unsigned long long* cs_key[2] = {nullptr, nullptr};  // capacity: pairing keys
+    unsigned int* cs_cell[2] = {nullptr, nullptr};       // capacity: cell of each grouped slot
+    unsigned int* cs_ord[2] = {nullptr, nullptr};        // capacity: slots grouped by cell, in key order
 
     // electron energy histogram (eepf_bins > 0): [k][bin], bins of eepf_de eV plus overflow
     unsigned long long* eepf = nullptr;
@@ -331,6 +333,8 @@ void launch_oml(pic_ctx* c, int with_cx, double* out);   // 6 values per grain f
 
 // coulomb.cu (built without fused multiply-add)
 void launch_coulomb(pic_ctx* c);                    // binary Coulomb collisions of the step's particles
+void launch_coulomb_fp64(pic_ctx* c);               // (its FP64 unit, built without fused multiply-add)
+void launch_coulomb_mixed(pic_ctx* c);              // (its float unit)
 size_t sort_scratch_setup(pic_ctx* c);
 
 // poisson.cu
