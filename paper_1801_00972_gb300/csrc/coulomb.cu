@@ -30,6 +30,7 @@
 // the oracle's operation for operation, so an FP64 run matches it bit for
 // bit.  The mixed unit works in float, in the particles' cells/step units.
 #include "pic_internal.cuh"
+#include <algorithm>
 
 namespace pic {
 namespace {
@@ -260,31 +261,6 @@ __device__ __forceinline__ float density(const CoulArgs& a, unsigned int n, floa
     return (float)n * a.wv32;
 }
 
-__device__ __forceinline__ uint32_t load_v(const CoulArgs& a, int sp, unsigned int q, double v[3])
-{
-    const double4 x = reinterpret_cast<const double4*>(sp == 0 ? a.vel[0] : a.vel[1])[q];
-    v[0] = x.x; v[1] = x.y; v[2] = x.z;
-    return (uint32_t)x.w;
-}
-__device__ __forceinline__ void store_v(const CoulArgs& a, int sp, unsigned int q, const double v[3])
-{
-    double4* p = reinterpret_cast<double4*>(sp == 0 ? a.vel[0] : a.vel[1]) + q;
-    const double w = p->w;
-    *p = make_double4(v[0], v[1], v[2], w);
-}
-__device__ __forceinline__ uint32_t load_v(const CoulArgs& a, int sp, unsigned int q, float v[3])
-{
-    const float4 x = reinterpret_cast<const float4*>(sp == 0 ? a.vel[0] : a.vel[1])[q];
-    v[0] = x.x; v[1] = x.y; v[2] = x.z;
-    return __float_as_uint(x.w);
-}
-__device__ __forceinline__ void store_v(const CoulArgs& a, int sp, unsigned int q, const float v[3])
-{
-    float4* p = reinterpret_cast<float4*>(sp == 0 ? a.vel[0] : a.vel[1]) + q;
-    const float w = p->w;
-    *p = make_float4(v[0], v[1], v[2], w);
-}
-
 // entries of the parameter tables by selects (an indexed read would copy the
 // kernel parameter to local memory)
 template <typename X>
@@ -299,28 +275,36 @@ __device__ __forceinline__ X pick(const X (&v)[3], int k)
 }
 
 // one collision of slot qa (species sa, the pair's first particle) with slot qb
-// (species sb); kind 0 e-e, 1 i-i, 2 e-i
+// (species sb); kind 0 e-e, 1 i-i, 2 e-i.  Whole records are read and written
+// back; their fourth word (the id) passes through.
 __device__ __forceinline__ void collide(const CoulArgs& a, int sa, unsigned int qa, int sb, unsigned int qb,
                                         int kind, double dens, bool half, uint32_t step, uint32_t purpose, double*)
 {
-    double va[3], vb[3];
-    const uint32_t ida = load_v(a, sa, qa, va);
-    load_v(a, sb, qb, vb);
+    double4* pa = reinterpret_cast<double4*>(sa == 0 ? a.vel[0] : a.vel[1]) + qa;
+    double4* pb = reinterpret_cast<double4*>(sb == 0 ? a.vel[0] : a.vel[1]) + qb;
+    double4 A = *pa, B = *pb;
+    double va[3] = {A.x, A.y, A.z}, vb[3] = {B.x, B.y, B.z};
     const double dt = half ? 0.5 * a.dt : a.dt;
-    coul_pair64(va, vb, pick(a.fac, sa, sb), pick(a.fac, sb, sa), pick(a.cf, kind), dens, dt, ida, step, purpose, a.pkey);
-    store_v(a, sa, qa, va);
-    store_v(a, sb, qb, vb);
+    coul_pair64(va, vb, pick(a.fac, sa, sb), pick(a.fac, sb, sa), pick(a.cf, kind), dens, dt, coul_id(A), step,
+                purpose, a.pkey);
+    A.x = va[0]; A.y = va[1]; A.z = va[2];
+    B.x = vb[0]; B.y = vb[1]; B.z = vb[2];
+    *pa = A;
+    *pb = B;
 }
 __device__ __forceinline__ void collide(const CoulArgs& a, int sa, unsigned int qa, int sb, unsigned int qb,
                                         int kind, float dens, bool half, uint32_t step, uint32_t purpose, float*)
 {
-    float va[3], vb[3];
-    const uint32_t ida = load_v(a, sa, qa, va);
-    load_v(a, sb, qb, vb);
-    coul_pair32(va, vb, pick(a.fac32, sa, sb), pick(a.fac32, sb, sa), pick(a.cf32, kind), dens, half ? 0.5f : 1.f, ida, step,
-                purpose, a.pkey);
-    store_v(a, sa, qa, va);
-    store_v(a, sb, qb, vb);
+    float4* pa = reinterpret_cast<float4*>(sa == 0 ? a.vel[0] : a.vel[1]) + qa;
+    float4* pb = reinterpret_cast<float4*>(sb == 0 ? a.vel[0] : a.vel[1]) + qb;
+    float4 A = *pa, B = *pb;
+    float va[3] = {A.x, A.y, A.z}, vb[3] = {B.x, B.y, B.z};
+    coul_pair32(va, vb, pick(a.fac32, sa, sb), pick(a.fac32, sb, sa), pick(a.cf32, kind), dens, half ? 0.5f : 1.f,
+                coul_id(A), step, purpose, a.pkey);
+    A.x = va[0]; A.y = va[1]; A.z = va[2];
+    B.x = vb[0]; B.y = vb[1]; B.z = vb[2];
+    *pa = A;
+    *pb = B;
 }
 
 struct CoulGroups {
@@ -587,10 +571,13 @@ void PIC_COUL_LAUNCH(pic_ctx* c)
     }
     g.cells = (unsigned int)nc;
     const int grid = grid_for(c->cap[0] + c->cap[1], 256, 152 * 16);
+    // the collision kernels: one resident wave, so that each warp's queue runs
+    // many full rounds before its last, partial ones
+    const int gridc = std::min(grid, 152 * PIC_COUL_MINB);
     k_coul_rank<<<grid, 256, 0, c->stream>>>(g, c->cs_key[0], c->cs_key[1], c->cs_idx[0], c->cs_idx[1],
                                              c->cs_ord[0], c->cs_ord[1]);
-    k_coul_like<CT><<<grid, 256, 0, c->stream>>>(a, g, c->cs_ord[0], c->cs_ord[1]);
-    k_coul_unlike<CT><<<grid, 256, 0, c->stream>>>(a, g, c->cs_ord[0], c->cs_ord[1]);
+    k_coul_like<CT><<<gridc, 256, 0, c->stream>>>(a, g, c->cs_ord[0], c->cs_ord[1]);
+    k_coul_unlike<CT><<<gridc, 256, 0, c->stream>>>(a, g, c->cs_ord[0], c->cs_ord[1]);
     c->launches += 3;
 }
 
