@@ -68,6 +68,7 @@ def args():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", type=int, default=4, help="headline workload (inputs.workload index)")
+    ap.add_argument("--no-f64-residual", action="store_true", help="skip the FP64-residual solve leg")
     ap.add_argument("--fp64-steps", type=int, default=6)
     ap.add_argument("--e2e-steps", type=int, default=100)
     ap.add_argument("--no-fp64", action="store_true")
@@ -429,6 +430,12 @@ def main():
     if not a.no_fp64:
         fp64 = run_gpu(P, I, wl, None, P.PIC_FP64, a.fp64_steps, min(a.warmup, 3), stream, local, flags,
                        tune=False, sort_every=mixed["sort_every"])
+    # the same solve with the refinement residual in FP64 arithmetic instead of
+    # double-float (PIC_F_F64_RESIDUAL), for the cost of that choice
+    f64r = None
+    if not a.no_f64_residual and world == 1:
+        f64r = run_gpu(P, I, wl, None, P.PIC_MIXED, a.fp64_steps, min(a.warmup, 3), stream, local,
+                       flags | P.PIC_F_F64_RESIDUAL, tune=False, tuning=mixed["tuning"])
     ee = None
     if not a.no_e2e and world == 1:
         ee = e2e(P, I, wl, P.PIC_MIXED, a.e2e_steps, stream, mixed["sort_every"])
@@ -512,6 +519,13 @@ def main():
                         "push_achieved_gbs": fach, "push_frac": fach / peak,
                         "poisson": poisson_block(fp, fp64["cold"], wl, BYTES_NODE_FP64, peak, peak_kind, "fp64"),
                         "mixed_speedup": (m_tot / m_ms) / (f[1] / f[0])}
+    if f64r is not None:
+        pb = poisson_block(f64r["prof"], f64r["cold"], wl, BYTES_NODE_MIXED, peak, peak_kind, "mixed")
+        line["poisson"]["f64_residual"] = {
+            "ms_per_solve": pb["ms_per_solve"], "iterations_per_solve": pb["iterations_per_solve"],
+            "cold": pb["cold"], "steps": a.fp64_steps,
+            "note": "the same mixed solve with the refinement residual in FP64 arithmetic (PIC_F_F64_RESIDUAL) "
+                    "instead of double-float sums"}
     if ee is not None:
         line["e2e"] = ee
     line.update(extra)

@@ -71,6 +71,11 @@ typedef enum { PIC_FP64 = 0, PIC_MIXED = 1 } pic_precision;
 #define PIC_F_NO_GRAPH   16   /* pic_step launches kernels one by one and runs the
                                  Poisson loop from the host (for profilers that
                                  cannot see inside CUDA graphs); same results */
+#define PIC_F_F64_RESIDUAL 64 /* mixed precision only: the refinement residual of the
+                                 Poisson solve in FP64 arithmetic instead of the
+                                 double-float (two-float) arithmetic; the potential is
+                                 still stored as two floats.  For measurement: same
+                                 convergence, slower on this GPU's FP64 units */
 
 /* Mesh: nx*ny*nz cubic cells of edge dx.  Phi and rho live on the cell corners
  * (Sec. III): nx*ny*(nz+1) nodes indexed (k*ny + j)*nx + i; x and y periodic,

@@ -25,7 +25,7 @@ PIC_OK, PIC_EINVAL, PIC_ENOMEM, PIC_ECUDA, PIC_ECAPACITY, PIC_ENONFINITE, PIC_EN
 STATUS = {0: "PIC_OK", 1: "PIC_EINVAL", 2: "PIC_ENOMEM", 3: "PIC_ECUDA", 4: "PIC_ECAPACITY",
           5: "PIC_ENONFINITE", 6: "PIC_ENOTCONV", 7: "PIC_ETIMEOUT"}
 PIC_FP64, PIC_MIXED = 0, 1
-PIC_F_NO_MCC, PIC_F_IONS_FROZEN, PIC_F_MOMENTS, PIC_F_NO_GRAPH, PIC_F_COULOMB = 1, 2, 8, 16, 32
+PIC_F_NO_MCC, PIC_F_IONS_FROZEN, PIC_F_MOMENTS, PIC_F_NO_GRAPH, PIC_F_COULOMB, PIC_F_F64_RESIDUAL = 1, 2, 8, 16, 32, 64
 COUNTERS = ("lost_bot_e", "lost_bot_i", "lost_top_e", "lost_top_i", "abs_e", "abs_i",
             "e_el", "e_exc", "e_ion", "i_el", "i_cx", "err", "pushed")
 PIC_C_N = len(COUNTERS)

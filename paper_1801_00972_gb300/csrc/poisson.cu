@@ -1758,6 +1758,9 @@ struct ResDf {
 // other buffer), R = h^2 f - (6 phi' - sum of the 6 neighbours of phi') with
 // the large parts summed exactly, ||R||^2 over the grid, and in the last block
 // the loop decision of the solve (the same rule as the FP64 solver's).
+// kF64: the same step with the residual formed in FP64 arithmetic from the
+// two-float values (the measured alternative to the double-float sums)
+template <bool kF64>
 __global__ void __launch_bounds__(256) k_resid_df(ResDf a, Dims d)
 {
     pdl_begin();
@@ -1781,6 +1784,22 @@ __global__ void __launch_bounds__(256) k_resid_df(ResDf a, Dims d)
             const int nb[6] = {row + ip, row + im, n + jp, n + jm, n + P, n - P};
             const float2 pc = cur[n];
             const float ec = a.e ? a.e[n] : 0.f;
+            if (kF64) {
+                const double pd = ((double)pc.x + (double)pc.y) + (double)ec;
+                double lap = 6.0 * pd;
+#pragma unroll
+                for (int q = 0; q < 6; ++q) {
+                    const float2 p = cur[nb[q]];
+                    const float eq = a.e ? a.e[nb[q]] : 0.f;
+                    lap -= ((double)p.x + (double)p.y) + (double)eq;
+                }
+                const float2 F = a.F[n];
+                const float R = (float)(((double)F.x + (double)F.y) - lap);
+                if (a.e) nxt[n] = df_of(pd);
+                a.r[n] = R * a.inv_h2;
+                acc += R * R;
+                continue;
+            }
             // 6 phi'_n - sum phi'_nb: hi parts exactly (s + err), the small parts in float
             float s = 6.f * pc.x;
             float err = fmaf(6.f, pc.x, -s);
@@ -1892,7 +1911,8 @@ void launch_resid_df(pic_ctx* c, double tol, int max_iters, const float* e, bool
     a.use_cond = graph ? 1 : 0;
     a.h = h;
     const Grid3 g = grid_norm(d.nx, d.ny, d.nz - 1);
-    launch_pdl(c->stream, g.grid, g.block, k_resid_df, a, d);
+    if (c->flags & PIC_F_F64_RESIDUAL) launch_pdl(c->stream, g.grid, g.block, k_resid_df<true>, a, d);
+    else launch_pdl(c->stream, g.grid, g.block, k_resid_df<false>, a, d);
     c->launches += 1;
 }
 

@@ -518,3 +518,27 @@ def test_diagnostics_of_an_empty_plasma(prec):
     # phi still follows the electrodes
     pg, po = run.moments(0), ref.moments(0)
     assert np.max(np.abs(pg - po)) <= 1e-6 * np.max(np.abs(po))
+
+
+def test_mixed_f64_residual_variant_converges_to_the_same_potential():
+    """PIC_F_F64_RESIDUAL forms the refinement residual in FP64 arithmetic: the
+    same charge density, the same converged potential to the solver tolerance,
+    the same iteration count within one."""
+    wl = I.small(nx=16, ny=16, nz=32, n_e=20000, n_i=20000, grains=2, v_dc=-50.0)
+    parts = I.sample_particles(wl)
+    a = P.Run(wl, parts, prec=P.PIC_MIXED, stream=_stream())
+    b = P.Run(wl, parts, prec=P.PIC_MIXED, flags=P.PIC_F_F64_RESIDUAL, stream=_stream())
+    assert np.array_equal(a.rho(), b.rho())
+    pa, pb = a.phi(), b.phi()
+    scale = max(1.0, np.max(np.abs(pa)))
+    assert np.max(np.abs(pa - pb)) <= 1e-8 * scale
+    zero = np.zeros_like(pa)
+    for r in (a, b):
+        r.set_phi(zero)
+    ia, ra = a.solve()
+    ib, rb = b.solve()
+    assert ra <= 1e-10 and rb <= 1e-10
+    assert abs(ia - ib) <= 1
+    assert np.max(np.abs(a.phi() - b.phi())) <= 1e-8 * scale
+    a.close()
+    b.close()
