@@ -1758,10 +1758,21 @@ struct ResDf {
 // other buffer), R = h^2 f - (6 phi' - sum of the 6 neighbours of phi') with
 // the large parts summed exactly, ||R||^2 over the grid, and in the last block
 // the loop decision of the solve (the same rule as the FP64 solver's).
+// the refinement step: planes per block (a 32 x 8 column tile of them) and
+// resident blocks per SM it is built for
+constexpr int kResidPlanes = 16;
+constexpr int kResidBlocks = 4;
+
+// the potential (hi + lo) and the V-cycle correction at one node
+struct PhiE {
+    float2 p;
+    float e;
+};
+
 // kF64: the same step with the residual formed in FP64 arithmetic from the
 // two-float values (the measured alternative to the double-float sums)
 template <bool kF64>
-__global__ void __launch_bounds__(256) k_resid_df(ResDf a, Dims d)
+__global__ void __launch_bounds__(256, kResidBlocks) k_resid_df(ResDf a, Dims d)
 {
     pdl_begin();
     __shared__ int s_sel;
@@ -1772,55 +1783,75 @@ __global__ void __launch_bounds__(256) k_resid_df(ResDf a, Dims d)
     float2* nxt = a.phi + (s_sel ? 0 : N);
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    const int k0 = 1 + (int)blockIdx.z * kResidPlanes;
+    const int k1 = min(k0 + kResidPlanes, d.nz);
     float acc = 0.f;
-    if (i < d.nx && j < d.ny) {
+    if (i < d.nx && j < d.ny && k0 < k1) {
         const int P = d.nx * d.ny;
-        const int ip = (i + 1 == d.nx) ? 0 : i + 1, im = (i == 0) ? d.nx - 1 : i - 1;
-        const int jp = (j + 1 == d.ny) ? -j * d.nx : d.nx, jm = (j == 0) ? (d.ny - 1) * d.nx : -d.nx;
-#pragma unroll 2
-        for (int k = 1 + blockIdx.z; k < d.nz; k += gridDim.z) {
-            const int n = k * P + j * d.nx + i;
-            const int row = n - i;
-            const int nb[6] = {row + ip, row + im, n + jp, n + jm, n + P, n - P};
-            const float2 pc = cur[n];
-            const float ec = a.e ? a.e[n] : 0.f;
+        const int off[4] = {(i + 1 == d.nx) ? 1 - d.nx : 1, (i == 0) ? d.nx - 1 : -1,
+                            (j + 1 == d.ny) ? -j * d.nx : d.nx, (j == 0) ? (d.ny - 1) * d.nx : -d.nx};
+        // The potential, correction and f are only read here (the new potential
+        // goes to the other buffer), so the loads take the read-only path.
+        auto ld = [&](int n) {
+            PhiE v;
+            v.p = __ldg(cur + n);
+            v.e = a.e ? __ldg(a.e + n) : 0.f;
+            return v;
+        };
+        // This thread's column, plane after plane: the values at k - 1, k and
+        // k + 1 roll through registers, and the loads for plane k + 1 (its
+        // in-plane neighbours and f, the column at k + 2) are issued before
+        // plane k is computed.
+        int n = (k0 * d.ny + j) * d.nx + i;
+        PhiE zm = ld(n - P), zc = ld(n), zp = ld(n + P);
+        PhiE X[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) X[q] = ld(n + off[q]);
+        float2 F = __ldg(a.F + n);
+        for (int k = k0; k < k1; ++k, n += P) {
+            PhiE Xn[4], zn = zp;
+            float2 Fn = F;
+            if (k + 1 < k1) {
+                zn = ld(n + 2 * P);
+#pragma unroll
+                for (int q = 0; q < 4; ++q) Xn[q] = ld(n + P + off[q]);
+                Fn = __ldg(a.F + n + P);
+            }
+            const PhiE nbv[6] = {X[0], X[1], X[2], X[3], zp, zm};
+            float R;
             if (kF64) {
-                const double pd = ((double)pc.x + (double)pc.y) + (double)ec;
+                const double pd = ((double)zc.p.x + (double)zc.p.y) + (double)zc.e;
                 double lap = 6.0 * pd;
 #pragma unroll
-                for (int q = 0; q < 6; ++q) {
-                    const float2 p = cur[nb[q]];
-                    const float eq = a.e ? a.e[nb[q]] : 0.f;
-                    lap -= ((double)p.x + (double)p.y) + (double)eq;
-                }
-                const float2 F = a.F[n];
-                const float R = (float)(((double)F.x + (double)F.y) - lap);
+                for (int q = 0; q < 6; ++q) lap -= ((double)nbv[q].p.x + (double)nbv[q].p.y) + (double)nbv[q].e;
+                R = (float)(((double)F.x + (double)F.y) - lap);
                 if (a.e) nxt[n] = df_of(pd);
-                a.r[n] = R * a.inv_h2;
-                acc += R * R;
-                continue;
-            }
-            // 6 phi'_n - sum phi'_nb: hi parts exactly (s + err), the small parts in float
-            float s = 6.f * pc.x;
-            float err = fmaf(6.f, pc.x, -s);
-            float small = 6.f * (pc.y + ec);
+            } else {
+                // 6 phi'_n - sum phi'_nb: hi parts exactly (s + err), the small parts in float
+                float sh = 6.f * zc.p.x;
+                float err = fmaf(6.f, zc.p.x, -sh);
+                float small = 6.f * (zc.p.y + zc.e);
 #pragma unroll
-            for (int q = 0; q < 6; ++q) {
-                const float2 p = cur[nb[q]];
-                const float eq = a.e ? a.e[nb[q]] : 0.f;
-                float s2, t;
-                two_sum(s, -p.x, s2, t);
-                s = s2;
-                err += t;
-                small -= p.y + eq;
+                for (int q = 0; q < 6; ++q) {
+                    float s2, t;
+                    two_sum(sh, -nbv[q].p.x, s2, t);
+                    sh = s2;
+                    err += t;
+                    small -= nbv[q].p.y + nbv[q].e;
+                }
+                float r1, t1;
+                two_sum(F.x, -sh, r1, t1);
+                R = r1 + ((t1 + F.y) - (err + small));
+                if (a.e) nxt[n] = df_add_f(zc.p, zc.e);
             }
-            const float2 F = a.F[n];
-            float r1, t1;
-            two_sum(F.x, -s, r1, t1);
-            const float R = r1 + ((t1 + F.y) - (err + small));
-            if (a.e) nxt[n] = df_add_f(pc, ec);
             a.r[n] = R * a.inv_h2;
             acc += R * R;
+            zm = zc;
+            zc = zp;
+            zp = zn;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) X[q] = Xn[q];
+            F = Fn;
         }
     }
     float r2;
@@ -1910,7 +1941,8 @@ void launch_resid_df(pic_ctx* c, double tol, int max_iters, const float* e, bool
     a.first = first ? 1 : 0;
     a.use_cond = graph ? 1 : 0;
     a.h = h;
-    const Grid3 g = grid_norm(d.nx, d.ny, d.nz - 1);
+    Grid3 g = grid3(d.nx, d.ny, 1);
+    g.grid.z = (unsigned)std::max(1, (d.nz - 1 + kResidPlanes - 1) / kResidPlanes);
     if (c->flags & PIC_F_F64_RESIDUAL) launch_pdl(c->stream, g.grid, g.block, k_resid_df<true>, a, d);
     else launch_pdl(c->stream, g.grid, g.block, k_resid_df<false>, a, d);
     c->launches += 1;
