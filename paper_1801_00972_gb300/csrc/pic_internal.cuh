@@ -136,6 +136,7 @@ struct MGLevel {
     void* u = nullptr;   // T[nodes]
     void* f = nullptr;
     void* r = nullptr;
+    int half = 0;        // > 0: u and f split by colour, node n of colour c at c * half + n / 2
 };
 
 }  // namespace pic

@@ -61,7 +61,18 @@ constexpr int kPost = PIC_MG_POST;       // post-smoothing sweeps
 
 struct Dims {
     int nx, ny, nz;
+    int half = 0;   // > 0: the level's u and f are split by colour (red-black layout)
 };
+
+// Red-black layout of a level (nx even): the red nodes (i + j + k even) in
+// the first half of the array, the black in the second, node n at n / 2 of
+// its half (n and n + 1 of a row pair always differ in colour).  A half-sweep
+// then reads one colour's half of u and f and the other colour's half of u,
+// instead of every line of both.  half == 0: natural order.
+__device__ __forceinline__ int lix(const Dims& d, int n, int colour)
+{
+    return d.half ? (colour ? d.half : 0) + (n >> 1) : n;
+}
 
 __device__ __forceinline__ size_t nid(const Dims& d, int i, int j, int k)
 {
@@ -150,6 +161,51 @@ __global__ void k_rbgs(T* __restrict__ u, const T* __restrict__ f, Dims d, T h2,
     u[n] = (s + h2 * f[n]) * (T)(1.0 / 6.0);
 }
 
+// The same half-sweep on a red-black split level (d.half > 0), by columns of
+// node pairs.  Pair m = k * P/2 + j * nx/2 + i2 holds nodes 2 i2 and 2 i2 + 1
+// of row (j, k), one of each colour, at m in the red half and m in the black
+// half.  Every neighbour of the updated node (offset p = (j + k + colour) & 1
+// in its pair) is of the other colour: in the same pair (x on one side), the
+// pair next to it (x on the other side), pairs m -+ nx/2 (y) and m -+ P/2
+// (z).  A thread walks its column up kRbPlanes planes; the other colour's
+// column values at k - 1, k, k + 1 roll through registers and the one at
+// k + 2 is loaded a plane ahead.  Each node's sum is k_rbgs's, term by term.
+constexpr int kRbPlanes = 16;
+
+template <typename T>
+__global__ void k_rbgs_split(T* __restrict__ u, const T* __restrict__ f, Dims d, T h2, int color, int zero)
+{
+    pdl_begin();
+    const int hx = d.nx >> 1, P2 = hx * d.ny;
+    const int i2 = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    const int k0 = 1 + (int)blockIdx.z * kRbPlanes;
+    const int k1 = min(k0 + kRbPlanes, d.nz);
+    if (i2 >= hx || j >= d.ny || k0 >= k1) return;
+    T* uc = u + (color ? d.half : 0);               // the colour being updated
+    const T* fc = f + (color ? d.half : 0);
+    const T* uo = u + (color ? 0 : d.half);         // the other colour
+    int m = k0 * P2 + j * hx + i2;
+    if (zero) {   // first sweep from a zero guess: the neighbours are still zero
+        for (int k = k0; k < k1; ++k, m += P2) uc[m] = (h2 * fc[m]) * (T)(1.0 / 6.0);
+        return;
+    }
+    const int dxp = (i2 + 1 == hx) ? 1 - hx : 1, dxm = (i2 == 0) ? hx - 1 : -1;
+    const int dyp = (j + 1 == d.ny) ? -j * hx : hx, dym = (j == 0) ? (d.ny - 1) * hx : -hx;
+    T om = uo[m - P2], oc = uo[m], op = uo[m + P2];
+    for (int k = k0; k < k1; ++k, m += P2) {
+        const T on = (k + 1 < k1) ? uo[m + 2 * P2] : op;
+        const int p = (j + k + color) & 1;
+        const T ox = uo[m + (p ? dxp : dxm)];
+        const T xp = p ? ox : oc, xm = p ? oc : ox;
+        const T s = xp + xm + uo[m + dyp] + uo[m + dym] + op + om;
+        uc[m] = (s + h2 * fc[m]) * (T)(1.0 / 6.0);
+        om = oc;
+        oc = op;
+        op = on;
+    }
+}
+
 // r = f - A u on the interior planes (the electrode planes of r stay zero)
 template <typename T>
 __global__ void k_resid(const T* __restrict__ u, const T* __restrict__ f, T* __restrict__ r, Dims d, T inv_h2)
@@ -207,8 +263,10 @@ __device__ __forceinline__ T res_at(const T* __restrict__ u, const T* __restrict
     const int ip = (i + 1 == d.nx) ? 0 : i + 1, im = (i == 0) ? d.nx - 1 : i - 1;
     const int jp = (j + 1 == d.ny) ? 0 : j + 1, jm = (j == 0) ? d.ny - 1 : j - 1;
     const int row = k * P + j * d.nx, n = row + i;
-    const T s = u[row + ip] + u[row + im] + u[k * P + jp * d.nx + i] + u[k * P + jm * d.nx + i] + u[n + P] + u[n - P];
-    return f[n] - ((T)6 * u[n] - s) * inv_h2;
+    const int c = (i + j + k) & 1, oc = c ^ 1;
+    const T s = u[lix(d, row + ip, oc)] + u[lix(d, row + im, oc)] + u[lix(d, k * P + jp * d.nx + i, oc)] +
+                u[lix(d, k * P + jm * d.nx + i, oc)] + u[lix(d, n + P, oc)] + u[lix(d, n - P, oc)];
+    return f[lix(d, n, c)] - ((T)6 * u[lix(d, n, c)] - s) * inv_h2;
 }
 
 // Full-weighting restriction of the residual f - A u, computed on the fly.
@@ -260,7 +318,7 @@ __global__ void k_prolong(T* __restrict__ uf, const T* __restrict__ uc, Dims df,
     // a coincident axis repeats its node, so the 1/8 weights give 1/2 or 1 per axis
     const T v = (T)0.125 * (a0[J0 * dc.nx + I0] + a0[J0 * dc.nx + I1] + a0[J1 * dc.nx + I0] + a0[J1 * dc.nx + I1] +
                             a1[J0 * dc.nx + I0] + a1[J0 * dc.nx + I1] + a1[J1 * dc.nx + I0] + a1[J1 * dc.nx + I1]);
-    uf[k * df.nx * df.ny + j * df.nx + i] += v;
+    uf[lix(df, k * df.nx * df.ny + j * df.nx + i, (i + j + k) & 1)] += v;
 }
 
 // ---- fused smoothing of a large grid-wide level ("2.5-D" blocking) ----------
@@ -449,7 +507,7 @@ __global__ void k_prolong_cell(T* __restrict__ uf, const T* __restrict__ uc, Dim
                 const T p00 = z0[0], p01 = z0[bx ? 1 : 0], p10 = z0[by ? 2 : 0], p11 = z0[(by ? 2 : 0) + (bx ? 1 : 0)];
                 const T q00 = z1[0], q01 = z1[bx ? 1 : 0], q10 = z1[by ? 2 : 0], q11 = z1[(by ? 2 : 0) + (bx ? 1 : 0)];
                 const T v = (T)0.125 * (p00 + p01 + p10 + p11 + q00 + q01 + q10 + q11);
-                uf[k * P + j * df.nx + i] += v;
+                uf[lix(df, k * P + j * df.nx + i, (i + j + k) & 1)] += v;
             }
         }
     }
@@ -516,19 +574,20 @@ __global__ void k_resid64(const double* __restrict__ phi, const T* __restrict__ 
             const int n = k * P + j * d.nx + i;
             const int row = n - i;
             const int nb[6] = {row + ip, row + im, n + jp, n + jm, n + P, n - P};
+            const int col = (i + j + k) & 1;
             double c = phi[n];
             double s = 0.0;
             if (e) {
-                c += (double)e[n];
+                c += (double)e[lix(d, n, col)];
 #pragma unroll
-                for (int q = 0; q < 6; ++q) s += phi[nb[q]] + (double)e[nb[q]];
+                for (int q = 0; q < 6; ++q) s += phi[nb[q]] + (double)e[lix(d, nb[q], col ^ 1)];
             } else {
 #pragma unroll
                 for (int q = 0; q < 6; ++q) s += phi[nb[q]];
             }
             if (phi_out) phi_out[n] = c;
             const double res = f[n] - (6.0 * c - s) * inv_h2;
-            r[n] = (T)res;
+            r[lix(d, n, col)] = (T)res;
             acc += res * res;
         }
     }
@@ -590,8 +649,9 @@ __global__ void k_add(double* __restrict__ phi, const T* __restrict__ e, Dims d)
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y * blockDim.y + threadIdx.y;
     if (i >= d.nx || j >= d.ny) return;
-    const int n = ((1 + blockIdx.z) * d.ny + j) * d.nx + i;
-    phi[n] += (double)e[n];
+    const int k = 1 + (int)blockIdx.z;
+    const int n = (k * d.ny + j) * d.nx + i;
+    phi[n] += (double)e[lix(d, n, (i + j + k) & 1)];
 }
 
 // electrode values at t = step * dt from the device step counter
@@ -1360,6 +1420,12 @@ inline Grid3 grid_norm(int nx, int ny, int planes)
 template <typename T>
 void run_rbgs(cudaStream_t s, T* u, const T* f, Dims d, T h2, int color, int zero)
 {
+    if (d.half) {
+        Grid3 g = grid3(d.nx / 2, d.ny, 1);
+        g.grid.z = (unsigned)std::max(1, (d.nz - 1 + kRbPlanes - 1) / kRbPlanes);
+        launch_pdl(s, g.grid, g.block, k_rbgs_split<T>, u, f, d, h2, color, zero);
+        return;
+    }
     const Grid3 g = grid3(d.nx / 2, d.ny, d.nz - 1);
     launch_pdl(s, g.grid, g.block, k_rbgs<T>, u, f, d, h2, color, zero);
 }
@@ -1420,7 +1486,7 @@ int fused_planes(const pic_ctx* c, int l)
 {
     if (!PIC_MG_FUSED || kPre != 2 || kPost != 2 || l + 1 >= (int)c->mg.size()) return 0;
     const MGLevel& L = c->mg[l];
-    if (L.nx % kSmTX || L.ny % kSmTY || L.nz < 8) return 0;
+    if (L.half || L.nx % kSmTX || L.ny % kSmTY || L.nz < 8) return 0;
     const long long cols = (long long)(L.nx / kSmTX) * (L.ny / kSmTY);
     const long long want = 2LL * 2 * 152;
     int tz = 64;
@@ -1454,7 +1520,7 @@ T* vcycle(pic_ctx* c, int l)
         return (T*)c->mg[l].u;
     }
     MGLevel& L = c->mg[l];
-    const Dims d{L.nx, L.ny, L.nz};
+    const Dims d{L.nx, L.ny, L.nz, L.half};
     const T h2 = (T)(L.h * L.h);
     T* u = (T*)L.u;
     T* f = (T*)L.f;
@@ -1497,7 +1563,7 @@ T* vcycle(pic_ctx* c, int l)
 template <typename T>
 pic_status solve_t(pic_ctx* c, double tol, int max_iters, int* iters, double* res)
 {
-    const Dims d{c->nx, c->ny, c->nz};
+    const Dims d{c->nx, c->ny, c->nz, c->mg[0].half};   // mg[0].f receives the residual
     const double inv_h2 = 1.0 / (c->dx * c->dx);
     MGLevel& L0 = c->mg[0];
     double h_norm[2];
@@ -1540,7 +1606,7 @@ pic_status solve_t(pic_ctx* c, double tol, int max_iters, int* iters, double* re
 template <typename T>
 void enqueue_iteration(pic_ctx* c, double tol, int max_iters, cudaGraphConditionalHandle h)
 {
-    const Dims d{c->nx, c->ny, c->nz};
+    const Dims d{c->nx, c->ny, c->nz, c->mg[0].half};   // mg[0].f receives the residual
     const T* e = vcycle<T>(c, 0);
     const Grid3 g = grid3(d.nx, d.ny, d.nz - 1);
     k_add<T><<<g.grid, g.block, 0, c->stream>>>(c->phi, e, d);
@@ -1556,7 +1622,7 @@ void enqueue_iteration(pic_ctx* c, double tol, int max_iters, cudaGraphCondition
 template <typename T>
 void enqueue_head(pic_ctx* c, double tol, int max_iters, cudaGraphConditionalHandle h)
 {
-    const Dims d{c->nx, c->ny, c->nz};
+    const Dims d{c->nx, c->ny, c->nz, c->mg[0].half};   // mg[0].f receives the residual
     cudaMemsetAsync(c->d_norm, 0, 2 * sizeof(double), c->stream);
     const Grid3 g = grid_norm(d.nx, d.ny, d.nz + 1);
     k_rhs_dev<<<g.grid, g.block, 0, c->stream>>>(c->rq, c->f64, c->phi, d, c->sp, c->d_step, c->d_norm,
@@ -1769,8 +1835,72 @@ struct PhiE {
     float e;
 };
 
-// kF64: the same step with the residual formed in FP64 arithmetic from the
-// two-float values (the measured alternative to the double-float sums)
+// R = h^2 f - (6 phi'_n - sum of the 6 neighbours' phi') at one node, phi' =
+// phi + e, and phi'_n itself (to `out`); neighbours in the order x+, x-, y+,
+// y-, z+, z-.  kF64: the residual formed in FP64 arithmetic from the
+// two-float values (the measured alternative to the double-float sums).
+template <bool kF64>
+__device__ __forceinline__ float node_resid(const PhiE& c, const PhiE (&nb)[6], float2 F, float2& out)
+{
+    if (kF64) {
+        const double pd = ((double)c.p.x + (double)c.p.y) + (double)c.e;
+        double lap = 6.0 * pd;
+#pragma unroll
+        for (int q = 0; q < 6; ++q) lap -= ((double)nb[q].p.x + (double)nb[q].p.y) + (double)nb[q].e;
+        out = df_of(pd);
+        return (float)(((double)F.x + (double)F.y) - lap);
+    }
+    // 6 phi'_n - sum phi'_nb: hi parts exactly (s + err), the small parts in float
+    float sh = 6.f * c.p.x;
+    float err = fmaf(6.f, c.p.x, -sh);
+    float small = 6.f * (c.p.y + c.e);
+#pragma unroll
+    for (int q = 0; q < 6; ++q) {
+        float s2, t;
+        two_sum(sh, -nb[q].p.x, s2, t);
+        sh = s2;
+        err += t;
+        small -= nb[q].p.y + nb[q].e;
+    }
+    float r1, t1;
+    two_sum(F.x, -sh, r1, t1);
+    out = df_add_f(c.p, c.e);
+    return r1 + ((t1 + F.y) - (err + small));
+}
+
+// the end of a refinement step: ||R||^2 over the grid and, in the last block,
+// the loop decision of the solve (the same rule as the FP64 solver's)
+__device__ __forceinline__ void resid_df_tail(const ResDf& a, float acc, int sel)
+{
+    float r2;
+    if (!grid_sum_last(acc, a.part, &a.st->cnt_res, r2)) return;
+    if (tid_flat() != 0) return;
+    const float b2 = a.st->b2;
+    const float target2 = a.tol2 * (b2 > 0.f ? b2 : a.h4);
+    const unsigned int it = a.first ? 0u : *a.iters + 1u;
+    *a.iters = it;
+    if (!a.first) *a.total += 1ull;
+    const bool ok = r2 <= target2;
+    const bool finite = isfinite(r2);
+    const bool more = !ok && finite && (int)it < a.max_iters;
+    *a.res = b2 > 0.f ? sqrt((double)r2 / (double)b2) : sqrt((double)r2 / (double)a.h4);
+    const int status = ok ? (int)PIC_OK : finite ? (int)PIC_ENOTCONV : (int)PIC_ENONFINITE;
+    if (!more && !ok && a.flag) atomicCAS(a.flag, 0, status);
+    a.st->status = status;
+    a.st->more = more ? 1 : 0;
+    if (a.e) a.st->sel = sel ^ 1;
+    if (a.use_cond) cudaGraphSetConditional(a.h, more ? 1u : 0u);
+}
+
+// One refinement step over the interior nodes: phi' = phi + e (written to the
+// other buffer), R = h^2 f - (6 phi' - sum of the 6 neighbours of phi') with
+// the large parts summed exactly, ||R||^2 over the grid, and the loop decision.
+// Natural layout of e and r; thread (i, j) walks kResidPlanes planes of its
+// column: the values at k - 1, k and k + 1 roll through registers, and the
+// loads for plane k + 1 (its in-plane neighbours and f, the column at k + 2)
+// are issued before plane k is computed.  The potential, correction and f are
+// only read here (the new potential goes to the other buffer), so the loads
+// take the read-only path.
 template <bool kF64>
 __global__ void __launch_bounds__(256, kResidBlocks) k_resid_df(ResDf a, Dims d)
 {
@@ -1790,18 +1920,12 @@ __global__ void __launch_bounds__(256, kResidBlocks) k_resid_df(ResDf a, Dims d)
         const int P = d.nx * d.ny;
         const int off[4] = {(i + 1 == d.nx) ? 1 - d.nx : 1, (i == 0) ? d.nx - 1 : -1,
                             (j + 1 == d.ny) ? -j * d.nx : d.nx, (j == 0) ? (d.ny - 1) * d.nx : -d.nx};
-        // The potential, correction and f are only read here (the new potential
-        // goes to the other buffer), so the loads take the read-only path.
         auto ld = [&](int n) {
             PhiE v;
             v.p = __ldg(cur + n);
             v.e = a.e ? __ldg(a.e + n) : 0.f;
             return v;
         };
-        // This thread's column, plane after plane: the values at k - 1, k and
-        // k + 1 roll through registers, and the loads for plane k + 1 (its
-        // in-plane neighbours and f, the column at k + 2) are issued before
-        // plane k is computed.
         int n = (k0 * d.ny + j) * d.nx + i;
         PhiE zm = ld(n - P), zc = ld(n), zp = ld(n + P);
         PhiE X[4];
@@ -1818,32 +1942,9 @@ __global__ void __launch_bounds__(256, kResidBlocks) k_resid_df(ResDf a, Dims d)
                 Fn = __ldg(a.F + n + P);
             }
             const PhiE nbv[6] = {X[0], X[1], X[2], X[3], zp, zm};
-            float R;
-            if (kF64) {
-                const double pd = ((double)zc.p.x + (double)zc.p.y) + (double)zc.e;
-                double lap = 6.0 * pd;
-#pragma unroll
-                for (int q = 0; q < 6; ++q) lap -= ((double)nbv[q].p.x + (double)nbv[q].p.y) + (double)nbv[q].e;
-                R = (float)(((double)F.x + (double)F.y) - lap);
-                if (a.e) nxt[n] = df_of(pd);
-            } else {
-                // 6 phi'_n - sum phi'_nb: hi parts exactly (s + err), the small parts in float
-                float sh = 6.f * zc.p.x;
-                float err = fmaf(6.f, zc.p.x, -sh);
-                float small = 6.f * (zc.p.y + zc.e);
-#pragma unroll
-                for (int q = 0; q < 6; ++q) {
-                    float s2, t;
-                    two_sum(sh, -nbv[q].p.x, s2, t);
-                    sh = s2;
-                    err += t;
-                    small -= nbv[q].p.y + nbv[q].e;
-                }
-                float r1, t1;
-                two_sum(F.x, -sh, r1, t1);
-                R = r1 + ((t1 + F.y) - (err + small));
-                if (a.e) nxt[n] = df_add_f(zc.p, zc.e);
-            }
+            float2 upd;
+            const float R = node_resid<kF64>(zc, nbv, F, upd);
+            if (a.e) nxt[n] = upd;
             a.r[n] = R * a.inv_h2;
             acc += R * R;
             zm = zc;
@@ -1854,24 +1955,96 @@ __global__ void __launch_bounds__(256, kResidBlocks) k_resid_df(ResDf a, Dims d)
             F = Fn;
         }
     }
-    float r2;
-    if (!grid_sum_last(acc, a.part, &a.st->cnt_res, r2)) return;
-    if (tid_flat() != 0) return;
-    const float b2 = a.st->b2;
-    const float target2 = a.tol2 * (b2 > 0.f ? b2 : a.h4);
-    const unsigned int it = a.first ? 0u : *a.iters + 1u;
-    *a.iters = it;
-    if (!a.first) *a.total += 1ull;
-    const bool ok = r2 <= target2;
-    const bool finite = isfinite(r2);
-    const bool more = !ok && finite && (int)it < a.max_iters;
-    *a.res = b2 > 0.f ? sqrt((double)r2 / (double)b2) : sqrt((double)r2 / (double)a.h4);
-    const int status = ok ? (int)PIC_OK : finite ? (int)PIC_ENOTCONV : (int)PIC_ENONFINITE;
-    if (!more && !ok && a.flag) atomicCAS(a.flag, 0, status);
-    a.st->status = status;
-    a.st->more = more ? 1 : 0;
-    if (a.e) a.st->sel = s_sel ^ 1;
-    if (a.use_cond) cudaGraphSetConditional(a.h, more ? 1u : 0u);
+    resid_df_tail(a, acc, s_sel);
+}
+
+// The same step on a red-black split finest level (d.half > 0: e and r split
+// by colour, the potential and f in natural order), by columns of node pairs:
+// thread (i2, j) takes nodes 2 i2 and 2 i2 + 1 of each row (j, k) of its
+// kResidPlanes planes, their potential and f as one 16-byte load each, their
+// corrections at pair index m in the red and black halves.  Each node's
+// neighbours are those of k_resid_df, in its order; the pairs at k - 1, k and
+// k + 1 roll through registers, the one at k + 2 is loaded a plane ahead.
+struct PairPE {
+    float4 p;       // the two nodes' potentials (hi, lo, hi, lo)
+    float e0, e1;   // their corrections
+};
+
+template <bool kF64>
+__global__ void __launch_bounds__(256, kResidBlocks) k_resid_df_pairs(ResDf a, Dims d)
+{
+    pdl_begin();
+    __shared__ int s_sel;
+    if (tid_flat() == 0) s_sel = a.st->sel;
+    __syncthreads();
+    const size_t N = (size_t)d.nx * d.ny * (d.nz + 1);
+    const float2* cur = a.phi + (s_sel ? N : 0);
+    float2* nxt = a.phi + (s_sel ? 0 : N);
+    const int hx = d.nx >> 1, P2 = hx * d.ny, P = d.nx * d.ny;
+    const int i2 = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    const int k0 = 1 + (int)blockIdx.z * kResidPlanes;
+    const int k1 = min(k0 + kResidPlanes, d.nz);
+    float acc = 0.f;
+    if (i2 < hx && j < d.ny && k0 < k1) {
+        const float* eR = a.e;
+        const float* eB = a.e ? a.e + d.half : nullptr;
+        // the pair at natural node n (even) and pair index m; c0 = colour of its node 0
+        auto ldp = [&](int n, int m, int c0) {
+            PairPE v;
+            v.p = __ldg(reinterpret_cast<const float4*>(cur + n));
+            v.e0 = a.e ? __ldg((c0 ? eB : eR) + m) : 0.f;
+            v.e1 = a.e ? __ldg((c0 ? eR : eB) + m) : 0.f;
+            return v;
+        };
+        // one node (float2 at natural n, correction of colour col at pair m)
+        auto ld1 = [&](int n, int m, int col) {
+            PhiE v;
+            v.p = __ldg(cur + n);
+            v.e = a.e ? __ldg((col ? eB : eR) + m) : 0.f;
+            return v;
+        };
+        const int dxp = (i2 + 1 == hx) ? 1 - hx : 1, dxm = (i2 == 0) ? hx - 1 : -1;
+        const int dyp = (j + 1 == d.ny) ? -j * hx : hx, dym = (j == 0) ? (d.ny - 1) * hx : -hx;
+        int m = k0 * P2 + j * hx + i2;
+        int n = 2 * m;   // natural index of node 0 (nx even: n = k P + j nx + 2 i2)
+        int c0 = (j + k0) & 1;
+        PairPE zm = ldp(n - P, m - P2, c0 ^ 1), zc = ldp(n, m, c0), zp = ldp(n + P, m + P2, c0 ^ 1);
+        for (int k = k0; k < k1; ++k, m += P2, n += P, c0 ^= 1) {
+            PairPE zn = zp;
+            if (k + 1 < k1) zn = ldp(n + 2 * P, m + 2 * P2, c0);
+            const PairPE yp = ldp(n + 2 * dyp, m + dyp, c0 ^ 1), ym = ldp(n + 2 * dym, m + dym, c0 ^ 1);
+            // x- of node 0: node 1 of the pair on the left (colour c0 ^ 1); x+ of
+            // node 1: node 0 of the pair on the right (colour c0)
+            const PhiE xl = ld1(n + 2 * dxm + 1, m + dxm, c0 ^ 1), xr = ld1(n + 2 * dxp, m + dxp, c0);
+            const float4 F = __ldg(reinterpret_cast<const float4*>(a.F + n));
+            const PhiE n0{make_float2(zc.p.x, zc.p.y), zc.e0}, n1{make_float2(zc.p.z, zc.p.w), zc.e1};
+            const PhiE nb0[6] = {n1,
+                                 xl,
+                                 {make_float2(yp.p.x, yp.p.y), yp.e0},
+                                 {make_float2(ym.p.x, ym.p.y), ym.e0},
+                                 {make_float2(zp.p.x, zp.p.y), zp.e0},
+                                 {make_float2(zm.p.x, zm.p.y), zm.e0}};
+            const PhiE nb1[6] = {xr,
+                                 n0,
+                                 {make_float2(yp.p.z, yp.p.w), yp.e1},
+                                 {make_float2(ym.p.z, ym.p.w), ym.e1},
+                                 {make_float2(zp.p.z, zp.p.w), zp.e1},
+                                 {make_float2(zm.p.z, zm.p.w), zm.e1}};
+            float2 u0, u1;
+            const float R0 = node_resid<kF64>(n0, nb0, make_float2(F.x, F.y), u0);
+            const float R1 = node_resid<kF64>(n1, nb1, make_float2(F.z, F.w), u1);
+            if (a.e) *reinterpret_cast<float4*>(nxt + n) = make_float4(u0.x, u0.y, u1.x, u1.y);
+            (c0 ? a.r + d.half : a.r)[m] = R0 * a.inv_h2;
+            (c0 ? a.r : a.r + d.half)[m] = R1 * a.inv_h2;
+            acc += R0 * R0;
+            acc += R1 * R1;
+            zm = zc;
+            zc = zp;
+            zp = zn;
+        }
+    }
+    resid_df_tail(a, acc, s_sel);
 }
 
 // after the loop: the current potential back into buffer 0
@@ -1921,7 +2094,7 @@ void launch_rhs_df(pic_ctx* c, const uint32_t* step, double scale, double vb, do
 
 void launch_resid_df(pic_ctx* c, double tol, int max_iters, const float* e, bool graph, cudaGraphConditionalHandle h)
 {
-    const Dims d{c->nx, c->ny, c->nz};
+    const Dims d{c->nx, c->ny, c->nz, c->mg[0].half};   // mg[0].f receives the residual
     ResDf a{};
     a.phi = c->phi2;
     const bool first = e == nullptr;
@@ -1941,10 +2114,16 @@ void launch_resid_df(pic_ctx* c, double tol, int max_iters, const float* e, bool
     a.first = first ? 1 : 0;
     a.use_cond = graph ? 1 : 0;
     a.h = h;
-    Grid3 g = grid3(d.nx, d.ny, 1);
+    const bool f64 = (c->flags & PIC_F_F64_RESIDUAL) != 0;
+    Grid3 g = grid3(d.half ? d.nx / 2 : d.nx, d.ny, 1);
     g.grid.z = (unsigned)std::max(1, (d.nz - 1 + kResidPlanes - 1) / kResidPlanes);
-    if (c->flags & PIC_F_F64_RESIDUAL) launch_pdl(c->stream, g.grid, g.block, k_resid_df<true>, a, d);
-    else launch_pdl(c->stream, g.grid, g.block, k_resid_df<false>, a, d);
+    if (d.half) {
+        if (f64) launch_pdl(c->stream, g.grid, g.block, k_resid_df_pairs<true>, a, d);
+        else launch_pdl(c->stream, g.grid, g.block, k_resid_df_pairs<false>, a, d);
+    } else {
+        if (f64) launch_pdl(c->stream, g.grid, g.block, k_resid_df<true>, a, d);
+        else launch_pdl(c->stream, g.grid, g.block, k_resid_df<false>, a, d);
+    }
     c->launches += 1;
 }
 
@@ -2090,6 +2269,9 @@ pic_status mg_setup(pic_ctx* c)
             }
         if (!found) return PIC_ECUDA;
     }
+    // the finest level, when it runs as grid-wide launches, in the red-black
+    // layout (its every kernel indexes it through lix)
+    c->mg[0].half = (c->mg_tail > 0 && c->mg.size() > 1 && c->mg[0].nx % 2 == 0) ? (int)(c->mg[0].nodes / 2) : 0;
     // the finest level below the first that one cluster can solve exactly
     c->ex_level = -1;
     for (int l = 1; PIC_MG_EXACT && l < (int)c->mg.size() && c->ex_level < 0; ++l)
