@@ -167,20 +167,28 @@ __global__ void k_rbgs(T* __restrict__ u, const T* __restrict__ f, Dims d, T h2,
 // half.  Every neighbour of the updated node (offset p = (j + k + colour) & 1
 // in its pair) is of the other colour: in the same pair (x on one side), the
 // pair next to it (x on the other side), pairs m -+ nx/2 (y) and m -+ P/2
-// (z).  A thread walks its column up kRbPlanes planes; the other colour's
+// (z).  A thread walks its column up zp planes; the other colour's
 // column values at k - 1, k, k + 1 roll through registers and the one at
 // k + 2 is loaded a plane ahead.  Each node's sum is k_rbgs's, term by term.
-constexpr int kRbPlanes = 16;
+constexpr int kRbPlanes = 16;   // most planes per block of the column kernels
+
+// planes per block of a column kernel over `planes` planes: up to `most`, fewer
+// when the columns alone would not give every SM four blocks
+inline int column_planes(const Grid3& g, int planes, int most)
+{
+    const long long z = (long long)g.grid.x * g.grid.y * planes / (152LL * 4);
+    return (int)std::max(1LL, std::min((long long)most, z));
+}
 
 template <typename T>
-__global__ void k_rbgs_split(T* __restrict__ u, const T* __restrict__ f, Dims d, T h2, int color, int zero)
+__global__ void k_rbgs_split(T* __restrict__ u, const T* __restrict__ f, Dims d, T h2, int color, int zero, int zp)
 {
     pdl_begin();
     const int hx = d.nx >> 1, P2 = hx * d.ny;
     const int i2 = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y * blockDim.y + threadIdx.y;
-    const int k0 = 1 + (int)blockIdx.z * kRbPlanes;
-    const int k1 = min(k0 + kRbPlanes, d.nz);
+    const int k0 = 1 + (int)blockIdx.z * zp;
+    const int k1 = min(k0 + zp, d.nz);
     if (i2 >= hx || j >= d.ny || k0 >= k1) return;
     T* uc = u + (color ? d.half : 0);               // the colour being updated
     const T* fc = f + (color ? d.half : 0);
@@ -510,6 +518,129 @@ __global__ void k_prolong_cell(T* __restrict__ uf, const T* __restrict__ uc, Dim
                 uf[lix(df, k * P + j * df.nx + i, (i + j + k) & 1)] += v;
             }
         }
+    }
+}
+
+// ---- red-black split finest level: restriction and prolongation by columns --
+constexpr int kSplitPlanes = 8;   // most coarse planes per block of the prolongation below
+
+// Red residual r = f - A u at the red nodes of a split level (the black ones
+// are zero after the black half-sweep), written to rr[m] at the red node's
+// pair index; columns of node pairs as in k_rbgs_split, the same terms in
+// res_at's order.
+template <typename T>
+__global__ void k_resid_red_split(const T* __restrict__ u, const T* __restrict__ f, T* __restrict__ rr, Dims d,
+                                  T inv_h2, int zp)
+{
+    pdl_begin();
+    const int hx = d.nx >> 1, P2 = hx * d.ny;
+    const int i2 = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    const int k0 = 1 + (int)blockIdx.z * zp;
+    const int k1 = min(k0 + zp, d.nz);
+    if (i2 >= hx || j >= d.ny || k0 >= k1) return;
+    const T* ur = u;               // red
+    const T* ub = u + d.half;      // black: every neighbour of a red node
+    const int dxp = (i2 + 1 == hx) ? 1 - hx : 1, dxm = (i2 == 0) ? hx - 1 : -1;
+    const int dyp = (j + 1 == d.ny) ? -j * hx : hx, dym = (j == 0) ? (d.ny - 1) * hx : -hx;
+    int m = k0 * P2 + j * hx + i2;
+    T om = ub[m - P2], oc = ub[m], op = ub[m + P2];
+    for (int k = k0; k < k1; ++k, m += P2) {
+        const T on = (k + 1 < k1) ? ub[m + 2 * P2] : op;
+        const int p = (j + k) & 1;   // offset of the red node in its pair
+        const T ox = ub[m + (p ? dxp : dxm)];
+        const T xp = p ? ox : oc, xm = p ? oc : ox;
+        const T s = xp + xm + ub[m + dyp] + ub[m + dym] + op + om;
+        rr[m] = f[m] - ((T)6 * ur[m] - s) * inv_h2;
+        om = oc;
+        oc = op;
+        op = on;
+    }
+}
+
+// Full-weighting restriction of the red residuals rr (as k_resid_restrict:
+// 1/8 at the coincident node, 1/32 at the 12 with two odd offsets, in its
+// order of terms), and the coarse level's first red half-sweep from zero.
+template <typename T>
+__global__ void k_restrict_red(const T* __restrict__ rr, T* __restrict__ fc, T* __restrict__ uc, Dims df, Dims dc,
+                               T h2c)
+{
+    pdl_begin();
+    const int I = blockIdx.x * blockDim.x + threadIdx.x;
+    const int J = blockIdx.y * blockDim.y + threadIdx.y;
+    const int K = 1 + blockIdx.z;
+    if (I >= dc.nx || J >= dc.ny) return;
+    const int i0 = 2 * I, j0 = 2 * J, k0 = 2 * K;
+    const int im = (i0 == 0) ? df.nx - 1 : i0 - 1, ip = i0 + 1;
+    const int jm = (j0 == 0) ? df.ny - 1 : j0 - 1, jp = j0 + 1;
+    const int P = df.nx * df.ny;
+    auto r = [&](int i, int j, int k) { return rr[(k * P + j * df.nx + i) >> 1]; };
+    T e = r(im, jm, k0) + r(ip, jm, k0) + r(im, jp, k0) + r(ip, jp, k0);
+    e += r(im, j0, k0 - 1) + r(ip, j0, k0 - 1) + r(im, j0, k0 + 1) + r(ip, j0, k0 + 1);
+    e += r(i0, jm, k0 - 1) + r(i0, jp, k0 - 1) + r(i0, jm, k0 + 1) + r(i0, jp, k0 + 1);
+    const T v = (T)0.125 * r(i0, j0, k0) + (T)0.03125 * e;
+    const int nc = K * dc.nx * dc.ny + J * dc.nx + I;
+    fc[nc] = v;
+    if (((I + J + K) & 1) == 0) uc[nc] = h2c * v * (T)(1.0 / 6.0);
+}
+
+// k_prolong_cell onto a split level: thread (I, J) walks zp coarse
+// planes of its column, the corners of plane K + 1 reused as those of the
+// next cell's plane K; the fine pair (I, 2J + b, 2K + c) gets its two nodes'
+// values added at pair index m in the red and black halves.
+template <typename T>
+__global__ void k_prolong_split(T* __restrict__ uf, const T* __restrict__ uc, Dims df, Dims dc, int zp)
+{
+    pdl_begin();
+    const int I = blockIdx.x * blockDim.x + threadIdx.x;
+    const int J = blockIdx.y * blockDim.y + threadIdx.y;
+    const int Kb = (int)blockIdx.z * zp;
+    const int Ke = min(Kb + zp, dc.nz);
+    if (I >= dc.nx || J >= dc.ny || Kb >= Ke) return;
+    const int I1 = (I + 1 == dc.nx) ? 0 : I + 1, J1 = (J + 1 == dc.ny) ? 0 : J + 1;
+    const int Pc = dc.nx * dc.ny, hx = df.nx >> 1, P2 = hx * df.ny;
+    const T* a = uc + Kb * Pc;
+    T c000 = a[J * dc.nx + I], c001 = a[J * dc.nx + I1], c010 = a[J1 * dc.nx + I], c011 = a[J1 * dc.nx + I1];
+    for (int K = Kb; K < Ke; ++K) {
+        a += Pc;
+        const T c100 = a[J * dc.nx + I], c101 = a[J * dc.nx + I1], c110 = a[J1 * dc.nx + I], c111 = a[J1 * dc.nx + I1];
+        // the 8 fine values of this cell: addresses and old values first (all
+        // loads in flight together), then the sums and stores
+        int adr[2][2][2];
+        T old[2][2][2];
+#pragma unroll
+        for (int cz = 0; cz < 2; ++cz)
+#pragma unroll
+            for (int by = 0; by < 2; ++by) {
+                const int k = 2 * K + cz, j = 2 * J + by;
+                const int m = k * P2 + j * hx + I;
+                const int c0 = (j + k) & 1;   // colour of node 0 of the pair
+                adr[cz][by][0] = (c0 ? df.half : 0) + m;
+                adr[cz][by][1] = (c0 ? 0 : df.half) + m;
+                const bool in = k >= 1 && k <= df.nz - 1;
+#pragma unroll
+                for (int bx = 0; bx < 2; ++bx) old[cz][by][bx] = in ? uf[adr[cz][by][bx]] : (T)0;
+            }
+#pragma unroll
+        for (int cz = 0; cz < 2; ++cz) {
+            const int k = 2 * K + cz;
+            if (k < 1 || k > df.nz - 1) continue;
+            const T z0[4] = {c000, c001, c010, c011};
+            const T z1[4] = {cz ? c100 : c000, cz ? c101 : c001, cz ? c110 : c010, cz ? c111 : c011};
+#pragma unroll
+            for (int by = 0; by < 2; ++by)
+#pragma unroll
+                for (int bx = 0; bx < 2; ++bx) {
+                    const T p00 = z0[0], p01 = z0[bx ? 1 : 0], p10 = z0[by ? 2 : 0], p11 = z0[(by ? 2 : 0) + (bx ? 1 : 0)];
+                    const T q00 = z1[0], q01 = z1[bx ? 1 : 0], q10 = z1[by ? 2 : 0], q11 = z1[(by ? 2 : 0) + (bx ? 1 : 0)];
+                    const T v = (T)0.125 * (p00 + p01 + p10 + p11 + q00 + q01 + q10 + q11);
+                    uf[adr[cz][by][bx]] = old[cz][by][bx] + v;
+                }
+        }
+        c000 = c100;
+        c001 = c101;
+        c010 = c110;
+        c011 = c111;
     }
 }
 
@@ -1422,8 +1553,9 @@ void run_rbgs(cudaStream_t s, T* u, const T* f, Dims d, T h2, int color, int zer
 {
     if (d.half) {
         Grid3 g = grid3(d.nx / 2, d.ny, 1);
-        g.grid.z = (unsigned)std::max(1, (d.nz - 1 + kRbPlanes - 1) / kRbPlanes);
-        launch_pdl(s, g.grid, g.block, k_rbgs_split<T>, u, f, d, h2, color, zero);
+        const int zp = column_planes(g, d.nz - 1, kRbPlanes);
+        g.grid.z = (unsigned)std::max(1, (d.nz - 1 + zp - 1) / zp);
+        launch_pdl(s, g.grid, g.block, k_rbgs_split<T>, u, f, d, h2, color, zero, zp);
         return;
     }
     const Grid3 g = grid3(d.nx / 2, d.ny, d.nz - 1);
@@ -1442,8 +1574,19 @@ void run_restrict(cudaStream_t s, const T* rf, T* fc, Dims df, Dims dc)
     k_restrict<T><<<g.grid, g.block, 0, s>>>(rf, fc, df, dc);
 }
 template <typename T>
-void run_resid_restrict(cudaStream_t s, const T* u, const T* f, T* fc, T* uc, Dims df, Dims dc, T inv_h2, T h2c)
+void run_resid_restrict(cudaStream_t s, const T* u, const T* f, T* fc, T* uc, Dims df, Dims dc, T inv_h2, T h2c,
+                        T* rr = nullptr)
 {
+    if (df.half && rr && df.nx == 2 * dc.nx && df.ny == 2 * dc.ny && df.nz == 2 * dc.nz) {
+        // split level: the red residuals in one pass, then the restriction
+        Grid3 g1 = grid3(df.nx / 2, df.ny, 1);
+        const int zp = column_planes(g1, df.nz - 1, kRbPlanes);
+        g1.grid.z = (unsigned)std::max(1, (df.nz - 1 + zp - 1) / zp);
+        launch_pdl(s, g1.grid, g1.block, k_resid_red_split<T>, u, f, rr, df, inv_h2, zp);
+        const Grid3 g2 = grid3(dc.nx, dc.ny, dc.nz - 1);
+        launch_pdl(s, g2.grid, g2.block, k_restrict_red<T>, (const T*)rr, fc, uc, df, dc, h2c);
+        return;
+    }
     const Grid3 g = grid3(dc.nx, dc.ny, dc.nz - 1);
     launch_pdl(s, g.grid, g.block, k_resid_restrict<T>, u, f, fc, uc, df, dc, inv_h2, h2c);
 }
@@ -1451,6 +1594,13 @@ template <typename T>
 void run_prolong(cudaStream_t s, T* uf, const T* uc, Dims df, Dims dc)
 {
     if (df.nx == 2 * dc.nx && df.ny == 2 * dc.ny && df.nz == 2 * dc.nz) {
+        if (df.half) {
+            Grid3 g = grid3(dc.nx, dc.ny, 1);
+            const int zp = column_planes(g, dc.nz, kSplitPlanes);
+            g.grid.z = (unsigned)std::max(1, (dc.nz + zp - 1) / zp);
+            launch_pdl(s, g.grid, g.block, k_prolong_split<T>, uf, uc, df, dc, zp);
+            return;
+        }
         const Grid3 g = grid3(dc.nx, dc.ny, dc.nz);
         launch_pdl(s, g.grid, g.block, k_prolong_cell<T>, uf, uc, df, dc);
         return;
@@ -1550,8 +1700,9 @@ T* vcycle(pic_ctx* c, int l)
         }
     MGLevel& C = c->mg[l + 1];
     const Dims dc{C.nx, C.ny, C.nz};
-    run_resid_restrict<T>(c->stream, u, f, (T*)C.f, (T*)C.u, d, dc, (T)(1.0 / (L.h * L.h)), (T)(C.h * C.h));
-    c->launches += 1;
+    run_resid_restrict<T>(c->stream, u, f, (T*)C.f, (T*)C.u, d, dc, (T)(1.0 / (L.h * L.h)), (T)(C.h * C.h),
+                          (T*)L.r);
+    c->launches += d.half ? 2 : 1;
     T* uc = vcycle<T>(c, l + 1);
     run_prolong<T>(c->stream, u, (const T*)uc, d, dc);
     c->launches += 1 + 2 * kPost;
@@ -1824,7 +1975,7 @@ struct ResDf {
 // other buffer), R = h^2 f - (6 phi' - sum of the 6 neighbours of phi') with
 // the large parts summed exactly, ||R||^2 over the grid, and in the last block
 // the loop decision of the solve (the same rule as the FP64 solver's).
-// the refinement step: planes per block (a 32 x 8 column tile of them) and
+// the refinement step: most planes per block (a 32 x 8 column tile of them) and
 // resident blocks per SM it is built for
 constexpr int kResidPlanes = 16;
 constexpr int kResidBlocks = 4;
@@ -1895,14 +2046,14 @@ __device__ __forceinline__ void resid_df_tail(const ResDf& a, float acc, int sel
 // One refinement step over the interior nodes: phi' = phi + e (written to the
 // other buffer), R = h^2 f - (6 phi' - sum of the 6 neighbours of phi') with
 // the large parts summed exactly, ||R||^2 over the grid, and the loop decision.
-// Natural layout of e and r; thread (i, j) walks kResidPlanes planes of its
+// Natural layout of e and r; thread (i, j) walks zp planes of its
 // column: the values at k - 1, k and k + 1 roll through registers, and the
 // loads for plane k + 1 (its in-plane neighbours and f, the column at k + 2)
 // are issued before plane k is computed.  The potential, correction and f are
 // only read here (the new potential goes to the other buffer), so the loads
 // take the read-only path.
 template <bool kF64>
-__global__ void __launch_bounds__(256, kResidBlocks) k_resid_df(ResDf a, Dims d)
+__global__ void __launch_bounds__(256, kResidBlocks) k_resid_df(ResDf a, Dims d, int zp)
 {
     pdl_begin();
     __shared__ int s_sel;
@@ -1913,8 +2064,8 @@ __global__ void __launch_bounds__(256, kResidBlocks) k_resid_df(ResDf a, Dims d)
     float2* nxt = a.phi + (s_sel ? 0 : N);
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y * blockDim.y + threadIdx.y;
-    const int k0 = 1 + (int)blockIdx.z * kResidPlanes;
-    const int k1 = min(k0 + kResidPlanes, d.nz);
+    const int k0 = 1 + (int)blockIdx.z * zp;
+    const int k1 = min(k0 + zp, d.nz);
     float acc = 0.f;
     if (i < d.nx && j < d.ny && k0 < k1) {
         const int P = d.nx * d.ny;
@@ -1961,7 +2112,7 @@ __global__ void __launch_bounds__(256, kResidBlocks) k_resid_df(ResDf a, Dims d)
 // The same step on a red-black split finest level (d.half > 0: e and r split
 // by colour, the potential and f in natural order), by columns of node pairs:
 // thread (i2, j) takes nodes 2 i2 and 2 i2 + 1 of each row (j, k) of its
-// kResidPlanes planes, their potential and f as one 16-byte load each, their
+// zp planes, their potential and f as one 16-byte load each, their
 // corrections at pair index m in the red and black halves.  Each node's
 // neighbours are those of k_resid_df, in its order; the pairs at k - 1, k and
 // k + 1 roll through registers, the one at k + 2 is loaded a plane ahead.
@@ -1971,7 +2122,7 @@ struct PairPE {
 };
 
 template <bool kF64>
-__global__ void __launch_bounds__(256, kResidBlocks) k_resid_df_pairs(ResDf a, Dims d)
+__global__ void __launch_bounds__(256, kResidBlocks) k_resid_df_pairs(ResDf a, Dims d, int zp)
 {
     pdl_begin();
     __shared__ int s_sel;
@@ -1983,8 +2134,8 @@ __global__ void __launch_bounds__(256, kResidBlocks) k_resid_df_pairs(ResDf a, D
     const int hx = d.nx >> 1, P2 = hx * d.ny, P = d.nx * d.ny;
     const int i2 = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y * blockDim.y + threadIdx.y;
-    const int k0 = 1 + (int)blockIdx.z * kResidPlanes;
-    const int k1 = min(k0 + kResidPlanes, d.nz);
+    const int k0 = 1 + (int)blockIdx.z * zp;
+    const int k1 = min(k0 + zp, d.nz);
     float acc = 0.f;
     if (i2 < hx && j < d.ny && k0 < k1) {
         const float* eR = a.e;
@@ -2116,13 +2267,14 @@ void launch_resid_df(pic_ctx* c, double tol, int max_iters, const float* e, bool
     a.h = h;
     const bool f64 = (c->flags & PIC_F_F64_RESIDUAL) != 0;
     Grid3 g = grid3(d.half ? d.nx / 2 : d.nx, d.ny, 1);
-    g.grid.z = (unsigned)std::max(1, (d.nz - 1 + kResidPlanes - 1) / kResidPlanes);
+    const int zp = column_planes(g, d.nz - 1, kResidPlanes);
+    g.grid.z = (unsigned)std::max(1, (d.nz - 1 + zp - 1) / zp);
     if (d.half) {
-        if (f64) launch_pdl(c->stream, g.grid, g.block, k_resid_df_pairs<true>, a, d);
-        else launch_pdl(c->stream, g.grid, g.block, k_resid_df_pairs<false>, a, d);
+        if (f64) launch_pdl(c->stream, g.grid, g.block, k_resid_df_pairs<true>, a, d, zp);
+        else launch_pdl(c->stream, g.grid, g.block, k_resid_df_pairs<false>, a, d, zp);
     } else {
-        if (f64) launch_pdl(c->stream, g.grid, g.block, k_resid_df<true>, a, d);
-        else launch_pdl(c->stream, g.grid, g.block, k_resid_df<false>, a, d);
+        if (f64) launch_pdl(c->stream, g.grid, g.block, k_resid_df<true>, a, d, zp);
+        else launch_pdl(c->stream, g.grid, g.block, k_resid_df<false>, a, d, zp);
     }
     c->launches += 1;
 }
