@@ -214,6 +214,64 @@ __global__ void k_rbgs_split(T* __restrict__ u, const T* __restrict__ f, Dims d,
     }
 }
 
+// k_rbgs_split with two adjacent pairs 2q, 2q + 1 per thread (nx a multiple of
+// 4), so each load moves two values: the other colour's column values and f
+// as one 8-byte (16-byte for double) load per plane, one scalar load for the x
+// neighbour outside the two pairs.  The same sum per node, term by term.
+template <typename T> struct Two;
+template <> struct Two<float> { using V = float2; };
+template <> struct Two<double> { using V = double2; };
+
+template <typename T>
+__global__ void k_rbgs_split2(T* __restrict__ u, const T* __restrict__ f, Dims d, T h2, int color, int zero, int zp)
+{
+    using V = typename Two<T>::V;
+    pdl_begin();
+    const int hx = d.nx >> 1, P2 = hx * d.ny, qx = hx >> 1;
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    const int k0 = 1 + (int)blockIdx.z * zp;
+    const int k1 = min(k0 + zp, d.nz);
+    if (q >= qx || j >= d.ny || k0 >= k1) return;
+    T* uc = u + (color ? d.half : 0);
+    const T* fc = f + (color ? d.half : 0);
+    const T* uo = u + (color ? 0 : d.half);
+    int m = k0 * P2 + j * hx + 2 * q;   // even: 2-element aligned
+    if (zero) {
+        for (int k = k0; k < k1; ++k, m += P2) {
+            const V ff = *reinterpret_cast<const V*>(fc + m);
+            V r;
+            r.x = (h2 * ff.x) * (T)(1.0 / 6.0);
+            r.y = (h2 * ff.y) * (T)(1.0 / 6.0);
+            *reinterpret_cast<V*>(uc + m) = r;
+        }
+        return;
+    }
+    const int dl = (q == 0) ? hx - 1 : -1;            // pair 2q - 1
+    const int dr = (q + 1 == qx) ? 2 - hx : 2;        // pair 2q + 2
+    const int dyp = (j + 1 == d.ny) ? -j * hx : hx, dym = (j == 0) ? (d.ny - 1) * hx : -hx;
+    auto ld = [&](int at) { return *reinterpret_cast<const V*>(uo + at); };
+    V om = ld(m - P2), oc = ld(m), op = ld(m + P2);
+    for (int k = k0; k < k1; ++k, m += P2) {
+        const V on = (k + 1 < k1) ? ld(m + 2 * P2) : op;
+        const int p = (j + k + color) & 1;
+        const T ox = uo[m + (p ? dr : dl)];
+        const V yp = ld(m + dyp), ym = ld(m + dym);
+        const V ff = *reinterpret_cast<const V*>(fc + m);
+        const T xp0 = p ? oc.y : oc.x, xm0 = p ? oc.x : ox;
+        const T xp1 = p ? ox : oc.y, xm1 = p ? oc.y : oc.x;
+        const T s0 = xp0 + xm0 + yp.x + ym.x + op.x + om.x;
+        const T s1 = xp1 + xm1 + yp.y + ym.y + op.y + om.y;
+        V r;
+        r.x = (s0 + h2 * ff.x) * (T)(1.0 / 6.0);
+        r.y = (s1 + h2 * ff.y) * (T)(1.0 / 6.0);
+        *reinterpret_cast<V*>(uc + m) = r;
+        om = oc;
+        oc = op;
+        op = on;
+    }
+}
+
 // r = f - A u on the interior planes (the electrode planes of r stay zero)
 template <typename T>
 __global__ void k_resid(const T* __restrict__ u, const T* __restrict__ f, T* __restrict__ r, Dims d, T inv_h2)
@@ -552,6 +610,45 @@ __global__ void k_resid_red_split(const T* __restrict__ u, const T* __restrict__
         const T xp = p ? ox : oc, xm = p ? oc : ox;
         const T s = xp + xm + ub[m + dyp] + ub[m + dym] + op + om;
         rr[m] = f[m] - ((T)6 * ur[m] - s) * inv_h2;
+        om = oc;
+        oc = op;
+        op = on;
+    }
+}
+
+// k_resid_red_split with two adjacent pairs per thread (as k_rbgs_split2)
+template <typename T>
+__global__ void k_resid_red_split2(const T* __restrict__ u, const T* __restrict__ f, T* __restrict__ rr, Dims d,
+                                   T inv_h2, int zp)
+{
+    using V = typename Two<T>::V;
+    pdl_begin();
+    const int hx = d.nx >> 1, P2 = hx * d.ny, qx = hx >> 1;
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    const int k0 = 1 + (int)blockIdx.z * zp;
+    const int k1 = min(k0 + zp, d.nz);
+    if (q >= qx || j >= d.ny || k0 >= k1) return;
+    const T* ur = u;
+    const T* ub = u + d.half;
+    const int dl = (q == 0) ? hx - 1 : -1, dr = (q + 1 == qx) ? 2 - hx : 2;
+    const int dyp = (j + 1 == d.ny) ? -j * hx : hx, dym = (j == 0) ? (d.ny - 1) * hx : -hx;
+    int m = k0 * P2 + j * hx + 2 * q;
+    auto ld = [&](const T* a, int at) { return *reinterpret_cast<const V*>(a + at); };
+    V om = ld(ub, m - P2), oc = ld(ub, m), op = ld(ub, m + P2);
+    for (int k = k0; k < k1; ++k, m += P2) {
+        const V on = (k + 1 < k1) ? ld(ub, m + 2 * P2) : op;
+        const int p = (j + k) & 1;   // offset of the red nodes in their pairs
+        const T ox = ub[m + (p ? dr : dl)];
+        const V yp = ld(ub, m + dyp), ym = ld(ub, m + dym), uu = ld(ur, m), ff = ld(f, m);
+        const T xp0 = p ? oc.y : oc.x, xm0 = p ? oc.x : ox;
+        const T xp1 = p ? ox : oc.y, xm1 = p ? oc.y : oc.x;
+        const T s0 = xp0 + xm0 + yp.x + ym.x + op.x + om.x;
+        const T s1 = xp1 + xm1 + yp.y + ym.y + op.y + om.y;
+        V r;
+        r.x = ff.x - ((T)6 * uu.x - s0) * inv_h2;
+        r.y = ff.y - ((T)6 * uu.y - s1) * inv_h2;
+        *reinterpret_cast<V*>(rr + m) = r;
         om = oc;
         oc = op;
         op = on;
@@ -1552,6 +1649,13 @@ template <typename T>
 void run_rbgs(cudaStream_t s, T* u, const T* f, Dims d, T h2, int color, int zero)
 {
     if (d.half) {
+        if (d.nx % 4 == 0 && d.half % 2 == 0) {
+            Grid3 g = grid3(d.nx / 4, d.ny, 1);
+            const int zp = column_planes(g, d.nz - 1, kRbPlanes);
+            g.grid.z = (unsigned)std::max(1, (d.nz - 1 + zp - 1) / zp);
+            launch_pdl(s, g.grid, g.block, k_rbgs_split2<T>, u, f, d, h2, color, zero, zp);
+            return;
+        }
         Grid3 g = grid3(d.nx / 2, d.ny, 1);
         const int zp = column_planes(g, d.nz - 1, kRbPlanes);
         g.grid.z = (unsigned)std::max(1, (d.nz - 1 + zp - 1) / zp);
@@ -1579,10 +1683,17 @@ void run_resid_restrict(cudaStream_t s, const T* u, const T* f, T* fc, T* uc, Di
 {
     if (df.half && rr && df.nx == 2 * dc.nx && df.ny == 2 * dc.ny && df.nz == 2 * dc.nz) {
         // split level: the red residuals in one pass, then the restriction
-        Grid3 g1 = grid3(df.nx / 2, df.ny, 1);
-        const int zp = column_planes(g1, df.nz - 1, kRbPlanes);
-        g1.grid.z = (unsigned)std::max(1, (df.nz - 1 + zp - 1) / zp);
-        launch_pdl(s, g1.grid, g1.block, k_resid_red_split<T>, u, f, rr, df, inv_h2, zp);
+        if (df.nx % 4 == 0 && df.half % 2 == 0) {
+            Grid3 g1 = grid3(df.nx / 4, df.ny, 1);
+            const int zp = column_planes(g1, df.nz - 1, kRbPlanes);
+            g1.grid.z = (unsigned)std::max(1, (df.nz - 1 + zp - 1) / zp);
+            launch_pdl(s, g1.grid, g1.block, k_resid_red_split2<T>, u, f, rr, df, inv_h2, zp);
+        } else {
+            Grid3 g1 = grid3(df.nx / 2, df.ny, 1);
+            const int zp = column_planes(g1, df.nz - 1, kRbPlanes);
+            g1.grid.z = (unsigned)std::max(1, (df.nz - 1 + zp - 1) / zp);
+            launch_pdl(s, g1.grid, g1.block, k_resid_red_split<T>, u, f, rr, df, inv_h2, zp);
+        }
         const Grid3 g2 = grid3(dc.nx, dc.ny, dc.nz - 1);
         launch_pdl(s, g2.grid, g2.block, k_restrict_red<T>, (const T*)rr, fc, uc, df, dc, h2c);
         return;
