@@ -677,8 +677,9 @@ __global__ void k_restrict_red(const T* __restrict__ rr, T* __restrict__ fc, T* 
     e += r(i0, jm, k0 - 1) + r(i0, jp, k0 - 1) + r(i0, jm, k0 + 1) + r(i0, jp, k0 + 1);
     const T v = (T)0.125 * r(i0, j0, k0) + (T)0.03125 * e;
     const int nc = K * dc.nx * dc.ny + J * dc.nx + I;
-    fc[nc] = v;
-    if (((I + J + K) & 1) == 0) uc[nc] = h2c * v * (T)(1.0 / 6.0);
+    const int col = (I + J + K) & 1;
+    fc[lix(dc, nc, col)] = v;
+    if (col == 0) uc[lix(dc, nc, 0)] = h2c * v * (T)(1.0 / 6.0);
 }
 
 // k_prolong_cell onto a split level: thread (I, J) walks zp coarse
@@ -696,11 +697,11 @@ __global__ void k_prolong_split(T* __restrict__ uf, const T* __restrict__ uc, Di
     if (I >= dc.nx || J >= dc.ny || Kb >= Ke) return;
     const int I1 = (I + 1 == dc.nx) ? 0 : I + 1, J1 = (J + 1 == dc.ny) ? 0 : J + 1;
     const int Pc = dc.nx * dc.ny, hx = df.nx >> 1, P2 = hx * df.ny;
-    const T* a = uc + Kb * Pc;
-    T c000 = a[J * dc.nx + I], c001 = a[J * dc.nx + I1], c010 = a[J1 * dc.nx + I], c011 = a[J1 * dc.nx + I1];
+    // a corner of coarse plane K (the coarse level may itself be split)
+    auto cr = [&](int K, int i, int j) { return uc[lix(dc, K * Pc + j * dc.nx + i, (i + j + K) & 1)]; };
+    T c000 = cr(Kb, I, J), c001 = cr(Kb, I1, J), c010 = cr(Kb, I, J1), c011 = cr(Kb, I1, J1);
     for (int K = Kb; K < Ke; ++K) {
-        a += Pc;
-        const T c100 = a[J * dc.nx + I], c101 = a[J * dc.nx + I1], c110 = a[J1 * dc.nx + I], c111 = a[J1 * dc.nx + I1];
+        const T c100 = cr(K + 1, I, J), c101 = cr(K + 1, I1, J), c110 = cr(K + 1, I, J1), c111 = cr(K + 1, I1, J1);
         // the 8 fine values of this cell: addresses and old values first (all
         // loads in flight together), then the sums and stores
         int adr[2][2][2];
@@ -1810,7 +1811,7 @@ T* vcycle(pic_ctx* c, int l)
             c->launches += 1;
         }
     MGLevel& C = c->mg[l + 1];
-    const Dims dc{C.nx, C.ny, C.nz};
+    const Dims dc{C.nx, C.ny, C.nz, C.half};
     run_resid_restrict<T>(c->stream, u, f, (T*)C.f, (T*)C.u, d, dc, (T)(1.0 / (L.h * L.h)), (T)(C.h * C.h),
                           (T*)L.r);
     c->launches += d.half ? 2 : 1;
@@ -2532,9 +2533,6 @@ pic_status mg_setup(pic_ctx* c)
             }
         if (!found) return PIC_ECUDA;
     }
-    // the finest level, when it runs as grid-wide launches, in the red-black
-    // layout (its every kernel indexes it through lix)
-    c->mg[0].half = (c->mg_tail > 0 && c->mg.size() > 1 && c->mg[0].nx % 2 == 0) ? (int)(c->mg[0].nodes / 2) : 0;
     // the finest level below the first that one cluster can solve exactly
     c->ex_level = -1;
     for (int l = 1; PIC_MG_EXACT && l < (int)c->mg.size() && c->ex_level < 0; ++l)
@@ -2553,6 +2551,21 @@ pic_status mg_setup(pic_ctx* c)
             c->ex_size = C;
             break;
         }
+    // Red-black split layout (every kernel indexes such a level through lix):
+    // the finest level when it runs as grid-wide launches, and each coarser
+    // grid-wide level reached from a split level by halving every axis (the
+    // restriction onto it and the prolongation from it then take the split
+    // kernels, which read and write it by colour).
+    for (int l = 0; l < (int)c->mg.size(); ++l) {
+        MGLevel& M = c->mg[l];
+        bool split = l < c->mg_tail && (c->ex_level < 0 || l < c->ex_level) && l + 1 < (int)c->mg.size() &&
+                     M.nx % 2 == 0;
+        if (l > 0) {
+            const MGLevel& F = c->mg[l - 1];
+            split = split && F.half > 0 && F.nx == 2 * M.nx && F.ny == 2 * M.ny && F.nz == 2 * M.nz;
+        }
+        M.half = split ? (int)(M.nodes / 2) : 0;
+    }
     if (c->ex_level >= 0) {
         const MGLevel& M = c->mg[c->ex_level];
         // orthonormal real Fourier basis of length n (rows) and the eigenvalue of
