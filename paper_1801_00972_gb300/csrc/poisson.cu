@@ -10,7 +10,12 @@
 // until ||r|| <= tol ||b||, b = f plus the electrode terms.  A V-cycle uses
 // red-black Gauss-Seidel smoothing, full-weighting restriction, trilinear
 // prolongation, the 7-point operator rediscretised on each level (spacing
-// doubling), and many smoothing sweeps on the coarsest level in one block.
+// doubling), the levels from a small one down in one thread-block cluster
+// (an exact Fourier-Thomas solve of the first level that fits, or sweeps).
+// The large grid-wide levels store u and f red-black split (lix), and their
+// half-sweeps, red residuals and prolongation run as column kernels over node
+// pairs, plane after plane; the mixed refinement keeps phi and f as two-float
+// sums (double-float arithmetic).
 #include <algorithm>
 #include <cmath>
 #include <mutex>
@@ -20,9 +25,6 @@
 
 #include "pic_internal.cuh"
 
-#ifndef PIC_MG_FUSED
-#define PIC_MG_FUSED 0            // fused 2.5-D smoothing passes on the large grid-wide levels (measured slower)
-#endif
 #ifndef PIC_MG_PRE
 #define PIC_MG_PRE 2
 #endif
@@ -385,154 +387,6 @@ __global__ void k_prolong(T* __restrict__ uf, const T* __restrict__ uc, Dims df,
     const T v = (T)0.125 * (a0[J0 * dc.nx + I0] + a0[J0 * dc.nx + I1] + a0[J1 * dc.nx + I0] + a0[J1 * dc.nx + I1] +
                             a1[J0 * dc.nx + I0] + a1[J0 * dc.nx + I1] + a1[J1 * dc.nx + I0] + a1[J1 * dc.nx + I1]);
     uf[lix(df, k * df.nx * df.ny + j * df.nx + i, (i + j + k) & 1)] += v;
-}
-
-// ---- fused smoothing of a large grid-wide level ("2.5-D" blocking) ----------
-// A CTA owns a tile of kSmTX x kSmTY node columns and a range of tz planes.
-// It keeps rings of planes of u and f over the tile plus a halo of H nodes in
-// x and y (periodic wrap) in shared memory and marches up through the planes:
-// at step t, stage s works on plane t - s, after stage s - 1 has finished the
-// planes around it, so one pass over the level does all the half-sweeps.
-// Each stage shrinks its x, y region by one node, and the planes beyond the
-// CTA's range are recomputed by the neighbouring CTA, so no CTA reads another
-// CTA's results.
-//   PRE  (H = 3): red from a zero guess (h^2 f / 6), black, red, black; the
-//        smoothed correction goes to u_out (u_in unused).
-//   POST (H = 4): u_in plus the trilinear prolongation of the coarse
-//        correction uc, then red, black, red, black, into u_out (u_out != u_in:
-//        neighbouring CTAs still read u_in).
-// Every node's arithmetic is that of k_rbgs / k_prolong in the same order, so
-// the result is bit-identical to the unfused sweeps.
-constexpr int kSmTX = 64, kSmTY = 16;
-
-__device__ __forceinline__ int wrap_idx(int i, int n)
-{
-    return i < 0 ? i + n : (i >= n ? i - n : i);
-}
-
-template <bool kPost>
-struct SmoothShape {
-    static constexpr int H = kPost ? 4 : 3;
-    static constexpr int S = kPost ? 4 : 3;      // last stage
-    // ring depths: the planes the stages read at step t (t - S - 1 .. t) plus the
-    // next plane, which is already on its way (asynchronous copy)
-    static constexpr int RU = S + 3, RF = S + 2;
-    static constexpr int WX = kSmTX + 2 * H, WY = kSmTY + 2 * H, PW = WX * WY;
-};
-
-__device__ __forceinline__ void cp_async4(void* smem, const void* gmem)
-{
-    const unsigned int a = (unsigned int)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(a), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_prev() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
-
-template <typename T, bool kPost>
-__global__ void __launch_bounds__(256) k_smooth_fused(const T* __restrict__ u_in, const T* __restrict__ f,
-                                                      T* __restrict__ u_out, const T* __restrict__ uc, Dims d,
-                                                      Dims dc, T h2, int tz)
-{
-    using Sh = SmoothShape<kPost>;
-    constexpr int H = Sh::H, S = Sh::S, RU = Sh::RU, RF = Sh::RF, WX = Sh::WX, WY = Sh::WY, PW = Sh::PW;
-    extern __shared__ unsigned char sm_raw[];
-    T* su = reinterpret_cast<T*>(sm_raw);
-    T* sf = su + RU * PW;
-    pdl_begin();
-    const int X0 = blockIdx.x * kSmTX - H, Y0 = blockIdx.y * kSmTY - H;   // global (i, j) of ring node (0, 0)
-    const int k0 = 1 + blockIdx.z * tz, k1 = min(d.nz, k0 + tz);           // output planes [k0, k1)
-    const int P = d.nx * d.ny, Pc = dc.nx * dc.ny;
-    const int tid = threadIdx.x;
-    const int t_last = k1 - 1 + S;
-    // plane t into the rings: asynchronous copies of f (and u_in), zeros on and
-    // beyond the electrode planes
-    auto fetch = [&](int t) {
-        T* ut = su + ((t % RU) + RU) % RU * PW;
-        T* ft = sf + ((t % RF) + RF) % RF * PW;
-        const bool inner = t >= 1 && t <= d.nz - 1;
-        for (int q = tid; q < PW; q += blockDim.x) {
-            const int ly = q / WX, lx = q - ly * WX;
-            if (!inner) {
-                ft[q] = (T)0;
-                ut[q] = (T)0;
-                continue;
-            }
-            const int n = t * P + wrap_idx(Y0 + ly, d.ny) * d.nx + wrap_idx(X0 + lx, d.nx);
-            if (sizeof(T) == 4) {
-                cp_async4(ft + q, f + n);
-                if (kPost) cp_async4(ut + q, u_in + n);
-            } else {
-                ft[q] = f[n];
-                if (kPost) ut[q] = u_in[n];
-            }
-        }
-        cp_async_commit();
-    };
-    fetch(k0 - H);
-    for (int t = k0 - H; t <= t_last; ++t) {
-        // the next plane goes out before this one is used; its ring slots are
-        // those of planes the stages of this step no longer read
-        if (t < t_last) fetch(t + 1);
-        else cp_async_commit();
-        cp_async_wait_prev();
-        __syncthreads();
-        // ---- stages: stage s on plane t - s, region [s, WX - s) x [s, WY - s)
-#pragma unroll 1
-        for (int st = 0; st <= S; ++st) {
-            const int p = t - st;
-            if (p < max(1, k0 - (H - st)) || p > min(d.nz - 1, k1 - 1 + (H - st))) continue;   // block-uniform
-            T* up = su + (p % RU) * PW;
-            const T* fp = sf + (p % RF) * PW;
-            const int rw = WX - 2 * st, rh = WY - 2 * st;
-            if (st == 0) {
-                for (int q = tid; q < rw * rh; q += blockDim.x) {
-                    const int ly = q / rw, lx = q - ly * rw;
-                    const int l = ly * WX + lx;
-                    const int i = wrap_idx(X0 + lx, d.nx), j = wrap_idx(Y0 + ly, d.ny);
-                    if (kPost) {
-                        const int I0 = i >> 1, I1 = (i & 1) ? ((I0 + 1 == dc.nx) ? 0 : I0 + 1) : I0;
-                        const int J0 = j >> 1, J1 = (j & 1) ? ((J0 + 1 == dc.ny) ? 0 : J0 + 1) : J0;
-                        const int K0 = p >> 1, K1 = (p & 1) ? K0 + 1 : K0;
-                        const T* a0 = uc + K0 * Pc;
-                        const T* a1 = uc + K1 * Pc;
-                        const T v = (T)0.125 * (a0[J0 * dc.nx + I0] + a0[J0 * dc.nx + I1] + a0[J1 * dc.nx + I0] +
-                                                a0[J1 * dc.nx + I1] + a1[J0 * dc.nx + I0] + a1[J0 * dc.nx + I1] +
-                                                a1[J1 * dc.nx + I0] + a1[J1 * dc.nx + I1]);
-                        up[l] += v;
-                    } else {
-                        up[l] = ((i + j + p) & 1) == 0 ? (h2 * fp[l]) * (T)(1.0 / 6.0) : (T)0;
-                    }
-                }
-            } else {
-                // PRE stages 1, 2, 3 = black, red, black; POST stages 1..4 = red, black, red, black
-                const int color = kPost ? ((st & 1) ? 0 : 1) : ((st & 1) ? 1 : 0);
-                const T* um = su + ((p - 1) % RU) * PW;
-                const T* upp = su + ((p + 1) % RU) * PW;
-                const int half = (rw + 1) >> 1;
-                for (int q = tid; q < half * rh; q += blockDim.x) {
-                    const int ly = q / half;
-                    int lx = st + 2 * (q - ly * half);
-                    const int gy = Y0 + st + ly;
-                    // this colour's nodes: (i + j + p + color) even
-                    if (((X0 + lx) + gy + p + color) & 1) ++lx;
-                    if (lx >= WX - st) continue;
-                    const int l = (st + ly) * WX + lx;
-                    const T s = up[l + 1] + up[l - 1] + up[l + WX] + up[l - WX] + upp[l] + um[l];
-                    up[l] = (s + h2 * fp[l]) * (T)(1.0 / 6.0);
-                }
-            }
-            __syncthreads();
-        }
-        // ---- plane t - S is final: its tile interior to u_out
-        const int qo = t - S;
-        if (qo >= k0 && qo < k1) {
-            const T* uq = su + (qo % RU) * PW;
-            for (int q = tid; q < kSmTX * kSmTY; q += blockDim.x) {
-                const int ly = q / kSmTX, lx = q - ly * kSmTX;
-                u_out[qo * P + (Y0 + H + ly) * d.nx + (X0 + H + lx)] = uq[(H + ly) * WX + (H + lx)];
-            }
-        }
-    }
 }
 
 // The same interpolation, one thread per coarse cell (I, J, K): its 8 corner
@@ -1732,30 +1586,6 @@ void run_resid64(cudaStream_t s, const double* phi, const T* e, const double* f,
     }
 }
 
-template <typename T, bool kPost>
-constexpr size_t smooth_smem()
-{
-    using Sh = SmoothShape<kPost>;
-    return sizeof(T) * (size_t)(Sh::RU + Sh::RF) * Sh::PW;
-}
-
-// Planes per CTA of the fused smoothers on grid-wide level l, or 0 to use the
-// unfused kernels: the level must be tiled by kSmTX x kSmTY columns, V(2,2),
-// and large enough for about two waves of CTAs at two CTAs per SM with at
-// least 16 planes each (smaller levels live in L2, where the unfused sweeps
-// are as fast).
-int fused_planes(const pic_ctx* c, int l)
-{
-    if (!PIC_MG_FUSED || kPre != 2 || kPost != 2 || l + 1 >= (int)c->mg.size()) return 0;
-    const MGLevel& L = c->mg[l];
-    if (L.half || L.nx % kSmTX || L.ny % kSmTY || L.nz < 8) return 0;
-    const long long cols = (long long)(L.nx / kSmTX) * (L.ny / kSmTY);
-    const long long want = 2LL * 2 * 152;
-    int tz = 64;
-    while (tz > 16 && cols * ((L.nz - 1 + tz - 1) / tz) < want) tz /= 2;
-    return cols * ((L.nz - 1 + tz - 1) / tz) >= want ? tz : 0;
-}
-
 // One V-cycle from level l down on A e = f (f in mg[l].f); returns the array
 // that holds the level's correction afterwards.
 template <typename T>
@@ -1786,22 +1616,6 @@ T* vcycle(pic_ctx* c, int l)
     const T h2 = (T)(L.h * L.h);
     T* u = (T*)L.u;
     T* f = (T*)L.f;
-    const int tz = fused_planes(c, l);
-    if (tz > 0) {
-        // one pass for the pre-smoothing, one for prolongation + post-smoothing
-        MGLevel& C = c->mg[l + 1];
-        const Dims dc{C.nx, C.ny, C.nz};
-        const dim3 grid((unsigned)(d.nx / kSmTX), (unsigned)(d.ny / kSmTY), (unsigned)((d.nz - 1 + tz - 1) / tz));
-        launch_pdl_smem(c->stream, grid, dim3(256), smooth_smem<T, false>(), k_smooth_fused<T, false>,
-                        (const T*)nullptr, (const T*)f, u, (const T*)nullptr, d, dc, h2, tz);
-        run_resid_restrict<T>(c->stream, u, f, (T*)C.f, (T*)C.u, d, dc, (T)(1.0 / (L.h * L.h)), (T)(C.h * C.h));
-        T* uc = vcycle<T>(c, l + 1);
-        T* out = (T*)L.r;
-        launch_pdl_smem(c->stream, grid, dim3(256), smooth_smem<T, true>(), k_smooth_fused<T, true>, (const T*)u,
-                        (const T*)f, out, (const T*)uc, d, dc, h2, tz);
-        c->launches += 3;
-        return out;
-    }
     // pre-smoothing from a zero guess: the first red pass needs no neighbours
     // (on the coarser levels the restriction above has already made it)
     for (int s = 0; s < kPre; ++s)
@@ -2489,24 +2303,6 @@ pic_status mg_setup(pic_ctx* c)
                          (nx / 2) % 2 == 0 && (ny / 2) % 2 == 0;
         if (!can) break;
         nx /= 2; ny /= 2; nz /= 2; h *= 2.0;
-    }
-    // the fused smoothers hold their plane rings in more than 48 KB of shared memory
-    {
-        cudaError_t e = cudaSuccess;
-        if (c->prec == PIC_MIXED) {
-            e = cudaFuncSetAttribute(k_smooth_fused<float, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)smooth_smem<float, false>());
-            if (e == cudaSuccess)
-                e = cudaFuncSetAttribute(k_smooth_fused<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smooth_smem<float, true>());
-        } else {
-            e = cudaFuncSetAttribute(k_smooth_fused<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)smooth_smem<double, false>());
-            if (e == cudaSuccess)
-                e = cudaFuncSetAttribute(k_smooth_fused<double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smooth_smem<double, true>());
-        }
-        if (e != cudaSuccess) return PIC_ECUDA;
     }
     // the levels from mg_tail down run in one thread-block cluster from shared
     // memory: the first level (smallest index) that fits, with the largest
