@@ -502,7 +502,7 @@ def main():
                    "parallelism": "replicas only" if world > 1 else "1 GPU",
                    "l2": "inputs larger than L2 (particle arrays 16 GB mixed / 32 GB FP64)",
                    "tuning": mixed["tuning"],
-                   "tuned": "fixed" if a.no_tune else "autotuned (pic_tune: tile shape, window margin, sort interval)",
+                   "tuned": "fixed" if a.no_tune else "autotuned (pic_tune: tile shape, window margin, sort order, sort interval)",
                    "tol": 1e-10},
         "roofline": push_roofline(mixed, peak, peak_kind, PUSH_PROFILE),
         "poisson": poisson_block(mixed["prof"], mixed["cold"], wl, BYTES_NODE_MIXED, peak, peak_kind, "mixed"),

@@ -190,12 +190,17 @@ pic_status pic_tune_sort(pic_ctx* ctx, int32_t steps_per_candidate, int32_t* cho
  *               deposit window around its tile, for the particles that drift
  *               out of the tile between sorts (in [0, 8]); the window of
  *               (tile + 1 + 2 halo) nodes per axis, 8 bytes each, must fit
- *               96 KB.
+ *               96 KB;
+ *   order       mixed precision: 0 = particles sorted by cell inside each tile
+ *               (the tile's cells row-major), 1 = by tile only (inside a tile
+ *               they keep the order the sort meets them in: a cheaper sort,
+ *               less locality in the push).
  * The FP64 path uses sort_every only. */
 typedef struct {
     int32_t sort_every;
     int32_t tile[3];
     int32_t halo;
+    int32_t order;
 } pic_tuning;
 
 /* Current choices of a run (out: host). */
@@ -209,7 +214,8 @@ pic_status pic_set_tuning(pic_ctx* ctx, const pic_tuning* t);
 /* Autotuner: times candidate choices on the run itself with CUDA events and
  * keeps the fastest, by coordinate search: tile shapes {8x8x8, 16x8x4, 8x8x4,
  * 16x8x8, 16x16x4, 32x8x4} (clipped to the mesh), then margins {1, 2, 3},
- * then sort intervals {2, 3, 4, 5, 6, 8, 10, 14, 20}; each candidate runs at
+ * then the sort order {cell, tile}, then sort intervals {2, 3, 4, 5, 6, 8, 10,
+ * 14, 20}; each candidate runs at
  * least steps_per_candidate steps over whole sort periods after one warm-up
  * period, and the run advances by all of them.  With cache_path (may be NULL)
  * a cached entry for this (device name, mesh, particle count to two digits,
@@ -219,7 +225,8 @@ pic_status pic_set_tuning(pic_ctx* ctx, const pic_tuning* t);
 pic_status pic_tune(pic_ctx* ctx, int32_t steps_per_candidate, const char* cache_path, pic_tuning* chosen);
 
 /* The autotuner's cache file, host only (no GPU): a JSON object with one
- * member per line, "key": {"sort_every": S, "tile": [X, Y, Z], "halo": H}.
+ * member per line, "key": {"sort_every": S, "tile": [X, Y, Z], "halo": H,
+ * "order": O} (an entry without "order" reads as order 0).
  * load: PIC_OK and *out when the file holds `key`, else PIC_EINVAL.  store:
  * adds or replaces `key` (no '"' or newline in it) and rewrites the file
  * through a temporary file in the same directory; PIC_EINVAL when it cannot

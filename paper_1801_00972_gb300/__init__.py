@@ -69,10 +69,11 @@ class pic_run(C.Structure):
 
 
 class pic_tuning(C.Structure):
-    _fields_ = [("sort_every", C.c_int32), ("tile", C.c_int32 * 3), ("halo", C.c_int32)]
+    _fields_ = [("sort_every", C.c_int32), ("tile", C.c_int32 * 3), ("halo", C.c_int32), ("order", C.c_int32)]
 
     def as_dict(self):
-        return {"sort_every": self.sort_every, "tile": [int(x) for x in self.tile], "halo": self.halo}
+        return {"sort_every": self.sort_every, "tile": [int(x) for x in self.tile], "halo": self.halo,
+                "order": self.order}
 
 
 class PicError(RuntimeError):
@@ -188,7 +189,7 @@ def pic_get_tuning(ctx):
 
 def _tuning(d):
     t = pic_tuning()
-    t.sort_every, t.halo = int(d["sort_every"]), int(d["halo"])
+    t.sort_every, t.halo, t.order = int(d["sort_every"]), int(d["halo"]), int(d.get("order", 0))
     for a in range(3):
         t.tile[a] = int(d["tile"][a])
     return t

@@ -1034,7 +1034,6 @@ void drop_graphs(pic_ctx* c)
         }
 }
 
-constexpr size_t kMaxWindowBytes = 96 * 1024;
 
 size_t tuning_window_bytes(const int32_t tile[3], int32_t halo)
 {
@@ -1120,6 +1119,7 @@ pic_status pic_get_tuning(const pic_ctx* c, pic_tuning* out)
     out->sort_every = c->sort_every;
     for (int a = 0; a < 3; ++a) out->tile[a] = c->tile[a];
     out->halo = c->halo;
+    out->order = c->sort_order;
     return PIC_OK;
 }
 
@@ -1136,12 +1136,13 @@ pic_status pic_set_tuning(pic_ctx* c, const pic_tuning* t)
         if (t->tile[a] < 1 || t->tile[a] > n[a] || t->tile[a] > 64)
             return fail(c, PIC_EINVAL, "tuning: tile edges in [1, min(mesh, 64)]");
     if (t->halo < 0 || t->halo > 8) return fail(c, PIC_EINVAL, "tuning: halo in [0, 8]");
+    if (t->order < 0 || t->order > 1) return fail(c, PIC_EINVAL, "tuning: order 0 (cell) or 1 (tile)");
     if (tuning_window_bytes(t->tile, t->halo) > kMaxWindowBytes)
         return fail(c, PIC_EINVAL, "tuning: the deposit window (tile + 1 + 2 halo nodes per axis, 8 B each) "
                                    "exceeds 96 KB");
     c->sort_every = t->sort_every;
     const bool same = t->tile[0] == c->tile[0] && t->tile[1] == c->tile[1] && t->tile[2] == c->tile[2] &&
-                      t->halo == c->halo;
+                      t->halo == c->halo && t->order == c->sort_order;
     if (same) return PIC_OK;
     // new sort keys: wait for queued work, size the key buffers, re-sort both
     // species now (the tile ranges must describe the new order), drop the step
@@ -1173,6 +1174,7 @@ pic_status pic_set_tuning(pic_ctx* c, const pic_tuning* t)
     c->ntiles = ntiles;
     c->nkeys = nkeys;
     c->halo = t->halo;
+    c->sort_order = t->order;
     e = push32_set_window(c);
     if (e != cudaSuccess) return cuda_fail(c, e, "tuning: push window size");
     drop_graphs(c);
@@ -1218,7 +1220,8 @@ pic_status pic_tune(pic_ctx* c, int32_t steps_per_candidate, const char* cache_p
         return PIC_OK;
     };
     float best_ms = 0.f;
-    // coordinate search: tile shape, then window margin, then sort interval
+    // coordinate search: tile shape, then window margin, then sort order, then
+    // sort interval
     if (c->prec == PIC_MIXED) {
         const int shapes[][3] = {{8, 8, 8}, {16, 8, 4}, {8, 8, 4}, {16, 8, 8}, {16, 16, 4}, {32, 8, 4}};
         for (const auto& sh : shapes) {
@@ -1237,6 +1240,13 @@ pic_status pic_tune(pic_ctx* c, int32_t steps_per_candidate, const char* cache_p
             float ms = 0.f;
             if ((st = time_it(t, &ms)) != PIC_OK) break;
             if (ms < best_ms) { best_ms = ms; best = t; }
+        }
+        if (st == PIC_OK) {
+            pic_tuning t = best;
+            t.order = 1 - best.order;
+            float ms = 0.f;
+            st = time_it(t, &ms);
+            if (st == PIC_OK && ms < best_ms) { best_ms = ms; best = t; }
         }
     }
     const int32_t sorts[] = {2, 3, 4, 5, 6, 8, 10, 14, 20};
@@ -1623,7 +1633,7 @@ pic_status pic_fine_moments(pic_ctx* c, int32_t what, double* out, size_t len)
 
 // ---------------------------------------------------------------------------
 // Tuning cache: a JSON object with one member per line,
-//   "<device>|<nx>x<ny>x<nz>|<particles>|<precision>": {"sort_every": S, "tile": [X, Y, Z], "halo": H},
+//   "<device>|<nx>x<ny>x<nz>|<particles>|<precision>": {"sort_every": S, "tile": [X, Y, Z], "halo": H, "order": O},
 // read and rewritten whole by pic_tune_cache_store (last write wins).
 extern "C" pic_status pic_tune_cache_load(const char* path, const char* key, pic_tuning* out)
 {
@@ -1637,8 +1647,11 @@ extern "C" pic_status pic_tune_cache_load(const char* path, const char* key, pic
         const char* at = std::strstr(line, want.c_str());
         if (!at) continue;
         pic_tuning t{};
-        if (std::sscanf(at + want.size(), " {\"sort_every\": %d, \"tile\": [%d, %d, %d], \"halo\": %d}",
-                        &t.sort_every, &t.tile[0], &t.tile[1], &t.tile[2], &t.halo) == 5) {
+        t.order = 0;   // entries written before the sort order was a choice
+        const int got = std::sscanf(at + want.size(),
+                                    " {\"sort_every\": %d, \"tile\": [%d, %d, %d], \"halo\": %d, \"order\": %d}",
+                                    &t.sort_every, &t.tile[0], &t.tile[1], &t.tile[2], &t.halo, &t.order);
+        if (got == 6 || got == 5) {
             *out = t;
             st = PIC_OK;
         }
@@ -1663,8 +1676,8 @@ extern "C" pic_status pic_tune_cache_store(const char* path, const char* key, co
         std::fclose(f);
     }
     char buf[512];
-    std::snprintf(buf, sizeof buf, "%s {\"sort_every\": %d, \"tile\": [%d, %d, %d], \"halo\": %d}", mine.c_str(),
-                  t->sort_every, t->tile[0], t->tile[1], t->tile[2], t->halo);
+    std::snprintf(buf, sizeof buf, "%s {\"sort_every\": %d, \"tile\": [%d, %d, %d], \"halo\": %d, \"order\": %d}",
+                  mine.c_str(), t->sort_every, t->tile[0], t->tile[1], t->tile[2], t->halo, t->order);
     keep.push_back(buf);
     const std::string tmp = std::string(path) + ".tmp";
     std::FILE* f = std::fopen(tmp.c_str(), "w");

@@ -1070,11 +1070,13 @@ void launch_push32(pic_ctx* c)
     c->launches += 8;
 }
 
-cudaError_t push32_set_window(pic_ctx* c)
+// The attribute belongs to the kernel, not to a run: it is raised to the
+// largest window any tiling may ask for (an upper bound only; each launch's
+// occupancy follows the window it actually takes), so that runs with
+// different tilings in one process never lower it below each other's needs.
+cudaError_t push32_set_window(pic_ctx*)
 {
-    const size_t win = sizeof(unsigned long long) * (size_t)(c->tile[0] + 1 + 2 * c->halo) *
-                       (size_t)(c->tile[1] + 1 + 2 * c->halo) * (size_t)(c->tile[2] + 1 + 2 * c->halo);
-    return cudaFuncSetAttribute(k_push32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)win);
+    return cudaFuncSetAttribute(k_push32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxWindowBytes);
 }
 
 void launch_deposit32(pic_ctx* c)

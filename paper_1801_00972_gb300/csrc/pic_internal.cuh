@@ -231,6 +231,7 @@ struct pic_ctx {
     int ntile[3] = {1, 1, 1};                // mixed: tiles per axis
     int64_t ntiles = 0;
     int halo = 2;                            // mixed: deposit window margin around a tile, in cells
+    int sort_order = 0;                      // mixed sort keys: 0 by cell inside the tile, 1 by tile only
     unsigned int* tstart[2] = {nullptr, nullptr};   // mixed: first slot of each tile after the last sort
                                                     // (ntiles + 1 entries; the last = particles sorted)
     std::vector<unsigned int*> scan_tmp;
@@ -316,7 +317,8 @@ void launch_init_plasma(pic_ctx* c, int sp, int64_t n, uint32_t id0, double t_ev
 // particles_mixed.cu
 void launch_efield32(pic_ctx* c);
 void launch_push32(pic_ctx* c);
-cudaError_t push32_set_window(pic_ctx* c);     // dynamic shared memory of the push for the current tiling
+constexpr size_t kMaxWindowBytes = 96 * 1024;  // largest deposit window of the mixed push (shared memory)
+cudaError_t push32_set_window(pic_ctx* c);     // lets the push take windows up to kMaxWindowBytes
 void launch_children32(pic_ctx* c);
 void launch_deposit32(pic_ctx* c);
 void launch_moments32(pic_ctx* c);

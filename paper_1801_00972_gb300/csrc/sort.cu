@@ -17,13 +17,14 @@ constexpr int kScanThreads = 256;
 constexpr int kScanPer = 4;
 constexpr int kScanBlock = kScanThreads * kScanPer;
 
-// sort key geometry: tiles of tx x ty x tz cells, ntx x nty tiles per plane
+// sort key geometry: tiles of tx x ty x tz cells, ntx x nty tiles per plane;
+// by_tile: one key per tile (no order inside it)
 struct KeyGeo {
-    int tx, ty, tz, ntx, nty;
+    int tx, ty, tz, ntx, nty, by_tile;
 };
 
 // mixed: tile index * (cells per tile) + the cell's row-major index inside its
-// tile, or -1 for a dead slot
+// tile (only the tile's first key when by_tile), or -1 for a dead slot
 __device__ __forceinline__ int key_of(const float4& p, const KeyGeo& g)
 {
     const int c = __float_as_int(p.w);   // packed i | j << 10 | k << 20
@@ -31,10 +32,16 @@ __device__ __forceinline__ int key_of(const float4& p, const KeyGeo& g)
     const int i = c & 1023, j = (c >> 10) & 1023, k = c >> 20;
     const int ti = i / g.tx, tj = j / g.ty, tk = k / g.tz;
     const int tile = (tk * g.nty + tj) * g.ntx + ti;
+    if (g.by_tile) return tile * (g.tx * g.ty * g.tz);
     return tile * (g.tx * g.ty * g.tz) + ((k - tk * g.tz) * g.ty + (j - tj * g.ty)) * g.tx + (i - ti * g.tx);
 }
 // FP64: the linear cell index (k*ny + j)*nx + i held in w
 __device__ __forceinline__ int key_of(const double4& p, const KeyGeo&) { return p.w < 0.0 ? -1 : (int)p.w; }
+
+// particles per thread and round of the histogram and scatter loops: their
+// loads are all issued before the first key's atomic, so one round costs one
+// memory latency instead of one per particle
+constexpr int kSortUnroll = 4;
 
 template <typename T4>
 __global__ void k_hist(const T4* __restrict__ pos, const unsigned long long* nslot, int sp, unsigned int* hist,
@@ -42,12 +49,24 @@ __global__ void k_hist(const T4* __restrict__ pos, const unsigned long long* nsl
 {
     const unsigned long long n = nslot[sp];
     const int lane = threadIdx.x & 31;
-    for (unsigned long long q = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; q < n;
-         q += (unsigned long long)gridDim.x * blockDim.x) {
-        const int c = key_of(pos[q], kg);
-        // lanes with the same key (common in nearly sorted input) add once
-        const unsigned m = __match_any_sync(__activemask(), c);
-        if (c >= 0 && lane == __ffs(m) - 1) atomicAdd(hist + c, (unsigned int)__popc(m));
+    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+    // the loop runs on the warp's first index, so every lane of a warp takes the
+    // same rounds (the warp-wide match and shuffle below need all 32)
+    for (unsigned long long w0 = blockIdx.x * (unsigned long long)blockDim.x + (threadIdx.x & ~31u); w0 < n;
+         w0 += kSortUnroll * stride) {
+        const unsigned long long q0 = w0 + (unsigned long long)lane;
+        int key[kSortUnroll];
+#pragma unroll
+        for (int u = 0; u < kSortUnroll; ++u) {
+            const unsigned long long q = q0 + u * stride;
+            key[u] = q < n ? key_of(pos[q], kg) : -1;
+        }
+#pragma unroll
+        for (int u = 0; u < kSortUnroll; ++u) {
+            // lanes with the same key (common in nearly sorted input) add once
+            const unsigned m = __match_any_sync(0xffffffffu, key[u]);
+            if (key[u] >= 0 && lane == __ffs(m) - 1) atomicAdd(hist + key[u], (unsigned int)__popc(m));
+        }
     }
 }
 
@@ -106,25 +125,46 @@ __global__ void k_scatter(const T4* __restrict__ pos, const T4* __restrict__ vel
 {
     const unsigned long long n = nslot[sp];
     const int lane = threadIdx.x & 31;
-    for (unsigned long long q = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; q < n;
-         q += (unsigned long long)gridDim.x * blockDim.x) {
-        const T4 p = pos[q];
-        const int c = key_of(p, kg);
-        // one cursor atomic per group of lanes with the same key; the group's
-        // lanes take consecutive slots in lane order
-        const unsigned m = __match_any_sync(__activemask(), c);
-        const int leader = __ffs(m) - 1;
-        unsigned int base = 0;
-        if (c >= 0 && lane == leader) base = atomicAdd(cursor + c, (unsigned int)__popc(m));
-        base = __shfl_sync(m, base, leader);
-        if (c < 0) continue;
-        const unsigned int d = base + (unsigned int)__popc(m & ((1u << lane) - 1u));
-        pos_out[d] = p;
-        vel_out[d] = vel[q];
-        if (md_next) {
-            const int pc = __float_as_int(p.w);   // mixed: packed cell
-            if (cell_ng[((pc >> 20) * ny + ((pc >> 10) & 1023)) * nx + (pc & 1023)] != 0)
-                md_next[atomicAdd(next_n, 1u)] = d;
+    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+    // the loop runs on the warp's first index, so every lane of a warp takes the
+    // same rounds (the warp-wide match and shuffle below need all 32)
+    for (unsigned long long w0 = blockIdx.x * (unsigned long long)blockDim.x + (threadIdx.x & ~31u); w0 < n;
+         w0 += kSortUnroll * stride) {
+        const unsigned long long q0 = w0 + (unsigned long long)lane;
+        T4 p[kSortUnroll], v[kSortUnroll];
+        int key[kSortUnroll];
+        unsigned int dst[kSortUnroll];
+#pragma unroll
+        for (int u = 0; u < kSortUnroll; ++u) {
+            const unsigned long long q = q0 + u * stride;
+            if (q < n) {
+                p[u] = pos[q];
+                v[u] = vel[q];
+            }
+            key[u] = q < n ? key_of(p[u], kg) : -1;
+        }
+#pragma unroll
+        for (int u = 0; u < kSortUnroll; ++u) {
+            // one cursor atomic per group of lanes with the same key; the
+            // group's lanes take consecutive slots in lane order
+            const unsigned m = __match_any_sync(0xffffffffu, key[u]);
+            const int leader = __ffs(m) - 1;
+            unsigned int base = 0;
+            if (key[u] >= 0 && lane == leader) base = atomicAdd(cursor + key[u], (unsigned int)__popc(m));
+            dst[u] = base;
+            dst[u] = __shfl_sync(0xffffffffu, dst[u], leader) + (unsigned int)__popc(m & ((1u << lane) - 1u));
+        }
+#pragma unroll
+        for (int u = 0; u < kSortUnroll; ++u) {
+            if (key[u] < 0) continue;
+            const unsigned int d = dst[u];
+            pos_out[d] = p[u];
+            vel_out[d] = v[u];
+            if (md_next) {
+                const int pc = __float_as_int(p[u].w);   // mixed: packed cell
+                if (cell_ng[((pc >> 20) * ny + ((pc >> 10) & 1023)) * nx + (pc & 1023)] != 0)
+                    md_next[atomicAdd(next_n, 1u)] = d;
+            }
         }
     }
 }
@@ -185,7 +225,7 @@ size_t sort_scratch_setup(pic_ctx* c)
 void sort_particles(pic_ctx* c, int sp)
 {
     const size_t nk = c->nkeys;
-    const KeyGeo kg{c->tile[0], c->tile[1], c->tile[2], c->ntile[0], c->ntile[1]};
+    const KeyGeo kg{c->tile[0], c->tile[1], c->tile[2], c->ntile[0], c->ntile[1], c->sort_order};
     cudaMemsetAsync(c->cursor, 0, sizeof(unsigned int) * nk, c->stream);
     const int grid = grid_for(c->cap[sp], 256, 152 * 8);
     if (c->prec == PIC_MIXED)
