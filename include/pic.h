@@ -194,7 +194,8 @@ pic_status pic_tune_sort(pic_ctx* ctx, int32_t steps_per_candidate, int32_t* cho
  *   order       mixed precision: 0 = particles sorted by cell inside each tile
  *               (the tile's cells row-major), 1 = by tile only (inside a tile
  *               they keep the order the sort meets them in: a cheaper sort,
- *               less locality in the push).
+ *               less locality in the push), 2 = by block of 2 x 2 x 2 cells
+ *               inside the tile (in between).
  * The FP64 path uses sort_every only. */
 typedef struct {
     int32_t sort_every;
@@ -214,7 +215,7 @@ pic_status pic_set_tuning(pic_ctx* ctx, const pic_tuning* t);
 /* Autotuner: times candidate choices on the run itself with CUDA events and
  * keeps the fastest, by coordinate search: tile shapes {8x8x8, 16x8x4, 8x8x4,
  * 16x8x8, 16x16x4, 32x8x4} (clipped to the mesh), then margins {1, 2, 3},
- * then the sort order {cell, tile}, then sort intervals {2, 3, 4, 5, 6, 8, 10,
+ * then the sort order {cell, tile, 2x2x2 blocks}, then sort intervals {2, 3, 4, 5, 6, 8, 10,
  * 14, 20}; each candidate runs at
  * least steps_per_candidate steps over whole sort periods after one warm-up
  * period, and the run advances by all of them.  With cache_path (may be NULL)

@@ -1136,7 +1136,8 @@ pic_status pic_set_tuning(pic_ctx* c, const pic_tuning* t)
         if (t->tile[a] < 1 || t->tile[a] > n[a] || t->tile[a] > 64)
             return fail(c, PIC_EINVAL, "tuning: tile edges in [1, min(mesh, 64)]");
     if (t->halo < 0 || t->halo > 8) return fail(c, PIC_EINVAL, "tuning: halo in [0, 8]");
-    if (t->order < 0 || t->order > 1) return fail(c, PIC_EINVAL, "tuning: order 0 (cell) or 1 (tile)");
+    if (t->order < 0 || t->order > 2)
+        return fail(c, PIC_EINVAL, "tuning: order 0 (cell), 1 (tile) or 2 (2x2x2-cell blocks)");
     if (tuning_window_bytes(t->tile, t->halo) > kMaxWindowBytes)
         return fail(c, PIC_EINVAL, "tuning: the deposit window (tile + 1 + 2 halo nodes per axis, 8 B each) "
                                    "exceeds 96 KB");
@@ -1241,9 +1242,11 @@ pic_status pic_tune(pic_ctx* c, int32_t steps_per_candidate, const char* cache_p
             if ((st = time_it(t, &ms)) != PIC_OK) break;
             if (ms < best_ms) { best_ms = ms; best = t; }
         }
-        if (st == PIC_OK) {
+        const int32_t order0 = best.order;
+        for (int32_t o = 0; o <= 2 && st == PIC_OK; ++o) {
+            if (o == order0) continue;
             pic_tuning t = best;
-            t.order = 1 - best.order;
+            t.order = o;
             float ms = 0.f;
             st = time_it(t, &ms);
             if (st == PIC_OK && ms < best_ms) { best_ms = ms; best = t; }

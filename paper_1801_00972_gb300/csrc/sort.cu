@@ -18,13 +18,15 @@ constexpr int kScanPer = 4;
 constexpr int kScanBlock = kScanThreads * kScanPer;
 
 // sort key geometry: tiles of tx x ty x tz cells, ntx x nty tiles per plane;
-// by_tile: one key per tile (no order inside it)
+// order: 0 one key per cell, 1 one key per tile (no order inside it), 2 one key
+// per block of 2 x 2 x 2 cells inside the tile
 struct KeyGeo {
-    int tx, ty, tz, ntx, nty, by_tile;
+    int tx, ty, tz, ntx, nty, order;
 };
 
 // mixed: tile index * (cells per tile) + the cell's row-major index inside its
-// tile (only the tile's first key when by_tile), or -1 for a dead slot
+// tile (or of its block of 2 x 2 x 2 cells, or only the tile's first key: the
+// sort order), or -1 for a dead slot
 __device__ __forceinline__ int key_of(const float4& p, const KeyGeo& g)
 {
     const int c = __float_as_int(p.w);   // packed i | j << 10 | k << 20
@@ -32,7 +34,12 @@ __device__ __forceinline__ int key_of(const float4& p, const KeyGeo& g)
     const int i = c & 1023, j = (c >> 10) & 1023, k = c >> 20;
     const int ti = i / g.tx, tj = j / g.ty, tk = k / g.tz;
     const int tile = (tk * g.nty + tj) * g.ntx + ti;
-    if (g.by_tile) return tile * (g.tx * g.ty * g.tz);
+    if (g.order == 1) return tile * (g.tx * g.ty * g.tz);
+    if (g.order == 2) {
+        const int bx = (g.tx + 1) >> 1, by = (g.ty + 1) >> 1;
+        return tile * (g.tx * g.ty * g.tz) + (((k - tk * g.tz) >> 1) * by + ((j - tj * g.ty) >> 1)) * bx +
+               ((i - ti * g.tx) >> 1);
+    }
     return tile * (g.tx * g.ty * g.tz) + ((k - tk * g.tz) * g.ty + (j - tj * g.ty)) * g.tx + (i - ti * g.tx);
 }
 // FP64: the linear cell index (k*ny + j)*nx + i held in w

@@ -186,7 +186,7 @@ def test_sort_autotune_does_not_change_results(prec):
 def test_tuned_run_is_bit_identical_to_untuned(tmp_path):
     """pic_tune (tile shape, deposit-window margin, sort order, sort interval)
     changes speed only: a run with the tuned choices, and ones with other
-    explicit choices (one of them sorting by tile only),
+    explicit choices (one sorting by tile only, one by blocks of 2 x 2 x 2 cells),
     reach the same particles, charge and grain counts bit for bit as a run
     with the defaults; a second tuning with the cache file applies the cached
     entry without stepping the run."""
@@ -200,7 +200,7 @@ def test_tuned_run_is_bit_identical_to_untuned(tmp_path):
     assert again.tune(4, cache_path=cache) == chosen
     assert again.step_index == 0
     again.close()
-    runs = [P.Run(wl, parts, prec=P.PIC_MIXED, stream=_stream(), sort_every=5) for _ in range(4)]
+    runs = [P.Run(wl, parts, prec=P.PIC_MIXED, stream=_stream(), sort_every=5) for _ in range(5)]
     runs[1].set_tuning(chosen)
     # a window of 23 x 23 x 11 nodes (46.5 KB, past the 48 KB default with the static shared memory)
     runs[2].set_tuning({"sort_every": 3, "tile": [16, 16, 4], "halo": 3, "order": 0})
@@ -208,6 +208,9 @@ def test_tuned_run_is_bit_identical_to_untuned(tmp_path):
     # particles ordered by tile only
     runs[3].set_tuning({"sort_every": 4, "tile": [8, 8, 8], "halo": 2, "order": 1})
     assert runs[3].tuning()["order"] == 1
+    # by blocks of 2 x 2 x 2 cells, with a tile of odd edges
+    runs[4].set_tuning({"sort_every": 2, "tile": [5, 8, 3], "halo": 2, "order": 2})
+    assert runs[4].tuning()["order"] == 2
     for r in runs:
         r.step(13)
     a = runs[0]
