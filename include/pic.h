@@ -71,6 +71,9 @@ typedef enum { PIC_FP64 = 0, PIC_MIXED = 1 } pic_precision;
 #define PIC_F_NO_GRAPH   16   /* pic_step launches kernels one by one and runs the
                                  Poisson loop from the host (for profilers that
                                  cannot see inside CUDA graphs); same results */
+#define PIC_F_STAGE_COPY 128  /* pic_init copies the particle arrays to device
+                                 scratch in chunks even where the device could read
+                                 them in place (same records; for testing) */
 #define PIC_F_F64_RESIDUAL 64 /* mixed precision only: the refinement residual of the
                                  Poisson solve in FP64 arithmetic instead of the
                                  double-float (two-float) arithmetic; the potential is
@@ -142,7 +145,13 @@ typedef struct {
 
 /* Create a run: copies every input to the device, deposits rho_0 (particles
  * plus grain charges, Sec. III), precomputes each grain's unit-charge mesh
- * field (Eq. 5) and solves phi_0 at t = 0.  On success *out owns the run. */
+ * field (Eq. 5) and solves phi_0 at t = 0.  On success *out owns the run.
+ * The particle arrays are converted into the run's records on the device,
+ * read in place where the device reads pageable host memory through the
+ * host's page tables (a coherent CPU-GPU link), else copied in chunks of 2^24
+ * particles; a particle outside the box or non-finite gives PIC_EINVAL after
+ * the device has checked it (the other arguments are checked first, on the
+ * host). */
 pic_status pic_init(const pic_mesh* mesh, const pic_electrodes* el, const pic_gas* gas,
                     const pic_grains* grains, const pic_run* run, void* cuda_stream,
                     pic_ctx** out);

@@ -26,6 +26,7 @@ STATUS = {0: "PIC_OK", 1: "PIC_EINVAL", 2: "PIC_ENOMEM", 3: "PIC_ECUDA", 4: "PIC
           5: "PIC_ENONFINITE", 6: "PIC_ENOTCONV", 7: "PIC_ETIMEOUT"}
 PIC_FP64, PIC_MIXED = 0, 1
 PIC_F_NO_MCC, PIC_F_IONS_FROZEN, PIC_F_MOMENTS, PIC_F_NO_GRAPH, PIC_F_COULOMB, PIC_F_F64_RESIDUAL = 1, 2, 8, 16, 32, 64
+PIC_F_STAGE_COPY = 128
 COUNTERS = ("lost_bot_e", "lost_bot_i", "lost_top_e", "lost_top_i", "abs_e", "abs_i",
             "e_el", "e_exc", "e_ion", "i_el", "i_cx", "err", "pushed")
 PIC_C_N = len(COUNTERS)

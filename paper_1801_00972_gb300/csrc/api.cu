@@ -61,23 +61,6 @@ namespace {
 
 thread_local std::string g_init_error;
 
-// fn(lo, hi) over [0, n) in contiguous chunks on the host's cores (the host
-// side of pic_init touches every particle: validation and layout conversion)
-template <class F>
-void host_parallel(int64_t n, F&& fn)
-{
-    const int64_t hw = std::max<int64_t>(1, std::min<int64_t>(64, (int64_t)std::thread::hardware_concurrency()));
-    const int64_t nt = std::max<int64_t>(1, std::min<int64_t>(hw, n / 65536));
-    if (nt <= 1) {
-        fn((int64_t)0, n);
-        return;
-    }
-    std::vector<std::thread> th;
-    th.reserve((size_t)nt);
-    for (int64_t t = 0; t < nt; ++t) th.emplace_back([&fn, t, nt, n] { fn(n * t / nt, n * (t + 1) / nt); });
-    for (auto& x : th) x.join();
-}
-
 pic_status fail(pic_ctx* c, pic_status s, const std::string& msg)
 {
     if (c) c->err = msg;
@@ -345,17 +328,7 @@ pic_status init_run(const pic_mesh* mesh, const pic_electrodes* el, const pic_ga
         }
         if (run->n[sp] > 0 && (!run->x_host[sp] || !run->v_host[sp] || !run->id_host[sp]))
             return fail(nullptr, PIC_EINVAL, "run: NULL particle arrays");
-        std::atomic<bool> bad{false};
-        host_parallel(run->n[sp], [&](int64_t lo, int64_t hi) {
-            for (int64_t q = lo; q < hi && !bad.load(std::memory_order_relaxed); ++q) {
-                const double* x = run->x_host[sp] + 3 * q;
-                const double* v = run->v_host[sp] + 3 * q;
-                if (!finite_all(x, 3) || !finite_all(v, 3) || x[0] < 0 || x[0] >= Lx || x[1] < 0 || x[1] >= Ly ||
-                    x[2] < 0 || x[2] > Lz)
-                    bad.store(true, std::memory_order_relaxed);
-            }
-        });
-        if (bad.load()) return fail(nullptr, PIC_EINVAL, "run: particle outside the box or non-finite");
+        // each particle is checked (finite, inside the box) where it is converted, on the device
     }
     if (t_ev && run->n[0] + run->n[1] > 0xFFFFFFFFLL)
         return fail(nullptr, PIC_EINVAL, "plasma: n_e + n_i must fit the 32-bit particle ids");
@@ -444,6 +417,7 @@ pic_status init_run(const pic_mesh* mesh, const pic_electrodes* el, const pic_ga
     }
     c->d_nslot = (unsigned long long*)dev_alloc(c, 2 * sizeof(unsigned long long));
     c->d_cnt = (unsigned long long*)dev_alloc(c, PIC_C_N * sizeof(unsigned long long));
+    c->d_live = (unsigned long long*)dev_alloc(c, 2 * sizeof(unsigned long long));
     c->d_err = (int*)dev_alloc(c, sizeof(int));
     c->d_nch = (unsigned long long*)dev_alloc(c, sizeof(unsigned long long));
     c->d_next_id = (unsigned int*)dev_alloc(c, sizeof(unsigned int));
@@ -544,7 +518,7 @@ pic_status init_run(const pic_mesh* mesh, const pic_electrodes* el, const pic_ga
         }
     }
     ok = ok && c->d_step && c->d_iters && c->d_res && c->d_solve_flag && c->d_iter_total && c->d_vb_last;
-    ok = ok && c->d_nslot && c->d_cnt && c->d_err && c->d_nch && c->d_next_id && c->d_child && c->rq && c->phi &&
+    ok = ok && c->d_nslot && c->d_cnt && c->d_live && c->d_err && c->d_nch && c->d_next_id && c->d_child && c->rq && c->phi &&
          c->phi_alt && c->f64 && (c->e32 || c->e64) && c->d_norm && c->xs64 && c->xs32 && c->gpos && c->grad &&
          c->gcell && c->gq && c->gabs && c->gtab && c->gtab32 && c->gq32 && c->goff32 && c->gr2_32 && c->cell_ng &&
          c->cell_g && c->cursor;
@@ -558,55 +532,63 @@ pic_status init_run(const pic_mesh* mesh, const pic_electrodes* el, const pic_ga
     }
 
     // ---- upload inputs
+    // The caller's particle arrays are converted into the run's records on the
+    // device (k_stage_particles, which also checks them).  Where the device reads
+    // pageable host memory through the host's page tables (a coherent CPU-GPU
+    // link), the kernel reads the arrays in place; elsewhere they go to device
+    // scratch chunk by chunk first.
     unsigned int max_id = 0;
     bool any = false;
     unsigned long long nslot[2] = {(unsigned long long)run->n[0], (unsigned long long)run->n[1]};
-    for (int sp = 0; sp < 2 && !t_ev; ++sp) {
-        const int64_t n = run->n[sp];
-        std::unique_ptr<char[]> buf(new (std::nothrow) char[2 * psz * (size_t)std::max<int64_t>(n, 1)]);
-        if (!buf) { destroy(c); return fail(nullptr, PIC_ENOMEM, "host staging buffer"); }
-        char* P = buf.get();
-        char* V = buf.get() + psz * std::max<int64_t>(n, 1);
-        std::mutex id_mu;
-        host_parallel(n, [&](int64_t lo, int64_t hi) {
-          uint32_t mx = 0;
-          bool got = false;
-          for (int64_t q = lo; q < hi; ++q) {
-            const double* x = run->x_host[sp] + 3 * q;
-            const double* v = run->v_host[sp] + 3 * q;
-            const uint32_t id = run->id_host[sp][q];
-            if (!got || id > mx) { mx = id; got = true; }
-            int ci[3];
-            double f[3];
-            const int nn[3] = {nx, ny, nz};
-            for (int a = 0; a < 3; ++a) locate1(x[a], mesh->dx, nn[a], ci[a], f[a]);
-            const int cell = mixed ? (ci[0] | (ci[1] << 10) | (ci[2] << 20)) : (ci[2] * ny + ci[1]) * nx + ci[0];
-            if (mixed) {
-                float4 p, w;
-                float o[3];
-                for (int a = 0; a < 3; ++a) o[a] = std::min((float)f[a], 0.99999994f);
-                p = make_float4(o[0], o[1], o[2], 0.f);
-                std::memcpy(&p.w, &cell, 4);
-                const double s = run->dt / mesh->dx;
-                w = make_float4((float)(v[0] * s), (float)(v[1] * s), (float)(v[2] * s), 0.f);
-                std::memcpy(&w.w, &id, 4);
-                std::memcpy(P + psz * q, &p, psz);
-                std::memcpy(V + psz * q, &w, psz);
-            } else {
-                const double4 p = make_double4(x[0], x[1], x[2], (double)cell);
-                const double4 w = make_double4(v[0], v[1], v[2], (double)id);
-                std::memcpy(P + psz * q, &p, psz);
-                std::memcpy(V + psz * q, &w, psz);
+    if (!t_ev && (run->n[0] > 0 || run->n[1] > 0)) {
+        int dev = 0, pma = 0, ats = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&pma, cudaDevAttrPageableMemoryAccess, dev);
+        cudaDeviceGetAttribute(&ats, cudaDevAttrPageableMemoryAccessUsesHostPageTables, dev);
+        const bool direct = pma && ats && !(run->flags & PIC_F_STAGE_COPY);
+        const int64_t nmax = std::max(run->n[0], run->n[1]);
+        const int64_t chunk = direct ? nmax : std::min<int64_t>(nmax, (int64_t)1 << 24);
+        unsigned int* flags = nullptr;   // [bad, largest id]
+        double* sx = nullptr;
+        double* sv = nullptr;
+        uint32_t* sid = nullptr;
+        cudaError_t e = cudaMalloc(&flags, 2 * sizeof(unsigned int));
+        if (e == cudaSuccess) e = cudaMemsetAsync(flags, 0, 2 * sizeof(unsigned int), c->stream);
+        if (e == cudaSuccess && !direct) e = cudaMalloc(&sx, 3 * sizeof(double) * (size_t)chunk);
+        if (e == cudaSuccess && !direct) e = cudaMalloc(&sv, 3 * sizeof(double) * (size_t)chunk);
+        if (e == cudaSuccess && !direct) e = cudaMalloc(&sid, sizeof(uint32_t) * (size_t)chunk);
+        for (int sp = 0; sp < 2 && e == cudaSuccess; ++sp)
+            for (int64_t q0 = 0; q0 < run->n[sp] && e == cudaSuccess; q0 += chunk) {
+                const int64_t m = std::min(chunk, run->n[sp] - q0);
+                const double* x = run->x_host[sp] + 3 * q0;
+                const double* v = run->v_host[sp] + 3 * q0;
+                const uint32_t* id = run->id_host[sp] + q0;
+                if (!direct) {
+                    e = cudaMemcpyAsync(sx, x, 3 * sizeof(double) * (size_t)m, cudaMemcpyHostToDevice, c->stream);
+                    if (e == cudaSuccess)
+                        e = cudaMemcpyAsync(sv, v, 3 * sizeof(double) * (size_t)m, cudaMemcpyHostToDevice, c->stream);
+                    if (e == cudaSuccess)
+                        e = cudaMemcpyAsync(sid, id, sizeof(uint32_t) * (size_t)m, cudaMemcpyHostToDevice, c->stream);
+                    x = sx;
+                    v = sv;
+                    id = sid;
+                }
+                if (e == cudaSuccess) launch_stage_particles(c, sp, x, v, id, m, q0, flags, flags + 1);
+                if (e == cudaSuccess) e = cudaGetLastError();
+                // the scratch is reused by the next chunk
+                if (e == cudaSuccess && !direct) e = cudaStreamSynchronize(c->stream);
             }
-          }
-          if (got) {
-              std::lock_guard<std::mutex> lk(id_mu);
-              if (!any || mx > max_id) { max_id = mx; any = true; }
-          }
-        });
-        cudaError_t e = cudaMemcpy(c->pos[sp], P, psz * n, cudaMemcpyHostToDevice);
-        if (e == cudaSuccess) e = cudaMemcpy(c->vel[sp], V, psz * n, cudaMemcpyHostToDevice);
+        unsigned int hf[2] = {0, 0};
+        if (e == cudaSuccess) e = cudaMemcpyAsync(hf, flags, sizeof hf, cudaMemcpyDeviceToHost, c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+        cudaFree(flags);
+        cudaFree(sx);
+        cudaFree(sv);
+        cudaFree(sid);
         if (e != cudaSuccess) { destroy(c); return cuda_fail(nullptr, e, "particle upload"); }
+        if (hf[0]) { destroy(c); return fail(nullptr, PIC_EINVAL, "run: particle outside the box or non-finite"); }
+        max_id = hf[1];
+        any = true;
     }
     const unsigned int next_id = t_ev ? (unsigned int)(run->n[0] + run->n[1]) : any ? max_id + 1 : 0;
     std::vector<float> xs32(5 * (size_t)c->n_xs);
@@ -1394,13 +1376,14 @@ pic_status pic_counts(pic_ctx* c, int64_t* n_live, int64_t* counters)
     pic_status k = check(c);
     if (k != PIC_OK) return k;
     if (n_live) {
-        for (int sp = 0; sp < 2; ++sp) {
-            std::vector<double> x, v;
-            std::vector<uint32_t> id;
-            k = fetch(c, sp, x, v, id);
-            if (k != PIC_OK) return k;
-            n_live[sp] = (int64_t)id.size();
-        }
+        // counted on the device (the records stay there)
+        count_live(c);
+        unsigned long long h[2] = {0, 0};
+        cudaError_t e = cudaMemcpyAsync(h, c->d_live, sizeof h, cudaMemcpyDeviceToHost, c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+        if (e != cudaSuccess) return cuda_fail(c, e, "live count");
+        n_live[0] = (int64_t)h[0];
+        n_live[1] = (int64_t)h[1];
     }
     if (counters) {
         const cudaError_t e = cudaMemcpy(counters, c->d_cnt, sizeof(int64_t) * PIC_C_N, cudaMemcpyDeviceToHost);

@@ -698,7 +698,83 @@ __global__ void k_init_plasma(const InitP p)
         }
     }
 }
+
+// Caller-supplied particles (x, v in SI as 3 doubles each, uint32 ids) into the
+// run's records, particle q of the arrays to slot q0 + q: the same conversion
+// as k_init_plasma's (cell and in-cell offset by `locate`; mixed velocities in
+// cells per step), checked as pic_init requires (finite, 0 <= x < Lx,
+// 0 <= y < Ly, 0 <= z <= Lz); a bad particle sets *bad.  *max_id takes the
+// largest id.  The arrays may be host memory the device reads directly.
+struct StageP {
+    Geo g;
+    double vs;
+    const double* x;
+    const double* v;
+    const uint32_t* id;
+    int64_t n, q0;
+    double4* pos64;
+    double4* vel64;
+    float4* pos32;
+    float4* vel32;
+    unsigned int* bad;
+    unsigned int* max_id;
+};
+
+__global__ void k_stage_particles(const StageP p)
+{
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < p.n; q += (int64_t)gridDim.x * blockDim.x) {
+        const double x[3] = {p.x[3 * q], p.x[3 * q + 1], p.x[3 * q + 2]};
+        const double v[3] = {p.v[3 * q], p.v[3 * q + 1], p.v[3 * q + 2]};
+        const uint32_t id = p.id[q];
+        atomicMax(p.max_id, id);
+        bool ok = true;
+        for (int a = 0; a < 3; ++a) ok = ok && isfinite(x[a]) && isfinite(v[a]);
+        ok = ok && x[0] >= 0.0 && x[0] < p.g.Lx && x[1] >= 0.0 && x[1] < p.g.Ly && x[2] >= 0.0 && x[2] <= p.g.Lz;
+        if (!ok) {
+            atomicOr(p.bad, 1u);
+            continue;
+        }
+        int c[3];
+        double f[3];
+        locate(p.g, x, c, f);
+        const int64_t d = p.q0 + q;
+        if (p.pos64) {
+            p.pos64[d] = make_double4(x[0], x[1], x[2], (double)cell_of(p.g, c));
+            p.vel64[d] = make_double4(v[0], v[1], v[2], (double)id);
+        } else {
+            float o[3];
+            for (int a = 0; a < 3; ++a) o[a] = fminf((float)f[a], 0.99999994f);
+            const int cell = c[0] | (c[1] << 10) | (c[2] << 20);
+            p.pos32[d] = make_float4(o[0], o[1], o[2], __int_as_float(cell));
+            p.vel32[d] = make_float4((float)(v[0] * p.vs), (float)(v[1] * p.vs), (float)(v[2] * p.vs),
+                                     __uint_as_float(id));
+        }
+    }
+}
 }  // namespace
+
+void launch_stage_particles(pic_ctx* c, int sp, const double* x, const double* v, const uint32_t* id, int64_t n,
+                            int64_t q0, unsigned int* bad, unsigned int* max_id)
+{
+    if (n <= 0) return;
+    StageP p;
+    p.g = Geo{c->nx, c->ny, c->nz, c->dx, c->Lx, c->Ly, c->Lz};
+    p.vs = c->dt / c->dx;
+    p.x = x;
+    p.v = v;
+    p.id = id;
+    p.n = n;
+    p.q0 = q0;
+    const bool mixed = c->prec == PIC_MIXED;
+    p.pos64 = mixed ? nullptr : (double4*)c->pos[sp];
+    p.vel64 = mixed ? nullptr : (double4*)c->vel[sp];
+    p.pos32 = mixed ? (float4*)c->pos[sp] : nullptr;
+    p.vel32 = mixed ? (float4*)c->vel[sp] : nullptr;
+    p.bad = bad;
+    p.max_id = max_id;
+    k_stage_particles<<<grid_for(n, 256, 152 * 16), 256, 0, c->stream>>>(p);
+    c->launches += 1;
+}
 
 void launch_push64(pic_ctx* c)
 {

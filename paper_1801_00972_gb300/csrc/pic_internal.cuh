@@ -168,6 +168,7 @@ struct pic_ctx {
     void* vel_alt[2] = {nullptr, nullptr};
     unsigned long long* d_nslot = nullptr;   // [2] slots in use (live + holes since the last sort)
     unsigned long long* d_cnt = nullptr;     // [PIC_C_N]
+    unsigned long long* d_live = nullptr;    // [2] live particles, counted on demand (pic_counts)
     int* d_err = nullptr;
     unsigned long long* d_nch = nullptr;     // children this step
     unsigned int* d_next_id = nullptr;
@@ -313,6 +314,8 @@ void launch_grains(pic_ctx* c);                  // Q from counts, grain CIC int
 void launch_grain_table(pic_ctx* c, int g);      // E of phi on grain g's 4x4x4 region nodes
 // the initial plasma of species sp drawn from the seed (ids id0 ..), either layout
 void launch_init_plasma(pic_ctx* c, int sp, int64_t n, uint32_t id0, double t_ev);
+void launch_stage_particles(pic_ctx* c, int sp, const double* x, const double* v, const uint32_t* id, int64_t n,
+                            int64_t q0, unsigned int* bad, unsigned int* max_id);   // caller particles into records
 
 // particles_mixed.cu
 void launch_efield32(pic_ctx* c);
@@ -326,6 +329,7 @@ void launch_moments_phi(pic_ctx* c);
 
 // sort.cu
 void sort_particles(pic_ctx* c, int sp);
+void count_live(pic_ctx* c);                         // live records of both species into d_live
 void scan_cells(pic_ctx* c, unsigned int* data);   // exclusive scan of one value per cell, in place
 
 // diagnostics.cu (built without fused multiply-add)

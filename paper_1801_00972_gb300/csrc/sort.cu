@@ -176,6 +176,21 @@ __global__ void k_scatter(const T4* __restrict__ pos, const T4* __restrict__ vel
     }
 }
 
+// live records (key >= 0) among the slots in use, one add per warp
+template <typename T4>
+__global__ void k_count_live(const T4* __restrict__ pos, const unsigned long long* nslot, int sp,
+                             unsigned long long* live)
+{
+    const unsigned long long n = nslot[sp];
+    const KeyGeo kg{1, 1, 1, 1, 1, 1};
+    unsigned int mine = 0;
+    for (unsigned long long q = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; q < n;
+         q += (unsigned long long)gridDim.x * blockDim.x)
+        mine += key_of(pos[q], kg) >= 0 ? 1u : 0u;
+    const unsigned int w = __reduce_add_sync(0xffffffffu, mine);
+    if ((threadIdx.x & 31) == 0 && w) atomicAdd(live + sp, (unsigned long long)w);
+}
+
 __global__ void k_set_nslot(unsigned long long* nslot, int sp, const unsigned int* total)
 {
     nslot[sp] = *total;
@@ -227,6 +242,19 @@ size_t sort_scratch_setup(pic_ctx* c)
         n = nb;
     }
     return bytes + 1;
+}
+
+void count_live(pic_ctx* c)
+{
+    cudaMemsetAsync(c->d_live, 0, 2 * sizeof(unsigned long long), c->stream);
+    for (int sp = 0; sp < 2; ++sp) {
+        const int grid = grid_for(c->cap[sp], 256, 152 * 8);
+        if (c->prec == PIC_MIXED)
+            k_count_live<float4><<<grid, 256, 0, c->stream>>>((const float4*)c->pos[sp], c->d_nslot, sp, c->d_live);
+        else
+            k_count_live<double4><<<grid, 256, 0, c->stream>>>((const double4*)c->pos[sp], c->d_nslot, sp, c->d_live);
+    }
+    c->launches += 2;
 }
 
 void sort_particles(pic_ctx* c, int sp)

@@ -61,7 +61,7 @@ def _args(wl, n=10):
     return mesh, el, gas, grains, run, keep
 
 
-@pytest.mark.parametrize("bad", ["nx_odd", "dx", "dt", "tol", "capacity", "grain_at_electrode", "particle_out",
+@pytest.mark.parametrize("bad", ["nx_odd", "dx", "dt", "tol", "capacity", "grain_at_electrode",
                                  "xs_nan", "prec", "coulomb_log", "phases_without_moments", "fine_partial",
                                  "fine_h"])
 def test_invalid_arguments_rejected(lib, bad):
@@ -80,8 +80,6 @@ def test_invalid_arguments_rejected(lib, bad):
     elif bad == "grain_at_electrode":
         wl.grain_pos[0, 2] = 0.5 * wl.dx
         mesh, el, gas, grains, run, keep = _args(wl)
-    elif bad == "particle_out":
-        keep[3][0] = -1e-6           # first electron position
     elif bad == "xs_nan":
         keep[0][0, 3] = np.nan
     elif bad == "prec":

@@ -1,8 +1,8 @@
 """Failure detection without faulting the GPU: every failure is made on the
 host (too little particle capacity, a NaN written into the potential, too few
-solver iterations); the kernels latch an error word that the next
-synchronising call returns as a status, and the context stays usable for
-queries."""
+solver iterations, a particle outside the box or NaN in pic_init's arrays);
+the kernels latch an error word that the next synchronising call returns as a
+status, and the context stays usable for queries."""
 import math
 
 import numpy as np
@@ -70,3 +70,38 @@ def test_solver_not_converged_is_reported():
     with pytest.raises(P.PicError) as e:
         P.Run(wl, I.sample_particles(wl), prec=P.PIC_MIXED, stream=_stream(), tol=1e-15, max_cycles=1).step(2)
     assert e.value.status == P.PIC_ENOTCONV
+
+
+@pytest.mark.parametrize("copy", [0, P.PIC_F_STAGE_COPY])
+@pytest.mark.parametrize("what", ["outside", "nan"])
+def test_bad_particle_rejected_by_the_device_check(what, copy):
+    wl = I.small(n_e=3000, n_i=3000, grains=1)
+    parts = I.sample_particles(wl)
+    x = parts[1][0].copy()
+    if what == "outside":
+        x[1234, 2] = -1e-7
+    else:
+        x[1234, 0] = np.nan
+    parts[1] = (x, parts[1][1], parts[1][2])
+    with pytest.raises(P.PicError) as e:
+        P.Run(wl, parts, prec=P.PIC_MIXED, flags=copy, stream=_stream())
+    assert e.value.status == P.PIC_EINVAL
+    assert "outside the box or non-finite" in str(e.value)
+
+
+@pytest.mark.parametrize("prec", [P.PIC_FP64, P.PIC_MIXED])
+def test_upload_paths_give_the_same_records(prec):
+    """pic_init reads the particle arrays in place where the device can, or
+    copies them in chunks: the same records either way, and the same ids."""
+    wl = I.small(nx=16, ny=16, nz=32, n_e=40000, n_i=30000, grains=2)
+    parts = I.sample_particles(wl)
+    a = P.Run(wl, parts, prec=prec, stream=_stream())
+    b = P.Run(wl, parts, prec=prec, flags=P.PIC_F_STAGE_COPY, stream=_stream())
+    for sp in range(2):
+        xa, va, ia = a.particles(sp)
+        xb, vb, ib = b.particles(sp)
+        assert np.array_equal(ia, ib) and np.array_equal(xa, xb) and np.array_equal(va, vb)
+        assert np.array_equal(np.sort(ia), np.sort(parts[sp][2]))
+    assert np.array_equal(a.rho(), b.rho())
+    a.close()
+    b.close()
