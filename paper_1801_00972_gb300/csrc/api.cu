@@ -4,12 +4,9 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
-#include <atomic>
 #include <memory>
-#include <mutex>
 #include <new>
 #include <string>
-#include <thread>
 #include <vector>
 
 #include "pic_internal.cuh"
