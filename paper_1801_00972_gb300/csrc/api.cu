@@ -648,19 +648,44 @@ pic_status init_run(const pic_mesh* mesh, const pic_electrodes* el, const pic_ga
     }
     if (e != cudaSuccess) { destroy(c); return cuda_fail(nullptr, e, "upload"); }
 
-    // ---- unit-charge mesh field of each grain on its region nodes (Eq. 5)
+    // ---- unit-charge mesh field of each grain on its region nodes (Eq. 5), by
+    // superposition: one solve per node plane that the grains' cell corners lie
+    // on, for a unit charge on node (0, 0, k) of that plane (the mesh is periodic
+    // in x and y, so a unit charge on node (i, j, k) gives the same potential
+    // moved by (i, j)); each grain's table is then the sum of its 8 corners'
+    // moved potentials with its CIC weights (launch_grain_tables_sup)
     {
         const double dx = mesh->dx;
         const double scale1 = ((1.0 / (dx * dx * dx)) * 0x1p-42) / kEPS0;
-        std::vector<unsigned long long> one(2 * ng1, 0);
-        for (int g = 0; g < c->ng; ++g) {
-            // deposit a unit charge at grain g alone: set its count so that net = +1
-            std::fill(one.begin(), one.end(), 0ull);
-            one[2 * g + 1] = 1;
-            cudaMemcpyAsync(c->gabs, one.data(), sizeof(unsigned long long) * 2 * ng1, cudaMemcpyHostToDevice,
-                            c->stream);
+        std::vector<int> plane((size_t)nz + 1, -1), planes;
+        for (int g = 0; g < c->ng; ++g)
+            for (int dz = 0; dz < 2; ++dz) {
+                const int k = gcell[3 * g + 2] + dz;
+                if (plane[k] < 0) {
+                    plane[k] = (int)planes.size();
+                    planes.push_back(k);
+                }
+            }
+        double* blk = nullptr;
+        int* dplane = nullptr;
+        cudaError_t eg = cudaSuccess;
+        if (!planes.empty()) {
+            eg = cudaMalloc(&blk, sizeof(double) * 343 * planes.size());
+            if (eg == cudaSuccess) eg = cudaMalloc(&dplane, sizeof(int) * plane.size());
+            if (eg == cudaSuccess)
+                eg = cudaMemcpy(dplane, plane.data(), sizeof(int) * plane.size(), cudaMemcpyHostToDevice);
+        }
+        if (eg != cudaSuccess) {
+            cudaFree(blk);
+            cudaFree(dplane);
+            destroy(c);
+            return cuda_fail(nullptr, eg, "grain tables");
+        }
+        const unsigned long long unit = 1ull << 42;   // one elementary charge in the deposit's fixed point
+        for (size_t q = 0; q < planes.size(); ++q) {
             cudaMemsetAsync(c->rq, 0, sizeof(unsigned long long) * nodes, c->stream);
-            launch_grains(c);
+            cudaMemcpyAsync(c->rq + (size_t)planes[q] * (size_t)nx * (size_t)ny, &unit, sizeof unit,
+                            cudaMemcpyHostToDevice, c->stream);
             cudaMemsetAsync(c->phi, 0, sizeof(double) * nodes, c->stream);
             if (c->phi2) cudaMemsetAsync(c->phi2, 0, sizeof(float2) * nodes, c->stream);
             launch_rhs(c, scale1, 0.0, 0.0, false);
@@ -668,12 +693,19 @@ pic_status init_run(const pic_mesh* mesh, const pic_electrodes* el, const pic_ga
             double res = 0;
             const pic_status s = mg_solve(c, 0.0, 0.0, 1e-12, 200, &it, &res);
             if (s != PIC_OK) {
+                cudaFree(blk);
+                cudaFree(dplane);
                 destroy(c);
                 return fail(nullptr, s, "grain field solve did not converge");
             }
             phi_sync_f64(c);
-            launch_grain_table(c, g);
+            launch_green_block(c, planes[q], blk + (size_t)343 * q);
         }
+        if (!planes.empty()) launch_grain_tables_sup(c, blk, dplane);
+        eg = cudaStreamSynchronize(c->stream);
+        cudaFree(blk);
+        cudaFree(dplane);
+        if (eg != cudaSuccess) { destroy(c); return cuda_fail(nullptr, eg, "grain tables"); }
         cudaMemsetAsync(c->gabs, 0, sizeof(unsigned long long) * 2 * ng1, c->stream);
         cudaMemsetAsync(c->phi, 0, sizeof(double) * nodes, c->stream);
         if (c->phi2) cudaMemsetAsync(c->phi2, 0, sizeof(float2) * 2 * nodes, c->stream);

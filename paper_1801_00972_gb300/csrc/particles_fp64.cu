@@ -581,6 +581,87 @@ __global__ void k_grain_table(int nx, int ny, int nz, double dx, const double* p
         o[2] = (phi[n - P] - phi[n + P]) / h2;
 }
 
+// The unit-charge tables by superposition: the mesh is periodic in x and y,
+// so the potential of a unit charge on node (i, j, k) is that of a unit charge
+// on node (0, 0, k) moved by (i, j).  One solve per node plane k that some
+// grain's cell corners lie on gives the potential of a unit charge at (0, 0, k);
+// k_green_block keeps its values at offsets -3..3 in x, y and z around that
+// node.  A grain's unit charge is its CIC deposit on the 8 corners of its cell
+// (the weights of k_grains, summing to 2^42), so its potential near the grain
+// is the weighted sum of the 8 corners' moved blocks, and k_grain_table_sup
+// takes its table from that sum with the differences of k_grain_table.
+constexpr int kGreenR = 3, kGreenW = 2 * kGreenR + 1;
+
+__global__ void k_green_block(int nx, int ny, int nz, const double* phi, int k, double* blk)
+{
+    const int t = threadIdx.x;
+    if (t >= kGreenW * kGreenW * kGreenW) return;
+    const int dx = t % kGreenW - kGreenR, dy = (t / kGreenW) % kGreenW - kGreenR, dz = t / (kGreenW * kGreenW) - kGreenR;
+    const int kk = k + dz;
+    double v = 0.0;
+    if (kk >= 0 && kk <= nz) {
+        const int i = (dx % nx + nx) % nx, j = (dy % ny + ny) % ny;
+        v = phi[((size_t)kk * ny + j) * nx + i];
+    }
+    blk[t] = v;
+}
+
+__device__ __forceinline__ int wrap_off(int d, int n)
+{
+    if (2 * d > n) d -= n;
+    if (2 * d < -n) d += n;
+    return d;
+}
+
+// potential of grain gi's unit charge at node (i, j, k) (i, j already wrapped)
+__device__ double sup_phi(const Geo& g, const double* blk, const int* plane, const int c[3], const long long w[3][2],
+                          int i, int j, int k)
+{
+    double s = 0.0;
+#pragma unroll
+    for (int dz = 0; dz < 2; ++dz)
+#pragma unroll
+        for (int dy = 0; dy < 2; ++dy)
+#pragma unroll
+            for (int di = 0; di < 2; ++di) {
+                const int ci = (c[0] + di) % g.nx, cj = (c[1] + dy) % g.ny, ck = c[2] + dz;
+                const int ox = wrap_off(i - ci, g.nx), oy = wrap_off(j - cj, g.ny), oz = k - ck;
+                const double wt = (double)(w[0][di] * w[1][dy] * w[2][dz]) * 0x1p-42;
+                const double* b = blk + (size_t)plane[ck] * (kGreenW * kGreenW * kGreenW);
+                s = s + wt * b[((oz + kGreenR) * kGreenW + (oy + kGreenR)) * kGreenW + (ox + kGreenR)];
+            }
+    return s;
+}
+
+__global__ void k_grain_table_sup(Geo g, const double* gpos, const int* gcell, const double* blk, const int* plane,
+                                  double* tab)
+{
+    const int gi = blockIdx.x, t = threadIdx.x;
+    if (t >= 64) return;
+    const double x[3] = {gpos[3 * gi], gpos[3 * gi + 1], gpos[3 * gi + 2]};
+    int c[3];
+    double f[3];
+    long long w[3][2];
+    locate(g, x, c, f);
+    qweights(f, w);
+    const int nx = g.nx, ny = g.ny, nz = g.nz;
+    const int li = t % 4, lj = (t / 4) % 4, lk = t / 16;
+    const int i = ((gcell[3 * gi] - 1 + li) % nx + nx) % nx;
+    const int j = ((gcell[3 * gi + 1] - 1 + lj) % ny + ny) % ny;
+    const int k = gcell[3 * gi + 2] - 1 + lk;
+    const double h2 = 2.0 * g.dx;
+    auto ph = [&](int a, int b, int z) { return sup_phi(g, blk, plane, c, w, a, b, z); };
+    double* o = tab + ((size_t)gi * 64 + t) * 3;
+    o[0] = (ph((i + nx - 1) % nx, j, k) - ph((i + 1) % nx, j, k)) / h2;
+    o[1] = (ph(i, (j + ny - 1) % ny, k) - ph(i, (j + 1) % ny, k)) / h2;
+    if (k == 0)
+        o[2] = ((3.0 * ph(i, j, k) - 4.0 * ph(i, j, k + 1)) + ph(i, j, k + 2)) / h2;
+    else if (k == nz)
+        o[2] = ((4.0 * ph(i, j, k - 1) - 3.0 * ph(i, j, k)) - ph(i, j, k - 2)) / h2;
+    else
+        o[2] = (ph(i, j, k - 1) - ph(i, j, k + 1)) / h2;
+}
+
 // node moments: CIC sums of 1 and v per species (double atomics), into the
 // slice of the sample's rf phase bin
 __global__ void k_moments64(Geo g, const double4* pos, const double4* vel, const unsigned long long* nslot, int sp,
@@ -870,6 +951,19 @@ void launch_grain_table(pic_ctx* c, int gi)
     k_grain_table<<<1, 64, 0, c->stream>>>(c->nx, c->ny, c->nz, c->dx, c->phi, c->gcell, gi, c->gtab);
     c->launches += 1;
 }
+void launch_green_block(pic_ctx* c, int k, double* blk)
+{
+    k_green_block<<<1, 352, 0, c->stream>>>(c->nx, c->ny, c->nz, c->phi, k, blk);
+    c->launches += 1;
+}
+
+void launch_grain_tables_sup(pic_ctx* c, const double* blk, const int* plane)
+{
+    if (c->ng == 0) return;
+    k_grain_table_sup<<<c->ng, 64, 0, c->stream>>>(geo(c), c->gpos, c->gcell, blk, plane, c->gtab);
+    c->launches += 1;
+}
+
 void launch_init_plasma(pic_ctx* c, int sp, int64_t n, uint32_t id0, double t_ev)
 {
     if (n <= 0) return;

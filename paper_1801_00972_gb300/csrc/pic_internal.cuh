@@ -314,6 +314,8 @@ void launch_grains(pic_ctx* c);                  // Q from counts, grain CIC int
 void launch_grain_table(pic_ctx* c, int g);      // E of phi on grain g's 4x4x4 region nodes
 // the initial plasma of species sp drawn from the seed (ids id0 ..), either layout
 void launch_init_plasma(pic_ctx* c, int sp, int64_t n, uint32_t id0, double t_ev);
+void launch_green_block(pic_ctx* c, int k, double* blk);   // phi near (0, 0, k) after a unit charge there
+void launch_grain_tables_sup(pic_ctx* c, const double* blk, const int* plane);   // every grain's table from them
 void launch_stage_particles(pic_ctx* c, int sp, const double* x, const double* v, const uint32_t* id, int64_t n,
                             int64_t q0, unsigned int* bad, unsigned int* max_id);   // caller particles into records
 
