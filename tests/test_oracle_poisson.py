@@ -137,3 +137,54 @@ def test_grain_tables_equal_a_full_solve(shape, grains):
                     k, j, i = c[2] - 1 + lk, (c[1] - 1 + lj) % ny, (c[0] - 1 + li) % nx
                     want[lk, lj, li] = ex[k, j, i], ey[k, j, i], ez[k, j, i]
         assert np.max(np.abs(tab[g] - want)) <= 1e-11 * np.max(np.abs(want)), g
+
+
+def test_unit_charge_tables_by_superposition_of_moved_node_solves():
+    """The construction the CUDA library uses for the grain tables, checked on
+    the exact solve: with x and y periodic, the potential of a unit charge on
+    node (i, j, k) is that of a unit charge on node (0, 0, k) moved by (i, j),
+    so a grain's table is the CIC-weighted sum of its 8 corners' moved node
+    potentials, one solve per corner plane; it equals the oracle's table."""
+    from paper_1801_00972_gb300 import inputs as I
+    nx, ny, nz = 12, 10, 14
+    wl = I.small(nx=nx, ny=ny, nz=nz, n_e=0, n_i=0, grains=3, seed=9)
+    s = O.Sim(wl, [(np.zeros((0, 3)), np.zeros((0, 3)), np.zeros(0, np.uint32))] * 2)
+    tab = s.gtab()
+    eps0, dx = 8.8541878128e-12, wl.dx
+    unit = 1.0 / dx ** 3 / eps0          # one coulomb on one node
+
+    def node_solve(i, j, k):
+        f = np.zeros((nz + 1, ny, nx))
+        f[k, j, i] = unit
+        return O.poisson(nx, ny, nz, dx, f, 0.0, 0.0)
+
+    # translation invariance in x and y on the exact solve
+    base = node_solve(0, 0, 5)
+    moved = np.roll(np.roll(base, 3, axis=2), 7, axis=1)
+    direct = node_solve(3, 7, 5)
+    assert np.max(np.abs(moved - direct)) <= 1e-12 * np.max(np.abs(direct))
+    # a different plane is a different solution (the electrodes break z invariance)
+    assert np.max(np.abs(np.roll(node_solve(0, 0, 6), -1, axis=0) - base)) > 1e-3 * np.max(np.abs(base))
+    planes = {}
+    for g, p in enumerate(wl.grain_pos):
+        q = p / dx
+        c = np.floor(q).astype(int)
+        a = np.clip(np.rint((q - c) * 16384).astype(np.int64), 0, 16384)
+        phi = np.zeros((nz + 1, ny, nx))
+        for dz in (0, 1):
+            k = c[2] + dz
+            if k not in planes:
+                planes[k] = node_solve(0, 0, k)
+            for dy in (0, 1):
+                for di in (0, 1):
+                    wgt = ((a[0] if di else 16384 - a[0]) * (a[1] if dy else 16384 - a[1])
+                           * (a[2] if dz else 16384 - a[2])) * 2.0 ** -42
+                    phi += wgt * np.roll(np.roll(planes[k], (c[1] + dy) % ny, axis=1), (c[0] + di) % nx, axis=2)
+        ex, ey, ez = O.efield(nx, ny, nz, dx, phi)
+        want = np.zeros((4, 4, 4, 3))
+        for lk in range(4):
+            for lj in range(4):
+                for li in range(4):
+                    k, j, i = c[2] - 1 + lk, (c[1] - 1 + lj) % ny, (c[0] - 1 + li) % nx
+                    want[lk, lj, li] = ex[k, j, i], ey[k, j, i], ez[k, j, i]
+        assert np.max(np.abs(tab[g] - want)) <= 1e-11 * np.max(np.abs(want)), g
